@@ -1,0 +1,521 @@
+"""RNS-CKKS oracle (O3): the scheme the paper evaluates its CNNs with.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+The paper uses CKKS through SEAL (Sec. II-B: Add, Mul and Rot on ciphertexts,
+levels and depth; Table II parameters).  It does not spell out the RNS
+details, so this module fixes them from the published scheme descriptions and
+records each choice (the "readings"):
+
+* Primes (reading C8): for each requested bit size, in order (data primes, then
+  special primes), the largest prime q < 2^bits with q = 1 mod 2N not already
+  taken.  psi = the smallest primitive 2N-th root of unity mod q.
+* Ciphertexts are (c0, c1) with m = c0 + c1*s, limbs q_0..q_{L'-1} in natural
+  order evaluation form.  Comparisons with other implementations are made in
+  coefficient form (``to_coeff``), which is independent of any NTT ordering.
+* Randomness (reading C9): counter-based SplitMix64 words (``o_rand_word``);
+  stream id = purpose<<56 | key_id<<32 | digit<<16 | limb.  Secret s and
+  encryption u ternary, errors centred binomial eta=21, uniform a = floor(r*q/2^64),
+  all sampled in coefficient form.
+* Hybrid key switching (reading C6, Han-Ki 2020): digits are consecutive groups
+  of alpha = ceil((L+1)/dnum) active limbs; ModUp is fast base conversion
+  without correction; inner product over Q_l u P; ModDown without rounding
+  correction.  Hoisted rotations apply sigma_g to the ModUp'ed digits.
+* Rotation (reading C5): Rot(v, r) moves slot j+r to slot j (paper Sec. II-B),
+  Galois element g = 5^(r mod N/2) mod 2N.
+* Rescale (reading C7): centred remainder of the top limb; new scale =
+  (scale)/q_top in FP64.
+* Public-key encryption (reading C14): c = (u*pk0 + e0 + m, u*pk1 + e1).
+* Decryption decodes from limb q_0 alone (valid while |m| < q_0/2).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_dp = ctypes.POINTER(ctypes.c_double)
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        L = ctypes.CDLL(_build.build())
+        u64, i32, vp, dbl = ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+        sig = {
+            "o_mulmod": (u64, [u64, u64, u64]),
+            "o_powmod": (u64, [u64, u64, u64]),
+            "o_invmod": (u64, [u64, u64]),
+            "o_ntt": (None, [vp, i32, u64, u64]),
+            "o_intt": (None, [vp, i32, u64, u64]),
+            "o_ntt_limbs": (None, [vp, i32, i32, vp, vp]),
+            "o_intt_limbs": (None, [vp, i32, i32, vp, vp]),
+            "o_mul": (None, [vp, vp, vp, i32, i32, vp]),
+            "o_add": (None, [vp, vp, vp, i32, i32, vp]),
+            "o_sub": (None, [vp, vp, vp, i32, i32, vp]),
+            "o_muladd": (None, [vp, vp, vp, i32, i32, vp]),
+            "o_reduce_signed": (None, [vp, vp, i32, i32, vp]),
+            "o_automorph_coeff": (None, [vp, vp, i32, i32, u64, vp]),
+            "o_automorph_eval": (None, [vp, vp, i32, i32, u64]),
+            "o_bconv": (None, [vp, vp, i32, vp, i32, vp, i32]),
+            "o_rescale": (None, [vp, vp, i32, i32, vp, vp]),
+            "o_moddown": (None, [vp, vp, i32, i32, i32, vp, vp, vp, vp]),
+            "o_modup_digit": (None, [vp, vp, i32, i32, i32, i32, i32, vp, vp, vp, vp]),
+            "o_rand_word": (u64, [u64, u64, u64]),
+            "o_sample_ternary": (None, [vp, u64, u64, i32]),
+            "o_sample_cbd": (None, [vp, u64, u64, i32]),
+            "o_sample_uniform": (None, [vp, u64, u64, i32, u64]),
+            "o_encode": (ctypes.c_int, [vp, vp, vp, i32, dbl]),
+            "o_decode": (None, [vp, vp, vp, i32]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"], "oracle arrays must be C-contiguous"
+    # data_as keeps a reference to the array for as long as the pointer lives
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _u(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint64))
+
+
+# ----------------------------------------------------------------- primes
+_MR_BASES = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37)
+
+
+def is_prime(n: int) -> bool:
+    """Deterministic Miller-Rabin; the first twelve prime bases are exact for n < 3.3e24."""
+    if n < 2:
+        return False
+    for p in _MR_BASES:
+        if n % p == 0:
+            return n == p
+    d, r = n - 1, 0
+    while d % 2 == 0:
+        d //= 2
+        r += 1
+    for a in _MR_BASES:
+        x = pow(a, d, n)
+        if x in (1, n - 1):
+            continue
+        for _ in range(r - 1):
+            x = x * x % n
+            if x == n - 1:
+                break
+        else:
+            return False
+    return True
+
+
+def gen_primes(bit_sizes, logn: int) -> list[int]:
+    """Largest primes q < 2^bits with q = 1 mod 2N, distinct, in request order."""
+    m = 2 << logn
+    taken: list[int] = []
+    for bits in bit_sizes:
+        c = ((1 << bits) - 1) // m * m + 1
+        if c >= (1 << bits):
+            c -= m
+        while c > m:
+            if c not in taken and is_prime(c):
+                taken.append(c)
+                break
+            c -= m
+        else:
+            raise ValueError(f"no {bits}-bit prime = 1 mod {m}")
+    return taken
+
+
+def smallest_psi(q: int, logn: int) -> int:
+    """Smallest primitive 2N-th root of unity modulo q."""
+    n = 1 << logn
+    m = 2 * n
+    assert (q - 1) % m == 0
+    root = None
+    for g in range(2, 1 << 20):
+        r = pow(g, (q - 1) // m, q)
+        if pow(r, n, q) == q - 1:
+            root = r
+            break
+    assert root is not None
+    best, x, r2 = root, root, root * root % q
+    for _ in range(n - 1):  # all odd powers root^(2k+1)
+        x = x * r2 % q
+        if x < best:
+            best = x
+    return best
+
+
+# ------------------------------------------------------------- randomness
+PURPOSE = {"sk": 1, "pk_a": 2, "pk_e": 3, "ksk_a": 4, "ksk_e": 5,
+           "enc_u": 6, "enc_e0": 7, "enc_e1": 8}
+
+
+def stream_id(purpose: str, key_id: int = 0, digit: int = 0, limb: int = 0) -> int:
+    return (PURPOSE[purpose] << 56) | (key_id << 32) | (digit << 16) | limb
+
+
+def sample_ternary(seed, stream, n):
+    out = np.zeros(n, dtype=np.int64)
+    lib().o_sample_ternary(_p(out), seed, stream, n)
+    return out
+
+
+def sample_cbd(seed, stream, n):
+    out = np.zeros(n, dtype=np.int64)
+    lib().o_sample_cbd(_p(out), seed, stream, n)
+    return out
+
+
+def sample_uniform(seed, stream, n, q):
+    out = np.zeros(n, dtype=np.uint64)
+    lib().o_sample_uniform(_p(out), seed, stream, n, q)
+    return out
+
+
+def galois_elt(r: int, logn: int) -> int:
+    """Galois element of a left rotation by r slots: 5^(r mod N/2) mod 2N."""
+    m = 1 << (logn - 1)
+    return pow(5, r % m, 2 << logn)
+
+
+# ------------------------------------------------------------ the scheme
+@dataclass
+class Ct:
+    """A ciphertext (c0, c1): array [2][L'][N] of residues, natural-order eval form."""
+    d: np.ndarray
+    scale: float
+
+    @property
+    def lp(self) -> int:
+        return self.d.shape[1]
+
+    def copy(self) -> "Ct":
+        return Ct(self.d.copy(), self.scale)
+
+
+@dataclass
+class Keys:
+    s: np.ndarray                     # [L+1+K][N] eval
+    pk: np.ndarray                    # [2][L+1][N]
+    rlk: tuple | None = None          # (b [dnum][L+1+K][N], a [...])
+    gk: dict = field(default_factory=dict)  # galois element -> (b, a)
+
+
+class Ckks:
+    def __init__(self, logn: int, data_bits, special_bits, dnum: int, log2_scale: float, seed: int):
+        self.logn = logn
+        self.n = 1 << logn
+        allp = gen_primes(list(data_bits) + list(special_bits), logn)
+        self.q = allp[: len(data_bits)]
+        self.p = allp[len(data_bits):]
+        self.L1 = len(self.q)            # number of data primes (L+1)
+        self.K = len(self.p)
+        self.dnum = dnum
+        self.alpha = -(-self.L1 // dnum)
+        self.scale = 2.0 ** log2_scale
+        self.seed = seed
+        self.qpsi = [smallest_psi(q, logn) for q in self.q]
+        self.ppsi = [smallest_psi(p, logn) for p in self.p]
+        self.keys: Keys | None = None
+
+    # ---- bases
+    def primes_all(self):
+        return self.q + self.p
+
+    def qa(self, lp):
+        return _u(self.q[:lp])
+
+    def qpsia(self, lp):
+        return _u(self.qpsi[:lp])
+
+    def ext_basis(self, lp):
+        """(primes, psis) of Q_l u P as arrays."""
+        return _u(self.q[:lp] + self.p), _u(self.qpsi[:lp] + self.ppsi)
+
+    # ---- transforms
+    def ntt(self, a: np.ndarray, primes, psis) -> np.ndarray:
+        a = _u(a).copy()
+        lib().o_ntt_limbs(_p(a), a.shape[0], self.logn, _p(_u(primes)), _p(_u(psis)))
+        return a
+
+    def intt(self, a: np.ndarray, primes, psis) -> np.ndarray:
+        a = _u(a).copy()
+        lib().o_intt_limbs(_p(a), a.shape[0], self.logn, _p(_u(primes)), _p(_u(psis)))
+        return a
+
+    def reduce_signed(self, v: np.ndarray, primes) -> np.ndarray:
+        v = np.ascontiguousarray(v, dtype=np.int64)
+        primes = _u(primes)
+        out = np.zeros((len(primes), self.n), dtype=np.uint64)
+        lib().o_reduce_signed(_p(out), _p(v), len(primes), self.n, _p(primes))
+        return out
+
+    def _bin(self, fn, a, b, primes):
+        primes = _u(primes)
+        a, b = _u(a), _u(b)
+        out = np.zeros_like(a)
+        getattr(lib(), fn)(_p(out), _p(a), _p(b), a.shape[0], self.n, _p(primes))
+        return out
+
+    def mul(self, a, b, primes):
+        return self._bin("o_mul", a, b, primes)
+
+    def add(self, a, b, primes):
+        return self._bin("o_add", a, b, primes)
+
+    def sub(self, a, b, primes):
+        return self._bin("o_sub", a, b, primes)
+
+    def neg(self, a, primes):
+        return self.sub(np.zeros_like(a), a, primes)
+
+    def automorph_eval(self, a, g):
+        a = _u(a)
+        out = np.zeros_like(a)
+        lib().o_automorph_eval(_p(out), _p(a), a.shape[0], self.logn, g)
+        return out
+
+    def automorph_coeff(self, a, g, primes):
+        a = _u(a)
+        out = np.zeros_like(a)
+        lib().o_automorph_coeff(_p(out), _p(a), a.shape[0], self.logn, g, _p(_u(primes)))
+        return out
+
+    # ---- encoding
+    def encode_coeffs(self, z, scale: float) -> np.ndarray:
+        """Slot values (length N/2, real or complex) -> rounded integer coefficients."""
+        z = np.asarray(z)
+        m = self.n // 2
+        assert z.shape == (m,)
+        zre = np.ascontiguousarray(z.real, dtype=np.float64)
+        zim = np.ascontiguousarray(z.imag if np.iscomplexobj(z) else np.zeros(m), dtype=np.float64)
+        out = np.zeros(self.n, dtype=np.int64)
+        rc = lib().o_encode(_p(out), _p(zre), _p(zim), self.logn, float(scale))
+        if rc != 0:
+            raise OverflowError("encoded coefficient exceeds 2^63")
+        return out
+
+    def encode(self, z, scale: float, lp: int) -> np.ndarray:
+        """Plaintext at level lp in eval form: [lp][N]."""
+        return self.ntt(self.reduce_signed(self.encode_coeffs(z, scale), self.q[:lp]),
+                        self.q[:lp], self.qpsi[:lp])
+
+    def decode_coeffs(self, coef: np.ndarray) -> np.ndarray:
+        coef = np.ascontiguousarray(coef, dtype=np.float64)
+        m = self.n // 2
+        zre = np.zeros(m)
+        zim = np.zeros(m)
+        lib().o_decode(_p(zre), _p(zim), _p(coef), self.logn)
+        return zre + 1j * zim
+
+    # ---- keys
+    def keygen(self, rot_steps=()):
+        n, seed = self.n, self.seed
+        allq = self.primes_all()
+        allpsi = self.qpsi + self.ppsi
+        s_int = sample_ternary(seed, stream_id("sk"), n)
+        s = self.ntt(self.reduce_signed(s_int, allq), allq, allpsi)
+        # public key over the data primes
+        qd = self.q
+        a = np.stack([sample_uniform(seed, stream_id("pk_a", 0, 0, l), n, qd[l]) for l in range(self.L1)])
+        a = self.ntt(a, qd, self.qpsi)
+        e = self.ntt(self.reduce_signed(sample_cbd(seed, stream_id("pk_e"), n), qd), qd, self.qpsi)
+        pk0 = self.add(self.neg(self.mul(a, s[: self.L1], qd), qd), e, qd)
+        self.keys = Keys(s=s, pk=np.stack([pk0, a]))
+        s2 = self.mul(s, s, allq)
+        self.keys.rlk = self.make_ksk(s2, key_id=0)
+        for r in rot_steps:
+            self.add_galois_key(galois_elt(r, self.logn))
+        return self.keys
+
+    def add_galois_key(self, g: int):
+        if g in self.keys.gk or g == 1:
+            return
+        sg = self.automorph_eval(self.keys.s, g)
+        self.keys.gk[g] = self.make_ksk(sg, key_id=g)
+
+    def P_mod(self, qi: int) -> int:
+        v = 1
+        for p in self.p:
+            v = v * p % qi
+        return v
+
+    def make_ksk(self, sprime: np.ndarray, key_id: int):
+        """Hybrid key-switching key: b_j = -a_j s + e_j + P*Qtilde_j*s' over Q u P."""
+        n, seed = self.n, self.seed
+        allq = self.primes_all()
+        allpsi = self.qpsi + self.ppsi
+        nt = len(allq)
+        bs, as_ = [], []
+        for j in range(self.dnum):
+            a = np.stack([sample_uniform(seed, stream_id("ksk_a", key_id, j, t), n, allq[t]) for t in range(nt)])
+            a = self.ntt(a, allq, allpsi)
+            e = self.ntt(self.reduce_signed(sample_cbd(seed, stream_id("ksk_e", key_id, j), n), allq), allq, allpsi)
+            b = self.add(self.neg(self.mul(a, self.keys.s, allq), allq), e, allq)
+            for t in range(j * self.alpha, min((j + 1) * self.alpha, self.L1)):
+                pm = np.full(n, self.P_mod(self.q[t]), dtype=np.uint64)
+                term = self.mul(pm[None, :], sprime[t:t + 1], [self.q[t]])
+                b[t:t + 1] = self.add(b[t:t + 1], term, [self.q[t]])
+            bs.append(b)
+            as_.append(a)
+        return np.stack(bs), np.stack(as_)
+
+    # ---- encryption
+    def encrypt_coeffs(self, m_int: np.ndarray, scale: float, enc_seed: int, lp: int | None = None) -> Ct:
+        lp = self.L1 if lp is None else lp
+        n = self.n
+        q, psi = self.q[:lp], self.qpsi[:lp]
+        u = self.ntt(self.reduce_signed(sample_ternary(enc_seed, stream_id("enc_u"), n), q), q, psi)
+        e0 = sample_cbd(enc_seed, stream_id("enc_e0"), n)
+        e1 = sample_cbd(enc_seed, stream_id("enc_e1"), n)
+        me = self.ntt(self.reduce_signed(m_int + e0, q), q, psi)
+        e1 = self.ntt(self.reduce_signed(e1, q), q, psi)
+        c0 = self.add(self.mul(u, self.keys.pk[0][:lp], q), me, q)
+        c1 = self.add(self.mul(u, self.keys.pk[1][:lp], q), e1, q)
+        return Ct(np.stack([c0, c1]), scale)
+
+    def encrypt(self, slots, enc_seed: int, lp: int | None = None) -> Ct:
+        return self.encrypt_coeffs(self.encode_coeffs(slots, self.scale), self.scale, enc_seed, lp)
+
+    def decrypt_coeffs(self, ct: Ct) -> np.ndarray:
+        """Centred integer coefficients of m = c0 + c1*s, from limb q_0."""
+        lp = ct.lp
+        q = self.q[:lp]
+        m = self.add(ct.d[0], self.mul(ct.d[1], self.keys.s[:lp], q), q)
+        m0 = self.intt(m[:1], q[:1], self.qpsi[:1])[0]
+        q0 = self.q[0]
+        return np.where(m0 > q0 // 2, m0.astype(np.int64) - np.int64(q0), m0.astype(np.int64))
+
+    def decrypt(self, ct: Ct) -> np.ndarray:
+        coef = self.decrypt_coeffs(ct)
+        return self.decode_coeffs(coef.astype(np.float64) / ct.scale).real
+
+    # ---- ciphertext arithmetic
+    def to_coeff(self, ct: Ct) -> np.ndarray:
+        q, psi = self.q[: ct.lp], self.qpsi[: ct.lp]
+        return np.stack([self.intt(ct.d[0], q, psi), self.intt(ct.d[1], q, psi)])
+
+    def ct_add(self, a: Ct, b: Ct) -> Ct:
+        assert a.lp == b.lp and a.scale == b.scale, "level/scale mismatch"
+        q = self.q[: a.lp]
+        return Ct(np.stack([self.add(a.d[0], b.d[0], q), self.add(a.d[1], b.d[1], q)]), a.scale)
+
+    def ct_add_plain(self, a: Ct, pt: np.ndarray) -> Ct:
+        q = self.q[: a.lp]
+        return Ct(np.stack([self.add(a.d[0], pt, q), a.d[1].copy()]), a.scale)
+
+    def ct_mul_plain(self, a: Ct, pt: np.ndarray, pt_scale: float) -> Ct:
+        q = self.q[: a.lp]
+        return Ct(np.stack([self.mul(a.d[0], pt, q), self.mul(a.d[1], pt, q)]), a.scale * pt_scale)
+
+    def rescale(self, a: Ct) -> Ct:
+        lp = a.lp
+        assert lp >= 2, "level exhausted"
+        q, psi = _u(self.q[:lp]), _u(self.qpsi[:lp])
+        out = np.zeros((2, lp - 1, self.n), dtype=np.uint64)
+        for k in range(2):
+            src = np.ascontiguousarray(a.d[k])
+            dst = np.zeros((lp - 1, self.n), dtype=np.uint64)
+            lib().o_rescale(_p(dst), _p(src), lp, self.logn, _p(q), _p(psi))
+            out[k] = dst
+        return Ct(out, a.scale / float(self.q[lp - 1]))
+
+    # ---- key switching
+    def digits(self, lp: int):
+        return [(lo, min(lo + self.alpha, lp)) for lo in range(0, lp, self.alpha)]
+
+    def modup(self, x: np.ndarray) -> np.ndarray:
+        """x [lp][N] eval -> [beta][lp+K][N] eval (one extended copy per digit)."""
+        lp = x.shape[0]
+        x = _u(x)
+        q, qpsi, p, ppsi = _u(self.q[:lp]), _u(self.qpsi[:lp]), _u(self.p), _u(self.ppsi)
+        ds = self.digits(lp)
+        out = np.zeros((len(ds), lp + self.K, self.n), dtype=np.uint64)
+        for j, (lo, hi) in enumerate(ds):
+            o = np.zeros((lp + self.K, self.n), dtype=np.uint64)
+            lib().o_modup_digit(_p(o), _p(x), lo, hi, lp, self.K, self.logn,
+                                _p(q), _p(qpsi), _p(p), _p(ppsi))
+            out[j] = o
+        return out
+
+    def key_limbs(self, key_poly: np.ndarray, lp: int) -> np.ndarray:
+        """Restrict a key polynomial over Q u P to Q_l u P."""
+        return np.ascontiguousarray(np.concatenate([key_poly[:lp], key_poly[self.L1:]], axis=0))
+
+    def ks_inner(self, digs: np.ndarray, key, g: int = 1):
+        lp = digs.shape[1] - self.K
+        basis, _ = self.ext_basis(lp)
+        kb, ka = key
+        acc0 = np.zeros((lp + self.K, self.n), dtype=np.uint64)
+        acc1 = np.zeros_like(acc0)
+        for j in range(digs.shape[0]):
+            d = digs[j] if g == 1 else self.automorph_eval(digs[j], g)
+            d = _u(d)
+            lib().o_muladd(_p(acc0), _p(d), _p(self.key_limbs(kb[j], lp)), lp + self.K, self.n, _p(basis))
+            lib().o_muladd(_p(acc1), _p(d), _p(self.key_limbs(ka[j], lp)), lp + self.K, self.n, _p(basis))
+        return acc0, acc1
+
+    def moddown(self, acc: np.ndarray) -> np.ndarray:
+        lp = acc.shape[0] - self.K
+        out = np.zeros((lp, self.n), dtype=np.uint64)
+        lib().o_moddown(_p(out), _p(_u(acc)), lp, self.K, self.logn,
+                        _p(_u(self.q[:lp])), _p(_u(self.qpsi[:lp])), _p(_u(self.p)), _p(_u(self.ppsi)))
+        return out
+
+    def keyswitch(self, x: np.ndarray, key):
+        acc0, acc1 = self.ks_inner(self.modup(x), key)
+        return self.moddown(acc0), self.moddown(acc1)
+
+    def rotate(self, ct: Ct, r: int) -> Ct:
+        """Single rotation: sigma_g on (c0, c1), then key switching of sigma_g(c1)."""
+        g = galois_elt(r, self.logn)
+        if g == 1:
+            return ct.copy()
+        q = self.q[: ct.lp]
+        c0 = self.automorph_eval(ct.d[0], g)
+        c1 = self.automorph_eval(ct.d[1], g)
+        k0, k1 = self.keyswitch(c1, self.keys.gk[g])
+        return Ct(np.stack([self.add(c0, k0, q), k1]), ct.scale)
+
+    def rotate_hoisted(self, ct: Ct, steps) -> dict:
+        """Several rotations of one ciphertext sharing one ModUp of c1."""
+        out = {}
+        digs = None
+        q = self.q[: ct.lp]
+        for r in steps:
+            g = galois_elt(r, self.logn)
+            if g == 1:
+                out[r] = ct.copy()
+                continue
+            if digs is None:
+                digs = self.modup(ct.d[1])
+            acc0, acc1 = self.ks_inner(digs, self.keys.gk[g], g)
+            c0 = self.automorph_eval(ct.d[0], g)
+            out[r] = Ct(np.stack([self.add(c0, self.moddown(acc0), q), self.moddown(acc1)]), ct.scale)
+        return out
+
+    def square(self, ct: Ct) -> Ct:
+        """Ciphertext tensor with itself, relinearisation, rescale (reading C15)."""
+        q = self.q[: ct.lp]
+        a0, a1 = ct.d[0], ct.d[1]
+        d0 = self.mul(a0, a0, q)
+        d1 = self.add(self.mul(a0, a1, q), self.mul(a1, a0, q), q)
+        d2 = self.mul(a1, a1, q)
+        k0, k1 = self.keyswitch(d2, self.keys.rlk)
+        t = Ct(np.stack([self.add(d0, k0, q), self.add(d1, k1, q)]), ct.scale * ct.scale)
+        return self.rescale(t)

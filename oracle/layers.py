@@ -1,0 +1,389 @@
+"""UniHENN layer algorithms and layout planner, written once against a backend.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+A backend supplies slot-vector operations:
+    rot(x, r)            Rot(x, r): left rotation by r slots (paper Sec. II-B)
+    rot_many(x, steps)   several rotations of one input (hoisted on ciphertexts)
+    add(x, y)            Add (C)
+    mul_mask(x, v)       Mul (P) by the slot vector v encoded at scale Delta
+    add_mask(x, v)       Add (P) of v encoded at x's current scale and level
+    rescale(x)           drop one level (identity on cleartext)
+    square(x)            Mul (C) of x by itself, relinearised and rescaled
+Two backends exist: ``slotsim.SlotSim`` (FP64 cleartext, O2) and
+``HeBackend`` below (the CKKS oracle, O3).  Running the same layer code on
+both is what lets the cleartext simulator pin the algorithm and the CKKS
+oracle pin the ciphertexts.
+
+Slot layout (paper Sec. III-A, III-B, V): sample b of a ciphertext starts at
+slot b*stride; inside a sample the value at (row r, column c) of the current
+feature map sits at I*(r*W_img + c), where I is the interval (product of the
+strides and pool sizes so far) and W_img the width of the original input.
+Masks are built over every sample position of the layout (``n_samples``),
+whatever the number of samples a ciphertext actually carries (reading C17).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Layout:
+    W_img: int
+    H_img: int
+    W: int
+    H: int
+    I: int
+    stride: int
+    n_samples: int
+    slots: int
+    dims: int = 2          # 2 (image) or 1 (signal: H_img = H = 1)
+    pending: float = 1.0   # deferred factor of average pooling (Sec. IV-C)
+    prev: str = "input"    # last layer that set the layout: input/conv/avgpool/flatten/fc
+    D: int = 0             # after flatten / FC: values at slots [0, D) of each sample
+
+    @property
+    def flat(self) -> bool:
+        return self.prev in ("flatten", "fc")
+
+
+def input_layout(W_img, H_img, stride, n_samples, slots, dims=2) -> Layout:
+    assert stride * n_samples <= slots, "samples do not fit in the slots"
+    return Layout(W_img, H_img, W_img, H_img, 1, stride, n_samples, slots, dims)
+
+
+def slot_vector(lay: Layout, positions, values) -> np.ndarray:
+    """Slot vector with values[i] at positions[i] of every sample, zero elsewhere."""
+    v = np.zeros(lay.slots)
+    positions = np.asarray(positions, dtype=np.int64)
+    values = np.broadcast_to(np.asarray(values, dtype=np.float64), positions.shape)
+    for b in range(lay.n_samples):
+        v[b * lay.stride + positions] = values
+    return v
+
+
+# --------------------------------------------------------------- layers
+def conv(be, xs, w, bias, S: int, lay: Layout, mode: str = "hoisted"):
+    """Algorithm 1 (Sec. IV-B).  w: [co][ci][K][K] (2-D) or [co][ci][K] (1-D).
+
+    Rotations Rot(C_in(i), I*(k + W_img*j)); per output channel o the sum of
+    Mul(C_rot(i,j,k), K(o,i,j,k)) with K(o,i,j,k) the weight (times the pending
+    pooling factor) at every valid output slot (reading C1), then rescale and
+    Add(bias at the valid output slots, reading C2).  I_out = I*S.
+    mode "hoisted": all rotations of one input share one ModUp (Alg. 1 as printed).
+    mode "incremental": each rotation is taken from the previous one, by I along a
+    kernel row and by I*(W_img - K + 1) at a row change (reading C3 of the prose).
+    """
+    w = np.asarray(w, dtype=np.float64)
+    if w.ndim == 3:
+        w = w[:, :, None, :]
+    co, ci, kh, kw = w.shape
+    assert ci == len(xs)
+    I = lay.I
+    offs = [(j, k) for j in range(kh) for k in range(kw)]
+    step = {o: I * (o[1] + lay.W_img * o[0]) for o in offs}
+    Hout = (lay.H - kh) // S + 1
+    Wout = (lay.W - kw) // S + 1
+    Iout = I * S
+    pos = [Iout * (r * lay.W_img + c) for r in range(Hout) for c in range(Wout)]
+    rots = []
+    for i in range(ci):
+        if mode == "hoisted":
+            rr = be.rot_many(xs[i], [step[o] for o in offs])
+            rots.append({o: rr[step[o]] for o in offs})
+        elif mode == "incremental":
+            rr = {offs[0]: xs[i]}
+            prev = xs[i]
+            for o in offs[1:]:
+                s = I if o[1] > 0 else I * (lay.W_img - kw + 1)
+                prev = be.rot(prev, s)
+                rr[o] = prev
+            rots.append(rr)
+        else:
+            raise ValueError(mode)
+    outs = []
+    for o in range(co):
+        acc = None
+        for i in range(ci):
+            for off in offs:
+                wv = float(w[o, i, off[0], off[1]]) * lay.pending
+                t = be.mul_mask(rots[i][off], slot_vector(lay, pos, wv))
+                acc = t if acc is None else be.add(acc, t)
+        acc = be.rescale(acc)
+        acc = be.add_mask(acc, slot_vector(lay, pos, float(bias[o])))
+        outs.append(acc)
+    return outs, replace(lay, W=Wout, H=Hout, I=Iout, pending=1.0, prev="conv")
+
+
+def conv_steps(lay: Layout, kh: int, kw: int, mode: str = "hoisted"):
+    if mode == "incremental":
+        return sorted({lay.I, lay.I * (lay.W_img - kw + 1)} if kh > 1 else {lay.I})
+    return sorted({lay.I * (k + lay.W_img * j) for j in range(kh) for k in range(kw)} - {0})
+
+
+def avgpool(be, xs, c: int, lay: Layout):
+    """Sec. IV-C: a c x c all-ones 'convolution' with stride c by rotations and
+    additions only (no mask, no level); 1/c^2 is deferred into ``pending``."""
+    ch = c if lay.dims == 2 else 1
+    steps = [lay.I * (k + lay.W_img * j) for j in range(ch) for k in range(c)]
+    outs = []
+    for x in xs:
+        rr = be.rot_many(x, steps)
+        acc = None
+        for s in steps:
+            acc = rr[s] if acc is None else be.add(acc, rr[s])
+        outs.append(acc)
+    Hout = lay.H // c if lay.dims == 2 else 1
+    return outs, replace(lay, W=lay.W // c, H=Hout, I=lay.I * c,
+                         pending=lay.pending / float(c ** lay.dims), prev="avgpool")
+
+
+def square(be, xs, lay: Layout):
+    """Square activation (Sec. IV-F, M2 table): one Mul (C) per channel, 1 level.
+    A pending pooling factor p becomes p^2 (Sec. IV-C)."""
+    return [be.square(x) for x in xs], replace(lay, pending=lay.pending * lay.pending)
+
+
+def flatten(be, xs, lay: Layout):
+    """Sec. IV-E: gather every channel's W x H values into one contiguous block.
+
+    After average pooling (IV-E-2): per column c' a mask carrying the pending
+    factor at I*(r*W_img + c'), rescale, rotate left c'*(I-1), sum.
+    After a convolution (IV-E-1, I > 1 and W > 1): sum of Rot(x, m*(I-1)) for
+    m < I, then per block u < ceil(W/I) a mask of the block's columns, rescale,
+    rotate left u*I*(I-1), sum.
+    Then, when H > 1 (IV-E-3): per row r a mask of the row, rescale, rotate
+    left r*(W_img*I - W), sum.  Finally (IV-E-4) channel o is rotated right by
+    o*W*H and the channels are added.  Readings C12.
+    """
+    I, W, H, Wi = lay.I, lay.W, lay.H, lay.W_img
+    rows = range(H)
+    cur = list(xs)
+    pending = lay.pending
+    if lay.prev == "avgpool":
+        new = []
+        for x in cur:
+            acc = None
+            for c in range(W):
+                pos = [I * (r * Wi + c) for r in rows]
+                t = be.rescale(be.mul_mask(x, slot_vector(lay, pos, pending)))
+                if c:
+                    t = be.rot(t, c * (I - 1))
+                acc = t if acc is None else be.add(acc, t)
+            new.append(acc)
+        cur, pending = new, 1.0
+    elif lay.prev == "conv":
+        assert pending == 1.0
+        if I > 1 and W > 1:
+            new = []
+            for x in cur:
+                rr = be.rot_many(x, [m * (I - 1) for m in range(I)])
+                y = None
+                for m in range(I):
+                    s = m * (I - 1)
+                    y = rr[s] if y is None else be.add(y, rr[s])
+                acc = None
+                for u in range(-(-W // I)):
+                    cols = range(I * u, min(I * u + I, W))
+                    pos = [I * r * Wi + I * I * u + (cc - I * u) for r in rows for cc in cols]
+                    t = be.rescale(be.mul_mask(y, slot_vector(lay, pos, 1.0)))
+                    if u:
+                        t = be.rot(t, u * I * (I - 1))
+                    acc = t if acc is None else be.add(acc, t)
+                new.append(acc)
+            cur = new
+    else:
+        raise ValueError("flatten must follow a convolution or an average pooling")
+    if H > 1:
+        new = []
+        for x in cur:
+            acc = None
+            for r in rows:
+                pos = [I * r * Wi + c for c in range(W)]
+                t = be.rescale(be.mul_mask(x, slot_vector(lay, pos, 1.0)))
+                if r:
+                    t = be.rot(t, r * (Wi * I - W))
+                acc = t if acc is None else be.add(acc, t)
+            new.append(acc)
+        cur = new
+    acc = None
+    for o, x in enumerate(cur):
+        t = be.rot(x, -o * W * H) if o else x
+        acc = t if acc is None else be.add(acc, t)
+    D = len(xs) * W * H
+    return [acc], replace(lay, pending=pending, prev="flatten", D=D, W=D, H=1, I=1)
+
+
+def fc_rot_matrix(M: np.ndarray):
+    """Steps 1-4 of the FC figure (Sec. IV-D, reading C13): pad the columns of
+    M (dout x din) with zeros to W_vec = ceil(din/dout)*dout and build
+    M_rot[o][t] = M_pad[t mod dout][(t + o) mod W_vec]."""
+    dout, din = M.shape
+    Wv = -(-din // dout) * dout
+    Mp = np.zeros((dout, Wv))
+    Mp[:, :din] = M
+    t = np.arange(Wv)
+    Mr = np.stack([Mp[t % dout, (t + o) % Wv] for o in range(dout)])
+    return Mr, Wv
+
+
+def fc(be, xs, M, bias, lay: Layout):
+    """Algorithm 2 (Sec. IV-D): C_sum = sum_o Rot(C,o)*V1_o + Rot(C,o-W_vec)*V2_o,
+    rescale, C_out = sum_{i < W_vec/dout} Rot(C_sum, i*dout), then Add(bias)
+    at slots [0, dout) of each sample."""
+    assert len(xs) == 1 and lay.flat
+    M = np.asarray(M, dtype=np.float64)
+    dout, din = M.shape
+    assert din == lay.D, f"FC expects {lay.D} inputs, got {din}"
+    if lay.pending != 1.0:
+        M = M * lay.pending
+    Mr, Wv = fc_rot_matrix(M)
+    x = xs[0]
+    steps = [o for o in range(dout)] + [o - Wv for o in range(1, dout)]
+    rr = be.rot_many(x, steps)
+    t_idx = np.arange(Wv)
+    acc = None
+    for o in range(dout):
+        v1 = np.where(t_idx < Wv - o, Mr[o], 0.0)
+        t = be.mul_mask(rr[o], slot_vector(lay, t_idx, v1))
+        acc = t if acc is None else be.add(acc, t)
+        if o:
+            v2 = np.where(t_idx >= Wv - o, Mr[o], 0.0)
+            acc = be.add(acc, be.mul_mask(rr[o - Wv], slot_vector(lay, t_idx, v2)))
+    acc = be.rescale(acc)
+    nsum = Wv // dout
+    rs = be.rot_many(acc, [i * dout for i in range(nsum)])
+    out = None
+    for i in range(nsum):
+        out = rs[i * dout] if out is None else be.add(out, rs[i * dout])
+    out = be.add_mask(out, slot_vector(lay, np.arange(dout), np.asarray(bias, dtype=np.float64)))
+    return [out], replace(lay, pending=1.0, prev="fc", D=dout, W=dout)
+
+
+# --------------------------------------------------------------- model
+def run_model(be, x, layers, lay: Layout, conv_mode: str = "hoisted"):
+    """Evaluate a layer list (dicts as produced by ``workloads``) on [x]."""
+    return run_layers(be, [x], layers, lay, conv_mode)
+
+
+def run_layers(be, xs, layers, lay: Layout, conv_mode: str = "hoisted"):
+    """Evaluate a layer list on the channel list xs."""
+    for spec in layers:
+        op = spec["op"]
+        if op in ("conv2d", "conv1d"):
+            xs, lay = conv(be, xs, spec["w"], spec["b"], spec["stride"], lay, conv_mode)
+        elif op == "square":
+            xs, lay = square(be, xs, lay)
+        elif op == "avgpool":
+            xs, lay = avgpool(be, xs, spec["k"], lay)
+        elif op == "flatten":
+            xs, lay = flatten(be, xs, lay)
+        elif op == "fc":
+            if not lay.flat:
+                xs, lay = flatten(be, xs, lay)
+            xs, lay = fc(be, xs, spec["w"], spec["b"], lay)
+        else:
+            raise ValueError(op)
+    return xs, lay
+
+
+def plan(layers, W_img: int, H_img: int, dims: int = 2):
+    """Layout sizes of Sec. V: the slots one sample needs (the stride), the number
+    of levels the model consumes, and the rotation steps it uses.
+
+    Stride = max(input W_img*H_img (Theorem 1 keeps every later valid value
+    inside it), CH*W*H of each flatten (V-C), W_vec of each FC (V-D)).
+    """
+    W, H, I, ch = W_img, H_img, 1, 1
+    prev = "input"
+    need = W_img * H_img
+    levels = 0
+    steps: set[int] = set()
+    flat_D = 0
+    for spec in layers:
+        op = spec["op"]
+        if op in ("conv2d", "conv1d"):
+            w = np.asarray(spec["w"])
+            kh = w.shape[2] if w.ndim == 4 else 1
+            kw = w.shape[-1]
+            S = spec["stride"]
+            steps |= {I * (k + W_img * j) for j in range(kh) for k in range(kw)}
+            H, W, I = (H - kh) // S + 1, (W - kw) // S + 1, I * S
+            ch = w.shape[0]
+            levels += 1
+            prev = "conv"
+        elif op == "square":
+            levels += 1
+        elif op == "avgpool":
+            c = spec["k"]
+            ckh = c if dims == 2 else 1
+            steps |= {I * (k + W_img * j) for j in range(ckh) for k in range(c)}
+            W, H, I = W // c, (H // c if dims == 2 else 1), I * c
+            prev = "avgpool"
+        elif op in ("flatten", "fc"):
+            if prev in ("conv", "avgpool"):
+                if prev == "avgpool":
+                    levels += 1
+                    steps |= {c * (I - 1) for c in range(W)}
+                elif I > 1 and W > 1:
+                    levels += 1
+                    steps |= {m * (I - 1) for m in range(I)}
+                    steps |= {u * I * (I - 1) for u in range(-(-W // I))}
+                if H > 1:
+                    levels += 1
+                    steps |= {r * (W_img * I - W) for r in range(H)}
+                steps |= {-o * W * H for o in range(ch)}
+                flat_D = ch * W * H
+                need = max(need, flat_D)
+                prev = "flatten"
+            if op == "fc":
+                dout, din = np.asarray(spec["w"]).shape
+                Wv = -(-din // dout) * dout
+                need = max(need, Wv)
+                steps |= set(range(dout)) | {o - Wv for o in range(1, dout)}
+                steps |= {i * dout for i in range(Wv // dout)}
+                levels += 1
+                prev = "fc"
+                flat_D = dout
+    steps.discard(0)
+    return {"stride": need, "levels": levels, "steps": sorted(steps)}
+
+
+# --------------------------------------------------------------- CKKS backend
+class HeBackend:
+    """The CKKS oracle as a layer backend; counts the operations it performs."""
+
+    def __init__(self, he):
+        self.he = he
+        self.count = {"rot": 0, "pmul": 0, "rescale": 0, "square": 0}
+
+    def rot(self, x, r):
+        self.count["rot"] += 1
+        return self.he.rotate(x, r)
+
+    def rot_many(self, x, steps):
+        self.count["rot"] += len({s for s in steps if s % (self.he.n // 2)})
+        return self.he.rotate_hoisted(x, steps)
+
+    def add(self, x, y):
+        return self.he.ct_add(x, y)
+
+    def mul_mask(self, x, v):
+        self.count["pmul"] += 1
+        pt = self.he.encode(v, self.he.scale, x.lp)
+        return self.he.ct_mul_plain(x, pt, self.he.scale)
+
+    def add_mask(self, x, v):
+        pt = self.he.encode(v, x.scale, x.lp)
+        return self.he.ct_add_plain(x, pt)
+
+    def rescale(self, x):
+        self.count["rescale"] += 1
+        return self.he.rescale(x)
+
+    def square(self, x):
+        self.count["square"] += 1
+        return self.he.square(x)

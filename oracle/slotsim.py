@@ -1,0 +1,60 @@
+"""Cleartext slot simulator (O2): the layer backend on FP64 slot vectors.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Rot(v, r) is ``np.roll(v, -r)`` (paper Sec. II-B: slot j+r moves to slot j),
+Mul (P) is the elementwise product with the mask, square is v*v.  Each vector
+carries the number of levels it has consumed: rescale adds one, and Add (C)
+refuses operands of different levels, as a CKKS library would.  Running
+``layers`` on this backend checks the paper's slot algorithms against the FP64
+CNN without encryption, and its level accounting against the #Mult tables.
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class SV:
+    v: np.ndarray
+    used: int = 0        # levels consumed so far
+    pending_rescale: bool = False
+
+
+class SlotSim:
+    def __init__(self):
+        self.count = {"rot": 0, "pmul": 0, "rescale": 0, "square": 0}
+
+    @staticmethod
+    def wrap(v):
+        return SV(np.asarray(v, dtype=np.float64))
+
+    def rot(self, x, r):
+        self.count["rot"] += 1
+        return SV(np.roll(x.v, -r), x.used, x.pending_rescale)
+
+    def rot_many(self, x, steps):
+        self.count["rot"] += len({s for s in steps if s % len(x.v)})
+        return {s: SV(np.roll(x.v, -s), x.used, x.pending_rescale) for s in steps}
+
+    def add(self, x, y):
+        assert x.used == y.used and x.pending_rescale == y.pending_rescale, "level mismatch"
+        return SV(x.v + y.v, x.used, x.pending_rescale)
+
+    def mul_mask(self, x, v):
+        assert not x.pending_rescale
+        self.count["pmul"] += 1
+        return SV(x.v * v, x.used, True)
+
+    def add_mask(self, x, v):
+        return SV(x.v + v, x.used, x.pending_rescale)
+
+    def rescale(self, x):
+        assert x.pending_rescale
+        self.count["rescale"] += 1
+        return SV(x.v, x.used + 1, False)
+
+    def square(self, x):
+        assert not x.pending_rescale
+        self.count["square"] += 1
+        return SV(x.v * x.v, x.used + 1, False)

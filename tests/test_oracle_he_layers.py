@@ -1,0 +1,65 @@
+"""The CKKS oracle running the paper's layers: decrypted results against the
+FP64 direct CNN (paper Sec. VII validation), packed samples against single
+samples, and levels consumed."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ckks, cnn, layers
+
+
+def _enc_run(P, model, samples, Wi, Hi, dims=2, mode="hoisted", n_slots_samples=None):
+    pl = layers.plan(model, Wi, Hi, dims)
+    steps = pl["steps"]
+    if mode == "incremental":
+        steps = sorted(set(steps) | {1, Wi - np.asarray(model[0]["w"]).shape[-1] + 1})
+    he = ckks.Ckks(seed=W.KEY_SEED, **P)
+    he.keygen(steps)
+    slots = he.n // 2
+    ns = n_slots_samples or len(samples)
+    lay = layers.input_layout(Wi, Hi, pl["stride"], ns, slots, dims)
+    x = np.zeros(slots)
+    for b, s in enumerate(samples):
+        x[b * pl["stride"]: b * pl["stride"] + np.asarray(s).size] = np.asarray(s).reshape(-1)
+    ct = he.encrypt(x, W.ENC_SEED)
+    be = layers.HeBackend(he)
+    ys, lay2 = layers.run_model(be, ct, model, lay, conv_mode=mode)
+    return he, ys, lay2, pl, be
+
+
+def test_single_conv_incremental_full_size():
+    """Single-convolution workload: N=8192, [60,40,40 | 60], one 5x5 kernel, incremental rotations."""
+    model = W.single_conv()
+    img = W.images(1)[0]
+    he, ys, lay, pl, be = _enc_run(W.PARAMS["conv1"], model, [img], 28, 28, mode="incremental")
+    dec = he.decrypt(ys[0])
+    ref = cnn.forward(img, model)             # 24 x 24
+    got = np.array([dec[r * 28 + c] for r in range(24) for c in range(24)])
+    assert np.abs(got - ref).max() < 1e-6
+    assert ys[0].lp == 2 and be.count["rot"] == 24 and be.count["pmul"] == 25
+
+
+def test_lenet1_small_ring_logits():
+    P = W.small_params("lenet1", 11)
+    model = W.lenet1()
+    img = W.images(1)[0]
+    he, ys, lay, pl, be = _enc_run(P, model, [img], 28, 28)
+    assert ys[0].lp == 1       # 8 data primes, 7 levels consumed
+    dec = he.decrypt(ys[0])[:10]
+    assert np.abs(dec - cnn.forward(img, model)).max() < 1e-3
+
+
+def test_packed_samples_equal_single():
+    P = dict(W.PARAMS["conv1"])
+    P["logn"] = 12            # 2048 slots: two 784-slot samples
+    model = W.single_conv()
+    imgs = W.images(2)
+    he, ys, _, pl, _ = _enc_run(P, model, imgs, 28, 28, n_slots_samples=2)
+    dec2 = he.decrypt(ys[0])
+    he1, ys1, _, _, _ = _enc_run(P, model, imgs[:1], 28, 28, n_slots_samples=2)
+    dec1 = he1.decrypt(ys1[0])
+    idx = np.array([r * 28 + c for r in range(24) for c in range(24)])
+    assert np.abs(dec2[idx] - dec1[idx]).max() < 1e-6
+    for b in range(2):
+        ref = cnn.forward(imgs[b], model)
+        assert np.abs(dec2[b * 784 + idx] - ref.reshape(-1)).max() < 1e-6

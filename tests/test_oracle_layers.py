@@ -1,0 +1,204 @@
+"""Pins of the layer algorithms (Alg. 1, Alg. 2, Sec. IV-C/E) on the cleartext
+slot simulator: results equal the FP64 direct CNN (itself checked against
+torch.nn.functional in float64), levels equal the paper's #Mult tables, and
+operation counts follow the paper's complexity statements."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import cnn, layers, slotsim
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+
+
+def build_model(spec_layers, seed=3):
+    rng = np.random.default_rng(seed)
+    out = []
+    for l in spec_layers:
+        if l[0] == "conv2d":
+            _, ci, co, k, s = l
+            out.append({"op": "conv2d", "w": rng.normal(0, 0.1, (co, ci, k, k)), "b": rng.normal(0, 0.1, co), "stride": s})
+        elif l[0] == "conv1d":
+            _, ci, co, k, s = l
+            out.append({"op": "conv1d", "w": rng.normal(0, 0.1, (co, ci, k)), "b": rng.normal(0, 0.1, co), "stride": s})
+        elif l[0] == "fc":
+            _, din, dout = l
+            out.append({"op": "fc", "w": rng.normal(0, 0.1, (dout, din)), "b": rng.normal(0, 0.1, dout)})
+        elif l[0] == "avgpool":
+            out.append({"op": "avgpool", "k": l[1]})
+        else:
+            out.append({"op": l[0]})
+    return out
+
+
+def pack(samples, stride, slots):
+    x = np.zeros(slots)
+    for b, s in enumerate(samples):
+        f = np.asarray(s).reshape(-1)
+        x[b * stride: b * stride + f.size] = f
+    return x
+
+
+def run_sim(model, samples, W_img, H_img, dims, slots):
+    pl = layers.plan(model, W_img, H_img, dims)
+    lay = layers.input_layout(W_img, H_img, pl["stride"], len(samples), slots, dims)
+    be = slotsim.SlotSim()
+    x = be.wrap(pack(samples, pl["stride"], slots))
+    ys, lay = layers.run_model(be, x, model, lay)
+    return ys[0], lay, be, pl
+
+
+def test_cnn_against_torch():
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    model = W.lenet1()
+    x = W.images(1)[0]
+    t = torch.tensor(x, dtype=torch.float64)[None, None]
+    for l in model:
+        if l["op"] == "conv2d":
+            t = F.conv2d(t, torch.tensor(l["w"]), torch.tensor(l["b"]), stride=l["stride"])
+        elif l["op"] == "square":
+            t = t * t
+        elif l["op"] == "avgpool":
+            t = F.avg_pool2d(t, l["k"])
+        elif l["op"] == "flatten":
+            t = t.reshape(1, -1)
+        elif l["op"] == "fc":
+            t = F.linear(t, torch.tensor(l["w"]), torch.tensor(l["b"]))
+    assert np.abs(t.numpy().reshape(-1) - cnn.forward(x, model)).max() < 1e-12
+    m1 = W.cnn1d()
+    s = W.signals(1)[0]
+    t = torch.tensor(s, dtype=torch.float64)[None]
+    for l in m1:
+        if l["op"] == "conv1d":
+            t = F.conv1d(t, torch.tensor(l["w"]), torch.tensor(l["b"]), stride=l["stride"])
+        elif l["op"] == "square":
+            t = t * t
+        elif l["op"] == "avgpool":
+            t = F.avg_pool1d(t, l["k"])
+        elif l["op"] == "flatten":
+            t = t.reshape(1, -1)
+        elif l["op"] == "fc":
+            t = F.linear(t.reshape(1, -1), torch.tensor(l["w"]), torch.tensor(l["b"]))
+    assert np.abs(t.numpy().reshape(-1) - cnn.forward(s[0], m1, dims=1)).max() < 1e-12
+
+
+@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "lenet5", "M1", "M7"])
+def test_slot_algorithms_equal_direct_cnn(name):
+    if name == "lenet1":
+        model, Wi, Hi, dims, slots = W.lenet1(), 28, 28, 2, 8192
+        gen = lambda n: W.images(n)
+    elif name == "cnn1d":
+        model, Wi, Hi, dims, slots = W.cnn1d(), 1024, 1, 1, 8192
+        gen = lambda n: W.signals(n)[:, 0]
+    elif name == "lenet5":
+        model, Wi, Hi, dims, slots = W.lenet5_sq(), 32, 32, 2, 16384
+        gen = lambda n: W.images(n, 32, 32)
+    elif name == "M1":
+        model, Wi, Hi, dims, slots = build_model(GOLD["mult_per_layer"]["M1"]["layers"]), 28, 28, 2, 8192
+        gen = lambda n: W.images(n)
+    else:
+        model, Wi, Hi, dims, slots = build_model(GOLD["mult_per_layer"]["M7"]["layers"]), 128, 1, 1, 4096
+        gen = lambda n: W.signals(n, 128)[:, 0]
+    pl = layers.plan(model, Wi, Hi, dims)
+    ns = slots // pl["stride"]
+    samples = gen(ns)
+    y, lay, be, _ = run_sim(model, samples, Wi, Hi, dims, slots)
+    for b in range(ns):
+        ref = cnn.forward(samples[b], model, dims=dims)
+        got = y.v[b * pl["stride"]: b * pl["stride"] + len(ref)]
+        assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+    # packing changes nothing: sample 0 alone gives the same numbers
+    y1, _, _, _ = run_sim(model, samples[:1], Wi, Hi, dims, slots)
+    assert np.abs(y1.v[:len(ref)] - y.v[:len(ref)]).max() < 1e-12
+
+
+@pytest.mark.parametrize("name", ["M1", "M2", "M4", "M7"])
+def test_levels_per_layer_match_paper_tables(name):
+    g = GOLD["mult_per_layer"][name]
+    model = build_model(g["layers"])
+    Wi, Hi = g["input"]
+    dims = 1 if Hi == 1 else 2
+    pl = layers.plan(model, Wi, Hi, dims)
+    slots = 1 << max(11, int(np.ceil(np.log2(pl["stride"]))))
+    lay = layers.input_layout(Wi, Hi, pl["stride"], 1, slots, dims)
+    be = slotsim.SlotSim()
+    xs = [be.wrap(pack(W.images(1, Hi, Wi) if dims == 2 else W.signals(1, Wi)[:, 0], pl["stride"], slots))]
+    used = []
+    for spec in model:
+        before = xs[0].used
+        xs, lay = layers.run_layers(be, xs, [spec], lay)
+        used.append(xs[0].used - before)
+    assert used == g["mult"], (used, g["mult"])
+    assert sum(used) == g["total"] == pl["levels"]
+
+
+def test_batch_capacity_matches_paper():
+    g = GOLD["batch_capacity"]
+    model = build_model(GOLD["mult_per_layer"][g["model"]]["layers"])
+    pl = layers.plan(model, 28, 28)
+    assert g["slots"] // pl["stride"] == g["samples"]
+    # LeNet-1 (M2) packs the same 10 images per ciphertext
+    assert 8192 // layers.plan(W.lenet1(), 28, 28)["stride"] == 10
+
+
+def _counts(model, Wi, Hi, dims=2, slots=8192):
+    _, _, be, _ = run_sim(model, W.images(1, Hi, Wi) if dims == 2 else W.signals(1, Wi)[:, 0], Wi, Hi, dims, slots)
+    return be.count
+
+
+@pytest.mark.parametrize("ci,co,k", [(1, 4, 5), (4, 12, 5), (2, 3, 3)])
+def test_conv_operation_counts(ci, co, k):
+    """Sec. IV-B: CH_in*CH_out*K^2 plaintext products, CH_in*K^2 rotations (one is the identity)."""
+    model = [{"op": "conv2d", "w": np.ones((co, ci, k, k)) * 0.1, "b": np.zeros(co), "stride": 1}]
+    rng = np.random.default_rng(0)
+    pl = layers.plan(model, 28, 28)
+    lay = layers.input_layout(28, 28, pl["stride"], 1, 8192)
+    be = slotsim.SlotSim()
+    xs = [be.wrap(pack([rng.uniform(size=(28, 28))], pl["stride"], 8192)) for _ in range(ci)]
+    ys, lay = layers.conv(be, xs, model[0]["w"], model[0]["b"], 1, lay)
+    assert be.count["pmul"] == ci * co * k * k
+    assert be.count["rot"] == ci * (k * k - 1)
+    assert be.count["rescale"] == co
+
+
+@pytest.mark.parametrize("din,dout", [(64, 10), (192, 10), (648, 64), (120, 84), (4080, 5)])
+def test_fc_operation_counts(din, dout):
+    """Sec. IV-D: O(DAT_out) products and O(DAT_in/DAT_out + DAT_out) rotations."""
+    rng = np.random.default_rng(1)
+    M = rng.normal(size=(dout, din))
+    Wv = -(-din // dout) * dout
+    lay = layers.Layout(W_img=din, H_img=1, W=din, H=1, I=1, stride=max(Wv, din), n_samples=1,
+                        slots=1 << int(np.ceil(np.log2(max(Wv, din)))) if max(Wv, din) > 1 else 1, dims=1,
+                        prev="flatten", D=din)
+    be = slotsim.SlotSim()
+    x = np.zeros(lay.slots)
+    x[:din] = rng.normal(size=din)
+    ys, _ = layers.fc(be, [be.wrap(x)], M, np.zeros(dout), lay)
+    assert np.abs(ys[0].v[:dout] - M @ x[:din]).max() < 1e-9
+    assert be.count["pmul"] == 2 * dout - 1
+    assert be.count["rot"] == 2 * (dout - 1) + (Wv // dout - 1)
+    if (din, dout) == (GOLD["fc_example"]["din"], GOLD["fc_example"]["dout"]):
+        assert be.count["pmul"] < 2 * dout and be.count["pmul"] < din
+
+
+def test_avgpool_uses_no_level_and_leaves_invalid_values():
+    lay = layers.input_layout(28, 28, 784, 1, 1024)
+    be = slotsim.SlotSim()
+    x = be.wrap(pack([W.images(1)[0]], 784, 1024))
+    ys, lay2 = layers.avgpool(be, [x], 2, lay)
+    assert ys[0].used == 0 and lay2.pending == 0.25 and lay2.I == 2
+    img = W.images(1)[0]
+    got = np.array([[ys[0].v[2 * (r * 28 + c)] for c in range(14)] for r in range(14)])
+    want = 4 * cnn.avgpool(img[None], 2)[0]
+    assert np.abs(got - want).max() < 1e-12
+    # between the valid outputs the slots hold non-zero "invalid values" (Sec. IV-C)
+    assert abs(ys[0].v[1]) > 0
+
+
+def test_plan_stride_lenet1():
+    pl = layers.plan(W.lenet1(), 28, 28)
+    assert pl["stride"] == 784 and pl["levels"] == 7

@@ -1,0 +1,94 @@
+"""Pins of the CKKS oracle: decrypt(encrypt(x)) round trips, rotation
+composition, key switching and the ciphertext product, all against cleartext."""
+import numpy as np
+import pytest
+
+from oracle import ckks
+
+
+@pytest.fixture(scope="module")
+def he():
+    h = ckks.Ckks(logn=10, data_bits=[60, 40, 40], special_bits=[60], dnum=3, log2_scale=40, seed=7)
+    h.keygen(rot_steps=[1, 3, 4, 7, -2, 100, 511])
+    return h
+
+
+@pytest.fixture(scope="module")
+def he_dnum():
+    # alpha = 2 limbs per digit, two special primes, a short last digit
+    h = ckks.Ckks(logn=10, data_bits=[60, 40, 40, 40, 40], special_bits=[60, 60], dnum=3, log2_scale=40, seed=8)
+    h.keygen(rot_steps=[1, 5])
+    return h
+
+
+def test_round_trip(he):
+    M = he.n // 2
+    z = np.random.default_rng(0).uniform(-1, 1, M)
+    ct = he.encrypt(z, 9000)
+    assert np.abs(he.decrypt(ct) - z).max() < 2.0 ** -25
+    # deterministic under the same seeds
+    assert np.array_equal(he.encrypt(z, 9000).d, ct.d)
+    assert not np.array_equal(he.encrypt(z, 9001).d, ct.d)
+
+
+def test_rotation_composition(he):
+    M = he.n // 2
+    z = np.random.default_rng(1).uniform(-1, 1, M)
+    ct = he.encrypt(z, 9000)
+    for a, b in [(1, 3), (4, -2), (7, 100)]:
+        r = he.rotate(he.rotate(ct, a), b)
+        assert np.abs(he.decrypt(r) - np.roll(z, -(a + b))).max() < 1e-6
+    # rotation by N/2 slots is the identity element (no key switch)
+    assert np.array_equal(he.rotate(ct, M).d, ct.d)
+
+
+def test_hoisted_equals_single_up_to_noise(he):
+    M = he.n // 2
+    z = np.random.default_rng(2).uniform(-1, 1, M)
+    ct = he.encrypt(z, 9002)
+    rr = he.rotate_hoisted(ct, [0, 1, 511, -2])
+    for r in [1, 511, -2]:
+        assert np.abs(he.decrypt(rr[r]) - np.roll(z, -r)).max() < 1e-6
+    assert np.array_equal(rr[0].d, ct.d)
+
+
+def test_general_digits(he_dnum):
+    he = he_dnum
+    M = he.n // 2
+    z = np.random.default_rng(3).uniform(-1, 1, M)
+    for lp in (5, 4, 3):   # full, short last digit, fewer digits
+        ct = he.encrypt(z, 9003, lp=lp)
+        assert np.abs(he.decrypt(he.rotate(ct, 5)) - np.roll(z, -5)).max() < 1e-6
+        sq = he.square(ct)
+        assert sq.lp == lp - 1
+        assert np.abs(he.decrypt(sq) - z * z).max() < 1e-6
+
+
+def test_square_and_plain_mult(he):
+    M = he.n // 2
+    rng = np.random.default_rng(4)
+    z = rng.uniform(-1, 1, M)
+    v = rng.uniform(-1, 1, M)
+    ct = he.encrypt(z, 9004)
+    sq = he.square(ct)
+    assert sq.lp == 2 and abs(sq.scale - he.scale ** 2 / he.q[2]) == 0
+    assert np.abs(he.decrypt(sq) - z * z).max() < 1e-6
+    pm = he.rescale(he.ct_mul_plain(ct, he.encode(v, he.scale, 3), he.scale))
+    assert np.abs(he.decrypt(pm) - z * v).max() < 1e-6
+    s = he.ct_add_plain(pm, he.encode(v, pm.scale, pm.lp))
+    assert np.abs(he.decrypt(s) - (z * v + v)).max() < 1e-6
+
+
+def test_keyswitch_relation(he):
+    """KS(x) decrypts to x*s' for the relinearisation key (s' = s^2)."""
+    n = he.n
+    q = he.q
+    rng = np.random.default_rng(5)
+    x = np.stack([rng.integers(0, qi, n, dtype=np.uint64) for qi in q])
+    k0, k1 = he.keyswitch(x, he.keys.rlk)
+    lhs = he.add(k0, he.mul(k1, he.keys.s[:3], q), q)
+    s2 = he.mul(he.keys.s[:3], he.keys.s[:3], q)
+    rhs = he.mul(x, s2, q)
+    diff = he.intt(he.sub(lhs, rhs, q), q, he.qpsi)[0]
+    c = np.where(diff > q[0] // 2, diff.astype(np.float64) - q[0], diff.astype(np.float64))
+    assert np.abs(c).max() < 2.0 ** 30   # small key-switching noise, x is uniform mod Q

@@ -1,0 +1,102 @@
+"""Seeded synthetic workloads shaped like the paper's experiments.
+
+Shared by the tests, the benchmark and the oracle as INPUT GENERATORS ONLY:
+nothing here performs homomorphic-encryption arithmetic.  MNIST, USPS and the
+ECG set are not available, so (paper Sec. VI datasets -> stand-ins):
+  * MNIST 28x28 gray images      -> U[0,1] 28x28 images, sample i seeded 1000+i
+  * 1-D ECG beats                -> N(0,1) signals of length 1024, seeded 1000+i
+  * trained weights               -> N(0, 0.1^2) weights and biases, seed 42
+Model shapes: a single 5x5 convolution
+(Exp. 1 style), the LeNet-1-shaped net of Exp. 2 (Table M2: conv 1->4 K5,
+x^2, avgpool 2, conv 4->12 K5, x^2, avgpool 2, flatten, FC 192->10) and a 1-D
+CNN in the family of Exp. 7.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+WEIGHT_SEED = 42
+INPUT_SEED = 1000
+KEY_SEED = 7
+ENC_SEED = 9000
+
+
+def _normal(rng, shape, sd=0.1):
+    return rng.normal(0.0, sd, size=shape)
+
+
+def single_conv(seed: int = WEIGHT_SEED, K: int = 5):
+    rng = np.random.default_rng(seed)
+    return [{"op": "conv2d", "w": _normal(rng, (1, 1, K, K)), "b": np.zeros(1), "stride": 1}]
+
+
+def lenet1(seed: int = WEIGHT_SEED):
+    rng = np.random.default_rng(seed)
+    return [
+        {"op": "conv2d", "w": _normal(rng, (4, 1, 5, 5)), "b": _normal(rng, (4,)), "stride": 1},
+        {"op": "square"},
+        {"op": "avgpool", "k": 2},
+        {"op": "conv2d", "w": _normal(rng, (12, 4, 5, 5)), "b": _normal(rng, (12,)), "stride": 1},
+        {"op": "square"},
+        {"op": "avgpool", "k": 2},
+        {"op": "flatten"},
+        {"op": "fc", "w": _normal(rng, (10, 192)), "b": _normal(rng, (10,))},
+    ]
+
+
+def cnn1d(seed: int = WEIGHT_SEED, length: int = 1024):
+    rng = np.random.default_rng(seed)
+    l1 = length - 2          # conv k3 s1
+    l2 = l1 // 2             # avgpool 2
+    l3 = (l2 - 3) // 2 + 1   # conv k3 s2
+    return [
+        {"op": "conv1d", "w": _normal(rng, (8, 1, 3)), "b": _normal(rng, (8,)), "stride": 1},
+        {"op": "square"},
+        {"op": "avgpool", "k": 2},
+        {"op": "conv1d", "w": _normal(rng, (16, 8, 3)), "b": _normal(rng, (16,)), "stride": 2},
+        {"op": "square"},
+        {"op": "flatten"},
+        {"op": "fc", "w": _normal(rng, (5, 16 * l3)), "b": _normal(rng, (5,))},
+    ]
+
+
+def lenet5_sq(seed: int = WEIGHT_SEED):
+    rng = np.random.default_rng(seed)
+    return [
+        {"op": "conv2d", "w": _normal(rng, (6, 1, 5, 5)), "b": _normal(rng, (6,)), "stride": 1},
+        {"op": "square"},
+        {"op": "avgpool", "k": 2},
+        {"op": "conv2d", "w": _normal(rng, (16, 6, 5, 5)), "b": _normal(rng, (16,)), "stride": 1},
+        {"op": "square"},
+        {"op": "avgpool", "k": 2},
+        {"op": "flatten"},
+        {"op": "fc", "w": _normal(rng, (120, 400)), "b": _normal(rng, (120,))},
+        {"op": "square"},
+        {"op": "fc", "w": _normal(rng, (84, 120)), "b": _normal(rng, (84,))},
+        {"op": "square"},
+        {"op": "fc", "w": _normal(rng, (10, 84)), "b": _normal(rng, (10,))},
+    ]
+
+
+def images(n: int, H: int = 28, W: int = 28, seed: int = INPUT_SEED) -> np.ndarray:
+    return np.stack([np.random.default_rng(seed + i).uniform(0.0, 1.0, (H, W)) for i in range(n)])
+
+
+def signals(n: int, length: int = 1024, seed: int = INPUT_SEED) -> np.ndarray:
+    return np.stack([np.random.default_rng(seed + i).normal(0.0, 1.0, (1, length)) for i in range(n)])
+
+
+# CKKS parameter sets of the workloads (bit sizes of the data chain, then the
+# special primes; dnum digits; log2 of the scale Delta).
+PARAMS = {
+    "conv1": dict(logn=13, data_bits=[60, 40, 40], special_bits=[60], dnum=3, log2_scale=40),
+    "lenet1": dict(logn=14, data_bits=[60] + [40] * 7, special_bits=[60], dnum=8, log2_scale=40),
+    "cnn1d": dict(logn=14, data_bits=[60] + [40] * 6, special_bits=[60], dnum=7, log2_scale=40),
+}
+
+
+def small_params(name: str, logn: int) -> dict:
+    """The same chain at a smaller ring degree (for oracle-speed parity cases)."""
+    p = dict(PARAMS[name])
+    p["logn"] = logn
+    return p
