@@ -1,0 +1,195 @@
+/*
+ * unihenn.h -- C ABI of the GB300 (sm_103a) library for UniHENN's encrypted
+ * CNN inference (Choi et al., "UniHENN: Designing Faster and More Versatile
+ * Homomorphic Encryption-based CNNs without im2col", arXiv 2402.03060).
+ *
+ * Every ring operation behind these calls runs as a CUDA kernel of
+ * libunihenn.so; no call has a CPU fallback.  Arguments are plain pointers
+ * and sizes.  Conventions for every entry point:
+ *   - the return value is a he_status; on failure he_last_error() gives a
+ *     thread-local message and no output handle is written;
+ *   - handles (he_ctx, he_ct, he_model) are allocated by the library and freed
+ *     by the caller with the matching *_free / *_destroy call;
+ *   - input arrays are borrowed for the duration of the call only;
+ *   - work is queued on the context's stream; calls that return data to host
+ *     memory (he_decrypt with a host buffer, he_ct_export, he_context_primes)
+ *     synchronise that stream before returning.
+ *
+ * Ciphertext layout in device memory: a he_ct is a BATCH of B ciphertexts of
+ * the same level, scale and slot layout, stored contiguously as
+ * [B][2][L'][N] uint64 residues (c0 then c1, limbs q_0..q_{L'-1}), evaluation
+ * form in bit-reversed order.  The slot layout is the paper's flattened
+ * single-ciphertext layout (Sec. III-A): sample k of a ciphertext occupies
+ * slots k*stride ... (Sec. III-B), value (r, c) of a feature map at
+ * I*(r*W_img + c) with I the interval (Sec. IV-B, V-A).
+ */
+#ifndef UNIHENN_H
+#define UNIHENN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HE_OK = 0,
+    HE_EINVAL = 1,     /* bad argument (null pointer, size out of range, shape mismatch) */
+    HE_ENOMEM = 2,     /* device allocation failed */
+    HE_ELEVEL = 3,     /* not enough levels left for the operation (paper Sec. II-B "depth") */
+    HE_ESCALE = 4,     /* operands of an addition have different scales */
+    HE_ESLOTS = 5,     /* the slot layout does not fit in N/2 slots (paper Sec. V) */
+    HE_ENOKEY = 6,     /* a rotation needs a Galois key that he_keygen did not create */
+    HE_ECUDA = 7,      /* a CUDA call or kernel failed */
+    HE_ETIMEOUT = 8,   /* a bounded device wait ran out */
+    HE_EOVERFLOW = 9   /* an encoded coefficient does not fit in 63 bits (scale too large) */
+} he_status;
+
+typedef struct he_ctx he_ctx;
+typedef struct he_ct he_ct;
+typedef struct he_model he_model;
+
+/* CKKS parameters (paper Sec. VI-D, Table II: slots, scale, modulus chain, depth).
+ * The modulus chain is the n_data data primes followed by n_special special
+ * primes; prime i is the largest prime below 2^prime_bits[i] that is 1 mod 2N
+ * and not used by an earlier entry.  Hybrid key switching uses dnum digits of
+ * ceil(n_data/dnum) consecutive data primes.  Depth = n_data - 1. */
+typedef struct {
+    uint32_t log2n;              /* N = 2^log2n; 4 <= log2n <= 14 */
+    uint32_t n_data;             /* data primes (L+1), 1..32 */
+    uint32_t n_special;          /* special primes K, 1..4 */
+    const uint32_t *prime_bits;  /* n_data + n_special bit sizes, each 20..60 */
+    uint32_t dnum;               /* 1..n_data */
+    double log2_scale;           /* Delta = 2^log2_scale */
+    uint64_t seed;               /* key-generation seed (counter-based SplitMix64) */
+    int device;                  /* CUDA device ordinal */
+    void *stream;                /* cudaStream_t to queue on; NULL = library-owned stream */
+} he_params;
+
+/* Create a context: primes, NTT/FFT tables and the device memory pool.
+ * Errors: HE_EINVAL (parameters out of range), HE_ECUDA, HE_ENOMEM. */
+he_status he_context_create(const he_params *p, he_ctx **out);
+void he_context_destroy(he_ctx *ctx);
+
+/* Copy the modulus chain (data primes, then special primes) to host out[n]. */
+he_status he_context_primes(const he_ctx *ctx, uint64_t *out, size_t n);
+
+/* Generate the secret key (kept on the device), the public key, the
+ * relinearisation key and one Galois key per rotation step in rot_steps
+ * (Rot(v, r) moves slot j+r to slot j, paper Sec. II-B; negative r rotates
+ * right).  Key sizes: each switching key is dnum*2*(n_data+n_special)*N words.
+ * Errors: HE_EINVAL, HE_ENOMEM, HE_ECUDA. */
+he_status he_keygen(he_ctx *ctx, const int32_t *rot_steps, size_t n_steps);
+
+/* Flatten and encrypt (paper Sec. III-A/B): x is [n_samples][H][W] doubles,
+ * host memory (x_on_device = 0) or device memory (1).  Sample k goes to
+ * ciphertext k / samples_per_ct at slot offset (k % samples_per_ct)*stride,
+ * row-major, zero elsewhere.  Ciphertext b is a public-key encryption at the
+ * top level with randomness seeded by enc_seed + b.  *out is a batch of
+ * ceil(n_samples / samples_per_ct) ciphertexts whose layout records
+ * (W_img = W, H_img = H, stride, samples_per_ct).
+ * Errors: HE_EINVAL, HE_ESLOTS (samples_per_ct*stride > N/2 or W*H > stride),
+ * HE_EOVERFLOW, HE_ECUDA. */
+he_status he_encrypt(he_ctx *ctx, const double *x, int x_on_device, uint32_t W, uint32_t H,
+                     uint32_t n_samples, uint32_t samples_per_ct, uint32_t stride,
+                     uint64_t enc_seed, he_ct **out);
+
+/* Decrypt and decode: out is [B*samples_per_ct][n_per_sample] doubles (host or
+ * device), the slots k*stride + [0, n_per_sample) of every sample position.
+ * Decoding reads limb q_0, valid while |message * scale| < q_0/2.
+ * Errors: HE_EINVAL, HE_ECUDA. */
+he_status he_decrypt(he_ctx *ctx, const he_ct *ct, double *out, int out_on_device, size_t n_per_sample);
+
+/* Batch size, active limbs L' and scale of a ciphertext batch. */
+he_status he_ct_info(const he_ct *ct, uint32_t *batch, uint32_t *limbs, double *scale);
+
+/* Slot layout of a ciphertext batch: sample positions per ciphertext, slots
+ * per sample, and the interval I of the current feature map. */
+he_status he_ct_layout(const he_ct *ct, uint32_t *samples_per_ct, uint32_t *stride, uint32_t *interval);
+
+/* Copy a ciphertext batch to host memory in COEFFICIENT form,
+ * [B][2][L'][N] uint64 (independent of the NTT ordering; used for parity). */
+he_status he_ct_export(he_ctx *ctx, const he_ct *ct, uint64_t *coeff);
+void he_ct_free(he_ct *ct);
+
+/* ---- ciphertext operations (paper Sec. II-B) ---------------------------- */
+/* Rot(ct, step) for every ciphertext of the batch: Galois automorphism and
+ * hybrid key switching.  Errors: HE_ENOKEY, HE_ECUDA. */
+he_status he_rotate(he_ctx *ctx, const he_ct *in, int32_t step, he_ct **out);
+/* Several rotations of the same batch sharing one ModUp of c1 (hoisting);
+ * out[i] receives Rot(in, steps[i]); a step of 0 (mod N/2) copies the input. */
+he_status he_rotate_hoisted(he_ctx *ctx, const he_ct *in, const int32_t *steps, size_t n, he_ct **out);
+/* Divide by the top prime (rescale); HE_ELEVEL at one limb. */
+he_status he_rescale(he_ctx *ctx, const he_ct *in, he_ct **out);
+/* Mul (P) by the slot vector v[N/2] (host) encoded at scale Delta; no rescale. */
+he_status he_mul_plain(he_ctx *ctx, const he_ct *in, const double *v, he_ct **out);
+/* Add (C); HE_ESCALE / HE_EINVAL on scale / level / batch mismatch. */
+he_status he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
+/* Mul (C) of each ciphertext by itself, relinearised and rescaled (square
+ * activation, paper Sec. IV-F). */
+he_status he_square(he_ctx *ctx, he_ct *const *in, uint32_t n, he_ct **out);
+
+/* ---- UniHENN layers (paper Sec. IV) on channel lists -------------------- */
+/* Algorithm 1: in[ch_in] -> out[ch_out]; w [ch_out][ch_in][K][K] (conv2d) or
+ * [ch_out][ch_in][K] (conv1d); bias [ch_out]; stride S.  incremental = 0:
+ * rotations of each input share one ModUp; 1: each rotation is taken from the
+ * previous one (the paper's "incremental rotations"). */
+he_status he_conv2d(he_ctx *ctx, he_ct *const *in, uint32_t ch_in, const double *w, const double *bias,
+                    uint32_t ch_out, uint32_t K, uint32_t S, int incremental, he_ct **out);
+he_status he_conv1d(he_ctx *ctx, he_ct *const *in, uint32_t ch_in, const double *w, const double *bias,
+                    uint32_t ch_out, uint32_t K, uint32_t S, int incremental, he_ct **out);
+/* Sec. IV-C: c x c average pooling by rotations and additions, no level;
+ * the factor 1/c^2 is carried in the layout and folded into the next linear layer. */
+he_status he_avgpool(he_ctx *ctx, he_ct *const *in, uint32_t ch, uint32_t c, he_ct **out);
+/* Sec. IV-E: remove intervals and invalid values and pack ch channels into one
+ * ciphertext (values at slots [0, ch*W*H) of each sample). */
+he_status he_flatten(he_ctx *ctx, he_ct *const *in, uint32_t ch, he_ct **out);
+/* Algorithm 2: FC din -> dout on a flattened ciphertext; W [dout][din], b [dout]. */
+he_status he_fc(he_ctx *ctx, const he_ct *in, const double *W, const double *b, uint32_t din,
+                uint32_t dout, he_ct **out);
+
+/* ---- compiled models, batched inference ------------------------------- */
+enum { HE_CONV2D = 1, HE_CONV1D = 2, HE_SQUARE = 3, HE_AVGPOOL = 4, HE_FLATTEN = 5, HE_FC = 6 };
+typedef struct {
+    uint32_t op;       /* HE_CONV2D ... HE_FC */
+    uint32_t ch_in;    /* conv: input channels; FC: DAT_in */
+    uint32_t ch_out;   /* conv: output channels; FC: DAT_out */
+    uint32_t k;        /* conv kernel size; average-pooling size */
+    uint32_t stride;   /* conv stride */
+    const double *w;   /* conv [ch_out][ch_in][k][k] (1-D: [ch_out][ch_in][k]); FC [ch_out][ch_in] */
+    const double *b;   /* [ch_out] */
+} he_layer;
+
+/* Plan a layer list for W_img x H_img inputs (H_img = 1: 1-D): the slots a
+ * sample needs (paper Sec. V), the levels consumed and the distinct rotation
+ * steps (to pass to he_keygen).  steps may be NULL to query *n_steps. */
+he_status he_model_plan(const he_layer *layers, size_t n, uint32_t W_img, uint32_t H_img,
+                        uint32_t *stride, uint32_t *levels, int32_t *steps, size_t *n_steps);
+/* Compile: copies the weights; plaintext masks are encoded on the device at
+ * the first he_infer and cached in the model.  Errors: HE_ENOKEY, HE_ELEVEL, HE_ESLOTS. */
+he_status he_model_compile(he_ctx *ctx, const he_layer *layers, size_t n, uint32_t W_img, uint32_t H_img,
+                           uint32_t samples_per_ct, he_model **out);
+/* Run the compiled model on a ciphertext batch (all layers, every ciphertext
+ * of the batch in the same kernel launches); *out receives the logits batch.
+ * use_graph = 1 replays a captured CUDA graph after the first call of a given
+ * batch size. */
+he_status he_infer(he_model *m, const he_ct *in, int use_graph, he_ct **out);
+void he_model_free(he_model *m);
+
+/* ---- low level ------------------------------------------------------- */
+/* In-place forward (inverse = 0) or inverse negacyclic NTT of n_limbs device
+ * limbs data[n_limbs][N]; limb i uses prime prime_idx[i] (index into the
+ * chain of he_context_primes).  Forward output is bit-reversed evaluation order. */
+he_status he_ntt(he_ctx *ctx, uint64_t *data, uint32_t n_limbs, const uint32_t *prime_idx, int inverse);
+/* Block until the context's stream is idle. */
+he_status he_sync(he_ctx *ctx);
+/* Number of kernels this context has launched so far. */
+uint64_t he_kernel_launches(const he_ctx *ctx);
+
+const char *he_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UNIHENN_H */

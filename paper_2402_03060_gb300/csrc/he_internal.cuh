@@ -1,0 +1,239 @@
+// he_internal.cuh -- shared device arithmetic and host structures of libunihenn.
+//
+// Residues are uint64 in [0, q) with every prime q < 2^61.  Three reductions:
+//   * Shoup (Harvey 2014) for a product by a constant w with w' = floor(w*2^64/q);
+//   * Barrett (Menezes et al., HAC Alg. 14.42 with base 2) for a product of two
+//     variables, mu = floor(2^(2s)/q), s = bit length of q;
+//   * reduce128 for a lazily accumulated 128-bit sum: (hi mod q) * (2^64 mod q)
+//     by Shoup plus lo mod q by a one-word Barrett.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/unihenn.h"
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+typedef int64_t i64;
+
+#define HE_MAX_PRIMES 40
+
+// ------------------------------------------------------------ device math
+struct PrimeDev {
+    u64 q;
+    u64 mu;      // floor(2^(2s) / q)
+    u64 mu64;    // floor(2^64 / q)
+    u64 r64;     // 2^64 mod q
+    u64 r64s;    // Shoup companion of r64
+    u64 ninv;    // N^{-1} mod q
+    u64 ninvs;
+    u32 s;       // bit length of q
+    u32 pad;
+};
+
+__device__ __forceinline__ u64 mulhi64(u64 a, u64 b) { return __umul64hi(a, b); }
+
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) {
+    u64 r = a + b;
+    return r >= q ? r - q : r;
+}
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+__device__ __forceinline__ u64 neg_mod(u64 a, u64 q) { return a ? q - a : 0; }
+
+// a * w mod q, w < q, ws = floor(w * 2^64 / q); any a < 2^64.
+__device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 ws, u64 q) {
+    u64 qh = mulhi64(a, ws);
+    u64 r = a * w - qh * q;
+    return r >= q ? r - q : r;
+}
+
+// x mod q for any 64-bit x (one-word Barrett: result of the estimate < 2q).
+__device__ __forceinline__ u64 reduce64(u64 x, const PrimeDev &P) {
+    u64 qh = mulhi64(x, P.mu64);
+    u64 r = x - qh * P.q;
+    return r >= P.q ? r - P.q : r;
+}
+
+// (hi * 2^64 + lo) mod q
+__device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const PrimeDev &P) {
+    u64 h = reduce64(hi, P);
+    u64 a = mul_shoup(h, P.r64, P.r64s, P.q);
+    u64 b = reduce64(lo, P);
+    return add_mod(a, b, P.q);
+}
+
+// a * b mod q for a, b < q (HAC 14.42, base 2, k = s)
+__device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeDev &P) {
+    u64 lo = a * b;
+    u64 hi = mulhi64(a, b);
+    u32 s = P.s;
+    u64 q1 = (hi << (65 - s)) | (lo >> (s - 1));
+    u64 t_lo = q1 * P.mu;
+    u64 t_hi = mulhi64(q1, P.mu);
+    u64 q3 = (t_hi << (63 - s)) | (t_lo >> (s + 1));
+    u64 r = lo - q3 * P.q;
+    if (r >= P.q) r -= P.q;
+    if (r >= P.q) r -= P.q;
+    return r;
+}
+
+// 128-bit accumulator
+struct Acc128 {
+    u64 lo, hi;
+};
+__device__ __forceinline__ void mac128(Acc128 &acc, u64 a, u64 b) {
+    u64 plo = a * b;
+    u64 phi = mulhi64(a, b);
+    u64 lo = acc.lo + plo;
+    acc.hi += phi + (lo < plo ? 1 : 0);
+    acc.lo = lo;
+}
+
+__device__ __forceinline__ u32 brev_bits(u32 x, int bits) { return __brev(x) >> (32 - bits); }
+
+// index in bit-reversed evaluation order whose value sigma_g takes for slot i:
+// slot i holds a(psi^(2*brev(i)+1)); sigma_g(a) there equals a(psi^(g*(2*brev(i)+1))).
+__device__ __forceinline__ u32 galois_src(u32 i, u32 g, int logn) {
+    u32 e = 2 * brev_bits(i, logn) + 1;
+    u32 m = (u32)(((u64)g * e) & ((2ull << logn) - 1));
+    return brev_bits((m - 1) >> 1, logn);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014; variant-13 finaliser), counter-based:
+// word i of stream `st` under `seed` = output #i of a SplitMix64 seeded with
+// output #st of a SplitMix64 seeded with `seed`.
+__host__ __device__ __forceinline__ u64 sm64_mix(u64 z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ u64 sm64_state(u64 seed, u64 stream) {
+    return sm64_mix(seed + (stream + 1) * 0x9e3779b97f4a7c15ULL);
+}
+__host__ __device__ __forceinline__ u64 sm64_word(u64 state, u64 i) {
+    return sm64_mix(state + (i + 1) * 0x9e3779b97f4a7c15ULL);
+}
+
+// randomness stream ids: purpose<<56 | key_id<<32 | digit<<16 | limb
+enum { RS_SK = 1, RS_PK_A = 2, RS_PK_E = 3, RS_KSK_A = 4, RS_KSK_E = 5, RS_ENC_U = 6, RS_ENC_E0 = 7, RS_ENC_E1 = 8 };
+__host__ __device__ __forceinline__ u64 stream_id(u64 purpose, u64 key, u64 digit, u64 limb) {
+    return (purpose << 56) | (key << 32) | (digit << 16) | limb;
+}
+
+// ------------------------------------------------------------ host side
+struct HeError : std::runtime_error {
+    he_status code;
+    HeError(he_status c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define CUDA_TRY(x)                                                                      \
+    do {                                                                                 \
+        cudaError_t e__ = (x);                                                           \
+        if (e__ != cudaSuccess)                                                          \
+            throw HeError(e__ == cudaErrorMemoryAllocation ? HE_ENOMEM : HE_ECUDA,       \
+                          std::string(#x) + ": " + cudaGetErrorString(e__));             \
+    } while (0)
+
+struct Ctx;
+void note_launch(Ctx *c, const char *what);   // error check + launch counter
+
+// Caching device allocator: buffers are returned to per-size free lists and
+// reused in stream order (all work of a context runs on one stream), so the
+// steady state of an inference issues no cudaMalloc/cudaFree.
+struct Pool {
+    std::map<size_t, std::vector<void *>> free_;
+    std::map<void *, size_t> size_;
+    size_t bytes_live = 0, bytes_cached = 0;
+    void *get(size_t bytes);
+    void put(void *p);
+    void release_cached();
+    void release_all();
+};
+
+// A device buffer owned through the pool
+struct DBuf {
+    Pool *pool = nullptr;
+    u64 *p = nullptr;
+    size_t words = 0;
+    DBuf() = default;
+    DBuf(Ctx *c, size_t w);
+    ~DBuf();
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : pool(o.pool), p(o.p), words(o.words) { o.p = nullptr; o.words = 0; }
+    DBuf &operator=(DBuf &&o) noexcept;
+};
+
+// slot layout of a ciphertext (paper Sec. III-A/B, IV, V)
+struct Layout {
+    u32 W_img = 0, H_img = 0;   // original row pitch / height
+    u32 W = 0, H = 0;           // current valid width/height
+    u32 I = 1;                  // interval
+    u32 stride = 0;             // slots per sample
+    u32 n_samples = 1;          // sample positions in masks
+    u32 dims = 2;               // 2-D image or 1-D signal
+    double pending = 1.0;       // deferred pooling factor
+    int prev = 0;               // 0 input, 1 conv, 2 avgpool, 3 flatten, 4 fc
+    u32 D = 0;                  // flattened length
+};
+enum { PREV_INPUT = 0, PREV_CONV = 1, PREV_POOL = 2, PREV_FLAT = 3, PREV_FC = 4 };
+
+struct Ctx {
+    // parameters
+    int logn = 0;
+    u32 N = 0, L1 = 0, K = 0, dnum = 0, alpha = 0;
+    double scale = 0;
+    u64 seed = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<u64> primes;       // L1 data then K special
+    std::vector<u64> psi;
+    std::vector<PrimeDev> pdev_h;
+    // device tables
+    PrimeDev *pdev = nullptr;      // [nprimes]
+    u64 *tw = nullptr;             // per prime: psi_rev, psi_rev_shoup, ipsi_rev, ipsi_rev_shoup (4N)
+    double *fft_w = nullptr;       // cos/sin of 2*pi*k/M, k < M/2 (interleaved)
+    double *fft_t = nullptr;       // cos/sin of pi*k/N, k < M (interleaved)
+    u32 *slot_pos_br = nullptr;    // bit-reversed DFT position of slot j
+    u32 *slot_pos = nullptr;       // DFT position of slot j
+    Pool pool;
+    Pool *active = nullptr;        // pool that new buffers come from (a model's private pool during graph capture)
+    // keys
+    bool have_keys = false;
+    DBuf sk;                       // [L1+K][N] eval
+    DBuf pk;                       // [2][L1][N]
+    DBuf rlk;                      // [dnum][2][L1+K][N]
+    std::map<u32, DBuf> gk;        // Galois element -> key [dnum][2][L+1+K][N]
+    // per-level constant tables (host-built, device-resident)
+    std::map<std::string, DBuf> cache;
+    uint64_t launches = 0;
+    int *err_flag = nullptr;       // device error word (encoder overflow etc.)
+
+    u32 nprimes() const { return L1 + K; }
+    u64 *tw_fwd(u32 p) const { return tw + (size_t)p * 4 * N; }
+    u32 galois_elt(int64_t step) const;
+    u64 *const_table(const std::string &key, const std::vector<u64> &host);
+};
+
+// ---- kernels / ops (defined across the .cu files)
+// ntt.cu
+struct RowSet {         // rows of N words: row r at base + off(r)*N, prime pidx(r)
+    const u32 *list;    // packed (limb_offset << 8 | prime), or nullptr for the regular form
+    u32 n;
+    u32 period, lp, pbase;   // regular form: row r -> offset r, prime (r%period<lp ? r%period : pbase + r%period - lp)
+};
+void ntt_forward(Ctx *c, u64 *base, const RowSet &rs);
+void ntt_inverse(Ctx *c, u64 *base, const RowSet &rs);
+RowSet rows_regular(u32 n, u32 period, u32 lp, u32 pbase);
+RowSet rows_list(Ctx *c, const std::string &key, const std::vector<u32> &packed);
+
+// keyswitch.cu, he.cu, layers.cu: see the respective files
+std::string fmt(const char *f, ...);

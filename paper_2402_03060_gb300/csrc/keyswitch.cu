@@ -1,0 +1,321 @@
+// keyswitch.cu -- hybrid key switching (Han & Ki 2020) and rescale kernels.
+//
+//   ModUp:   per digit j (consecutive alpha limbs of q_0..q_{lp-1}), fast base
+//            conversion (Bajard et al. 2016 / Halevi-Polyakov-Shoup 2018, no
+//            correction) of the digit's coefficients to every other limb of
+//            Q_l u P; the digit's own limbs are copied in evaluation form.
+//   inner:   acc_k[t] = sum_j D_j[t] (o) ksk_j,k[t] over Q_l u P, 128-bit lazy,
+//            with the Galois automorphism applied while loading D (hoisting).
+//   ModDown: out_i = (acc_i - BConv_{P->q_i}([acc]_P)) * P^{-1} mod q_i, the
+//            conversion, its forward NTT and the combination fused per limb,
+//            plus an optional addend (sigma_g(c0) for rotations, d0/d1 for
+//            relinearisation).
+//   Rescale: c'_i = (c_i - [c_top]_centred) * q_top^{-1} mod q_i, fused the same way.
+#include "keyswitch.cuh"
+#include "ntt_block.cuh"
+
+#define MAX_ALPHA 8
+
+__global__ void modup_kernel(u64 *D, const u64 *__restrict__ xc, const u64 *__restrict__ xe, size_t xe_bstride,
+                             u32 lp, u32 K, u32 L1, u32 alpha, u32 beta, int logn, const u64 *__restrict__ tab,
+                             const PrimeDev *__restrict__ pd) {
+    const u32 N = 1u << logn;
+    const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const u32 j = blockIdx.y, b = blockIdx.z;
+    const u32 lo = j * alpha;
+    const u32 hi = lo + alpha < lp ? lo + alpha : lp;
+    const u32 nd = hi - lo;
+    const u32 E = lp + K;
+    const u64 *tj = tab + (size_t)j * (2 * alpha + alpha * E);
+    u64 v[MAX_ALPHA];
+#pragma unroll
+    for (u32 i = 0; i < MAX_ALPHA; ++i) {
+        if (i < nd) {
+            u64 x = xc[((size_t)b * lp + lo + i) * N + n];
+            v[i] = nd == 1 ? x : mul_shoup(x, tj[i], tj[alpha + i], pd[lo + i].q);
+        }
+    }
+    u64 *Db = D + ((size_t)b * beta + j) * E * N + n;
+    for (u32 t = 0; t < E; ++t) {
+        u64 o;
+        if (t >= lo && t < hi) {
+            o = xe[(size_t)b * xe_bstride + (size_t)t * N + n];
+        } else {
+            const PrimeDev &P = pd[t < lp ? t : L1 + (t - lp)];
+            if (nd == 1) {
+                o = reduce64(v[0], P);
+            } else {
+                Acc128 acc = {0, 0};
+#pragma unroll
+                for (u32 i = 0; i < MAX_ALPHA; ++i)
+                    if (i < nd) mac128(acc, v[i], tj[2 * alpha + (size_t)i * E + t]);
+                o = reduce128(acc.lo, acc.hi, P);
+            }
+        }
+        Db[(size_t)t * N] = o;
+    }
+}
+
+__global__ void ks_inner_kernel(u64 *acc, const u64 *__restrict__ D, KeyList kl, u32 B, u32 beta, u32 lp, u32 K,
+                                u32 L1, int logn, const PrimeDev *__restrict__ pd) {
+    const u32 N = 1u << logn;
+    const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const u32 t = blockIdx.y;
+    const u32 s = blockIdx.z / B, b = blockIdx.z % B;
+    const u32 E = lp + K;
+    const u32 pt = t < lp ? t : L1 + (t - lp);
+    const u32 g = kl.g[s];
+    const u64 *key = kl.key[s];
+    const u32 src = g == 1 ? n : galois_src(n, g, logn);
+    const size_t kstride = (size_t)(L1 + K) * N;
+    Acc128 a0 = {0, 0}, a1 = {0, 0};
+    const u64 *Db = D + ((size_t)b * beta * E + t) * N + src;
+    for (u32 j = 0; j < beta; ++j) {
+        const u64 d = Db[(size_t)j * E * N];
+        const u64 *kj = key + (size_t)j * 2 * kstride + (size_t)pt * N + n;
+        mac128(a0, d, __ldg(kj));
+        mac128(a1, d, __ldg(kj + kstride));
+    }
+    const PrimeDev &P = pd[pt];
+    u64 *o = acc + (((size_t)s * B + b) * 2 * E + t) * N + n;
+    o[0] = reduce128(a0.lo, a0.hi, P);
+    o[(size_t)E * N] = reduce128(a1.lo, a1.hi, P);
+}
+
+__global__ void __launch_bounds__(1024) moddown_kernel(u64 *out, const u64 *__restrict__ acc,
+                                                       const u64 *__restrict__ addend, size_t addend_bstride,
+                                                       u32 add_mask, KeyList kl, u32 B, u32 lp, u32 K, u32 L1,
+                                                       int logn, const u64 *__restrict__ mdtab,
+                                                       const u64 *__restrict__ tw_all,
+                                                       const PrimeDev *__restrict__ pd) {
+    extern __shared__ u64 sm[];
+    const u32 N = 1u << logn;
+    const u32 i = blockIdx.x, k = blockIdx.y;
+    const u32 s = blockIdx.z / B, b = blockIdx.z % B;
+    const u32 E = lp + K;
+    const PrimeDev P = pd[i];
+    const u64 *ab = acc + (((size_t)s * B + b) * 2 + k) * E * N;
+    // mdtab: phinv[K], phinv_s[K], phmod[K][L1], Pinv[L1], Pinv_s[L1]
+    for (u32 n = threadIdx.x; n < N; n += blockDim.x) {
+        u64 v;
+        if (K == 1) {
+            v = reduce64(ab[(size_t)lp * N + n], P);
+        } else {
+            Acc128 a = {0, 0};
+            for (u32 kk = 0; kk < K; ++kk) {
+                const PrimeDev &Pk = pd[L1 + kk];
+                u64 y = mul_shoup(ab[(size_t)(lp + kk) * N + n], mdtab[kk], mdtab[K + kk], Pk.q);
+                mac128(a, y, mdtab[2 * K + (size_t)kk * L1 + i]);
+            }
+            v = reduce128(a.lo, a.hi, P);
+        }
+        sm[n] = v;
+    }
+    __syncthreads();
+    block_ntt_fwd(sm, logn, tw_all + (size_t)i * 4 * N, P.q);
+    const u64 pinv = mdtab[2 * K + (size_t)K * L1 + i];
+    const u64 pinvs = mdtab[2 * K + (size_t)K * L1 + L1 + i];
+    const bool add = addend && ((add_mask >> k) & 1);
+    const u32 g = kl.g[s];
+    const u64 *adb = add ? addend + (size_t)b * addend_bstride + ((size_t)k * lp + i) * N : nullptr;
+    u64 *ob = out + ((((size_t)s * B + b) * 2 + k) * lp + i) * N;
+    for (u32 n = threadIdx.x; n < N; n += blockDim.x) {
+        u64 o = mul_shoup(sub_mod(ab[(size_t)i * N + n], sm[n], P.q), pinv, pinvs, P.q);
+        if (add) o = add_mod(o, adb[g == 1 ? n : galois_src(n, g, logn)], P.q);
+        ob[n] = o;
+    }
+}
+
+__global__ void __launch_bounds__(1024) rescale_kernel(u64 *out, const u64 *__restrict__ in,
+                                                       const u64 *__restrict__ top, u32 lp, int logn,
+                                                       const u64 *__restrict__ rtab, const u64 *__restrict__ tw_all,
+                                                       const PrimeDev *__restrict__ pd) {
+    extern __shared__ u64 sm[];
+    const u32 N = 1u << logn;
+    const u32 i = blockIdx.x, k = blockIdx.y, b = blockIdx.z;
+    const PrimeDev P = pd[i];
+    const u64 qt = pd[lp - 1].q;
+    const u64 *tb = top + ((size_t)b * 2 + k) * N;
+    for (u32 n = threadIdx.x; n < N; n += blockDim.x) {
+        u64 v = tb[n];
+        sm[n] = v > qt / 2 ? neg_mod(reduce64(qt - v, P), P.q) : reduce64(v, P);
+    }
+    __syncthreads();
+    block_ntt_fwd(sm, logn, tw_all + (size_t)i * 4 * N, P.q);
+    const u64 w = rtab[i], ws = rtab[lp - 1 + i];
+    const u64 *ib = in + (((size_t)b * 2 + k) * lp + i) * N;
+    u64 *ob = out + (((size_t)b * 2 + k) * (lp - 1) + i) * N;
+    for (u32 n = threadIdx.x; n < N; n += blockDim.x) ob[n] = mul_shoup(sub_mod(ib[n], sm[n], P.q), w, ws, P.q);
+}
+
+// ------------------------------------------------------------------ host
+static u64 mulmod_h(u64 a, u64 b, u64 q) { return (u64)((unsigned __int128)a * b % q); }
+static u64 powmod_h(u64 a, u64 e, u64 q) {
+    u64 r = 1;
+    a %= q;
+    while (e) {
+        if (e & 1) r = mulmod_h(r, a, q);
+        a = mulmod_h(a, a, q);
+        e >>= 1;
+    }
+    return r;
+}
+static u64 invmod_h(u64 a, u64 q) { return powmod_h(a, q - 2, q); }
+static u64 shoup_h(u64 w, u64 q) { return (u64)(((unsigned __int128)w << 64) / q); }
+
+static void set_big_smem(const void *fn) {
+    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+}
+
+void keyswitch_init(Ctx *c) {
+    set_big_smem((const void *)moddown_kernel);
+    set_big_smem((const void *)rescale_kernel);
+}
+
+u32 ks_digits(const Ctx *c, u32 lp) { return (lp + c->alpha - 1) / c->alpha; }
+
+// ModUp constants for level lp: per digit j: qhinv[alpha], qhinv_s[alpha], qhmod[alpha][lp+K]
+static const u64 *modup_table(Ctx *c, u32 lp) {
+    std::string key = fmt("modup:%u", lp);
+    auto it = c->cache.find(key);
+    if (it != c->cache.end()) return it->second.p;
+    const u32 E = lp + c->K, A = c->alpha, beta = ks_digits(c, lp);
+    std::vector<u64> h((size_t)beta * (2 * A + A * E), 0);
+    for (u32 j = 0; j < beta; ++j) {
+        u32 lo = j * A, hi = std::min(lo + A, lp);
+        u64 *tj = h.data() + (size_t)j * (2 * A + A * E);
+        for (u32 i = lo; i < hi; ++i) {
+            u64 qi = c->primes[i];
+            u64 hh = 1;
+            for (u32 k = lo; k < hi; ++k)
+                if (k != i) hh = mulmod_h(hh, c->primes[k] % qi, qi);
+            u64 inv = invmod_h(hh, qi);
+            tj[i - lo] = inv;
+            tj[A + i - lo] = shoup_h(inv, qi);
+            for (u32 t = 0; t < E; ++t) {
+                u64 pt = c->primes[t < lp ? t : c->L1 + (t - lp)];
+                u64 m = 1;
+                for (u32 k = lo; k < hi; ++k)
+                    if (k != i) m = mulmod_h(m, c->primes[k] % pt, pt);
+                tj[2 * A + (size_t)(i - lo) * E + t] = m;
+            }
+        }
+    }
+    return c->const_table(key, h);
+}
+
+static const u64 *moddown_table(Ctx *c) {
+    std::string key = "moddown";
+    auto it = c->cache.find(key);
+    if (it != c->cache.end()) return it->second.p;
+    const u32 K = c->K, L1 = c->L1;
+    std::vector<u64> h(2 * K + (size_t)K * L1 + 2 * L1, 0);
+    for (u32 k = 0; k < K; ++k) {
+        u64 pk = c->primes[L1 + k];
+        u64 hh = 1;
+        for (u32 m = 0; m < K; ++m)
+            if (m != k) hh = mulmod_h(hh, c->primes[L1 + m] % pk, pk);
+        h[k] = invmod_h(hh, pk);
+        h[K + k] = shoup_h(h[k], pk);
+        for (u32 i = 0; i < L1; ++i) {
+            u64 qi = c->primes[i], m2 = 1;
+            for (u32 m = 0; m < K; ++m)
+                if (m != k) m2 = mulmod_h(m2, c->primes[L1 + m] % qi, qi);
+            h[2 * K + (size_t)k * L1 + i] = m2;
+        }
+    }
+    for (u32 i = 0; i < L1; ++i) {
+        u64 qi = c->primes[i], P = 1;
+        for (u32 k = 0; k < K; ++k) P = mulmod_h(P, c->primes[L1 + k] % qi, qi);
+        u64 inv = invmod_h(P, qi);
+        h[2 * K + (size_t)K * L1 + i] = inv;
+        h[2 * K + (size_t)K * L1 + L1 + i] = shoup_h(inv, qi);
+    }
+    return c->const_table(key, h);
+}
+
+static const u64 *rescale_table(Ctx *c, u32 lp) {
+    std::string key = fmt("rescale:%u", lp);
+    auto it = c->cache.find(key);
+    if (it != c->cache.end()) return it->second.p;
+    std::vector<u64> h(2 * (lp - 1));
+    u64 qt = c->primes[lp - 1];
+    for (u32 i = 0; i + 1 < lp; ++i) {
+        u64 qi = c->primes[i];
+        u64 inv = invmod_h(qt % qi, qi);
+        h[i] = inv;
+        h[lp - 1 + i] = shoup_h(inv, qi);
+    }
+    return c->const_table(key, h);
+}
+
+// D [B][beta][lp+K][N] from x: coefficient copy xc [B][lp][N] and eval rows at xe (+ b*xe_bstride)
+void ks_modup(Ctx *c, u64 *D, const u64 *xe, size_t xe_bstride, u32 B, u32 lp) {
+    const u32 N = c->N, E = lp + c->K, beta = ks_digits(c, lp);
+    if (c->alpha > MAX_ALPHA) throw HeError(HE_EINVAL, "digit size above 8 limbs is not supported");
+    DBuf xc(c, (size_t)B * lp * N);
+    // contiguous copy of the eval rows, then inverse NTT to coefficient form
+    CUDA_TRY(cudaMemcpy2DAsync(xc.p, (size_t)lp * N * 8, xe, xe_bstride * 8, (size_t)lp * N * 8, B,
+                               cudaMemcpyDeviceToDevice, c->stream));
+    ntt_inverse(c, xc.p, rows_regular(B * lp, lp, lp, 0));
+    const u64 *tab = modup_table(c, lp);
+    dim3 grid((N + 255) / 256, beta, B);
+    modup_kernel<<<grid, 256, 0, c->stream>>>(D, xc.p, xe, xe_bstride, lp, c->K, c->L1, c->alpha, beta, c->logn, tab,
+                                               c->pdev);
+    note_launch(c, "modup");
+    // forward NTT of every converted (non-own) row
+    std::string key = fmt("modup_rows:%u:%u", B, lp);
+    std::vector<u32> rows;
+    for (u32 b = 0; b < B; ++b)
+        for (u32 j = 0; j < beta; ++j) {
+            u32 lo = j * c->alpha, hi = std::min(lo + c->alpha, lp);
+            for (u32 t = 0; t < E; ++t) {
+                if (t >= lo && t < hi) continue;
+                u32 prime = t < lp ? t : c->L1 + (t - lp);
+                rows.push_back(((((u32)b * beta + j) * E + t) << 8) | prime);
+            }
+        }
+    RowSet rs = rows_list(c, key, rows);
+    ntt_forward(c, D, rs);
+}
+
+// acc [S][B][2][lp+K][N] = sum_j sigma_{g_s}(D_j) (o) key_s,j
+void ks_inner(Ctx *c, u64 *acc, const u64 *D, const KeyList &kl, u32 S, u32 B, u32 lp) {
+    const u32 N = c->N, E = lp + c->K;
+    dim3 grid((N + 255) / 256, E, S * B);
+    ks_inner_kernel<<<grid, 256, 0, c->stream>>>(acc, D, kl, B, ks_digits(c, lp), lp, c->K, c->L1, c->logn, c->pdev);
+    note_launch(c, "ks_inner");
+}
+
+// out [S][B][2][lp][N] = ModDown(acc) (+ addend: poly k of ct b gathered by sigma_{g_s} when add_mask bit k)
+void ks_moddown(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bstride, u32 add_mask,
+                const KeyList &kl, u32 S, u32 B, u32 lp) {
+    const u32 N = c->N, E = lp + c->K;
+    // inverse NTT of the special-prime rows of acc
+    std::string key = fmt("md_rows:%u:%u:%u", S, B, lp);
+    std::vector<u32> rows;
+    for (u32 sb = 0; sb < S * B; ++sb)
+        for (u32 k = 0; k < 2; ++k)
+            for (u32 kk = 0; kk < c->K; ++kk) rows.push_back((((sb * 2 + k) * E + lp + kk) << 8) | (c->L1 + kk));
+    ntt_inverse(c, acc, rows_list(c, key, rows));
+    dim3 grid(lp, 2, S * B);
+    moddown_kernel<<<grid, ntt_threads(N), (size_t)N * 8, c->stream>>>(out, acc, addend, addend_bstride, add_mask, kl, B,
+                                                                      lp, c->K, c->L1, c->logn, moddown_table(c),
+                                                                      c->tw, c->pdev);
+    note_launch(c, "moddown");
+}
+
+// out [B][2][lp-1][N] = rescale(in [B][2][lp][N])
+void rescale_batch(Ctx *c, u64 *out, const u64 *in, u32 B, u32 lp) {
+    const u32 N = c->N;
+    if (lp < 2) throw HeError(HE_ELEVEL, "rescale: no level left");
+    DBuf top(c, (size_t)B * 2 * N);
+    gather_rows(c, top.p, in + (size_t)(lp - 1) * N, B * 2, lp);
+    ntt_inverse(c, top.p, rows_regular(B * 2, 1, 0, lp - 1));
+    dim3 grid(lp - 1, 2, B);
+    rescale_kernel<<<grid, ntt_threads(N), (size_t)N * 8, c->stream>>>(out, in, top.p, lp, c->logn,
+                                                                      rescale_table(c, lp), c->tw, c->pdev);
+    note_launch(c, "rescale");
+}

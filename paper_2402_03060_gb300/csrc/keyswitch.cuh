@@ -1,0 +1,20 @@
+// keyswitch.cuh -- hybrid key switching and rescale (keyswitch.cu).
+#pragma once
+#include "he_internal.cuh"
+#include "ring.cuh"
+
+#define KEYLIST_MAX 64
+// Per rotation step s of one launch: the switching key [dnum][2][L+1+K][N] and
+// the Galois element applied to the ModUp'ed digits (1 = none).
+struct KeyList {
+    const u64 *key[KEYLIST_MAX];
+    u32 g[KEYLIST_MAX];
+};
+
+void keyswitch_init(Ctx *c);
+u32 ks_digits(const Ctx *c, u32 lp);
+void ks_modup(Ctx *c, u64 *D, const u64 *xe, size_t xe_bstride, u32 B, u32 lp);
+void ks_inner(Ctx *c, u64 *acc, const u64 *D, const KeyList &kl, u32 S, u32 B, u32 lp);
+void ks_moddown(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bstride, u32 add_mask,
+                const KeyList &kl, u32 S, u32 B, u32 lp);
+void rescale_batch(Ctx *c, u64 *out, const u64 *in, u32 B, u32 lp);

@@ -1,0 +1,990 @@
+// layers.cu -- UniHENN's layers (paper Sec. IV), the layout planner (Sec. V),
+// compiled models with batched / graph-replayed inference, and the C ABI.
+//
+// A feature map is held as ONE ciphertext batch of CH*B ciphertexts
+// (channel-major: ciphertext index ch*B + b), so every per-channel operation
+// of a layer -- rotations by the same steps, masks, squares, rescales -- is a
+// single set of kernel launches over all channels and all ciphertexts.
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <set>
+
+#include "ops.cuh"
+
+// ------------------------------------------------------------------ helpers
+struct Feat {
+    Cts x;        // CH*B ciphertexts
+    u32 CH = 1, B = 1;
+    Cts chan(Ctx *c, u32 ch) const { return cts_view(x, (size_t)ch * B * cts_ct_words(c, x.lp), B); }
+};
+
+// cached encoded plaintexts of a compiled model (nullptr: encode every call)
+struct PtCache {
+    std::map<std::string, DBuf> pts;
+};
+
+struct LayerSpec {
+    u32 op = 0, ci = 0, co = 0, k = 0, s = 1;
+    std::vector<double> w, b;
+};
+
+static std::vector<u32> valid_positions(const Layout &L, u32 Hout, u32 Wout, u32 Iout) {
+    std::vector<u32> pos;
+    for (u32 r = 0; r < Hout; ++r)
+        for (u32 c = 0; c < Wout; ++c) pos.push_back(Iout * (r * L.W_img + c));
+    return pos;
+}
+
+// encoded plaintexts for nv sparse slot vectors at level lp / scale; cached under key
+static const u64 *get_pts(Ctx *c, PtCache *pc, const std::string &key, std::vector<DBuf> &tmp, const Layout &L,
+                          const std::vector<u32> &off, const std::vector<u32> &pos, const std::vector<double> &val,
+                          double scale, u32 lp) {
+    if (pc) {
+        auto it = pc->pts.find(key);
+        if (it != pc->pts.end()) return it->second.p;
+    }
+    u32 nv = (u32)off.size() - 1;
+    Pool *saved = c->active;
+    if (pc) c->active = nullptr;   // cached plaintexts live in the context pool
+    DBuf out(c, (size_t)nv * lp * c->N);
+    c->active = saved;
+    encode_sparse(c, out.p, key, off, pos, val, L.stride, L.n_samples, scale, lp);
+    u64 *p = out.p;
+    if (pc)
+        pc->pts.emplace(key, std::move(out));
+    else
+        tmp.push_back(std::move(out));
+    return p;
+}
+
+static Cts stack_sum(Ctx *c, const Cts &base, u32 T, u32 Bt) {
+    // sum of T consecutive batches of Bt ciphertexts inside base
+    const size_t w = (size_t)Bt * cts_ct_words(c, base.lp);
+    Cts acc = cts_alloc(c, Bt, base.lp, base.scale, base.lay);
+    CUDA_TRY(cudaMemcpyAsync(acc.data(), base.data(), w * 8, cudaMemcpyDeviceToDevice, c->stream));
+    for (u32 t = 1; t < T; ++t)
+        ew_binop(c, OP_ADD, acc.data(), acc.data(), base.data() + t * w, Bt * 2 * base.lp, base.lp, base.lp, 0);
+    return acc;
+}
+
+// ------------------------------------------------------------------ layers
+// Algorithm 1 (Sec. IV-B).  w: [co][ci][kh][kw].  Rotations Rot(C_in(i), I*(k + W_img*j));
+// per output channel: sum of Mul(rot, K(o,i,j,k)) with K the weight (times the
+// pending pooling factor) at every valid output slot, rescale, Add(bias at the
+// valid output slots).  I_out = I*S.
+static Feat layer_conv(Ctx *c, const Feat &in, const LayerSpec &sp, u32 kh, u32 kw, bool incremental, PtCache *pc,
+                       const std::string &key) {
+    const Layout &L = in.x.lay;
+    const u32 ci = sp.ci, co = sp.co, S = sp.s, B = in.B, lp = in.x.lp, N = c->N;
+    if (in.CH != ci) throw HeError(HE_EINVAL, "conv: channel count mismatch");
+    if (lp < 2) throw HeError(HE_ELEVEL, "conv: no level left");
+    if (kh > L.H || kw > L.W) throw HeError(HE_EINVAL, "conv: kernel larger than the feature map");
+    const u32 Hout = (L.H - kh) / S + 1, Wout = (L.W - kw) / S + 1, Iout = L.I * S;
+    const u32 KK = kh * kw;
+    std::vector<int> steps;
+    for (u32 j = 0; j < kh; ++j)
+        for (u32 k = 0; k < kw; ++k) steps.push_back((int)(L.I * (k + L.W_img * j)));
+    // rotated inputs R[off][ch*B + b]  (T index = off*ci + ch)
+    const size_t ctw = cts_ct_words(c, lp);
+    Cts R = cts_alloc(c, KK * ci * B, lp, in.x.scale, L);
+    if (!incremental) {
+        ct_rotate_hoisted_into(c, in.x, steps, R.data());
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(R.data(), in.x.data(), (size_t)ci * B * ctw * 8, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+        for (u32 t = 1; t < KK; ++t) {
+            u32 k = t % kw;
+            int st = (int)(k > 0 ? L.I : L.I * (L.W_img - kw + 1));
+            Cts prev = cts_view(R, (size_t)(t - 1) * ci * B * ctw, ci * B);
+            Cts r = ct_rotate(c, prev, st);
+            CUDA_TRY(cudaMemcpyAsync(R.data() + (size_t)t * ci * B * ctw, r.data(), (size_t)ci * B * ctw * 8,
+                                     cudaMemcpyDeviceToDevice, c->stream));
+        }
+    }
+    // plaintexts pt[o][off*ci + i]
+    std::vector<u32> vpos = valid_positions(L, Hout, Wout, Iout);
+    const u32 T = KK * ci;
+    std::vector<DBuf> tmp;
+    const u64 *pts;
+    {
+        std::vector<u32> off, pos;
+        std::vector<double> val;
+        if (!pc || !pc->pts.count(key + ":w")) {
+            off.push_back(0);
+            for (u32 o = 0; o < co; ++o)
+                for (u32 t = 0; t < T; ++t) {
+                    u32 kk = t / ci, i = t % ci, j = kk / kw, k = kk % kw;
+                    double wv = sp.w[(((size_t)o * ci + i) * kh + j) * kw + k] * L.pending;
+                    for (u32 p : vpos) {
+                        pos.push_back(p);
+                        val.push_back(wv);
+                    }
+                    off.push_back((u32)pos.size());
+                }
+        }
+        pts = get_pts(c, pc, key + ":w", tmp, L, off, pos, val, c->scale, lp);
+    }
+    Cts acc = cts_alloc(c, co * B, lp, in.x.scale * c->scale, L);
+    // R[off][i*B + b] is block t = off*ci + i of B ciphertexts
+    mac(c, acc.data(), (size_t)B * ctw, R.data(), (size_t)B * ctw, pts, co, T, B, lp);
+    Cts out = ct_rescale(c, acc);
+    {
+        std::vector<u32> off, pos;
+        std::vector<double> val;
+        if (!pc || !pc->pts.count(key + ":b")) {
+            off.push_back(0);
+            for (u32 o = 0; o < co; ++o) {
+                for (u32 p : vpos) {
+                    pos.push_back(p);
+                    val.push_back(sp.b[o]);
+                }
+                off.push_back((u32)pos.size());
+            }
+        }
+        const u64 *bp = get_pts(c, pc, key + ":b", tmp, L, off, pos, val, out.scale, lp - 1);
+        add_plain_multi(c, out.data(), bp, co, B, lp - 1, (size_t)B * cts_ct_words(c, lp - 1));
+    }
+    Layout L2 = L;
+    L2.W = Wout;
+    L2.H = Hout;
+    L2.I = Iout;
+    L2.pending = 1.0;
+    L2.prev = PREV_CONV;
+    out.lay = L2;
+    Feat f;
+    f.x = out;
+    f.CH = co;
+    f.B = B;
+    (void)N;
+    return f;
+}
+
+// Sec. IV-C: c x c average pooling by rotations and additions, no level; 1/c^2 deferred.
+static Feat layer_avgpool(Ctx *c, const Feat &in, u32 cc) {
+    const Layout &L = in.x.lay;
+    const u32 ch = L.dims == 2 ? cc : 1;
+    std::vector<int> steps;
+    for (u32 j = 0; j < ch; ++j)
+        for (u32 k = 0; k < cc; ++k) steps.push_back((int)(L.I * (k + L.W_img * j)));
+    const u32 Bt = in.CH * in.B;
+    Cts R = cts_alloc(c, (u32)steps.size() * Bt, in.x.lp, in.x.scale, L);
+    ct_rotate_hoisted_into(c, in.x, steps, R.data());
+    Cts out = stack_sum(c, R, (u32)steps.size(), Bt);
+    Layout L2 = L;
+    L2.W = L.W / cc;
+    L2.H = L.dims == 2 ? L.H / cc : 1;
+    L2.I = L.I * cc;
+    L2.pending = L.pending / (double)(L.dims == 2 ? cc * cc : cc);
+    L2.prev = PREV_POOL;
+    out.lay = L2;
+    Feat f = in;
+    f.x = out;
+    return f;
+}
+
+// square activation: Mul (C), relinearise, rescale; pending p -> p^2
+static Feat layer_square(Ctx *c, const Feat &in) {
+    Feat f = in;
+    f.x = ct_square(c, in.x);
+    f.x.lay.pending = in.x.lay.pending * in.x.lay.pending;
+    return f;
+}
+
+// multiply every ciphertext of x by one mask (Delta), rescale, rotate left by r
+static Cts mask_rescale_rotate(Ctx *c, const Cts &x, const u64 *pt, int r) {
+    Cts t = ct_rescale(c, ct_mul_pt(c, x, pt, c->scale));
+    return r ? ct_rotate(c, t, r) : t;
+}
+
+static void accumulate(Ctx *c, Cts &acc, bool &have, const Cts &t) {
+    if (!have) {
+        acc = t;
+        have = true;
+    } else {
+        ct_add_inplace(c, acc, t);
+    }
+}
+
+// Sec. IV-E: remove intervals / invalid values, pack the channels.
+static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string &key) {
+    const Layout &L = in.x.lay;
+    const u32 I = L.I, W = L.W, H = L.H, Wi = L.W_img;
+    std::vector<DBuf> tmp;
+    Cts cur = in.x;
+    double pending = L.pending;
+    auto mask_pt = [&](const std::string &k, const std::vector<u32> &pos, double v, u32 lp) {
+        std::vector<u32> off{0, (u32)pos.size()};
+        std::vector<double> val(pos.size(), v);
+        return get_pts(c, pc, key + k, tmp, L, off, pos, val, c->scale, lp);
+    };
+    if (L.prev == PREV_POOL) {
+        Cts acc;
+        bool have = false;
+        for (u32 cc = 0; cc < W; ++cc) {
+            std::vector<u32> pos;
+            for (u32 r = 0; r < H; ++r) pos.push_back(I * (r * Wi + cc));
+            const u64 *pt = mask_pt(fmt(":col%u", cc), pos, pending, cur.lp);
+            accumulate(c, acc, have, mask_rescale_rotate(c, cur, pt, (int)(cc * (I - 1))));
+        }
+        cur = acc;
+        pending = 1.0;
+    } else if (L.prev == PREV_CONV) {
+        if (pending != 1.0) throw HeError(HE_EINVAL, "flatten: unexpected pending factor");
+        if (I > 1 && W > 1) {
+            std::vector<int> st;
+            for (u32 m = 0; m < I; ++m) st.push_back((int)(m * (I - 1)));
+            Cts R = cts_alloc(c, I * cur.B, cur.lp, cur.scale, L);
+            ct_rotate_hoisted_into(c, cur, st, R.data());
+            Cts y = stack_sum(c, R, I, cur.B);
+            Cts acc;
+            bool have = false;
+            for (u32 u = 0; u < (W + I - 1) / I; ++u) {
+                std::vector<u32> pos;
+                for (u32 r = 0; r < H; ++r)
+                    for (u32 cc = I * u; cc < std::min(I * u + I, W); ++cc)
+                        pos.push_back(I * r * Wi + I * I * u + (cc - I * u));
+                const u64 *pt = mask_pt(fmt(":blk%u", u), pos, 1.0, y.lp);
+                accumulate(c, acc, have, mask_rescale_rotate(c, y, pt, (int)(u * I * (I - 1))));
+            }
+            cur = acc;
+        }
+    } else {
+        throw HeError(HE_EINVAL, "flatten must follow a convolution or an average pooling");
+    }
+    if (H > 1) {
+        Cts acc;
+        bool have = false;
+        for (u32 r = 0; r < H; ++r) {
+            std::vector<u32> pos;
+            for (u32 cc = 0; cc < W; ++cc) pos.push_back(I * r * Wi + cc);
+            const u64 *pt = mask_pt(fmt(":row%u", r), pos, 1.0, cur.lp);
+            accumulate(c, acc, have, mask_rescale_rotate(c, cur, pt, (int)(r * (Wi * I - W))));
+        }
+        cur = acc;
+    }
+    // pack: channel o rotated right by o*W*H
+    Feat f;
+    f.CH = 1;
+    f.B = in.B;
+    Cts acc;
+    bool have = false;
+    for (u32 o = 0; o < in.CH; ++o) {
+        Cts x = cts_view(cur, (size_t)o * in.B * cts_ct_words(c, cur.lp), in.B);
+        if (o) x = ct_rotate(c, x, -(int)(o * W * H));
+        if (!have) {
+            acc = cts_alloc(c, in.B, x.lp, x.scale, x.lay);
+            CUDA_TRY(cudaMemcpyAsync(acc.data(), x.data(), (size_t)in.B * cts_ct_words(c, x.lp) * 8,
+                                     cudaMemcpyDeviceToDevice, c->stream));
+            have = true;
+        } else {
+            ct_add_inplace(c, acc, x);
+        }
+    }
+    Layout L2 = L;
+    L2.pending = pending;
+    L2.prev = PREV_FLAT;
+    L2.D = in.CH * W * H;
+    L2.W = L2.D;
+    L2.H = 1;
+    L2.I = 1;
+    acc.lay = L2;
+    f.x = acc;
+    return f;
+}
+
+// Algorithm 2 (Sec. IV-D) on a flattened ciphertext; M [dout][din]
+static Feat layer_fc(Ctx *c, const Feat &in, const LayerSpec &sp, PtCache *pc, const std::string &key) {
+    const Layout &L = in.x.lay;
+    const u32 din = sp.ci, dout = sp.co, B = in.B;
+    if (in.CH != 1 || (L.prev != PREV_FLAT && L.prev != PREV_FC)) throw HeError(HE_EINVAL, "FC needs a flattened input");
+    if (din != L.D) throw HeError(HE_EINVAL, fmt("FC expects %u inputs, layout has %u", din, L.D));
+    if (in.x.lp < 2) throw HeError(HE_ELEVEL, "FC: no level left");
+    const u32 Wv = (din + dout - 1) / dout * dout;
+    // steps: o for o < dout, then o - Wv for 1 <= o < dout
+    std::vector<int> steps;
+    for (u32 o = 0; o < dout; ++o) steps.push_back((int)o);
+    for (u32 o = 1; o < dout; ++o) steps.push_back((int)o - (int)Wv);
+    const u32 T = (u32)steps.size();
+    const u32 lp = in.x.lp;
+    const size_t ctw = cts_ct_words(c, lp);
+    std::vector<DBuf> tmp;
+    const u64 *pts;
+    {
+        std::vector<u32> off, pos;
+        std::vector<double> val;
+        if (!pc || !pc->pts.count(key + ":w")) {
+            // M_rot[o][t] = M_pad[t mod dout][(t + o) mod Wv] (times the pending factor)
+            auto mrot = [&](u32 o, u32 t) -> double {
+                u32 row = t % dout, col = (t + o) % Wv;
+                if (col >= din) return 0.0;
+                double m = sp.w[(size_t)row * din + col];
+                return L.pending != 1.0 ? m * L.pending : m;
+            };
+            off.push_back(0);
+            for (u32 o = 0; o < dout; ++o) {   // V1_o: t < Wv - o
+                for (u32 t = 0; t < Wv - o; ++t) {
+                    pos.push_back(t);
+                    val.push_back(mrot(o, t));
+                }
+                off.push_back((u32)pos.size());
+            }
+            for (u32 o = 1; o < dout; ++o) {   // V2_o: t >= Wv - o
+                for (u32 t = Wv - o; t < Wv; ++t) {
+                    pos.push_back(t);
+                    val.push_back(mrot(o, t));
+                }
+                off.push_back((u32)pos.size());
+            }
+        }
+        pts = get_pts(c, pc, key + ":w", tmp, L, off, pos, val, c->scale, lp);
+    }
+    Cts R = cts_alloc(c, T * B, lp, in.x.scale, L);
+    ct_rotate_hoisted_into(c, in.x, steps, R.data());
+    Cts acc = cts_alloc(c, B, lp, in.x.scale * c->scale, L);
+    mac(c, acc.data(), (size_t)B * ctw, R.data(), (size_t)B * ctw, pts, 1, T, B, lp);
+    Cts cs = ct_rescale(c, acc);
+    const u32 nsum = Wv / dout;
+    std::vector<int> st2;
+    for (u32 i = 0; i < nsum; ++i) st2.push_back((int)(i * dout));
+    Cts R2 = cts_alloc(c, nsum * B, cs.lp, cs.scale, L);
+    ct_rotate_hoisted_into(c, cs, st2, R2.data());
+    Cts out = stack_sum(c, R2, nsum, B);
+    {
+        std::vector<u32> off{0}, pos;
+        std::vector<double> val;
+        if (!pc || !pc->pts.count(key + ":b")) {
+            for (u32 t = 0; t < dout; ++t) {
+                pos.push_back(t);
+                val.push_back(sp.b[t]);
+            }
+            off.push_back((u32)pos.size());
+        }
+        const u64 *bp = get_pts(c, pc, key + ":b", tmp, L, off, pos, val, out.scale, out.lp);
+        ct_add_pt_inplace(c, out, bp);
+    }
+    Layout L2 = L;
+    L2.pending = 1.0;
+    L2.prev = PREV_FC;
+    L2.D = dout;
+    L2.W = dout;
+    out.lay = L2;
+    Feat f;
+    f.x = out;
+    f.CH = 1;
+    f.B = B;
+    return f;
+}
+
+// ------------------------------------------------------------------ planner
+struct Plan {
+    u32 stride = 0, levels = 0;
+    std::vector<int> steps;
+};
+
+// Sec. V: the slots one sample needs = max(input W*H (Theorem 1 keeps every later
+// valid value inside it), CH*W*H of a flatten, W_vec of an FC); levels and steps.
+static Plan plan_layers(const std::vector<LayerSpec> &ls, u32 Wi, u32 Hi) {
+    const u32 dims = Hi == 1 ? 1 : 2;
+    u32 W = Wi, H = Hi, I = 1, ch = 1, need = Wi * Hi, levels = 0;
+    int prev = PREV_INPUT;
+    std::set<int> st;
+    for (const LayerSpec &s : ls) {
+        if (s.op == HE_CONV2D || s.op == HE_CONV1D) {
+            u32 kh = s.op == HE_CONV2D ? s.k : 1, kw = s.k;
+            if (s.op == HE_CONV2D && dims == 1) throw HeError(HE_EINVAL, "conv2d on a 1-D input");
+            if (kh > H || kw > W || s.s < 1) throw HeError(HE_EINVAL, "conv kernel does not fit");
+            for (u32 j = 0; j < kh; ++j)
+                for (u32 k = 0; k < kw; ++k) st.insert((int)(I * (k + Wi * j)));
+            H = (H - kh) / s.s + 1;
+            W = (W - kw) / s.s + 1;
+            I *= s.s;
+            ch = s.co;
+            levels += 1;
+            prev = PREV_CONV;
+        } else if (s.op == HE_SQUARE) {
+            levels += 1;
+        } else if (s.op == HE_AVGPOOL) {
+            u32 c = s.k, ckh = dims == 2 ? c : 1;
+            if (c < 1 || c > W) throw HeError(HE_EINVAL, "pool size does not fit");
+            for (u32 j = 0; j < ckh; ++j)
+                for (u32 k = 0; k < c; ++k) st.insert((int)(I * (k + Wi * j)));
+            W /= c;
+            H = dims == 2 ? H / c : 1;
+            I *= c;
+            prev = PREV_POOL;
+        } else if (s.op == HE_FLATTEN || s.op == HE_FC) {
+            if (prev == PREV_CONV || prev == PREV_POOL) {
+                if (prev == PREV_POOL) {
+                    levels += 1;
+                    for (u32 c = 0; c < W; ++c) st.insert((int)(c * (I - 1)));
+                } else if (I > 1 && W > 1) {
+                    levels += 1;
+                    for (u32 m = 0; m < I; ++m) st.insert((int)(m * (I - 1)));
+                    for (u32 u = 0; u < (W + I - 1) / I; ++u) st.insert((int)(u * I * (I - 1)));
+                }
+                if (H > 1) {
+                    levels += 1;
+                    for (u32 r = 0; r < H; ++r) st.insert((int)(r * (Wi * I - W)));
+                }
+                for (u32 o = 0; o < ch; ++o) st.insert(-(int)(o * W * H));
+                need = std::max(need, ch * W * H);
+                prev = PREV_FLAT;
+                W = ch * W * H;
+                H = 1;
+                I = 1;
+                ch = 1;
+            }
+            if (s.op == HE_FC) {
+                if (prev != PREV_FLAT && prev != PREV_FC) throw HeError(HE_EINVAL, "FC needs a flattened input");
+                if (s.ci != W) throw HeError(HE_EINVAL, fmt("FC DAT_in %u does not match %u", s.ci, W));
+                u32 Wv = (s.ci + s.co - 1) / s.co * s.co;
+                need = std::max(need, Wv);
+                for (u32 o = 0; o < s.co; ++o) st.insert((int)o);
+                for (u32 o = 1; o < s.co; ++o) st.insert((int)o - (int)Wv);
+                for (u32 i = 0; i < Wv / s.co; ++i) st.insert((int)(i * s.co));
+                levels += 1;
+                prev = PREV_FC;
+                W = s.co;
+            }
+        } else {
+            throw HeError(HE_EINVAL, "unknown layer op");
+        }
+    }
+    st.erase(0);
+    Plan p;
+    p.stride = need;
+    p.levels = levels;
+    p.steps.assign(st.begin(), st.end());
+    return p;
+}
+
+static std::vector<LayerSpec> copy_layers(const he_layer *layers, size_t n, u32 Hi) {
+    std::vector<LayerSpec> out;
+    for (size_t i = 0; i < n; ++i) {
+        const he_layer &l = layers[i];
+        LayerSpec s;
+        s.op = l.op;
+        s.ci = l.ch_in;
+        s.co = l.ch_out;
+        s.k = l.k;
+        s.s = l.stride ? l.stride : 1;
+        size_t nw = 0;
+        if (l.op == HE_CONV2D) nw = (size_t)l.ch_out * l.ch_in * l.k * l.k;
+        if (l.op == HE_CONV1D) nw = (size_t)l.ch_out * l.ch_in * l.k;
+        if (l.op == HE_FC) nw = (size_t)l.ch_out * l.ch_in;
+        if (nw) {
+            if (!l.w || !l.b) throw HeError(HE_EINVAL, "layer weights missing");
+            s.w.assign(l.w, l.w + nw);
+            s.b.assign(l.b, l.b + l.ch_out);
+        }
+        if (l.op < HE_CONV2D || l.op > HE_FC) throw HeError(HE_EINVAL, "unknown layer op");
+        out.push_back(std::move(s));
+    }
+    (void)Hi;
+    return out;
+}
+
+static Feat run_layers(Ctx *c, Feat f, const std::vector<LayerSpec> &ls, PtCache *pc) {
+    for (size_t i = 0; i < ls.size(); ++i) {
+        const LayerSpec &s = ls[i];
+        std::string key = fmt("L%zu", i);
+        switch (s.op) {
+            case HE_CONV2D: f = layer_conv(c, f, s, s.k, s.k, false, pc, key); break;
+            case HE_CONV1D: f = layer_conv(c, f, s, 1, s.k, false, pc, key); break;
+            case HE_SQUARE: f = layer_square(c, f); break;
+            case HE_AVGPOOL: f = layer_avgpool(c, f, s.k); break;
+            case HE_FLATTEN: f = layer_flatten(c, f, pc, key); break;
+            case HE_FC:
+                if (f.x.lay.prev != PREV_FLAT && f.x.lay.prev != PREV_FC) f = layer_flatten(c, f, pc, key + "f");
+                f = layer_fc(c, f, s, pc, key);
+                break;
+        }
+    }
+    return f;
+}
+
+// ------------------------------------------------------------------ model
+struct ModelGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    Cts in, out;
+};
+
+struct he_model {
+    Ctx *c = nullptr;
+    std::vector<LayerSpec> layers;
+    u32 W_img = 0, H_img = 0, spc = 0;
+    Plan plan;
+    PtCache pc;
+    Pool gpool;                            // private pool of the captured graphs
+    std::map<std::string, ModelGraph> graphs;
+    ~he_model() {
+        for (auto &kv : graphs) {
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+        }
+        graphs.clear();
+        pc.pts.clear();
+        gpool.release_all();
+    }
+};
+
+struct he_ct {
+    Ctx *c = nullptr;
+    Cts x;
+};
+
+struct he_ctx {
+    Ctx *c = nullptr;
+};
+
+// ------------------------------------------------------------------ C ABI
+static thread_local std::string g_err;
+
+template <class F>
+static he_status guard(F &&f) {
+    try {
+        f();
+        return HE_OK;
+    } catch (const HeError &e) {
+        g_err = e.what();
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        g_err = "host allocation failed";
+        return HE_ENOMEM;
+    } catch (const std::exception &e) {
+        g_err = e.what();
+        return HE_EINVAL;
+    }
+}
+
+static Ctx *CX(he_ctx *h) {
+    if (!h || !h->c) throw HeError(HE_EINVAL, "null context");
+    CUDA_TRY(cudaSetDevice(h->c->device));
+    return h->c;
+}
+
+static he_ct *wrap(Ctx *c, const Cts &x) {
+    he_ct *h = new he_ct();
+    h->c = c;
+    h->x = x;
+    return h;
+}
+
+static Feat gather_channels(Ctx *c, he_ct *const *in, u32 ch) {
+    if (!in || !ch) throw HeError(HE_EINVAL, "no input channels");
+    for (u32 i = 0; i < ch; ++i)
+        if (!in[i]) throw HeError(HE_EINVAL, "null ciphertext");
+    const Cts &a = in[0]->x;
+    for (u32 i = 1; i < ch; ++i) {
+        const Cts &b = in[i]->x;
+        if (b.B != a.B || b.lp != a.lp) throw HeError(HE_EINVAL, "channels differ in batch or level");
+        if (b.scale != a.scale) throw HeError(HE_ESCALE, "channels differ in scale");
+    }
+    Feat f;
+    f.CH = ch;
+    f.B = a.B;
+    if (ch == 1) {
+        f.x = a;
+        return f;
+    }
+    f.x = cts_alloc(c, ch * a.B, a.lp, a.scale, a.lay);
+    const size_t w = (size_t)a.B * cts_ct_words(c, a.lp);
+    for (u32 i = 0; i < ch; ++i)
+        CUDA_TRY(cudaMemcpyAsync(f.x.data() + i * w, in[i]->x.data(), w * 8, cudaMemcpyDeviceToDevice, c->stream));
+    return f;
+}
+
+static void scatter_channels(Ctx *c, const Feat &f, he_ct **out) {
+    for (u32 i = 0; i < f.CH; ++i) out[i] = wrap(c, f.chan(c, i));
+}
+
+extern "C" {
+
+const char *he_last_error(void) { return g_err.c_str(); }
+
+he_status he_context_create(const he_params *p, he_ctx **out) {
+    return guard([&] {
+        if (!out) throw HeError(HE_EINVAL, "null output");
+        Ctx *c = ctx_create(p);
+        he_ctx *h = new he_ctx();
+        h->c = c;
+        *out = h;
+    });
+}
+
+void he_context_destroy(he_ctx *h) {
+    if (!h) return;
+    ctx_destroy(h->c);
+    delete h;
+}
+
+he_status he_context_primes(const he_ctx *h, uint64_t *out, size_t n) {
+    return guard([&] {
+        if (!h || !out || n < h->c->primes.size()) throw HeError(HE_EINVAL, "bad arguments");
+        memcpy(out, h->c->primes.data(), h->c->primes.size() * 8);
+    });
+}
+
+he_status he_keygen(he_ctx *h, const int32_t *steps, size_t n) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (n && !steps) throw HeError(HE_EINVAL, "null steps");
+        keygen(c, std::vector<int>(steps, steps + n));
+    });
+}
+
+he_status he_encrypt(he_ctx *h, const double *x, int x_on_device, uint32_t W, uint32_t H, uint32_t nsamp,
+                     uint32_t spc, uint32_t stride, uint64_t enc_seed, he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!x || !out || !W || !H || !nsamp) throw HeError(HE_EINVAL, "bad arguments");
+        const size_t len = (size_t)nsamp * W * H;
+        const double *xd = x;
+        DBuf tmp;
+        if (!x_on_device) {
+            tmp = DBuf(c, len);
+            CUDA_TRY(cudaMemcpyAsync(tmp.p, x, len * 8, cudaMemcpyHostToDevice, c->stream));
+            xd = reinterpret_cast<const double *>(tmp.p);
+        }
+        Cts ct = encrypt(c, xd, W, H, nsamp, spc, stride, enc_seed);
+        if (!x_on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
+        *out = wrap(c, ct);
+    });
+}
+
+he_status he_decrypt(he_ctx *h, const he_ct *ct, double *out, int out_on_device, size_t nper) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!ct || !out || !nper) throw HeError(HE_EINVAL, "bad arguments");
+        const Cts &x = ct->x;
+        if (nper > x.lay.stride && x.lay.n_samples > 1) throw HeError(HE_EINVAL, "n_per_sample above the stride");
+        const size_t total = (size_t)x.B * x.lay.n_samples * nper;
+        if (out_on_device) {
+            decrypt_decode(c, out, x.data(), x.B, x.lp, x.scale, x.lay.stride, x.lay.n_samples, (u32)nper);
+        } else {
+            DBuf d(c, total);
+            decrypt_decode(c, reinterpret_cast<double *>(d.p), x.data(), x.B, x.lp, x.scale, x.lay.stride,
+                           x.lay.n_samples, (u32)nper);
+            CUDA_TRY(cudaMemcpyAsync(out, d.p, total * 8, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+        }
+    });
+}
+
+he_status he_ct_info(const he_ct *ct, uint32_t *batch, uint32_t *limbs, double *scale) {
+    return guard([&] {
+        if (!ct) throw HeError(HE_EINVAL, "null ciphertext");
+        if (batch) *batch = ct->x.B;
+        if (limbs) *limbs = ct->x.lp;
+        if (scale) *scale = ct->x.scale;
+    });
+}
+
+he_status he_ct_layout(const he_ct *ct, uint32_t *spc, uint32_t *stride, uint32_t *interval) {
+    return guard([&] {
+        if (!ct) throw HeError(HE_EINVAL, "null ciphertext");
+        if (spc) *spc = ct->x.lay.n_samples;
+        if (stride) *stride = ct->x.lay.stride;
+        if (interval) *interval = ct->x.lay.I;
+    });
+}
+
+he_status he_ct_export(he_ctx *h, const he_ct *ct, uint64_t *coeff) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!ct || !coeff) throw HeError(HE_EINVAL, "bad arguments");
+        const Cts &x = ct->x;
+        const size_t w = (size_t)x.B * cts_ct_words(c, x.lp);
+        DBuf t(c, w);
+        CUDA_TRY(cudaMemcpyAsync(t.p, x.data(), w * 8, cudaMemcpyDeviceToDevice, c->stream));
+        ntt_inverse(c, t.p, rows_regular(x.B * 2 * x.lp, x.lp, x.lp, 0));
+        CUDA_TRY(cudaMemcpyAsync(coeff, t.p, w * 8, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    });
+}
+
+void he_ct_free(he_ct *ct) { delete ct; }
+
+he_status he_rotate(he_ctx *h, const he_ct *in, int32_t step, he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!in || !out) throw HeError(HE_EINVAL, "bad arguments");
+        *out = wrap(c, ct_rotate(c, in->x, step));
+    });
+}
+
+he_status he_rotate_hoisted(he_ctx *h, const he_ct *in, const int32_t *steps, size_t n, he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!in || !out || !steps || !n) throw HeError(HE_EINVAL, "bad arguments");
+        std::vector<Cts> r = ct_rotate_hoisted(c, in->x, std::vector<int>(steps, steps + n));
+        for (size_t i = 0; i < n; ++i) out[i] = wrap(c, r[i]);
+    });
+}
+
+he_status he_rescale(he_ctx *h, const he_ct *in, he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!in || !out) throw HeError(HE_EINVAL, "bad arguments");
+        *out = wrap(c, ct_rescale(c, in->x));
+    });
+}
+
+he_status he_mul_plain(he_ctx *h, const he_ct *in, const double *v, he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!in || !out || !v) throw HeError(HE_EINVAL, "bad arguments");
+        const u32 M = c->N / 2;
+        Layout one = in->x.lay;
+        one.stride = M;
+        one.n_samples = 1;
+        std::vector<u32> off{0}, pos;
+        std::vector<double> val;
+        for (u32 j = 0; j < M; ++j)
+            if (v[j] != 0.0) {
+                pos.push_back(j);
+                val.push_back(v[j]);
+            }
+        off.push_back((u32)pos.size());
+        std::vector<DBuf> tmp;
+        const u64 *pt = get_pts(c, nullptr, "mulplain", tmp, one, off, pos, val, c->scale, in->x.lp);
+        *out = wrap(c, ct_mul_pt(c, in->x, pt, c->scale));
+    });
+}
+
+he_status he_add(he_ctx *h, const he_ct *a, const he_ct *b, he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!a || !b || !out) throw HeError(HE_EINVAL, "bad arguments");
+        *out = wrap(c, ct_add(c, a->x, b->x));
+    });
+}
+
+he_status he_square(he_ctx *h, he_ct *const *in, uint32_t n, he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!out) throw HeError(HE_EINVAL, "bad arguments");
+        Feat f = gather_channels(c, in, n);
+        scatter_channels(c, layer_square(c, f), out);
+    });
+}
+
+static he_status conv_common(he_ctx *h, he_ct *const *in, uint32_t ci, const double *w, const double *bias,
+                             uint32_t co, uint32_t K, uint32_t S, int incremental, he_ct **out, bool two_d) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!w || !bias || !out || !co || !K || !S) throw HeError(HE_EINVAL, "bad arguments");
+        Feat f = gather_channels(c, in, ci);
+        LayerSpec s;
+        s.op = two_d ? HE_CONV2D : HE_CONV1D;
+        s.ci = ci;
+        s.co = co;
+        s.k = K;
+        s.s = S;
+        size_t nw = (size_t)co * ci * K * (two_d ? K : 1);
+        s.w.assign(w, w + nw);
+        s.b.assign(bias, bias + co);
+        u32 kh = two_d ? K : 1;
+        std::vector<int> need;
+        for (u32 j = 0; j < kh; ++j)
+            for (u32 k = 0; k < K; ++k)
+                if (!incremental) require_key(c, (int)(f.x.lay.I * (k + f.x.lay.W_img * j)));
+        Feat r = layer_conv(c, f, s, kh, K, incremental != 0, nullptr, "conv");
+        scatter_channels(c, r, out);
+    });
+}
+
+he_status he_conv2d(he_ctx *h, he_ct *const *in, uint32_t ci, const double *w, const double *bias, uint32_t co,
+                    uint32_t K, uint32_t S, int incremental, he_ct **out) {
+    return conv_common(h, in, ci, w, bias, co, K, S, incremental, out, true);
+}
+
+he_status he_conv1d(he_ctx *h, he_ct *const *in, uint32_t ci, const double *w, const double *bias, uint32_t co,
+                    uint32_t K, uint32_t S, int incremental, he_ct **out) {
+    return conv_common(h, in, ci, w, bias, co, K, S, incremental, out, false);
+}
+
+he_status he_avgpool(he_ctx *h, he_ct *const *in, uint32_t ch, uint32_t cc, he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!out || !cc) throw HeError(HE_EINVAL, "bad arguments");
+        Feat f = gather_channels(c, in, ch);
+        scatter_channels(c, layer_avgpool(c, f, cc), out);
+    });
+}
+
+he_status he_flatten(he_ctx *h, he_ct *const *in, uint32_t ch, he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!out) throw HeError(HE_EINVAL, "bad arguments");
+        Feat f = gather_channels(c, in, ch);
+        *out = wrap(c, layer_flatten(c, f, nullptr, "flatten").x);
+    });
+}
+
+he_status he_fc(he_ctx *h, const he_ct *in, const double *Wm, const double *b, uint32_t din, uint32_t dout,
+                he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!in || !Wm || !b || !out || !din || !dout) throw HeError(HE_EINVAL, "bad arguments");
+        LayerSpec s;
+        s.op = HE_FC;
+        s.ci = din;
+        s.co = dout;
+        s.w.assign(Wm, Wm + (size_t)din * dout);
+        s.b.assign(b, b + dout);
+        Feat f;
+        f.x = in->x;
+        f.CH = 1;
+        f.B = in->x.B;
+        *out = wrap(c, layer_fc(c, f, s, nullptr, "fc").x);
+    });
+}
+
+he_status he_model_plan(const he_layer *layers, size_t n, uint32_t Wi, uint32_t Hi, uint32_t *stride,
+                        uint32_t *levels, int32_t *steps, size_t *n_steps) {
+    return guard([&] {
+        if (!layers || !n || !Wi || !Hi) throw HeError(HE_EINVAL, "bad arguments");
+        Plan p = plan_layers(copy_layers(layers, n, Hi), Wi, Hi);
+        if (stride) *stride = p.stride;
+        if (levels) *levels = p.levels;
+        if (n_steps) {
+            if (steps) {
+                if (*n_steps < p.steps.size()) throw HeError(HE_EINVAL, "steps buffer too small");
+                for (size_t i = 0; i < p.steps.size(); ++i) steps[i] = p.steps[i];
+            }
+            *n_steps = p.steps.size();
+        }
+    });
+}
+
+he_status he_model_compile(he_ctx *h, const he_layer *layers, size_t n, uint32_t Wi, uint32_t Hi, uint32_t spc,
+                           he_model **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!layers || !n || !out || !spc) throw HeError(HE_EINVAL, "bad arguments");
+        std::unique_ptr<he_model> m(new he_model());
+        m->c = c;
+        m->layers = copy_layers(layers, n, Hi);
+        m->W_img = Wi;
+        m->H_img = Hi;
+        m->spc = spc;
+        m->plan = plan_layers(m->layers, Wi, Hi);
+        if ((u64)m->plan.stride * spc > c->N / 2) throw HeError(HE_ESLOTS, "samples do not fit in the slots");
+        if (m->plan.levels + 1 > c->L1) throw HeError(HE_ELEVEL, "the modulus chain is too short for this model");
+        for (int s : m->plan.steps) require_key(c, s);
+        *out = m.release();
+    });
+}
+
+static void check_input(const he_model *m, const Cts &x) {
+    const Layout &L = x.lay;
+    if (L.W_img != m->W_img || L.H_img != m->H_img || L.n_samples != m->spc || L.stride < m->plan.stride ||
+        L.prev != PREV_INPUT)
+        throw HeError(HE_EINVAL, "ciphertext layout does not match the model");
+    if (x.lp < m->plan.levels + 1) throw HeError(HE_ELEVEL, "not enough levels for this model");
+}
+
+he_status he_infer(he_model *m, const he_ct *in, int use_graph, he_ct **out) {
+    return guard([&] {
+        if (!m || !in || !out) throw HeError(HE_EINVAL, "bad arguments");
+        Ctx *c = m->c;
+        CUDA_TRY(cudaSetDevice(c->device));
+        check_input(m, in->x);
+        Feat f;
+        f.x = in->x;
+        f.CH = 1;
+        f.B = in->x.B;
+        if (!use_graph) {
+            Feat r = run_layers(c, f, m->layers, &m->pc);
+            *out = wrap(c, r.x);
+            return;
+        }
+        const Cts &x = in->x;
+        std::string key = fmt("%u:%u:%.17g", x.B, x.lp, x.scale);
+        auto it = m->graphs.find(key);
+        const size_t inw = (size_t)x.B * cts_ct_words(c, x.lp);
+        if (it == m->graphs.end()) {
+            // eager run (fills the plaintext cache and sizes the private pool), then capture
+            run_layers(c, f, m->layers, &m->pc);
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            ModelGraph g;
+            c->active = &m->gpool;
+            try {
+                g.in = cts_alloc(c, x.B, x.lp, x.scale, x.lay);
+                Feat fi = f;
+                fi.x = g.in;
+                {   // warm the private pool with one run of the same shapes
+                    Feat w = run_layers(c, fi, m->layers, &m->pc);
+                }
+                CUDA_TRY(cudaStreamSynchronize(c->stream));
+                CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+                Feat r;
+                try {
+                    r = run_layers(c, fi, m->layers, &m->pc);
+                } catch (...) {
+                    cudaGraph_t tmpg;
+                    cudaStreamEndCapture(c->stream, &tmpg);
+                    if (tmpg) cudaGraphDestroy(tmpg);
+                    throw;
+                }
+                CUDA_TRY(cudaStreamEndCapture(c->stream, &g.graph));
+                CUDA_TRY(cudaGraphInstantiate(&g.exec, g.graph, 0));
+                g.out = r.x;   // keeps the output buffer alive in the private pool
+            } catch (...) {
+                c->active = nullptr;
+                throw;
+            }
+            c->active = nullptr;
+            it = m->graphs.emplace(key, std::move(g)).first;
+        }
+        ModelGraph &g = it->second;
+        CUDA_TRY(cudaMemcpyAsync(g.in.data(), x.data(), inw * 8, cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(cudaGraphLaunch(g.exec, c->stream));
+        c->launches++;
+        Cts o = cts_alloc(c, g.out.B, g.out.lp, g.out.scale, g.out.lay);
+        CUDA_TRY(cudaMemcpyAsync(o.data(), g.out.data(), (size_t)g.out.B * cts_ct_words(c, g.out.lp) * 8,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+        *out = wrap(c, o);
+    });
+}
+
+void he_model_free(he_model *m) {
+    if (!m) return;
+    cudaSetDevice(m->c->device);
+    cudaStreamSynchronize(m->c->stream);
+    delete m;
+}
+
+he_status he_ntt(he_ctx *h, uint64_t *data, uint32_t n_limbs, const uint32_t *prime_idx, int inverse) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        if (!data || !prime_idx || !n_limbs) throw HeError(HE_EINVAL, "bad arguments");
+        std::vector<u32> rows;
+        for (u32 i = 0; i < n_limbs; ++i) {
+            if (prime_idx[i] >= c->nprimes()) throw HeError(HE_EINVAL, "prime index out of range");
+            rows.push_back((i << 8) | prime_idx[i]);
+        }
+        std::string key = "user";
+        for (u32 i = 0; i < n_limbs; ++i) key += fmt(":%u", prime_idx[i]);
+        RowSet rs = rows_list(c, key, rows);
+        if (inverse)
+            ntt_inverse(c, data, rs);
+        else
+            ntt_forward(c, data, rs);
+    });
+}
+
+he_status he_sync(he_ctx *h) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    });
+}
+
+uint64_t he_kernel_launches(const he_ctx *h) { return h && h->c ? h->c->launches : 0; }
+
+}  // extern "C"

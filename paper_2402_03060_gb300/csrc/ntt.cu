@@ -1,0 +1,70 @@
+// ntt.cu -- batched negacyclic NTT / inverse NTT over sets of limbs.
+// One CTA per limb (row of N words); the limb is staged in shared memory
+// (N*8 bytes: 128 KiB at N = 16384), transformed with block_ntt_* and written back.
+#include "ntt_block.cuh"
+
+__device__ __forceinline__ void row_of(const RowSet &rs, u32 r, u32 &off, u32 &prime) {
+    if (rs.list) {
+        u32 v = rs.list[r];
+        off = v >> 8;
+        prime = v & 0xff;
+    } else {
+        off = r;
+        u32 w = r % rs.period;
+        prime = w < rs.lp ? w : rs.pbase + (w - rs.lp);
+    }
+}
+
+__global__ void __launch_bounds__(1024) ntt_rows_kernel(u64 *base, RowSet rs, const u64 *tw_all,
+                                                        const PrimeDev *pd, int logn, int inverse) {
+    extern __shared__ u64 sm[];
+    const u32 N = 1u << logn;
+    u32 off, prime;
+    row_of(rs, blockIdx.x, off, prime);
+    u64 *g = base + (size_t)off * N;
+    const u64 *tw = tw_all + (size_t)prime * 4 * N;
+    const PrimeDev P = pd[prime];
+    block_load(sm, g, N);
+    if (inverse)
+        block_ntt_inv(sm, logn, tw, P.q, P.ninv, P.ninvs);
+    else
+        block_ntt_fwd(sm, logn, tw, P.q);
+    block_store(g, sm, N);
+}
+
+static void ntt_launch(Ctx *c, u64 *base, const RowSet &rs, int inverse) {
+    if (rs.n == 0) return;
+    size_t smem = (size_t)c->N * sizeof(u64);
+    ntt_rows_kernel<<<rs.n, ntt_threads(c->N), smem, c->stream>>>(base, rs, c->tw, c->pdev, c->logn, inverse);
+    note_launch(c, inverse ? "intt" : "ntt");
+}
+
+void ntt_forward(Ctx *c, u64 *base, const RowSet &rs) { ntt_launch(c, base, rs, 0); }
+void ntt_inverse(Ctx *c, u64 *base, const RowSet &rs) { ntt_launch(c, base, rs, 1); }
+
+RowSet rows_regular(u32 n, u32 period, u32 lp, u32 pbase) {
+    RowSet r;
+    r.list = nullptr;
+    r.n = n;
+    r.period = period;
+    r.lp = lp;
+    r.pbase = pbase;
+    return r;
+}
+
+RowSet rows_list(Ctx *c, const std::string &key, const std::vector<u32> &packed) {
+    RowSet r;
+    r.n = (u32)packed.size();
+    r.period = 1;
+    r.lp = 1;
+    r.pbase = 0;
+    std::vector<u64> h((packed.size() + 1) / 2 + 1, 0);
+    memcpy(h.data(), packed.data(), packed.size() * sizeof(u32));
+    r.list = reinterpret_cast<const u32 *>(c->const_table("rows:" + key, h));
+    return r;
+}
+
+void ntt_init_attrs(Ctx *c) {
+    (void)c;
+    CUDA_TRY(cudaFuncSetAttribute(ntt_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+}

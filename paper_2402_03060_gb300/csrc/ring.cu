@@ -1,0 +1,270 @@
+// ring.cu -- elementwise ring kernels: modular add/sub/mul with batch
+// broadcasting, Galois permutation, ciphertext tensor, counter-based samplers,
+// and the plaintext-mask multiply-accumulate of the convolution / FC layers.
+// All arrays are rows of N residues; the prime of row r is given by a regular
+// map (w = r % period; prime = w < lp ? w : pbase + w - lp).
+#include "ring.cuh"
+
+__device__ __forceinline__ u32 map_prime(u32 r, u32 period, u32 lp, u32 pbase) {
+    u32 w = r % period;
+    return w < lp ? w : pbase + (w - lp);
+}
+
+// ---------------------------------------------------------------- binops
+__global__ void binop_kernel(int op, u64 *out, const u64 *a, const u64 *b, u32 rows, u32 logn, u32 period, u32 lp,
+                             u32 pbase, const PrimeDev *pd) {
+    const u32 N = 1u << logn;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)rows * N) return;
+    u32 r = (u32)(idx >> logn);
+    const PrimeDev &P = pd[map_prime(r, period, lp, pbase)];
+    u64 x = a[idx], y = b ? b[idx] : 0, z;
+    switch (op) {
+        case OP_ADD: z = add_mod(x, y, P.q); break;
+        case OP_SUB: z = sub_mod(x, y, P.q); break;
+        case OP_MUL: z = mul_mod(x, y, P); break;
+        case OP_NEG: z = neg_mod(x, P.q); break;
+        default: z = x;
+    }
+    out[idx] = z;
+}
+
+void ew_binop(Ctx *c, int op, u64 *out, const u64 *a, const u64 *b, u32 rows, u32 period, u32 lp, u32 pbase) {
+    size_t total = (size_t)rows * c->N;
+    if (!total) return;
+    binop_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(op, out, a, b, rows, c->logn, period, lp,
+                                                                        pbase, c->pdev);
+    note_launch(c, "binop");
+}
+
+// out[b][k][l][n] = a[b][k][l][n] (op) pt[l][n] for the polys k in kmask; other polys copied.
+__global__ void bcast_kernel(int op, u64 *out, const u64 *a, const u64 *pt, u32 B, u32 lp, u32 logn, u32 kmask,
+                             const PrimeDev *pd) {
+    const u32 N = 1u << logn;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)B * 2 * lp * N;
+    if (idx >= total) return;
+    u32 n = (u32)(idx & (N - 1));
+    size_t r = idx >> logn;
+    u32 l = (u32)(r % lp);
+    u32 k = (u32)((r / lp) & 1);
+    u64 x = a[idx];
+    if ((kmask >> k) & 1) {
+        const PrimeDev &P = pd[l];
+        u64 y = pt[(size_t)l * N + n];
+        x = op == OP_MUL ? mul_mod(x, y, P) : add_mod(x, y, P.q);
+    }
+    out[idx] = x;
+}
+
+void ew_bcast(Ctx *c, int op, u64 *out, const u64 *a, const u64 *pt, u32 B, u32 lp, u32 kmask) {
+    size_t total = (size_t)B * 2 * lp * c->N;
+    if (!total) return;
+    bcast_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(op, out, a, pt, B, lp, c->logn, kmask,
+                                                                        c->pdev);
+    note_launch(c, "bcast");
+}
+
+// out[o][b][0][l][n] += pt[o][l][n]   (bias of channel o, added to c0 of every ciphertext)
+__global__ void add_plain_multi_kernel(u64 *out, const u64 *pt, u32 O, u32 B, u32 lp, u32 logn, size_t o_stride,
+                                       const PrimeDev *pd) {
+    const u32 N = 1u << logn;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)O * B * lp * N;
+    if (idx >= total) return;
+    u32 n = (u32)(idx & (N - 1));
+    size_t r = idx >> logn;
+    u32 l = (u32)(r % lp);
+    size_t ob = r / lp;
+    u32 b = (u32)(ob % B), o = (u32)(ob / B);
+    u64 *p = out + o * o_stride + ((size_t)b * 2 * lp + l) * N + n;
+    *p = add_mod(*p, pt[((size_t)o * lp + l) * N + n], pd[l].q);
+}
+
+void add_plain_multi(Ctx *c, u64 *out, const u64 *pt, u32 O, u32 B, u32 lp, size_t o_stride) {
+    size_t total = (size_t)O * B * lp * c->N;
+    if (!total) return;
+    add_plain_multi_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(out, pt, O, B, lp, c->logn,
+                                                                                  o_stride, c->pdev);
+    note_launch(c, "add_plain");
+}
+
+// --------------------------------------------------------------- Galois
+__global__ void perm_kernel(u64 *out, const u64 *in, u32 rows, u32 logn, u32 g) {
+    const u32 N = 1u << logn;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)rows * N) return;
+    u32 n = (u32)(idx & (N - 1));
+    size_t r = idx >> logn;
+    out[idx] = in[r * N + galois_src(n, g, logn)];
+}
+
+void galois_permute(Ctx *c, u64 *out, const u64 *in, u32 rows, u32 g) {
+    size_t total = (size_t)rows * c->N;
+    if (!total) return;
+    perm_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(out, in, rows, c->logn, g);
+    note_launch(c, "galois");
+}
+
+// --------------------------------------------------------------- tensor
+// d[b][0..2][l] = (a0*a0, 2*a0*a1, a1*a1)
+__global__ void tensor_sq_kernel(u64 *d, const u64 *a, u32 B, u32 lp, u32 logn, const PrimeDev *pd) {
+    const u32 N = 1u << logn;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)B * lp * N;
+    if (idx >= total) return;
+    u32 n = (u32)(idx & (N - 1));
+    size_t r = idx >> logn;
+    u32 l = (u32)(r % lp);
+    u32 b = (u32)(r / lp);
+    const PrimeDev &P = pd[l];
+    const u64 *ab = a + (size_t)b * 2 * lp * N;
+    u64 a0 = ab[(size_t)l * N + n], a1 = ab[(size_t)(lp + l) * N + n];
+    u64 m01 = mul_mod(a0, a1, P);
+    u64 *db = d + (size_t)b * 3 * lp * N;
+    db[(size_t)l * N + n] = mul_mod(a0, a0, P);
+    db[(size_t)(lp + l) * N + n] = add_mod(m01, m01, P.q);
+    db[(size_t)(2 * lp + l) * N + n] = mul_mod(a1, a1, P);
+}
+
+void tensor_square(Ctx *c, u64 *d, const u64 *a, u32 B, u32 lp) {
+    size_t total = (size_t)B * lp * c->N;
+    tensor_sq_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(d, a, B, lp, c->logn, c->pdev);
+    note_launch(c, "tensor");
+}
+
+// --------------------------------------------------------------- samplers
+// Small polynomial (ternary or centred binomial eta=21): vector v draws word n
+// of stream (seeds.seed[v], seeds.stream[v]); the value is reduced into every
+// row's prime: out[v][row][n].
+__global__ void sample_small_kernel(u64 *out, SeedList sl, u32 nvec, u32 rows, u32 period, u32 lp, u32 pbase,
+                                   int kind, u32 logn, const PrimeDev *pd) {
+    const u32 N = 1u << logn;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)nvec * N) return;
+    u32 n = (u32)(idx & (N - 1));
+    u32 v = (u32)(idx >> logn);
+    u64 w = sm64_word(sm64_state(sl.seed[v], sl.stream[v]), n);
+    i64 x;
+    if (kind == 0) {
+        x = (i64)(w % 3) - 1;
+    } else {
+        x = (i64)__popcll(w & 0x1FFFFFULL) - (i64)__popcll((w >> 21) & 0x1FFFFFULL);
+    }
+    for (u32 r = 0; r < rows; ++r) {
+        const PrimeDev &P = pd[map_prime(r, period, lp, pbase)];
+        u64 y = x >= 0 ? (u64)x : P.q - (u64)(-x);
+        out[((size_t)v * rows + r) * N + n] = y;
+    }
+}
+
+void sample_small(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u32 period, u32 lp, u32 pbase,
+                  int kind) {
+    if (nvec > SEEDLIST_MAX) throw HeError(HE_EINVAL, "sample_small: too many vectors");
+    size_t total = (size_t)nvec * c->N;
+    sample_small_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(out, sl, nvec, rows, period, lp,
+                                                                               pbase, kind, c->logn, c->pdev);
+    note_launch(c, "sample_small");
+}
+
+// Uniform residues: row r of vector v uses stream (seed[v], stream[v] + prime(r));
+// value = floor(w * q / 2^64).
+__global__ void sample_uniform_kernel(u64 *out, SeedList sl, u32 nvec, u32 rows, u32 period, u32 lp, u32 pbase,
+                                     u32 logn, const PrimeDev *pd) {
+    const u32 N = 1u << logn;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)nvec * rows * N) return;
+    u32 n = (u32)(idx & (N - 1));
+    u32 R = (u32)(idx >> logn);
+    u32 r = R % rows, v = R / rows;
+    u32 pr = map_prime(r, period, lp, pbase);
+    const PrimeDev &P = pd[pr];
+    out[idx] = mulhi64(sm64_word(sm64_state(sl.seed[v], sl.stream[v] + pr), n), P.q);
+}
+
+void sample_uniform(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u32 period, u32 lp, u32 pbase) {
+    if (nvec > SEEDLIST_MAX) throw HeError(HE_EINVAL, "sample_uniform: too many vectors");
+    size_t total = (size_t)nvec * rows * c->N;
+    sample_uniform_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(out, sl, nvec, rows, period, lp,
+                                                                                 pbase, c->logn, c->pdev);
+    note_launch(c, "sample_uniform");
+}
+
+// --------------------------------------------------------------- MAC
+// out[o][b][k][l][n] = sum_t pt[o][t][l][n] * x[t][b][k][l][n]   (mod q_l)
+// 128-bit lazy accumulation (each product < 2^120, reduced every 128 terms).
+// One thread per (n, l, b, k), all O outputs in registers; CTAs that share
+// (l, n-tile) are adjacent in the grid so the plaintext tile is read from HBM
+// once and then hit in L2 by the other (b, k) CTAs.
+template <int OMAX>
+__global__ void __launch_bounds__(256) mac_kernel(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt,
+                                                  u32 O, u32 T, u32 B, u32 lp, u32 logn, size_t x_tstride,
+                                                  size_t out_ostride, const PrimeDev *pd) {
+    const u32 N = 1u << logn;
+    const u32 bk = blockIdx.x;                  // b*2 + k
+    const u32 n = blockIdx.y * blockDim.x + threadIdx.x;
+    const u32 l = blockIdx.z;
+    if (n >= N) return;
+    const u32 b = bk >> 1, k = bk & 1;
+    const PrimeDev P = pd[l];
+    Acc128 acc[OMAX];
+#pragma unroll
+    for (int o = 0; o < OMAX; ++o) acc[o].lo = acc[o].hi = 0;
+    const size_t xoff = (((size_t)b * 2 + k) * lp + l) * N + n;
+    const size_t poff = (size_t)l * N + n;
+    const size_t pstride_t = (size_t)lp * N, pstride_o = (size_t)T * lp * N;
+    for (u32 t = 0; t < T; ++t) {
+        const u64 xv = __ldg(x + t * x_tstride + xoff);
+#pragma unroll
+        for (int o = 0; o < OMAX; ++o)
+            if (o < (int)O) mac128(acc[o], __ldg(pt + o * pstride_o + t * pstride_t + poff), xv);
+        if ((t & 127) == 127) {
+#pragma unroll
+            for (int o = 0; o < OMAX; ++o) {
+                acc[o].lo = reduce128(acc[o].lo, acc[o].hi, P);
+                acc[o].hi = 0;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < OMAX; ++o)
+        if (o < (int)O) out[o * out_ostride + xoff] = reduce128(acc[o].lo, acc[o].hi, P);
+}
+
+void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O, u32 T, u32 B,
+         u32 lp) {
+    // pt [O][T][lp][N]; x [T] blocks of [B][2][lp][N] at x_tstride; out [O] blocks at out_ostride
+    for (u32 o0 = 0; o0 < O; o0 += 16) {
+        u32 oc = O - o0 < 16 ? O - o0 : 16;
+        dim3 grid(B * 2, (c->N + 255) / 256, lp);
+        const u64 *ptc = pt + (size_t)o0 * T * lp * c->N;
+        u64 *outc = out + (size_t)o0 * out_ostride;
+        if (oc <= 1)
+            mac_kernel<1><<<grid, 256, 0, c->stream>>>(outc, x, ptc, oc, T, B, lp, c->logn, x_tstride, out_ostride, c->pdev);
+        else if (oc <= 4)
+            mac_kernel<4><<<grid, 256, 0, c->stream>>>(outc, x, ptc, oc, T, B, lp, c->logn, x_tstride, out_ostride, c->pdev);
+        else if (oc <= 8)
+            mac_kernel<8><<<grid, 256, 0, c->stream>>>(outc, x, ptc, oc, T, B, lp, c->logn, x_tstride, out_ostride, c->pdev);
+        else
+            mac_kernel<16><<<grid, 256, 0, c->stream>>>(outc, x, ptc, oc, T, B, lp, c->logn, x_tstride, out_ostride, c->pdev);
+        note_launch(c, "mac");
+    }
+}
+
+// --------------------------------------------------------------- copies
+__global__ void gather_rows_kernel(u64 *out, const u64 *in, u32 nrows, size_t in_row_stride_words, u32 logn) {
+    const u32 N = 1u << logn;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)nrows * N) return;
+    size_t r = idx >> logn;
+    out[idx] = in[r * in_row_stride_words + (idx & (N - 1))];
+}
+
+// out[r] = in[r * stride_rows] (rows of N words)
+void gather_rows(Ctx *c, u64 *out, const u64 *in, u32 nrows, size_t stride_rows) {
+    size_t total = (size_t)nrows * c->N;
+    if (!total) return;
+    gather_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(out, in, nrows, stride_rows * c->N,
+                                                                              c->logn);
+    note_launch(c, "gather_rows");
+}

@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point the
+header declares, and its host-side planner (he_model_plan, no GPU needed)
+agrees with the oracle's planner."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import layers as olayers
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "unihenn.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2402_03060_gb300 import build
+    build.build()
+    import paper_2402_03060_gb300 as G
+    return G
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(he_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_paper_calls():
+    names = declared_functions()
+    for n in ["he_keygen", "he_encrypt", "he_conv2d", "he_conv1d", "he_avgpool", "he_fc", "he_square",
+              "he_decrypt", "he_flatten", "he_infer"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import subprocess
+    from paper_2402_03060_gb300 import _lib
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (he_[a-z0-9_]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    # and the binding declares each of them with the same name
+    assert set(declared_functions()) <= set(_lib.SIGNATURES)
+    L = lib.load()
+    for n in declared_functions():
+        assert hasattr(L, n)
+
+
+@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "lenet5", "conv"])
+def test_planner_matches_oracle(lib, name):
+    if name == "lenet1":
+        model, Wi, Hi = W.lenet1(), 28, 28
+    elif name == "cnn1d":
+        model, Wi, Hi = W.cnn1d(), 1024, 1
+    elif name == "lenet5":
+        model, Wi, Hi = W.lenet5_sq(), 32, 32
+    else:
+        model, Wi, Hi = W.single_conv(), 28, 28
+    stride, levels, steps = lib.plan(model, Wi, Hi)
+    p = olayers.plan(model, Wi, Hi, 1 if Hi == 1 else 2)
+    assert stride == p["stride"] and levels == p["levels"] and steps == p["steps"]
+
+
+def test_planner_rejects_bad_models(lib):
+    from paper_2402_03060_gb300 import HeError
+    bad = [{"op": "conv2d", "w": np.zeros((1, 1, 30, 30)), "b": np.zeros(1), "stride": 1}]
+    with pytest.raises(HeError) as e:
+        lib.plan(bad, 28, 28)
+    assert e.value.status == 1
+    bad_fc = W.lenet1()[:-1] + [{"op": "fc", "w": np.zeros((10, 100)), "b": np.zeros(10)}]
+    with pytest.raises(HeError):
+        lib.plan(bad_fc, 28, 28)

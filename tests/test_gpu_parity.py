@@ -1,0 +1,269 @@
+"""GPU parity: every ciphertext the CUDA library produces is compared limb by
+limb, in coefficient form, with the CPU oracle's on the same seeded inputs
+(bit-exact), and decrypted logits with the FP64 CNN (max-abs 1e-3)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ckks, cnn, layers as olayers
+
+pytestmark = pytest.mark.gpu
+
+U64 = np.uint64
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_03060_gb300 import build
+    build.build()
+    import paper_2402_03060_gb300 as lib
+    return lib
+
+
+def make_pair(G, P, steps, seed=W.KEY_SEED):
+    ctx = G.Context(seed=seed, **P)
+    ctx.keygen(steps)
+    he = ckks.Ckks(seed=seed, **P)
+    he.keygen(steps)
+    return ctx, he
+
+
+def slots_of(samples, stride, slots):
+    x = np.zeros(slots)
+    for b, s in enumerate(samples):
+        f = np.asarray(s).reshape(-1)
+        x[b * stride: b * stride + f.size] = f
+    return x
+
+
+def assert_same(ctx, gct, he, oct_, b=0):
+    got = ctx.export(gct)[b]
+    want = he.to_coeff(oct_)
+    assert got.shape == want.shape, (got.shape, want.shape)
+    bad = np.argwhere(got != want)
+    assert bad.size == 0, f"{len(bad)} residues differ, first at {bad[:3].tolist()}"
+
+
+P_SMALL = dict(logn=10, data_bits=[60, 40, 40, 40], special_bits=[60], dnum=4, log2_scale=40)
+P_DIGITS = dict(logn=10, data_bits=[60, 40, 40, 40, 40], special_bits=[60, 60], dnum=3, log2_scale=40)
+
+
+def test_primes_match_oracle(G):
+    for P in (P_SMALL, P_DIGITS, W.PARAMS["lenet1"], W.PARAMS["conv1"]):
+        ctx = G.Context(seed=1, **P)
+        assert ctx.primes() == ckks.gen_primes(list(P["data_bits"]) + list(P["special_bits"]), P["logn"])
+
+
+@pytest.mark.parametrize("logn", [4, 10, 13, 14])
+def test_ntt_matches_oracle(G, logn):
+    import torch
+    P = dict(logn=logn, data_bits=[60, 40], special_bits=[60], dnum=2, log2_scale=30)
+    ctx = G.Context(seed=1, **P)
+    he = ckks.Ckks(seed=1, **P)
+    qs = ctx.primes()
+    rng = np.random.default_rng(logn)
+    idx = [0, 1, 2, 1, 0]   # ragged mix of primes
+    a = np.stack([rng.integers(0, qs[i], 1 << logn, dtype=U64) for i in idx])
+    d = torch.from_numpy(a.view(np.int64).copy()).cuda()
+    ctx.ntt(d.data_ptr(), len(idx), idx)
+    ctx.sync()
+    got = d.cpu().numpy().view(U64)
+    allpsi = he.qpsi + he.ppsi
+    br = np.array([int(format(k, f"0{logn}b")[::-1], 2) for k in range(1 << logn)])
+    for r, i in enumerate(idx):
+        want = he.ntt(a[r][None], [qs[i]], [allpsi[i]])[0]
+        assert np.array_equal(got[r], want[br]), f"row {r}"
+    ctx.ntt(d.data_ptr(), len(idx), idx, inverse=True)
+    ctx.sync()
+    assert np.array_equal(d.cpu().numpy().view(U64), a)
+
+
+@pytest.fixture(scope="module")
+def pair_small(G):
+    return make_pair(G, P_SMALL, [1, 3, 7, -2, 100, 511])
+
+
+@pytest.fixture(scope="module")
+def pair_digits(G):
+    return make_pair(G, P_DIGITS, [1, 5, -9])
+
+
+def enc_both(ctx, he, samples, stride, spc, seed=9000, lp=None):
+    slots = he.n // 2
+    gct = ctx.encrypt(np.asarray(samples), spc, stride, seed)
+    oct_ = he.encrypt(slots_of(samples, stride, slots), seed)
+    return gct, oct_
+
+
+@pytest.mark.parametrize("which", ["small", "digits"])
+def test_encrypt_and_ops_bit_exact(G, pair_small, pair_digits, which):
+    ctx, he = pair_small if which == "small" else pair_digits
+    rng = np.random.default_rng(3)
+    M = he.n // 2
+    samples = rng.uniform(-1, 1, (1, M))
+    gct, oct_ = enc_both(ctx, he, samples, M, 1)
+    assert_same(ctx, gct, he, oct_)
+    assert np.abs(ctx.decrypt(gct, M)[0] - samples[0]).max() < 2.0 ** -25
+    steps = [1, 3, 7, -2, 100, 511] if which == "small" else [1, 5, -9]
+    for s in steps:
+        assert_same(ctx, ctx.rotate(gct, s), he, he.rotate(oct_, s))
+    hs = ctx.rotate_hoisted(gct, [0] + steps)
+    ho = he.rotate_hoisted(oct_, [0] + steps)
+    for i, s in enumerate([0] + steps):
+        assert_same(ctx, hs[i], he, ho[s])
+    assert_same(ctx, ctx.rescale(gct), he, he.rescale(oct_))
+    assert_same(ctx, ctx.square([gct])[0], he, he.square(oct_))
+    v = rng.uniform(-1, 1, M)
+    pm = ctx.mul_plain(gct, v)
+    po = he.ct_mul_plain(oct_, he.encode(v, he.scale, oct_.lp), he.scale)
+    assert_same(ctx, pm, he, po)
+    assert_same(ctx, ctx.add(pm, pm), he, he.ct_add(po, po))
+    assert np.abs(ctx.decrypt(ctx.rescale(pm), M)[0] - samples[0] * v).max() < 1e-6
+    # a lower level: the last digit becomes short / digits drop out
+    low = ctx.rescale(ctx.rescale(gct))
+    lowo = he.rescale(he.rescale(oct_))
+    assert_same(ctx, ctx.rotate(low, steps[0]), he, he.rotate(lowo, steps[0]))
+    assert_same(ctx, ctx.square([low])[0], he, he.square(lowo))
+
+
+def test_single_conv_incremental_full_size(G):
+    """Single 5x5 convolution, N=8192, [60,40,40 | 60], incremental rotations."""
+    P = W.PARAMS["conv1"]
+    model = W.single_conv()
+    steps = [1, 24]
+    ctx, he = make_pair(G, P, steps)
+    img = W.images(1)
+    gct, oct_ = enc_both(ctx, he, img, 784, 1)
+    assert_same(ctx, gct, he, oct_)
+    gout = ctx.conv2d([gct], model[0]["w"], model[0]["b"], 1, incremental=True)[0]
+    lay = olayers.input_layout(28, 28, 784, 1, he.n // 2)
+    oout, _ = olayers.conv(olayers.HeBackend(he), [oct_], model[0]["w"], model[0]["b"], 1, lay, "incremental")
+    assert_same(ctx, gout, he, oout[0])
+    dec = ctx.decrypt(gout, 784)[0]
+    ref = cnn.forward(img[0], model)
+    got = np.array([dec[r * 28 + c] for r in range(24) for c in range(24)])
+    assert np.abs(got - ref).max() < 1e-6
+
+
+def run_oracle_model(he, model, samples, Wi, Hi, stride, spc, seed, dims=2):
+    lay = olayers.input_layout(Wi, Hi, stride, spc, he.n // 2, dims)
+    x = slots_of(samples, stride, he.n // 2)
+    ct = he.encrypt(x, seed)
+    ys, _ = olayers.run_model(olayers.HeBackend(he), ct, model, lay)
+    return ys[0]
+
+
+def test_lenet1_small_ring_bit_exact(G):
+    P = W.small_params("lenet1", 11)
+    model = W.lenet1()
+    stride, levels, steps = G.plan(model, 28, 28)
+    ctx, he = make_pair(G, P, steps)
+    img = W.images(1)
+    gct = ctx.encrypt(img, 1, stride, W.ENC_SEED)
+    m = ctx.compile(model, 28, 28, 1)
+    out_eager = m.infer(gct)
+    out_graph1 = m.infer(gct, use_graph=True)
+    out_graph2 = m.infer(gct, use_graph=True)
+    want = run_oracle_model(he, model, img, 28, 28, stride, 1, W.ENC_SEED)
+    assert_same(ctx, out_eager, he, want)
+    assert_same(ctx, out_graph1, he, want)
+    assert_same(ctx, out_graph2, he, want)
+    logits = ctx.decrypt(out_eager, 10)[0]
+    assert np.abs(logits - cnn.forward(img[0], model)).max() < 1e-3
+
+
+def test_batched_equals_single_and_uneven_tail(G):
+    """3 ciphertexts x 2 samples (5 samples: an uneven last ciphertext) in one
+    batch give the same ciphertexts as each ciphertext alone."""
+    P = W.small_params("lenet1", 12)
+    model = W.lenet1()
+    stride, levels, steps = G.plan(model, 28, 28)
+    ctx = G.Context(seed=W.KEY_SEED, **P)
+    ctx.keygen(steps)
+    imgs = W.images(5)
+    m = ctx.compile(model, 28, 28, 2)
+    batch = ctx.encrypt(imgs, 2, stride, W.ENC_SEED)
+    assert batch.batch == 3
+    out = m.infer(batch, use_graph=True)
+    ob = ctx.export(out)
+    for b in range(3):
+        single = ctx.encrypt(imgs[2 * b: 2 * b + 2], 2, stride, W.ENC_SEED + b)
+        os_ = ctx.export(m.infer(single))
+        assert np.array_equal(ob[b], os_[0])
+    logits = ctx.decrypt(out, 10)
+    for k in range(5):
+        assert np.abs(logits[k] - cnn.forward(imgs[k], model)).max() < 1e-3
+
+
+def test_layer_calls_match_model(G):
+    """The layer-by-layer C calls give the compiled model's ciphertext."""
+    P = W.small_params("lenet1", 11)
+    model = W.lenet1()
+    stride, levels, steps = G.plan(model, 28, 28)
+    ctx = G.Context(seed=W.KEY_SEED, **P)
+    ctx.keygen(steps)
+    img = W.images(1)
+    ct = ctx.encrypt(img, 1, stride, W.ENC_SEED)
+    ref = ctx.export(ctx.compile(model, 28, 28, 1).infer(ct))
+    x = ctx.conv2d([ct], model[0]["w"], model[0]["b"], 1)
+    x = ctx.square(x)
+    x = ctx.avgpool(x, 2)
+    x = ctx.conv2d(x, model[3]["w"], model[3]["b"], 1)
+    x = ctx.square(x)
+    x = ctx.avgpool(x, 2)
+    f = ctx.flatten(x)
+    y = ctx.fc(f, model[7]["w"], model[7]["b"])
+    assert np.array_equal(ctx.export(y), ref)
+
+
+def test_cnn1d_logits(G):
+    P = dict(W.PARAMS["cnn1d"])
+    P["logn"] = 13
+    model = W.cnn1d()
+    stride, levels, steps = G.plan(model, 1024, 1)
+    ctx = G.Context(seed=W.KEY_SEED, **P)
+    ctx.keygen(steps)
+    sig = W.signals(1)[:, 0]
+    m = ctx.compile(model, 1024, 1, 1)
+    out = m.infer(ctx.encrypt(sig, 1, stride, W.ENC_SEED))
+    assert np.abs(ctx.decrypt(out, 5)[0] - cnn.forward(sig[0], model, dims=1)).max() < 1e-3
+
+
+def test_error_codes(G, pair_small):
+    from paper_2402_03060_gb300 import HeError
+    ctx, he = pair_small
+    M = he.n // 2
+    ct = ctx.encrypt(np.zeros((1, M)), 1, M, 1)
+    with pytest.raises(HeError) as e:
+        ctx.rotate(ct, 2)                  # no key for step 2
+    assert e.value.status == 6
+    one = ctx.rescale(ctx.rescale(ctx.rescale(ct)))
+    with pytest.raises(HeError) as e:
+        ctx.rescale(one)                   # one limb left
+    assert e.value.status == 3
+    with pytest.raises(HeError) as e:
+        ctx.encrypt(np.zeros((3, 400)), 3, 400, 1)   # 1200 slots > 512
+    assert e.value.status == 5
+    with pytest.raises(HeError) as e:
+        ctx.add(ct, ctx.rescale(ct))       # level mismatch
+    assert e.value.status == 1
+
+
+@pytest.mark.slow
+def test_lenet1_full_size_bit_exact(G):
+    """LeNet-1 at N=16384 with 10 samples in one ciphertext, against the oracle."""
+    P = W.PARAMS["lenet1"]
+    model = W.lenet1()
+    stride, levels, steps = G.plan(model, 28, 28)
+    ctx, he = make_pair(G, P, steps)
+    imgs = W.images(10)
+    m = ctx.compile(model, 28, 28, 10)
+    out = m.infer(ctx.encrypt(imgs, 10, stride, W.ENC_SEED), use_graph=True)
+    want = run_oracle_model(he, model, imgs, 28, 28, stride, 10, W.ENC_SEED)
+    assert_same(ctx, out, he, want)
+    logits = ctx.decrypt(out, 10)
+    for k in range(10):
+        assert np.abs(logits[k] - cnn.forward(imgs[k], model)).max() < 1e-3
