@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark: batched encrypted LeNet-1-shaped inference on one GB300.
+
+Workload (the batched LeNet-1 configuration): 633 synthetic 28x28 U[0,1]
+images packed 10 per ciphertext (stride 784 slots) into 64 ciphertexts, the
+last carrying 3; CKKS N = 16384, chain [60, 40 x 7 | 60], Delta = 2^40,
+dnum = 8; LeNet-1 shape conv 1->4 K5, x^2, avgpool 2, conv 4->12 K5, x^2,
+avgpool 2, flatten, FC 192->10 with N(0, 0.1^2) weights.
+
+One step = the whole path for the batch: flatten + encode + encrypt of every
+sample, the encrypted network (one CUDA graph over all 64 ciphertexts), and
+decrypt + decode of the logits.
+  value : inputs resident on the device, logits left on the device.
+  e2e   : the same through the C ABI with host buffers (pinned input copied in,
+          logits copied out inside the timed region).
+  plain : the one-op-per-launch path (each ciphertext through the layers on
+          its own, eager launches, no graph), per-sample rate on a sample.
+Timing: CUDA events on the library's stream after warm-up; every step's
+working set (keys ~1.7 GB, cached plaintext masks ~1.3 GB, ciphertexts) is far
+larger than the 126 MB L2.
+
+--impl reference runs the CPU oracle (oracle/, plain C with __int128 '%') on a
+bounded sample of the same workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+N_SAMPLES = 633
+SPC = 10
+METRIC = "encrypted LeNet-1 inferences/s (batched)"
+UNIT = "samples/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-op-per-launch comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--samples", type=int, default=N_SAMPLES)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def lenet_setup(G, torch, device, stream, n_samples):
+    P = W.PARAMS["lenet1"]
+    model = W.lenet1()
+    stride, levels, steps = G.plan(model, 28, 28)
+    ctx = G.Context(seed=W.KEY_SEED, device=device, stream=stream.cuda_stream, **P)
+    ctx.keygen(steps)
+    m = ctx.compile(model, 28, 28, SPC)
+    imgs = W.images(n_samples)
+    return ctx, m, stride, model, imgs
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_03060_gb300 as G
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    stream = torch.cuda.Stream()
+    ctx, model, stride, layers, imgs = lenet_setup(G, torch, local, stream, args.samples)
+    n_ct = -(-args.samples // SPC)
+    x_dev = torch.from_numpy(imgs).to(f"cuda:{local}")
+    x_host = torch.from_numpy(imgs).pin_memory()
+    logits_dev = torch.zeros((n_ct * SPC, 10), dtype=torch.float64, device=f"cuda:{local}")
+    seed = W.ENC_SEED + 100000 * rank
+
+    def step_device():
+        ct = ctx.encrypt(x_dev, SPC, stride, seed)
+        out = model.infer(ct, use_graph=True)
+        ctx.decrypt(out, 10, out=logits_dev)
+        return out
+
+    def step_e2e():
+        ct = ctx.encrypt(x_host.numpy(), SPC, stride, seed)
+        out = model.infer(ct, use_graph=True)
+        return ctx.decrypt(out, 10)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        barrier()
+        return e0.elapsed_time(e1), wall * 1e3
+
+    for _ in range(max(args.warmup, 3)):
+        step_device()
+    # correctness check of the measured configuration: logits against the FP64 CNN on a few samples
+    from oracle import cnn
+    torch.cuda.synchronize()
+    chk = logits_dev.cpu().numpy()
+    worst = 0.0
+    for k in list(range(0, args.samples, max(1, args.samples // 7)))[:8] + [args.samples - 1]:
+        worst = max(worst, float(np.abs(chk[k] - cnn.forward(imgs[k], layers)).max()))
+
+    clocks = Clocks(local)
+    launches0 = ctx.launches()
+    clocks.start()
+    ms_dev, _ = timed(step_device, args.steps)
+    clk = clocks.stop()
+    launches = (ctx.launches() - launches0) // max(1, args.steps)
+
+    for _ in range(2):
+        step_e2e()
+    ms_e2e_ev, ms_e2e_wall = timed(step_e2e, args.steps)
+
+    # per-kernel CUDA-event timing of one eager step (roofline of the dominant kernel)
+    ctx.profile_begin()
+    ct = ctx.encrypt(x_dev, SPC, stride, seed)
+    out = model.infer(ct, use_graph=False)
+    ctx.decrypt(out, 10, out=logits_dev)
+    stats = ctx.profile_end()
+
+    # one-op-per-launch path: each ciphertext alone, eager
+    plain = None
+    if not args.no_plain:
+        k = 4
+        cts = [ctx.encrypt(x_dev[SPC * i: SPC * (i + 1)], SPC, stride, seed + i) for i in range(k)]
+        model.infer(cts[0])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for c in cts:
+            model.infer(c, use_graph=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        plain = {"value": k * SPC / (ms / 1e3), "unit": UNIT, "ms_per_ct": ms / k,
+                 "sample": f"{k} ciphertexts x {SPC} samples, one ciphertext per launch, eager"}
+
+    # max over ranks
+    ms_step = ms_dev / args.steps
+    ms_e2e = ms_e2e_wall / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step, ms_e2e], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, ms_e2e = float(t[0]), float(t[1])
+    total_samples = args.samples * world
+    pk = peaks()
+    roof = None
+    if stats:
+        top = max(stats.items(), key=lambda kv: kv[1][1])
+        name, (nl, tms, byt) = top
+        share = tms / sum(v[1] for v in stats.values())
+        achieved = (byt / nl) / (tms / nl / 1e3) / 1e9 if tms > 0 else 0.0
+        peak = pk["hbm_gbs"] if pk else 6800.0
+        roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "launches_per_step": nl,
+                "avg_launch_us": round(tms / nl * 1e3, 2), "share_of_eager_step": round(share, 3),
+                "peak_source": "measured" if pk else "fallback",
+                "kernels": {k: {"launches": v[0], "ms": round(v[1], 3),
+                                "GBps": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 else None}
+                            for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1])}}
+    res = {
+        "metric": METRIC, "value": round(total_samples / (ms_step / 1e3), 3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS residues), f64 encode",
+        "data": "synthetic U[0,1] 28x28 images, N(0,0.1^2) weights (MNIST / trained weights absent)",
+        "config": {"workload": "batched LeNet-1-shaped, 64 ciphertexts x 10 samples (last 3), 633 samples",
+                   "ckks": "N=16384, [60,40x7|60], Delta=2^40, dnum=8", "samples_per_gpu": args.samples,
+                   "l2": "working set > L2 (keys + masks + ciphertexts, several GB)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(total_samples / (ms_e2e / 1e3), 3), "unit": UNIT,
+                "h2d_bytes_per_step": int(args.samples * 784 * 8), "d2h_bytes_per_step": int(n_ct * SPC * 10 * 8)},
+        "gpu_launches": int(launches),
+        "max_abs_logit_err": worst,
+        "plain": plain,
+        "roofline": roof,
+        "clocks": clk,
+    }
+    return res, ctx
+
+
+def oracle_sample(budget_s: float):
+    """The CPU oracle on one ciphertext (10 samples) of the workload; keys are
+    generated first (not timed, like the GPU's).  Returns (samples/s, seconds, note)."""
+    from oracle import ckks, layers
+    P = W.PARAMS["lenet1"]
+    model = W.lenet1()
+    pl = layers.plan(model, 28, 28)
+    he = ckks.Ckks(seed=W.KEY_SEED, **P)
+    t0 = time.perf_counter()
+    he.keygen(pl["steps"])
+    tk = time.perf_counter() - t0
+    imgs = W.images(SPC)
+    lay = layers.input_layout(28, 28, pl["stride"], SPC, he.n // 2)
+    x = np.zeros(he.n // 2)
+    for b in range(SPC):
+        x[b * pl["stride"]: b * pl["stride"] + 784] = imgs[b].reshape(-1)
+    t0 = time.perf_counter()
+    ct = he.encrypt(x, W.ENC_SEED)
+    ys, _ = layers.run_model(layers.HeBackend(he), ct, model, lay)
+    he.decrypt(ys[0])
+    t = time.perf_counter() - t0
+    return SPC / t, t, f"one ciphertext (10 samples) end to end: encrypt, LeNet-1, decrypt; keygen {tk:.1f} s untimed"
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        k = max(1, args.steps)
+        vals = []
+        for _ in range(max(0, min(args.warmup, 0))):
+            pass
+        v, t, note = oracle_sample(30.0)
+        vals.append(v)
+        res = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": world,
+               "steps": 1, "warmup": 0, "ms_per_step": round(t * 1e3, 1), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS residues), f64 encode",
+               "data": "synthetic", "config": {"workload": "batched LeNet-1-shaped (one ciphertext sample)"},
+               "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": note},
+               "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(res))
+        return
+    res, ctx = run_ours(args, rank, world, local)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, t, note = oracle_sample(30.0)
+        res["cpu_baseline"] = {"value": round(v, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": note,
+                               "seconds": round(t, 1)}
+    if rank == 0:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

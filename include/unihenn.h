@@ -184,8 +184,23 @@ void he_model_free(he_model *m);
 he_status he_ntt(he_ctx *ctx, uint64_t *data, uint32_t n_limbs, const uint32_t *prime_idx, int inverse);
 /* Block until the context's stream is idle. */
 he_status he_sync(he_ctx *ctx);
-/* Number of kernels this context has launched so far. */
+/* Number of kernels this context has launched so far (a graph replay counts
+ * the kernels of the graph). */
 uint64_t he_kernel_launches(const he_ctx *ctx);
+
+/* Per-kernel timing: between he_profile_begin and he_profile_end every kernel
+ * the context launches eagerly is bracketed by two CUDA events on the
+ * context's stream.  he_profile_end synchronises and aggregates by kernel
+ * name: launches, summed event time, and the algorithmic bytes of those
+ * launches (the bytes the operation must read and write at least once). */
+typedef struct {
+    char name[32];
+    uint64_t launches;
+    double total_ms;
+    double bytes;
+} he_kernel_stat;
+he_status he_profile_begin(he_ctx *ctx);
+he_status he_profile_end(he_ctx *ctx, he_kernel_stat *out, size_t cap, size_t *n);
 
 const char *he_last_error(void);
 

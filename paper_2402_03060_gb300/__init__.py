@@ -106,7 +106,8 @@ def plan(layers, W_img: int, H_img: int):
 
 class Model:
     def __init__(self, ctx: "Context", h, keep):
-        self.ctx, self.h, self._keep = ctx, ctypes.c_void_p(h), keep
+        self.ctx, self._keep = ctx, keep
+        self.h = h if isinstance(h, ctypes.c_void_p) else ctypes.c_void_p(h)
 
     def infer(self, ct: Ct, use_graph: bool = False) -> Ct:
         out = ctypes.c_void_p()
@@ -168,6 +169,18 @@ class Context:
 
     def launches(self) -> int:
         return int(load().he_kernel_launches(self.h))
+
+    def profile_begin(self):
+        check(load().he_profile_begin(self.h))
+
+    def profile_end(self):
+        """-> {kernel: (launches, total_ms, algorithmic_bytes)} of the eager launches since profile_begin."""
+        cap = 128
+        buf = (_lib.he_kernel_stat * cap)()
+        n = ctypes.c_size_t(0)
+        check(load().he_profile_end(self.h, buf, cap, ctypes.byref(n)))
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), float(buf[i].bytes))
+                for i in range(min(n.value, cap))}
 
     # ---- client side
     def encrypt(self, x, samples_per_ct: int, stride: int, enc_seed: int) -> Ct:

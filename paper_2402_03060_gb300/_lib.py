@@ -31,6 +31,11 @@ class he_layer(ctypes.Structure):
                 ("b", ctypes.POINTER(ctypes.c_double))]
 
 
+class he_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
 class HeError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
@@ -71,6 +76,8 @@ SIGNATURES = {
     "he_ntt": (_int, [_vp, _vp, _u32, ctypes.POINTER(_u32), _int]),
     "he_sync": (_int, [_vp]),
     "he_kernel_launches": (_u64, [_vp]),
+    "he_profile_begin": (_int, [_vp]),
+    "he_profile_end": (_int, [_vp, ctypes.POINTER(he_kernel_stat), _sz, ctypes.POINTER(_sz)]),
     "he_last_error": (ctypes.c_char_p, []),
 }
 

@@ -206,6 +206,7 @@ static void check_err(Ctx *c) {
 void encode_dense(Ctx *c, u64 *out, const double *z, u32 nv, double scale, u32 lp, bool check) {
     const u32 M = c->N / 2;
     double f = scale / (double)M;
+    prof_begin(c);
     encode_dense_kernel<<<nv, fft_threads(M), (size_t)M * 16, c->stream>>>(out, z, lp, c->logn, f, c->fft_w, c->fft_t,
                                                                            c->slot_pos_br, c->pdev, c->err_flag);
     note_launch(c, "encode_dense");
@@ -229,6 +230,7 @@ void encode_sparse(Ctx *c, u64 *out, const std::string &key, const std::vector<u
     CUDA_TRY(cudaMemcpyAsync(tmp.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream));
     u64 *d = tmp.p;
     double f = scale / (double)M;
+    prof_begin(c);
     encode_sparse_kernel<<<nv, fft_threads(M), (size_t)M * 16, c->stream>>>(
         out, reinterpret_cast<const u32 *>(d + o_off), reinterpret_cast<const u32 *>(d + o_pos),
         reinterpret_cast<const double *>(d + o_val), stride, ns, lp, c->logn, f, c->fft_w, c->fft_t, c->slot_pos_br,
@@ -243,12 +245,14 @@ void check_encode_errors(Ctx *c) { check_err(c); }
 void pack_samples(Ctx *c, double *z, const double *x, u32 nsamp, u32 spc, u32 stride, u32 len, u32 nct) {
     const u32 M = c->N / 2;
     size_t total = (size_t)nct * M;
+    prof_begin(c);
     pack_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(z, x, nsamp, spc, stride, len, M, nct);
     note_launch(c, "pack");
 }
 
 void enc_combine(Ctx *c, u64 *ct, const u64 *u, const u64 *me, const u64 *e1, u32 lp, u32 B) {
     size_t total = (size_t)B * lp * c->N;
+    prof_begin(c);
     enc_combine_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(ct, u, me, e1, c->pk.p, c->L1, lp,
                                                                               c->logn, c->pdev, B);
     note_launch(c, "enc_combine");
@@ -259,10 +263,12 @@ void decrypt_decode(Ctx *c, double *out, const u64 *ct, u32 B, u32 lp, double sc
     const u32 N = c->N, M = N / 2;
     DBuf m(c, (size_t)B * N);
     size_t total = (size_t)B * N;
+    prof_begin(c);
     dec_combine_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(m.p, ct, c->sk.p, lp, c->logn, c->pdev,
                                                                               B);
     note_launch(c, "dec_combine");
     ntt_inverse(c, m.p, rows_regular(B, 1, 1, 0));
+    prof_begin(c);
     decode_kernel<<<B, fft_threads(M), (size_t)M * 16, c->stream>>>(out, m.p, scale, stride, ns, nper, c->logn,
                                                                      c->fft_w, c->fft_t, c->slot_pos, c->primes[0]);
     note_launch(c, "decode");

@@ -19,10 +19,33 @@ std::string fmt(const char *f, ...) {
     return buf;
 }
 
-void note_launch(Ctx *c, const char *what) {
+cudaEvent_t Ctx::new_event() {
+    if (!ev_free.empty()) {
+        cudaEvent_t e = ev_free.back();
+        ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    CUDA_TRY(cudaEventCreate(&e));
+    return e;
+}
+
+void prof_begin(Ctx *c) {
+    if (!c->profiling) return;
+    c->prof_start = c->new_event();
+    CUDA_TRY(cudaEventRecord(c->prof_start, c->stream));
+}
+
+void note_launch(Ctx *c, const char *what, double bytes) {
     c->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw HeError(HE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    if (c->profiling && c->prof_start) {
+        cudaEvent_t b = c->new_event();
+        CUDA_TRY(cudaEventRecord(b, c->stream));
+        c->recs.push_back({what, bytes, c->prof_start, b});
+        c->prof_start = nullptr;
+    }
 }
 
 // ------------------------------------------------------------------ pool
@@ -385,6 +408,7 @@ static void make_ksk(Ctx *c, u64 *key, const u64 *sp, u32 key_id) {
         u32 lo = j * c->alpha, hi = std::min(lo + c->alpha, c->L1);
         if (lo < hi) {
             size_t total = (size_t)(hi - lo) * N;
+            prof_begin(c);
             add_scaled_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(b, sp, 0, 0, lo, hi,
                                                                                           c->logn, pmd, c->pdev);
             note_launch(c, "ksk_gadget");

@@ -142,7 +142,8 @@ struct HeError : std::runtime_error {
     } while (0)
 
 struct Ctx;
-void note_launch(Ctx *c, const char *what);   // error check + launch counter
+void prof_begin(Ctx *c);                                        // start event of the next launch (profiling)
+void note_launch(Ctx *c, const char *what, double bytes = 0);   // error check, launch counter, end event
 
 // Caching device allocator: buffers are returned to per-size free lists and
 // reused in stream order (all work of a context runs on one stream), so the
@@ -215,6 +216,17 @@ struct Ctx {
     // per-level constant tables (host-built, device-resident)
     std::map<std::string, DBuf> cache;
     uint64_t launches = 0;
+    // per-launch CUDA-event profiling (he_profile_begin / he_profile_end)
+    struct ProfRec {
+        const char *name;
+        double bytes;
+        cudaEvent_t a, b;
+    };
+    bool profiling = false;
+    cudaEvent_t prof_start = nullptr;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<ProfRec> recs;
+    cudaEvent_t new_event();
     int *err_flag = nullptr;       // device error word (encoder overflow etc.)
 
     u32 nprimes() const { return L1 + K; }

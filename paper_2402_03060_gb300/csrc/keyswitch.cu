@@ -262,9 +262,10 @@ void ks_modup(Ctx *c, u64 *D, const u64 *xe, size_t xe_bstride, u32 B, u32 lp) {
     ntt_inverse(c, xc.p, rows_regular(B * lp, lp, lp, 0));
     const u64 *tab = modup_table(c, lp);
     dim3 grid((N + 255) / 256, beta, B);
+    prof_begin(c);
     modup_kernel<<<grid, 256, 0, c->stream>>>(D, xc.p, xe, xe_bstride, lp, c->K, c->L1, c->alpha, beta, c->logn, tab,
                                                c->pdev);
-    note_launch(c, "modup");
+    note_launch(c, "modup", 8.0 * N * ((double)B * lp * 2 + (double)B * beta * E));
     // forward NTT of every converted (non-own) row
     std::string key = fmt("modup_rows:%u:%u", B, lp);
     std::vector<u32> rows;
@@ -285,8 +286,13 @@ void ks_modup(Ctx *c, u64 *D, const u64 *xe, size_t xe_bstride, u32 B, u32 lp) {
 void ks_inner(Ctx *c, u64 *acc, const u64 *D, const KeyList &kl, u32 S, u32 B, u32 lp) {
     const u32 N = c->N, E = lp + c->K;
     dim3 grid((N + 255) / 256, E, S * B);
+    prof_begin(c);
     ks_inner_kernel<<<grid, 256, 0, c->stream>>>(acc, D, kl, B, ks_digits(c, lp), lp, c->K, c->L1, c->logn, c->pdev);
-    note_launch(c, "ks_inner");
+    {
+        const double beta = ks_digits(c, lp);
+        // digits read once, each step's key read once, accumulators written once
+        note_launch(c, "ks_inner", 8.0 * N * ((double)B * beta * E + (double)S * 2 * beta * E + (double)S * B * 2 * E));
+    }
 }
 
 // out [S][B][2][lp][N] = ModDown(acc) (+ addend: poly k of ct b gathered by sigma_{g_s} when add_mask bit k)
@@ -301,10 +307,12 @@ void ks_moddown(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bst
             for (u32 kk = 0; kk < c->K; ++kk) rows.push_back((((sb * 2 + k) * E + lp + kk) << 8) | (c->L1 + kk));
     ntt_inverse(c, acc, rows_list(c, key, rows));
     dim3 grid(lp, 2, S * B);
+    prof_begin(c);
     moddown_kernel<<<grid, ntt_threads(N), (size_t)N * 8, c->stream>>>(out, acc, addend, addend_bstride, add_mask, kl, B,
                                                                       lp, c->K, c->L1, c->logn, moddown_table(c),
                                                                       c->tw, c->pdev);
-    note_launch(c, "moddown");
+    note_launch(c, "moddown",
+                8.0 * N * (double)S * B * (2.0 * E + (addend ? __builtin_popcount(add_mask) : 0) * lp + 2.0 * lp));
 }
 
 // out [B][2][lp-1][N] = rescale(in [B][2][lp][N])
@@ -315,7 +323,8 @@ void rescale_batch(Ctx *c, u64 *out, const u64 *in, u32 B, u32 lp) {
     gather_rows(c, top.p, in + (size_t)(lp - 1) * N, B * 2, lp);
     ntt_inverse(c, top.p, rows_regular(B * 2, 1, 0, lp - 1));
     dim3 grid(lp - 1, 2, B);
+    prof_begin(c);
     rescale_kernel<<<grid, ntt_threads(N), (size_t)N * 8, c->stream>>>(out, in, top.p, lp, c->logn,
                                                                       rescale_table(c, lp), c->tw, c->pdev);
-    note_launch(c, "rescale");
+    note_launch(c, "rescale", 8.0 * N * (double)B * 2 * (lp + 1 + lp - 1));
 }

@@ -510,6 +510,7 @@ struct ModelGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     Cts in, out;
+    u64 kernels = 0;   // kernel nodes in the graph
 };
 
 struct he_model {
@@ -921,16 +922,23 @@ he_status he_infer(he_model *m, const he_ct *in, int use_graph, he_ct **out) {
                     Feat w = run_layers(c, fi, m->layers, &m->pc);
                 }
                 CUDA_TRY(cudaStreamSynchronize(c->stream));
+                const bool prof = c->profiling;
+                c->profiling = false;   // no event records inside the graph
+                const u64 before = c->launches;
                 CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
                 Feat r;
                 try {
                     r = run_layers(c, fi, m->layers, &m->pc);
                 } catch (...) {
-                    cudaGraph_t tmpg;
+                    cudaGraph_t tmpg = nullptr;
                     cudaStreamEndCapture(c->stream, &tmpg);
                     if (tmpg) cudaGraphDestroy(tmpg);
+                    c->profiling = prof;
                     throw;
                 }
+                c->profiling = prof;
+                g.kernels = c->launches - before;
+                c->launches = before;
                 CUDA_TRY(cudaStreamEndCapture(c->stream, &g.graph));
                 CUDA_TRY(cudaGraphInstantiate(&g.exec, g.graph, 0));
                 g.out = r.x;   // keeps the output buffer alive in the private pool
@@ -944,7 +952,7 @@ he_status he_infer(he_model *m, const he_ct *in, int use_graph, he_ct **out) {
         ModelGraph &g = it->second;
         CUDA_TRY(cudaMemcpyAsync(g.in.data(), x.data(), inw * 8, cudaMemcpyDeviceToDevice, c->stream));
         CUDA_TRY(cudaGraphLaunch(g.exec, c->stream));
-        c->launches++;
+        c->launches += g.kernels;
         Cts o = cts_alloc(c, g.out.B, g.out.lp, g.out.scale, g.out.lay);
         CUDA_TRY(cudaMemcpyAsync(o.data(), g.out.data(), (size_t)g.out.B * cts_ct_words(c, g.out.lp) * 8,
                                  cudaMemcpyDeviceToDevice, c->stream));
@@ -986,5 +994,44 @@ he_status he_sync(he_ctx *h) {
 }
 
 uint64_t he_kernel_launches(const he_ctx *h) { return h && h->c ? h->c->launches : 0; }
+
+he_status he_profile_begin(he_ctx *h) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        c->recs.clear();
+        c->profiling = true;
+    });
+}
+
+he_status he_profile_end(he_ctx *h, he_kernel_stat *out, size_t cap, size_t *n) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        c->profiling = false;
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        std::map<std::string, he_kernel_stat> agg;
+        std::vector<std::string> order;
+        for (auto &r : c->recs) {
+            float ms = 0;
+            CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+            auto it = agg.find(r.name);
+            if (it == agg.end()) {
+                he_kernel_stat s;
+                memset(&s, 0, sizeof s);
+                strncpy(s.name, r.name, sizeof s.name - 1);
+                it = agg.emplace(r.name, s).first;
+                order.push_back(r.name);
+            }
+            it->second.launches++;
+            it->second.total_ms += ms;
+            it->second.bytes += r.bytes;
+            c->ev_free.push_back(r.a);
+            c->ev_free.push_back(r.b);
+        }
+        c->recs.clear();
+        if (n) *n = order.size();
+        if (out)
+            for (size_t i = 0; i < order.size() && i < cap; ++i) out[i] = agg[order[i]];
+    });
+}
 
 }  // extern "C"

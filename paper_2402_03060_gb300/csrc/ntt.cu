@@ -35,8 +35,9 @@ __global__ void __launch_bounds__(1024) ntt_rows_kernel(u64 *base, RowSet rs, co
 static void ntt_launch(Ctx *c, u64 *base, const RowSet &rs, int inverse) {
     if (rs.n == 0) return;
     size_t smem = (size_t)c->N * sizeof(u64);
+    prof_begin(c);
     ntt_rows_kernel<<<rs.n, ntt_threads(c->N), smem, c->stream>>>(base, rs, c->tw, c->pdev, c->logn, inverse);
-    note_launch(c, inverse ? "intt" : "ntt");
+    note_launch(c, inverse ? "intt" : "ntt", 16.0 * rs.n * c->N);   // each limb read and written once
 }
 
 void ntt_forward(Ctx *c, u64 *base, const RowSet &rs) { ntt_launch(c, base, rs, 0); }

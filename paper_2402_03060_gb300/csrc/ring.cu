@@ -32,9 +32,10 @@ __global__ void binop_kernel(int op, u64 *out, const u64 *a, const u64 *b, u32 r
 void ew_binop(Ctx *c, int op, u64 *out, const u64 *a, const u64 *b, u32 rows, u32 period, u32 lp, u32 pbase) {
     size_t total = (size_t)rows * c->N;
     if (!total) return;
+    prof_begin(c);
     binop_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(op, out, a, b, rows, c->logn, period, lp,
                                                                         pbase, c->pdev);
-    note_launch(c, "binop");
+    note_launch(c, "binop", 8.0 * total * (b ? 3 : 2));
 }
 
 // out[b][k][l][n] = a[b][k][l][n] (op) pt[l][n] for the polys k in kmask; other polys copied.
@@ -60,9 +61,10 @@ __global__ void bcast_kernel(int op, u64 *out, const u64 *a, const u64 *pt, u32 
 void ew_bcast(Ctx *c, int op, u64 *out, const u64 *a, const u64 *pt, u32 B, u32 lp, u32 kmask) {
     size_t total = (size_t)B * 2 * lp * c->N;
     if (!total) return;
+    prof_begin(c);
     bcast_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(op, out, a, pt, B, lp, c->logn, kmask,
                                                                         c->pdev);
-    note_launch(c, "bcast");
+    note_launch(c, "bcast", 8.0 * (2.0 * total + (double)lp * c->N));
 }
 
 // out[o][b][0][l][n] += pt[o][l][n]   (bias of channel o, added to c0 of every ciphertext)
@@ -84,6 +86,7 @@ __global__ void add_plain_multi_kernel(u64 *out, const u64 *pt, u32 O, u32 B, u3
 void add_plain_multi(Ctx *c, u64 *out, const u64 *pt, u32 O, u32 B, u32 lp, size_t o_stride) {
     size_t total = (size_t)O * B * lp * c->N;
     if (!total) return;
+    prof_begin(c);
     add_plain_multi_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(out, pt, O, B, lp, c->logn,
                                                                                   o_stride, c->pdev);
     note_launch(c, "add_plain");
@@ -102,6 +105,7 @@ __global__ void perm_kernel(u64 *out, const u64 *in, u32 rows, u32 logn, u32 g) 
 void galois_permute(Ctx *c, u64 *out, const u64 *in, u32 rows, u32 g) {
     size_t total = (size_t)rows * c->N;
     if (!total) return;
+    prof_begin(c);
     perm_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(out, in, rows, c->logn, g);
     note_launch(c, "galois");
 }
@@ -129,6 +133,7 @@ __global__ void tensor_sq_kernel(u64 *d, const u64 *a, u32 B, u32 lp, u32 logn, 
 
 void tensor_square(Ctx *c, u64 *d, const u64 *a, u32 B, u32 lp) {
     size_t total = (size_t)B * lp * c->N;
+    prof_begin(c);
     tensor_sq_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(d, a, B, lp, c->logn, c->pdev);
     note_launch(c, "tensor");
 }
@@ -162,6 +167,7 @@ void sample_small(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u32 
                   int kind) {
     if (nvec > SEEDLIST_MAX) throw HeError(HE_EINVAL, "sample_small: too many vectors");
     size_t total = (size_t)nvec * c->N;
+    prof_begin(c);
     sample_small_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(out, sl, nvec, rows, period, lp,
                                                                                pbase, kind, c->logn, c->pdev);
     note_launch(c, "sample_small");
@@ -185,6 +191,7 @@ __global__ void sample_uniform_kernel(u64 *out, SeedList sl, u32 nvec, u32 rows,
 void sample_uniform(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u32 period, u32 lp, u32 pbase) {
     if (nvec > SEEDLIST_MAX) throw HeError(HE_EINVAL, "sample_uniform: too many vectors");
     size_t total = (size_t)nvec * rows * c->N;
+    prof_begin(c);
     sample_uniform_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(out, sl, nvec, rows, period, lp,
                                                                                  pbase, c->logn, c->pdev);
     note_launch(c, "sample_uniform");
@@ -238,6 +245,7 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
         u32 oc = O - o0 < 16 ? O - o0 : 16;
         dim3 grid(B * 2, (c->N + 255) / 256, lp);
         const u64 *ptc = pt + (size_t)o0 * T * lp * c->N;
+        prof_begin(c);
         u64 *outc = out + (size_t)o0 * out_ostride;
         if (oc <= 1)
             mac_kernel<1><<<grid, 256, 0, c->stream>>>(outc, x, ptc, oc, T, B, lp, c->logn, x_tstride, out_ostride, c->pdev);
@@ -247,7 +255,7 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
             mac_kernel<8><<<grid, 256, 0, c->stream>>>(outc, x, ptc, oc, T, B, lp, c->logn, x_tstride, out_ostride, c->pdev);
         else
             mac_kernel<16><<<grid, 256, 0, c->stream>>>(outc, x, ptc, oc, T, B, lp, c->logn, x_tstride, out_ostride, c->pdev);
-        note_launch(c, "mac");
+        note_launch(c, "mac", 8.0 * c->N * ((double)oc * T * lp + (double)T * B * 2 * lp + (double)oc * B * 2 * lp));
     }
 }
 
@@ -264,6 +272,7 @@ __global__ void gather_rows_kernel(u64 *out, const u64 *in, u32 nrows, size_t in
 void gather_rows(Ctx *c, u64 *out, const u64 *in, u32 nrows, size_t stride_rows) {
     size_t total = (size_t)nrows * c->N;
     if (!total) return;
+    prof_begin(c);
     gather_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(out, in, nrows, stride_rows * c->N,
                                                                               c->logn);
     note_launch(c, "gather_rows");
