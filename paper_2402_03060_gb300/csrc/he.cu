@@ -78,7 +78,9 @@ void *Pool::get(size_t bytes) {
 
 void Pool::put(void *p) {
     if (!p) return;
-    size_t bytes = size_.at(p);
+    auto sz = size_.find(p);
+    if (sz == size_.end()) return;   // not from this pool (already released)
+    size_t bytes = sz->second;
     free_[bytes].push_back(p);
     bytes_live -= bytes;
     bytes_cached += bytes;

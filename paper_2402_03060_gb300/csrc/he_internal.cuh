@@ -186,7 +186,7 @@ struct Layout {
 };
 enum { PREV_INPUT = 0, PREV_CONV = 1, PREV_POOL = 2, PREV_FLAT = 3, PREV_FC = 4 };
 
-struct Ctx {
+struct Ctx : std::enable_shared_from_this<Ctx> {
     // parameters
     int logn = 0;
     u32 N = 0, L1 = 0, K = 0, dnum = 0, alpha = 0;

@@ -513,7 +513,10 @@ struct ModelGraph {
     u64 kernels = 0;   // kernel nodes in the graph
 };
 
+// Handles share ownership of their context: it is torn down when the last
+// context, ciphertext or model handle that refers to it has been freed.
 struct he_model {
+    std::shared_ptr<Ctx> keep;
     Ctx *c = nullptr;
     std::vector<LayerSpec> layers;
     u32 W_img = 0, H_img = 0, spc = 0;
@@ -533,12 +536,13 @@ struct he_model {
 };
 
 struct he_ct {
+    std::shared_ptr<Ctx> keep;   // declared first: destroyed after the buffers of x
     Ctx *c = nullptr;
     Cts x;
 };
 
 struct he_ctx {
-    Ctx *c = nullptr;
+    std::shared_ptr<Ctx> c;
 };
 
 // ------------------------------------------------------------------ C ABI
@@ -564,11 +568,12 @@ static he_status guard(F &&f) {
 static Ctx *CX(he_ctx *h) {
     if (!h || !h->c) throw HeError(HE_EINVAL, "null context");
     CUDA_TRY(cudaSetDevice(h->c->device));
-    return h->c;
+    return h->c.get();
 }
 
 static he_ct *wrap(Ctx *c, const Cts &x) {
     he_ct *h = new he_ct();
+    h->keep = c->shared_from_this();
     h->c = c;
     h->x = x;
     return h;
@@ -611,15 +616,14 @@ he_status he_context_create(const he_params *p, he_ctx **out) {
         if (!out) throw HeError(HE_EINVAL, "null output");
         Ctx *c = ctx_create(p);
         he_ctx *h = new he_ctx();
-        h->c = c;
+        h->c = std::shared_ptr<Ctx>(c, ctx_destroy);
         *out = h;
     });
 }
 
 void he_context_destroy(he_ctx *h) {
     if (!h) return;
-    ctx_destroy(h->c);
-    delete h;
+    delete h;   // the context itself goes when its last ciphertext / model handle is freed
 }
 
 he_status he_context_primes(const he_ctx *h, uint64_t *out, size_t n) {
@@ -868,6 +872,7 @@ he_status he_model_compile(he_ctx *h, const he_layer *layers, size_t n, uint32_t
         Ctx *c = CX(h);
         if (!layers || !n || !out || !spc) throw HeError(HE_EINVAL, "bad arguments");
         std::unique_ptr<he_model> m(new he_model());
+        m->keep = c->shared_from_this();
         m->c = c;
         m->layers = copy_layers(layers, n, Hi);
         m->W_img = Wi;
