@@ -84,7 +84,7 @@ __global__ void ks_inner_kernel(u64 *acc, const u64 *__restrict__ D, KeyList kl,
     o[(size_t)E * N] = reduce128(a1.lo, a1.hi, P);
 }
 
-__global__ void __launch_bounds__(1024) moddown_kernel(u64 *out, const u64 *__restrict__ acc,
+__global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, const u64 *__restrict__ acc,
                                                        const u64 *__restrict__ addend, size_t addend_bstride,
                                                        u32 add_mask, KeyList kl, u32 B, u32 lp, u32 K, u32 L1,
                                                        int logn, const u64 *__restrict__ mdtab,
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(1024) moddown_kernel(u64 *out, const u64 *__re
             }
             v = reduce128(a.lo, a.hi, P);
         }
-        sm[n] = v;
+        sm[spad(n)] = v;
     }
     __syncthreads();
     block_ntt_fwd(sm, logn, tw_all + (size_t)i * 4 * N, P.q);
@@ -122,13 +122,13 @@ __global__ void __launch_bounds__(1024) moddown_kernel(u64 *out, const u64 *__re
     const u64 *adb = add ? addend + (size_t)b * addend_bstride + ((size_t)k * lp + i) * N : nullptr;
     u64 *ob = out + ((((size_t)s * B + b) * 2 + k) * lp + i) * N;
     for (u32 n = threadIdx.x; n < N; n += blockDim.x) {
-        u64 o = mul_shoup(sub_mod(ab[(size_t)i * N + n], sm[n], P.q), pinv, pinvs, P.q);
+        u64 o = mul_shoup(sub_mod(ab[(size_t)i * N + n], sm[spad(n)], P.q), pinv, pinvs, P.q);
         if (add) o = add_mod(o, adb[g == 1 ? n : galois_src(n, g, logn)], P.q);
         ob[n] = o;
     }
 }
 
-__global__ void __launch_bounds__(1024) rescale_kernel(u64 *out, const u64 *__restrict__ in,
+__global__ void __launch_bounds__(NTT_MAX_THREADS) rescale_kernel(u64 *out, const u64 *__restrict__ in,
                                                        const u64 *__restrict__ top, u32 lp, int logn,
                                                        const u64 *__restrict__ rtab, const u64 *__restrict__ tw_all,
                                                        const PrimeDev *__restrict__ pd) {
@@ -140,14 +140,15 @@ __global__ void __launch_bounds__(1024) rescale_kernel(u64 *out, const u64 *__re
     const u64 *tb = top + ((size_t)b * 2 + k) * N;
     for (u32 n = threadIdx.x; n < N; n += blockDim.x) {
         u64 v = tb[n];
-        sm[n] = v > qt / 2 ? neg_mod(reduce64(qt - v, P), P.q) : reduce64(v, P);
+        sm[spad(n)] = v > qt / 2 ? neg_mod(reduce64(qt - v, P), P.q) : reduce64(v, P);
     }
     __syncthreads();
     block_ntt_fwd(sm, logn, tw_all + (size_t)i * 4 * N, P.q);
     const u64 w = rtab[i], ws = rtab[lp - 1 + i];
     const u64 *ib = in + (((size_t)b * 2 + k) * lp + i) * N;
     u64 *ob = out + (((size_t)b * 2 + k) * (lp - 1) + i) * N;
-    for (u32 n = threadIdx.x; n < N; n += blockDim.x) ob[n] = mul_shoup(sub_mod(ib[n], sm[n], P.q), w, ws, P.q);
+    for (u32 n = threadIdx.x; n < N; n += blockDim.x)
+        ob[n] = mul_shoup(sub_mod(ib[n], sm[spad(n)], P.q), w, ws, P.q);
 }
 
 // ------------------------------------------------------------------ host
@@ -308,7 +309,7 @@ void ks_moddown(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bst
     ntt_inverse(c, acc, rows_list(c, key, rows));
     dim3 grid(lp, 2, S * B);
     prof_begin(c);
-    moddown_kernel<<<grid, ntt_threads(N), (size_t)N * 8, c->stream>>>(out, acc, addend, addend_bstride, add_mask, kl, B,
+    moddown_kernel<<<grid, ntt_threads(N), (size_t)ntt_smem_words(N) * 8, c->stream>>>(out, acc, addend, addend_bstride, add_mask, kl, B,
                                                                       lp, c->K, c->L1, c->logn, moddown_table(c),
                                                                       c->tw, c->pdev);
     note_launch(c, "moddown",
@@ -324,7 +325,7 @@ void rescale_batch(Ctx *c, u64 *out, const u64 *in, u32 B, u32 lp) {
     ntt_inverse(c, top.p, rows_regular(B * 2, 1, 0, lp - 1));
     dim3 grid(lp - 1, 2, B);
     prof_begin(c);
-    rescale_kernel<<<grid, ntt_threads(N), (size_t)N * 8, c->stream>>>(out, in, top.p, lp, c->logn,
+    rescale_kernel<<<grid, ntt_threads(N), (size_t)ntt_smem_words(N) * 8, c->stream>>>(out, in, top.p, lp, c->logn,
                                                                       rescale_table(c, lp), c->tw, c->pdev);
     note_launch(c, "rescale", 8.0 * N * (double)B * 2 * (lp + 1 + lp - 1));
 }

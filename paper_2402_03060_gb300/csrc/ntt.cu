@@ -15,7 +15,7 @@ __device__ __forceinline__ void row_of(const RowSet &rs, u32 r, u32 &off, u32 &p
     }
 }
 
-__global__ void __launch_bounds__(1024) ntt_rows_kernel(u64 *base, RowSet rs, const u64 *tw_all,
+__global__ void __launch_bounds__(NTT_MAX_THREADS) ntt_rows_kernel(u64 *base, RowSet rs, const u64 *tw_all,
                                                         const PrimeDev *pd, int logn, int inverse) {
     extern __shared__ u64 sm[];
     const u32 N = 1u << logn;
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(1024) ntt_rows_kernel(u64 *base, RowSet rs, co
 
 static void ntt_launch(Ctx *c, u64 *base, const RowSet &rs, int inverse) {
     if (rs.n == 0) return;
-    size_t smem = (size_t)c->N * sizeof(u64);
+    size_t smem = (size_t)ntt_smem_words(c->N) * sizeof(u64);
     prof_begin(c);
     ntt_rows_kernel<<<rs.n, ntt_threads(c->N), smem, c->stream>>>(base, rs, c->tw, c->pdev, c->logn, inverse);
     note_launch(c, inverse ? "intt" : "ntt", 16.0 * rs.n * c->N);   // each limb read and written once

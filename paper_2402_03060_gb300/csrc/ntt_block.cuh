@@ -6,9 +6,14 @@
 // psi powers (their Alg. 2) followed by the N^{-1} scaling.  Twiddle tables
 // per prime: [psi_rev | psi_rev_shoup | ipsi_rev | ipsi_rev_shoup], N words each.
 //
-// Lazy reduction (Harvey 2014): values are kept in [0, 4q) between the
-// butterflies of the forward transform and in [0, 2q) in the inverse one, and
-// reduced to [0, q) at the end; all primes are below 2^61, so 4q < 2^63.
+// Lazy reduction (Harvey 2014): values stay in [0, 4q) between forward
+// butterflies and in [0, 2q) between inverse ones; all primes are below 2^61.
+//
+// Register blocking: for N >= 1024 every thread holds 16 coefficients of a
+// butterfly group and runs 4 stages on them in registers, so a limb of 2^14
+// coefficients takes 4 shared-memory passes (and 4 barriers) instead of 14,
+// and a group loads 15 twiddle pairs for 32 butterflies.  Shared memory is
+// padded by one word per 16 so that the strided group loads are conflict-free.
 #pragma once
 #include "he_internal.cuh"
 
@@ -18,73 +23,204 @@ __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q) {
     return a * w - qh * q;
 }
 
-// in-place forward transform of a[0..N) in shared memory; all threads of the CTA call it.
-__device__ __forceinline__ void block_ntt_fwd(u64 *a, int logn, const u64 *__restrict__ tw, u64 q) {
+__device__ __forceinline__ u32 spad(u32 i) { return i + (i >> 4); }
+// shared-memory words a limb of N coefficients occupies (padded)
+__host__ __device__ __forceinline__ u32 ntt_smem_words(u32 N) { return N + N / 16; }
+
+// threads of a CTA that transforms one limb: two 16-coefficient register groups
+// per thread per pass (so a thread may use up to 128 registers without spilling)
+#define NTT_MAX_THREADS 512
+static inline u32 ntt_threads(u32 N) { return N >= 1024 ? N / 32 : (N / 2 < 32 ? 32 : N / 2); }
+
+// ---------------------------------------------------------------- forward
+__device__ __forceinline__ void fwd_radix2_stage(u64 *a, int logn, int lgm, const u64 *__restrict__ tw, u64 q) {
     const u32 N = 1u << logn;
     const u64 *tws = tw + N;
-    const u64 q2 = 2 * q, q4 = 4 * q;
-    for (int lgm = 0; lgm < logn; ++lgm) {
-        const int lgt = logn - 1 - lgm;
-        const u32 t = 1u << lgt;
-        for (u32 b = threadIdx.x; b < N / 2; b += blockDim.x) {
-            const u32 i = b >> lgt;
-            const u32 j = (i << (lgt + 1)) + (b & (t - 1));
-            const u64 S = __ldg(tw + (1u << lgm) + i);
-            const u64 Ss = __ldg(tws + (1u << lgm) + i);
-            u64 U = a[j];
-            if (U >= q2) U -= q2;
-            const u64 V = shoup_lazy(a[j + t], S, Ss, q);
-            a[j] = U + V;                 // < 4q
-            a[j + t] = U - V + q2;        // < 4q
-        }
-        __syncthreads();
+    const u64 q2 = 2 * q;
+    const int lgt = logn - 1 - lgm;
+    const u32 t = 1u << lgt;
+    for (u32 b = threadIdx.x; b < N / 2; b += blockDim.x) {
+        const u32 i = b >> lgt;
+        const u32 j = (i << (lgt + 1)) + (b & (t - 1));
+        const u64 S = __ldg(tw + (1u << lgm) + i), Ss = __ldg(tws + (1u << lgm) + i);
+        u64 U = a[spad(j)];
+        if (U >= q2) U -= q2;
+        const u64 V = shoup_lazy(a[spad(j + t)], S, Ss, q);
+        a[spad(j)] = U + V;
+        a[spad(j + t)] = U - V + q2;
     }
+}
+
+// R stages starting at stage st on groups of 2^R coefficients held in registers
+template <int R>
+__device__ __forceinline__ void fwd_pass(u64 *a, int logn, int st, const u64 *__restrict__ tw, u64 q) {
+    const u32 N = 1u << logn;
+    const u64 *tws = tw + N;
+    const u64 q2 = 2 * q;
+    const int lgt0 = logn - 1 - st;          // log2 of the first distance t0
+    const int lgtl = lgt0 - (R - 1);         // log2 of the smallest distance
+    const u32 tl = 1u << lgtl;
+    const u32 groups = N >> R;
+    for (u32 g = threadIdx.x; g < groups; g += blockDim.x) {
+        const u32 base = ((g >> lgtl) << (lgt0 + 1)) + (g & (tl - 1));
+        u64 v[1 << R];
+#pragma unroll
+        for (int k = 0; k < (1 << R); ++k) v[k] = a[spad(base + ((u32)k << lgtl))];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const int lgd = lgt0 - u;                 // distance 2^lgd at stage st+u
+            const u32 m = 1u << (st + u);
+            const int half = 1 << (R - 1 - u);
+#pragma unroll
+            for (int blk = 0; blk < (1 << u); ++blk) {
+                const u32 j = base + ((u32)(blk * 2 * half) << lgtl);
+                const u32 i = j >> (lgd + 1);
+                const u64 S = __ldg(tw + m + i), Ss = __ldg(tws + m + i);
+#pragma unroll
+                for (int h = 0; h < half; ++h) {
+                    const int k = blk * 2 * half + h;
+                    u64 U = v[k];
+                    if (U >= q2) U -= q2;
+                    const u64 V = shoup_lazy(v[k + half], S, Ss, q);
+                    v[k] = U + V;
+                    v[k + half] = U - V + q2;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < (1 << R); ++k) a[spad(base + ((u32)k << lgtl))] = v[k];
+    }
+}
+
+// in-place forward transform of a[spad(0..N)] in shared memory; output in [0, q).
+__device__ __forceinline__ void block_ntt_fwd(u64 *a, int logn, const u64 *__restrict__ tw, u64 q) {
+    const u32 N = 1u << logn;
+    if (logn >= 10) {
+        int st = 0;
+        for (; st + 4 <= logn; st += 4) {
+            fwd_pass<4>(a, logn, st, tw, q);
+            __syncthreads();
+        }
+        const int rem = logn - st;
+        if (rem == 3) fwd_pass<3>(a, logn, st, tw, q);
+        if (rem == 2) fwd_pass<2>(a, logn, st, tw, q);
+        if (rem == 1) fwd_pass<1>(a, logn, st, tw, q);
+        if (rem) __syncthreads();
+    } else {
+        for (int lgm = 0; lgm < logn; ++lgm) {
+            fwd_radix2_stage(a, logn, lgm, tw, q);
+            __syncthreads();
+        }
+    }
+    const u64 q2 = 2 * q;
     for (u32 k = threadIdx.x; k < N; k += blockDim.x) {
-        u64 v = a[k];
+        u64 v = a[spad(k)];
         if (v >= q2) v -= q2;
         if (v >= q) v -= q;
-        a[k] = v;
+        a[spad(k)] = v;
     }
     __syncthreads();
+}
+
+// ---------------------------------------------------------------- inverse
+__device__ __forceinline__ void inv_radix2_stage(u64 *a, int logn, int lgt, const u64 *__restrict__ tw, u64 q) {
+    const u32 N = 1u << logn;
+    const u64 *itw = tw + 2 * N, *itws = tw + 3 * N;
+    const u64 q2 = 2 * q;
+    const u32 t = 1u << lgt;
+    const u32 h = N >> (lgt + 1);
+    for (u32 b = threadIdx.x; b < N / 2; b += blockDim.x) {
+        const u32 i = b >> lgt;
+        const u32 j = (i << (lgt + 1)) + (b & (t - 1));
+        const u64 S = __ldg(itw + h + i), Ss = __ldg(itws + h + i);
+        const u64 U = a[spad(j)], V = a[spad(j + t)];
+        u64 s = U + V;
+        if (s >= q2) s -= q2;
+        a[spad(j)] = s;
+        a[spad(j + t)] = shoup_lazy(U - V + q2, S, Ss, q);
+    }
+}
+
+// R Gentleman-Sande stages with distances 2^lgtl .. 2^(lgtl+R-1)
+template <int R>
+__device__ __forceinline__ void inv_pass(u64 *a, int logn, int lgtl, const u64 *__restrict__ tw, u64 q) {
+    const u32 N = 1u << logn;
+    const u64 *itw = tw + 2 * N, *itws = tw + 3 * N;
+    const u64 q2 = 2 * q;
+    const u32 tl = 1u << lgtl;
+    const u32 groups = N >> R;
+    for (u32 g = threadIdx.x; g < groups; g += blockDim.x) {
+        const u32 base = ((g >> lgtl) << (lgtl + R)) + (g & (tl - 1));
+        u64 v[1 << R];
+#pragma unroll
+        for (int k = 0; k < (1 << R); ++k) v[k] = a[spad(base + ((u32)k << lgtl))];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const int lgd = lgtl + u;               // distance at this stage
+            const u32 h = N >> (lgd + 1);
+            const int half = 1 << u;
+#pragma unroll
+            for (int blk = 0; blk < (1 << (R - 1 - u)); ++blk) {
+                const u32 j = base + ((u32)(blk * 2 * half) << lgtl);
+                const u32 i = j >> (lgd + 1);
+                const u64 S = __ldg(itw + h + i), Ss = __ldg(itws + h + i);
+#pragma unroll
+                for (int hh = 0; hh < half; ++hh) {
+                    const int k = blk * 2 * half + hh;
+                    const u64 U = v[k], V = v[k + half];
+                    u64 s = U + V;
+                    if (s >= q2) s -= q2;
+                    v[k] = s;
+                    v[k + half] = shoup_lazy(U - V + q2, S, Ss, q);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < (1 << R); ++k) a[spad(base + ((u32)k << lgtl))] = v[k];
+    }
 }
 
 // in-place inverse transform including the N^{-1} factor; input in [0, q).
 __device__ __forceinline__ void block_ntt_inv(u64 *a, int logn, const u64 *__restrict__ tw, u64 q, u64 ninv,
                                               u64 ninvs) {
     const u32 N = 1u << logn;
-    const u64 *itw = tw + 2 * N;
-    const u64 *itws = tw + 3 * N;
-    const u64 q2 = 2 * q;
-    for (int lgt = 0; lgt < logn; ++lgt) {
-        const u32 t = 1u << lgt;
-        const u32 h = N >> (lgt + 1);
-        for (u32 b = threadIdx.x; b < N / 2; b += blockDim.x) {
-            const u32 i = b >> lgt;
-            const u32 j = (i << (lgt + 1)) + (b & (t - 1));
-            const u64 S = __ldg(itw + h + i);
-            const u64 Ss = __ldg(itws + h + i);
-            const u64 U = a[j], V = a[j + t];   // both < 2q
-            u64 s = U + V;
-            if (s >= q2) s -= q2;
-            a[j] = s;                          // < 2q
-            a[j + t] = shoup_lazy(U - V + q2, S, Ss, q);   // < 2q
+    if (logn >= 10) {
+        int lgt = 0;
+        for (; lgt + 4 <= logn; lgt += 4) {
+            inv_pass<4>(a, logn, lgt, tw, q);
+            __syncthreads();
         }
-        __syncthreads();
+        const int rem = logn - lgt;
+        if (rem == 3) inv_pass<3>(a, logn, lgt, tw, q);
+        if (rem == 2) inv_pass<2>(a, logn, lgt, tw, q);
+        if (rem == 1) inv_pass<1>(a, logn, lgt, tw, q);
+        if (rem) __syncthreads();
+    } else {
+        for (int lgt = 0; lgt < logn; ++lgt) {
+            inv_radix2_stage(a, logn, lgt, tw, q);
+            __syncthreads();
+        }
     }
-    for (u32 k = threadIdx.x; k < N; k += blockDim.x) a[k] = mul_shoup(a[k], ninv, ninvs, q);
+    for (u32 k = threadIdx.x; k < N; k += blockDim.x) a[spad(k)] = mul_shoup(a[spad(k)], ninv, ninvs, q);
     __syncthreads();
 }
 
+// global <-> padded shared memory, 16-byte vector accesses on the global side
 __device__ __forceinline__ void block_load(u64 *s, const u64 *__restrict__ g, u32 N) {
     const ulonglong2 *g2 = reinterpret_cast<const ulonglong2 *>(g);
-    ulonglong2 *s2 = reinterpret_cast<ulonglong2 *>(s);
-    for (u32 k = threadIdx.x; k < N / 2; k += blockDim.x) s2[k] = g2[k];
+    for (u32 k = threadIdx.x; k < N / 2; k += blockDim.x) {
+        ulonglong2 v = g2[k];
+        s[spad(2 * k)] = v.x;
+        s[spad(2 * k + 1)] = v.y;
+    }
     __syncthreads();
 }
 __device__ __forceinline__ void block_store(u64 *__restrict__ g, const u64 *s, u32 N) {
-    const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(s);
     ulonglong2 *g2 = reinterpret_cast<ulonglong2 *>(g);
-    for (u32 k = threadIdx.x; k < N / 2; k += blockDim.x) g2[k] = s2[k];
+    for (u32 k = threadIdx.x; k < N / 2; k += blockDim.x) {
+        ulonglong2 v;
+        v.x = s[spad(2 * k)];
+        v.y = s[spad(2 * k + 1)];
+        g2[k] = v;
+    }
 }
-
-static inline u32 ntt_threads(u32 N) { return N >= 2048 ? 1024 : N / 2; }

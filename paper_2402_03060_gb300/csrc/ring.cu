@@ -199,40 +199,61 @@ void sample_uniform(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u3
 
 // --------------------------------------------------------------- MAC
 // out[o][b][k][l][n] = sum_t pt[o][t][l][n] * x[t][b][k][l][n]   (mod q_l)
-// 128-bit lazy accumulation (each product < 2^120, reduced every 128 terms).
-// One thread per (n, l, b, k), all O outputs in registers; CTAs that share
-// (l, n-tile) are adjacent in the grid so the plaintext tile is read from HBM
-// once and then hit in L2 by the other (b, k) CTAs.
+//
+// A CTA owns NT consecutive coefficients of one limb and 256/NT
+// (ciphertext, poly) pairs; it stages the plaintext tile pt[0..O)[t-chunk][l][n-tile]
+// in shared memory once and every thread reuses it for its own pair, so a
+// plaintext word is read from global memory once per 256/NT pairs instead of
+// once per pair.  Lanes of a warp cover 4+ consecutive coefficients of 8 or
+// fewer pairs, so every ciphertext load is a full 32-byte sector.  Each thread
+// keeps all O sums as 128-bit accumulators (products < 2^120, folded every 128 terms).
 template <int OMAX>
 __global__ void __launch_bounds__(256) mac_kernel(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt,
-                                                  u32 O, u32 T, u32 B, u32 lp, u32 logn, size_t x_tstride,
-                                                  size_t out_ostride, const PrimeDev *pd) {
-    const u32 N = 1u << logn;
-    const u32 bk = blockIdx.x;                  // b*2 + k
-    const u32 n = blockIdx.y * blockDim.x + threadIdx.x;
+                                                  u32 O, u32 T, u32 BK, u32 lp, u32 logn, size_t x_tstride,
+                                                  size_t out_ostride, u32 ntlog, u32 tc,
+                                                  const PrimeDev *__restrict__ pd) {
+    extern __shared__ u64 ps[];   // [O][tc][NT]
+    const u32 N = 1u << logn, NT = 1u << ntlog;
+    const u32 tid = threadIdx.x;
+    const u32 nl = tid & (NT - 1);
+    const u32 bk = blockIdx.x * (256u >> ntlog) + (tid >> ntlog);
+    const u32 n0 = blockIdx.y * NT;
     const u32 l = blockIdx.z;
-    if (n >= N) return;
-    const u32 b = bk >> 1, k = bk & 1;
+    const bool active = bk < BK;
     const PrimeDev P = pd[l];
     Acc128 acc[OMAX];
 #pragma unroll
     for (int o = 0; o < OMAX; ++o) acc[o].lo = acc[o].hi = 0;
-    const size_t xoff = (((size_t)b * 2 + k) * lp + l) * N + n;
-    const size_t poff = (size_t)l * N + n;
-    const size_t pstride_t = (size_t)lp * N, pstride_o = (size_t)T * lp * N;
-    for (u32 t = 0; t < T; ++t) {
-        const u64 xv = __ldg(x + t * x_tstride + xoff);
+    const size_t xoff = ((size_t)bk * lp + l) * N + n0 + nl;   // bk = b*2 + k
+    const size_t pstride_t = (size_t)lp * N;
+    u32 cnt = 0;
+    for (u32 t0 = 0; t0 < T; t0 += tc) {
+        const u32 tcc = T - t0 < tc ? T - t0 : tc;
+        __syncthreads();
+        for (u32 idx = tid; idx < O * tcc * NT; idx += blockDim.x) {
+            const u32 j = idx & (NT - 1), r = idx >> ntlog;
+            const u32 tt = r % tcc, o = r / tcc;
+            ps[((size_t)o * tc + tt) * NT + j] = pt[((size_t)o * T + t0 + tt) * pstride_t + (size_t)l * N + n0 + j];
+        }
+        __syncthreads();
+        if (active) {
+            for (u32 tt = 0; tt < tcc; ++tt) {
+                const u64 xv = __ldcs(x + (size_t)(t0 + tt) * x_tstride + xoff);
 #pragma unroll
-        for (int o = 0; o < OMAX; ++o)
-            if (o < (int)O) mac128(acc[o], __ldg(pt + o * pstride_o + t * pstride_t + poff), xv);
-        if ((t & 127) == 127) {
+                for (int o = 0; o < OMAX; ++o)
+                    if (o < (int)O) mac128(acc[o], ps[((size_t)o * tc + tt) * NT + nl], xv);
+                if (++cnt == 128) {
+                    cnt = 0;
 #pragma unroll
-            for (int o = 0; o < OMAX; ++o) {
-                acc[o].lo = reduce128(acc[o].lo, acc[o].hi, P);
-                acc[o].hi = 0;
+                    for (int o = 0; o < OMAX; ++o) {
+                        acc[o].lo = reduce128(acc[o].lo, acc[o].hi, P);
+                        acc[o].hi = 0;
+                    }
+                }
             }
         }
     }
+    if (!active) return;
 #pragma unroll
     for (int o = 0; o < OMAX; ++o)
         if (o < (int)O) out[o * out_ostride + xoff] = reduce128(acc[o].lo, acc[o].hi, P);
@@ -241,20 +262,35 @@ __global__ void __launch_bounds__(256) mac_kernel(u64 *out, const u64 *__restric
 void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O, u32 T, u32 B,
          u32 lp) {
     // pt [O][T][lp][N]; x [T] blocks of [B][2][lp][N] at x_tstride; out [O] blocks at out_ostride
+    const u32 BK = 2 * B;
+    u32 bkc = 1;
+    while (bkc < BK && bkc < 64) bkc <<= 1;
+    u32 ntlog = 0;
+    while ((1u << ntlog) * bkc < 256) ++ntlog;
+    if ((1u << ntlog) > c->N) throw HeError(HE_EINVAL, "mac: ring too small");
+    const u32 NT = 1u << ntlog;
     for (u32 o0 = 0; o0 < O; o0 += 16) {
-        u32 oc = O - o0 < 16 ? O - o0 : 16;
-        dim3 grid(B * 2, (c->N + 255) / 256, lp);
+        const u32 oc = O - o0 < 16 ? O - o0 : 16;
+        u32 tc = 6144 / (oc * NT);
+        if (tc < 1) tc = 1;
+        if (tc > T) tc = T;
+        const size_t smem = (size_t)oc * tc * NT * 8;
+        dim3 grid((BK + bkc - 1) / bkc, c->N / NT, lp);
         const u64 *ptc = pt + (size_t)o0 * T * lp * c->N;
-        prof_begin(c);
         u64 *outc = out + (size_t)o0 * out_ostride;
+        prof_begin(c);
         if (oc <= 1)
-            mac_kernel<1><<<grid, 256, 0, c->stream>>>(outc, x, ptc, oc, T, B, lp, c->logn, x_tstride, out_ostride, c->pdev);
+            mac_kernel<1><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride, out_ostride,
+                                                          ntlog, tc, c->pdev);
         else if (oc <= 4)
-            mac_kernel<4><<<grid, 256, 0, c->stream>>>(outc, x, ptc, oc, T, B, lp, c->logn, x_tstride, out_ostride, c->pdev);
+            mac_kernel<4><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride, out_ostride,
+                                                          ntlog, tc, c->pdev);
         else if (oc <= 8)
-            mac_kernel<8><<<grid, 256, 0, c->stream>>>(outc, x, ptc, oc, T, B, lp, c->logn, x_tstride, out_ostride, c->pdev);
+            mac_kernel<8><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride, out_ostride,
+                                                          ntlog, tc, c->pdev);
         else
-            mac_kernel<16><<<grid, 256, 0, c->stream>>>(outc, x, ptc, oc, T, B, lp, c->logn, x_tstride, out_ostride, c->pdev);
+            mac_kernel<16><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride,
+                                                           out_ostride, ntlog, tc, c->pdev);
         note_launch(c, "mac", 8.0 * c->N * ((double)oc * T * lp + (double)T * B * 2 * lp + (double)oc * B * 2 * lp));
     }
 }
