@@ -208,7 +208,7 @@ void sample_uniform(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u3
 // fewer pairs, so every ciphertext load is a full 32-byte sector.  Each thread
 // keeps all O sums as 128-bit accumulators (products < 2^120, folded every 128 terms).
 template <int OMAX>
-__global__ void __launch_bounds__(256) mac_kernel(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt,
+__global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt,
                                                   u32 O, u32 T, u32 BK, u32 lp, u32 logn, size_t x_tstride,
                                                   size_t out_ostride, u32 ntlog, u32 tc,
                                                   const PrimeDev *__restrict__ pd) {
@@ -279,18 +279,24 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
         const u64 *ptc = pt + (size_t)o0 * T * lp * c->N;
         u64 *outc = out + (size_t)o0 * out_ostride;
         prof_begin(c);
+#define MAC_LAUNCH(OM)                                                                                        \
+    mac_kernel<OM><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride, out_ostride, \
+                                                   ntlog, tc, c->pdev)
         if (oc <= 1)
-            mac_kernel<1><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride, out_ostride,
-                                                          ntlog, tc, c->pdev);
+            MAC_LAUNCH(1);
+        else if (oc <= 2)
+            MAC_LAUNCH(2);
         else if (oc <= 4)
-            mac_kernel<4><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride, out_ostride,
-                                                          ntlog, tc, c->pdev);
+            MAC_LAUNCH(4);
+        else if (oc <= 6)
+            MAC_LAUNCH(6);
         else if (oc <= 8)
-            mac_kernel<8><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride, out_ostride,
-                                                          ntlog, tc, c->pdev);
+            MAC_LAUNCH(8);
+        else if (oc <= 12)
+            MAC_LAUNCH(12);
         else
-            mac_kernel<16><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride,
-                                                           out_ostride, ntlog, tc, c->pdev);
+            MAC_LAUNCH(16);
+#undef MAC_LAUNCH
         note_launch(c, "mac", 8.0 * c->N * ((double)oc * T * lp + (double)T * B * 2 * lp + (double)oc * B * 2 * lp));
     }
 }
