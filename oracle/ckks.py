@@ -509,6 +509,69 @@ class Ckks:
             out[r] = Ct(np.stack([self.add(c0, self.moddown(acc0), q), self.moddown(acc1)]), ct.scale)
         return out
 
+    def encode_ext(self, z, scale: float, lp: int) -> np.ndarray:
+        """Plaintext over Q_l u P (eval form, [lp+K][N]): the same rounded integer
+        polynomial as ``encode`` reduced into the special primes as well."""
+        basis, psis = self.ext_basis(lp)
+        return self.ntt(self.reduce_signed(self.encode_coeffs(z, scale), basis), basis, psis)
+
+    def lincomb(self, cts, steps, weights=None, pt_scale: float = 1.0):
+        """Hoisted linear combination of rotations with one ModDown per output:
+
+            Y_o = sum_i sum_s w[o][i][s] (.) Rot(ct_i, steps[s])
+
+        computed as Y_o = ModDown(Z_o), Z_o = sum_{i,s} w[o][i][s] (.) A_{i,s} over Q_l u P, where
+            A_{i,s} = (sum_j sigma_g(D_j) (.) ksk_g,j,0 + P*sigma_g(c0),  sum_j sigma_g(D_j) (.) ksk_g,j,1)
+        (D = ModUp(c1) of ct_i, g = 5^steps[s]) and A_{i,s} = (P*c0, P*c1) for a step of 0.
+        Because ModDown(A + P*x) = ModDown(A) + x exactly, Y_o decrypts to the same
+        message as the rotate-then-multiply composition; only the rounding of the
+        single ModDown differs.  w[o][i][s] are plaintexts over Q_l u P (``encode_ext``)
+        or None (all ones, a plain sum of rotations); the output scale is
+        ct.scale * pt_scale."""
+        lp = cts[0].lp
+        K = self.K
+        E = lp + K
+        basis, _ = self.ext_basis(lp)
+        q = self.q[:lp]
+        pq = np.array([self.P_mod(qi) for qi in q], dtype=np.uint64)
+        Pq = np.repeat(pq[:, None], self.n, axis=1)
+        zero_p = np.zeros((K, self.n), dtype=np.uint64)
+        A = []   # A[i][s] = (a0, a1) over E limbs
+        for ct in cts:
+            assert ct.lp == lp and ct.scale == cts[0].scale
+            digs = None
+            row = []
+            for r in steps:
+                g = galois_elt(r, self.logn)
+                if g == 1:
+                    a0 = np.concatenate([self.mul(ct.d[0], Pq, q), zero_p])
+                    a1 = np.concatenate([self.mul(ct.d[1], Pq, q), zero_p])
+                else:
+                    if digs is None:
+                        digs = self.modup(ct.d[1])
+                    a0, a1 = self.ks_inner(digs, self.keys.gk[g], g)
+                    c0g = self.automorph_eval(ct.d[0], g)
+                    a0 = np.concatenate([self.add(a0[:lp], self.mul(c0g, Pq, q), q), a0[lp:]])
+                row.append((a0, a1))
+            A.append(row)
+        n_out = 1 if weights is None else len(weights)
+        outs = []
+        for o in range(n_out):
+            z0 = np.zeros((E, self.n), dtype=np.uint64)
+            z1 = np.zeros_like(z0)
+            for i in range(len(cts)):
+                for s in range(len(steps)):
+                    a0, a1 = A[i][s]
+                    if weights is None:
+                        z0 = self.add(z0, a0, basis)
+                        z1 = self.add(z1, a1, basis)
+                    else:
+                        w = weights[o][i][s]
+                        lib().o_muladd(_p(z0), _p(_u(a0)), _p(_u(w)), E, self.n, _p(basis))
+                        lib().o_muladd(_p(z1), _p(_u(a1)), _p(_u(w)), E, self.n, _p(basis))
+            outs.append(Ct(np.stack([self.moddown(z0), self.moddown(z1)]), cts[0].scale * pt_scale))
+        return outs
+
     def square(self, ct: Ct) -> Ct:
         """Ciphertext tensor with itself, relinearisation, rescale (reading C15)."""
         q = self.q[: ct.lp]

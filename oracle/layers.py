@@ -5,6 +5,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 A backend supplies slot-vector operations:
     rot(x, r)            Rot(x, r): left rotation by r slots (paper Sec. II-B)
     rot_many(x, steps)   several rotations of one input (hoisted on ciphertexts)
+    lincomb(xs, steps, w)  Y_o = sum_i sum_s w[o][i][s] * Rot(xs[i], steps[s]) (w None: a
+                         single plain sum of the rotations); on ciphertexts all rotations
+                         of an input share one ModUp and each output one ModDown
     add(x, y)            Add (C)
     mul_mask(x, v)       Mul (P) by the slot vector v encoded at scale Delta
     add_mask(x, v)       Add (P) of v encoded at x's current scale and level
@@ -89,12 +92,17 @@ def conv(be, xs, w, bias, S: int, lay: Layout, mode: str = "hoisted"):
     Wout = (lay.W - kw) // S + 1
     Iout = I * S
     pos = [Iout * (r * lay.W_img + c) for r in range(Hout) for c in range(Wout)]
-    rots = []
-    for i in range(ci):
-        if mode == "hoisted":
-            rr = be.rot_many(xs[i], [step[o] for o in offs])
-            rots.append({o: rr[step[o]] for o in offs})
-        elif mode == "incremental":
+    def kvec(o, i, off):
+        return slot_vector(lay, pos, float(w[o, i, off[0], off[1]]) * lay.pending)
+
+    if mode == "hoisted":
+        # all rotations of every input channel and all products in one hoisted
+        # linear combination per output channel
+        weights = [[[kvec(o, i, off) for off in offs] for i in range(ci)] for o in range(co)]
+        sums = be.lincomb(xs, [step[o] for o in offs], weights)
+    elif mode == "incremental":
+        rots = []
+        for i in range(ci):
             rr = {offs[0]: xs[i]}
             prev = xs[i]
             for o in offs[1:]:
@@ -102,17 +110,19 @@ def conv(be, xs, w, bias, S: int, lay: Layout, mode: str = "hoisted"):
                 prev = be.rot(prev, s)
                 rr[o] = prev
             rots.append(rr)
-        else:
-            raise ValueError(mode)
+        sums = []
+        for o in range(co):
+            acc = None
+            for i in range(ci):
+                for off in offs:
+                    t = be.mul_mask(rots[i][off], kvec(o, i, off))
+                    acc = t if acc is None else be.add(acc, t)
+            sums.append(acc)
+    else:
+        raise ValueError(mode)
     outs = []
     for o in range(co):
-        acc = None
-        for i in range(ci):
-            for off in offs:
-                wv = float(w[o, i, off[0], off[1]]) * lay.pending
-                t = be.mul_mask(rots[i][off], slot_vector(lay, pos, wv))
-                acc = t if acc is None else be.add(acc, t)
-        acc = be.rescale(acc)
+        acc = be.rescale(sums[o])
         acc = be.add_mask(acc, slot_vector(lay, pos, float(bias[o])))
         outs.append(acc)
     return outs, replace(lay, W=Wout, H=Hout, I=Iout, pending=1.0, prev="conv")
@@ -129,13 +139,7 @@ def avgpool(be, xs, c: int, lay: Layout):
     additions only (no mask, no level); 1/c^2 is deferred into ``pending``."""
     ch = c if lay.dims == 2 else 1
     steps = [lay.I * (k + lay.W_img * j) for j in range(ch) for k in range(c)]
-    outs = []
-    for x in xs:
-        rr = be.rot_many(x, steps)
-        acc = None
-        for s in steps:
-            acc = rr[s] if acc is None else be.add(acc, rr[s])
-        outs.append(acc)
+    outs = [be.lincomb([x], steps, None)[0] for x in xs]
     Hout = lay.H // c if lay.dims == 2 else 1
     return outs, replace(lay, W=lay.W // c, H=Hout, I=lay.I * c,
                          pending=lay.pending / float(c ** lay.dims), prev="avgpool")
@@ -180,11 +184,7 @@ def flatten(be, xs, lay: Layout):
         if I > 1 and W > 1:
             new = []
             for x in cur:
-                rr = be.rot_many(x, [m * (I - 1) for m in range(I)])
-                y = None
-                for m in range(I):
-                    s = m * (I - 1)
-                    y = rr[s] if y is None else be.add(y, rr[s])
+                y = be.lincomb([x], [m * (I - 1) for m in range(I)], None)[0]
                 acc = None
                 for u in range(-(-W // I)):
                     cols = range(I * u, min(I * u + I, W))
@@ -242,23 +242,15 @@ def fc(be, xs, M, bias, lay: Layout):
         M = M * lay.pending
     Mr, Wv = fc_rot_matrix(M)
     x = xs[0]
+    # rotations by o (with V1_o) then by o - W_vec (with V2_o, o >= 1): one hoisted combination
     steps = [o for o in range(dout)] + [o - Wv for o in range(1, dout)]
-    rr = be.rot_many(x, steps)
     t_idx = np.arange(Wv)
-    acc = None
-    for o in range(dout):
-        v1 = np.where(t_idx < Wv - o, Mr[o], 0.0)
-        t = be.mul_mask(rr[o], slot_vector(lay, t_idx, v1))
-        acc = t if acc is None else be.add(acc, t)
-        if o:
-            v2 = np.where(t_idx >= Wv - o, Mr[o], 0.0)
-            acc = be.add(acc, be.mul_mask(rr[o - Wv], slot_vector(lay, t_idx, v2)))
+    vecs = [slot_vector(lay, t_idx, np.where(t_idx < Wv - o, Mr[o], 0.0)) for o in range(dout)]
+    vecs += [slot_vector(lay, t_idx, np.where(t_idx >= Wv - o, Mr[o], 0.0)) for o in range(1, dout)]
+    acc = be.lincomb([x], steps, [[vecs]])[0]
     acc = be.rescale(acc)
     nsum = Wv // dout
-    rs = be.rot_many(acc, [i * dout for i in range(nsum)])
-    out = None
-    for i in range(nsum):
-        out = rs[i * dout] if out is None else be.add(out, rs[i * dout])
+    out = be.lincomb([acc], [i * dout for i in range(nsum)], None)[0]
     out = be.add_mask(out, slot_vector(lay, np.arange(dout), np.asarray(bias, dtype=np.float64)))
     return [out], replace(lay, pending=1.0, prev="fc", D=dout, W=dout)
 
@@ -367,6 +359,16 @@ class HeBackend:
     def rot_many(self, x, steps):
         self.count["rot"] += len({s for s in steps if s % (self.he.n // 2)})
         return self.he.rotate_hoisted(x, steps)
+
+    def lincomb(self, xs, steps, weights):
+        m = self.he.n // 2
+        self.count["rot"] += len(xs) * len({s % m for s in steps if s % m})
+        if weights is None:
+            return self.he.lincomb(xs, steps, None)
+        self.count["pmul"] += sum(len(wi) for wo in weights for wi in wo)
+        lp = xs[0].lp
+        enc = [[[self.he.encode_ext(v, self.he.scale, lp) for v in wi] for wi in wo] for wo in weights]
+        return self.he.lincomb(xs, steps, enc, self.he.scale)
 
     def add(self, x, y):
         return self.he.ct_add(x, y)

@@ -37,6 +37,24 @@ class SlotSim:
         self.count["rot"] += len({s for s in steps if s % len(x.v)})
         return {s: SV(np.roll(x.v, -s), x.used, x.pending_rescale) for s in steps}
 
+    def lincomb(self, xs, steps, weights):
+        m = len(xs[0].v)
+        self.count["rot"] += len(xs) * len({s % m for s in steps if s % m})
+        for x in xs[1:]:
+            assert x.used == xs[0].used and not x.pending_rescale
+        if weights is None:
+            v = sum(np.roll(x.v, -s) for x in xs for s in steps)
+            return [SV(v, xs[0].used, False)]
+        outs = []
+        for wo in weights:
+            v = np.zeros(m)
+            for i, x in enumerate(xs):
+                for s, w in zip(steps, wo[i]):
+                    self.count["pmul"] += 1
+                    v = v + np.roll(x.v, -s) * w
+            outs.append(SV(v, xs[0].used, True))
+        return outs
+
     def add(self, x, y):
         assert x.used == y.used and x.pending_rescale == y.pending_rescale, "level mismatch"
         return SV(x.v + y.v, x.used, x.pending_rescale)

@@ -92,3 +92,38 @@ def test_keyswitch_relation(he):
     diff = he.intt(he.sub(lhs, rhs, q), q, he.qpsi)[0]
     c = np.where(diff > q[0] // 2, diff.astype(np.float64) - q[0], diff.astype(np.float64))
     assert np.abs(c).max() < 2.0 ** 30   # small key-switching noise, x is uniform mod Q
+
+
+def test_moddown_absorbs_multiples_of_P(he_dnum):
+    """ModDown(A + P*x) = ModDown(A) + x exactly: the identity the hoisted linear
+    combination relies on to fold sigma(c0) into the Q u P accumulator."""
+    he = he_dnum
+    lp = 4
+    basis, psis = he.ext_basis(lp)
+    rng = np.random.default_rng(8)
+    A = np.stack([rng.integers(0, m, he.n, dtype=np.uint64) for m in basis])
+    x = np.stack([rng.integers(0, qi, he.n, dtype=np.uint64) for qi in he.q[:lp]])
+    Pq = np.array([[he.P_mod(qi)] * he.n for qi in he.q[:lp]], dtype=np.uint64)
+    Px = np.concatenate([he.mul(x, Pq, he.q[:lp]), np.zeros((he.K, he.n), dtype=np.uint64)])
+    lhs = he.moddown(he.add(A, Px, basis))
+    rhs = he.add(he.moddown(A), x, he.q[:lp])
+    assert np.array_equal(lhs, rhs)
+
+
+@pytest.mark.parametrize("which", ["he", "he_dnum"])
+def test_lincomb_decrypts_to_weighted_rotation_sum(request, which):
+    he = request.getfixturevalue(which)
+    M = he.n // 2
+    rng = np.random.default_rng(9)
+    steps = [0, 1, 5] if which == "he_dnum" else [0, 1, 7, -2]
+    zs = [rng.uniform(-1, 1, M) for _ in range(2)]
+    cts = [he.encrypt(z, 9100 + i) for i, z in enumerate(zs)]
+    w = [[[rng.uniform(-1, 1, M) for _ in steps] for _ in zs] for _ in range(2)]
+    enc = [[[he.encode_ext(v, he.scale, cts[0].lp) for v in wi] for wi in wo] for wo in w]
+    outs = he.lincomb(cts, steps, enc, he.scale)
+    for o in range(2):
+        want = sum(w[o][i][k] * np.roll(zs[i], -s) for i in range(2) for k, s in enumerate(steps))
+        got = he.decrypt(he.rescale(outs[o]))
+        assert np.abs(got - want).max() < 1e-5
+    plain = he.lincomb(cts[:1], steps, None)[0]
+    assert np.abs(he.decrypt(plain) - sum(np.roll(zs[0], -s) for s in steps)).max() < 1e-6
