@@ -41,8 +41,10 @@ __device__ __forceinline__ u64 red_signed(i64 v, const PrimeDev &P) {
 }
 
 // after the inverse FFT: untwist, scale, round, reduce into lp limbs
+// (limb l < lpq: data prime l; limb l >= lpq: special prime pbase + l - lpq)
 __device__ void encode_finish(const double *re, const double *im, u64 *out, u32 lp, int logn, double f,
-                              const double *__restrict__ tw, const PrimeDev *__restrict__ pd, int *err) {
+                              const double *__restrict__ tw, const PrimeDev *__restrict__ pd, int *err,
+                              u32 lpq = 0xffffffffu, u32 pbase = 0) {
     const u32 N = 1u << logn, M = N / 2;
     for (u32 k = threadIdx.x; k < M; k += blockDim.x) {
         const double tr = tw[2 * k], ti = -tw[2 * k + 1];
@@ -55,8 +57,9 @@ __device__ void encode_finish(const double *re, const double *im, u64 *out, u32 
         }
         const i64 ia = __double2ll_rn(a), ib = __double2ll_rn(b);
         for (u32 l = 0; l < lp; ++l) {
-            out[(size_t)l * N + k] = red_signed(ia, pd[l]);
-            out[(size_t)l * N + k + M] = red_signed(ib, pd[l]);
+            const PrimeDev &P = pd[l < lpq ? l : pbase + (l - lpq)];
+            out[(size_t)l * N + k] = red_signed(ia, P);
+            out[(size_t)l * N + k + M] = red_signed(ib, P);
         }
     }
 }
@@ -89,7 +92,8 @@ __global__ void __launch_bounds__(1024) encode_sparse_kernel(u64 *out, const u32
                                                              u32 lp, int logn, double f, const double *__restrict__ fw,
                                                              const double *__restrict__ ft,
                                                              const u32 *__restrict__ pos_br,
-                                                             const PrimeDev *__restrict__ pd, int *err) {
+                                                             const PrimeDev *__restrict__ pd, int *err, u32 lpq,
+                                                             u32 pbase) {
     extern __shared__ double smd[];
     const u32 N = 1u << logn, M = N / 2;
     double *re = smd, *im = smd + M;
@@ -107,7 +111,7 @@ __global__ void __launch_bounds__(1024) encode_sparse_kernel(u64 *out, const u32
     }
     __syncthreads();
     block_fft(re, im, logn - 1, fw, true);
-    encode_finish(re, im, out + (size_t)blockIdx.x * lp * N, lp, logn, f, ft, pd, err);
+    encode_finish(re, im, out + (size_t)blockIdx.x * lp * N, lp, logn, f, ft, pd, err, lpq, pbase);
 }
 
 // decode: coefficient-form limb q_0 of m (rows [v][N], residues) -> selected slots
@@ -214,11 +218,14 @@ void encode_dense(Ctx *c, u64 *out, const double *z, u32 nv, double scale, u32 l
     if (check) check_err(c);
 }
 
-// sparse slot vectors (host arrays, uploaded once under `key`), eval form out [nv][lp][N]
+// sparse slot vectors (host arrays), eval form out [nv][lp + ext][N]: limbs q_0..q_{lp-1},
+// then (ext = K) the special primes, i.e. the plaintext over Q_l u P.
 void encode_sparse(Ctx *c, u64 *out, const std::string &key, const std::vector<u32> &off,
                    const std::vector<u32> &pos, const std::vector<double> &val, u32 stride, u32 ns, double scale,
-                   u32 lp) {
+                   u32 lp, u32 ext) {
     const u32 M = c->N / 2;
+    const u32 lpq = lp;
+    lp += ext;
     u32 nv = (u32)off.size() - 1;
     std::vector<u64> h(off.size() / 2 + 1 + pos.size() / 2 + 1 + val.size() + 2, 0);
     size_t o_off = 0, o_pos = off.size() / 2 + 1, o_val = o_pos + pos.size() / 2 + 1;
@@ -234,9 +241,9 @@ void encode_sparse(Ctx *c, u64 *out, const std::string &key, const std::vector<u
     encode_sparse_kernel<<<nv, fft_threads(M), (size_t)M * 16, c->stream>>>(
         out, reinterpret_cast<const u32 *>(d + o_off), reinterpret_cast<const u32 *>(d + o_pos),
         reinterpret_cast<const double *>(d + o_val), stride, ns, lp, c->logn, f, c->fft_w, c->fft_t, c->slot_pos_br,
-        c->pdev, c->err_flag);
+        c->pdev, c->err_flag, lpq, c->L1);
     note_launch(c, "encode_sparse");
-    ntt_forward(c, out, rows_regular(nv * lp, lp, lp, 0));
+    ntt_forward(c, out, rows_regular(nv * lp, lp, lpq, c->L1));
     check_err(c);   // also keeps the host staging vector alive until the upload is done
 }
 

@@ -649,3 +649,58 @@ Cts ct_square(Ctx *c, const Cts &a) {
     ks_moddown(c, r.data(), acc.p, d.p, (size_t)3 * lp * N, 3, kl, 1, B, lp);
     return ct_rescale(c, r);
 }
+
+// Hoisted linear combination of rotations with one ModDown per output:
+//   Y_o = sum_i sum_s w[o][i][s] (.) Rot(X_i, steps[s])
+// X holds CH*B ciphertexts (channel-major).  pts: [O][S*CH][lp+K][N] plaintexts over
+// Q_l u P with t = s*CH + i, or nullptr for the plain sums Y_i = sum_s Rot(X_i, steps[s])
+// (one output per channel).  The weighted key-switch accumulators, with P*sigma(c0)
+// folded in, are summed over Q_l u P and ModDown runs once per output ciphertext.
+Cts ct_lincomb(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps, const u64 *pts, u32 O,
+               double pt_scale) {
+    const u32 N = c->N, lp = X.lp, E = lp + c->K, Bt = CH * B, S = (u32)steps.size();
+    if (X.B != Bt) throw HeError(HE_EINVAL, "lincomb: batch mismatch");
+    bool any_ks = false;
+    for (int s : steps)
+        if (c->galois_elt(s) != 1) {
+            require_key(c, s);
+            any_ks = true;
+        }
+    DBuf D;
+    if (any_ks) {
+        D = DBuf(c, (size_t)Bt * ks_digits(c, lp) * E * N);
+        ks_modup(c, D.p, X.data() + (size_t)lp * N, (size_t)2 * lp * N, Bt, lp);
+    }
+    const u32 nout = pts ? O : CH;   // outputs, each a batch of B ciphertexts
+    const size_t zw = (size_t)B * 2 * E * N;    // one output batch over Q u P
+    DBuf Z(c, (size_t)nout * zw);
+    // steps per chunk: bounded by the key list and by ~4 GB of accumulators
+    const size_t per_step = (size_t)Bt * 2 * E * N * 8;
+    size_t chunk = ((size_t)4 << 30) / (per_step ? per_step : 1);
+    chunk = std::max<size_t>(1, std::min<size_t>(chunk, KEYLIST_MAX));
+    DBuf acc(c, std::min<size_t>(chunk, S) * Bt * 2 * E * N);
+    for (u32 s0 = 0; s0 < S; s0 += (u32)chunk) {
+        const u32 Sc = std::min<u32>((u32)chunk, S - s0);
+        KeyList kl;
+        for (u32 s = 0; s < Sc; ++s) {
+            u32 g = c->galois_elt(steps[s0 + s]);
+            kl.g[s] = g;
+            kl.key[s] = g == 1 ? nullptr : c->gk.at(g).p;
+        }
+        ks_lazy(c, acc.p, D.p, X.data(), kl, Sc, Bt, lp);
+        if (pts) {
+            // Z_o += sum_{t in chunk} pts[o][t] (.) acc[t], t = s*CH + i, blocks of B ciphertexts
+            mac(c, Z.p, zw, acc.p, zw, pts + (size_t)s0 * CH * E * N, O, Sc * CH, B, E, lp, c->L1, s0 > 0,
+                (size_t)S * CH * E * N);
+        } else {
+            // Z_i += sum_s acc[s][i]
+            sum_stack(c, Z.p, acc.p, (size_t)Bt * 2 * E * N, Sc, Bt * 2 * E, E, lp, c->L1, s0 > 0);
+        }
+    }
+    Cts out = cts_alloc(c, nout * B, lp, X.scale * (pts ? pt_scale : 1.0), X.lay);
+    KeyList none;
+    none.g[0] = 1;
+    none.key[0] = nullptr;
+    ks_moddown(c, out.data(), Z.p, nullptr, 0, 0, none, 1, nout * B, lp);
+    return out;
+}

@@ -84,6 +84,51 @@ __global__ void ks_inner_kernel(u64 *acc, const u64 *__restrict__ D, KeyList kl,
     o[(size_t)E * N] = reduce128(a1.lo, a1.hi, P);
 }
 
+// Accumulators of a hoisted linear combination, before any ModDown:
+//   step with g != 1: A0 = sum_j sigma_g(D_j) (o) ksk_j,0 + P*sigma_g(c0)   (P*x is 0 on special limbs)
+//                     A1 = sum_j sigma_g(D_j) (o) ksk_j,1
+//   step with g == 1: A = (P*c0, P*c1)
+// acc [S][B][2][lp+K][N]; x: the input ciphertexts [B][2][lp][N]; pq: [P]_{q_t} and Shoup pairs.
+__global__ void ks_lazy_kernel(u64 *acc, const u64 *__restrict__ D, const u64 *__restrict__ x, KeyList kl,
+                               u32 B, u32 beta, u32 lp, u32 K, u32 L1, int logn, const u64 *__restrict__ pq,
+                               const PrimeDev *__restrict__ pd) {
+    const u32 N = 1u << logn;
+    const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const u32 t = blockIdx.y;
+    const u32 s = blockIdx.z / B, b = blockIdx.z % B;
+    const u32 E = lp + K;
+    const u32 pt = t < lp ? t : L1 + (t - lp);
+    const PrimeDev &P = pd[pt];
+    const u32 g = kl.g[s];
+    const u64 *xb = x + (size_t)b * 2 * lp * N;
+    u64 *o = acc + (((size_t)s * B + b) * 2 * E + t) * N + n;
+    if (g == 1) {
+        u64 r0 = 0, r1 = 0;
+        if (t < lp) {
+            r0 = mul_shoup(xb[(size_t)t * N + n], pq[2 * t], pq[2 * t + 1], P.q);
+            r1 = mul_shoup(xb[(size_t)(lp + t) * N + n], pq[2 * t], pq[2 * t + 1], P.q);
+        }
+        o[0] = r0;
+        o[(size_t)E * N] = r1;
+        return;
+    }
+    const u64 *key = kl.key[s];
+    const u32 src = galois_src(n, g, logn);
+    const size_t kstride = (size_t)(L1 + K) * N;
+    Acc128 a0 = {0, 0}, a1 = {0, 0};
+    const u64 *Db = D + ((size_t)b * beta * E + t) * N + src;
+    for (u32 j = 0; j < beta; ++j) {
+        const u64 d = Db[(size_t)j * E * N];
+        const u64 *kj = key + (size_t)j * 2 * kstride + (size_t)pt * N + n;
+        mac128(a0, d, __ldg(kj));
+        mac128(a1, d, __ldg(kj + kstride));
+    }
+    if (t < lp) mac128(a0, xb[(size_t)t * N + src], pq[2 * t]);
+    o[0] = reduce128(a0.lo, a0.hi, P);
+    o[(size_t)E * N] = reduce128(a1.lo, a1.hi, P);
+}
+
 __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, const u64 *__restrict__ acc,
                                                        const u64 *__restrict__ addend, size_t addend_bstride,
                                                        u32 add_mask, KeyList kl, u32 B, u32 lp, u32 K, u32 L1,
@@ -294,6 +339,33 @@ void ks_inner(Ctx *c, u64 *acc, const u64 *D, const KeyList &kl, u32 S, u32 B, u
         // digits read once, each step's key read once, accumulators written once
         note_launch(c, "ks_inner", 8.0 * N * ((double)B * beta * E + (double)S * 2 * beta * E + (double)S * B * 2 * E));
     }
+}
+
+// [P]_{q_t} with Shoup companions for the data primes
+static const u64 *pmod_table(Ctx *c) {
+    std::string key = "Pq";
+    auto it = c->cache.find(key);
+    if (it != c->cache.end()) return it->second.p;
+    std::vector<u64> h(2 * c->L1);
+    for (u32 t = 0; t < c->L1; ++t) {
+        u64 q = c->primes[t], v = 1;
+        for (u32 k = 0; k < c->K; ++k) v = mulmod_h(v, c->primes[c->L1 + k] % q, q);
+        h[2 * t] = v;
+        h[2 * t + 1] = shoup_h(v, q);
+    }
+    return c->const_table(key, h);
+}
+
+// acc [S][B][2][lp+K][N]: lazy key-switch accumulators of the steps in kl (key nullptr, g = 1: identity)
+void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u32 S, u32 B, u32 lp) {
+    const u32 N = c->N, E = lp + c->K;
+    const u32 beta = ks_digits(c, lp);
+    dim3 grid((N + 255) / 256, E, S * B);
+    prof_begin(c);
+    ks_lazy_kernel<<<grid, 256, 0, c->stream>>>(acc, D, x, kl, B, beta, lp, c->K, c->L1, c->logn, pmod_table(c),
+                                                 c->pdev);
+    note_launch(c, "ks_lazy", 8.0 * N * ((double)B * beta * E + (double)S * 2 * beta * E + (double)B * 2 * lp +
+                                         (double)S * B * 2 * E));
 }
 
 // out [S][B][2][lp][N] = ModDown(acc) (+ addend: poly k of ct b gathered by sigma_{g_s} when add_mask bit k)

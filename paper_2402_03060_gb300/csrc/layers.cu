@@ -40,7 +40,7 @@ static std::vector<u32> valid_positions(const Layout &L, u32 Hout, u32 Wout, u32
 // encoded plaintexts for nv sparse slot vectors at level lp / scale; cached under key
 static const u64 *get_pts(Ctx *c, PtCache *pc, const std::string &key, std::vector<DBuf> &tmp, const Layout &L,
                           const std::vector<u32> &off, const std::vector<u32> &pos, const std::vector<double> &val,
-                          double scale, u32 lp) {
+                          double scale, u32 lp, u32 ext = 0) {
     if (pc) {
         auto it = pc->pts.find(key);
         if (it != pc->pts.end()) return it->second.p;
@@ -48,9 +48,9 @@ static const u64 *get_pts(Ctx *c, PtCache *pc, const std::string &key, std::vect
     u32 nv = (u32)off.size() - 1;
     Pool *saved = c->active;
     if (pc) c->active = nullptr;   // cached plaintexts live in the context pool
-    DBuf out(c, (size_t)nv * lp * c->N);
+    DBuf out(c, (size_t)nv * (lp + ext) * c->N);
     c->active = saved;
-    encode_sparse(c, out.p, key, off, pos, val, L.stride, L.n_samples, scale, lp);
+    encode_sparse(c, out.p, key, off, pos, val, L.stride, L.n_samples, scale, lp, ext);
     u64 *p = out.p;
     if (pc)
         pc->pts.emplace(key, std::move(out));
@@ -86,12 +86,38 @@ static Feat layer_conv(Ctx *c, const Feat &in, const LayerSpec &sp, u32 kh, u32 
     std::vector<int> steps;
     for (u32 j = 0; j < kh; ++j)
         for (u32 k = 0; k < kw; ++k) steps.push_back((int)(L.I * (k + L.W_img * j)));
-    // rotated inputs R[off][ch*B + b]  (T index = off*ci + ch)
     const size_t ctw = cts_ct_words(c, lp);
-    Cts R = cts_alloc(c, KK * ci * B, lp, in.x.scale, L);
+    std::vector<u32> vpos = valid_positions(L, Hout, Wout, Iout);
+    const u32 T = KK * ci;
+    std::vector<DBuf> tmp;
+    // plaintexts pt[o][off*ci + i]: the weight (times the pending factor) at every valid output slot
+    auto weight_pts = [&](u32 ext) {
+        std::vector<u32> off, pos;
+        std::vector<double> val;
+        const std::string k = key + (ext ? ":wx" : ":w");
+        if (!pc || !pc->pts.count(k)) {
+            off.push_back(0);
+            for (u32 o = 0; o < co; ++o)
+                for (u32 t = 0; t < T; ++t) {
+                    u32 kk = t / ci, i = t % ci, j = kk / kw, k2 = kk % kw;
+                    double wv = sp.w[(((size_t)o * ci + i) * kh + j) * kw + k2] * L.pending;
+                    for (u32 p : vpos) {
+                        pos.push_back(p);
+                        val.push_back(wv);
+                    }
+                    off.push_back((u32)pos.size());
+                }
+        }
+        return get_pts(c, pc, k, tmp, L, off, pos, val, c->scale, lp, ext);
+    };
+    Cts acc;
     if (!incremental) {
-        ct_rotate_hoisted_into(c, in.x, steps, R.data());
+        // one hoisted linear combination per output channel, one ModDown each
+        const u64 *pts = weight_pts(c->K);
+        acc = ct_lincomb(c, in.x, ci, B, steps, pts, co, c->scale);
     } else {
+        // rotated inputs R[off][ch*B + b]  (T index = off*ci + ch)
+        Cts R = cts_alloc(c, KK * ci * B, lp, in.x.scale, L);
         CUDA_TRY(cudaMemcpyAsync(R.data(), in.x.data(), (size_t)ci * B * ctw * 8, cudaMemcpyDeviceToDevice,
                                  c->stream));
         for (u32 t = 1; t < KK; ++t) {
@@ -102,33 +128,11 @@ static Feat layer_conv(Ctx *c, const Feat &in, const LayerSpec &sp, u32 kh, u32 
             CUDA_TRY(cudaMemcpyAsync(R.data() + (size_t)t * ci * B * ctw, r.data(), (size_t)ci * B * ctw * 8,
                                      cudaMemcpyDeviceToDevice, c->stream));
         }
+        const u64 *pts = weight_pts(0);
+        acc = cts_alloc(c, co * B, lp, in.x.scale * c->scale, L);
+        // R[off][i*B + b] is block t = off*ci + i of B ciphertexts
+        mac(c, acc.data(), (size_t)B * ctw, R.data(), (size_t)B * ctw, pts, co, T, B, lp);
     }
-    // plaintexts pt[o][off*ci + i]
-    std::vector<u32> vpos = valid_positions(L, Hout, Wout, Iout);
-    const u32 T = KK * ci;
-    std::vector<DBuf> tmp;
-    const u64 *pts;
-    {
-        std::vector<u32> off, pos;
-        std::vector<double> val;
-        if (!pc || !pc->pts.count(key + ":w")) {
-            off.push_back(0);
-            for (u32 o = 0; o < co; ++o)
-                for (u32 t = 0; t < T; ++t) {
-                    u32 kk = t / ci, i = t % ci, j = kk / kw, k = kk % kw;
-                    double wv = sp.w[(((size_t)o * ci + i) * kh + j) * kw + k] * L.pending;
-                    for (u32 p : vpos) {
-                        pos.push_back(p);
-                        val.push_back(wv);
-                    }
-                    off.push_back((u32)pos.size());
-                }
-        }
-        pts = get_pts(c, pc, key + ":w", tmp, L, off, pos, val, c->scale, lp);
-    }
-    Cts acc = cts_alloc(c, co * B, lp, in.x.scale * c->scale, L);
-    // R[off][i*B + b] is block t = off*ci + i of B ciphertexts
-    mac(c, acc.data(), (size_t)B * ctw, R.data(), (size_t)B * ctw, pts, co, T, B, lp);
     Cts out = ct_rescale(c, acc);
     {
         std::vector<u32> off, pos;
@@ -169,9 +173,7 @@ static Feat layer_avgpool(Ctx *c, const Feat &in, u32 cc) {
     for (u32 j = 0; j < ch; ++j)
         for (u32 k = 0; k < cc; ++k) steps.push_back((int)(L.I * (k + L.W_img * j)));
     const u32 Bt = in.CH * in.B;
-    Cts R = cts_alloc(c, (u32)steps.size() * Bt, in.x.lp, in.x.scale, L);
-    ct_rotate_hoisted_into(c, in.x, steps, R.data());
-    Cts out = stack_sum(c, R, (u32)steps.size(), Bt);
+    Cts out = ct_lincomb(c, in.x, 1, Bt, steps, nullptr, 0, 1.0);
     Layout L2 = L;
     L2.W = L.W / cc;
     L2.H = L.dims == 2 ? L.H / cc : 1;
@@ -235,9 +237,7 @@ static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string
         if (I > 1 && W > 1) {
             std::vector<int> st;
             for (u32 m = 0; m < I; ++m) st.push_back((int)(m * (I - 1)));
-            Cts R = cts_alloc(c, I * cur.B, cur.lp, cur.scale, L);
-            ct_rotate_hoisted_into(c, cur, st, R.data());
-            Cts y = stack_sum(c, R, I, cur.B);
+            Cts y = ct_lincomb(c, cur, 1, cur.B, st, nullptr, 0, 1.0);
             Cts acc;
             bool have = false;
             for (u32 u = 0; u < (W + I - 1) / I; ++u) {
@@ -314,7 +314,7 @@ static Feat layer_fc(Ctx *c, const Feat &in, const LayerSpec &sp, PtCache *pc, c
     {
         std::vector<u32> off, pos;
         std::vector<double> val;
-        if (!pc || !pc->pts.count(key + ":w")) {
+        if (!pc || !pc->pts.count(key + ":wx")) {
             // M_rot[o][t] = M_pad[t mod dout][(t + o) mod Wv] (times the pending factor)
             auto mrot = [&](u32 o, u32 t) -> double {
                 u32 row = t % dout, col = (t + o) % Wv;
@@ -338,19 +338,18 @@ static Feat layer_fc(Ctx *c, const Feat &in, const LayerSpec &sp, PtCache *pc, c
                 off.push_back((u32)pos.size());
             }
         }
-        pts = get_pts(c, pc, key + ":w", tmp, L, off, pos, val, c->scale, lp);
+        pts = get_pts(c, pc, key + ":wx", tmp, L, off, pos, val, c->scale, lp, c->K);
     }
-    Cts R = cts_alloc(c, T * B, lp, in.x.scale, L);
-    ct_rotate_hoisted_into(c, in.x, steps, R.data());
-    Cts acc = cts_alloc(c, B, lp, in.x.scale * c->scale, L);
-    mac(c, acc.data(), (size_t)B * ctw, R.data(), (size_t)B * ctw, pts, 1, T, B, lp);
+    (void)T;
+    (void)ctw;
+    // C_sum: every rotation of the input with its V1 / V2 vector, one ModDown
+    Cts acc = ct_lincomb(c, in.x, 1, B, steps, pts, 1, c->scale);
     Cts cs = ct_rescale(c, acc);
+    // C_out = sum_i Rot(C_sum, i * dout), one ModDown
     const u32 nsum = Wv / dout;
     std::vector<int> st2;
     for (u32 i = 0; i < nsum; ++i) st2.push_back((int)(i * dout));
-    Cts R2 = cts_alloc(c, nsum * B, cs.lp, cs.scale, L);
-    ct_rotate_hoisted_into(c, cs, st2, R2.data());
-    Cts out = stack_sum(c, R2, nsum, B);
+    Cts out = ct_lincomb(c, cs, 1, B, st2, nullptr, 0, 1.0);
     {
         std::vector<u32> off{0}, pos;
         std::vector<double> val;

@@ -28,7 +28,7 @@ void encode_init(Ctx *c);
 void encode_dense(Ctx *c, u64 *out, const double *z, u32 nv, double scale, u32 lp, bool check);
 void encode_sparse(Ctx *c, u64 *out, const std::string &key, const std::vector<u32> &off,
                    const std::vector<u32> &pos, const std::vector<double> &val, u32 stride, u32 ns, double scale,
-                   u32 lp);
+                   u32 lp, u32 ext = 0);
 void check_encode_errors(Ctx *c);
 void pack_samples(Ctx *c, double *z, const double *x, u32 nsamp, u32 spc, u32 stride, u32 len, u32 nct);
 void enc_combine(Ctx *c, u64 *ct, const u64 *u, const u64 *me, const u64 *e1, u32 lp, u32 B);
@@ -45,6 +45,8 @@ Cts ct_rotate(Ctx *c, const Cts &a, int step);
 std::vector<Cts> ct_rotate_hoisted(Ctx *c, const Cts &a, const std::vector<int> &steps);
 void ct_rotate_hoisted_into(Ctx *c, const Cts &a, const std::vector<int> &steps, u64 *out);
 Cts ct_square(Ctx *c, const Cts &a);
+Cts ct_lincomb(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps, const u64 *pts, u32 O,
+               double pt_scale);
 Cts ct_mul_pt(Ctx *c, const Cts &a, const u64 *pt, double pt_scale);
 void ct_add_pt_inplace(Ctx *c, Cts &a, const u64 *pt);
 void require_key(Ctx *c, int step);

@@ -210,7 +210,8 @@ void sample_uniform(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u3
 template <int OMAX>
 __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt,
                                                   u32 O, u32 T, u32 BK, u32 lp, u32 logn, size_t x_tstride,
-                                                  size_t out_ostride, u32 ntlog, u32 tc,
+                                                  size_t out_ostride, u32 ntlog, u32 tc, u32 lpq, u32 pbase,
+                                                  int accumulate, size_t pt_ostride,
                                                   const PrimeDev *__restrict__ pd) {
     extern __shared__ u64 ps[];   // [O][tc][NT]
     const u32 N = 1u << logn, NT = 1u << ntlog;
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
     const u32 n0 = blockIdx.y * NT;
     const u32 l = blockIdx.z;
     const bool active = bk < BK;
-    const PrimeDev P = pd[l];
+    const PrimeDev P = pd[l < lpq ? l : pbase + (l - lpq)];
     Acc128 acc[OMAX];
 #pragma unroll
     for (int o = 0; o < OMAX; ++o) acc[o].lo = acc[o].hi = 0;
@@ -233,7 +234,8 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
         for (u32 idx = tid; idx < O * tcc * NT; idx += blockDim.x) {
             const u32 j = idx & (NT - 1), r = idx >> ntlog;
             const u32 tt = r % tcc, o = r / tcc;
-            ps[((size_t)o * tc + tt) * NT + j] = pt[((size_t)o * T + t0 + tt) * pstride_t + (size_t)l * N + n0 + j];
+            ps[((size_t)o * tc + tt) * NT + j] =
+                pt[(size_t)o * pt_ostride + (size_t)(t0 + tt) * pstride_t + (size_t)l * N + n0 + j];
         }
         __syncthreads();
         if (active) {
@@ -256,12 +258,19 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
     if (!active) return;
 #pragma unroll
     for (int o = 0; o < OMAX; ++o)
-        if (o < (int)O) out[o * out_ostride + xoff] = reduce128(acc[o].lo, acc[o].hi, P);
+        if (o < (int)O) {
+            u64 *dst = out + o * out_ostride + xoff;
+            if (accumulate) mac128(acc[o], *dst, 1);
+            *dst = reduce128(acc[o].lo, acc[o].hi, P);
+        }
 }
 
 void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O, u32 T, u32 B,
-         u32 lp) {
-    // pt [O][T][lp][N]; x [T] blocks of [B][2][lp][N] at x_tstride; out [O] blocks at out_ostride
+         u32 lp, u32 lpq, u32 pbase, int accumulate, size_t pt_ostride) {
+    if (!pt_ostride) pt_ostride = (size_t)T * lp * c->N;
+    // pt [O][T][lp][N]; x [T] blocks of [B][2][lp][N] at x_tstride; out [O] blocks at out_ostride.
+    // Limb l < lpq uses data prime l, limb l >= lpq special prime pbase + l - lpq.
+    if (lpq == ~0u) lpq = lp;
     const u32 BK = 2 * B;
     u32 bkc = 1;
     while (bkc < BK && bkc < 64) bkc <<= 1;
@@ -276,12 +285,12 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
         if (tc > T) tc = T;
         const size_t smem = (size_t)oc * tc * NT * 8;
         dim3 grid((BK + bkc - 1) / bkc, c->N / NT, lp);
-        const u64 *ptc = pt + (size_t)o0 * T * lp * c->N;
+        const u64 *ptc = pt + (size_t)o0 * pt_ostride;
         u64 *outc = out + (size_t)o0 * out_ostride;
         prof_begin(c);
 #define MAC_LAUNCH(OM)                                                                                        \
     mac_kernel<OM><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride, out_ostride, \
-                                                   ntlog, tc, c->pdev)
+                                                   ntlog, tc, lpq, pbase, accumulate, pt_ostride, c->pdev)
         if (oc <= 1)
             MAC_LAUNCH(1);
         else if (oc <= 2)
@@ -318,4 +327,33 @@ void gather_rows(Ctx *c, u64 *out, const u64 *in, u32 nrows, size_t stride_rows)
     gather_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(out, in, nrows, stride_rows * c->N,
                                                                               c->logn);
     note_launch(c, "gather_rows");
+}
+
+// --------------------------------------------------------------- stack sum
+// out[r][n] = (accumulate ? out[r][n] : 0) + sum_s a[s][r][n], 128-bit lazy
+__global__ void sum_stack_kernel(u64 *out, const u64 *__restrict__ a, size_t stride_words, u32 S, u32 nrows,
+                                 u32 logn, u32 period, u32 lp, u32 pbase, int accumulate, const PrimeDev *pd) {
+    const u32 N = 1u << logn;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)nrows * N) return;
+    const u32 r = (u32)(idx >> logn);
+    const PrimeDev &P = pd[map_prime(r, period, lp, pbase)];
+    Acc128 acc = {accumulate ? out[idx] : 0, 0};
+    for (u32 s = 0; s < S; ++s) {
+        u64 v = a[s * stride_words + idx];
+        u64 lo = acc.lo + v;
+        acc.hi += lo < v;
+        acc.lo = lo;
+    }
+    out[idx] = reduce128(acc.lo, acc.hi, P);
+}
+
+void sum_stack(Ctx *c, u64 *out, const u64 *a, size_t stride_words, u32 S, u32 nrows, u32 period, u32 lp, u32 pbase,
+               int accumulate) {
+    size_t total = (size_t)nrows * c->N;
+    if (!total) return;
+    prof_begin(c);
+    sum_stack_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(out, a, stride_words, S, nrows, c->logn,
+                                                                            period, lp, pbase, accumulate, c->pdev);
+    note_launch(c, "sum_stack", 8.0 * total * (S + 1 + (accumulate ? 1 : 0)));
 }
