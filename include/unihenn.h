@@ -182,6 +182,24 @@ void he_model_free(he_model *m);
  * limbs data[n_limbs][N]; limb i uses prime prime_idx[i] (index into the
  * chain of he_context_primes).  Forward output is bit-reversed evaluation order. */
 he_status he_ntt(he_ctx *ctx, uint64_t *data, uint32_t n_limbs, const uint32_t *prime_idx, int inverse);
+/* Rescale that allocates no device memory.  The paper has no counterpart: this
+ * is a library service for callers that cannot allocate when they rescale --
+ * code inside a CUDA stream capture (an allocation breaks the capture),
+ * serving processes that reserve their whole memory budget up front and must
+ * not fail with out-of-memory mid-request, and hosts whose device memory is
+ * owned by another allocator.
+ * in: device [batch][2][limbs][N] evaluation-form ciphertexts (the he_ct
+ * layout); out: device [batch][2][limbs-1][N]; the result equals he_rescale's.
+ * Work is queued on the context's stream.  The only working memory is a
+ * file-scope device array of 2^19 words (4 MiB) held by every GPU that loads
+ * the library until the process exits: batch*2*N must not exceed 2^19 (16
+ * ciphertexts at N = 2^14), else HE_EINVAL.  The array is fully overwritten
+ * before use; calls share it, so calls that overlap on the GPU (other streams
+ * or contexts on the same device) race.  The first call on a device looks up
+ * the array's device address and sets kernel attributes: make that first call
+ * before any stream capture.  Errors: HE_EINVAL, HE_ELEVEL (limbs < 2), HE_ECUDA. */
+he_status he_rescale_noalloc(he_ctx *ctx, const uint64_t *in, uint64_t *out, uint32_t batch, uint32_t limbs);
+
 /* Block until the context's stream is idle. */
 he_status he_sync(he_ctx *ctx);
 /* Number of kernels this context has launched so far (a graph replay counts

@@ -74,6 +74,7 @@ SIGNATURES = {
     "he_infer": (_int, [_vp, _vp, _int, _pp]),
     "he_model_free": (None, [_vp]),
     "he_ntt": (_int, [_vp, _vp, _u32, ctypes.POINTER(_u32), _int]),
+    "he_rescale_noalloc": (_int, [_vp, _vp, _vp, _u32, _u32]),
     "he_sync": (_int, [_vp]),
     "he_kernel_launches": (_u64, [_vp]),
     "he_profile_begin": (_int, [_vp]),

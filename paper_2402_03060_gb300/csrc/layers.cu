@@ -540,12 +540,14 @@ struct he_ct {
     Cts x;
 };
 
-struct he_ctx {
-    std::shared_ptr<Ctx> c;
-};
-
 // ------------------------------------------------------------------ C ABI
 static thread_local std::string g_err;
+
+// lets entry points in other translation units report through he_last_error()
+const char *noalloc_set_error(const char *msg) {
+    g_err = msg;
+    return g_err.c_str();
+}
 
 template <class F>
 static he_status guard(F &&f) {

@@ -4,6 +4,11 @@
 #include "keyswitch.cuh"
 #include "ring.cuh"
 
+// the C handle of a context (shared by its ciphertext and model handles)
+struct he_ctx {
+    std::shared_ptr<Ctx> c;
+};
+
 // A ciphertext batch that may be a view into a larger buffer
 struct Cts {
     std::shared_ptr<DBuf> mem;
