@@ -139,6 +139,18 @@ u64 *Ctx::const_table(const std::string &key, const std::vector<u64> &host) {
     return p;
 }
 
+// g^{-1} mod 2N: the odd residues mod 2N form a group of order N, so g^{-1} = g^{N-1}
+u32 Ctx::galois_inverse(u32 g) const {
+    const u64 twoN = 2ull * N;
+    u64 r = 1, b = g, e = N - 1;
+    while (e) {
+        if (e & 1) r = r * b % twoN;
+        b = b * b % twoN;
+        e >>= 1;
+    }
+    return (u32)r;
+}
+
 u32 Ctx::galois_elt(int64_t step) const {
     const u64 M = N / 2, twoN = 2ull * N;
     u64 e = (u64)(((step % (int64_t)M) + (int64_t)M) % (int64_t)M);
@@ -354,6 +366,7 @@ void ctx_destroy(Ctx *c) {
     c->pk = DBuf();
     c->rlk = DBuf();
     c->gk.clear();
+    c->gkp.clear();
     c->cache.clear();
     c->pool.release_all();
     cudaFree(c->pdev);
@@ -445,6 +458,7 @@ void keygen(Ctx *c, const std::vector<int> &steps) {
     make_ksk(c, c->rlk.p, s2.p, 0);
     // Galois keys: s' = sigma_g(s)
     c->gk.clear();
+    c->gkp.clear();
     DBuf sg(c, (size_t)E * N);
     for (int st : steps) {
         u32 g = c->galois_elt(st);
@@ -452,7 +466,11 @@ void keygen(Ctx *c, const std::vector<int> &steps) {
         galois_permute(c, sg.p, c->sk.p, E, g);
         DBuf k(c, (size_t)c->dnum * 2 * E * N);
         make_ksk(c, k.p, sg.p, g);
+        // the same key with every limb permuted by sigma_g^{-1} (read coalesced by hoisted rotations)
+        DBuf kp(c, (size_t)c->dnum * 2 * E * N);
+        galois_permute(c, kp.p, k.p, c->dnum * 2 * E, c->galois_inverse(g));
         c->gk.emplace(g, std::move(k));
+        c->gkp.emplace(g, std::move(kp));
     }
     c->have_keys = true;
     CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -685,7 +703,9 @@ Cts ct_lincomb(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &step
         for (u32 s = 0; s < Sc; ++s) {
             u32 g = c->galois_elt(steps[s0 + s]);
             kl.g[s] = g;
+            kl.ginv[s] = c->galois_inverse(g);
             kl.key[s] = g == 1 ? nullptr : c->gk.at(g).p;
+            kl.keyp[s] = g == 1 ? nullptr : c->gkp.at(g).p;
         }
         ks_lazy(c, acc.p, D.p, X.data(), kl, Sc, Bt, lp);
         if (pts) {

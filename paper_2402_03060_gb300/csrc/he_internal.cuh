@@ -213,6 +213,7 @@ struct Ctx : std::enable_shared_from_this<Ctx> {
     DBuf pk;                       // [2][L1][N]
     DBuf rlk;                      // [dnum][2][L1+K][N]
     std::map<u32, DBuf> gk;        // Galois element -> key [dnum][2][L+1+K][N]
+    std::map<u32, DBuf> gkp;       // the same keys permuted by sigma_g^{-1}
     // per-level constant tables (host-built, device-resident)
     std::map<std::string, DBuf> cache;
     uint64_t launches = 0;
@@ -232,6 +233,7 @@ struct Ctx : std::enable_shared_from_this<Ctx> {
     u32 nprimes() const { return L1 + K; }
     u64 *tw_fwd(u32 p) const { return tw + (size_t)p * 4 * N; }
     u32 galois_elt(int64_t step) const;
+    u32 galois_inverse(u32 g) const;
     u64 *const_table(const std::string &key, const std::vector<u64> &host);
 };
 

@@ -129,6 +129,59 @@ __global__ void ks_lazy_kernel(u64 *acc, const u64 *__restrict__ D, const u64 *_
     o[(size_t)E * N] = reduce128(a1.lo, a1.hi, P);
 }
 
+// Same accumulators, computed with keys stored pre-permuted: K'_{g,j} = sigma_g^{-1}(K_{g,j}), so
+//   A_s = sigma_g(A'_s),  A'_s = sum_j D_j (o) K'_j  (+ P*c0 on poly 0),
+// i.e. every thread reads its digits D_j[b][t][n] and c0, c1 once (coalesced) and reuses them
+// for all S steps; the permutation is applied on the write: A_s[galois_src(n, g^-1)] = A'_s[n].
+// Grid: x = n-tile (fastest, so the scattered writes of one limb merge in L2), y = ciphertext, z = limb.
+__global__ void __launch_bounds__(256) ks_lazy_perm_kernel(u64 *acc, const u64 *__restrict__ D,
+                                                            const u64 *__restrict__ x, KeyList kl, u32 S, u32 B,
+                                                            u32 beta, u32 lp, u32 K, u32 L1, int logn,
+                                                            const u64 *__restrict__ pq,
+                                                            const PrimeDev *__restrict__ pd) {
+    const u32 N = 1u << logn;
+    const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const u32 b = blockIdx.y, t = blockIdx.z;
+    const u32 E = lp + K;
+    const u32 pt = t < lp ? t : L1 + (t - lp);
+    const PrimeDev P = pd[pt];
+    u64 d[MAX_ALPHA * 2];
+    const u64 *Db = D + ((size_t)b * beta * E + t) * N + n;
+#pragma unroll
+    for (u32 j = 0; j < MAX_ALPHA * 2; ++j)
+        if (j < beta) d[j] = Db[(size_t)j * E * N];
+    const u64 *xb = x + (size_t)b * 2 * lp * N;
+    u64 pc0 = 0, pc1 = 0;   // P*c0, P*c1 on data limbs
+    if (t < lp) {
+        pc0 = mul_shoup(xb[(size_t)t * N + n], pq[2 * t], pq[2 * t + 1], P.q);
+        pc1 = mul_shoup(xb[(size_t)(lp + t) * N + n], pq[2 * t], pq[2 * t + 1], P.q);
+    }
+    const size_t kstride = (size_t)(L1 + K) * N;
+    for (u32 s = 0; s < S; ++s) {
+        u64 *o = acc + (((size_t)s * B + b) * 2 * E + t) * N;
+        const u32 g = kl.g[s];
+        if (g == 1) {
+            o[n] = pc0;
+            o[(size_t)E * N + n] = pc1;
+            continue;
+        }
+        const u64 *key = kl.keyp[s] + (size_t)pt * N + n;
+        Acc128 a0 = {pc0, 0}, a1 = {0, 0};
+#pragma unroll
+        for (u32 j = 0; j < MAX_ALPHA * 2; ++j) {
+            if (j < beta) {
+                const u64 *kj = key + (size_t)j * 2 * kstride;
+                mac128(a0, d[j], __ldg(kj));
+                mac128(a1, d[j], __ldg(kj + kstride));
+            }
+        }
+        const u32 dst = galois_src(n, kl.ginv[s], logn);
+        o[dst] = reduce128(a0.lo, a0.hi, P);
+        o[(size_t)E * N + dst] = reduce128(a1.lo, a1.hi, P);
+    }
+}
+
 __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, const u64 *__restrict__ acc,
                                                        const u64 *__restrict__ addend, size_t addend_bstride,
                                                        u32 add_mask, KeyList kl, u32 B, u32 lp, u32 K, u32 L1,
@@ -360,10 +413,19 @@ static const u64 *pmod_table(Ctx *c) {
 void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u32 S, u32 B, u32 lp) {
     const u32 N = c->N, E = lp + c->K;
     const u32 beta = ks_digits(c, lp);
-    dim3 grid((N + 255) / 256, E, S * B);
+    bool perm = beta <= 2 * MAX_ALPHA && B <= 65535;
+    for (u32 s = 0; s < S; ++s)
+        if (kl.g[s] != 1 && !kl.keyp[s]) perm = false;
     prof_begin(c);
-    ks_lazy_kernel<<<grid, 256, 0, c->stream>>>(acc, D, x, kl, B, beta, lp, c->K, c->L1, c->logn, pmod_table(c),
-                                                 c->pdev);
+    if (perm) {
+        dim3 grid((N + 255) / 256, B, E);
+        ks_lazy_perm_kernel<<<grid, 256, 0, c->stream>>>(acc, D, x, kl, S, B, beta, lp, c->K, c->L1, c->logn,
+                                                          pmod_table(c), c->pdev);
+    } else {
+        dim3 grid((N + 255) / 256, E, S * B);
+        ks_lazy_kernel<<<grid, 256, 0, c->stream>>>(acc, D, x, kl, B, beta, lp, c->K, c->L1, c->logn, pmod_table(c),
+                                                     c->pdev);
+    }
     note_launch(c, "ks_lazy", 8.0 * N * ((double)B * beta * E + (double)S * 2 * beta * E + (double)B * 2 * lp +
                                          (double)S * B * 2 * E));
 }

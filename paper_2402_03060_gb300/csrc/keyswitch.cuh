@@ -5,10 +5,13 @@
 
 #define KEYLIST_MAX 64
 // Per rotation step s of one launch: the switching key [dnum][2][L+1+K][N] and
-// the Galois element applied to the ModUp'ed digits (1 = none).
+// the Galois element applied to the ModUp'ed digits (1 = none); for the
+// pre-permuted form, ginv is the inverse Galois element g^{-1} mod 2N.
 struct KeyList {
-    const u64 *key[KEYLIST_MAX];
+    const u64 *key[KEYLIST_MAX];    // K_{g,j}
+    const u64 *keyp[KEYLIST_MAX];   // K'_{g,j} = sigma_g^{-1}(K_{g,j}) (Galois keys only)
     u32 g[KEYLIST_MAX];
+    u32 ginv[KEYLIST_MAX];
 };
 
 void keyswitch_init(Ctx *c);

@@ -239,17 +239,26 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
         }
         __syncthreads();
         if (active) {
-            for (u32 tt = 0; tt < tcc; ++tt) {
-                const u64 xv = __ldcs(x + (size_t)(t0 + tt) * x_tstride + xoff);
+            for (u32 tt0 = 0; tt0 < tcc; tt0 += 4) {
+                // four streaming loads in flight before the products that need them
+                u64 xv[4];
 #pragma unroll
-                for (int o = 0; o < OMAX; ++o)
-                    if (o < (int)O) mac128(acc[o], ps[((size_t)o * tc + tt) * NT + nl], xv);
-                if (++cnt == 128) {
-                    cnt = 0;
+                for (int u = 0; u < 4; ++u)
+                    xv[u] = tt0 + u < tcc ? __ldcs(x + (size_t)(t0 + tt0 + u) * x_tstride + xoff) : 0;
 #pragma unroll
-                    for (int o = 0; o < OMAX; ++o) {
-                        acc[o].lo = reduce128(acc[o].lo, acc[o].hi, P);
-                        acc[o].hi = 0;
+                for (int u = 0; u < 4; ++u) {
+                    const u32 tt = tt0 + u;
+                    if (tt >= tcc) break;
+#pragma unroll
+                    for (int o = 0; o < OMAX; ++o)
+                        if (o < (int)O) mac128(acc[o], ps[((size_t)o * tc + tt) * NT + nl], xv[u]);
+                    if (++cnt == 128) {
+                        cnt = 0;
+#pragma unroll
+                        for (int o = 0; o < OMAX; ++o) {
+                            acc[o].lo = reduce128(acc[o].lo, acc[o].hi, P);
+                            acc[o].hi = 0;
+                        }
                     }
                 }
             }
@@ -278,8 +287,9 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
     while ((1u << ntlog) * bkc < 256) ++ntlog;
     if ((1u << ntlog) > c->N) throw HeError(HE_EINVAL, "mac: ring too small");
     const u32 NT = 1u << ntlog;
-    for (u32 o0 = 0; o0 < O; o0 += 16) {
-        const u32 oc = O - o0 < 16 ? O - o0 : 16;
+    // outputs in groups of at most 12 (the accumulators of a group live in registers)
+    for (u32 o0 = 0; o0 < O; o0 += 12) {
+        const u32 oc = O - o0 < 12 ? O - o0 : 12;
         u32 tc = 6144 / (oc * NT);
         if (tc < 1) tc = 1;
         if (tc > T) tc = T;
@@ -301,10 +311,8 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
             MAC_LAUNCH(6);
         else if (oc <= 8)
             MAC_LAUNCH(8);
-        else if (oc <= 12)
-            MAC_LAUNCH(12);
         else
-            MAC_LAUNCH(16);
+            MAC_LAUNCH(12);
 #undef MAC_LAUNCH
         note_launch(c, "mac", 8.0 * c->N * ((double)oc * T * lp + (double)T * B * 2 * lp + (double)oc * B * 2 * lp));
     }
