@@ -218,7 +218,18 @@ def run_ours(args, rank, world, local):
     ct = ctx.encrypt(x_dev, SPC, stride, seed)
     out = model.infer(ct, use_graph=False)
     ctx.decrypt(out, 10, out=logits_dev)
-    stats = ctx.profile_end()
+    tagged = ctx.profile_end()
+    # records are "layer/kernel" (or "kernel" outside the network): totals per kernel and per layer
+    stats, layer_ms = {}, {}
+    for key, (nl, ms, byt) in tagged.items():
+        layer, _, kern = key.rpartition("/")
+        s = stats.setdefault(kern, [0, 0.0, 0.0])
+        s[0] += nl
+        s[1] += ms
+        s[2] += byt
+        lk = layer or "encrypt/decrypt"
+        layer_ms[lk] = layer_ms.get(lk, 0.0) + ms
+    stats = {k: tuple(v) for k, v in stats.items()}
 
     # one-op-per-launch path: each ciphertext alone, eager
     plain = None
@@ -260,7 +271,8 @@ def run_ours(args, rank, world, local):
                 "peak_source": "measured" if pk else "fallback",
                 "kernels": {k: {"launches": v[0], "ms": round(v[1], 3),
                                 "GBps": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 else None}
-                            for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1])}}
+                            for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1])},
+                "layers_ms": {k: round(v, 3) for k, v in layer_ms.items()}}
     res = {
         "metric": METRIC, "value": round(total_samples / (ms_step / 1e3), 3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 3),

@@ -43,7 +43,7 @@ void note_launch(Ctx *c, const char *what, double bytes) {
     if (c->profiling && c->prof_start) {
         cudaEvent_t b = c->new_event();
         CUDA_TRY(cudaEventRecord(b, c->stream));
-        c->recs.push_back({what, bytes, c->prof_start, b});
+        c->recs.push_back({what, bytes, c->prof_start, b, c->prof_tag});
         c->prof_start = nullptr;
     }
 }

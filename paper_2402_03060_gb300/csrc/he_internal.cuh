@@ -222,8 +222,10 @@ struct Ctx : std::enable_shared_from_this<Ctx> {
         const char *name;
         double bytes;
         cudaEvent_t a, b;
+        std::string tag;
     };
     bool profiling = false;
+    std::string prof_tag;          // e.g. the layer being evaluated
     cudaEvent_t prof_start = nullptr;
     std::vector<cudaEvent_t> ev_free;
     std::vector<ProfRec> recs;

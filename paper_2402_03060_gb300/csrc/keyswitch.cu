@@ -134,7 +134,11 @@ __global__ void ks_lazy_kernel(u64 *acc, const u64 *__restrict__ D, const u64 *_
 // i.e. every thread reads its digits D_j[b][t][n] and c0, c1 once (coalesced) and reuses them
 // for all S steps; the permutation is applied on the write: A_s[galois_src(n, g^-1)] = A'_s[n].
 // Grid: x = n-tile (fastest, so the scattered writes of one limb merge in L2), y = ciphertext, z = limb.
-__global__ void __launch_bounds__(256) ks_lazy_perm_kernel(u64 *acc, const u64 *__restrict__ D,
+// Each thread handles LAZY_BT ciphertexts of one coefficient so that every key word it
+// loads serves LAZY_BT products.
+#define LAZY_BT 2
+#define LAZY_MAXD 8
+__global__ void __launch_bounds__(256, 2) ks_lazy_perm_kernel(u64 *acc, const u64 *__restrict__ D,
                                                             const u64 *__restrict__ x, KeyList kl, u32 S, u32 B,
                                                             u32 beta, u32 lp, u32 K, u32 L1, int logn,
                                                             const u64 *__restrict__ pq,
@@ -142,43 +146,59 @@ __global__ void __launch_bounds__(256) ks_lazy_perm_kernel(u64 *acc, const u64 *
     const u32 N = 1u << logn;
     const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const u32 b = blockIdx.y, t = blockIdx.z;
+    const u32 b0 = blockIdx.y * LAZY_BT, t = blockIdx.z;
     const u32 E = lp + K;
     const u32 pt = t < lp ? t : L1 + (t - lp);
     const PrimeDev P = pd[pt];
-    u64 d[MAX_ALPHA * 2];
-    const u64 *Db = D + ((size_t)b * beta * E + t) * N + n;
+    u64 d[LAZY_BT][LAZY_MAXD];
+    u64 pc0[LAZY_BT], pc1[LAZY_BT];   // P*c0, P*c1 on data limbs
 #pragma unroll
-    for (u32 j = 0; j < MAX_ALPHA * 2; ++j)
-        if (j < beta) d[j] = Db[(size_t)j * E * N];
-    const u64 *xb = x + (size_t)b * 2 * lp * N;
-    u64 pc0 = 0, pc1 = 0;   // P*c0, P*c1 on data limbs
-    if (t < lp) {
-        pc0 = mul_shoup(xb[(size_t)t * N + n], pq[2 * t], pq[2 * t + 1], P.q);
-        pc1 = mul_shoup(xb[(size_t)(lp + t) * N + n], pq[2 * t], pq[2 * t + 1], P.q);
+    for (int u = 0; u < LAZY_BT; ++u) {
+        const u32 b = b0 + u < B ? b0 + u : B - 1;   // clamp: duplicates are computed but not stored
+        const u64 *Db = D + ((size_t)b * beta * E + t) * N + n;
+#pragma unroll
+        for (u32 j = 0; j < LAZY_MAXD; ++j) d[u][j] = j < beta ? Db[(size_t)j * E * N] : 0;
+        const u64 *xb = x + (size_t)b * 2 * lp * N;
+        pc0[u] = pc1[u] = 0;
+        if (t < lp) {
+            pc0[u] = mul_shoup(xb[(size_t)t * N + n], pq[2 * t], pq[2 * t + 1], P.q);
+            pc1[u] = mul_shoup(xb[(size_t)(lp + t) * N + n], pq[2 * t], pq[2 * t + 1], P.q);
+        }
     }
     const size_t kstride = (size_t)(L1 + K) * N;
     for (u32 s = 0; s < S; ++s) {
-        u64 *o = acc + (((size_t)s * B + b) * 2 * E + t) * N;
         const u32 g = kl.g[s];
-        if (g == 1) {
-            o[n] = pc0;
-            o[(size_t)E * N + n] = pc1;
-            continue;
-        }
-        const u64 *key = kl.keyp[s] + (size_t)pt * N + n;
-        Acc128 a0 = {pc0, 0}, a1 = {0, 0};
+        u32 dst = n;
+        u64 k0[LAZY_MAXD], k1[LAZY_MAXD];
+        if (g != 1) {
+            const u64 *key = kl.keyp[s] + (size_t)pt * N + n;
 #pragma unroll
-        for (u32 j = 0; j < MAX_ALPHA * 2; ++j) {
-            if (j < beta) {
-                const u64 *kj = key + (size_t)j * 2 * kstride;
-                mac128(a0, d[j], __ldg(kj));
-                mac128(a1, d[j], __ldg(kj + kstride));
+            for (u32 j = 0; j < LAZY_MAXD; ++j) {
+                k0[j] = j < beta ? __ldg(key + (size_t)j * 2 * kstride) : 0;
+                k1[j] = j < beta ? __ldg(key + (size_t)j * 2 * kstride + kstride) : 0;
             }
+            dst = galois_src(n, kl.ginv[s], logn);
         }
-        const u32 dst = galois_src(n, kl.ginv[s], logn);
-        o[dst] = reduce128(a0.lo, a0.hi, P);
-        o[(size_t)E * N + dst] = reduce128(a1.lo, a1.hi, P);
+#pragma unroll
+        for (int u = 0; u < LAZY_BT; ++u) {
+            if (b0 + u >= B) break;
+            u64 *o = acc + (((size_t)s * B + b0 + u) * 2 * E + t) * N;
+            if (g == 1) {
+                o[n] = pc0[u];
+                o[(size_t)E * N + n] = pc1[u];
+                continue;
+            }
+            Acc128 a0 = {pc0[u], 0}, a1 = {0, 0};
+#pragma unroll
+            for (u32 j = 0; j < LAZY_MAXD; ++j) {
+                if (j < beta) {
+                    mac128(a0, d[u][j], k0[j]);
+                    mac128(a1, d[u][j], k1[j]);
+                }
+            }
+            o[dst] = reduce128(a0.lo, a0.hi, P);
+            o[(size_t)E * N + dst] = reduce128(a1.lo, a1.hi, P);
+        }
     }
 }
 
@@ -413,12 +433,12 @@ static const u64 *pmod_table(Ctx *c) {
 void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u32 S, u32 B, u32 lp) {
     const u32 N = c->N, E = lp + c->K;
     const u32 beta = ks_digits(c, lp);
-    bool perm = beta <= 2 * MAX_ALPHA && B <= 65535;
+    bool perm = beta <= LAZY_MAXD && (B + LAZY_BT - 1) / LAZY_BT <= 65535;
     for (u32 s = 0; s < S; ++s)
         if (kl.g[s] != 1 && !kl.keyp[s]) perm = false;
     prof_begin(c);
     if (perm) {
-        dim3 grid((N + 255) / 256, B, E);
+        dim3 grid((N + 255) / 256, (B + LAZY_BT - 1) / LAZY_BT, E);
         ks_lazy_perm_kernel<<<grid, 256, 0, c->stream>>>(acc, D, x, kl, S, B, beta, lp, c->K, c->L1, c->logn,
                                                           pmod_table(c), c->pdev);
     } else {

@@ -486,9 +486,11 @@ static std::vector<LayerSpec> copy_layers(const he_layer *layers, size_t n, u32 
 }
 
 static Feat run_layers(Ctx *c, Feat f, const std::vector<LayerSpec> &ls, PtCache *pc) {
+    static const char *opname[] = {"?", "conv2d", "conv1d", "square", "avgpool", "flatten", "fc"};
     for (size_t i = 0; i < ls.size(); ++i) {
         const LayerSpec &s = ls[i];
         std::string key = fmt("L%zu", i);
+        c->prof_tag = fmt("%zu%s", i, opname[s.op <= HE_FC ? s.op : 0]);
         switch (s.op) {
             case HE_CONV2D: f = layer_conv(c, f, s, s.k, s.k, false, pc, key); break;
             case HE_CONV1D: f = layer_conv(c, f, s, 1, s.k, false, pc, key); break;
@@ -501,6 +503,7 @@ static Feat run_layers(Ctx *c, Feat f, const std::vector<LayerSpec> &ls, PtCache
                 break;
         }
     }
+    c->prof_tag.clear();
     return f;
 }
 
@@ -1019,13 +1022,14 @@ he_status he_profile_end(he_ctx *h, he_kernel_stat *out, size_t cap, size_t *n) 
         for (auto &r : c->recs) {
             float ms = 0;
             CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
-            auto it = agg.find(r.name);
+            const std::string key = r.tag.empty() ? std::string(r.name) : r.tag + "/" + r.name;
+            auto it = agg.find(key);
             if (it == agg.end()) {
                 he_kernel_stat s;
                 memset(&s, 0, sizeof s);
-                strncpy(s.name, r.name, sizeof s.name - 1);
-                it = agg.emplace(r.name, s).first;
-                order.push_back(r.name);
+                strncpy(s.name, key.c_str(), sizeof s.name - 1);
+                it = agg.emplace(key, s).first;
+                order.push_back(key);
             }
             it->second.launches++;
             it->second.total_ms += ms;
