@@ -572,6 +572,39 @@ class Ckks:
             outs.append(Ct(np.stack([self.moddown(z0), self.moddown(z1)]), cts[0].scale * pt_scale))
         return outs
 
+    def lincomb_diag(self, cts, steps) -> Ct:
+        """sum_i Rot(ct_i, steps[i]) with one ModDown: each input contributes the
+        accumulator A_i of its own step (as in ``lincomb``), the A_i are added over
+        Q_l u P and ModDown is applied once."""
+        lp = cts[0].lp
+        basis, _ = self.ext_basis(lp)
+        E = lp + self.K
+        z0 = np.zeros((E, self.n), dtype=np.uint64)
+        z1 = np.zeros_like(z0)
+        for ct, r in zip(cts, steps):
+            assert ct.lp == lp and ct.scale == cts[0].scale
+            # a one-step combination with no weights gives exactly the accumulator pair
+            a0, a1 = self._lazy_acc(ct, r)
+            z0 = self.add(z0, a0, basis)
+            z1 = self.add(z1, a1, basis)
+        return Ct(np.stack([self.moddown(z0), self.moddown(z1)]), cts[0].scale)
+
+    def _lazy_acc(self, ct: Ct, r: int, digs=None):
+        """The Q_l u P accumulator pair of Rot(ct, r) before ModDown (see ``lincomb``)."""
+        lp = ct.lp
+        q = self.q[:lp]
+        zero_p = np.zeros((self.K, self.n), dtype=np.uint64)
+        Pq = np.repeat(np.array([self.P_mod(qi) for qi in q], dtype=np.uint64)[:, None], self.n, axis=1)
+        g = galois_elt(r, self.logn)
+        if g == 1:
+            return (np.concatenate([self.mul(ct.d[0], Pq, q), zero_p]),
+                    np.concatenate([self.mul(ct.d[1], Pq, q), zero_p]))
+        if digs is None:
+            digs = self.modup(ct.d[1])
+        a0, a1 = self.ks_inner(digs, self.keys.gk[g], g)
+        c0g = self.automorph_eval(ct.d[0], g)
+        return np.concatenate([self.add(a0[:lp], self.mul(c0g, Pq, q), q), a0[lp:]]), a1
+
     def square(self, ct: Ct) -> Ct:
         """Ciphertext tensor with itself, relinearisation, rescale (reading C15)."""
         q = self.q[: ct.lp]

@@ -162,57 +162,48 @@ def flatten(be, xs, lay: Layout):
     Then, when H > 1 (IV-E-3): per row r a mask of the row, rescale, rotate
     left r*(W_img*I - W), sum.  Finally (IV-E-4) channel o is rotated right by
     o*W*H and the channels are added.  Readings C12.
+
+    Each mask-rotate-sum stage sum_k Rot(m_k (.) x, r_k) is evaluated as the
+    single hoisted combination sum_k Rot(m_k, r_k) (.) Rot(x, r_k) (the same
+    slot algebra: Rot is elementwise-multiplicative), followed by one rescale;
+    the channel packing is one combination of the per-channel rotations.
     """
     I, W, H, Wi = lay.I, lay.W, lay.H, lay.W_img
     rows = range(H)
     cur = list(xs)
     pending = lay.pending
+
+    def masked_rotation_sum(x, masks, steps):
+        rolled = [np.roll(m, -s) for m, s in zip(masks, steps)]
+        return be.rescale(be.lincomb([x], steps, [[rolled]])[0])
+
     if lay.prev == "avgpool":
-        new = []
-        for x in cur:
-            acc = None
-            for c in range(W):
-                pos = [I * (r * Wi + c) for r in rows]
-                t = be.rescale(be.mul_mask(x, slot_vector(lay, pos, pending)))
-                if c:
-                    t = be.rot(t, c * (I - 1))
-                acc = t if acc is None else be.add(acc, t)
-            new.append(acc)
-        cur, pending = new, 1.0
+        steps = [c * (I - 1) for c in range(W)]
+        masks = [slot_vector(lay, [I * (r * Wi + c) for r in rows], pending) for c in range(W)]
+        cur = [masked_rotation_sum(x, masks, steps) for x in cur]
+        pending = 1.0
     elif lay.prev == "conv":
         assert pending == 1.0
         if I > 1 and W > 1:
+            nblk = -(-W // I)
+            steps = [u * I * (I - 1) for u in range(nblk)]
+            masks = []
+            for u in range(nblk):
+                cols = range(I * u, min(I * u + I, W))
+                masks.append(slot_vector(lay, [I * r * Wi + I * I * u + (cc - I * u) for r in rows for cc in cols],
+                                         1.0))
             new = []
             for x in cur:
                 y = be.lincomb([x], [m * (I - 1) for m in range(I)], None)[0]
-                acc = None
-                for u in range(-(-W // I)):
-                    cols = range(I * u, min(I * u + I, W))
-                    pos = [I * r * Wi + I * I * u + (cc - I * u) for r in rows for cc in cols]
-                    t = be.rescale(be.mul_mask(y, slot_vector(lay, pos, 1.0)))
-                    if u:
-                        t = be.rot(t, u * I * (I - 1))
-                    acc = t if acc is None else be.add(acc, t)
-                new.append(acc)
+                new.append(masked_rotation_sum(y, masks, steps))
             cur = new
     else:
         raise ValueError("flatten must follow a convolution or an average pooling")
     if H > 1:
-        new = []
-        for x in cur:
-            acc = None
-            for r in rows:
-                pos = [I * r * Wi + c for c in range(W)]
-                t = be.rescale(be.mul_mask(x, slot_vector(lay, pos, 1.0)))
-                if r:
-                    t = be.rot(t, r * (Wi * I - W))
-                acc = t if acc is None else be.add(acc, t)
-            new.append(acc)
-        cur = new
-    acc = None
-    for o, x in enumerate(cur):
-        t = be.rot(x, -o * W * H) if o else x
-        acc = t if acc is None else be.add(acc, t)
+        steps = [r * (Wi * I - W) for r in rows]
+        masks = [slot_vector(lay, [I * r * Wi + c for c in range(W)], 1.0) for r in rows]
+        cur = [masked_rotation_sum(x, masks, steps) for x in cur]
+    acc = be.lincomb_diag(cur, [-o * W * H for o in range(len(cur))]) if len(cur) > 1 else cur[0]
     D = len(xs) * W * H
     return [acc], replace(lay, pending=pending, prev="flatten", D=D, W=D, H=1, I=1)
 
@@ -359,6 +350,11 @@ class HeBackend:
     def rot_many(self, x, steps):
         self.count["rot"] += len({s for s in steps if s % (self.he.n // 2)})
         return self.he.rotate_hoisted(x, steps)
+
+    def lincomb_diag(self, xs, steps):
+        m = self.he.n // 2
+        self.count["rot"] += len([s for s in steps if s % m])
+        return self.he.lincomb_diag(xs, steps)
 
     def lincomb(self, xs, steps, weights):
         m = self.he.n // 2

@@ -37,6 +37,13 @@ class SlotSim:
         self.count["rot"] += len({s for s in steps if s % len(x.v)})
         return {s: SV(np.roll(x.v, -s), x.used, x.pending_rescale) for s in steps}
 
+    def lincomb_diag(self, xs, steps):
+        m = len(xs[0].v)
+        self.count["rot"] += len([s for s in steps if s % m])
+        for x in xs[1:]:
+            assert x.used == xs[0].used and not x.pending_rescale
+        return SV(sum(np.roll(x.v, -s) for x, s in zip(xs, steps)), xs[0].used, False)
+
     def lincomb(self, xs, steps, weights):
         m = len(xs[0].v)
         self.count["rot"] += len(xs) * len({s % m for s in steps if s % m})

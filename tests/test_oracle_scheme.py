@@ -127,3 +127,14 @@ def test_lincomb_decrypts_to_weighted_rotation_sum(request, which):
         assert np.abs(got - want).max() < 1e-5
     plain = he.lincomb(cts[:1], steps, None)[0]
     assert np.abs(he.decrypt(plain) - sum(np.roll(zs[0], -s) for s in steps)).max() < 1e-6
+
+
+def test_lincomb_diag_decrypts_to_sum_of_rotations(he):
+    M = he.n // 2
+    rng = np.random.default_rng(10)
+    zs = [rng.uniform(-1, 1, M) for _ in range(3)]
+    cts = [he.encrypt(z, 9200 + i) for i, z in enumerate(zs)]
+    steps = [0, -2, 7]
+    out = he.lincomb_diag(cts, steps)
+    want = sum(np.roll(z, -s) for z, s in zip(zs, steps))
+    assert np.abs(he.decrypt(out) - want).max() < 1e-6
