@@ -668,6 +668,45 @@ Cts ct_square(Ctx *c, const Cts &a) {
     return ct_rescale(c, r);
 }
 
+// Y = sum_i Rot(X_i, steps[i]) over the CH channels of X (CH*B ciphertexts, channel-major),
+// with one ModDown: each channel's accumulator pair for its own step is summed over Q_l u P.
+Cts ct_lincomb_diag(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps) {
+    const u32 N = c->N, lp = X.lp, E = lp + c->K, Bt = CH * B;
+    if (X.B != Bt || steps.size() != CH) throw HeError(HE_EINVAL, "lincomb_diag: shape mismatch");
+    const u32 beta = ks_digits(c, lp);
+    bool any_ks = false;
+    for (int s : steps)
+        if (c->galois_elt(s) != 1) {
+            require_key(c, s);
+            any_ks = true;
+        }
+    DBuf D;
+    if (any_ks) {
+        D = DBuf(c, (size_t)Bt * beta * E * N);
+        ks_modup(c, D.p, X.data() + (size_t)lp * N, (size_t)2 * lp * N, Bt, lp);
+    }
+    const size_t zw = (size_t)B * 2 * E * N;
+    DBuf acc(c, (size_t)CH * zw);
+    for (u32 i = 0; i < CH; ++i) {
+        KeyList kl;
+        const u32 g = c->galois_elt(steps[i]);
+        kl.g[0] = g;
+        kl.ginv[0] = c->galois_inverse(g);
+        kl.key[0] = g == 1 ? nullptr : c->gk.at(g).p;
+        kl.keyp[0] = g == 1 ? nullptr : c->gkp.at(g).p;
+        const u64 *Di = any_ks ? D.p + (size_t)i * B * beta * E * N : nullptr;
+        ks_lazy(c, acc.p + (size_t)i * zw, Di, X.data() + (size_t)i * B * cts_ct_words(c, lp), kl, 1, B, lp);
+    }
+    DBuf Z(c, zw);
+    sum_stack(c, Z.p, acc.p, zw, CH, B * 2 * E, E, lp, c->L1, 0);
+    Cts out = cts_alloc(c, B, lp, X.scale, X.lay);
+    KeyList none;
+    none.g[0] = 1;
+    none.key[0] = nullptr;
+    ks_moddown(c, out.data(), Z.p, nullptr, 0, 0, none, 1, B, lp);
+    return out;
+}
+
 // Hoisted linear combination of rotations with one ModDown per output:
 //   Y_o = sum_i sum_s w[o][i][s] (.) Rot(X_i, steps[s])
 // X holds CH*B ciphertexts (channel-major).  pts: [O][S*CH][lp+K][N] plaintexts over

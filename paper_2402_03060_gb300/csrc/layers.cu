@@ -194,43 +194,51 @@ static Feat layer_square(Ctx *c, const Feat &in) {
     return f;
 }
 
-// multiply every ciphertext of x by one mask (Delta), rescale, rotate left by r
-static Cts mask_rescale_rotate(Ctx *c, const Cts &x, const u64 *pt, int r) {
-    Cts t = ct_rescale(c, ct_mul_pt(c, x, pt, c->scale));
-    return r ? ct_rotate(c, t, r) : t;
-}
-
-static void accumulate(Ctx *c, Cts &acc, bool &have, const Cts &t) {
-    if (!have) {
-        acc = t;
-        have = true;
-    } else {
-        ct_add_inplace(c, acc, t);
-    }
-}
-
 // Sec. IV-E: remove intervals / invalid values, pack the channels.
+// Every mask-rotate-sum stage  sum_k Rot(m_k (.) x, r_k)  is evaluated as one hoisted
+// combination  sum_k Rot(m_k, r_k) (.) Rot(x, r_k)  (the masks are rotated in the clear),
+// followed by one rescale; channel o is then rotated right by o*W*H and all channels are
+// summed with one ModDown.
 static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string &key) {
     const Layout &L = in.x.lay;
     const u32 I = L.I, W = L.W, H = L.H, Wi = L.W_img;
+    const u32 M = c->N / 2;
     std::vector<DBuf> tmp;
     Cts cur = in.x;
     double pending = L.pending;
-    auto mask_pt = [&](const std::string &k, const std::vector<u32> &pos, double v, u32 lp) {
-        std::vector<u32> off{0, (u32)pos.size()};
-        std::vector<double> val(pos.size(), v);
-        return get_pts(c, pc, key + k, tmp, L, off, pos, val, c->scale, lp);
+    // masks (within-sample positions, one value each) rotated left by their steps and
+    // replicated over every sample position; encoded over Q_l u P at the input level
+    auto stage = [&](const Cts &x, const std::string &k, const std::vector<std::vector<u32>> &pos,
+                     const std::vector<int> &steps, double v) {
+        const std::string name = key + k;
+        std::vector<u32> off, apos;
+        std::vector<double> val;
+        if (!pc || !pc->pts.count(name)) {
+            off.push_back(0);
+            for (size_t m = 0; m < pos.size(); ++m) {
+                for (u32 b = 0; b < L.n_samples; ++b)
+                    for (u32 p : pos[m]) {
+                        int64_t a = ((int64_t)b * L.stride + p - steps[m]) % (int64_t)M;
+                        apos.push_back((u32)(a < 0 ? a + M : a));
+                        val.push_back(v);
+                    }
+                off.push_back((u32)apos.size());
+            }
+        }
+        Layout flat = L;
+        flat.n_samples = 1;
+        flat.stride = M;
+        const u64 *pts = get_pts(c, pc, name, tmp, flat, off, apos, val, c->scale, x.lp, c->K);
+        return ct_rescale(c, ct_lincomb(c, x, 1, x.B, steps, pts, 1, c->scale));
     };
     if (L.prev == PREV_POOL) {
-        Cts acc;
-        bool have = false;
+        std::vector<std::vector<u32>> pos(W);
+        std::vector<int> steps;
         for (u32 cc = 0; cc < W; ++cc) {
-            std::vector<u32> pos;
-            for (u32 r = 0; r < H; ++r) pos.push_back(I * (r * Wi + cc));
-            const u64 *pt = mask_pt(fmt(":col%u", cc), pos, pending, cur.lp);
-            accumulate(c, acc, have, mask_rescale_rotate(c, cur, pt, (int)(cc * (I - 1))));
+            for (u32 r = 0; r < H; ++r) pos[cc].push_back(I * (r * Wi + cc));
+            steps.push_back((int)(cc * (I - 1)));
         }
-        cur = acc;
+        cur = stage(cur, ":cols", pos, steps, pending);
         pending = 1.0;
     } else if (L.prev == PREV_CONV) {
         if (pending != 1.0) throw HeError(HE_EINVAL, "flatten: unexpected pending factor");
@@ -238,49 +246,37 @@ static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string
             std::vector<int> st;
             for (u32 m = 0; m < I; ++m) st.push_back((int)(m * (I - 1)));
             Cts y = ct_lincomb(c, cur, 1, cur.B, st, nullptr, 0, 1.0);
-            Cts acc;
-            bool have = false;
-            for (u32 u = 0; u < (W + I - 1) / I; ++u) {
-                std::vector<u32> pos;
+            const u32 nblk = (W + I - 1) / I;
+            std::vector<std::vector<u32>> pos(nblk);
+            std::vector<int> steps;
+            for (u32 u = 0; u < nblk; ++u) {
                 for (u32 r = 0; r < H; ++r)
                     for (u32 cc = I * u; cc < std::min(I * u + I, W); ++cc)
-                        pos.push_back(I * r * Wi + I * I * u + (cc - I * u));
-                const u64 *pt = mask_pt(fmt(":blk%u", u), pos, 1.0, y.lp);
-                accumulate(c, acc, have, mask_rescale_rotate(c, y, pt, (int)(u * I * (I - 1))));
+                        pos[u].push_back(I * r * Wi + I * I * u + (cc - I * u));
+                steps.push_back((int)(u * I * (I - 1)));
             }
-            cur = acc;
+            cur = stage(y, ":blks", pos, steps, 1.0);
         }
     } else {
         throw HeError(HE_EINVAL, "flatten must follow a convolution or an average pooling");
     }
     if (H > 1) {
-        Cts acc;
-        bool have = false;
+        std::vector<std::vector<u32>> pos(H);
+        std::vector<int> steps;
         for (u32 r = 0; r < H; ++r) {
-            std::vector<u32> pos;
-            for (u32 cc = 0; cc < W; ++cc) pos.push_back(I * r * Wi + cc);
-            const u64 *pt = mask_pt(fmt(":row%u", r), pos, 1.0, cur.lp);
-            accumulate(c, acc, have, mask_rescale_rotate(c, cur, pt, (int)(r * (Wi * I - W))));
+            for (u32 cc = 0; cc < W; ++cc) pos[r].push_back(I * r * Wi + cc);
+            steps.push_back((int)(r * (Wi * I - W)));
         }
-        cur = acc;
+        cur = stage(cur, ":rows", pos, steps, 1.0);
     }
-    // pack: channel o rotated right by o*W*H
-    Feat f;
-    f.CH = 1;
-    f.B = in.B;
+    // pack: channel o rotated right by o*W*H, one ModDown for the sum
     Cts acc;
-    bool have = false;
-    for (u32 o = 0; o < in.CH; ++o) {
-        Cts x = cts_view(cur, (size_t)o * in.B * cts_ct_words(c, cur.lp), in.B);
-        if (o) x = ct_rotate(c, x, -(int)(o * W * H));
-        if (!have) {
-            acc = cts_alloc(c, in.B, x.lp, x.scale, x.lay);
-            CUDA_TRY(cudaMemcpyAsync(acc.data(), x.data(), (size_t)in.B * cts_ct_words(c, x.lp) * 8,
-                                     cudaMemcpyDeviceToDevice, c->stream));
-            have = true;
-        } else {
-            ct_add_inplace(c, acc, x);
-        }
+    if (in.CH > 1) {
+        std::vector<int> steps;
+        for (u32 o = 0; o < in.CH; ++o) steps.push_back(-(int)(o * W * H));
+        acc = ct_lincomb_diag(c, cur, in.CH, in.B, steps);
+    } else {
+        acc = cur;
     }
     Layout L2 = L;
     L2.pending = pending;
@@ -290,6 +286,9 @@ static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string
     L2.H = 1;
     L2.I = 1;
     acc.lay = L2;
+    Feat f;
+    f.CH = 1;
+    f.B = in.B;
     f.x = acc;
     return f;
 }
