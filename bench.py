@@ -272,7 +272,9 @@ def run_ours(args, rank, world, local):
                 "kernels": {k: {"launches": v[0], "ms": round(v[1], 3),
                                 "GBps": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 else None}
                             for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1])},
-                "layers_ms": {k: round(v, 3) for k, v in layer_ms.items()}}
+                "layers_ms": {k: round(v, 3) for k, v in layer_ms.items()},
+                "top_layer_kernels_ms": {k: round(v[1], 3) for k, v in
+                                         sorted(tagged.items(), key=lambda kv: -kv[1][1])[:12]}}
     res = {
         "metric": METRIC, "value": round(total_samples / (ms_step / 1e3), 3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 3),
