@@ -207,13 +207,27 @@ void sample_uniform(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u3
 // once per pair.  Lanes of a warp cover 4+ consecutive coefficients of 8 or
 // fewer pairs, so every ciphertext load is a full 32-byte sector.  Each thread
 // keeps all O sums as 128-bit accumulators (products < 2^120, folded every 128 terms).
+// asynchronous 8-byte global -> shared copies (one per thread, per pipeline stage)
+__device__ __forceinline__ void cp_async8(u64 *smem, const u64 *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+
+#define MAC_DEPTH 8
 template <int OMAX>
 __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt,
                                                   u32 O, u32 T, u32 BK, u32 lp, u32 logn, size_t x_tstride,
                                                   size_t out_ostride, u32 ntlog, u32 tc, u32 lpq, u32 pbase,
                                                   int accumulate, size_t pt_ostride,
                                                   const PrimeDev *__restrict__ pd) {
-    extern __shared__ u64 ps[];   // [O][tc][NT]
+    extern __shared__ u64 smem[];
+    u64 *xs = smem;                          // [256][MAC_DEPTH]: each thread's own pipeline slots
+    u64 *ps = smem + 256 * MAC_DEPTH;        // [O][tc][NT]: the plaintext tile
     const u32 N = 1u << logn, NT = 1u << ntlog;
     const u32 tid = threadIdx.x;
     const u32 nl = tid & (NT - 1);
@@ -227,6 +241,13 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
     for (int o = 0; o < OMAX; ++o) acc[o].lo = acc[o].hi = 0;
     const size_t xoff = ((size_t)bk * lp + l) * N + n0 + nl;   // bk = b*2 + k
     const size_t pstride_t = (size_t)lp * N;
+    u64 *myx = xs + tid * MAC_DEPTH;
+    // prologue: the first MAC_DEPTH terms in flight (one commit group per term)
+#pragma unroll
+    for (int d = 0; d < MAC_DEPTH; ++d) {
+        if (active && (u32)d < T) cp_async8(myx + d, x + (size_t)d * x_tstride + xoff);
+        cp_commit();
+    }
     u32 cnt = 0;
     for (u32 t0 = 0; t0 < T; t0 += tc) {
         const u32 tcc = T - t0 < tc ? T - t0 : tc;
@@ -238,32 +259,28 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
                 pt[(size_t)o * pt_ostride + (size_t)(t0 + tt) * pstride_t + (size_t)l * N + n0 + j];
         }
         __syncthreads();
-        if (active) {
-            for (u32 tt0 = 0; tt0 < tcc; tt0 += 4) {
-                // four streaming loads in flight before the products that need them
-                u64 xv[4];
+        for (u32 tt = 0; tt < tcc; ++tt) {
+            const u32 t = t0 + tt;
+            cp_wait<MAC_DEPTH - 1>();        // the copy of term t has landed
+            const u64 xv = myx[t % MAC_DEPTH];
+            if (active) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    xv[u] = tt0 + u < tcc ? __ldcs(x + (size_t)(t0 + tt0 + u) * x_tstride + xoff) : 0;
+                for (int o = 0; o < OMAX; ++o)
+                    if (o < (int)O) mac128(acc[o], ps[((size_t)o * tc + tt) * NT + nl], xv);
+            }
+            if (active && t + MAC_DEPTH < T) cp_async8(myx + t % MAC_DEPTH, x + (size_t)(t + MAC_DEPTH) * x_tstride + xoff);
+            cp_commit();
+            if (++cnt == 128) {
+                cnt = 0;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const u32 tt = tt0 + u;
-                    if (tt >= tcc) break;
-#pragma unroll
-                    for (int o = 0; o < OMAX; ++o)
-                        if (o < (int)O) mac128(acc[o], ps[((size_t)o * tc + tt) * NT + nl], xv[u]);
-                    if (++cnt == 128) {
-                        cnt = 0;
-#pragma unroll
-                        for (int o = 0; o < OMAX; ++o) {
-                            acc[o].lo = reduce128(acc[o].lo, acc[o].hi, P);
-                            acc[o].hi = 0;
-                        }
-                    }
+                for (int o = 0; o < OMAX; ++o) {
+                    acc[o].lo = reduce128(acc[o].lo, acc[o].hi, P);
+                    acc[o].hi = 0;
                 }
             }
         }
     }
+    cp_wait<0>();
     if (!active) return;
 #pragma unroll
     for (int o = 0; o < OMAX; ++o)
@@ -290,10 +307,11 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
     // outputs in groups of at most 12 (the accumulators of a group live in registers)
     for (u32 o0 = 0; o0 < O; o0 += 12) {
         const u32 oc = O - o0 < 12 ? O - o0 : 12;
-        u32 tc = 6144 / (oc * NT);
+        // shared memory: pipeline slots + plaintext tile within the 48 KB default
+        u32 tc = (6144 - 256 * MAC_DEPTH) / (oc * NT);
         if (tc < 1) tc = 1;
         if (tc > T) tc = T;
-        const size_t smem = (size_t)oc * tc * NT * 8;
+        const size_t smem = ((size_t)oc * tc * NT + 256 * MAC_DEPTH) * 8;
         dim3 grid((BK + bkc - 1) / bkc, c->N / NT, lp);
         const u64 *ptc = pt + (size_t)o0 * pt_ostride;
         u64 *outc = out + (size_t)o0 * out_ostride;
