@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
                                                   const PrimeDev *__restrict__ pd) {
     extern __shared__ u64 smem[];
     u64 *xs = smem;                          // [256][MAC_DEPTH]: each thread's own pipeline slots
-    u64 *ps = smem + 256 * MAC_DEPTH;        // [O][tc][NT]: the plaintext tile
+    u64 *ps = smem + 256 * MAC_DEPTH;        // [tc][NT][OMAX]: the plaintext tile
     const u32 N = 1u << logn, NT = 1u << ntlog;
     const u32 tid = threadIdx.x;
     const u32 nl = tid & (NT - 1);
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
         for (u32 idx = tid; idx < O * tcc * NT; idx += blockDim.x) {
             const u32 j = idx & (NT - 1), r = idx >> ntlog;
             const u32 tt = r % tcc, o = r / tcc;
-            ps[((size_t)o * tc + tt) * NT + j] =
+            ps[(tt * NT + j) * OMAX + o] =
                 pt[(size_t)o * pt_ostride + (size_t)(t0 + tt) * pstride_t + (size_t)l * N + n0 + j];
         }
         __syncthreads();
@@ -264,9 +264,18 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
             cp_wait<MAC_DEPTH - 1>();        // the copy of term t has landed
             const u64 xv = myx[t % MAC_DEPTH];
             if (active) {
+                // this thread's OMAX plaintext words of term t, 16-byte loads at fixed offsets
+                const ulonglong2 *pv = reinterpret_cast<const ulonglong2 *>(ps + (tt * NT + nl) * OMAX);
+                u64 pw[OMAX];
 #pragma unroll
-                for (int o = 0; o < OMAX; ++o)
-                    if (o < (int)O) mac128(acc[o], ps[((size_t)o * tc + tt) * NT + nl], xv);
+                for (int o = 0; o < OMAX / 2; ++o) {
+                    const ulonglong2 v = pv[o];
+                    pw[2 * o] = v.x;
+                    pw[2 * o + 1] = v.y;
+                }
+                if (OMAX & 1) pw[OMAX - 1] = ps[(tt * NT + nl) * OMAX + OMAX - 1];
+#pragma unroll
+                for (int o = 0; o < OMAX; ++o) mac128(acc[o], pw[o], xv);
             }
             if (active && t + MAC_DEPTH < T) cp_async8(myx + t % MAC_DEPTH, x + (size_t)(t + MAC_DEPTH) * x_tstride + xoff);
             cp_commit();
@@ -308,10 +317,11 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
     for (u32 o0 = 0; o0 < O; o0 += 12) {
         const u32 oc = O - o0 < 12 ? O - o0 : 12;
         // shared memory: pipeline slots + plaintext tile within the 48 KB default
-        u32 tc = (6144 - 256 * MAC_DEPTH) / (oc * NT);
+        const u32 ow = oc <= 1 ? 1 : oc <= 2 ? 2 : oc <= 4 ? 4 : oc <= 6 ? 6 : oc <= 8 ? 8 : 12;   // template width
+        u32 tc = (6144 - 256 * MAC_DEPTH) / (ow * NT);
         if (tc < 1) tc = 1;
         if (tc > T) tc = T;
-        const size_t smem = ((size_t)oc * tc * NT + 256 * MAC_DEPTH) * 8;
+        const size_t smem = ((size_t)ow * tc * NT + 256 * MAC_DEPTH) * 8;
         dim3 grid((BK + bkc - 1) / bkc, c->N / NT, lp);
         const u64 *ptc = pt + (size_t)o0 * pt_ostride;
         u64 *outc = out + (size_t)o0 * out_ostride;
