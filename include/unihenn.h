@@ -215,8 +215,16 @@ typedef struct {
     char name[32];
     uint64_t launches;
     double total_ms;
-    double bytes;
+    double bytes;   /* algorithmic bytes */
+    double ops;     /* algorithmic primitive operations: NTT butterflies (NTT, ModDown, rescale)
+                       or 64x64->128 multiply-accumulates (MAC, key inner products) */
 } he_kernel_stat;
+/* Measured integer roofline: register-only throughput on this device of the
+ * modular primitives the kernels use.  out[0] = lazy NTT butterflies/s,
+ * out[1] = 64x64->128-bit multiply-accumulates/s, out[2] = Barrett modular
+ * products/s.  Runs a few short kernels on the context's stream and waits. */
+he_status he_ubench(he_ctx *ctx, double *out);
+
 he_status he_profile_begin(he_ctx *ctx);
 he_status he_profile_end(he_ctx *ctx, he_kernel_stat *out, size_t cap, size_t *n);
 

@@ -174,13 +174,20 @@ class Context:
         check(load().he_profile_begin(self.h))
 
     def profile_end(self):
-        """-> {kernel: (launches, total_ms, algorithmic_bytes)} of the eager launches since profile_begin."""
-        cap = 128
+        """-> {"layer/kernel": (launches, total_ms, algorithmic_bytes, algorithmic_ops)} of the eager
+        launches since profile_begin."""
+        cap = 256
         buf = (_lib.he_kernel_stat * cap)()
         n = ctypes.c_size_t(0)
         check(load().he_profile_end(self.h, buf, cap, ctypes.byref(n)))
-        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), float(buf[i].bytes))
-                for i in range(min(n.value, cap))}
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), float(buf[i].bytes),
+                                       float(buf[i].ops)) for i in range(min(n.value, cap))}
+
+    def ubench(self):
+        """Measured register-only throughput: (butterflies/s, 128-bit MACs/s, Barrett products/s)."""
+        out = (ctypes.c_double * 3)()
+        check(load().he_ubench(self.h, out))
+        return tuple(out)
 
     # ---- client side
     def encrypt(self, x, samples_per_ct: int, stride: int, enc_seed: int) -> Ct:

@@ -33,7 +33,7 @@ class he_layer(ctypes.Structure):
 
 class he_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
-                ("bytes", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("ops", ctypes.c_double)]
 
 
 class HeError(RuntimeError):
@@ -77,6 +77,7 @@ SIGNATURES = {
     "he_rescale_noalloc": (_int, [_vp, _vp, _vp, _u32, _u32]),
     "he_sync": (_int, [_vp]),
     "he_kernel_launches": (_u64, [_vp]),
+    "he_ubench": (_int, [_vp, ctypes.POINTER(_dbl)]),
     "he_profile_begin": (_int, [_vp]),
     "he_profile_end": (_int, [_vp, ctypes.POINTER(he_kernel_stat), _sz, ctypes.POINTER(_sz)]),
     "he_last_error": (ctypes.c_char_p, []),

@@ -36,14 +36,14 @@ void prof_begin(Ctx *c) {
     CUDA_TRY(cudaEventRecord(c->prof_start, c->stream));
 }
 
-void note_launch(Ctx *c, const char *what, double bytes) {
+void note_launch(Ctx *c, const char *what, double bytes, double ops) {
     c->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw HeError(HE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
     if (c->profiling && c->prof_start) {
         cudaEvent_t b = c->new_event();
         CUDA_TRY(cudaEventRecord(b, c->stream));
-        c->recs.push_back({what, bytes, c->prof_start, b, c->prof_tag});
+        c->recs.push_back({what, bytes, ops, c->prof_start, b, c->prof_tag});
         c->prof_start = nullptr;
     }
 }

@@ -143,7 +143,9 @@ struct HeError : std::runtime_error {
 
 struct Ctx;
 void prof_begin(Ctx *c);                                        // start event of the next launch (profiling)
-void note_launch(Ctx *c, const char *what, double bytes = 0);   // error check, launch counter, end event
+// error check, launch counter, end event; bytes = algorithmic bytes, ops = algorithmic primitive
+// operations of the launch (NTT butterflies or 64x64->128 multiply-accumulates)
+void note_launch(Ctx *c, const char *what, double bytes = 0, double ops = 0);
 
 // Caching device allocator: buffers are returned to per-size free lists and
 // reused in stream order (all work of a context runs on one stream), so the
@@ -220,7 +222,7 @@ struct Ctx : std::enable_shared_from_this<Ctx> {
     // per-launch CUDA-event profiling (he_profile_begin / he_profile_end)
     struct ProfRec {
         const char *name;
-        double bytes;
+        double bytes, ops;
         cudaEvent_t a, b;
         std::string tag;
     };

@@ -446,8 +446,9 @@ void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u3
         ks_lazy_kernel<<<grid, 256, 0, c->stream>>>(acc, D, x, kl, B, beta, lp, c->K, c->L1, c->logn, pmod_table(c),
                                                      c->pdev);
     }
-    note_launch(c, "ks_lazy", 8.0 * N * ((double)B * beta * E + (double)S * 2 * beta * E + (double)B * 2 * lp +
-                                         (double)S * B * 2 * E));
+    note_launch(c, "ks_lazy",
+                8.0 * N * ((double)B * beta * E + (double)S * 2 * beta * E + (double)B * 2 * lp + (double)S * B * 2 * E),
+                (double)S * B * E * N * 2 * beta);
 }
 
 // out [S][B][2][lp][N] = ModDown(acc) (+ addend: poly k of ct b gathered by sigma_{g_s} when add_mask bit k)
@@ -467,7 +468,8 @@ void ks_moddown(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bst
                                                                       lp, c->K, c->L1, c->logn, moddown_table(c),
                                                                       c->tw, c->pdev);
     note_launch(c, "moddown",
-                8.0 * N * (double)S * B * (2.0 * E + (addend ? __builtin_popcount(add_mask) : 0) * lp + 2.0 * lp));
+                8.0 * N * (double)S * B * (2.0 * E + (addend ? __builtin_popcount(add_mask) : 0) * lp + 2.0 * lp),
+                (double)S * B * 2 * lp * (N / 2) * c->logn);
 }
 
 // out [B][2][lp-1][N] = rescale(in [B][2][lp][N])
@@ -481,5 +483,5 @@ void rescale_batch(Ctx *c, u64 *out, const u64 *in, u32 B, u32 lp) {
     prof_begin(c);
     rescale_kernel<<<grid, ntt_threads(N), (size_t)ntt_smem_words(N) * 8, c->stream>>>(out, in, top.p, lp, c->logn,
                                                                       rescale_table(c, lp), c->tw, c->pdev);
-    note_launch(c, "rescale", 8.0 * N * (double)B * 2 * (lp + 1 + lp - 1));
+    note_launch(c, "rescale", 8.0 * N * (double)B * 2 * (lp + 1 + lp - 1), (double)B * 2 * (lp - 1) * (N / 2) * c->logn);
 }

@@ -1033,6 +1033,7 @@ he_status he_profile_end(he_ctx *h, he_kernel_stat *out, size_t cap, size_t *n) 
             it->second.launches++;
             it->second.total_ms += ms;
             it->second.bytes += r.bytes;
+            it->second.ops += r.ops;
             c->ev_free.push_back(r.a);
             c->ev_free.push_back(r.b);
         }

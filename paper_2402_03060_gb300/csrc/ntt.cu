@@ -37,7 +37,8 @@ static void ntt_launch(Ctx *c, u64 *base, const RowSet &rs, int inverse) {
     size_t smem = (size_t)ntt_smem_words(c->N) * sizeof(u64);
     prof_begin(c);
     ntt_rows_kernel<<<rs.n, ntt_threads(c->N), smem, c->stream>>>(base, rs, c->tw, c->pdev, c->logn, inverse);
-    note_launch(c, inverse ? "intt" : "ntt", 16.0 * rs.n * c->N);   // each limb read and written once
+    // each limb read and written once; (N/2) log2 N butterflies per limb
+    note_launch(c, inverse ? "intt" : "ntt", 16.0 * rs.n * c->N, (double)rs.n * (c->N / 2) * c->logn);
 }
 
 void ntt_forward(Ctx *c, u64 *base, const RowSet &rs) { ntt_launch(c, base, rs, 0); }

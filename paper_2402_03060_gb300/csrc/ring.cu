@@ -342,7 +342,8 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
         else
             MAC_LAUNCH(12);
 #undef MAC_LAUNCH
-        note_launch(c, "mac", 8.0 * c->N * ((double)oc * T * lp + (double)T * B * 2 * lp + (double)oc * B * 2 * lp));
+        note_launch(c, "mac", 8.0 * c->N * ((double)oc * T * lp + (double)T * B * 2 * lp + (double)oc * B * 2 * lp),
+                    (double)oc * T * B * 2 * lp * c->N);
     }
 }
 
