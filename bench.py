@@ -20,7 +20,10 @@ working set (keys ~1.7 GB, cached plaintext masks ~1.3 GB, ciphertexts) is far
 larger than the 126 MB L2.
 
 --impl reference runs the CPU oracle (oracle/, plain C with __int128 '%') on a
-bounded sample of the same workload on this host's cores.
+bounded sample of the same workload on this host's cores: K steps of one
+ciphertext each, on min(K, cores) concurrent single-threaded processes.
+--ncu-step / --ncu-conv run one eager step / one conv2d layer call between
+cudaProfilerStart and cudaProfilerStop for `ncu --profile-from-start off`.
 """
 from __future__ import annotations
 
@@ -58,6 +61,9 @@ def parse():
     ap.add_argument("--ncu-step", action="store_true",
                     help="after set-up and warm-up run ONE eager step between cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off) and exit")
+    ap.add_argument("--ncu-conv", action="store_true",
+                    help="small case for full ncu captures: ONE hoisted conv2d layer call (4 -> 12 channels, 5x5, "
+                         "8 ciphertexts per channel, N = 16384, top level) between cudaProfilerStart/Stop, then exit")
     return ap.parse_args()
 
 
@@ -130,6 +136,31 @@ def lenet_setup(G, torch, device, stream, n_samples):
     m = ctx.compile(model, 28, 28, SPC)
     imgs = W.images(n_samples)
     return ctx, m, stride, model, imgs
+
+
+def conv_case(args, local):
+    """The second LeNet-1 convolution's shape as one layer call: 25 rotation keys,
+    4 input channels x 8 ciphertexts, 12 output channels (about 2.5 GB on the device)."""
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_03060_gb300 as G
+    P = W.PARAMS["lenet1"]
+    w = W.lenet1()[3]
+    stream = torch.cuda.Stream()
+    ctx = G.Context(seed=W.KEY_SEED, device=local, stream=stream.cuda_stream, **P)
+    ctx.keygen(sorted({k + 28 * j for j in range(5) for k in range(5)} - {0}))
+    imgs = W.images(80)
+    cts = [ctx.encrypt(imgs, SPC, 784, W.ENC_SEED + c) for c in range(4)]
+    for _ in range(max(args.warmup, 1)):
+        ctx.conv2d(cts, w["w"], w["b"])
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    ctx.conv2d(cts, w["w"], w["b"])
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    return {"ncu_conv": True}
 
 
 def run_ours(args, rank, world, local):
@@ -322,17 +353,28 @@ def run_ours(args, rank, world, local):
     return res, ctx
 
 
-def oracle_sample(budget_s: float):
+def oracle_sample():
     """The CPU oracle on one ciphertext (10 samples) of the workload; keys are
     generated first (not timed, like the GPU's).  Returns (samples/s, seconds, note)."""
+    he, pl, model = _oracle_setup()
+    t = _oracle_step(he, pl, model)
+    return SPC / t, t, "one ciphertext (10 samples) end to end: encrypt, LeNet-1, decrypt; keygen untimed"
+
+
+def _oracle_setup():
     from oracle import ckks, layers
     P = W.PARAMS["lenet1"]
     model = W.lenet1()
     pl = layers.plan(model, 28, 28)
     he = ckks.Ckks(seed=W.KEY_SEED, **P)
-    t0 = time.perf_counter()
     he.keygen(pl["steps"])
-    tk = time.perf_counter() - t0
+    return he, pl, model
+
+
+def _oracle_step(he, pl, model) -> float:
+    """One step of the reference arm: encrypt, run and decrypt one ciphertext of
+    10 samples with the oracle; returns its seconds."""
+    from oracle import layers
     imgs = W.images(SPC)
     lay = layers.input_layout(28, 28, pl["stride"], SPC, he.n // 2)
     x = np.zeros(he.n // 2)
@@ -342,29 +384,62 @@ def oracle_sample(budget_s: float):
     ct = he.encrypt(x, W.ENC_SEED)
     ys, _ = layers.run_model(layers.HeBackend(he), ct, model, lay)
     he.decrypt(ys[0])
-    t = time.perf_counter() - t0
-    return SPC / t, t, f"one ciphertext (10 samples) end to end: encrypt, LeNet-1, decrypt; keygen {tk:.1f} s untimed"
+    return time.perf_counter() - t0
+
+
+def _oracle_worker(n_steps, barrier, out):
+    """Spawned process: keygen (its warm-up, untimed), wait for every worker,
+    then n_steps timed oracle steps; reports (start, end) on the monotonic clock."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    he, pl, model = _oracle_setup()
+    barrier.wait()
+    t0 = time.monotonic()
+    for _ in range(n_steps):
+        _oracle_step(he, pl, model)
+    out.put((t0, time.monotonic()))
+
+
+def run_reference(args):
+    """The reference arm: the oracle as it stands, K steps of one ciphertext each,
+    spread over min(K, host cores) single-threaded processes that start together."""
+    import multiprocessing as mp
+    from oracle import build as oracle_build
+    oracle_build.build()  # once, before the workers load it
+    k = max(1, args.steps)
+    procs = max(1, min(k, os.cpu_count() or 1))
+    per = [k // procs + (1 if i < k % procs else 0) for i in range(procs)]
+    sp = mp.get_context("spawn")
+    barrier, q = sp.Barrier(procs), sp.Queue()
+    ps = [sp.Process(target=_oracle_worker, args=(n, barrier, q)) for n in per]
+    for p in ps:
+        p.start()
+    spans = [q.get() for _ in ps]
+    for p in ps:
+        p.join()
+    t = max(e for _, e in spans) - min(s for s, _ in spans)
+    v = k * SPC / t
+    note = (f"{k} steps of one ciphertext (10 samples) each, end to end (encrypt, LeNet-1, decrypt), on "
+            f"{procs} concurrent single-threaded processes; each process generates its keys first (untimed, "
+            "its warm-up)")
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": 1,
+            "steps": k, "warmup": 0, "ms_per_step": round(t * 1e3 / k, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS residues), f64 encode",
+            "data": "synthetic U[0,1] 28x28 images, N(0,0.1^2) weights",
+            "config": {"workload": "batched LeNet-1-shaped, one ciphertext of 10 samples per step",
+                       "ckks": "N=16384, [60,40x7|60], Delta=2^40, dnum=8"},
+            "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": procs, "kind": "oracle", "sample": note},
+            "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
-        if rank != 0:
-            return
-        k = max(1, args.steps)
-        vals = []
-        for _ in range(max(0, min(args.warmup, 0))):
-            pass
-        v, t, note = oracle_sample(30.0)
-        vals.append(v)
-        res = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": world,
-               "steps": 1, "warmup": 0, "ms_per_step": round(t * 1e3, 1), "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS residues), f64 encode",
-               "data": "synthetic", "config": {"workload": "batched LeNet-1-shaped (one ciphertext sample)"},
-               "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": note},
-               "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(res))
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    if args.ncu_conv:
+        print(json.dumps(conv_case(args, local)))
         return
     res, ctx = run_ours(args, rank, world, local)
     if args.ncu_step:
@@ -372,7 +447,7 @@ def main():
         return
     chk, imgs, layers = res.pop("_logits", (None, None, None))
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, t, note = oracle_sample(30.0)
+        v, t, note = oracle_sample()
         res["cpu_baseline"] = {"value": round(v, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": note,
                                "seconds": round(t, 1)}
         # the timed configuration's logits against the FP64 CNN on a spread of samples
