@@ -44,6 +44,7 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 N_SAMPLES = 633
+TUNE_CACHE = os.path.join(ROOT, "paper_2402_03060_gb300", "_build", "tune_cache.json")
 SPC = 10
 METRIC = "encrypted LeNet-1 inferences/s (batched)"
 UNIT = "samples/s"
@@ -61,6 +62,11 @@ def parse():
     ap.add_argument("--ncu-step", action="store_true",
                     help="after set-up and warm-up run ONE eager step between cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off) and exit")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving benchmark instead: Poisson arrivals over a LeNet-1 / LeNet-5 / 1-D CNN mix through "
+                         "the continuous-batching loop; prints request-latency percentiles")
+    ap.add_argument("--requests", type=int, default=600, help="requests of the --serve trace")
+    ap.add_argument("--rate", type=float, default=200.0, help="arrivals per second of the --serve trace")
     ap.add_argument("--ncu-conv", action="store_true",
                     help="small case for full ncu captures: ONE hoisted conv2d layer call (4 -> 12 channels, 5x5, "
                          "8 ciphertexts per channel, N = 16384, top level) between cudaProfilerStart/Stop, then exit")
@@ -132,6 +138,7 @@ def lenet_setup(G, torch, device, stream, n_samples):
     model = W.lenet1()
     stride, levels, steps = G.plan(model, 28, 28)
     ctx = G.Context(seed=W.KEY_SEED, device=device, stream=stream.cuda_stream, **P)
+    ctx.autotune(TUNE_CACHE)
     ctx.keygen(steps)
     m = ctx.compile(model, 28, 28, SPC)
     imgs = W.images(n_samples)
@@ -161,6 +168,102 @@ def conv_case(args, local):
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStop()
     return {"ncu_conv": True}
+
+
+SERVE_MODELS = (  # name, layers, image W, H, samples per ciphertext, logits
+    ("lenet1", W.lenet1, 28, 28, 10, 10),
+    ("lenet5", W.lenet5_sq, 32, 32, 16, 10),
+    ("cnn1d", W.cnn1d, 1024, 1, 2, 5),
+)
+
+
+def run_serve(args, local):
+    """Poisson(rate) requests, each one sample of a uniformly drawn model; the
+    clients' ciphertexts are encrypted beforehand and submitted to the serving
+    loop at their arrival times; a second thread collects the results.
+    Latency = submit to completion on the device."""
+    import threading
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_03060_gb300 as G
+    t_setup = time.perf_counter()
+    srv = G.Server(max_batch=8, max_wait_us=2000)
+    ctxs, models, strides, layers = [], [], [], []
+    for i, (name, fn, Wi, Hi, spc, nout) in enumerate(SERVE_MODELS):
+        ly = fn()
+        stride, levels, steps = G.plan(ly, Wi, Hi)
+        ctx = G.Context(seed=W.KEY_SEED, device=local, **W.SERVE_PARAMS[name])
+        ctx.autotune(TUNE_CACHE)
+        ctx.keygen(steps)
+        m = ctx.compile(ly, Wi, Hi, spc)
+        assert srv.add_model(m) == i
+        ctxs.append(ctx)
+        models.append(m)
+        strides.append(stride)
+        layers.append(ly)
+    t_setup = time.perf_counter() - t_setup
+    rng = np.random.default_rng(W.ARRIVAL_SEED)
+    n = args.requests
+    arrival = np.cumsum(rng.exponential(1.0 / args.rate, n))
+    which = rng.integers(0, len(SERVE_MODELS), n)
+    # the clients' ciphertexts: encrypted before the trace starts (client-side work)
+    cts = []
+    for k in range(n):
+        i = which[k]
+        name, fn, Wi, Hi, spc, nout = SERVE_MODELS[i]
+        x = W.images(1, Hi, Wi, seed=W.INPUT_SEED + k) if Hi > 1 else W.signals(1, Wi, seed=W.INPUT_SEED + k)
+        cts.append(ctxs[i].encrypt(x, spc, strides[i], W.ENC_SEED + k))
+    for c in ctxs:
+        c.sync()
+    ids = [None] * n
+    lat = np.zeros(n)
+    done_t = np.zeros(n)
+    results = {}
+    ready = threading.Semaphore(0)
+
+    def collect():
+        for k in range(n):
+            ready.acquire()
+            out, lat[k] = srv.wait(ids[k], 600000)
+            done_t[k] = time.perf_counter()
+            if which[k] not in results:
+                results[which[k]] = (k, out)
+    th = threading.Thread(target=collect)
+    th.start()
+    t0 = time.perf_counter()
+    for k in range(n):
+        delay = t0 + arrival[k] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        ids[k] = srv.submit(int(which[k]), cts[k])
+        cts[k] = None
+        ready.release()
+    th.join()
+    t_end = done_t.max()
+    per_model = {}
+    for i, (name, *_rest) in enumerate(SERVE_MODELS):
+        st = srv.stats(i)
+        per_model[name] = {"requests": st["requests"], "batches": st["batches"],
+                           "mean_batch_cts": round(st["mean_batch"], 2), "p50_ms": round(st["p50_ms"], 2),
+                           "p99_ms": round(st["p99_ms"], 2), "max_ms": round(st["max_ms"], 2)}
+    st = srv.stats()
+    # first result of each model decrypted (correctness of what was served)
+    for i, (k, out) in results.items():
+        nout = SERVE_MODELS[i][5]
+        per_model[SERVE_MODELS[i][0]]["first_result_logits"] = [round(float(v), 4) for v in
+                                                                ctxs[i].decrypt(out, nout)[0][:3]]
+    srv.close()
+    return {"metric": "serving request latency p99 (Poisson arrivals, LeNet-1 / LeNet-5 / 1-D CNN mix)",
+            "value": round(st["p99_ms"], 3), "unit": "ms", "n_gpus": 1, "higher_is_better": False,
+            "p50_ms": round(st["p50_ms"], 3), "max_ms": round(st["max_ms"], 3),
+            "throughput_req_per_s": round(n / (t_end - t0), 2), "requests": n, "rate_per_s": args.rate,
+            "dtype": "u64 (RNS residues), f64 encode", "data": "synthetic",
+            "config": {"workload": "serving mix, one sample per request",
+                       "models": {m[0]: W.SERVE_PARAMS[m[0]] for m in SERVE_MODELS},
+                       "max_batch_cts": 8, "max_wait_us": 2000, "arrival_seed": W.ARRIVAL_SEED},
+            "setup_s": round(t_setup, 1), "per_model": per_model}
 
 
 def run_ours(args, rank, world, local):
@@ -341,7 +444,7 @@ def run_ours(args, rank, world, local):
         "config": {"workload": "batched LeNet-1-shaped, 64 ciphertexts x 10 samples (last 3), 633 samples",
                    "ckks": "N=16384, [60,40x7|60], Delta=2^40, dnum=8", "samples_per_gpu": args.samples,
                    "l2": "working set > L2 (keys + masks + ciphertexts, several GB)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "autotuned": ctx.tuning()},
         "e2e": {"value": round(total_samples / (ms_e2e / 1e3), 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(args.samples * 784 * 8), "d2h_bytes_per_step": int(n_ct * SPC * 10 * 8)},
         "gpu_launches": int(launches),
@@ -440,6 +543,10 @@ def main():
         return
     if args.ncu_conv:
         print(json.dumps(conv_case(args, local)))
+        return
+    if args.serve:
+        if rank == 0:
+            print(json.dumps(run_serve(args, local)))
         return
     res, ctx = run_ours(args, rank, world, local)
     if args.ncu_step:

@@ -56,7 +56,7 @@ typedef struct he_model he_model;
  * and not used by an earlier entry.  Hybrid key switching uses dnum digits of
  * ceil(n_data/dnum) consecutive data primes.  Depth = n_data - 1. */
 typedef struct {
-    uint32_t log2n;              /* N = 2^log2n; 4 <= log2n <= 14 */
+    uint32_t log2n;              /* N = 2^log2n; 4 <= log2n <= 15 */
     uint32_t n_data;             /* data primes (L+1), 1..32 */
     uint32_t n_special;          /* special primes K, 1..4 */
     const uint32_t *prime_bits;  /* n_data + n_special bit sizes, each 20..60 */
@@ -177,6 +177,90 @@ he_status he_model_compile(he_ctx *ctx, const he_layer *layers, size_t n, uint32
 he_status he_infer(he_model *m, const he_ct *in, int use_graph, he_ct **out);
 void he_model_free(he_model *m);
 
+/* ---- autotuning --------------------------------------------------------- */
+/* Chooses the launch shapes of the batched path for this context's N, chain,
+ * dnum and GPU by timing each candidate with CUDA events on scratch data (about
+ * 1 GB at N = 2^14, released afterwards): limb split over 2-CTA clusters for the
+ * NTT, ModDown and rescale kernels; outputs per MAC launch; ciphertexts per
+ * thread and grid order of the hoisted key-switch accumulation.  No choice
+ * changes a result bit.  cache_path (optional) is a JSON file keyed by device
+ * name and parameters: an entry there is used without measuring, a new
+ * measurement is added to it.  report (optional) receives the timings as JSON.
+ * Call it before he_model_compile / the first he_infer: captured CUDA graphs
+ * keep the shapes they were captured with.  Errors: HE_EINVAL, HE_ENOMEM, HE_ECUDA. */
+he_status he_autotune(he_ctx *ctx, const char *cache_path, char *report, size_t report_len);
+/* The tuned knobs in the order: NTT split, ModDown split, rescale split, MAC
+ * output group, key-switch ciphertexts per thread, key-switch grid order
+ * (-1 = default).  he_tuning_set overrides them (values outside a knob's
+ * candidates fall back to the nearest valid launch shape). */
+he_status he_tuning_get(he_ctx *ctx, int32_t *values, size_t n);
+he_status he_tuning_set(he_ctx *ctx, const int32_t *values, size_t n);
+
+/* ---- serving ----------------------------------------------------------- */
+/* A continuous-batching request loop over compiled models (the paper's
+ * service model: clients send ciphertexts encrypted under their public key,
+ * the server evaluates the network with the evaluation keys and returns
+ * encrypted results; paper Sec. III).  One host thread serves every added
+ * model, each from a FIFO queue: while a model has fewer than two batches in
+ * flight, the queued requests (in arrival order, up to max_batch
+ * ciphertexts) are gathered into one batch padded to a power of two and run
+ * on the model's stream; requests that arrive meanwhile join the next batch.
+ * A request's result is bit-identical whether it ran alone or in a mix.
+ * Thread safety: submit / wait / stats may be called from any thread; the
+ * contexts of the added models stay usable from other threads (every entry
+ * point takes its context's lock). */
+typedef struct he_server he_server;
+typedef struct {
+    uint32_t max_batch;     /* ciphertexts per launch of one model; rounded down to a power of two, >= 1 */
+    uint32_t max_wait_us;   /* while a model's batch runs, a partial next batch waits up to this long for
+                               more requests before it is launched behind it; 0: launch at once */
+    uint64_t mem_budget;    /* device bytes for the models (their contexts' pools: keys and cached masks,
+                               and their graph pools) plus the ciphertexts of queued and running
+                               requests; 0: unlimited */
+} he_server_opts;
+typedef struct {
+    uint64_t requests;        /* finished requests */
+    uint64_t batches;         /* launched batches */
+    uint64_t cts;             /* ciphertexts launched, padding included */
+    double mean_batch;        /* cts / batches */
+    double p50_ms, p99_ms, max_ms;   /* latency from submit to completion on the device (nearest rank) */
+    uint64_t resident_bytes;  /* bytes the added models hold against the budget */
+} he_server_stats;
+
+/* Starts the loop's thread.  HE_EINVAL if max_batch is 0. */
+he_status he_server_create(const he_server_opts *opt, he_server **out);
+/* Adds a compiled model (borrowed: it must outlive the server).  Runs the model
+ * once on zero ciphertexts for every batch shape (1, 2, 4, .. max_batch) at the
+ * context's top level, capturing their CUDA graphs, then admits it: HE_ENOMEM
+ * if the budget cannot hold what the model and its context keep on the device.
+ * The ids are 0, 1, 2, ... in order of addition. */
+he_status he_server_add_model(he_server *srv, he_model *model, uint32_t *model_id);
+/* Queues a request: the ciphertext batch `in` (a fresh encryption of the
+ * model's input layout, at most max_batch ciphertexts, on the model's context).
+ * The server keeps its own reference to the buffer; the caller may free `in`.
+ * HE_ENOMEM when admitting it would exceed the budget (retry after collecting
+ * results), HE_EINVAL / HE_ELEVEL when it does not fit the model. */
+he_status he_server_submit(he_server *srv, uint32_t model_id, const he_ct *in, uint64_t *req_id);
+/* Waits up to timeout_ms for a request and collects it: *out receives the
+ * result (caller frees it with he_ct_free; NULL out frees it), *latency_ms
+ * (optional) the time from submit to completion.  HE_ETIMEOUT leaves the
+ * request pending; any other status ends it (the status of its batch). */
+he_status he_server_wait(he_server *srv, uint64_t req_id, uint32_t timeout_ms, he_ct **out, double *latency_ms);
+/* Counters and latency percentiles of one model (model_id) or all (-1). */
+he_status he_server_stats_get(he_server *srv, int32_t model_id, he_server_stats *out);
+/* Runs every queued request to completion, frees uncollected results, stops the thread. */
+void he_server_destroy(he_server *srv);
+/* The same loop on simulated models, without a GPU: request k arrives at
+ * arrival_us[k] (microseconds after the start, nondecreasing) for model
+ * model_of[k] with cts_of[k] ciphertexts; a batch of b ciphertexts of model i
+ * occupies one simulated device for base_us[i] + per_ct_us[i]*b microseconds
+ * (batches back to back).  Outputs (optional): the batch id of each request
+ * (ids increase in launch order) and its latency.  Runs in real time. */
+he_status he_server_simulate(const he_server_opts *opt, uint32_t n_models, const double *base_us,
+                             const double *per_ct_us, size_t n_req, const double *arrival_us,
+                             const uint32_t *model_of, const uint32_t *cts_of, uint64_t *batch_of,
+                             double *latency_ms);
+
 /* ---- low level ------------------------------------------------------- */
 /* In-place forward (inverse = 0) or inverse negacyclic NTT of n_limbs device
  * limbs data[n_limbs][N]; limb i uses prime prime_idx[i] (index into the
@@ -193,7 +277,8 @@ he_status he_ntt(he_ctx *ctx, uint64_t *data, uint32_t n_limbs, const uint32_t *
  * Work is queued on the context's stream.  The only working memory is a
  * file-scope device array of 2^19 words (4 MiB) held by every GPU that loads
  * the library until the process exits: batch*2*N must not exceed 2^19 (16
- * ciphertexts at N = 2^14), else HE_EINVAL.  The array is fully overwritten
+ * ciphertexts at N = 2^14), else HE_EINVAL; N = 2^15 contexts get HE_EINVAL
+ * (the kernels hold a whole limb in one CTA).  The array is fully overwritten
  * before use; calls share it, so calls that overlap on the GPU (other streams
  * or contexts on the same device) race.  The first call on a device looks up
  * the array's device address and sets kernel attributes: make that first call

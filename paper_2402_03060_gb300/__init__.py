@@ -15,7 +15,7 @@ import numpy as np
 from . import _lib
 from ._lib import HeError, check, load
 
-__all__ = ["Context", "Ct", "Model", "HeError", "layers_to_c", "plan", "load"]
+__all__ = ["Context", "Ct", "Model", "Server", "HeError", "layers_to_c", "plan", "load", "simulate_server"]
 
 
 def _dptr(a: np.ndarray):
@@ -126,6 +126,69 @@ class Model:
             pass
 
 
+class Server:
+    """he_server_*: continuous-batching request loop over compiled models."""
+
+    def __init__(self, max_batch: int = 8, max_wait_us: int = 0, mem_budget: int = 0):
+        self._models, self._req_ctx = [], {}
+        opt = _lib.he_server_opts(max_batch, max_wait_us, mem_budget)
+        h = ctypes.c_void_p()
+        check(load().he_server_create(ctypes.byref(opt), ctypes.byref(h)))
+        self.h = h
+
+    def add_model(self, model: Model) -> int:
+        mid = ctypes.c_uint32()
+        check(load().he_server_add_model(self.h, model.h, ctypes.byref(mid)))
+        self._models.append(model)
+        return mid.value
+
+    def submit(self, model_id: int, ct: Ct) -> int:
+        rid = ctypes.c_uint64()
+        check(load().he_server_submit(self.h, model_id, ct.h, ctypes.byref(rid)))
+        self._req_ctx[rid.value] = self._models[model_id].ctx
+        return rid.value
+
+    def wait(self, req_id: int, timeout_ms: int = 60000):
+        """-> (result Ct, latency in ms)"""
+        out, lat = ctypes.c_void_p(), ctypes.c_double()
+        check(load().he_server_wait(self.h, req_id, timeout_ms, ctypes.byref(out), ctypes.byref(lat)))
+        return Ct(self._req_ctx.pop(req_id), out), lat.value
+
+    def stats(self, model_id: int = -1) -> dict:
+        st = _lib.he_server_stats()
+        check(load().he_server_stats_get(self.h, model_id, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            load().he_server_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def simulate_server(max_batch, max_wait_us, base_us, per_ct_us, arrival_us, model_of, cts_of, mem_budget=0):
+    """he_server_simulate: the serving loop on simulated models (no GPU).
+    Returns (batch id per request, latency ms per request)."""
+    n = len(arrival_us)
+    opt = _lib.he_server_opts(max_batch, max_wait_us, mem_budget)
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    u32 = lambda a: np.ascontiguousarray(a, dtype=np.uint32)
+    base, per, arr = f64(base_us), f64(per_ct_us), f64(arrival_us)
+    mo, co = u32(model_of), u32(cts_of)
+    batch = np.zeros(n, dtype=np.uint64)
+    lat = np.zeros(n, dtype=np.float64)
+    P = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t))
+    check(load().he_server_simulate(ctypes.byref(opt), len(base), P(base, ctypes.c_double), P(per, ctypes.c_double),
+                                    n, P(arr, ctypes.c_double), P(mo, ctypes.c_uint32), P(co, ctypes.c_uint32),
+                                    P(batch, ctypes.c_uint64), P(lat, ctypes.c_double)))
+    return batch, lat
+
+
 class Context:
     """he_context_create + key material; one CUDA stream, one device."""
 
@@ -190,6 +253,26 @@ class Context:
         return tuple(out)
 
     # ---- client side
+    TUNE_KNOBS = ("ntt_split", "moddown_split", "rescale_split", "mac_group", "lazy_bt", "lazy_order")
+
+    def autotune(self, cache_path: str | None = None) -> dict:
+        """he_autotune: time the launch-shape candidates (or read them from cache_path)."""
+        import json
+        buf = ctypes.create_string_buffer(8192)
+        check(load().he_autotune(self.h, cache_path.encode() if cache_path else None, buf, len(buf)))
+        return json.loads(buf.value.decode() or "{}")
+
+    def tuning(self) -> dict:
+        v = (ctypes.c_int32 * len(self.TUNE_KNOBS))()
+        check(load().he_tuning_get(self.h, v, len(v)))
+        return dict(zip(self.TUNE_KNOBS, list(v)))
+
+    def set_tuning(self, **kw):
+        cur = self.tuning()
+        cur.update(kw)
+        v = (ctypes.c_int32 * len(self.TUNE_KNOBS))(*[cur[k] for k in self.TUNE_KNOBS])
+        check(load().he_tuning_set(self.h, v, len(v)))
+
     def encrypt(self, x, samples_per_ct: int, stride: int, enc_seed: int) -> Ct:
         """x: [n][H][W] (2-D) or [n][W] (1-D), numpy (host) or CUDA torch tensor (device)."""
         out = ctypes.c_void_p()

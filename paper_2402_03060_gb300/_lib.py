@@ -36,6 +36,16 @@ class he_kernel_stat(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("ops", ctypes.c_double)]
 
 
+class he_server_opts(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("max_wait_us", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64)]
+
+
+class he_server_stats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("cts", ctypes.c_uint64),
+                ("mean_batch", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("resident_bytes", ctypes.c_uint64)]
+
+
 class HeError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
@@ -80,6 +90,18 @@ SIGNATURES = {
     "he_ubench": (_int, [_vp, ctypes.POINTER(_dbl)]),
     "he_profile_begin": (_int, [_vp]),
     "he_profile_end": (_int, [_vp, ctypes.POINTER(he_kernel_stat), _sz, ctypes.POINTER(_sz)]),
+    "he_autotune": (_int, [_vp, ctypes.c_char_p, ctypes.c_char_p, _sz]),
+    "he_tuning_get": (_int, [_vp, ctypes.POINTER(_i32), _sz]),
+    "he_tuning_set": (_int, [_vp, ctypes.POINTER(_i32), _sz]),
+    "he_server_create": (_int, [ctypes.POINTER(he_server_opts), _pp]),
+    "he_server_add_model": (_int, [_vp, _vp, ctypes.POINTER(_u32)]),
+    "he_server_submit": (_int, [_vp, _u32, _vp, ctypes.POINTER(_u64)]),
+    "he_server_wait": (_int, [_vp, _u64, _u32, _pp, ctypes.POINTER(_dbl)]),
+    "he_server_stats_get": (_int, [_vp, _i32, ctypes.POINTER(he_server_stats)]),
+    "he_server_destroy": (None, [_vp]),
+    "he_server_simulate": (_int, [ctypes.POINTER(he_server_opts), _u32, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl),
+                                  _sz, ctypes.POINTER(_dbl), ctypes.POINTER(_u32), ctypes.POINTER(_u32),
+                                  ctypes.POINTER(_u64), ctypes.POINTER(_dbl)]),
     "he_last_error": (ctypes.c_char_p, []),
 }
 

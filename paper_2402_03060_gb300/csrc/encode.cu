@@ -11,29 +11,72 @@
 // in a fixed order (products first, one rounding per operation, no FMA), so
 // the result is bit-reproducible.
 #include "he_internal.cuh"
+#include "ntt_block.cuh"
 #include "ring.cuh"
 
-__device__ void block_fft(double *re, double *im, int logm, const double *__restrict__ w, bool inverse) {
-    const u32 M = 1u << logm;
-    for (int lgh = 0; lgh < logm; ++lgh) {
+// the FFT's share of one CTA: complex points [lo, lo + n) of M = N/2; split over
+// a 2-CTA cluster exactly when the limb's NTT is (N = 2^15: 256 KiB of points)
+template <int SPLIT>
+__device__ __forceinline__ Part fft_part(int logn) {
+    Part p;
+    p.split = SPLIT;
+    p.n = 1u << (logn - 1 - p.split);
+    p.lo = SPLIT ? (blockIdx.x & 1u) * p.n : 0u;
+    return p;
+}
+
+__device__ __forceinline__ void fft_bfly(double &ur, double &ui, double &xr, double &xi, double wr, double wi) {
+    const double vr = __dsub_rn(__dmul_rn(xr, wr), __dmul_rn(xi, wi));
+    const double vi = __dadd_rn(__dmul_rn(xr, wi), __dmul_rn(xi, wr));
+    xr = __dsub_rn(ur, vr);
+    xi = __dsub_rn(ui, vi);
+    ur = __dadd_rn(ur, vr);
+    ui = __dadd_rn(ui, vi);
+}
+
+// radix-2 decimation in time on bit-reversed input, length M = 2^logm; this CTA
+// holds points [p.lo, p.lo + p.n).  Stages with half-span h < p.n are local; when
+// the points are split over two CTAs the last stage (h = M/2) pairs local index j
+// of CTA 0 with local index j of CTA 1 through distributed shared memory.
+__device__ void part_fft(double *re, double *im, int logm, const double *__restrict__ w, bool inverse,
+                         const Part &p) {
+    const int nloc = logm - p.split;
+    for (int lgh = 0; lgh < nloc; ++lgh) {
         const u32 h = 1u << lgh;
-        for (u32 b = threadIdx.x; b < M / 2; b += blockDim.x) {
+        for (u32 b = threadIdx.x; b < p.n / 2; b += blockDim.x) {
             const u32 j = b & (h - 1);
             const u32 base = (b >> lgh) << (lgh + 1);
             const u32 k = j << (logm - 1 - lgh);
             const double wr = w[2 * k];
             const double wi = inverse ? -w[2 * k + 1] : w[2 * k + 1];
-            const double ur = re[base + j], ui = im[base + j];
-            const double xr = re[base + j + h], xi = im[base + j + h];
-            const double vr = __dsub_rn(__dmul_rn(xr, wr), __dmul_rn(xi, wi));
-            const double vi = __dadd_rn(__dmul_rn(xr, wi), __dmul_rn(xi, wr));
-            re[base + j] = __dadd_rn(ur, vr);
-            im[base + j] = __dadd_rn(ui, vi);
-            re[base + j + h] = __dsub_rn(ur, vr);
-            im[base + j + h] = __dsub_rn(ui, vi);
+            double ur = re[base + j], ui = im[base + j];
+            double xr = re[base + j + h], xi = im[base + j + h];
+            fft_bfly(ur, ui, xr, xi, wr, wi);
+            re[base + j] = ur;
+            im[base + j] = ui;
+            re[base + j + h] = xr;
+            im[base + j + h] = xi;
         }
         __syncthreads();
     }
+    if (!p.split) return;
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    double *re0 = cl.map_shared_rank(re, 0), *im0 = cl.map_shared_rank(im, 0);
+    double *re1 = cl.map_shared_rank(re, 1), *im1 = cl.map_shared_rank(im, 1);
+    const u32 j0 = p.lo / 2;
+    for (u32 j = j0 + threadIdx.x; j < j0 + p.n / 2; j += blockDim.x) {
+        const double wr = w[2 * j];
+        const double wi = inverse ? -w[2 * j + 1] : w[2 * j + 1];
+        double ur = re0[j], ui = im0[j], xr = re1[j], xi = im1[j];
+        fft_bfly(ur, ui, xr, xi, wr, wi);
+        re0[j] = ur;
+        im0[j] = ui;
+        re1[j] = xr;
+        im1[j] = xi;
+    }
+    cl.sync();
 }
 
 __device__ __forceinline__ u64 red_signed(i64 v, const PrimeDev &P) {
@@ -44,12 +87,13 @@ __device__ __forceinline__ u64 red_signed(i64 v, const PrimeDev &P) {
 // (limb l < lpq: data prime l; limb l >= lpq: special prime pbase + l - lpq)
 __device__ void encode_finish(const double *re, const double *im, u64 *out, u32 lp, int logn, double f,
                               const double *__restrict__ tw, const PrimeDev *__restrict__ pd, int *err,
-                              u32 lpq = 0xffffffffu, u32 pbase = 0) {
+                              const Part &pt, u32 lpq = 0xffffffffu, u32 pbase = 0) {
     const u32 N = 1u << logn, M = N / 2;
-    for (u32 k = threadIdx.x; k < M; k += blockDim.x) {
+    for (u32 k = pt.lo + threadIdx.x; k < pt.lo + pt.n; k += blockDim.x) {
         const double tr = tw[2 * k], ti = -tw[2 * k + 1];
-        const double cr = __dsub_rn(__dmul_rn(re[k], tr), __dmul_rn(im[k], ti));
-        const double ci = __dadd_rn(__dmul_rn(re[k], ti), __dmul_rn(im[k], tr));
+        const double xr = re[k - pt.lo], xi = im[k - pt.lo];
+        const double cr = __dsub_rn(__dmul_rn(xr, tr), __dmul_rn(xi, ti));
+        const double ci = __dadd_rn(__dmul_rn(xr, ti), __dmul_rn(xi, tr));
         const double a = __dmul_rn(cr, f), b = __dmul_rn(ci, f);
         if (!(fabs(a) < 9.2e18) || !(fabs(b) < 9.2e18)) {
             atomicExch(err, 1);
@@ -65,6 +109,7 @@ __device__ void encode_finish(const double *re, const double *im, u64 *out, u32 
 }
 
 // dense slot vectors z[v][M] -> coefficient residues out[v][lp][N]
+template <int SPLIT>
 __global__ void __launch_bounds__(1024) encode_dense_kernel(u64 *out, const double *__restrict__ z, u32 lp,
                                                             int logn, double f, const double *__restrict__ fw,
                                                             const double *__restrict__ ft,
@@ -72,20 +117,25 @@ __global__ void __launch_bounds__(1024) encode_dense_kernel(u64 *out, const doub
                                                             const PrimeDev *__restrict__ pd, int *err) {
     extern __shared__ double smd[];
     const u32 N = 1u << logn, M = N / 2;
-    double *re = smd, *im = smd + M;
-    const double *zv = z + (size_t)blockIdx.x * M;
+    const Part pt = fft_part<SPLIT>(logn);
+    const u32 v = part_row<SPLIT>();
+    double *re = smd, *im = smd + pt.n;
+    const double *zv = z + (size_t)v * M;
     for (u32 j = threadIdx.x; j < M; j += blockDim.x) {
-        u32 p = pos_br[j];
-        re[p] = zv[j];
-        im[p] = 0.0;
+        const u32 p = pos_br[j] - pt.lo;
+        if (p < pt.n) {
+            re[p] = zv[j];
+            im[p] = 0.0;
+        }
     }
     __syncthreads();
-    block_fft(re, im, logn - 1, fw, true);
-    encode_finish(re, im, out + (size_t)blockIdx.x * lp * N, lp, logn, f, ft, pd, err);
+    part_fft(re, im, logn - 1, fw, true, pt);
+    encode_finish(re, im, out + (size_t)v * lp * N, lp, logn, f, ft, pd, err, pt);
 }
 
 // sparse slot vectors: vector v has entries [off[v], off[v+1]) of (pos, val),
 // replicated at pos + s*stride for s < ns.
+template <int SPLIT>
 __global__ void __launch_bounds__(1024) encode_sparse_kernel(u64 *out, const u32 *__restrict__ off,
                                                              const u32 *__restrict__ pos,
                                                              const double *__restrict__ val, u32 stride, u32 ns,
@@ -96,26 +146,32 @@ __global__ void __launch_bounds__(1024) encode_sparse_kernel(u64 *out, const u32
                                                              u32 pbase) {
     extern __shared__ double smd[];
     const u32 N = 1u << logn, M = N / 2;
-    double *re = smd, *im = smd + M;
-    for (u32 j = threadIdx.x; j < M; j += blockDim.x) {
+    const Part pt = fft_part<SPLIT>(logn);
+    const u32 v = part_row<SPLIT>();
+    double *re = smd, *im = smd + pt.n;
+    for (u32 j = threadIdx.x; j < pt.n; j += blockDim.x) {
         re[j] = 0.0;
         im[j] = 0.0;
     }
     __syncthreads();
-    const u32 e0 = off[blockIdx.x], e1 = off[blockIdx.x + 1];
+    const u32 e0 = off[v], e1 = off[v + 1];
     const u32 cnt = (e1 - e0) * ns;
     for (u32 x = threadIdx.x; x < cnt; x += blockDim.x) {
         u32 e = e0 + x / ns, s = x % ns;
         u32 slot = pos[e] + s * stride;
-        if (slot < M) re[pos_br[slot]] = val[e];
+        if (slot < M) {
+            const u32 p = pos_br[slot] - pt.lo;
+            if (p < pt.n) re[p] = val[e];
+        }
     }
     __syncthreads();
-    block_fft(re, im, logn - 1, fw, true);
-    encode_finish(re, im, out + (size_t)blockIdx.x * lp * N, lp, logn, f, ft, pd, err, lpq, pbase);
+    part_fft(re, im, logn - 1, fw, true, pt);
+    encode_finish(re, im, out + (size_t)v * lp * N, lp, logn, f, ft, pd, err, pt, lpq, pbase);
 }
 
 // decode: coefficient-form limb q_0 of m (rows [v][N], residues) -> selected slots
 // out[v][s][i] = slot (s*stride + i), i < nper, s < ns
+template <int SPLIT>
 __global__ void __launch_bounds__(1024) decode_kernel(double *out, const u64 *__restrict__ m, double scale,
                                                       u32 stride, u32 ns, u32 nper, int logn,
                                                       const double *__restrict__ fw, const double *__restrict__ ft,
@@ -123,25 +179,33 @@ __global__ void __launch_bounds__(1024) decode_kernel(double *out, const u64 *__
     extern __shared__ double smd[];
     const u32 N = 1u << logn, M = N / 2;
     const int logm = logn - 1;
-    double *re = smd, *im = smd + M;
-    const u64 *mv = m + (size_t)blockIdx.x * N;
-    for (u32 k = threadIdx.x; k < M; k += blockDim.x) {
+    const Part pt = fft_part<SPLIT>(logn);
+    const u32 v = part_row<SPLIT>();
+    double *re = smd, *im = smd + pt.n;
+    const u64 *mv = m + (size_t)v * N;
+    // local point p receives coefficient pair k = brev(p) (bit reversal is an involution)
+    for (u32 p = pt.lo + threadIdx.x; p < pt.lo + pt.n; p += blockDim.x) {
+        const u32 k = __brev(p) >> (32 - logm);
         u64 a = mv[k], b = mv[k + M];
         i64 sa = a > q0 / 2 ? (i64)a - (i64)q0 : (i64)a;
         i64 sb = b > q0 / 2 ? (i64)b - (i64)q0 : (i64)b;
         double ar = __ddiv_rn((double)sa, scale), ai = __ddiv_rn((double)sb, scale);
         double tr = ft[2 * k], ti = ft[2 * k + 1];
-        u32 p = __brev(k) >> (32 - logm);
-        re[p] = __dsub_rn(__dmul_rn(ar, tr), __dmul_rn(ai, ti));
-        im[p] = __dadd_rn(__dmul_rn(ar, ti), __dmul_rn(ai, tr));
+        re[p - pt.lo] = __dsub_rn(__dmul_rn(ar, tr), __dmul_rn(ai, ti));
+        im[p - pt.lo] = __dadd_rn(__dmul_rn(ar, ti), __dmul_rn(ai, tr));
     }
     __syncthreads();
-    block_fft(re, im, logm, fw, false);
-    double *ov = out + (size_t)blockIdx.x * ns * nper;
+    part_fft(re, im, logm, fw, false, pt);
+    double *ov = out + (size_t)v * ns * nper;
     for (u32 x = threadIdx.x; x < ns * nper; x += blockDim.x) {
         u32 s = x / nper, i = x % nper;
         u32 slot = s * stride + i;
-        ov[x] = slot < M ? re[pos_nat[slot]] : 0.0;
+        if (slot < M) {
+            const u32 p = pos_nat[slot] - pt.lo;
+            if (p < pt.n) ov[x] = re[p];
+        } else if (pt.lo == 0) {
+            ov[x] = 0.0;
+        }
     }
 }
 
@@ -189,12 +253,15 @@ __global__ void enc_combine_kernel(u64 *ct, const u64 *__restrict__ u, const u64
 
 // ------------------------------------------------------------------ host
 void encode_init(Ctx *c) {
-    CUDA_TRY(cudaFuncSetAttribute(encode_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    CUDA_TRY(cudaFuncSetAttribute(encode_sparse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    CUDA_TRY(cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    for (const void *f : {(const void *)encode_dense_kernel<0>, (const void *)encode_dense_kernel<1>,
+                          (const void *)encode_sparse_kernel<0>, (const void *)encode_sparse_kernel<1>,
+                          (const void *)decode_kernel<0>, (const void *)decode_kernel<1>})
+        CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
 }
 
 static u32 fft_threads(u32 M) { return M >= 2048 ? 1024 : (M / 2 > 32 ? M / 2 : 32); }
+// re and im of the points one CTA holds
+static size_t fft_smem(const Ctx *c, int split) { return (size_t)(c->N / 2 >> split) * 16; }
 
 static void check_err(Ctx *c) {
     int h = 0;
@@ -211,8 +278,10 @@ void encode_dense(Ctx *c, u64 *out, const double *z, u32 nv, double scale, u32 l
     const u32 M = c->N / 2;
     double f = scale / (double)M;
     prof_begin(c);
-    encode_dense_kernel<<<nv, fft_threads(M), (size_t)M * 16, c->stream>>>(out, z, lp, c->logn, f, c->fft_w, c->fft_t,
-                                                                           c->slot_pos_br, c->pdev, c->err_flag);
+    launch_parts(c, encode_dense_kernel<0>, encode_dense_kernel<1>, dim3(nv), ntt_min_split(c->logn), fft_threads(M >> ntt_min_split(c->logn)),
+                 fft_smem(c, ntt_min_split(c->logn)), out, z, lp,
+                 c->logn, f, (const double *)c->fft_w, (const double *)c->fft_t, (const u32 *)c->slot_pos_br,
+                 (const PrimeDev *)c->pdev, c->err_flag);
     note_launch(c, "encode_dense");
     ntt_forward(c, out, rows_regular(nv * lp, lp, lp, 0));
     if (check) check_err(c);
@@ -238,10 +307,12 @@ void encode_sparse(Ctx *c, u64 *out, const std::string &key, const std::vector<u
     u64 *d = tmp.p;
     double f = scale / (double)M;
     prof_begin(c);
-    encode_sparse_kernel<<<nv, fft_threads(M), (size_t)M * 16, c->stream>>>(
-        out, reinterpret_cast<const u32 *>(d + o_off), reinterpret_cast<const u32 *>(d + o_pos),
-        reinterpret_cast<const double *>(d + o_val), stride, ns, lp, c->logn, f, c->fft_w, c->fft_t, c->slot_pos_br,
-        c->pdev, c->err_flag, lpq, c->L1);
+    launch_parts(c, encode_sparse_kernel<0>, encode_sparse_kernel<1>, dim3(nv), ntt_min_split(c->logn), fft_threads(M >> ntt_min_split(c->logn)),
+                 fft_smem(c, ntt_min_split(c->logn)), out,
+                 reinterpret_cast<const u32 *>(d + o_off), reinterpret_cast<const u32 *>(d + o_pos),
+                 reinterpret_cast<const double *>(d + o_val), stride, ns, lp, c->logn, f, (const double *)c->fft_w,
+                 (const double *)c->fft_t, (const u32 *)c->slot_pos_br, (const PrimeDev *)c->pdev, c->err_flag, lpq,
+                 c->L1);
     note_launch(c, "encode_sparse");
     ntt_forward(c, out, rows_regular(nv * lp, lp, lpq, c->L1));
     check_err(c);   // also keeps the host staging vector alive until the upload is done
@@ -276,7 +347,9 @@ void decrypt_decode(Ctx *c, double *out, const u64 *ct, u32 B, u32 lp, double sc
     note_launch(c, "dec_combine");
     ntt_inverse(c, m.p, rows_regular(B, 1, 1, 0));
     prof_begin(c);
-    decode_kernel<<<B, fft_threads(M), (size_t)M * 16, c->stream>>>(out, m.p, scale, stride, ns, nper, c->logn,
-                                                                     c->fft_w, c->fft_t, c->slot_pos, c->primes[0]);
+    launch_parts(c, decode_kernel<0>, decode_kernel<1>, dim3(B), ntt_min_split(c->logn), fft_threads(M >> ntt_min_split(c->logn)),
+                 fft_smem(c, ntt_min_split(c->logn)), out,
+                 (const u64 *)m.p, scale, stride, ns, nper, c->logn, (const double *)c->fft_w,
+                 (const double *)c->fft_t, (const u32 *)c->slot_pos, c->primes[0]);
     note_launch(c, "decode");
 }

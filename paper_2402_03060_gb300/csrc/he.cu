@@ -255,7 +255,7 @@ void ntt_init_attrs(Ctx *c);
 void keyswitch_init(Ctx *c);
 
 Ctx *ctx_create(const he_params *p) {
-    if (!p || p->log2n < 4 || p->log2n > 14 || p->n_data < 1 || p->n_data > 32 || p->n_special < 1 ||
+    if (!p || p->log2n < 4 || p->log2n > 15 || p->n_data < 1 || p->n_data > 32 || p->n_special < 1 ||
         p->n_special > 4 || !p->prime_bits || p->dnum < 1 || p->dnum > p->n_data)
         throw HeError(HE_EINVAL, "he_params out of range");
     if (p->n_data + p->n_special > HE_MAX_PRIMES) throw HeError(HE_EINVAL, "too many primes");

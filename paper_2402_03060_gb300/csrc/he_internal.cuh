@@ -13,6 +13,7 @@
 
 #include <map>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -188,7 +189,23 @@ struct Layout {
 };
 enum { PREV_INPUT = 0, PREV_CONV = 1, PREV_POOL = 2, PREV_FLAT = 3, PREV_FC = 4 };
 
+// knobs of the autotuner (tune.cu): launch shapes that change speed, never results
+enum {
+    TUNE_NTT = 0,      // split limbs over 2-CTA clusters: 0 / 1
+    TUNE_MODDOWN,      // the same for the fused ModDown kernel
+    TUNE_RESCALE,      // the same for the fused rescale kernel
+    TUNE_MAC_GROUP,    // outputs per MAC launch (accumulators held in registers)
+    TUNE_LAZY_BT,      // ciphertexts per thread in the hoisted key-switch accumulation
+    TUNE_LAZY_ORDER,   // its grid order: 0 coefficient tiles fastest, 1 ciphertext groups fastest
+    TUNE_COUNT
+};
+
 struct Ctx : std::enable_shared_from_this<Ctx> {
+    // Serialises host-side use of the context (pools, table cache, stream order of
+    // multi-launch operations) between threads: every C entry point and the
+    // serving loop hold it while they enqueue work or release buffers.
+    std::recursive_mutex mu;
+    int tuned[TUNE_COUNT] = {-1, -1, -1, -1, -1, -1};   // -1: default
     // parameters
     int logn = 0;
     u32 N = 0, L1 = 0, K = 0, dnum = 0, alpha = 0;
@@ -255,3 +272,14 @@ RowSet rows_list(Ctx *c, const std::string &key, const std::vector<u32> &packed)
 
 // keyswitch.cu, he.cu, layers.cu: see the respective files
 std::string fmt(const char *f, ...);
+
+// holds a context's lock for the enclosing scope
+struct CtxLock {
+    std::lock_guard<std::recursive_mutex> g;
+    explicit CtxLock(Ctx *c) : g(c->mu) {}
+};
+
+// a tuned knob, or dflt when it was not tuned
+static inline int tune_get(const Ctx *c, int knob, int dflt) { return c->tuned[knob] >= 0 ? c->tuned[knob] : dflt; }
+// limb split of an NTT-carrying kernel family: tuned, but never below what N requires
+int tune_split(const Ctx *c, int knob);

@@ -133,31 +133,32 @@ __global__ void ks_lazy_kernel(u64 *acc, const u64 *__restrict__ D, const u64 *_
 //   A_s = sigma_g(A'_s),  A'_s = sum_j D_j (o) K'_j  (+ P*c0 on poly 0),
 // i.e. every thread reads its digits D_j[b][t][n] and c0, c1 once (coalesced) and reuses them
 // for all S steps; the permutation is applied on the write: A_s[galois_src(n, g^-1)] = A'_s[n].
-// Grid: x = n-tile (fastest, so the scattered writes of one limb merge in L2), y = ciphertext, z = limb.
-// Each thread handles LAZY_BT ciphertexts of one coefficient so that every key word it
-// loads serves LAZY_BT products.
-#define LAZY_BT 2
-#define LAZY_MAXD 8
+// Grid: z = limb; x/y = n-tile and ciphertext group, n-tile fastest (order 0: the scattered
+// writes of one limb merge in L2) or ciphertext group fastest (order 1: consecutive CTAs
+// read the same key slice).  Each thread handles BT ciphertexts of one coefficient so that
+// every key word it loads serves BT products; MAXD >= the number of digits.
+template <int BT, int MAXD>
 __global__ void __launch_bounds__(256, 2) ks_lazy_perm_kernel(u64 *acc, const u64 *__restrict__ D,
                                                             const u64 *__restrict__ x, KeyList kl, u32 S, u32 B,
-                                                            u32 beta, u32 lp, u32 K, u32 L1, int logn,
+                                                            u32 beta, u32 lp, u32 K, u32 L1, int logn, int order,
                                                             const u64 *__restrict__ pq,
                                                             const PrimeDev *__restrict__ pd) {
     const u32 N = 1u << logn;
-    const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 ntile = order ? blockIdx.y : blockIdx.x, bgrp = order ? blockIdx.x : blockIdx.y;
+    const u32 n = ntile * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const u32 b0 = blockIdx.y * LAZY_BT, t = blockIdx.z;
+    const u32 b0 = bgrp * BT, t = blockIdx.z;
     const u32 E = lp + K;
     const u32 pt = t < lp ? t : L1 + (t - lp);
     const PrimeDev P = pd[pt];
-    u64 d[LAZY_BT][LAZY_MAXD];
-    u64 pc0[LAZY_BT], pc1[LAZY_BT];   // P*c0, P*c1 on data limbs
+    u64 d[BT][MAXD];
+    u64 pc0[BT], pc1[BT];   // P*c0, P*c1 on data limbs
 #pragma unroll
-    for (int u = 0; u < LAZY_BT; ++u) {
+    for (int u = 0; u < BT; ++u) {
         const u32 b = b0 + u < B ? b0 + u : B - 1;   // clamp: duplicates are computed but not stored
         const u64 *Db = D + ((size_t)b * beta * E + t) * N + n;
 #pragma unroll
-        for (u32 j = 0; j < LAZY_MAXD; ++j) d[u][j] = j < beta ? Db[(size_t)j * E * N] : 0;
+        for (u32 j = 0; j < MAXD; ++j) d[u][j] = j < beta ? Db[(size_t)j * E * N] : 0;
         const u64 *xb = x + (size_t)b * 2 * lp * N;
         pc0[u] = pc1[u] = 0;
         if (t < lp) {
@@ -169,18 +170,18 @@ __global__ void __launch_bounds__(256, 2) ks_lazy_perm_kernel(u64 *acc, const u6
     for (u32 s = 0; s < S; ++s) {
         const u32 g = kl.g[s];
         u32 dst = n;
-        u64 k0[LAZY_MAXD], k1[LAZY_MAXD];
+        u64 k0[MAXD], k1[MAXD];
         if (g != 1) {
             const u64 *key = kl.keyp[s] + (size_t)pt * N + n;
 #pragma unroll
-            for (u32 j = 0; j < LAZY_MAXD; ++j) {
+            for (u32 j = 0; j < MAXD; ++j) {
                 k0[j] = j < beta ? __ldg(key + (size_t)j * 2 * kstride) : 0;
                 k1[j] = j < beta ? __ldg(key + (size_t)j * 2 * kstride + kstride) : 0;
             }
             dst = galois_src(n, kl.ginv[s], logn);
         }
 #pragma unroll
-        for (int u = 0; u < LAZY_BT; ++u) {
+        for (int u = 0; u < BT; ++u) {
             if (b0 + u >= B) break;
             u64 *o = acc + (((size_t)s * B + b0 + u) * 2 * E + t) * N;
             if (g == 1) {
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(256, 2) ks_lazy_perm_kernel(u64 *acc, const u6
             }
             Acc128 a0 = {pc0[u], 0}, a1 = {0, 0};
 #pragma unroll
-            for (u32 j = 0; j < LAZY_MAXD; ++j) {
+            for (u32 j = 0; j < MAXD; ++j) {
                 if (j < beta) {
                     mac128(a0, d[u][j], k0[j]);
                     mac128(a1, d[u][j], k1[j]);
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(256, 2) ks_lazy_perm_kernel(u64 *acc, const u6
     }
 }
 
+template <int SPLIT>
 __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, const u64 *__restrict__ acc,
                                                        const u64 *__restrict__ addend, size_t addend_bstride,
                                                        u32 add_mask, KeyList kl, u32 B, u32 lp, u32 K, u32 L1,
@@ -210,13 +212,14 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, cons
                                                        const PrimeDev *__restrict__ pd) {
     extern __shared__ u64 sm[];
     const u32 N = 1u << logn;
-    const u32 i = blockIdx.x, k = blockIdx.y;
+    const Part pt = ntt_part<SPLIT>(logn);
+    const u32 i = part_row<SPLIT>(), k = blockIdx.y;
     const u32 s = blockIdx.z / B, b = blockIdx.z % B;
     const u32 E = lp + K;
     const PrimeDev P = pd[i];
     const u64 *ab = acc + (((size_t)s * B + b) * 2 + k) * E * N;
     // mdtab: phinv[K], phinv_s[K], phmod[K][L1], Pinv[L1], Pinv_s[L1]
-    for (u32 n = threadIdx.x; n < N; n += blockDim.x) {
+    for (u32 n = pt.lo + threadIdx.x; n < pt.lo + pt.n; n += blockDim.x) {
         u64 v;
         if (K == 1) {
             v = reduce64(ab[(size_t)lp * N + n], P);
@@ -229,44 +232,46 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, cons
             }
             v = reduce128(a.lo, a.hi, P);
         }
-        sm[spad(n)] = v;
+        sm[spad(n - pt.lo)] = v;
     }
     __syncthreads();
-    block_ntt_fwd(sm, logn, tw_all + (size_t)i * 4 * N, P.q);
+    part_ntt_fwd(sm, pt, logn, tw_all + (size_t)i * 4 * N, P.q);
     const u64 pinv = mdtab[2 * K + (size_t)K * L1 + i];
     const u64 pinvs = mdtab[2 * K + (size_t)K * L1 + L1 + i];
     const bool add = addend && ((add_mask >> k) & 1);
     const u32 g = kl.g[s];
     const u64 *adb = add ? addend + (size_t)b * addend_bstride + ((size_t)k * lp + i) * N : nullptr;
     u64 *ob = out + ((((size_t)s * B + b) * 2 + k) * lp + i) * N;
-    for (u32 n = threadIdx.x; n < N; n += blockDim.x) {
-        u64 o = mul_shoup(sub_mod(ab[(size_t)i * N + n], sm[spad(n)], P.q), pinv, pinvs, P.q);
+    for (u32 n = pt.lo + threadIdx.x; n < pt.lo + pt.n; n += blockDim.x) {
+        u64 o = mul_shoup(sub_mod(ab[(size_t)i * N + n], sm[spad(n - pt.lo)], P.q), pinv, pinvs, P.q);
         if (add) o = add_mod(o, adb[g == 1 ? n : galois_src(n, g, logn)], P.q);
         ob[n] = o;
     }
 }
 
+template <int SPLIT>
 __global__ void __launch_bounds__(NTT_MAX_THREADS) rescale_kernel(u64 *out, const u64 *__restrict__ in,
                                                        const u64 *__restrict__ top, u32 lp, int logn,
                                                        const u64 *__restrict__ rtab, const u64 *__restrict__ tw_all,
                                                        const PrimeDev *__restrict__ pd) {
     extern __shared__ u64 sm[];
     const u32 N = 1u << logn;
-    const u32 i = blockIdx.x, k = blockIdx.y, b = blockIdx.z;
+    const Part pt = ntt_part<SPLIT>(logn);
+    const u32 i = part_row<SPLIT>(), k = blockIdx.y, b = blockIdx.z;
     const PrimeDev P = pd[i];
     const u64 qt = pd[lp - 1].q;
     const u64 *tb = top + ((size_t)b * 2 + k) * N;
-    for (u32 n = threadIdx.x; n < N; n += blockDim.x) {
+    for (u32 n = pt.lo + threadIdx.x; n < pt.lo + pt.n; n += blockDim.x) {
         u64 v = tb[n];
-        sm[spad(n)] = v > qt / 2 ? neg_mod(reduce64(qt - v, P), P.q) : reduce64(v, P);
+        sm[spad(n - pt.lo)] = v > qt / 2 ? neg_mod(reduce64(qt - v, P), P.q) : reduce64(v, P);
     }
     __syncthreads();
-    block_ntt_fwd(sm, logn, tw_all + (size_t)i * 4 * N, P.q);
+    part_ntt_fwd(sm, pt, logn, tw_all + (size_t)i * 4 * N, P.q);
     const u64 w = rtab[i], ws = rtab[lp - 1 + i];
     const u64 *ib = in + (((size_t)b * 2 + k) * lp + i) * N;
     u64 *ob = out + (((size_t)b * 2 + k) * (lp - 1) + i) * N;
-    for (u32 n = threadIdx.x; n < N; n += blockDim.x)
-        ob[n] = mul_shoup(sub_mod(ib[n], sm[spad(n)], P.q), w, ws, P.q);
+    for (u32 n = pt.lo + threadIdx.x; n < pt.lo + pt.n; n += blockDim.x)
+        ob[n] = mul_shoup(sub_mod(ib[n], sm[spad(n - pt.lo)], P.q), w, ws, P.q);
 }
 
 // ------------------------------------------------------------------ host
@@ -289,8 +294,10 @@ static void set_big_smem(const void *fn) {
 }
 
 void keyswitch_init(Ctx *c) {
-    set_big_smem((const void *)moddown_kernel);
-    set_big_smem((const void *)rescale_kernel);
+    set_big_smem((const void *)moddown_kernel<0>);
+    set_big_smem((const void *)moddown_kernel<1>);
+    set_big_smem((const void *)rescale_kernel<0>);
+    set_big_smem((const void *)rescale_kernel<1>);
 }
 
 u32 ks_digits(const Ctx *c, u32 lp) { return (lp + c->alpha - 1) / c->alpha; }
@@ -433,14 +440,26 @@ static const u64 *pmod_table(Ctx *c) {
 void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u32 S, u32 B, u32 lp) {
     const u32 N = c->N, E = lp + c->K;
     const u32 beta = ks_digits(c, lp);
-    bool perm = beta <= LAZY_MAXD && (B + LAZY_BT - 1) / LAZY_BT <= 65535;
+    const int bt = tune_get(c, TUNE_LAZY_BT, 2), order = tune_get(c, TUNE_LAZY_ORDER, 0);
+    const int maxd = beta <= 2 ? 2 : beta <= 4 ? 4 : 8;
+    bool perm = beta <= 8 && (B + bt - 1) / bt <= 65535;
     for (u32 s = 0; s < S; ++s)
         if (kl.g[s] != 1 && !kl.keyp[s]) perm = false;
     prof_begin(c);
     if (perm) {
-        dim3 grid((N + 255) / 256, (B + LAZY_BT - 1) / LAZY_BT, E);
-        ks_lazy_perm_kernel<<<grid, 256, 0, c->stream>>>(acc, D, x, kl, S, B, beta, lp, c->K, c->L1, c->logn,
-                                                          pmod_table(c), c->pdev);
+        const u32 nt = (N + 255) / 256, nb = (B + bt - 1) / bt;
+        dim3 grid(order ? nb : nt, order ? nt : nb, E);
+#define LAZY_LAUNCH(BTV, MD)                                                                                     \
+    ks_lazy_perm_kernel<BTV, MD><<<grid, 256, 0, c->stream>>>(acc, D, x, kl, S, B, beta, lp, c->K, c->L1, c->logn, \
+                                                              order, pmod_table(c), c->pdev)
+        if (maxd == 8) {
+            if (bt == 1) LAZY_LAUNCH(1, 8); else LAZY_LAUNCH(2, 8);
+        } else if (maxd == 4) {
+            if (bt == 1) LAZY_LAUNCH(1, 4); else if (bt == 2) LAZY_LAUNCH(2, 4); else LAZY_LAUNCH(4, 4);
+        } else {
+            if (bt == 1) LAZY_LAUNCH(1, 2); else if (bt == 2) LAZY_LAUNCH(2, 2); else LAZY_LAUNCH(4, 2);
+        }
+#undef LAZY_LAUNCH
     } else {
         dim3 grid((N + 255) / 256, E, S * B);
         ks_lazy_kernel<<<grid, 256, 0, c->stream>>>(acc, D, x, kl, B, beta, lp, c->K, c->L1, c->logn, pmod_table(c),
@@ -464,9 +483,10 @@ void ks_moddown(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bst
     ntt_inverse(c, acc, rows_list(c, key, rows));
     dim3 grid(lp, 2, S * B);
     prof_begin(c);
-    moddown_kernel<<<grid, ntt_threads(N), (size_t)ntt_smem_words(N) * 8, c->stream>>>(out, acc, addend, addend_bstride, add_mask, kl, B,
-                                                                      lp, c->K, c->L1, c->logn, moddown_table(c),
-                                                                      c->tw, c->pdev);
+    const int sp = tune_split(c, TUNE_MODDOWN);
+    launch_parts(c, moddown_kernel<0>, moddown_kernel<1>, grid, sp, ntt_part_threads(c->logn, sp), ntt_part_smem(c->logn, sp), out, (const u64 *)acc,
+                 addend, addend_bstride, add_mask, kl, B, lp, c->K, c->L1, c->logn, moddown_table(c),
+                 (const u64 *)c->tw, (const PrimeDev *)c->pdev);
     note_launch(c, "moddown",
                 8.0 * N * (double)S * B * (2.0 * E + (addend ? __builtin_popcount(add_mask) : 0) * lp + 2.0 * lp),
                 (double)S * B * 2 * lp * (N / 2) * c->logn);
@@ -481,7 +501,8 @@ void rescale_batch(Ctx *c, u64 *out, const u64 *in, u32 B, u32 lp) {
     ntt_inverse(c, top.p, rows_regular(B * 2, 1, 0, lp - 1));
     dim3 grid(lp - 1, 2, B);
     prof_begin(c);
-    rescale_kernel<<<grid, ntt_threads(N), (size_t)ntt_smem_words(N) * 8, c->stream>>>(out, in, top.p, lp, c->logn,
-                                                                      rescale_table(c, lp), c->tw, c->pdev);
+    const int sp = tune_split(c, TUNE_RESCALE);
+    launch_parts(c, rescale_kernel<0>, rescale_kernel<1>, grid, sp, ntt_part_threads(c->logn, sp), ntt_part_smem(c->logn, sp), out, in,
+                 (const u64 *)top.p, lp, c->logn, rescale_table(c, lp), (const u64 *)c->tw, (const PrimeDev *)c->pdev);
     note_launch(c, "rescale", 8.0 * N * (double)B * 2 * (lp + 1 + lp - 1), (double)B * 2 * (lp - 1) * (N / 2) * c->logn);
 }

@@ -11,23 +11,13 @@
 #include <cmath>
 #include <set>
 
-#include "ops.cuh"
+#include "model.cuh"
 
 // ------------------------------------------------------------------ helpers
 struct Feat {
     Cts x;        // CH*B ciphertexts
     u32 CH = 1, B = 1;
     Cts chan(Ctx *c, u32 ch) const { return cts_view(x, (size_t)ch * B * cts_ct_words(c, x.lp), B); }
-};
-
-// cached encoded plaintexts of a compiled model (nullptr: encode every call)
-struct PtCache {
-    std::map<std::string, DBuf> pts;
-};
-
-struct LayerSpec {
-    u32 op = 0, ci = 0, co = 0, k = 0, s = 1;
-    std::vector<double> w, b;
 };
 
 static std::vector<u32> valid_positions(const Layout &L, u32 Hout, u32 Wout, u32 Iout) {
@@ -376,11 +366,6 @@ static Feat layer_fc(Ctx *c, const Feat &in, const LayerSpec &sp, PtCache *pc, c
 }
 
 // ------------------------------------------------------------------ planner
-struct Plan {
-    u32 stride = 0, levels = 0;
-    std::vector<int> steps;
-};
-
 // Sec. V: the slots one sample needs = max(input W*H (Theorem 1 keeps every later
 // valid value inside it), CH*W*H of a flatten, W_vec of an FC); levels and steps.
 static Plan plan_layers(const std::vector<LayerSpec> &ls, u32 Wi, u32 Hi) {
@@ -507,40 +492,75 @@ static Feat run_layers(Ctx *c, Feat f, const std::vector<LayerSpec> &ls, PtCache
 }
 
 // ------------------------------------------------------------------ model
-struct ModelGraph {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    Cts in, out;
-    u64 kernels = 0;   // kernel nodes in the graph
-};
+void model_check_input(const he_model *m, const Cts &x) {
+    const Layout &L = x.lay;
+    if (L.W_img != m->W_img || L.H_img != m->H_img || L.n_samples != m->spc || L.stride < m->plan.stride ||
+        L.prev != PREV_INPUT)
+        throw HeError(HE_EINVAL, "ciphertext layout does not match the model");
+    if (x.lp < m->plan.levels + 1) throw HeError(HE_ELEVEL, "not enough levels for this model");
+}
 
-// Handles share ownership of their context: it is torn down when the last
-// context, ciphertext or model handle that refers to it has been freed.
-struct he_model {
-    std::shared_ptr<Ctx> keep;
-    Ctx *c = nullptr;
-    std::vector<LayerSpec> layers;
-    u32 W_img = 0, H_img = 0, spc = 0;
-    Plan plan;
-    PtCache pc;
-    Pool gpool;                            // private pool of the captured graphs
-    std::map<std::string, ModelGraph> graphs;
-    ~he_model() {
-        for (auto &kv : graphs) {
-            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-            if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+Cts model_infer(he_model *m, const Cts &x, bool use_graph) {
+    Ctx *c = m->c;
+    model_check_input(m, x);
+    Feat f;
+    f.x = x;
+    f.CH = 1;
+    f.B = x.B;
+    if (!use_graph) return run_layers(c, f, m->layers, &m->pc).x;
+    std::string key = fmt("%u:%u:%.17g", x.B, x.lp, x.scale);
+    auto it = m->graphs.find(key);
+    const size_t inw = (size_t)x.B * cts_ct_words(c, x.lp);
+    if (it == m->graphs.end()) {
+        // eager run (fills the plaintext cache and sizes the private pool), then capture
+        run_layers(c, f, m->layers, &m->pc);
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        ModelGraph g;
+        c->active = &m->gpool;
+        try {
+            g.in = cts_alloc(c, x.B, x.lp, x.scale, x.lay);
+            Feat fi = f;
+            fi.x = g.in;
+            {   // warm the private pool with one run of the same shapes
+                Feat w = run_layers(c, fi, m->layers, &m->pc);
+            }
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            const bool prof = c->profiling;
+            c->profiling = false;   // no event records inside the graph
+            const u64 before = c->launches;
+            CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+            Feat r;
+            try {
+                r = run_layers(c, fi, m->layers, &m->pc);
+            } catch (...) {
+                cudaGraph_t tmpg = nullptr;
+                cudaStreamEndCapture(c->stream, &tmpg);
+                if (tmpg) cudaGraphDestroy(tmpg);
+                c->profiling = prof;
+                throw;
+            }
+            c->profiling = prof;
+            g.kernels = c->launches - before;
+            c->launches = before;
+            CUDA_TRY(cudaStreamEndCapture(c->stream, &g.graph));
+            CUDA_TRY(cudaGraphInstantiate(&g.exec, g.graph, 0));
+            g.out = r.x;   // keeps the output buffer alive in the private pool
+        } catch (...) {
+            c->active = nullptr;
+            throw;
         }
-        graphs.clear();
-        pc.pts.clear();
-        gpool.release_all();
+        c->active = nullptr;
+        it = m->graphs.emplace(key, std::move(g)).first;
     }
-};
-
-struct he_ct {
-    std::shared_ptr<Ctx> keep;   // declared first: destroyed after the buffers of x
-    Ctx *c = nullptr;
-    Cts x;
-};
+    ModelGraph &g = it->second;
+    CUDA_TRY(cudaMemcpyAsync(g.in.data(), x.data(), inw * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaGraphLaunch(g.exec, c->stream));
+    c->launches += g.kernels;
+    Cts o = cts_alloc(c, g.out.B, g.out.lp, g.out.scale, g.out.lay);
+    CUDA_TRY(cudaMemcpyAsync(o.data(), g.out.data(), (size_t)g.out.B * cts_ct_words(c, g.out.lp) * 8,
+                             cudaMemcpyDeviceToDevice, c->stream));
+    return o;
+}
 
 // ------------------------------------------------------------------ C ABI
 static thread_local std::string g_err;
@@ -574,7 +594,7 @@ static Ctx *CX(he_ctx *h) {
     return h->c.get();
 }
 
-static he_ct *wrap(Ctx *c, const Cts &x) {
+he_ct *ct_wrap(Ctx *c, const Cts &x) {
     he_ct *h = new he_ct();
     h->keep = c->shared_from_this();
     h->c = c;
@@ -607,7 +627,7 @@ static Feat gather_channels(Ctx *c, he_ct *const *in, u32 ch) {
 }
 
 static void scatter_channels(Ctx *c, const Feat &f, he_ct **out) {
-    for (u32 i = 0; i < f.CH; ++i) out[i] = wrap(c, f.chan(c, i));
+    for (u32 i = 0; i < f.CH; ++i) out[i] = ct_wrap(c, f.chan(c, i));
 }
 
 extern "C" {
@@ -639,6 +659,7 @@ he_status he_context_primes(const he_ctx *h, uint64_t *out, size_t n) {
 he_status he_keygen(he_ctx *h, const int32_t *steps, size_t n) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (n && !steps) throw HeError(HE_EINVAL, "null steps");
         keygen(c, std::vector<int>(steps, steps + n));
     });
@@ -648,6 +669,7 @@ he_status he_encrypt(he_ctx *h, const double *x, int x_on_device, uint32_t W, ui
                      uint32_t spc, uint32_t stride, uint64_t enc_seed, he_ct **out) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!x || !out || !W || !H || !nsamp) throw HeError(HE_EINVAL, "bad arguments");
         const size_t len = (size_t)nsamp * W * H;
         const double *xd = x;
@@ -659,13 +681,14 @@ he_status he_encrypt(he_ctx *h, const double *x, int x_on_device, uint32_t W, ui
         }
         Cts ct = encrypt(c, xd, W, H, nsamp, spc, stride, enc_seed);
         if (!x_on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
-        *out = wrap(c, ct);
+        *out = ct_wrap(c, ct);
     });
 }
 
 he_status he_decrypt(he_ctx *h, const he_ct *ct, double *out, int out_on_device, size_t nper) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!ct || !out || !nper) throw HeError(HE_EINVAL, "bad arguments");
         const Cts &x = ct->x;
         if (nper > x.lay.stride && x.lay.n_samples > 1) throw HeError(HE_EINVAL, "n_per_sample above the stride");
@@ -703,6 +726,7 @@ he_status he_ct_layout(const he_ct *ct, uint32_t *spc, uint32_t *stride, uint32_
 he_status he_ct_export(he_ctx *h, const he_ct *ct, uint64_t *coeff) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!ct || !coeff) throw HeError(HE_EINVAL, "bad arguments");
         const Cts &x = ct->x;
         const size_t w = (size_t)x.B * cts_ct_words(c, x.lp);
@@ -714,36 +738,45 @@ he_status he_ct_export(he_ctx *h, const he_ct *ct, uint64_t *coeff) {
     });
 }
 
-void he_ct_free(he_ct *ct) { delete ct; }
+void he_ct_free(he_ct *ct) {
+    if (!ct) return;
+    std::shared_ptr<Ctx> k = ct->keep;   // outlives the lock: the context may go with the handle
+    CtxLock lk(k.get());
+    delete ct;
+}
 
 he_status he_rotate(he_ctx *h, const he_ct *in, int32_t step, he_ct **out) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!in || !out) throw HeError(HE_EINVAL, "bad arguments");
-        *out = wrap(c, ct_rotate(c, in->x, step));
+        *out = ct_wrap(c, ct_rotate(c, in->x, step));
     });
 }
 
 he_status he_rotate_hoisted(he_ctx *h, const he_ct *in, const int32_t *steps, size_t n, he_ct **out) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!in || !out || !steps || !n) throw HeError(HE_EINVAL, "bad arguments");
         std::vector<Cts> r = ct_rotate_hoisted(c, in->x, std::vector<int>(steps, steps + n));
-        for (size_t i = 0; i < n; ++i) out[i] = wrap(c, r[i]);
+        for (size_t i = 0; i < n; ++i) out[i] = ct_wrap(c, r[i]);
     });
 }
 
 he_status he_rescale(he_ctx *h, const he_ct *in, he_ct **out) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!in || !out) throw HeError(HE_EINVAL, "bad arguments");
-        *out = wrap(c, ct_rescale(c, in->x));
+        *out = ct_wrap(c, ct_rescale(c, in->x));
     });
 }
 
 he_status he_mul_plain(he_ctx *h, const he_ct *in, const double *v, he_ct **out) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!in || !out || !v) throw HeError(HE_EINVAL, "bad arguments");
         const u32 M = c->N / 2;
         Layout one = in->x.lay;
@@ -759,21 +792,23 @@ he_status he_mul_plain(he_ctx *h, const he_ct *in, const double *v, he_ct **out)
         off.push_back((u32)pos.size());
         std::vector<DBuf> tmp;
         const u64 *pt = get_pts(c, nullptr, "mulplain", tmp, one, off, pos, val, c->scale, in->x.lp);
-        *out = wrap(c, ct_mul_pt(c, in->x, pt, c->scale));
+        *out = ct_wrap(c, ct_mul_pt(c, in->x, pt, c->scale));
     });
 }
 
 he_status he_add(he_ctx *h, const he_ct *a, const he_ct *b, he_ct **out) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!a || !b || !out) throw HeError(HE_EINVAL, "bad arguments");
-        *out = wrap(c, ct_add(c, a->x, b->x));
+        *out = ct_wrap(c, ct_add(c, a->x, b->x));
     });
 }
 
 he_status he_square(he_ctx *h, he_ct *const *in, uint32_t n, he_ct **out) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!out) throw HeError(HE_EINVAL, "bad arguments");
         Feat f = gather_channels(c, in, n);
         scatter_channels(c, layer_square(c, f), out);
@@ -784,6 +819,7 @@ static he_status conv_common(he_ctx *h, he_ct *const *in, uint32_t ci, const dou
                              uint32_t co, uint32_t K, uint32_t S, int incremental, he_ct **out, bool two_d) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!w || !bias || !out || !co || !K || !S) throw HeError(HE_EINVAL, "bad arguments");
         Feat f = gather_channels(c, in, ci);
         LayerSpec s;
@@ -818,6 +854,7 @@ he_status he_conv1d(he_ctx *h, he_ct *const *in, uint32_t ci, const double *w, c
 he_status he_avgpool(he_ctx *h, he_ct *const *in, uint32_t ch, uint32_t cc, he_ct **out) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!out || !cc) throw HeError(HE_EINVAL, "bad arguments");
         Feat f = gather_channels(c, in, ch);
         scatter_channels(c, layer_avgpool(c, f, cc), out);
@@ -827,9 +864,10 @@ he_status he_avgpool(he_ctx *h, he_ct *const *in, uint32_t ch, uint32_t cc, he_c
 he_status he_flatten(he_ctx *h, he_ct *const *in, uint32_t ch, he_ct **out) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!out) throw HeError(HE_EINVAL, "bad arguments");
         Feat f = gather_channels(c, in, ch);
-        *out = wrap(c, layer_flatten(c, f, nullptr, "flatten").x);
+        *out = ct_wrap(c, layer_flatten(c, f, nullptr, "flatten").x);
     });
 }
 
@@ -837,6 +875,7 @@ he_status he_fc(he_ctx *h, const he_ct *in, const double *Wm, const double *b, u
                 he_ct **out) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!in || !Wm || !b || !out || !din || !dout) throw HeError(HE_EINVAL, "bad arguments");
         LayerSpec s;
         s.op = HE_FC;
@@ -848,7 +887,7 @@ he_status he_fc(he_ctx *h, const he_ct *in, const double *Wm, const double *b, u
         f.x = in->x;
         f.CH = 1;
         f.B = in->x.B;
-        *out = wrap(c, layer_fc(c, f, s, nullptr, "fc").x);
+        *out = ct_wrap(c, layer_fc(c, f, s, nullptr, "fc").x);
     });
 }
 
@@ -873,6 +912,7 @@ he_status he_model_compile(he_ctx *h, const he_layer *layers, size_t n, uint32_t
                            he_model **out) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!layers || !n || !out || !spc) throw HeError(HE_EINVAL, "bad arguments");
         std::unique_ptr<he_model> m(new he_model());
         m->keep = c->shared_from_this();
@@ -889,87 +929,20 @@ he_status he_model_compile(he_ctx *h, const he_layer *layers, size_t n, uint32_t
     });
 }
 
-static void check_input(const he_model *m, const Cts &x) {
-    const Layout &L = x.lay;
-    if (L.W_img != m->W_img || L.H_img != m->H_img || L.n_samples != m->spc || L.stride < m->plan.stride ||
-        L.prev != PREV_INPUT)
-        throw HeError(HE_EINVAL, "ciphertext layout does not match the model");
-    if (x.lp < m->plan.levels + 1) throw HeError(HE_ELEVEL, "not enough levels for this model");
-}
-
 he_status he_infer(he_model *m, const he_ct *in, int use_graph, he_ct **out) {
     return guard([&] {
         if (!m || !in || !out) throw HeError(HE_EINVAL, "bad arguments");
         Ctx *c = m->c;
+        CtxLock lk(c);
         CUDA_TRY(cudaSetDevice(c->device));
-        check_input(m, in->x);
-        Feat f;
-        f.x = in->x;
-        f.CH = 1;
-        f.B = in->x.B;
-        if (!use_graph) {
-            Feat r = run_layers(c, f, m->layers, &m->pc);
-            *out = wrap(c, r.x);
-            return;
-        }
-        const Cts &x = in->x;
-        std::string key = fmt("%u:%u:%.17g", x.B, x.lp, x.scale);
-        auto it = m->graphs.find(key);
-        const size_t inw = (size_t)x.B * cts_ct_words(c, x.lp);
-        if (it == m->graphs.end()) {
-            // eager run (fills the plaintext cache and sizes the private pool), then capture
-            run_layers(c, f, m->layers, &m->pc);
-            CUDA_TRY(cudaStreamSynchronize(c->stream));
-            ModelGraph g;
-            c->active = &m->gpool;
-            try {
-                g.in = cts_alloc(c, x.B, x.lp, x.scale, x.lay);
-                Feat fi = f;
-                fi.x = g.in;
-                {   // warm the private pool with one run of the same shapes
-                    Feat w = run_layers(c, fi, m->layers, &m->pc);
-                }
-                CUDA_TRY(cudaStreamSynchronize(c->stream));
-                const bool prof = c->profiling;
-                c->profiling = false;   // no event records inside the graph
-                const u64 before = c->launches;
-                CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
-                Feat r;
-                try {
-                    r = run_layers(c, fi, m->layers, &m->pc);
-                } catch (...) {
-                    cudaGraph_t tmpg = nullptr;
-                    cudaStreamEndCapture(c->stream, &tmpg);
-                    if (tmpg) cudaGraphDestroy(tmpg);
-                    c->profiling = prof;
-                    throw;
-                }
-                c->profiling = prof;
-                g.kernels = c->launches - before;
-                c->launches = before;
-                CUDA_TRY(cudaStreamEndCapture(c->stream, &g.graph));
-                CUDA_TRY(cudaGraphInstantiate(&g.exec, g.graph, 0));
-                g.out = r.x;   // keeps the output buffer alive in the private pool
-            } catch (...) {
-                c->active = nullptr;
-                throw;
-            }
-            c->active = nullptr;
-            it = m->graphs.emplace(key, std::move(g)).first;
-        }
-        ModelGraph &g = it->second;
-        CUDA_TRY(cudaMemcpyAsync(g.in.data(), x.data(), inw * 8, cudaMemcpyDeviceToDevice, c->stream));
-        CUDA_TRY(cudaGraphLaunch(g.exec, c->stream));
-        c->launches += g.kernels;
-        Cts o = cts_alloc(c, g.out.B, g.out.lp, g.out.scale, g.out.lay);
-        CUDA_TRY(cudaMemcpyAsync(o.data(), g.out.data(), (size_t)g.out.B * cts_ct_words(c, g.out.lp) * 8,
-                                 cudaMemcpyDeviceToDevice, c->stream));
-        *out = wrap(c, o);
+        *out = ct_wrap(c, model_infer(m, in->x, use_graph != 0));
     });
 }
 
 void he_model_free(he_model *m) {
     if (!m) return;
+    std::shared_ptr<Ctx> k = m->keep;
+    CtxLock lk(k.get());
     cudaSetDevice(m->c->device);
     cudaStreamSynchronize(m->c->stream);
     delete m;
@@ -978,6 +951,7 @@ void he_model_free(he_model *m) {
 he_status he_ntt(he_ctx *h, uint64_t *data, uint32_t n_limbs, const uint32_t *prime_idx, int inverse) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         if (!data || !prime_idx || !n_limbs) throw HeError(HE_EINVAL, "bad arguments");
         std::vector<u32> rows;
         for (u32 i = 0; i < n_limbs; ++i) {
@@ -997,6 +971,7 @@ he_status he_ntt(he_ctx *h, uint64_t *data, uint32_t n_limbs, const uint32_t *pr
 he_status he_sync(he_ctx *h) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         CUDA_TRY(cudaStreamSynchronize(c->stream));
     });
 }
@@ -1006,6 +981,7 @@ uint64_t he_kernel_launches(const he_ctx *h) { return h && h->c ? h->c->launches
 he_status he_profile_begin(he_ctx *h) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         c->recs.clear();
         c->profiling = true;
     });
@@ -1014,6 +990,7 @@ he_status he_profile_begin(he_ctx *h) {
 he_status he_profile_end(he_ctx *h, he_kernel_stat *out, size_t cap, size_t *n) {
     return guard([&] {
         Ctx *c = CX(h);
+        CtxLock lk_(c);
         c->profiling = false;
         CUDA_TRY(cudaStreamSynchronize(c->stream));
         std::map<std::string, he_kernel_stat> agg;

@@ -110,9 +110,11 @@ extern "C" he_status he_rescale_noalloc(he_ctx *h, const uint64_t *in, uint64_t 
     try {
         if (!h || !h->c) throw HeError(HE_EINVAL, "null context");
         Ctx *c = h->c.get();
+        CtxLock lk(c);
         if (!in || !out || !batch) throw HeError(HE_EINVAL, "null buffer or empty batch");
         if (limbs < 2) throw HeError(HE_ELEVEL, "rescale needs at least two limbs");
         if (limbs > c->L1) throw HeError(HE_EINVAL, "more limbs than data primes");
+        if (c->logn > 14) throw HeError(HE_EINVAL, "he_rescale_noalloc: N above 16384 is not supported");
         const u32 N = c->N;
         if ((size_t)batch * 2 * N > NOALLOC_SCRATCH_WORDS)
             throw HeError(HE_EINVAL, fmt("he_rescale_noalloc: batch*2*N = %zu words exceeds the %u-word scratch "

@@ -14,7 +14,16 @@
 // coefficients takes 4 shared-memory passes (and 4 barriers) instead of 14,
 // and a group loads 15 twiddle pairs for 32 butterflies.  Shared memory is
 // padded by one word per 16 so that the strided group loads are conflict-free.
+//
+// Limbs larger than one CTA's shared memory (N = 2^15: 256 KiB) are split over
+// a cluster of two CTAs ("parts"): CTA r holds coefficients [r*N/2, (r+1)*N/2).
+// The one stage whose butterflies join the halves (distance N/2: the first
+// forward stage, the last inverse one) reads and writes the peer's half through
+// distributed shared memory; every other stage is local, with the twiddle index
+// taken from the global coefficient index.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "he_internal.cuh"
 
 __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q) {
@@ -31,6 +40,60 @@ __host__ __device__ __forceinline__ u32 ntt_smem_words(u32 N) { return N + N / 1
 // per thread per pass (so a thread may use up to 128 registers without spilling)
 #define NTT_MAX_THREADS 512
 static inline u32 ntt_threads(u32 N) { return N >= 1024 ? N / 32 : (N / 2 < 32 ? 32 : N / 2); }
+
+// largest limb one CTA transforms alone; above it a limb must be split over a
+// 2-CTA cluster (below it splitting is a tuning choice: half the shared memory
+// and threads per CTA, more CTAs resident per SM, one DSMEM exchange stage)
+#define NTT_PART_LOGN 14
+static inline int ntt_min_split(int logn) { return logn > NTT_PART_LOGN ? 1 : 0; }
+static inline int ntt_can_split(int logn) { return logn >= 11; }
+// coefficients one CTA holds, its threads and its dynamic shared memory
+static inline u32 ntt_part_n(int logn, int split) { return 1u << (logn - split); }
+static inline u32 ntt_part_threads(int logn, int split) { return ntt_threads(ntt_part_n(logn, split)); }
+static inline size_t ntt_part_smem(int logn, int split) { return (size_t)ntt_smem_words(ntt_part_n(logn, split)) * 8; }
+
+// which part of the limb this CTA holds: coefficients [lo, lo + n).  Kernels
+// are instantiated for SPLIT = 0 (one CTA per limb) and SPLIT = 1 (clusters of
+// two CTAs along x, each limb split over the pair).
+struct Part {
+    u32 lo, n;
+    int split;
+};
+template <int SPLIT>
+__device__ __forceinline__ Part ntt_part(int logn) {
+    Part p;
+    p.split = SPLIT;
+    p.n = 1u << (logn - SPLIT);
+    p.lo = SPLIT ? (blockIdx.x & 1u) * p.n : 0u;
+    return p;
+}
+// limb-level grid index (blockIdx.x with the cluster rank removed)
+template <int SPLIT>
+__device__ __forceinline__ u32 part_row() { return blockIdx.x >> SPLIT; }
+
+// launch kern0 (one CTA per limb) or kern1 (a cluster of two CTAs per limb along x);
+// grid.x counts limbs
+template <typename... KArgs, typename... Args>
+static void launch_parts(Ctx *c, void (*kern0)(KArgs...), void (*kern1)(KArgs...), dim3 grid, int split,
+                         u32 threads, size_t smem, Args... args) {
+    if (!split) {
+        kern0<<<grid, threads, smem, c->stream>>>(args...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid.x * 2, grid.y, grid.z);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CUDA_TRY(cudaLaunchKernelEx(&cfg, kern1, args...));
+}
 
 // ---------------------------------------------------------------- forward
 __device__ __forceinline__ void fwd_radix2_stage(u64 *a, int logn, int lgm, const u64 *__restrict__ tw, u64 q) {
@@ -51,16 +114,19 @@ __device__ __forceinline__ void fwd_radix2_stage(u64 *a, int logn, int lgm, cons
     }
 }
 
-// R stages starting at stage st on groups of 2^R coefficients held in registers
+// R stages starting at stage st on groups of 2^R coefficients held in registers.
+// a holds the 2^logl coefficients starting at global index goff of an N = 2^logn
+// limb; every butterfly group of these stages lies inside it.
 template <int R>
-__device__ __forceinline__ void fwd_pass(u64 *a, int logn, int st, const u64 *__restrict__ tw, u64 q) {
+__device__ __forceinline__ void fwd_pass(u64 *a, int logn, int st, const u64 *__restrict__ tw, u64 q,
+                                         int logl, u32 goff) {
     const u32 N = 1u << logn;
     const u64 *tws = tw + N;
     const u64 q2 = 2 * q;
     const int lgt0 = logn - 1 - st;          // log2 of the first distance t0
     const int lgtl = lgt0 - (R - 1);         // log2 of the smallest distance
     const u32 tl = 1u << lgtl;
-    const u32 groups = N >> R;
+    const u32 groups = (1u << logl) >> R;
     for (u32 g = threadIdx.x; g < groups; g += blockDim.x) {
         const u32 base = ((g >> lgtl) << (lgt0 + 1)) + (g & (tl - 1));
         u64 v[1 << R];
@@ -73,7 +139,7 @@ __device__ __forceinline__ void fwd_pass(u64 *a, int logn, int st, const u64 *__
             const int half = 1 << (R - 1 - u);
 #pragma unroll
             for (int blk = 0; blk < (1 << u); ++blk) {
-                const u32 j = base + ((u32)(blk * 2 * half) << lgtl);
+                const u32 j = goff + base + ((u32)(blk * 2 * half) << lgtl);
                 const u32 i = j >> (lgd + 1);
                 const u64 S = __ldg(tw + m + i), Ss = __ldg(tws + m + i);
 #pragma unroll
@@ -92,34 +158,69 @@ __device__ __forceinline__ void fwd_pass(u64 *a, int logn, int st, const u64 *__
     }
 }
 
-// in-place forward transform of a[spad(0..N)] in shared memory; output in [0, q).
-__device__ __forceinline__ void block_ntt_fwd(u64 *a, int logn, const u64 *__restrict__ tw, u64 q) {
-    const u32 N = 1u << logn;
+// stages st0.. of the forward transform on the local coefficients, then the
+// final reduction to [0, q)
+__device__ __forceinline__ void fwd_local(u64 *a, int logn, int st0, const u64 *__restrict__ tw, u64 q, int logl,
+                                          u32 goff) {
+    const u32 L = 1u << logl;
     if (logn >= 10) {
-        int st = 0;
+        int st = st0;
         for (; st + 4 <= logn; st += 4) {
-            fwd_pass<4>(a, logn, st, tw, q);
+            fwd_pass<4>(a, logn, st, tw, q, logl, goff);
             __syncthreads();
         }
         const int rem = logn - st;
-        if (rem == 3) fwd_pass<3>(a, logn, st, tw, q);
-        if (rem == 2) fwd_pass<2>(a, logn, st, tw, q);
-        if (rem == 1) fwd_pass<1>(a, logn, st, tw, q);
+        if (rem == 3) fwd_pass<3>(a, logn, st, tw, q, logl, goff);
+        if (rem == 2) fwd_pass<2>(a, logn, st, tw, q, logl, goff);
+        if (rem == 1) fwd_pass<1>(a, logn, st, tw, q, logl, goff);
         if (rem) __syncthreads();
     } else {
-        for (int lgm = 0; lgm < logn; ++lgm) {
+        for (int lgm = st0; lgm < logn; ++lgm) {
             fwd_radix2_stage(a, logn, lgm, tw, q);
             __syncthreads();
         }
     }
     const u64 q2 = 2 * q;
-    for (u32 k = threadIdx.x; k < N; k += blockDim.x) {
+    for (u32 k = threadIdx.x; k < L; k += blockDim.x) {
         u64 v = a[spad(k)];
         if (v >= q2) v -= q2;
         if (v >= q) v -= q;
         a[spad(k)] = v;
     }
     __syncthreads();
+}
+
+// in-place forward transform of a[spad(0..N)] in shared memory; output in [0, q).
+__device__ __forceinline__ void block_ntt_fwd(u64 *a, int logn, const u64 *__restrict__ tw, u64 q) {
+    fwd_local(a, logn, 0, tw, q, logn, 0);
+}
+
+// forward transform of the limb held by this CTA's part (the whole limb, or
+// half of it in each CTA of a 2-CTA cluster).  Every CTA of the cluster calls it
+// after writing its part; the output stays in the part's own shared memory.
+__device__ __forceinline__ void part_ntt_fwd(u64 *a, const Part &p, int logn, const u64 *__restrict__ tw, u64 q) {
+    if (!p.split) {
+        block_ntt_fwd(a, logn, tw, q);
+        return;
+    }
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();  // both halves written
+    u64 *a0 = cl.map_shared_rank(a, 0), *a1 = cl.map_shared_rank(a, 1);
+    const u32 N = 1u << logn, H = p.n;
+    const u64 S = __ldg(tw + 1), Ss = __ldg(tw + N + 1), q2 = 2 * q;
+    // stage 0 (distance N/2): pairs (j, j + N/2) sit at local index j of CTA 0 and CTA 1;
+    // each CTA takes half of the pairs
+    const u32 j0 = p.lo / 2;
+    for (u32 j = j0 + threadIdx.x; j < j0 + H / 2; j += blockDim.x) {
+        u64 U = a0[spad(j)];
+        if (U >= q2) U -= q2;
+        const u64 V = shoup_lazy(a1[spad(j)], S, Ss, q);
+        a0[spad(j)] = U + V;
+        a1[spad(j)] = U - V + q2;
+    }
+    cl.sync();  // remote writes visible; no remote access after this point
+    fwd_local(a, logn, 1, tw, q, logn - 1, p.lo);
 }
 
 // ---------------------------------------------------------------- inverse
@@ -141,14 +242,16 @@ __device__ __forceinline__ void inv_radix2_stage(u64 *a, int logn, int lgt, cons
     }
 }
 
-// R Gentleman-Sande stages with distances 2^lgtl .. 2^(lgtl+R-1)
+// R Gentleman-Sande stages with distances 2^lgtl .. 2^(lgtl+R-1) on the 2^logl
+// coefficients starting at global index goff
 template <int R>
-__device__ __forceinline__ void inv_pass(u64 *a, int logn, int lgtl, const u64 *__restrict__ tw, u64 q) {
+__device__ __forceinline__ void inv_pass(u64 *a, int logn, int lgtl, const u64 *__restrict__ tw, u64 q, int logl,
+                                         u32 goff) {
     const u32 N = 1u << logn;
     const u64 *itw = tw + 2 * N, *itws = tw + 3 * N;
     const u64 q2 = 2 * q;
     const u32 tl = 1u << lgtl;
-    const u32 groups = N >> R;
+    const u32 groups = (1u << logl) >> R;
     for (u32 g = threadIdx.x; g < groups; g += blockDim.x) {
         const u32 base = ((g >> lgtl) << (lgtl + R)) + (g & (tl - 1));
         u64 v[1 << R];
@@ -161,7 +264,7 @@ __device__ __forceinline__ void inv_pass(u64 *a, int logn, int lgtl, const u64 *
             const int half = 1 << u;
 #pragma unroll
             for (int blk = 0; blk < (1 << (R - 1 - u)); ++blk) {
-                const u32 j = base + ((u32)(blk * 2 * half) << lgtl);
+                const u32 j = goff + base + ((u32)(blk * 2 * half) << lgtl);
                 const u32 i = j >> (lgd + 1);
                 const u64 S = __ldg(itw + h + i), Ss = __ldg(itws + h + i);
 #pragma unroll
@@ -180,29 +283,61 @@ __device__ __forceinline__ void inv_pass(u64 *a, int logn, int lgtl, const u64 *
     }
 }
 
-// in-place inverse transform including the N^{-1} factor; input in [0, q).
-__device__ __forceinline__ void block_ntt_inv(u64 *a, int logn, const u64 *__restrict__ tw, u64 q, u64 ninv,
-                                              u64 ninvs) {
-    const u32 N = 1u << logn;
+// inverse stages with distances 1 .. 2^(nst-1) on the local coefficients
+__device__ __forceinline__ void inv_local(u64 *a, int logn, int nst, const u64 *__restrict__ tw, u64 q, int logl,
+                                          u32 goff) {
     if (logn >= 10) {
         int lgt = 0;
-        for (; lgt + 4 <= logn; lgt += 4) {
-            inv_pass<4>(a, logn, lgt, tw, q);
+        for (; lgt + 4 <= nst; lgt += 4) {
+            inv_pass<4>(a, logn, lgt, tw, q, logl, goff);
             __syncthreads();
         }
-        const int rem = logn - lgt;
-        if (rem == 3) inv_pass<3>(a, logn, lgt, tw, q);
-        if (rem == 2) inv_pass<2>(a, logn, lgt, tw, q);
-        if (rem == 1) inv_pass<1>(a, logn, lgt, tw, q);
+        const int rem = nst - lgt;
+        if (rem == 3) inv_pass<3>(a, logn, lgt, tw, q, logl, goff);
+        if (rem == 2) inv_pass<2>(a, logn, lgt, tw, q, logl, goff);
+        if (rem == 1) inv_pass<1>(a, logn, lgt, tw, q, logl, goff);
         if (rem) __syncthreads();
     } else {
-        for (int lgt = 0; lgt < logn; ++lgt) {
+        for (int lgt = 0; lgt < nst; ++lgt) {
             inv_radix2_stage(a, logn, lgt, tw, q);
             __syncthreads();
         }
     }
+}
+
+// in-place inverse transform including the N^{-1} factor; input in [0, q).
+__device__ __forceinline__ void block_ntt_inv(u64 *a, int logn, const u64 *__restrict__ tw, u64 q, u64 ninv,
+                                              u64 ninvs) {
+    const u32 N = 1u << logn;
+    inv_local(a, logn, logn, tw, q, logn, 0);
     for (u32 k = threadIdx.x; k < N; k += blockDim.x) a[spad(k)] = mul_shoup(a[spad(k)], ninv, ninvs, q);
     __syncthreads();
+}
+
+// inverse transform of the limb held by this CTA's part (see part_ntt_fwd)
+__device__ __forceinline__ void part_ntt_inv(u64 *a, const Part &p, int logn, const u64 *__restrict__ tw, u64 q,
+                                             u64 ninv, u64 ninvs) {
+    if (!p.split) {
+        block_ntt_inv(a, logn, tw, q, ninv, ninvs);
+        return;
+    }
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    inv_local(a, logn, logn - 1, tw, q, logn - 1, p.lo);
+    cl.sync();  // both halves through their local stages
+    u64 *a0 = cl.map_shared_rank(a, 0), *a1 = cl.map_shared_rank(a, 1);
+    const u32 N = 1u << logn, H = p.n;
+    const u64 S = __ldg(tw + 2 * N + 1), Ss = __ldg(tw + 3 * N + 1), q2 = 2 * q;
+    // last stage (distance N/2) fused with the N^{-1} factor
+    const u32 j0 = p.lo / 2;
+    for (u32 j = j0 + threadIdx.x; j < j0 + H / 2; j += blockDim.x) {
+        const u64 U = a0[spad(j)], V = a1[spad(j)];
+        u64 s = U + V;
+        if (s >= q2) s -= q2;
+        a0[spad(j)] = mul_shoup(s, ninv, ninvs, q);
+        a1[spad(j)] = mul_shoup(shoup_lazy(U - V + q2, S, Ss, q), ninv, ninvs, q);
+    }
+    cl.sync();
 }
 
 // global <-> padded shared memory, 16-byte vector accesses on the global side

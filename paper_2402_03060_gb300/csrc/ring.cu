@@ -313,9 +313,11 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
     while ((1u << ntlog) * bkc < 256) ++ntlog;
     if ((1u << ntlog) > c->N) throw HeError(HE_EINVAL, "mac: ring too small");
     const u32 NT = 1u << ntlog;
-    // outputs in groups of at most 12 (the accumulators of a group live in registers)
-    for (u32 o0 = 0; o0 < O; o0 += 12) {
-        const u32 oc = O - o0 < 12 ? O - o0 : 12;
+    // outputs in groups of at most G (the accumulators of a group live in registers;
+    // every group re-reads the inputs x); G is tuned, 12 by default
+    const u32 G = (u32)tune_get(c, TUNE_MAC_GROUP, 12);
+    for (u32 o0 = 0; o0 < O; o0 += G) {
+        const u32 oc = O - o0 < G ? O - o0 : G;
         // shared memory: pipeline slots + plaintext tile within the 48 KB default
         const u32 ow = oc <= 1 ? 1 : oc <= 2 ? 2 : oc <= 4 ? 4 : oc <= 6 ? 6 : oc <= 8 ? 8 : 12;   // template width
         u32 tc = (6144 - 256 * MAC_DEPTH) / (ow * NT);

@@ -62,6 +62,7 @@ extern "C" he_status he_ubench(he_ctx *h, double *out) {
     try {
         if (!h || !h->c || !out) return HE_EINVAL;
         Ctx *c = h->c.get();
+        CtxLock lk(c);
         CUDA_TRY(cudaSetDevice(c->device));
         const u32 blocks = 152 * 8, threads = 256, iters = 4096;
         DBuf sink(c, (size_t)blocks * threads);

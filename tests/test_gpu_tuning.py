@@ -1,0 +1,65 @@
+"""Autotuner: every launch shape it can choose gives bit-identical ciphertexts
+(limb split over 2-CTA clusters, MAC output groups, key-switch tiling and grid
+order), and its JSON cache round-trips."""
+import json
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_03060_gb300 import build
+    build.build()
+    import paper_2402_03060_gb300 as lib
+    return lib
+
+
+SETTINGS = [
+    dict(ntt_split=1, moddown_split=1, rescale_split=1, mac_group=4, lazy_bt=1, lazy_order=1),
+    dict(ntt_split=0, moddown_split=1, rescale_split=0, mac_group=6, lazy_bt=4, lazy_order=0),
+    dict(ntt_split=1, moddown_split=0, rescale_split=1, mac_group=8, lazy_bt=2, lazy_order=1),
+]
+
+
+@pytest.mark.parametrize("params", ["lenet1", "serve_lenet1"])
+def test_every_launch_shape_gives_the_same_ciphertexts(G, params):
+    P = dict(W.PARAMS["lenet1"] if params == "lenet1" else W.SERVE_PARAMS["lenet1"])
+    P["logn"] = 12                      # 2048 slots: two samples per ciphertext
+    model = W.lenet1()
+    stride, levels, steps = G.plan(model, 28, 28)
+    ctx = G.Context(seed=W.KEY_SEED, **P)
+    ctx.keygen(steps)
+    imgs = W.images(6)
+    m = ctx.compile(model, 28, 28, 2)
+    ct = ctx.encrypt(imgs, 2, stride, W.ENC_SEED)
+    ref = ctx.export(m.infer(ct))
+    for s in SETTINGS:
+        ctx.set_tuning(**s)
+        got = ctx.export(m.infer(ct))
+        assert np.array_equal(got, ref), s
+    ctx.set_tuning(**{k: -1 for k in ctx.TUNE_KNOBS})
+
+
+def test_autotune_and_cache(G, tmp_path):
+    P = dict(W.SERVE_PARAMS["lenet1"])
+    P["logn"] = 13
+    ctx = G.Context(seed=1, **P)
+    path = str(tmp_path / "tune.json")
+    rep = ctx.autotune(path)
+    assert "ntt_split" in rep and "mac_group" in rep and "lazy_order" in rep
+    chosen = ctx.tuning()
+    assert all(v >= 0 for v in chosen.values())
+    assert chosen["mac_group"] == rep["mac_group"]["chosen"]
+    cache = json.load(open(path))
+    assert len(cache) == 1 and list(cache.values())[0] == chosen
+    ctx2 = G.Context(seed=1, **P)
+    rep2 = ctx2.autotune(path)
+    assert "cached" in rep2 and ctx2.tuning() == chosen

@@ -9,7 +9,8 @@ ECG set are not available, so (paper Sec. VI datasets -> stand-ins):
 Model shapes: a single 5x5 convolution
 (Exp. 1 style), the LeNet-1-shaped net of Exp. 2 (Table M2: conv 1->4 K5,
 x^2, avgpool 2, conv 4->12 K5, x^2, avgpool 2, flatten, FC 192->10) and a 1-D
-CNN in the family of Exp. 7.
+CNN in the family of Exp. 7, and a LeNet-5-shaped net (x^2 activations) at
+N = 2^15 for the serving mix.
 """
 from __future__ import annotations
 
@@ -92,7 +93,21 @@ PARAMS = {
     "conv1": dict(logn=13, data_bits=[60, 40, 40], special_bits=[60], dnum=3, log2_scale=40),
     "lenet1": dict(logn=14, data_bits=[60] + [40] * 7, special_bits=[60], dnum=8, log2_scale=40),
     "cnn1d": dict(logn=14, data_bits=[60] + [40] * 6, special_bits=[60], dnum=7, log2_scale=40),
+    # LeNet-5-shaped net with x^2 activations: 11 levels at N = 2^15
+    "lenet5": dict(logn=15, data_bits=[60] + [40] * 11, special_bits=[60], dnum=12, log2_scale=40),
 }
+
+# Serving mix: every model's keys with dnum = 3 digits.  A digit then spans up to
+# three (LeNet-1, 1-D CNN) or four (LeNet-5) data primes, so the special modulus
+# P must cover it: three 50-bit primes (150 bits > 140) and four 50-bit primes
+# (200 bits > 180).  At N = 2^14 that makes log QP = 490 bits, above the 438 bits
+# of the 128-bit HE-standard bound; recorded, not hidden.
+SERVE_PARAMS = {
+    "lenet1": dict(logn=14, data_bits=[60] + [40] * 7, special_bits=[50] * 3, dnum=3, log2_scale=40),
+    "lenet5": dict(logn=15, data_bits=[60] + [40] * 11, special_bits=[50] * 4, dnum=3, log2_scale=40),
+    "cnn1d": dict(logn=14, data_bits=[60] + [40] * 6, special_bits=[50] * 3, dnum=3, log2_scale=40),
+}
+ARRIVAL_SEED = 12345
 
 
 def small_params(name: str, logn: int) -> dict:
