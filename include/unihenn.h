@@ -155,7 +155,11 @@ typedef struct {
     uint32_t op;       /* HE_CONV2D ... HE_FC */
     uint32_t ch_in;    /* conv: input channels; FC: DAT_in */
     uint32_t ch_out;   /* conv: output channels; FC: DAT_out */
-    uint32_t k;        /* conv kernel size; average-pooling size */
+    uint32_t k;        /* conv kernel size; average-pooling size; FC: how the final rotation sum
+                          sum_{i < W_vec/DAT_out} Rot(C, i*DAT_out) of Alg. 2 is evaluated --
+                          0 as printed (one hoisted combination of the rotations), 1 by binary
+                          doubling (about log2 + popcount rotations; other key switches, so other
+                          ciphertexts, same slot values) */
     uint32_t stride;   /* conv stride */
     const double *w;   /* conv [ch_out][ch_in][k][k] (1-D: [ch_out][ch_in][k]); FC [ch_out][ch_in] */
     const double *b;   /* [ch_out] */

@@ -221,10 +221,49 @@ def fc_rot_matrix(M: np.ndarray):
     return Mr, Wv
 
 
-def fc(be, xs, M, bias, lay: Layout):
+def tree_steps(d: int, m: int):
+    """Rotation steps of rotation_sum's binary form: the doublings k*d (k = 1, 2, 4, ..
+    while 2k <= m) and the shifts off*d of the set bits of m below the highest."""
+    steps, k = [], 1
+    while 2 * k <= m:
+        steps.append(k * d)
+        k *= 2
+    off = 0
+    for b in reversed(range(m.bit_length())):
+        if m >> b & 1:
+            if off:
+                steps.append(off * d)
+            off += 1 << b
+    return steps
+
+
+def rotation_sum(be, x, d: int, m: int, mode: str = "linear"):
+    """sum_{i<m} Rot(x, i*d), the last step of Algorithm 2.  "linear": the m
+    rotations as one hoisted combination (as printed).  "tree": binary
+    doubling, T_1 = x, T_2k = T_k + Rot(T_k, k*d), then the blocks T_{2^b} of
+    the set bits b of m, high to low, each rotated by the total of the blocks
+    before it: about log2(m) + popcount(m) rotations instead of m - 1.  Both
+    compute the same slot sums; their ciphertexts differ (other key switches)."""
+    if mode == "linear" or m == 1:
+        return be.lincomb([x], [i * d for i in range(m)], None)[0]
+    assert mode == "tree", mode
+    T, k = [x], 1
+    while 2 * k <= m:
+        T.append(be.add(T[-1], be.rot(T[-1], k * d)))
+        k *= 2
+    acc, off = None, 0
+    for b in reversed(range(len(T))):
+        if m >> b & 1:
+            term = T[b] if off == 0 else be.rot(T[b], off * d)
+            acc = term if acc is None else be.add(acc, term)
+            off += 1 << b
+    return acc
+
+
+def fc(be, xs, M, bias, lay: Layout, sum_mode: str = "linear"):
     """Algorithm 2 (Sec. IV-D): C_sum = sum_o Rot(C,o)*V1_o + Rot(C,o-W_vec)*V2_o,
-    rescale, C_out = sum_{i < W_vec/dout} Rot(C_sum, i*dout), then Add(bias)
-    at slots [0, dout) of each sample."""
+    rescale, C_out = sum_{i < W_vec/dout} Rot(C_sum, i*dout) (rotation_sum, in
+    sum_mode), then Add(bias) at slots [0, dout) of each sample."""
     assert len(xs) == 1 and lay.flat
     M = np.asarray(M, dtype=np.float64)
     dout, din = M.shape
@@ -241,7 +280,7 @@ def fc(be, xs, M, bias, lay: Layout):
     acc = be.lincomb([x], steps, [[vecs]])[0]
     acc = be.rescale(acc)
     nsum = Wv // dout
-    out = be.lincomb([acc], [i * dout for i in range(nsum)], None)[0]
+    out = rotation_sum(be, acc, dout, nsum, sum_mode)
     out = be.add_mask(out, slot_vector(lay, np.arange(dout), np.asarray(bias, dtype=np.float64)))
     return [out], replace(lay, pending=1.0, prev="fc", D=dout, W=dout)
 
@@ -267,7 +306,7 @@ def run_layers(be, xs, layers, lay: Layout, conv_mode: str = "hoisted"):
         elif op == "fc":
             if not lay.flat:
                 xs, lay = flatten(be, xs, lay)
-            xs, lay = fc(be, xs, spec["w"], spec["b"], lay)
+            xs, lay = fc(be, xs, spec["w"], spec["b"], lay, spec.get("sum", "linear"))
         else:
             raise ValueError(op)
     return xs, lay
@@ -327,7 +366,10 @@ def plan(layers, W_img: int, H_img: int, dims: int = 2):
                 Wv = -(-din // dout) * dout
                 need = max(need, Wv)
                 steps |= set(range(dout)) | {o - Wv for o in range(1, dout)}
-                steps |= {i * dout for i in range(Wv // dout)}
+                if spec.get("sum", "linear") == "tree":
+                    steps |= set(tree_steps(dout, Wv // dout))
+                else:
+                    steps |= {i * dout for i in range(Wv // dout)}
                 levels += 1
                 prev = "fc"
                 flat_D = dout

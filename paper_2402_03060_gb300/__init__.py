@@ -79,6 +79,7 @@ def layers_to_c(layers):
             keep += [w, b]
             e.op = _lib.HE_FC
             e.ch_out, e.ch_in = w.shape
+            e.k = {"linear": 0, "tree": 1}[l.get("sum", "linear")]
             e.w, e.b = _dptr(w), _dptr(b)
         elif op == "square":
             e.op = _lib.HE_SQUARE

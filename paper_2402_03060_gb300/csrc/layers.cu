@@ -284,6 +284,31 @@ static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string
 }
 
 // Algorithm 2 (Sec. IV-D) on a flattened ciphertext; M [dout][din]
+// sum_{i<m} Rot(x, i*d), the last step of Alg. 2: one hoisted combination of the m
+// rotations (as printed), or (tree) binary doubling T_1 = x, T_2k = T_k + Rot(T_k, k*d)
+// and the blocks T_{2^b} of the set bits of m, high to low, each rotated by the total
+// of the blocks before it -- about log2(m) + popcount(m) rotations.
+static Cts rotation_sum(Ctx *c, const Cts &x, u32 B, u32 d, u32 m, bool tree) {
+    if (!tree || m == 1) {
+        std::vector<int> st;
+        for (u32 i = 0; i < m; ++i) st.push_back((int)(i * d));
+        return ct_lincomb(c, x, 1, B, st, nullptr, 0, 1.0);
+    }
+    std::vector<Cts> T{x};   // T[b] = T_{2^b}
+    for (u32 k = 1; 2 * k <= m; k *= 2) T.push_back(ct_add(c, T.back(), ct_rotate(c, T.back(), (int)(k * d))));
+    Cts acc;
+    bool have = false;
+    u32 off = 0;
+    for (int b = (int)T.size() - 1; b >= 0; --b) {
+        if (!((m >> b) & 1)) continue;
+        Cts term = off == 0 ? T[b] : ct_rotate(c, T[b], (int)(off * d));
+        acc = have ? ct_add(c, acc, term) : term;
+        have = true;
+        off += 1u << b;
+    }
+    return acc;
+}
+
 static Feat layer_fc(Ctx *c, const Feat &in, const LayerSpec &sp, PtCache *pc, const std::string &key) {
     const Layout &L = in.x.lay;
     const u32 din = sp.ci, dout = sp.co, B = in.B;
@@ -334,11 +359,8 @@ static Feat layer_fc(Ctx *c, const Feat &in, const LayerSpec &sp, PtCache *pc, c
     // C_sum: every rotation of the input with its V1 / V2 vector, one ModDown
     Cts acc = ct_lincomb(c, in.x, 1, B, steps, pts, 1, c->scale);
     Cts cs = ct_rescale(c, acc);
-    // C_out = sum_i Rot(C_sum, i * dout), one ModDown
-    const u32 nsum = Wv / dout;
-    std::vector<int> st2;
-    for (u32 i = 0; i < nsum; ++i) st2.push_back((int)(i * dout));
-    Cts out = ct_lincomb(c, cs, 1, B, st2, nullptr, 0, 1.0);
+    // C_out = sum_i Rot(C_sum, i * dout); FC field k = 1 selects the tree form
+    Cts out = rotation_sum(c, cs, B, dout, Wv / dout, sp.k == 1);
     {
         std::vector<u32> off{0}, pos;
         std::vector<double> val;
@@ -426,7 +448,19 @@ static Plan plan_layers(const std::vector<LayerSpec> &ls, u32 Wi, u32 Hi) {
                 need = std::max(need, Wv);
                 for (u32 o = 0; o < s.co; ++o) st.insert((int)o);
                 for (u32 o = 1; o < s.co; ++o) st.insert((int)o - (int)Wv);
-                for (u32 i = 0; i < Wv / s.co; ++i) st.insert((int)(i * s.co));
+                const u32 m = Wv / s.co;
+                if (s.k == 1) {   // tree form of the final rotation sum
+                    u32 k = 1;
+                    for (; 2 * k <= m; k *= 2) st.insert((int)(k * s.co));
+                    u32 off = 0;
+                    for (int b = 31; b >= 0; --b)
+                        if ((m >> b) & 1) {
+                            if (off) st.insert((int)(off * s.co));
+                            off += 1u << b;
+                        }
+                } else {
+                    for (u32 i = 0; i < m; ++i) st.insert((int)(i * s.co));
+                }
                 levels += 1;
                 prev = PREV_FC;
                 W = s.co;

@@ -50,12 +50,14 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(L, n)
 
 
-@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "lenet5", "conv"])
+@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "conv"])
 def test_planner_matches_oracle(lib, name):
     if name == "lenet1":
         model, Wi, Hi = W.lenet1(), 28, 28
     elif name == "cnn1d":
         model, Wi, Hi = W.cnn1d(), 1024, 1
+    elif name == "cnn1d_tree":
+        model, Wi, Hi = W.cnn1d(fc_sum="tree"), 1024, 1
     elif name == "lenet5":
         model, Wi, Hi = W.lenet5_sq(), 32, 32
     else:

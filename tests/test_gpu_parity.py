@@ -225,6 +225,24 @@ def test_lenet5_full_ring_logits(G):
     assert np.array_equal(ctx.export(out)[1], ctx.export(single)[0])
 
 
+def test_cnn1d_tree_fc_dnum3_bit_exact(G):
+    """The serving mix's 1-D CNN: dnum = 3 keys (three-prime digits, three special
+    primes) and the FC's rotation sum in binary form, N = 8192 (one sample per
+    ciphertext), bit-exact against the oracle."""
+    P = dict(W.SERVE_PARAMS["cnn1d"])
+    P["logn"] = 13
+    model = W.cnn1d(fc_sum="tree")
+    stride, levels, steps = G.plan(model, 1024, 1)
+    assert len(steps) < 120
+    ctx, he = make_pair(G, P, steps)
+    x = W.signals(1)
+    gct = ctx.encrypt(x, 1, stride, W.ENC_SEED)
+    out = ctx.compile(model, 1024, 1, 1).infer(gct, use_graph=True)
+    want = run_oracle_model(he, model, x[:, 0], 1024, 1, stride, 1, W.ENC_SEED, dims=1)
+    assert_same(ctx, out, he, want)
+    assert np.abs(ctx.decrypt(out, 5)[0] - cnn.forward(x[0, 0], model, dims=1)).max() < 1e-3
+
+
 def test_batched_equals_single_and_uneven_tail(G):
     """3 ciphertexts x 2 samples (5 samples: an uneven last ciphertext) in one
     batch give the same ciphertexts as each ciphertext alone."""

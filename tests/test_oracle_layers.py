@@ -86,13 +86,14 @@ def test_cnn_against_torch():
     assert np.abs(t.numpy().reshape(-1) - cnn.forward(s[0], m1, dims=1)).max() < 1e-12
 
 
-@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "lenet5", "M1", "M7"])
+@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "M1", "M7"])
 def test_slot_algorithms_equal_direct_cnn(name):
     if name == "lenet1":
         model, Wi, Hi, dims, slots = W.lenet1(), 28, 28, 2, 8192
         gen = lambda n: W.images(n)
-    elif name == "cnn1d":
-        model, Wi, Hi, dims, slots = W.cnn1d(), 1024, 1, 1, 8192
+    elif name.startswith("cnn1d"):
+        model = W.cnn1d(fc_sum="tree" if name.endswith("tree") else "linear")
+        Wi, Hi, dims, slots = 1024, 1, 1, 8192
         gen = lambda n: W.signals(n)[:, 0]
     elif name == "lenet5":
         model, Wi, Hi, dims, slots = W.lenet5_sq(), 32, 32, 2, 16384
@@ -202,3 +203,19 @@ def test_avgpool_uses_no_level_and_leaves_invalid_values():
 def test_plan_stride_lenet1():
     pl = layers.plan(W.lenet1(), 28, 28)
     assert pl["stride"] == 784 and pl["levels"] == 7
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 7, 8, 9, 20, 816])
+def test_tree_rotation_sum(m):
+    """The binary form of Alg. 2's final sum gives the slot sums of the printed
+    form, with about log2(m) + popcount(m) rotations instead of m - 1."""
+    rng = np.random.default_rng(m)
+    slots, d = 8192, 5
+    v = rng.normal(size=slots)
+    lin, tree = slotsim.SlotSim(), slotsim.SlotSim()
+    a = layers.rotation_sum(lin, lin.wrap(v), d, m, "linear")
+    b = layers.rotation_sum(tree, tree.wrap(v), d, m, "tree")
+    direct = sum(np.roll(v, -i * d) for i in range(m))
+    assert np.abs(a.v - direct).max() < 1e-9 and np.abs(b.v - direct).max() < 1e-9
+    n_rot = (m.bit_length() - 1) + bin(m).count("1") - 1
+    assert tree.count["rot"] == n_rot == len(layers.tree_steps(d, m))

@@ -45,7 +45,9 @@ def lenet1(seed: int = WEIGHT_SEED):
     ]
 
 
-def cnn1d(seed: int = WEIGHT_SEED, length: int = 1024):
+def cnn1d(seed: int = WEIGHT_SEED, length: int = 1024, fc_sum: str = "linear"):
+    """fc_sum: how the FC's final rotation sum is evaluated ("linear" as in Alg. 2,
+    or "tree": binary doubling, the form the serving mix uses)."""
     rng = np.random.default_rng(seed)
     l1 = length - 2          # conv k3 s1
     l2 = l1 // 2             # avgpool 2
@@ -57,7 +59,7 @@ def cnn1d(seed: int = WEIGHT_SEED, length: int = 1024):
         {"op": "conv1d", "w": _normal(rng, (16, 8, 3)), "b": _normal(rng, (16,)), "stride": 2},
         {"op": "square"},
         {"op": "flatten"},
-        {"op": "fc", "w": _normal(rng, (5, 16 * l3)), "b": _normal(rng, (5,))},
+        {"op": "fc", "w": _normal(rng, (5, 16 * l3)), "b": _normal(rng, (5,)), "sum": fc_sum},
     ]
 
 
