@@ -477,6 +477,23 @@ class Ckks:
                         _p(_u(self.q[:lp])), _p(_u(self.qpsi[:lp])), _p(_u(self.p)), _p(_u(self.ppsi)))
         return out
 
+    def moddown_rescale(self, acc: np.ndarray) -> np.ndarray:
+        """ModDown and rescale as one division by D = q_top * P: the dropped basis is
+        the top data prime and the special primes, and (reading C6/C7 applied to
+        that basis) out_i = (acc_i - BConv_{D->q_i}([acc]_D)) * D^{-1} mod q_i for
+        the lp - 1 remaining limbs, fast base conversion without correction.
+        acc [lp+K][N] over Q_l u P (data limbs, then special) -> [lp-1][N]:
+        floor(x / D) - e with 0 <= e < K + 1.  Equals ModDown then rescale up to
+        that rounding (one base conversion instead of two)."""
+        lp = acc.shape[0] - self.K
+        assert lp >= 2, "level exhausted"
+        out = np.zeros((lp - 1, self.n), dtype=np.uint64)
+        drop = [self.q[lp - 1]] + list(self.p)
+        dpsi = [self.qpsi[lp - 1]] + list(self.ppsi)
+        lib().o_moddown(_p(out), _p(_u(acc)), lp - 1, self.K + 1, self.logn,
+                        _p(_u(self.q[:lp - 1])), _p(_u(self.qpsi[:lp - 1])), _p(_u(drop)), _p(_u(dpsi)))
+        return out
+
     def keyswitch(self, x: np.ndarray, key):
         acc0, acc1 = self.ks_inner(self.modup(x), key)
         return self.moddown(acc0), self.moddown(acc1)
@@ -515,7 +532,7 @@ class Ckks:
         basis, psis = self.ext_basis(lp)
         return self.ntt(self.reduce_signed(self.encode_coeffs(z, scale), basis), basis, psis)
 
-    def lincomb(self, cts, steps, weights=None, pt_scale: float = 1.0):
+    def lincomb(self, cts, steps, weights=None, pt_scale: float = 1.0, rescale: bool = False):
         """Hoisted linear combination of rotations with one ModDown per output:
 
             Y_o = sum_i sum_s w[o][i][s] (.) Rot(ct_i, steps[s])
@@ -527,7 +544,8 @@ class Ckks:
         message as the rotate-then-multiply composition; only the rounding of the
         single ModDown differs.  w[o][i][s] are plaintexts over Q_l u P (``encode_ext``)
         or None (all ones, a plain sum of rotations); the output scale is
-        ct.scale * pt_scale."""
+        ct.scale * pt_scale.  With rescale, each output is also rescaled: the
+        single division by q_top * P of ``moddown_rescale`` replaces ModDown."""
         lp = cts[0].lp
         K = self.K
         E = lp + K
@@ -569,7 +587,11 @@ class Ckks:
                         w = weights[o][i][s]
                         lib().o_muladd(_p(z0), _p(_u(a0)), _p(_u(w)), E, self.n, _p(basis))
                         lib().o_muladd(_p(z1), _p(_u(a1)), _p(_u(w)), E, self.n, _p(basis))
-            outs.append(Ct(np.stack([self.moddown(z0), self.moddown(z1)]), cts[0].scale * pt_scale))
+            if rescale:
+                outs.append(Ct(np.stack([self.moddown_rescale(z0), self.moddown_rescale(z1)]),
+                               cts[0].scale * pt_scale / float(self.q[lp - 1])))
+            else:
+                outs.append(Ct(np.stack([self.moddown(z0), self.moddown(z1)]), cts[0].scale * pt_scale))
         return outs
 
     def lincomb_diag(self, cts, steps) -> Ct:
@@ -606,12 +628,20 @@ class Ckks:
         return np.concatenate([self.add(a0[:lp], self.mul(c0g, Pq, q), q), a0[lp:]]), a1
 
     def square(self, ct: Ct) -> Ct:
-        """Ciphertext tensor with itself, relinearisation, rescale (reading C15)."""
-        q = self.q[: ct.lp]
+        """Ciphertext tensor with itself, relinearisation, rescale (reading C15).
+        Relinearisation and rescale end in one division by q_top * P: the key-switch
+        accumulators of d2 over Q_l u P get P*(d0, d1) added on the data limbs
+        (ModDown(A + P*d) = ModDown(A) + d) and go through ``moddown_rescale``."""
+        lp = ct.lp
+        assert lp >= 2, "level exhausted"
+        q = self.q[:lp]
         a0, a1 = ct.d[0], ct.d[1]
         d0 = self.mul(a0, a0, q)
         d1 = self.add(self.mul(a0, a1, q), self.mul(a1, a0, q), q)
         d2 = self.mul(a1, a1, q)
-        k0, k1 = self.keyswitch(d2, self.keys.rlk)
-        t = Ct(np.stack([self.add(d0, k0, q), self.add(d1, k1, q)]), ct.scale * ct.scale)
-        return self.rescale(t)
+        acc0, acc1 = self.ks_inner(self.modup(d2), self.keys.rlk)
+        Pq = np.repeat(np.array([self.P_mod(qi) for qi in q], dtype=np.uint64)[:, None], self.n, axis=1)
+        acc0 = np.concatenate([self.add(acc0[:lp], self.mul(d0, Pq, q), q), acc0[lp:]])
+        acc1 = np.concatenate([self.add(acc1[:lp], self.mul(d1, Pq, q), q), acc1[lp:]])
+        return Ct(np.stack([self.moddown_rescale(acc0), self.moddown_rescale(acc1)]),
+                  ct.scale * ct.scale / float(self.q[lp - 1]))

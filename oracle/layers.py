@@ -12,6 +12,7 @@ A backend supplies slot-vector operations:
     mul_mask(x, v)       Mul (P) by the slot vector v encoded at scale Delta
     add_mask(x, v)       Add (P) of v encoded at x's current scale and level
     rescale(x)           drop one level (identity on cleartext)
+    lincomb_rescale(xs, steps, w)  lincomb followed by rescale of every output
     square(x)            Mul (C) of x by itself, relinearised and rescaled
 Two backends exist: ``slotsim.SlotSim`` (FP64 cleartext, O2) and
 ``HeBackend`` below (the CKKS oracle, O3).  Running the same layer code on
@@ -97,9 +98,9 @@ def conv(be, xs, w, bias, S: int, lay: Layout, mode: str = "hoisted"):
 
     if mode == "hoisted":
         # all rotations of every input channel and all products in one hoisted
-        # linear combination per output channel
+        # linear combination per output channel, rescaled
         weights = [[[kvec(o, i, off) for off in offs] for i in range(ci)] for o in range(co)]
-        sums = be.lincomb(xs, [step[o] for o in offs], weights)
+        scaled = be.lincomb_rescale(xs, [step[o] for o in offs], weights)
     elif mode == "incremental":
         rots = []
         for i in range(ci):
@@ -118,12 +119,12 @@ def conv(be, xs, w, bias, S: int, lay: Layout, mode: str = "hoisted"):
                     t = be.mul_mask(rots[i][off], kvec(o, i, off))
                     acc = t if acc is None else be.add(acc, t)
             sums.append(acc)
+        scaled = [be.rescale(x) for x in sums]
     else:
         raise ValueError(mode)
     outs = []
     for o in range(co):
-        acc = be.rescale(sums[o])
-        acc = be.add_mask(acc, slot_vector(lay, pos, float(bias[o])))
+        acc = be.add_mask(scaled[o], slot_vector(lay, pos, float(bias[o])))
         outs.append(acc)
     return outs, replace(lay, W=Wout, H=Hout, I=Iout, pending=1.0, prev="conv")
 
@@ -175,7 +176,7 @@ def flatten(be, xs, lay: Layout):
 
     def masked_rotation_sum(x, masks, steps):
         rolled = [np.roll(m, -s) for m, s in zip(masks, steps)]
-        return be.rescale(be.lincomb([x], steps, [[rolled]])[0])
+        return be.lincomb_rescale([x], steps, [[rolled]])[0]
 
     if lay.prev == "avgpool":
         steps = [c * (I - 1) for c in range(W)]
@@ -277,8 +278,7 @@ def fc(be, xs, M, bias, lay: Layout, sum_mode: str = "linear"):
     t_idx = np.arange(Wv)
     vecs = [slot_vector(lay, t_idx, np.where(t_idx < Wv - o, Mr[o], 0.0)) for o in range(dout)]
     vecs += [slot_vector(lay, t_idx, np.where(t_idx >= Wv - o, Mr[o], 0.0)) for o in range(1, dout)]
-    acc = be.lincomb([x], steps, [[vecs]])[0]
-    acc = be.rescale(acc)
+    acc = be.lincomb_rescale([x], steps, [[vecs]])[0]
     nsum = Wv // dout
     out = rotation_sum(be, acc, dout, nsum, sum_mode)
     out = be.add_mask(out, slot_vector(lay, np.arange(dout), np.asarray(bias, dtype=np.float64)))
@@ -407,6 +407,15 @@ class HeBackend:
         lp = xs[0].lp
         enc = [[[self.he.encode_ext(v, self.he.scale, lp) for v in wi] for wi in wo] for wo in weights]
         return self.he.lincomb(xs, steps, enc, self.he.scale)
+
+    def lincomb_rescale(self, xs, steps, weights):
+        m = self.he.n // 2
+        self.count["rot"] += len(xs) * len({s % m for s in steps if s % m})
+        self.count["pmul"] += sum(len(wi) for wo in weights for wi in wo)
+        self.count["rescale"] += len(weights)
+        lp = xs[0].lp
+        enc = [[[self.he.encode_ext(v, self.he.scale, lp) for v in wi] for wi in wo] for wo in weights]
+        return self.he.lincomb(xs, steps, enc, self.he.scale, rescale=True)
 
     def add(self, x, y):
         return self.he.ct_add(x, y)

@@ -62,6 +62,9 @@ class SlotSim:
             outs.append(SV(v, xs[0].used, True))
         return outs
 
+    def lincomb_rescale(self, xs, steps, weights):
+        return [self.rescale(y) for y in self.lincomb(xs, steps, weights)]
+
     def add(self, x, y):
         assert x.used == y.used and x.pending_rescale == y.pending_rescale, "level mismatch"
         return SV(x.v + y.v, x.used, x.pending_rescale)

@@ -224,3 +224,21 @@ def test_sampler_distributions():
     q = (1 << 40) - 87
     u = ckks.sample_uniform(5, 3, n, q)
     assert int(u.max()) < q and abs(float(np.mean(u.astype(np.float64))) / q - 0.5) < 0.01
+
+
+def test_moddown_rescale_is_floor_division_by_q_top_times_P():
+    """The fused ModDown + rescale divides by D = q_top * P in one base conversion:
+    out = floor(X / D) - e with 0 <= e < K + 1, X the CRT value over Q_l u P."""
+    he = ckks.Ckks(logn=3, data_bits=[60, 40, 40], special_bits=[60, 55], dnum=3, log2_scale=30, seed=1)
+    qs, ps = he.q, he.p
+    basis = qs + ps
+    rng = np.random.default_rng(14)
+    coef = np.stack([rng.integers(0, m, he.n, dtype=U64) for m in basis])
+    acc = np.concatenate([he.ntt(coef[:3], qs, he.qpsi), he.ntt(coef[3:], ps, he.ppsi)])
+    out = he.intt(he.moddown_rescale(acc), qs[:2], he.qpsi[:2])
+    D = qs[2] * ps[0] * ps[1]
+    for c in range(he.n):
+        X, _ = _crt([coef[i, c] for i in range(len(basis))], basis)
+        Y, Q2 = _crt([out[i, c] for i in range(2)], qs[:2])
+        d = (Y - X // D) % Q2
+        assert d == 0 or Q2 - d < len(ps) + 1, (c, d)

@@ -138,3 +138,22 @@ def test_lincomb_diag_decrypts_to_sum_of_rotations(he):
     out = he.lincomb_diag(cts, steps)
     want = sum(np.roll(z, -s) for z, s in zip(zs, steps))
     assert np.abs(he.decrypt(out) - want).max() < 1e-6
+
+
+@pytest.mark.parametrize("which", ["he", "he_dnum"])
+def test_lincomb_with_rescale_matches_lincomb_then_rescale(which, request):
+    """The fused division gives the message of ModDown followed by rescale."""
+    he = request.getfixturevalue(which)
+    rng = np.random.default_rng(21)
+    M = he.n // 2
+    x = rng.uniform(-1, 1, M)
+    ct = he.encrypt(x, 5)
+    steps = [0, 1]
+    ws = [rng.uniform(-1, 1, M) for _ in steps]
+    enc = [[[he.encode_ext(w, he.scale, ct.lp) for w in ws]]]
+    fused = he.lincomb([ct], steps, enc, he.scale, rescale=True)[0]
+    plain = he.rescale(he.lincomb([ct], steps, enc, he.scale)[0])
+    assert fused.lp == plain.lp == ct.lp - 1 and fused.scale == plain.scale
+    want = sum(np.roll(x, -s) * w for s, w in zip(steps, ws))
+    assert np.abs(he.decrypt(fused)[:M] - want).max() < 1e-5
+    assert np.abs(he.decrypt(fused)[:M] - he.decrypt(plain)[:M]).max() < 1e-5
