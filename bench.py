@@ -318,6 +318,23 @@ def run_serve(args, local):
                                   / 1e3, 3)}
 
 
+def max_over_ranks(vals, dist, device):
+    """Element-wise maximum of the per-rank timings (every rank gets it); replicas
+    exchange nothing else."""
+    if dist is None:
+        return list(vals)
+    import torch
+    t = torch.tensor(list(vals), device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def whole_job_rate(samples_per_rank, world, ms_step_max):
+    """Weak scaling: every rank processes its own batch; the job's rate is all
+    ranks' samples over the slowest rank's step time."""
+    return samples_per_rank * world / (ms_step_max / 1e3)
+
+
 def run_ours(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
@@ -435,12 +452,7 @@ def run_ours(args, rank, world, local):
                  "sample": f"{k} ciphertexts x {SPC} samples, one ciphertext per launch, eager"}
 
     # max over ranks
-    ms_step = ms_dev / args.steps
-    ms_e2e = ms_e2e_wall / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_step, ms_e2e], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, ms_e2e = float(t[0]), float(t[1])
+    ms_step, ms_e2e = max_over_ranks([ms_dev / args.steps, ms_e2e_wall / args.steps], dist, f"cuda:{local}")
     total_samples = args.samples * world
     pk = peaks()
     roof = None
@@ -489,7 +501,7 @@ def run_ours(args, rank, world, local):
                      "top_layer_kernels_ms": {k: round(v[1], 3) for k, v in
                                               sorted(tagged.items(), key=lambda kv: -kv[1][1])[:12]}})
     res = {
-        "metric": METRIC, "value": round(total_samples / (ms_step / 1e3), 3), "unit": UNIT,
+        "metric": METRIC, "value": round(whole_job_rate(args.samples, world, ms_step), 3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS residues), f64 encode",
         "data": "synthetic U[0,1] 28x28 images, N(0,0.1^2) weights (MNIST / trained weights absent)",

@@ -256,7 +256,7 @@ void keyswitch_init(Ctx *c);
 
 Ctx *ctx_create(const he_params *p) {
     if (!p || p->log2n < 4 || p->log2n > 15 || p->n_data < 1 || p->n_data > 32 || p->n_special < 1 ||
-        p->n_special > 4 || !p->prime_bits || p->dnum < 1 || p->dnum > p->n_data)
+        p->n_special > 4 || !p->prime_bits || p->dnum < 1 || p->dnum > p->n_data || p->dnum > 16)
         throw HeError(HE_EINVAL, "he_params out of range");
     if (p->n_data + p->n_special > HE_MAX_PRIMES) throw HeError(HE_EINVAL, "too many primes");
     std::vector<u32> bits(p->prime_bits, p->prime_bits + p->n_data + p->n_special);
@@ -294,6 +294,11 @@ Ctx *ctx_create(const he_params *p) {
         d.mu64 = (u64)((((unsigned __int128)1) << 64) / q);
         d.r64 = (u64)((((unsigned __int128)1) << 64) % q);
         d.r64s = (u64)(((unsigned __int128)d.r64 << 64) / q);
+        {
+            u64 inv = q;   // Newton iteration for q^{-1} mod 2^64 (q odd): 5 steps double 3 correct bits to 96
+            for (int it = 0; it < 5; ++it) inv *= 2 - q * inv;
+            d.qneginv = (u64)0 - inv;
+        }
         d.ninv = powm(N % q, q - 2, q);
         d.ninvs = (u64)(((unsigned __int128)d.ninv << 64) / q);
         c->pdev_h.push_back(d);
@@ -311,12 +316,12 @@ Ctx *ctx_create(const he_params *p) {
             pw[k] = mulm(pw[k - 1], psi, q);
             ipw[k] = mulm(ipw[k - 1], ipsi, q);
         }
-        for (u32 k = 0; k < N; ++k) {
+        for (u32 k = 0; k < N; ++k) {   // (w, w') pairs, forward then inverse
             u64 w = pw[bitrev(k, c->logn)], iw = ipw[bitrev(k, c->logn)];
-            t[k] = w;
-            t[N + k] = (u64)(((unsigned __int128)w << 64) / q);
-            t[2 * N + k] = iw;
-            t[3 * N + k] = (u64)(((unsigned __int128)iw << 64) / q);
+            t[2 * k] = w;
+            t[2 * k + 1] = (u64)(((unsigned __int128)w << 64) / q);
+            t[2 * N + 2 * k] = iw;
+            t[2 * N + 2 * k + 1] = (u64)(((unsigned __int128)iw << 64) / q);
         }
     }
     CUDA_TRY(cudaMalloc(&c->tw, tw.size() * 8));
@@ -395,6 +400,15 @@ __global__ void add_scaled_rows_kernel(u64 *out, const u64 *x, u64 c0, u64 c1, u
     out[o] = add_mod(out[o], mul_shoup(x[o], cst[2 * t], cst[2 * t + 1], q), q);
 }
 
+// a[r][n] *= 2^64 mod q, q the prime of row r (rows r % period: 0..period-1 = every prime of the chain)
+__global__ void to_montgomery_kernel(u64 *a, u32 rows, u32 period, u32 logn, const PrimeDev *pd) {
+    const u32 N = 1u << logn;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)rows * N) return;
+    const PrimeDev &P = pd[(u32)(idx >> logn) % period];
+    a[idx] = mul_shoup(a[idx], P.r64, P.r64s, P.q);
+}
+
 static void make_ksk(Ctx *c, u64 *key, const u64 *sp, u32 key_id) {
     const u32 E = c->nprimes(), N = c->N;
     // [P]_{q_t} (Shoup pairs) for t < L1
@@ -429,6 +443,13 @@ static void make_ksk(Ctx *c, u64 *key, const u64 *sp, u32 key_id) {
             note_launch(c, "ksk_gadget");
         }
     }
+    // stored in Montgomery form (times 2^64 mod q): the key-switch inner products
+    // reduce their 128-bit sums with one Montgomery reduction
+    const size_t total = (size_t)c->dnum * 2 * E * N;
+    prof_begin(c);
+    to_montgomery_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(key, c->dnum * 2 * E, E, c->logn,
+                                                                              c->pdev);
+    note_launch(c, "ksk_montgomery");
 }
 
 void keygen(Ctx *c, const std::vector<int> &steps) {
@@ -663,9 +684,11 @@ Cts ct_square(Ctx *c, const Cts &a) {
     kl.g[0] = 1;
     DBuf acc(c, (size_t)B * 2 * E * N);
     ks_inner(c, acc.p, D.p, kl, 1, B, lp);
-    Cts r = cts_alloc(c, B, lp, a.scale * a.scale, a.lay);
-    ks_moddown(c, r.data(), acc.p, d.p, (size_t)3 * lp * N, 3, kl, 1, B, lp);
-    return ct_rescale(c, r);
+    // relinearise and rescale as one division by q_top * P: P * (d0, d1) joins the accumulators
+    ks_add_p_times(c, acc.p, d.p, B, lp);
+    Cts r = cts_alloc(c, B, lp - 1, a.scale * a.scale / (double)c->primes[lp - 1], a.lay);
+    ks_moddown_rescale(c, r.data(), acc.p, B, lp);
+    return r;
 }
 
 // Y = sum_i Rot(X_i, steps[i]) over the CH channels of X (CH*B ciphertexts, channel-major),
@@ -714,7 +737,7 @@ Cts ct_lincomb_diag(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> 
 // (one output per channel).  The weighted key-switch accumulators, with P*sigma(c0)
 // folded in, are summed over Q_l u P and ModDown runs once per output ciphertext.
 Cts ct_lincomb(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps, const u64 *pts, u32 O,
-               double pt_scale) {
+               double pt_scale, bool rescale) {
     const u32 N = c->N, lp = X.lp, E = lp + c->K, Bt = CH * B, S = (u32)steps.size();
     if (X.B != Bt) throw HeError(HE_EINVAL, "lincomb: batch mismatch");
     bool any_ks = false;
@@ -756,7 +779,14 @@ Cts ct_lincomb(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &step
             sum_stack(c, Z.p, acc.p, (size_t)Bt * 2 * E * N, Sc, Bt * 2 * E, E, lp, c->L1, s0 > 0);
         }
     }
-    Cts out = cts_alloc(c, nout * B, lp, X.scale * (pts ? pt_scale : 1.0), X.lay);
+    const double scale = X.scale * (pts ? pt_scale : 1.0);
+    if (rescale) {
+        if (lp < 2) throw HeError(HE_ELEVEL, "rescale: no level left");
+        Cts out = cts_alloc(c, nout * B, lp - 1, scale / (double)c->primes[lp - 1], X.lay);
+        ks_moddown_rescale(c, out.data(), Z.p, nout * B, lp);
+        return out;
+    }
+    Cts out = cts_alloc(c, nout * B, lp, scale, X.lay);
     KeyList none;
     none.g[0] = 1;
     none.key[0] = nullptr;

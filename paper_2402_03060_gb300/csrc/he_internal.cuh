@@ -35,6 +35,7 @@ struct PrimeDev {
     u64 r64s;    // Shoup companion of r64
     u64 ninv;    // N^{-1} mod q
     u64 ninvs;
+    u64 qneginv; // -q^{-1} mod 2^64 (Montgomery reduction)
     u32 s;       // bit length of q
     u32 pad;
 };
@@ -68,6 +69,14 @@ __device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const PrimeDev &P) {
     u64 a = mul_shoup(h, P.r64, P.r64s, P.q);
     u64 b = reduce64(lo, P);
     return add_mod(a, b, P.q);
+}
+
+// Montgomery reduction (Montgomery 1985) of a 128-bit x = hi*2^64 + lo < q*2^64:
+// x * 2^{-64} mod q in [0, q).  m = lo * (-q^{-1}) makes x + m*q divisible by 2^64.
+__device__ __forceinline__ u64 redc128(u64 lo, u64 hi, const PrimeDev &P) {
+    const u64 m = lo * P.qneginv;
+    const u64 t = hi + mulhi64(m, P.q) + (lo != 0 ? 1 : 0);
+    return t >= P.q ? t - P.q : t;
 }
 
 // a * b mod q for a, b < q (HAC 14.42, base 2, k = s)
@@ -219,7 +228,7 @@ struct Ctx : std::enable_shared_from_this<Ctx> {
     std::vector<PrimeDev> pdev_h;
     // device tables
     PrimeDev *pdev = nullptr;      // [nprimes]
-    u64 *tw = nullptr;             // per prime: psi_rev, psi_rev_shoup, ipsi_rev, ipsi_rev_shoup (4N)
+    u64 *tw = nullptr;             // per prime (4N words): (psi_rev, Shoup) pairs, then (ipsi_rev, Shoup) pairs
     double *fft_w = nullptr;       // cos/sin of 2*pi*k/M, k < M/2 (interleaved)
     double *fft_t = nullptr;       // cos/sin of pi*k/N, k < M (interleaved)
     u32 *slot_pos_br = nullptr;    // bit-reversed DFT position of slot j

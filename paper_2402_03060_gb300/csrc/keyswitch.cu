@@ -80,8 +80,8 @@ __global__ void ks_inner_kernel(u64 *acc, const u64 *__restrict__ D, KeyList kl,
     }
     const PrimeDev &P = pd[pt];
     u64 *o = acc + (((size_t)s * B + b) * 2 * E + t) * N + n;
-    o[0] = reduce128(a0.lo, a0.hi, P);
-    o[(size_t)E * N] = reduce128(a1.lo, a1.hi, P);
+    o[0] = redc128(a0.lo, a0.hi, P);   // keys are in Montgomery form
+    o[(size_t)E * N] = redc128(a1.lo, a1.hi, P);
 }
 
 // Accumulators of a hoisted linear combination, before any ModDown:
@@ -124,9 +124,10 @@ __global__ void ks_lazy_kernel(u64 *acc, const u64 *__restrict__ D, const u64 *_
         mac128(a0, d, __ldg(kj));
         mac128(a1, d, __ldg(kj + kstride));
     }
-    if (t < lp) mac128(a0, xb[(size_t)t * N + src], pq[2 * t]);
-    o[0] = reduce128(a0.lo, a0.hi, P);
-    o[(size_t)E * N] = reduce128(a1.lo, a1.hi, P);
+    u64 r0 = redc128(a0.lo, a0.hi, P);   // keys are in Montgomery form
+    if (t < lp) r0 = add_mod(r0, mul_shoup(xb[(size_t)t * N + src], pq[2 * t], pq[2 * t + 1], P.q), P.q);
+    o[0] = r0;
+    o[(size_t)E * N] = redc128(a1.lo, a1.hi, P);
 }
 
 // Same accumulators, computed with keys stored pre-permuted: K'_{g,j} = sigma_g^{-1}(K_{g,j}), so
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(256, 2) ks_lazy_perm_kernel(u64 *acc, const u6
                 o[(size_t)E * N + n] = pc1[u];
                 continue;
             }
-            Acc128 a0 = {pc0[u], 0}, a1 = {0, 0};
+            Acc128 a0 = {0, 0}, a1 = {0, 0};
 #pragma unroll
             for (u32 j = 0; j < MAXD; ++j) {
                 if (j < beta) {
@@ -197,17 +198,23 @@ __global__ void __launch_bounds__(256, 2) ks_lazy_perm_kernel(u64 *acc, const u6
                     mac128(a1, d[u][j], k1[j]);
                 }
             }
-            o[dst] = reduce128(a0.lo, a0.hi, P);
-            o[(size_t)E * N + dst] = reduce128(a1.lo, a1.hi, P);
+            // keys are in Montgomery form: one Montgomery reduction per sum
+            o[dst] = add_mod(redc128(a0.lo, a0.hi, P), pc0[u], P.q);
+            o[(size_t)E * N + dst] = redc128(a1.lo, a1.hi, P);
         }
     }
 }
 
+// Division by the dropped basis D of the accumulators acc [S][B][2][lp+K][N]: D is
+// the KD rows starting at row dbase (dbase = lp: the special primes, ModDown;
+// dbase = lp-1: the top data prime and the special primes, ModDown and rescale in
+// one).  Output limb i < lpo: (acc_i - BConv_{D->q_i}) * D^{-1}, plus the addend.
 template <int SPLIT>
 __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, const u64 *__restrict__ acc,
                                                        const u64 *__restrict__ addend, size_t addend_bstride,
                                                        u32 add_mask, KeyList kl, u32 B, u32 lp, u32 K, u32 L1,
-                                                       int logn, const u64 *__restrict__ mdtab,
+                                                       u32 dbase, u32 KD, u32 lpo, int logn,
+                                                       const u64 *__restrict__ mdtab,
                                                        const u64 *__restrict__ tw_all,
                                                        const PrimeDev *__restrict__ pd) {
     extern __shared__ u64 sm[];
@@ -218,17 +225,18 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, cons
     const u32 E = lp + K;
     const PrimeDev P = pd[i];
     const u64 *ab = acc + (((size_t)s * B + b) * 2 + k) * E * N;
-    // mdtab: phinv[K], phinv_s[K], phmod[K][L1], Pinv[L1], Pinv_s[L1]
+    // mdtab: dhinv[KD], dhinv_s[KD], dhmod[KD][L1], Dinv[L1], Dinv_s[L1]
     for (u32 n = pt.lo + threadIdx.x; n < pt.lo + pt.n; n += blockDim.x) {
         u64 v;
-        if (K == 1) {
-            v = reduce64(ab[(size_t)lp * N + n], P);
+        if (KD == 1) {
+            v = reduce64(ab[(size_t)dbase * N + n], P);
         } else {
             Acc128 a = {0, 0};
-            for (u32 kk = 0; kk < K; ++kk) {
-                const PrimeDev &Pk = pd[L1 + kk];
-                u64 y = mul_shoup(ab[(size_t)(lp + kk) * N + n], mdtab[kk], mdtab[K + kk], Pk.q);
-                mac128(a, y, mdtab[2 * K + (size_t)kk * L1 + i]);
+            for (u32 kk = 0; kk < KD; ++kk) {
+                const u32 row = dbase + kk;
+                const PrimeDev &Pk = pd[row < lp ? row : L1 + (row - lp)];
+                u64 y = mul_shoup(ab[(size_t)row * N + n], mdtab[kk], mdtab[KD + kk], Pk.q);
+                mac128(a, y, mdtab[2 * KD + (size_t)kk * L1 + i]);
             }
             v = reduce128(a.lo, a.hi, P);
         }
@@ -236,17 +244,32 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, cons
     }
     __syncthreads();
     part_ntt_fwd(sm, pt, logn, tw_all + (size_t)i * 4 * N, P.q);
-    const u64 pinv = mdtab[2 * K + (size_t)K * L1 + i];
-    const u64 pinvs = mdtab[2 * K + (size_t)K * L1 + L1 + i];
+    const u64 pinv = mdtab[2 * KD + (size_t)KD * L1 + i];
+    const u64 pinvs = mdtab[2 * KD + (size_t)KD * L1 + L1 + i];
     const bool add = addend && ((add_mask >> k) & 1);
     const u32 g = kl.g[s];
-    const u64 *adb = add ? addend + (size_t)b * addend_bstride + ((size_t)k * lp + i) * N : nullptr;
-    u64 *ob = out + ((((size_t)s * B + b) * 2 + k) * lp + i) * N;
+    const u64 *adb = add ? addend + (size_t)b * addend_bstride + ((size_t)k * lpo + i) * N : nullptr;
+    u64 *ob = out + ((((size_t)s * B + b) * 2 + k) * lpo + i) * N;
     for (u32 n = pt.lo + threadIdx.x; n < pt.lo + pt.n; n += blockDim.x) {
         u64 o = mul_shoup(sub_mod(ab[(size_t)i * N + n], sm[spad(n - pt.lo)], P.q), pinv, pinvs, P.q);
         if (add) o = add_mod(o, adb[g == 1 ? n : galois_src(n, g, logn)], P.q);
         ob[n] = o;
     }
+}
+
+// acc[b][k][t] += P * d[b][k][t] on the data limbs t < lp (d: [B][3][lp][N], k < 2)
+__global__ void add_p_times_kernel(u64 *acc, const u64 *__restrict__ d, u32 lp, u32 K, int logn,
+                                   const u64 *__restrict__ pq, const PrimeDev *__restrict__ pd, u32 B) {
+    const u32 N = 1u << logn;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)B * 2 * lp * N) return;
+    const u32 n = (u32)(idx & (N - 1));
+    size_t r = idx >> logn;
+    const u32 t = (u32)(r % lp), k = (u32)((r / lp) % 2), b = (u32)(r / (2 * lp));
+    const u64 q = pd[t].q;
+    u64 *a = acc + (((size_t)b * 2 + k) * (lp + K) + t) * N + n;
+    const u64 x = d[(((size_t)b * 3 + k) * lp + t) * N + n];
+    *a = add_mod(*a, mul_shoup(x, pq[2 * t], pq[2 * t + 1], q), q);
 }
 
 template <int SPLIT>
@@ -332,34 +355,47 @@ static const u64 *modup_table(Ctx *c, u32 lp) {
     return c->const_table(key, h);
 }
 
-static const u64 *moddown_table(Ctx *c) {
-    std::string key = "moddown";
+// Division table of a dropped basis D = {d_0..d_{KD-1}} (prime indices dp) onto the data primes:
+// dhinv[KD], dhinv_s[KD] ((D/d_k)^{-1} mod d_k), dhmod[KD][L1] ((D/d_k) mod q_i), Dinv[L1], Dinv_s[L1]
+static const u64 *drop_table(Ctx *c, const std::string &key, const std::vector<u32> &dp) {
     auto it = c->cache.find(key);
     if (it != c->cache.end()) return it->second.p;
-    const u32 K = c->K, L1 = c->L1;
-    std::vector<u64> h(2 * K + (size_t)K * L1 + 2 * L1, 0);
-    for (u32 k = 0; k < K; ++k) {
-        u64 pk = c->primes[L1 + k];
+    const u32 KD = (u32)dp.size(), L1 = c->L1;
+    std::vector<u64> h(2 * KD + (size_t)KD * L1 + 2 * L1, 0);
+    for (u32 k = 0; k < KD; ++k) {
+        u64 pk = c->primes[dp[k]];
         u64 hh = 1;
-        for (u32 m = 0; m < K; ++m)
-            if (m != k) hh = mulmod_h(hh, c->primes[L1 + m] % pk, pk);
+        for (u32 m = 0; m < KD; ++m)
+            if (m != k) hh = mulmod_h(hh, c->primes[dp[m]] % pk, pk);
         h[k] = invmod_h(hh, pk);
-        h[K + k] = shoup_h(h[k], pk);
+        h[KD + k] = shoup_h(h[k], pk);
         for (u32 i = 0; i < L1; ++i) {
             u64 qi = c->primes[i], m2 = 1;
-            for (u32 m = 0; m < K; ++m)
-                if (m != k) m2 = mulmod_h(m2, c->primes[L1 + m] % qi, qi);
-            h[2 * K + (size_t)k * L1 + i] = m2;
+            for (u32 m = 0; m < KD; ++m)
+                if (m != k) m2 = mulmod_h(m2, c->primes[dp[m]] % qi, qi);
+            h[2 * KD + (size_t)k * L1 + i] = m2;
         }
     }
     for (u32 i = 0; i < L1; ++i) {
-        u64 qi = c->primes[i], P = 1;
-        for (u32 k = 0; k < K; ++k) P = mulmod_h(P, c->primes[L1 + k] % qi, qi);
-        u64 inv = invmod_h(P, qi);
-        h[2 * K + (size_t)K * L1 + i] = inv;
-        h[2 * K + (size_t)K * L1 + L1 + i] = shoup_h(inv, qi);
+        u64 qi = c->primes[i], D = 1;
+        for (u32 k = 0; k < KD; ++k) D = mulmod_h(D, c->primes[dp[k]] % qi, qi);
+        u64 inv = D ? invmod_h(D, qi) : 0;   // D = 0 mod q_i only for the dropped data prime itself (never an output)
+        h[2 * KD + (size_t)KD * L1 + i] = inv;
+        h[2 * KD + (size_t)KD * L1 + L1 + i] = shoup_h(inv, qi);
     }
     return c->const_table(key, h);
+}
+
+static const u64 *moddown_table(Ctx *c) {
+    std::vector<u32> dp;
+    for (u32 k = 0; k < c->K; ++k) dp.push_back(c->L1 + k);
+    return drop_table(c, "moddown", dp);
+}
+
+static const u64 *moddown_rescale_table(Ctx *c, u32 lp) {
+    std::vector<u32> dp{lp - 1};
+    for (u32 k = 0; k < c->K; ++k) dp.push_back(c->L1 + k);
+    return drop_table(c, fmt("moddown_rs:%u", lp), dp);
 }
 
 static const u64 *rescale_table(Ctx *c, u32 lp) {
@@ -484,12 +520,49 @@ void ks_moddown(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bst
     dim3 grid(lp, 2, S * B);
     prof_begin(c);
     const int sp = tune_split(c, TUNE_MODDOWN);
-    launch_parts(c, moddown_kernel<0>, moddown_kernel<1>, grid, sp, ntt_part_threads(c->logn, sp), ntt_part_smem(c->logn, sp), out, (const u64 *)acc,
-                 addend, addend_bstride, add_mask, kl, B, lp, c->K, c->L1, c->logn, moddown_table(c),
-                 (const u64 *)c->tw, (const PrimeDev *)c->pdev);
+    launch_parts(c, moddown_kernel<0>, moddown_kernel<1>, grid, sp, ntt_part_threads(c->logn, sp),
+                 ntt_part_smem(c->logn, sp), out, (const u64 *)acc, addend, addend_bstride, add_mask, kl, B, lp,
+                 c->K, c->L1, lp, c->K, lp, c->logn, moddown_table(c), (const u64 *)c->tw,
+                 (const PrimeDev *)c->pdev);
     note_launch(c, "moddown",
                 8.0 * N * (double)S * B * (2.0 * E + (addend ? __builtin_popcount(add_mask) : 0) * lp + 2.0 * lp),
                 (double)S * B * 2 * lp * (N / 2) * c->logn);
+}
+
+// out [nct][2][lp-1][N] = ModDown and rescale of acc [nct][2][lp+K][N] as one division by q_top * P
+void ks_moddown_rescale(Ctx *c, u64 *out, u64 *acc, u32 nct, u32 lp) {
+    const u32 N = c->N, E = lp + c->K;
+    if (lp < 2) throw HeError(HE_ELEVEL, "rescale: no level left");
+    // inverse NTT of the dropped rows: the top data limb and the special limbs
+    std::string key = fmt("mdrs_rows:%u:%u", nct, lp);
+    std::vector<u32> rows;
+    for (u32 b = 0; b < nct; ++b)
+        for (u32 k = 0; k < 2; ++k) {
+            rows.push_back((((b * 2 + k) * E + lp - 1) << 8) | (lp - 1));
+            for (u32 kk = 0; kk < c->K; ++kk) rows.push_back((((b * 2 + k) * E + lp + kk) << 8) | (c->L1 + kk));
+        }
+    ntt_inverse(c, acc, rows_list(c, key, rows));
+    KeyList none;
+    none.g[0] = 1;
+    none.key[0] = nullptr;
+    dim3 grid(lp - 1, 2, nct);
+    prof_begin(c);
+    const int sp = tune_split(c, TUNE_MODDOWN);
+    launch_parts(c, moddown_kernel<0>, moddown_kernel<1>, grid, sp, ntt_part_threads(c->logn, sp),
+                 ntt_part_smem(c->logn, sp), out, (const u64 *)acc, (const u64 *)nullptr, (size_t)0, 0u, none,
+                 nct, lp, c->K, c->L1, lp - 1, c->K + 1, lp - 1, c->logn, moddown_rescale_table(c, lp),
+                 (const u64 *)c->tw, (const PrimeDev *)c->pdev);
+    note_launch(c, "moddown", 8.0 * N * (double)nct * (2.0 * E + 2.0 * (lp - 1)),
+                (double)nct * 2 * (lp - 1) * (N / 2) * c->logn);
+}
+
+// acc [B][2][lp+K][N] += P * (d0, d1) on the data limbs; d [B][3][lp][N]
+void ks_add_p_times(Ctx *c, u64 *acc, const u64 *d, u32 B, u32 lp) {
+    const size_t total = (size_t)B * 2 * lp * c->N;
+    prof_begin(c);
+    add_p_times_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(acc, d, lp, c->K, c->logn,
+                                                                            pmod_table(c), c->pdev, B);
+    note_launch(c, "add_p_times", 8.0 * c->N * (double)B * 2 * lp * 3);
 }
 
 // out [B][2][lp-1][N] = rescale(in [B][2][lp][N])

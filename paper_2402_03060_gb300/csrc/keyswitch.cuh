@@ -22,3 +22,5 @@ void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u3
 void ks_moddown(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bstride, u32 add_mask,
                 const KeyList &kl, u32 S, u32 B, u32 lp);
 void rescale_batch(Ctx *c, u64 *out, const u64 *in, u32 B, u32 lp);
+void ks_moddown_rescale(Ctx *c, u64 *out, u64 *acc, u32 nct, u32 lp);
+void ks_add_p_times(Ctx *c, u64 *acc, const u64 *d, u32 B, u32 lp);

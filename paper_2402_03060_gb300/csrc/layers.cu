@@ -100,11 +100,11 @@ static Feat layer_conv(Ctx *c, const Feat &in, const LayerSpec &sp, u32 kh, u32 
         }
         return get_pts(c, pc, k, tmp, L, off, pos, val, c->scale, lp, ext);
     };
-    Cts acc;
+    Cts out;
     if (!incremental) {
-        // one hoisted linear combination per output channel, one ModDown each
+        // one hoisted linear combination per output channel, ModDown and rescale as one division each
         const u64 *pts = weight_pts(c->K);
-        acc = ct_lincomb(c, in.x, ci, B, steps, pts, co, c->scale);
+        out = ct_lincomb(c, in.x, ci, B, steps, pts, co, c->scale, true);
     } else {
         // rotated inputs R[off][ch*B + b]  (T index = off*ci + ch)
         Cts R = cts_alloc(c, KK * ci * B, lp, in.x.scale, L);
@@ -119,11 +119,11 @@ static Feat layer_conv(Ctx *c, const Feat &in, const LayerSpec &sp, u32 kh, u32 
                                      cudaMemcpyDeviceToDevice, c->stream));
         }
         const u64 *pts = weight_pts(0);
-        acc = cts_alloc(c, co * B, lp, in.x.scale * c->scale, L);
+        Cts acc = cts_alloc(c, co * B, lp, in.x.scale * c->scale, L);
         // R[off][i*B + b] is block t = off*ci + i of B ciphertexts
         mac(c, acc.data(), (size_t)B * ctw, R.data(), (size_t)B * ctw, pts, co, T, B, lp);
+        out = ct_rescale(c, acc);
     }
-    Cts out = ct_rescale(c, acc);
     {
         std::vector<u32> off, pos;
         std::vector<double> val;
@@ -219,7 +219,7 @@ static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string
         flat.n_samples = 1;
         flat.stride = M;
         const u64 *pts = get_pts(c, pc, name, tmp, flat, off, apos, val, c->scale, x.lp, c->K);
-        return ct_rescale(c, ct_lincomb(c, x, 1, x.B, steps, pts, 1, c->scale));
+        return ct_lincomb(c, x, 1, x.B, steps, pts, 1, c->scale, true);
     };
     if (L.prev == PREV_POOL) {
         std::vector<std::vector<u32>> pos(W);
@@ -357,8 +357,7 @@ static Feat layer_fc(Ctx *c, const Feat &in, const LayerSpec &sp, PtCache *pc, c
     (void)T;
     (void)ctw;
     // C_sum: every rotation of the input with its V1 / V2 vector, one ModDown
-    Cts acc = ct_lincomb(c, in.x, 1, B, steps, pts, 1, c->scale);
-    Cts cs = ct_rescale(c, acc);
+    Cts cs = ct_lincomb(c, in.x, 1, B, steps, pts, 1, c->scale, true);
     // C_out = sum_i Rot(C_sum, i * dout); FC field k = 1 selects the tree form
     Cts out = rotation_sum(c, cs, B, dout, Wv / dout, sp.k == 1);
     {

@@ -3,8 +3,9 @@
 // Forward: Cooley-Tukey butterflies with psi powers in bit-reversed order
 // (Longa & Naehrig 2016, Alg. 1), output in bit-reversed evaluation order:
 // slot i holds a(psi^(2*brev(i)+1)).  Inverse: Gentleman-Sande with inverse
-// psi powers (their Alg. 2) followed by the N^{-1} scaling.  Twiddle tables
-// per prime: [psi_rev | psi_rev_shoup | ipsi_rev | ipsi_rev_shoup], N words each.
+// psi powers (their Alg. 2) followed by the N^{-1} scaling.  Twiddle table per
+// prime (4N words): N pairs (psi_rev[i], Shoup companion), then N pairs for the
+// inverse powers -- one 16-byte load per twiddle.
 //
 // Lazy reduction (Harvey 2014): values stay in [0, 4q) between forward
 // butterflies and in [0, 2q) between inverse ones; all primes are below 2^61.
@@ -95,17 +96,25 @@ static void launch_parts(Ctx *c, void (*kern0)(KArgs...), void (*kern1)(KArgs...
     CUDA_TRY(cudaLaunchKernelEx(&cfg, kern1, args...));
 }
 
+// twiddle pair i of the forward / inverse table
+__device__ __forceinline__ ulonglong2 tw_fwd(const u64 *__restrict__ tw, u32 i) {
+    return __ldg(reinterpret_cast<const ulonglong2 *>(tw) + i);
+}
+__device__ __forceinline__ ulonglong2 tw_inv(const u64 *__restrict__ tw, u32 N, u32 i) {
+    return __ldg(reinterpret_cast<const ulonglong2 *>(tw + 2 * (size_t)N) + i);
+}
+
 // ---------------------------------------------------------------- forward
 __device__ __forceinline__ void fwd_radix2_stage(u64 *a, int logn, int lgm, const u64 *__restrict__ tw, u64 q) {
     const u32 N = 1u << logn;
-    const u64 *tws = tw + N;
     const u64 q2 = 2 * q;
     const int lgt = logn - 1 - lgm;
     const u32 t = 1u << lgt;
     for (u32 b = threadIdx.x; b < N / 2; b += blockDim.x) {
         const u32 i = b >> lgt;
         const u32 j = (i << (lgt + 1)) + (b & (t - 1));
-        const u64 S = __ldg(tw + (1u << lgm) + i), Ss = __ldg(tws + (1u << lgm) + i);
+        const ulonglong2 W = tw_fwd(tw, (1u << lgm) + i);
+        const u64 S = W.x, Ss = W.y;
         u64 U = a[spad(j)];
         if (U >= q2) U -= q2;
         const u64 V = shoup_lazy(a[spad(j + t)], S, Ss, q);
@@ -117,11 +126,10 @@ __device__ __forceinline__ void fwd_radix2_stage(u64 *a, int logn, int lgm, cons
 // R stages starting at stage st on groups of 2^R coefficients held in registers.
 // a holds the 2^logl coefficients starting at global index goff of an N = 2^logn
 // limb; every butterfly group of these stages lies inside it.
-template <int R>
+// With LAST the outputs are reduced to [0, q) before they are stored.
+template <int R, bool LAST = false>
 __device__ __forceinline__ void fwd_pass(u64 *a, int logn, int st, const u64 *__restrict__ tw, u64 q,
                                          int logl, u32 goff) {
-    const u32 N = 1u << logn;
-    const u64 *tws = tw + N;
     const u64 q2 = 2 * q;
     const int lgt0 = logn - 1 - st;          // log2 of the first distance t0
     const int lgtl = lgt0 - (R - 1);         // log2 of the smallest distance
@@ -141,7 +149,8 @@ __device__ __forceinline__ void fwd_pass(u64 *a, int logn, int st, const u64 *__
             for (int blk = 0; blk < (1 << u); ++blk) {
                 const u32 j = goff + base + ((u32)(blk * 2 * half) << lgtl);
                 const u32 i = j >> (lgd + 1);
-                const u64 S = __ldg(tw + m + i), Ss = __ldg(tws + m + i);
+                const ulonglong2 W = tw_fwd(tw, m + i);
+                const u64 S = W.x, Ss = W.y;
 #pragma unroll
                 for (int h = 0; h < half; ++h) {
                     const int k = blk * 2 * half + h;
@@ -151,6 +160,15 @@ __device__ __forceinline__ void fwd_pass(u64 *a, int logn, int st, const u64 *__
                     v[k] = U + V;
                     v[k + half] = U - V + q2;
                 }
+            }
+        }
+        if (LAST) {
+#pragma unroll
+            for (int k = 0; k < (1 << R); ++k) {
+                u64 w = v[k];
+                if (w >= q2) w -= q2;
+                if (w >= q) w -= q;
+                v[k] = w;
             }
         }
 #pragma unroll
@@ -164,21 +182,23 @@ __device__ __forceinline__ void fwd_local(u64 *a, int logn, int st0, const u64 *
                                           u32 goff) {
     const u32 L = 1u << logl;
     if (logn >= 10) {
+        // passes of 4 stages; the last pass (4, 3, 2 or 1 stages) also reduces to [0, q)
         int st = st0;
-        for (; st + 4 <= logn; st += 4) {
+        for (; st + 4 < logn; st += 4) {
             fwd_pass<4>(a, logn, st, tw, q, logl, goff);
             __syncthreads();
         }
         const int rem = logn - st;
-        if (rem == 3) fwd_pass<3>(a, logn, st, tw, q, logl, goff);
-        if (rem == 2) fwd_pass<2>(a, logn, st, tw, q, logl, goff);
-        if (rem == 1) fwd_pass<1>(a, logn, st, tw, q, logl, goff);
-        if (rem) __syncthreads();
-    } else {
-        for (int lgm = st0; lgm < logn; ++lgm) {
-            fwd_radix2_stage(a, logn, lgm, tw, q);
-            __syncthreads();
-        }
+        if (rem == 4) fwd_pass<4, true>(a, logn, st, tw, q, logl, goff);
+        if (rem == 3) fwd_pass<3, true>(a, logn, st, tw, q, logl, goff);
+        if (rem == 2) fwd_pass<2, true>(a, logn, st, tw, q, logl, goff);
+        if (rem == 1) fwd_pass<1, true>(a, logn, st, tw, q, logl, goff);
+        __syncthreads();
+        return;
+    }
+    for (int lgm = st0; lgm < logn; ++lgm) {
+        fwd_radix2_stage(a, logn, lgm, tw, q);
+        __syncthreads();
     }
     const u64 q2 = 2 * q;
     for (u32 k = threadIdx.x; k < L; k += blockDim.x) {
@@ -208,7 +228,9 @@ __device__ __forceinline__ void part_ntt_fwd(u64 *a, const Part &p, int logn, co
     cl.sync();  // both halves written
     u64 *a0 = cl.map_shared_rank(a, 0), *a1 = cl.map_shared_rank(a, 1);
     const u32 N = 1u << logn, H = p.n;
-    const u64 S = __ldg(tw + 1), Ss = __ldg(tw + N + 1), q2 = 2 * q;
+    const ulonglong2 W = tw_fwd(tw, 1);
+    const u64 S = W.x, Ss = W.y, q2 = 2 * q;
+    (void)N;
     // stage 0 (distance N/2): pairs (j, j + N/2) sit at local index j of CTA 0 and CTA 1;
     // each CTA takes half of the pairs
     const u32 j0 = p.lo / 2;
@@ -226,14 +248,14 @@ __device__ __forceinline__ void part_ntt_fwd(u64 *a, const Part &p, int logn, co
 // ---------------------------------------------------------------- inverse
 __device__ __forceinline__ void inv_radix2_stage(u64 *a, int logn, int lgt, const u64 *__restrict__ tw, u64 q) {
     const u32 N = 1u << logn;
-    const u64 *itw = tw + 2 * N, *itws = tw + 3 * N;
     const u64 q2 = 2 * q;
     const u32 t = 1u << lgt;
     const u32 h = N >> (lgt + 1);
     for (u32 b = threadIdx.x; b < N / 2; b += blockDim.x) {
         const u32 i = b >> lgt;
         const u32 j = (i << (lgt + 1)) + (b & (t - 1));
-        const u64 S = __ldg(itw + h + i), Ss = __ldg(itws + h + i);
+        const ulonglong2 W = tw_inv(tw, N, h + i);
+        const u64 S = W.x, Ss = W.y;
         const u64 U = a[spad(j)], V = a[spad(j + t)];
         u64 s = U + V;
         if (s >= q2) s -= q2;
@@ -244,11 +266,11 @@ __device__ __forceinline__ void inv_radix2_stage(u64 *a, int logn, int lgt, cons
 
 // R Gentleman-Sande stages with distances 2^lgtl .. 2^(lgtl+R-1) on the 2^logl
 // coefficients starting at global index goff
-template <int R>
+// With LAST the outputs are multiplied by N^{-1} (ninv, Shoup companion ninvs) before they are stored.
+template <int R, bool LAST = false>
 __device__ __forceinline__ void inv_pass(u64 *a, int logn, int lgtl, const u64 *__restrict__ tw, u64 q, int logl,
-                                         u32 goff) {
+                                         u32 goff, u64 ninv = 0, u64 ninvs = 0) {
     const u32 N = 1u << logn;
-    const u64 *itw = tw + 2 * N, *itws = tw + 3 * N;
     const u64 q2 = 2 * q;
     const u32 tl = 1u << lgtl;
     const u32 groups = (1u << logl) >> R;
@@ -266,7 +288,8 @@ __device__ __forceinline__ void inv_pass(u64 *a, int logn, int lgtl, const u64 *
             for (int blk = 0; blk < (1 << (R - 1 - u)); ++blk) {
                 const u32 j = goff + base + ((u32)(blk * 2 * half) << lgtl);
                 const u32 i = j >> (lgd + 1);
-                const u64 S = __ldg(itw + h + i), Ss = __ldg(itws + h + i);
+                const ulonglong2 W = tw_inv(tw, N, h + i);
+                const u64 S = W.x, Ss = W.y;
 #pragma unroll
                 for (int hh = 0; hh < half; ++hh) {
                     const int k = blk * 2 * half + hh;
@@ -278,40 +301,55 @@ __device__ __forceinline__ void inv_pass(u64 *a, int logn, int lgtl, const u64 *
                 }
             }
         }
+        if (LAST) {
+#pragma unroll
+            for (int k = 0; k < (1 << R); ++k) v[k] = mul_shoup(v[k], ninv, ninvs, q);
+        }
 #pragma unroll
         for (int k = 0; k < (1 << R); ++k) a[spad(base + ((u32)k << lgtl))] = v[k];
     }
 }
 
-// inverse stages with distances 1 .. 2^(nst-1) on the local coefficients
+// inverse stages with distances 1 .. 2^(nst-1) on the local coefficients; with
+// scale the last pass also multiplies by N^{-1} (the radix-2 path for N < 1024
+// does it in a separate loop)
 __device__ __forceinline__ void inv_local(u64 *a, int logn, int nst, const u64 *__restrict__ tw, u64 q, int logl,
-                                          u32 goff) {
+                                          u32 goff, bool scale, u64 ninv, u64 ninvs) {
     if (logn >= 10) {
         int lgt = 0;
-        for (; lgt + 4 <= nst; lgt += 4) {
+        for (; lgt + 4 < nst; lgt += 4) {
             inv_pass<4>(a, logn, lgt, tw, q, logl, goff);
             __syncthreads();
         }
         const int rem = nst - lgt;
-        if (rem == 3) inv_pass<3>(a, logn, lgt, tw, q, logl, goff);
-        if (rem == 2) inv_pass<2>(a, logn, lgt, tw, q, logl, goff);
-        if (rem == 1) inv_pass<1>(a, logn, lgt, tw, q, logl, goff);
-        if (rem) __syncthreads();
-    } else {
-        for (int lgt = 0; lgt < nst; ++lgt) {
-            inv_radix2_stage(a, logn, lgt, tw, q);
-            __syncthreads();
+        if (scale) {
+            if (rem == 4) inv_pass<4, true>(a, logn, lgt, tw, q, logl, goff, ninv, ninvs);
+            if (rem == 3) inv_pass<3, true>(a, logn, lgt, tw, q, logl, goff, ninv, ninvs);
+            if (rem == 2) inv_pass<2, true>(a, logn, lgt, tw, q, logl, goff, ninv, ninvs);
+            if (rem == 1) inv_pass<1, true>(a, logn, lgt, tw, q, logl, goff, ninv, ninvs);
+        } else {
+            if (rem == 4) inv_pass<4>(a, logn, lgt, tw, q, logl, goff);
+            if (rem == 3) inv_pass<3>(a, logn, lgt, tw, q, logl, goff);
+            if (rem == 2) inv_pass<2>(a, logn, lgt, tw, q, logl, goff);
+            if (rem == 1) inv_pass<1>(a, logn, lgt, tw, q, logl, goff);
         }
+        __syncthreads();
+        return;
+    }
+    for (int lgt = 0; lgt < nst; ++lgt) {
+        inv_radix2_stage(a, logn, lgt, tw, q);
+        __syncthreads();
+    }
+    if (scale) {
+        for (u32 k = threadIdx.x; k < (1u << logl); k += blockDim.x) a[spad(k)] = mul_shoup(a[spad(k)], ninv, ninvs, q);
+        __syncthreads();
     }
 }
 
 // in-place inverse transform including the N^{-1} factor; input in [0, q).
 __device__ __forceinline__ void block_ntt_inv(u64 *a, int logn, const u64 *__restrict__ tw, u64 q, u64 ninv,
                                               u64 ninvs) {
-    const u32 N = 1u << logn;
-    inv_local(a, logn, logn, tw, q, logn, 0);
-    for (u32 k = threadIdx.x; k < N; k += blockDim.x) a[spad(k)] = mul_shoup(a[spad(k)], ninv, ninvs, q);
-    __syncthreads();
+    inv_local(a, logn, logn, tw, q, logn, 0, true, ninv, ninvs);
 }
 
 // inverse transform of the limb held by this CTA's part (see part_ntt_fwd)
@@ -323,11 +361,12 @@ __device__ __forceinline__ void part_ntt_inv(u64 *a, const Part &p, int logn, co
     }
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
-    inv_local(a, logn, logn - 1, tw, q, logn - 1, p.lo);
+    inv_local(a, logn, logn - 1, tw, q, logn - 1, p.lo, false, 0, 0);
     cl.sync();  // both halves through their local stages
     u64 *a0 = cl.map_shared_rank(a, 0), *a1 = cl.map_shared_rank(a, 1);
     const u32 N = 1u << logn, H = p.n;
-    const u64 S = __ldg(tw + 2 * N + 1), Ss = __ldg(tw + 3 * N + 1), q2 = 2 * q;
+    const ulonglong2 W = tw_inv(tw, N, 1);
+    const u64 S = W.x, Ss = W.y, q2 = 2 * q;
     // last stage (distance N/2) fused with the N^{-1} factor
     const u32 j0 = p.lo / 2;
     for (u32 j = j0 + threadIdx.x; j < j0 + H / 2; j += blockDim.x) {

@@ -50,8 +50,9 @@ Cts ct_rotate(Ctx *c, const Cts &a, int step);
 std::vector<Cts> ct_rotate_hoisted(Ctx *c, const Cts &a, const std::vector<int> &steps);
 void ct_rotate_hoisted_into(Ctx *c, const Cts &a, const std::vector<int> &steps, u64 *out);
 Cts ct_square(Ctx *c, const Cts &a);
+// with rescale every output is also rescaled: ModDown and rescale as one division by q_top * P
 Cts ct_lincomb(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps, const u64 *pts, u32 O,
-               double pt_scale);
+               double pt_scale, bool rescale = false);
 Cts ct_lincomb_diag(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps);
 Cts ct_mul_pt(Ctx *c, const Cts &a, const u64 *pt, double pt_scale);
 void ct_add_pt_inplace(Ctx *c, Cts &a, const u64 *pt);
