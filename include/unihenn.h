@@ -185,7 +185,7 @@ void he_model_free(he_model *m);
 /* Chooses the launch shapes of the batched path for this context's N, chain,
  * dnum and GPU by timing each candidate with CUDA events on scratch data (about
  * 1 GB at N = 2^14, released afterwards): limb split over 2-CTA clusters for the
- * NTT, ModDown and rescale kernels; outputs per MAC launch; ciphertexts per
+ * NTT, ModDown and rescale kernels; outputs and polynomials per MAC launch; ciphertexts per
  * thread and grid order of the hoisted key-switch accumulation.  No choice
  * changes a result bit.  cache_path (optional) is a JSON file keyed by device
  * name and parameters: an entry there is used without measuring, a new
@@ -194,8 +194,8 @@ void he_model_free(he_model *m);
  * keep the shapes they were captured with.  Errors: HE_EINVAL, HE_ENOMEM, HE_ECUDA. */
 he_status he_autotune(he_ctx *ctx, const char *cache_path, char *report, size_t report_len);
 /* The tuned knobs in the order: NTT split, ModDown split, rescale split, MAC
- * output group, key-switch ciphertexts per thread, key-switch grid order
- * (-1 = default).  he_tuning_set overrides them (values outside a knob's
+ * output group, key-switch ciphertexts per thread, key-switch grid order,
+ * polynomials per MAC CTA (-1 = default).  he_tuning_set overrides them (values outside a knob's
  * candidates fall back to the nearest valid launch shape). */
 he_status he_tuning_get(he_ctx *ctx, int32_t *values, size_t n);
 he_status he_tuning_set(he_ctx *ctx, const int32_t *values, size_t n);

@@ -307,8 +307,9 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
     // Limb l < lpq uses data prime l, limb l >= lpq special prime pbase + l - lpq.
     if (lpq == ~0u) lpq = lp;
     const u32 BK = 2 * B;
+    const u32 bk_max = (u32)tune_get(c, TUNE_MAC_BK, 64);   // polynomials per CTA (tuned: 16, 32, 64)
     u32 bkc = 1;
-    while (bkc < BK && bkc < 64) bkc <<= 1;
+    while (bkc < BK && bkc < bk_max) bkc <<= 1;
     u32 ntlog = 0;
     while ((1u << ntlog) * bkc < 256) ++ntlog;
     if ((1u << ntlog) > c->N) throw HeError(HE_EINVAL, "mac: ring too small");

@@ -32,7 +32,7 @@ int tune_split(const Ctx *c, int knob) {
 namespace {
 
 const char *knob_name[TUNE_COUNT] = {"ntt_split", "moddown_split", "rescale_split", "mac_group", "lazy_bt",
-                                     "lazy_order"};
+                                     "lazy_order", "mac_bk"};
 
 float time_ms(Ctx *c, const std::function<void()> &f) {
     f();   // warm-up
@@ -155,14 +155,18 @@ void measure(Ctx *c, std::ostringstream &rep) {
         }
     }
     {   // MAC: 12 outputs of 8 terms over Q u P (a convolution's shape)
-        const u32 O = 12, T = 8, Bm = 8;
+        const u32 O = 12, T = 8, Bm = 32;
         DBuf pt(c, (size_t)O * T * E * N), x(c, (size_t)T * Bm * 2 * E * N), out(c, (size_t)O * Bm * 2 * E * N);
         CUDA_TRY(cudaMemsetAsync(pt.p, 0, pt.words * 8, c->stream));
         CUDA_TRY(cudaMemsetAsync(x.p, 0, x.words * 8, c->stream));
         rep << ", ";
-        sweep(c, TUNE_MAC_GROUP, {12, 8, 6, 4}, [&] {
+        auto run = [&] {
             mac(c, out.p, (size_t)Bm * 2 * E * N, x.p, (size_t)Bm * 2 * E * N, pt.p, O, T, Bm, E, lp, c->L1, 0, 0);
-        }, rep);
+        };
+        c->tuned[TUNE_MAC_BK] = 64;
+        sweep(c, TUNE_MAC_GROUP, {12, 8, 6, 4}, run, rep);
+        rep << ", ";
+        sweep(c, TUNE_MAC_BK, {64, 32, 16}, run, rep);
     }
     if (beta <= 8) {   // hoisted key-switch accumulation: 8 steps of 16 ciphertexts
         const u32 S = 8;

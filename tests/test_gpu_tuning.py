@@ -23,9 +23,9 @@ def G():
 
 
 SETTINGS = [
-    dict(ntt_split=1, moddown_split=1, rescale_split=1, mac_group=4, lazy_bt=1, lazy_order=1),
-    dict(ntt_split=0, moddown_split=1, rescale_split=0, mac_group=6, lazy_bt=4, lazy_order=0),
-    dict(ntt_split=1, moddown_split=0, rescale_split=1, mac_group=8, lazy_bt=2, lazy_order=1),
+    dict(ntt_split=1, moddown_split=1, rescale_split=1, mac_group=4, lazy_bt=1, lazy_order=1, mac_bk=16),
+    dict(ntt_split=0, moddown_split=1, rescale_split=0, mac_group=6, lazy_bt=4, lazy_order=0, mac_bk=32),
+    dict(ntt_split=1, moddown_split=0, rescale_split=1, mac_group=8, lazy_bt=2, lazy_order=1, mac_bk=64),
 ]
 
 
@@ -54,7 +54,7 @@ def test_autotune_and_cache(G, tmp_path):
     ctx = G.Context(seed=1, **P)
     path = str(tmp_path / "tune.json")
     rep = ctx.autotune(path)
-    assert "ntt_split" in rep and "mac_group" in rep and "lazy_order" in rep
+    assert "ntt_split" in rep and "mac_group" in rep and "lazy_order" in rep and "mac_bk" in rep
     chosen = ctx.tuning()
     assert all(v >= 0 for v in chosen.values())
     assert chosen["mac_group"] == rep["mac_group"]["chosen"]
