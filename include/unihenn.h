@@ -250,6 +250,10 @@ he_status he_server_submit(he_server *srv, uint32_t model_id, const he_ct *in, u
  * (optional) the time from submit to completion.  HE_ETIMEOUT leaves the
  * request pending; any other status ends it (the status of its batch). */
 he_status he_server_wait(he_server *srv, uint64_t req_id, uint32_t timeout_ms, he_ct **out, double *latency_ms);
+/* Non-blocking: *done = 1 once the request has finished (collect it with
+ * he_server_wait), 0 while it is queued or running.  HE_EINVAL for an unknown
+ * (or already collected) request. */
+he_status he_server_poll(he_server *srv, uint64_t req_id, int *done);
 /* Counters and latency percentiles of one model (model_id) or all (-1). */
 he_status he_server_stats_get(he_server *srv, int32_t model_id, he_server_stats *out);
 /* Runs every queued request to completion, frees uncollected results, stops the thread. */

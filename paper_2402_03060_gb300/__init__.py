@@ -149,6 +149,11 @@ class Server:
         self._req_ctx[rid.value] = self._models[model_id].ctx
         return rid.value
 
+    def poll(self, req_id: int) -> bool:
+        done = ctypes.c_int()
+        check(load().he_server_poll(self.h, req_id, ctypes.byref(done)))
+        return bool(done.value)
+
     def wait(self, req_id: int, timeout_ms: int = 60000):
         """-> (result Ct, latency in ms)"""
         out, lat = ctypes.c_void_p(), ctypes.c_double()

@@ -97,6 +97,7 @@ SIGNATURES = {
     "he_server_add_model": (_int, [_vp, _vp, ctypes.POINTER(_u32)]),
     "he_server_submit": (_int, [_vp, _u32, _vp, ctypes.POINTER(_u64)]),
     "he_server_wait": (_int, [_vp, _u64, _u32, _pp, ctypes.POINTER(_dbl)]),
+    "he_server_poll": (_int, [_vp, _u64, ctypes.POINTER(_int)]),
     "he_server_stats_get": (_int, [_vp, _i32, ctypes.POINTER(he_server_stats)]),
     "he_server_destroy": (None, [_vp]),
     "he_server_simulate": (_int, [ctypes.POINTER(he_server_opts), _u32, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl),

@@ -393,6 +393,16 @@ he_status he_server_wait(he_server *s, uint64_t req_id, uint32_t timeout_ms, he_
     });
 }
 
+he_status he_server_poll(he_server *s, uint64_t req_id, int *done) {
+    return srv_guard([&] {
+        if (!s || !done) throw HeError(HE_EINVAL, "bad arguments");
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(req_id);
+        if (it == s->reqs.end()) throw HeError(HE_EINVAL, "unknown request id");
+        *done = it->second->state == 2 ? 1 : 0;
+    });
+}
+
 he_status he_server_stats_get(he_server *s, int32_t model_id, he_server_stats *out) {
     return srv_guard([&] {
         if (!s || !out) throw HeError(HE_EINVAL, "bad arguments");

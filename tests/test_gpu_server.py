@@ -63,6 +63,7 @@ def test_results_identical_alone_and_mixed(G, two_models):
         del ct                     # the server keeps its own reference
     outs = []
     for (mid, ctx, rid), want in zip(ids, alone):
+        assert srv.poll(rid) in (False, True)
         out, lat = srv.wait(rid)
         assert lat > 0
         got = ctx.export(out)
