@@ -479,6 +479,7 @@ def run_ours(args, rank, world, local):
     if stats:
         peak_hbm = pk["hbm_gbs"] if pk else 6800.0
         alu_peak = {"ntt": bfly_peak, "intt": bfly_peak, "moddown": bfly_peak, "rescale": bfly_peak,
+                    "modup_ntt": bfly_peak,
                     "mac": mac_peak, "ks_lazy": mac_peak, "ks_inner": mac_peak}
 
         def views(v):

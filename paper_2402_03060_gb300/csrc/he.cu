@@ -525,6 +525,7 @@ Cts cts_view(const Cts &base, size_t off_words, u32 B) {
 
 Cts encrypt(Ctx *c, const double *x_dev, u32 W, u32 H, u32 nsamp, u32 spc, u32 stride, u64 enc_seed) {
     if (!c->have_keys) throw HeError(HE_EINVAL, "he_keygen has not run");
+    if (!nsamp) throw HeError(HE_EINVAL, "no samples to encrypt");
     const u32 N = c->N, M = N / 2, L1 = c->L1;
     if (!spc || !stride || (u64)spc * stride > M || (u64)W * H > stride)
         throw HeError(HE_ESLOTS, "samples do not fit in the slots");

@@ -3,7 +3,8 @@
 //   ModUp:   per digit j (consecutive alpha limbs of q_0..q_{lp-1}), fast base
 //            conversion (Bajard et al. 2016 / Halevi-Polyakov-Shoup 2018, no
 //            correction) of the digit's coefficients to every other limb of
-//            Q_l u P; the digit's own limbs are copied in evaluation form.
+//            Q_l u P, fused with that limb's forward NTT; the digit's own limbs
+//            are copied in evaluation form.
 //   inner:   acc_k[t] = sum_j D_j[t] (o) ksk_j,k[t] over Q_l u P, 128-bit lazy,
 //            with the Galois automorphism applied while loading D (hoisting).
 //   ModDown: out_i = (acc_i - BConv_{P->q_i}([acc]_P)) * P^{-1} mod q_i, the
@@ -14,47 +15,77 @@
 #include "keyswitch.cuh"
 #include "ntt_block.cuh"
 
-#define MAX_ALPHA 8
-
-__global__ void modup_kernel(u64 *D, const u64 *__restrict__ xc, const u64 *__restrict__ xe, size_t xe_bstride,
-                             u32 lp, u32 K, u32 L1, u32 alpha, u32 beta, int logn, const u64 *__restrict__ tab,
-                             const PrimeDev *__restrict__ pd) {
+// ModUp rows that need a conversion, fused with their forward NTT: row r of the list is
+// (offset << 8 | prime) with offset = (b*beta + j)*E + t, t outside digit j.  The CTA (or
+// 2-CTA cluster) converts digit j of ciphertext b (coefficient form in xc) to q_t in shared
+// memory -- the same base conversion as modup_kernel -- transforms it and writes D.
+template <int SPLIT>
+__global__ void __launch_bounds__(NTT_MAX_THREADS) modup_ntt_kernel(u64 *D, const u64 *__restrict__ xc, RowSet rs,
+                                                         u32 lp, u32 K, u32 alpha, u32 beta, int logn,
+                                                         const u64 *__restrict__ tab,
+                                                         const u64 *__restrict__ tw_all,
+                                                         const PrimeDev *__restrict__ pd) {
+    extern __shared__ u64 sm[];
     const u32 N = 1u << logn;
-    const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    const u32 j = blockIdx.y, b = blockIdx.z;
+    const Part pt = ntt_part<SPLIT>(logn);
+    const u32 v = rs.list[part_row<SPLIT>()];
+    const u32 off = v >> 8, prime = v & 0xff;
+    const u32 E = lp + K;
+    const u32 t = off % E, bj = off / E;
+    const u32 j = bj % beta, b = bj / beta;
     const u32 lo = j * alpha;
     const u32 hi = lo + alpha < lp ? lo + alpha : lp;
     const u32 nd = hi - lo;
-    const u32 E = lp + K;
+    const PrimeDev P = pd[prime];
     const u64 *tj = tab + (size_t)j * (2 * alpha + alpha * E);
-    u64 v[MAX_ALPHA];
+    const u64 *xb = xc + ((size_t)b * lp + lo) * N;
+    if (nd == 1) {
+        // single-limb digit: reduce each coefficient mod q_t; 16-byte loads, four in flight per thread
+        const ulonglong2 *x2 = reinterpret_cast<const ulonglong2 *>(xb + pt.lo);
+        const u32 half = pt.n / 2;
+        for (u32 k0 = threadIdx.x; k0 < half; k0 += 4 * blockDim.x) {
+            ulonglong2 v[4];
 #pragma unroll
-    for (u32 i = 0; i < MAX_ALPHA; ++i) {
-        if (i < nd) {
-            u64 x = xc[((size_t)b * lp + lo + i) * N + n];
-            v[i] = nd == 1 ? x : mul_shoup(x, tj[i], tj[alpha + i], pd[lo + i].q);
-        }
-    }
-    u64 *Db = D + ((size_t)b * beta + j) * E * N + n;
-    for (u32 t = 0; t < E; ++t) {
-        u64 o;
-        if (t >= lo && t < hi) {
-            o = xe[(size_t)b * xe_bstride + (size_t)t * N + n];
-        } else {
-            const PrimeDev &P = pd[t < lp ? t : L1 + (t - lp)];
-            if (nd == 1) {
-                o = reduce64(v[0], P);
-            } else {
-                Acc128 acc = {0, 0};
+            for (int u = 0; u < 4; ++u) {
+                const u32 k = k0 + u * blockDim.x;
+                if (k < half) v[u] = __ldg(x2 + k);
+            }
 #pragma unroll
-                for (u32 i = 0; i < MAX_ALPHA; ++i)
-                    if (i < nd) mac128(acc, v[i], tj[2 * alpha + (size_t)i * E + t]);
-                o = reduce128(acc.lo, acc.hi, P);
+            for (int u = 0; u < 4; ++u) {
+                const u32 k = k0 + u * blockDim.x;
+                if (k < half) {
+                    sm[spad(2 * k)] = reduce64(v[u].x, P);
+                    sm[spad(2 * k + 1)] = reduce64(v[u].y, P);
+                }
             }
         }
-        Db[(size_t)t * N] = o;
     }
+    for (u32 n = pt.lo + threadIdx.x; nd > 1 && n < pt.lo + pt.n; n += blockDim.x) {
+        u64 o;
+        {
+            Acc128 acc = {0, 0};
+            for (u32 i = 0; i < nd; ++i) {
+                const u64 y = mul_shoup(xb[(size_t)i * N + n], tj[i], tj[alpha + i], pd[lo + i].q);
+                mac128(acc, y, tj[2 * alpha + (size_t)i * E + t]);
+            }
+            o = reduce128(acc.lo, acc.hi, P);
+        }
+        sm[spad(n - pt.lo)] = o;
+    }
+    __syncthreads();
+    part_ntt_fwd(sm, pt, logn, tw_all + (size_t)prime * 4 * N, P.q);
+    block_store(D + (size_t)off * N + pt.lo, sm, pt.n);
+}
+
+// the digits' own rows of D, copied from the evaluation-form input: D[b][j][t] = xe[b][t], t in digit j
+__global__ void modup_own_kernel(u64 *D, const u64 *__restrict__ xe, size_t xe_bstride, u32 lp, u32 K, u32 alpha,
+                                 u32 beta, int logn) {
+    const u32 N = 1u << logn;
+    const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 t = blockIdx.y, b = blockIdx.z;
+    if (n >= N || t >= lp) return;
+    const u32 j = t / alpha, E = lp + K;
+    D[(((size_t)b * beta + j) * E + t) * N + n] = xe[(size_t)b * xe_bstride + (size_t)t * N + n];
 }
 
 __global__ void ks_inner_kernel(u64 *acc, const u64 *__restrict__ D, KeyList kl, u32 B, u32 beta, u32 lp, u32 K,
@@ -157,9 +188,10 @@ __global__ void __launch_bounds__(256, 2) ks_lazy_perm_kernel(u64 *acc, const u6
 #pragma unroll
     for (int u = 0; u < BT; ++u) {
         const u32 b = b0 + u < B ? b0 + u : B - 1;   // clamp: duplicates are computed but not stored
-        const u64 *Db = D + ((size_t)b * beta * E + t) * N + n;
+        // D is null when every step of the launch is the identity (no digit is read then)
+        const u64 *Db = D ? D + ((size_t)b * beta * E + t) * N + n : nullptr;
 #pragma unroll
-        for (u32 j = 0; j < MAXD; ++j) d[u][j] = j < beta ? Db[(size_t)j * E * N] : 0;
+        for (u32 j = 0; j < MAXD; ++j) d[u][j] = (Db && j < beta) ? Db[(size_t)j * E * N] : 0;
         const u64 *xb = x + (size_t)b * 2 * lp * N;
         pc0[u] = pc1[u] = 0;
         if (t < lp) {
@@ -226,21 +258,30 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, cons
     const PrimeDev P = pd[i];
     const u64 *ab = acc + (((size_t)s * B + b) * 2 + k) * E * N;
     // mdtab: dhinv[KD], dhinv_s[KD], dhmod[KD][L1], Dinv[L1], Dinv_s[L1]
-    for (u32 n = pt.lo + threadIdx.x; n < pt.lo + pt.n; n += blockDim.x) {
-        u64 v;
+    // base conversion of two coefficients per thread and iteration (16-byte loads)
+    const u32 half = pt.n / 2;
+    for (u32 k2 = threadIdx.x; k2 < half; k2 += blockDim.x) {
+        const u32 n = pt.lo + 2 * k2;
+        u64 v0, v1;
         if (KD == 1) {
-            v = reduce64(ab[(size_t)dbase * N + n], P);
+            const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ab + (size_t)dbase * N + n);
+            v0 = reduce64(x.x, P);
+            v1 = reduce64(x.y, P);
         } else {
-            Acc128 a = {0, 0};
+            Acc128 a0 = {0, 0}, a1 = {0, 0};
             for (u32 kk = 0; kk < KD; ++kk) {
                 const u32 row = dbase + kk;
                 const PrimeDev &Pk = pd[row < lp ? row : L1 + (row - lp)];
-                u64 y = mul_shoup(ab[(size_t)row * N + n], mdtab[kk], mdtab[KD + kk], Pk.q);
-                mac128(a, y, mdtab[2 * KD + (size_t)kk * L1 + i]);
+                const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ab + (size_t)row * N + n);
+                const u64 hm = mdtab[2 * KD + (size_t)kk * L1 + i];
+                mac128(a0, mul_shoup(x.x, mdtab[kk], mdtab[KD + kk], Pk.q), hm);
+                mac128(a1, mul_shoup(x.y, mdtab[kk], mdtab[KD + kk], Pk.q), hm);
             }
-            v = reduce128(a.lo, a.hi, P);
+            v0 = reduce128(a0.lo, a0.hi, P);
+            v1 = reduce128(a1.lo, a1.hi, P);
         }
-        sm[spad(n - pt.lo)] = v;
+        sm[spad(2 * k2)] = v0;
+        sm[spad(2 * k2 + 1)] = v1;
     }
     __syncthreads();
     part_ntt_fwd(sm, pt, logn, tw_all + (size_t)i * 4 * N, P.q);
@@ -250,10 +291,19 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, cons
     const u32 g = kl.g[s];
     const u64 *adb = add ? addend + (size_t)b * addend_bstride + ((size_t)k * lpo + i) * N : nullptr;
     u64 *ob = out + ((((size_t)s * B + b) * 2 + k) * lpo + i) * N;
-    for (u32 n = pt.lo + threadIdx.x; n < pt.lo + pt.n; n += blockDim.x) {
-        u64 o = mul_shoup(sub_mod(ab[(size_t)i * N + n], sm[spad(n - pt.lo)], P.q), pinv, pinvs, P.q);
-        if (add) o = add_mod(o, adb[g == 1 ? n : galois_src(n, g, logn)], P.q);
-        ob[n] = o;
+    for (u32 k2 = threadIdx.x; k2 < half; k2 += blockDim.x) {
+        const u32 n = pt.lo + 2 * k2;
+        const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ab + (size_t)i * N + n);
+        u64 o0 = mul_shoup(sub_mod(x.x, sm[spad(2 * k2)], P.q), pinv, pinvs, P.q);
+        u64 o1 = mul_shoup(sub_mod(x.y, sm[spad(2 * k2 + 1)], P.q), pinv, pinvs, P.q);
+        if (add) {
+            o0 = add_mod(o0, adb[g == 1 ? n : galois_src(n, g, logn)], P.q);
+            o1 = add_mod(o1, adb[g == 1 ? n + 1 : galois_src(n + 1, g, logn)], P.q);
+        }
+        ulonglong2 r;
+        r.x = o0;
+        r.y = o1;
+        *reinterpret_cast<ulonglong2 *>(ob + n) = r;
     }
 }
 
@@ -317,6 +367,8 @@ static void set_big_smem(const void *fn) {
 }
 
 void keyswitch_init(Ctx *c) {
+    set_big_smem((const void *)modup_ntt_kernel<0>);
+    set_big_smem((const void *)modup_ntt_kernel<1>);
     set_big_smem((const void *)moddown_kernel<0>);
     set_big_smem((const void *)moddown_kernel<1>);
     set_big_smem((const void *)rescale_kernel<0>);
@@ -416,19 +468,21 @@ static const u64 *rescale_table(Ctx *c, u32 lp) {
 // D [B][beta][lp+K][N] from x: coefficient copy xc [B][lp][N] and eval rows at xe (+ b*xe_bstride)
 void ks_modup(Ctx *c, u64 *D, const u64 *xe, size_t xe_bstride, u32 B, u32 lp) {
     const u32 N = c->N, E = lp + c->K, beta = ks_digits(c, lp);
-    if (c->alpha > MAX_ALPHA) throw HeError(HE_EINVAL, "digit size above 8 limbs is not supported");
+    if ((size_t)B * beta * E >= (1u << 24)) throw HeError(HE_EINVAL, "ModUp: batch too large for one launch");
     DBuf xc(c, (size_t)B * lp * N);
     // contiguous copy of the eval rows, then inverse NTT to coefficient form
     CUDA_TRY(cudaMemcpy2DAsync(xc.p, (size_t)lp * N * 8, xe, xe_bstride * 8, (size_t)lp * N * 8, B,
                                cudaMemcpyDeviceToDevice, c->stream));
     ntt_inverse(c, xc.p, rows_regular(B * lp, lp, lp, 0));
     const u64 *tab = modup_table(c, lp);
-    dim3 grid((N + 255) / 256, beta, B);
-    prof_begin(c);
-    modup_kernel<<<grid, 256, 0, c->stream>>>(D, xc.p, xe, xe_bstride, lp, c->K, c->L1, c->alpha, beta, c->logn, tab,
-                                               c->pdev);
-    note_launch(c, "modup", 8.0 * N * ((double)B * lp * 2 + (double)B * beta * E));
-    // forward NTT of every converted (non-own) row
+    // own rows: copies of the evaluation-form input
+    {
+        dim3 grid((N + 255) / 256, lp, B);
+        prof_begin(c);
+        modup_own_kernel<<<grid, 256, 0, c->stream>>>(D, xe, xe_bstride, lp, c->K, c->alpha, beta, c->logn);
+        note_launch(c, "modup", 16.0 * N * (double)B * lp);
+    }
+    // every other row: base conversion of its digit fused with the forward NTT
     std::string key = fmt("modup_rows:%u:%u", B, lp);
     std::vector<u32> rows;
     for (u32 b = 0; b < B; ++b)
@@ -441,7 +495,15 @@ void ks_modup(Ctx *c, u64 *D, const u64 *xe, size_t xe_bstride, u32 B, u32 lp) {
             }
         }
     RowSet rs = rows_list(c, key, rows);
-    ntt_forward(c, D, rs);
+    if (rs.n == 0) return;
+    prof_begin(c);
+    const int sp = tune_split(c, TUNE_NTT);
+    launch_parts(c, modup_ntt_kernel<0>, modup_ntt_kernel<1>, dim3(rs.n), sp, ntt_part_threads(c->logn, sp),
+                 ntt_part_smem(c->logn, sp), D, (const u64 *)xc.p, rs, lp, c->K, c->alpha, beta, c->logn, tab,
+                 (const u64 *)c->tw, (const PrimeDev *)c->pdev);
+    // the digit rows read (mostly from L2), each converted row written once; butterflies of its NTT
+    note_launch(c, "modup_ntt", 8.0 * N * (double)rs.n * (1.0 + c->alpha),
+                (double)rs.n * (N / 2) * c->logn);
 }
 
 // acc [S][B][2][lp+K][N] = sum_j sigma_{g_s}(D_j) (o) key_s,j
@@ -479,8 +541,10 @@ void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u3
     const int bt = tune_get(c, TUNE_LAZY_BT, 2), order = tune_get(c, TUNE_LAZY_ORDER, 0);
     const int maxd = beta <= 2 ? 2 : beta <= 4 ? 4 : 8;
     bool perm = beta <= 8 && (B + bt - 1) / bt <= 65535;
-    for (u32 s = 0; s < S; ++s)
+    for (u32 s = 0; s < S; ++s) {
         if (kl.g[s] != 1 && !kl.keyp[s]) perm = false;
+        if (kl.g[s] != 1 && !D) throw HeError(HE_EINVAL, "ks_lazy: a key-switched step without ModUp digits");
+    }
     prof_begin(c);
     if (perm) {
         const u32 nt = (N + 255) / 256, nb = (B + bt - 1) / bt;

@@ -320,6 +320,35 @@ def test_error_codes(G, pair_small):
     assert e.value.status == 1
 
 
+def test_degenerate_cases(G, pair_small):
+    """Rotation by 0 and by N/2 (the identity Galois element), a hoisted set made
+    only of the identity, a 1x1 convolution, an empty or out-of-range encryption."""
+    from paper_2402_03060_gb300 import HeError
+    ctx, he = pair_small
+    M = he.n // 2
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1, 1, (1, M))
+    ct = ctx.encrypt(x, 1, M, 3)
+    ref = ctx.export(ct)
+    assert np.array_equal(ctx.export(ctx.rotate(ct, 0)), ref)
+    assert np.array_equal(ctx.export(ctx.rotate(ct, M)), ref)
+    hs = ctx.rotate_hoisted(ct, [0, 0])
+    assert np.array_equal(ctx.export(hs[0]), ref) and np.array_equal(ctx.export(hs[1]), ref)
+    # 1x1 convolution: one plaintext product per output, no rotation, no key needed
+    w = np.full((2, 1, 1, 1), 0.5)
+    b = np.array([0.0, 0.25])
+    img = rng.uniform(0, 1, (1, 4, 4))
+    c2 = ctx.encrypt(img, 1, 16, 4)
+    outs = ctx.conv2d([c2], w, b)
+    for o in range(2):
+        got = ctx.decrypt(outs[o], 16)[0]
+        assert np.abs(got - (0.5 * img[0].reshape(-1) + b[o])).max() < 1e-6
+    with pytest.raises(HeError):
+        ctx.encrypt(np.zeros((0, 16)), 1, 16, 1)     # no samples
+    with pytest.raises(HeError):
+        ctx.conv2d([c2], np.zeros((1, 1, 5, 5)), np.zeros(1))   # kernel larger than the image
+
+
 @pytest.mark.slow
 def test_lenet1_full_size_bit_exact(G):
     """LeNet-1 at N=16384 with 10 samples in one ciphertext, against the oracle."""
