@@ -60,7 +60,7 @@ typedef struct {
     uint32_t n_data;             /* data primes (L+1), 1..32 */
     uint32_t n_special;          /* special primes K, 1..4 */
     const uint32_t *prime_bits;  /* n_data + n_special bit sizes, each 20..60 */
-    uint32_t dnum;               /* 1..min(n_data, 16) */
+    uint32_t dnum;               /* 1..min(n_data, 16), with ceil(n_data/dnum) <= 8 */
     double log2_scale;           /* Delta = 2^log2_scale */
     uint64_t seed;               /* key-generation seed (counter-based SplitMix64) */
     int device;                  /* CUDA device ordinal */

@@ -269,6 +269,7 @@ Ctx *ctx_create(const he_params *p) {
     c->K = p->n_special;
     c->dnum = p->dnum;
     c->alpha = (c->L1 + c->dnum - 1) / c->dnum;
+    if (c->alpha > 8) throw HeError(HE_EINVAL, "digits of more than 8 data primes are not supported (raise dnum)");
     c->scale = std::pow(2.0, p->log2_scale);
     c->seed = p->seed;
     c->device = p->device;

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) modup_ntt_kernel(u64 *D, cons
                 const u64 y = mul_shoup(xb[(size_t)i * N + n], tj[i], tj[alpha + i], pd[lo + i].q);
                 mac128(acc, y, tj[2 * alpha + (size_t)i * E + t]);
             }
-            o = reduce128(acc.lo, acc.hi, P);
+            o = redc128(acc.lo, acc.hi, P);
         }
         sm[spad(n - pt.lo)] = o;
     }
@@ -273,12 +273,12 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, cons
                 const u32 row = dbase + kk;
                 const PrimeDev &Pk = pd[row < lp ? row : L1 + (row - lp)];
                 const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ab + (size_t)row * N + n);
-                const u64 hm = mdtab[2 * KD + (size_t)kk * L1 + i];
+                const u64 hm = mdtab[2 * KD + (size_t)kk * L1 + i];   // Montgomery form
                 mac128(a0, mul_shoup(x.x, mdtab[kk], mdtab[KD + kk], Pk.q), hm);
                 mac128(a1, mul_shoup(x.y, mdtab[kk], mdtab[KD + kk], Pk.q), hm);
             }
-            v0 = reduce128(a0.lo, a0.hi, P);
-            v1 = reduce128(a1.lo, a1.hi, P);
+            v0 = redc128(a0.lo, a0.hi, P);
+            v1 = redc128(a1.lo, a1.hi, P);
         }
         sm[spad(2 * k2)] = v0;
         sm[spad(2 * k2 + 1)] = v1;
@@ -378,6 +378,7 @@ void keyswitch_init(Ctx *c) {
 u32 ks_digits(const Ctx *c, u32 lp) { return (lp + c->alpha - 1) / c->alpha; }
 
 // ModUp constants for level lp: per digit j: qhinv[alpha], qhinv_s[alpha], qhmod[alpha][lp+K]
+// (qhmod in Montgomery form: the conversion sum of at most 8 terms is reduced with one REDC)
 static const u64 *modup_table(Ctx *c, u32 lp) {
     std::string key = fmt("modup:%u", lp);
     auto it = c->cache.find(key);
@@ -400,7 +401,7 @@ static const u64 *modup_table(Ctx *c, u32 lp) {
                 u64 m = 1;
                 for (u32 k = lo; k < hi; ++k)
                     if (k != i) m = mulmod_h(m, c->primes[k] % pt, pt);
-                tj[2 * A + (size_t)(i - lo) * E + t] = m;
+                tj[2 * A + (size_t)(i - lo) * E + t] = (u64)(((unsigned __int128)m << 64) % pt);   // Montgomery form
             }
         }
     }
@@ -408,7 +409,8 @@ static const u64 *modup_table(Ctx *c, u32 lp) {
 }
 
 // Division table of a dropped basis D = {d_0..d_{KD-1}} (prime indices dp) onto the data primes:
-// dhinv[KD], dhinv_s[KD] ((D/d_k)^{-1} mod d_k), dhmod[KD][L1] ((D/d_k) mod q_i), Dinv[L1], Dinv_s[L1]
+// dhinv[KD], dhinv_s[KD] ((D/d_k)^{-1} mod d_k), dhmod[KD][L1] ((D/d_k) * 2^64 mod q_i: Montgomery
+// form, the conversion sum is reduced with one REDC), Dinv[L1], Dinv_s[L1]
 static const u64 *drop_table(Ctx *c, const std::string &key, const std::vector<u32> &dp) {
     auto it = c->cache.find(key);
     if (it != c->cache.end()) return it->second.p;
@@ -425,7 +427,7 @@ static const u64 *drop_table(Ctx *c, const std::string &key, const std::vector<u
             u64 qi = c->primes[i], m2 = 1;
             for (u32 m = 0; m < KD; ++m)
                 if (m != k) m2 = mulmod_h(m2, c->primes[dp[m]] % qi, qi);
-            h[2 * KD + (size_t)k * L1 + i] = m2;
+            h[2 * KD + (size_t)k * L1 + i] = (u64)(((unsigned __int128)m2 << 64) % qi);
         }
     }
     for (u32 i = 0; i < L1; ++i) {
