@@ -79,6 +79,17 @@ __device__ __forceinline__ u64 redc128(u64 lo, u64 hi, const PrimeDev &P) {
     return t >= P.q ? t - P.q : t;
 }
 
+// asynchronous 8-byte global -> shared copies (cp.async, grouped with commit / wait)
+__device__ __forceinline__ void cp_async8(u64 *smem, const u64 *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+
 // a * b mod q for a, b < q (HAC 14.42, base 2, k = s)
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeDev &P) {
     u64 lo = a * b;

@@ -200,19 +200,33 @@ __global__ void __launch_bounds__(256, 2) ks_lazy_perm_kernel(u64 *acc, const u6
         }
     }
     const size_t kstride = (size_t)(L1 + K) * N;
-    for (u32 s = 0; s < S; ++s) {
-        const u32 g = kl.g[s];
-        u32 dst = n;
-        u64 k0[MAXD], k1[MAXD];
-        if (g != 1) {
+    // the key words of step s+1 are copied into shared memory (cp.async) while step s
+    // computes: buffer layout [2][2 polys][MAXD][256 threads], each thread its own slots
+    extern __shared__ u64 ksm[];
+    auto issue = [&](u32 s, u32 buf) {
+        if (kl.g[s] != 1) {
             const u64 *key = kl.keyp[s] + (size_t)pt * N + n;
 #pragma unroll
-            for (u32 j = 0; j < MAXD; ++j) {
-                k0[j] = j < beta ? __ldg(key + (size_t)j * 2 * kstride) : 0;
-                k1[j] = j < beta ? __ldg(key + (size_t)j * 2 * kstride + kstride) : 0;
-            }
-            dst = galois_src(n, kl.ginv[s], logn);
+            for (u32 j = 0; j < MAXD; ++j)
+                if (j < beta) {
+                    cp_async8(ksm + ((buf * 2 + 0) * MAXD + j) * 256 + threadIdx.x, key + (size_t)j * 2 * kstride);
+                    cp_async8(ksm + ((buf * 2 + 1) * MAXD + j) * 256 + threadIdx.x,
+                              key + (size_t)j * 2 * kstride + kstride);
+                }
         }
+        cp_commit();
+    };
+    issue(0, 0);
+    for (u32 s = 0; s < S; ++s) {
+        const u32 g = kl.g[s];
+        if (s + 1 < S)
+            issue(s + 1, (s + 1) & 1);
+        else
+            cp_commit();
+        cp_wait<1>();   // the copies of step s have landed
+        const u64 *k0 = ksm + ((s & 1) * 2 + 0) * MAXD * 256 + threadIdx.x;
+        const u64 *k1 = ksm + ((s & 1) * 2 + 1) * MAXD * 256 + threadIdx.x;
+        const u32 dst = g == 1 ? n : galois_src(n, kl.ginv[s], logn);
 #pragma unroll
         for (int u = 0; u < BT; ++u) {
             if (b0 + u >= B) break;
@@ -226,8 +240,8 @@ __global__ void __launch_bounds__(256, 2) ks_lazy_perm_kernel(u64 *acc, const u6
 #pragma unroll
             for (u32 j = 0; j < MAXD; ++j) {
                 if (j < beta) {
-                    mac128(a0, d[u][j], k0[j]);
-                    mac128(a1, d[u][j], k1[j]);
+                    mac128(a0, d[u][j], k0[j * 256]);
+                    mac128(a1, d[u][j], k1[j * 256]);
                 }
             }
             // keys are in Montgomery form: one Montgomery reduction per sum
@@ -367,6 +381,12 @@ static void set_big_smem(const void *fn) {
 }
 
 void keyswitch_init(Ctx *c) {
+    // the hoisted accumulation double-buffers its key words: 2 x 2 x MAXD x 256 words of shared memory
+    for (const void *f : {(const void *)ks_lazy_perm_kernel<1, 8>, (const void *)ks_lazy_perm_kernel<2, 8>,
+                          (const void *)ks_lazy_perm_kernel<1, 4>, (const void *)ks_lazy_perm_kernel<2, 4>,
+                          (const void *)ks_lazy_perm_kernel<4, 4>, (const void *)ks_lazy_perm_kernel<1, 2>,
+                          (const void *)ks_lazy_perm_kernel<2, 2>, (const void *)ks_lazy_perm_kernel<4, 2>})
+        CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
     set_big_smem((const void *)modup_ntt_kernel<0>);
     set_big_smem((const void *)modup_ntt_kernel<1>);
     set_big_smem((const void *)moddown_kernel<0>);
@@ -551,9 +571,9 @@ void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u3
     if (perm) {
         const u32 nt = (N + 255) / 256, nb = (B + bt - 1) / bt;
         dim3 grid(order ? nb : nt, order ? nt : nb, E);
-#define LAZY_LAUNCH(BTV, MD)                                                                                     \
-    ks_lazy_perm_kernel<BTV, MD><<<grid, 256, 0, c->stream>>>(acc, D, x, kl, S, B, beta, lp, c->K, c->L1, c->logn, \
-                                                              order, pmod_table(c), c->pdev)
+#define LAZY_LAUNCH(BTV, MD)                                                                                   \
+    ks_lazy_perm_kernel<BTV, MD><<<grid, 256, (size_t)2 * 2 * MD * 256 * 8, c->stream>>>(                     \
+        acc, D, x, kl, S, B, beta, lp, c->K, c->L1, c->logn, order, pmod_table(c), c->pdev)
         if (maxd == 8) {
             if (bt == 1) LAZY_LAUNCH(1, 8); else LAZY_LAUNCH(2, 8);
         } else if (maxd == 4) {

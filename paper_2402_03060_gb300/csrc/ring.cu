@@ -207,17 +207,6 @@ void sample_uniform(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u3
 // once per pair.  Lanes of a warp cover 4+ consecutive coefficients of 8 or
 // fewer pairs, so every ciphertext load is a full 32-byte sector.  Each thread
 // keeps all O sums as 128-bit accumulators (products < 2^120, folded every 128 terms).
-// asynchronous 8-byte global -> shared copies (one per thread, per pipeline stage)
-__device__ __forceinline__ void cp_async8(u64 *smem, const u64 *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
-}
-
 #define MAC_DEPTH 8
 template <int OMAX>
 __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt,
