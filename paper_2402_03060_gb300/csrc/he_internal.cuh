@@ -110,11 +110,13 @@ struct Acc128 {
     u64 lo, hi;
 };
 __device__ __forceinline__ void mac128(Acc128 &acc, u64 a, u64 b) {
-    u64 plo = a * b;
-    u64 phi = mulhi64(a, b);
-    u64 lo = acc.lo + plo;
-    acc.hi += phi + (lo < plo ? 1 : 0);
-    acc.lo = lo;
+    const u64 plo = a * b;
+    const u64 phi = mulhi64(a, b);
+    // 128-bit add through the carry flag (add.cc / addc) rather than a compare
+    asm("add.cc.u64 %0, %0, %2;\n\t"
+        "addc.u64 %1, %1, %3;"
+        : "+l"(acc.lo), "+l"(acc.hi)
+        : "l"(plo), "l"(phi));
 }
 
 __device__ __forceinline__ u32 brev_bits(u32 x, int bits) { return __brev(x) >> (32 - bits); }
