@@ -289,6 +289,54 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
         }
 }
 
+// The same sums for one or two outputs: one thread per (ciphertext, poly, limb, coefficient),
+// no shared-memory tile (nothing to share between polynomials when O <= 2), loads unrolled
+// four terms deep; a memory-bound kernel that keeps the whole GPU occupied.
+template <int OM>
+__global__ void __launch_bounds__(256) mac_small_kernel(u64 *out, const u64 *__restrict__ x,
+                                                        const u64 *__restrict__ pt, u32 O, u32 T, u32 BK, u32 lp,
+                                                        u32 logn, size_t x_tstride, size_t out_ostride, u32 lpq,
+                                                        u32 pbase, int accumulate, size_t pt_ostride,
+                                                        const PrimeDev *__restrict__ pd) {
+    const u32 N = 1u << logn;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)BK * lp * N) return;
+    const u32 n = (u32)(idx & (N - 1));
+    const size_t r = idx >> logn;
+    const u32 l = (u32)(r % lp), bk = (u32)(r / lp);
+    const PrimeDev P = pd[l < lpq ? l : pbase + (l - lpq)];
+    const size_t xoff = ((size_t)bk * lp + l) * N + n;
+    const size_t poff = (size_t)l * N + n, pstride_t = (size_t)lp * N;
+    Acc128 acc[OM];
+#pragma unroll
+    for (int o = 0; o < OM; ++o) acc[o].lo = acc[o].hi = 0;
+    u32 t = 0;
+    while (t < T) {
+        const u32 tend = T - t > 128 ? t + 128 : T;   // fold every 128 terms (products < 2^120)
+#pragma unroll 4
+        for (; t < tend; ++t) {
+            const u64 xv = __ldg(x + (size_t)t * x_tstride + xoff);
+#pragma unroll
+            for (int o = 0; o < OM; ++o)
+                if (o < (int)O) mac128(acc[o], __ldg(pt + (size_t)o * pt_ostride + (size_t)t * pstride_t + poff), xv);
+        }
+        if (t < T) {
+#pragma unroll
+            for (int o = 0; o < OM; ++o) {
+                acc[o].lo = reduce128(acc[o].lo, acc[o].hi, P);
+                acc[o].hi = 0;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < OM; ++o)
+        if (o < (int)O) {
+            u64 *dst = out + o * out_ostride + xoff;
+            if (accumulate) mac128(acc[o], *dst, 1);
+            *dst = reduce128(acc[o].lo, acc[o].hi, P);
+        }
+}
+
 void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O, u32 T, u32 B,
          u32 lp, u32 lpq, u32 pbase, int accumulate, size_t pt_ostride) {
     if (!pt_ostride) pt_ostride = (size_t)T * lp * c->N;
@@ -296,6 +344,19 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
     // Limb l < lpq uses data prime l, limb l >= lpq special prime pbase + l - lpq.
     if (lpq == ~0u) lpq = lp;
     const u32 BK = 2 * B;
+    if (O <= 2) {
+        const size_t total = (size_t)BK * lp * c->N;
+        prof_begin(c);
+        if (O == 1)
+            mac_small_kernel<1><<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(
+                out, x, pt, O, T, BK, lp, c->logn, x_tstride, out_ostride, lpq, pbase, accumulate, pt_ostride, c->pdev);
+        else
+            mac_small_kernel<2><<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(
+                out, x, pt, O, T, BK, lp, c->logn, x_tstride, out_ostride, lpq, pbase, accumulate, pt_ostride, c->pdev);
+        note_launch(c, "mac", 8.0 * c->N * ((double)O * T * lp + (double)T * B * 2 * lp + (double)O * B * 2 * lp),
+                    (double)O * T * B * 2 * lp * c->N);
+        return;
+    }
     const u32 bk_max = (u32)tune_get(c, TUNE_MAC_BK, 64);   // polynomials per CTA (tuned: 16, 32, 64)
     u32 bkc = 1;
     while (bkc < BK && bkc < bk_max) bkc <<= 1;
