@@ -383,6 +383,7 @@ static void set_big_smem(const void *fn) {
 void keyswitch_init(Ctx *c) {
     // the hoisted accumulation double-buffers its key words: 2 x 2 x MAXD x 256 words of shared memory
     for (const void *f : {(const void *)ks_lazy_perm_kernel<1, 8>, (const void *)ks_lazy_perm_kernel<2, 8>,
+                          (const void *)ks_lazy_perm_kernel<4, 8>,
                           (const void *)ks_lazy_perm_kernel<1, 4>, (const void *)ks_lazy_perm_kernel<2, 4>,
                           (const void *)ks_lazy_perm_kernel<4, 4>, (const void *)ks_lazy_perm_kernel<1, 2>,
                           (const void *)ks_lazy_perm_kernel<2, 2>, (const void *)ks_lazy_perm_kernel<4, 2>})
@@ -575,7 +576,7 @@ void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u3
     ks_lazy_perm_kernel<BTV, MD><<<grid, 256, (size_t)2 * 2 * MD * 256 * 8, c->stream>>>(                     \
         acc, D, x, kl, S, B, beta, lp, c->K, c->L1, c->logn, order, pmod_table(c), c->pdev)
         if (maxd == 8) {
-            if (bt == 1) LAZY_LAUNCH(1, 8); else LAZY_LAUNCH(2, 8);
+            if (bt == 1) LAZY_LAUNCH(1, 8); else if (bt == 2) LAZY_LAUNCH(2, 8); else LAZY_LAUNCH(4, 8);
         } else if (maxd == 4) {
             if (bt == 1) LAZY_LAUNCH(1, 4); else if (bt == 2) LAZY_LAUNCH(2, 4); else LAZY_LAUNCH(4, 4);
         } else {

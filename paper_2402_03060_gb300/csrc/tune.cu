@@ -183,7 +183,7 @@ void measure(Ctx *c, std::ostringstream &rep) {
             kl.key[s] = kl.keyp[s] = keys.p + (size_t)s * c->dnum * 2 * (c->L1 + K) * N;
         }
         auto run = [&] { ks_lazy(c, acc.p, D.p, x.p, kl, S, B, lp); };
-        const std::vector<int> bts = beta > 4 ? std::vector<int>{1, 2} : std::vector<int>{1, 2, 4};
+        const std::vector<int> bts = {1, 2, 4};
         rep << ", ";
         c->tuned[TUNE_LAZY_ORDER] = 0;
         sweep(c, TUNE_LAZY_BT, bts, run, rep);
