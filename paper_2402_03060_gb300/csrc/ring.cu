@@ -241,12 +241,16 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
     for (u32 t0 = 0; t0 < T; t0 += tc) {
         const u32 tcc = T - t0 < tc ? T - t0 : tc;
         __syncthreads();
+        // the tile is copied with cp.async, every word in flight at once, then waited for
+        // (the older ciphertext copies of the pipeline complete with it)
         for (u32 idx = tid; idx < O * tcc * NT; idx += blockDim.x) {
             const u32 j = idx & (NT - 1), r = idx >> ntlog;
             const u32 tt = r % tcc, o = r / tcc;
-            ps[(tt * NT + j) * OMAX + o] =
-                pt[(size_t)o * pt_ostride + (size_t)(t0 + tt) * pstride_t + (size_t)l * N + n0 + j];
+            cp_async8(ps + (tt * NT + j) * OMAX + o,
+                      pt + (size_t)o * pt_ostride + (size_t)(t0 + tt) * pstride_t + (size_t)l * N + n0 + j);
         }
+        cp_commit();
+        cp_wait<0>();
         __syncthreads();
         for (u32 tt = 0; tt < tcc; ++tt) {
             const u32 t = t0 + tt;

@@ -54,20 +54,24 @@ float time_ms(Ctx *c, const std::function<void()> &f) {
     return best;
 }
 
-// times f for every candidate value of knob; keeps the fastest
+// times f for every candidate value of knob; keeps the fastest, but stays with the first
+// candidate (the default shape) unless another one is at least 2 % faster, so that timing
+// noise does not flip the choice from one process to the next
 void sweep(Ctx *c, int knob, const std::vector<int> &cands, const std::function<void()> &f, std::ostringstream &rep) {
     int best = cands[0];
-    float best_ms = 1e30f;
+    float best_ms = 1e30f, first_ms = 0;
     rep << "\"" << knob_name[knob] << "\": {";
     for (size_t i = 0; i < cands.size(); ++i) {
         c->tuned[knob] = cands[i];
         const float ms = time_ms(c, f);
+        if (i == 0) first_ms = ms;
         rep << (i ? ", " : "") << "\"" << cands[i] << "\": " << ms;
         if (ms < best_ms) {
             best_ms = ms;
             best = cands[i];
         }
     }
+    if (best_ms > 0.98f * first_ms) best = cands[0];
     rep << ", \"chosen\": " << best << "}";
     c->tuned[knob] = best;
 }
@@ -183,7 +187,7 @@ void measure(Ctx *c, std::ostringstream &rep) {
             kl.key[s] = kl.keyp[s] = keys.p + (size_t)s * c->dnum * 2 * (c->L1 + K) * N;
         }
         auto run = [&] { ks_lazy(c, acc.p, D.p, x.p, kl, S, B, lp); };
-        const std::vector<int> bts = {1, 2, 4};
+        const std::vector<int> bts = {2, 1, 4};
         rep << ", ";
         c->tuned[TUNE_LAZY_ORDER] = 0;
         sweep(c, TUNE_LAZY_BT, bts, run, rep);
