@@ -184,7 +184,7 @@ void he_model_free(he_model *m);
 /* ---- autotuning --------------------------------------------------------- */
 /* Chooses the launch shapes of the batched path for this context's N, chain,
  * dnum and GPU by timing each candidate with CUDA events on scratch data (about
- * 1 GB at N = 2^14, released afterwards): limb split over 2-CTA clusters for the
+ * 4 GB at N = 2^14, released afterwards): limb split over 2-CTA clusters for the
  * NTT, ModDown and rescale kernels; outputs and polynomials per MAC launch; ciphertexts per
  * thread and grid order of the hoisted key-switch accumulation.  No choice
  * changes a result bit.  cache_path (optional) is a JSON file keyed by device

@@ -90,6 +90,12 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
 }
 
+// bulk prefetch of a contiguous global region into L2 (one instruction, TMA unit);
+// address 16-byte aligned, size a multiple of 16 bytes
+__device__ __forceinline__ void l2_prefetch_bulk(const void *gmem, u32 bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
+}
+
 // a * b mod q for a, b < q (HAC 14.42, base 2, k = s)
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeDev &P) {
     u64 lo = a * b;

@@ -271,6 +271,13 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, cons
     const u32 E = lp + K;
     const PrimeDev P = pd[i];
     const u64 *ab = acc + (((size_t)s * B + b) * 2 + k) * E * N;
+    const bool add = addend && ((add_mask >> k) & 1);
+    const u64 *adb = add ? addend + (size_t)b * addend_bstride + ((size_t)k * lpo + i) * N : nullptr;
+    if (threadIdx.x == 0) {
+        // the rows the combination reads after the NTT are pulled into L2 meanwhile (bulk prefetch)
+        l2_prefetch_bulk(ab + (size_t)i * N + pt.lo, pt.n * 8);
+        if (add) l2_prefetch_bulk(adb, N * 8);
+    }
     // mdtab: dhinv[KD], dhinv_s[KD], dhmod[KD][L1], Dinv[L1], Dinv_s[L1]
     // base conversion of two coefficients per thread and iteration (16-byte loads)
     const u32 half = pt.n / 2;
@@ -301,9 +308,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, cons
     part_ntt_fwd(sm, pt, logn, tw_all + (size_t)i * 4 * N, P.q);
     const u64 pinv = mdtab[2 * KD + (size_t)KD * L1 + i];
     const u64 pinvs = mdtab[2 * KD + (size_t)KD * L1 + L1 + i];
-    const bool add = addend && ((add_mask >> k) & 1);
     const u32 g = kl.g[s];
-    const u64 *adb = add ? addend + (size_t)b * addend_bstride + ((size_t)k * lpo + i) * N : nullptr;
     u64 *ob = out + ((((size_t)s * B + b) * 2 + k) * lpo + i) * N;
     for (u32 k2 = threadIdx.x; k2 < half; k2 += blockDim.x) {
         const u32 n = pt.lo + 2 * k2;

@@ -11,7 +11,7 @@
 //     registers vs. registers per thread) and grid order (coefficient tiles
 //     fastest vs. ciphertext groups fastest, i.e. key-slice reuse in L2).
 // Each knob is timed with CUDA events on scratch data shaped like the context's
-// top level (16 ciphertexts), the fastest kept; results are cached in a JSON
+// top level (16 to 64 ciphertexts), the fastest kept; results are cached in a JSON
 // file keyed by device name and parameters so a later process skips the sweep.
 #include <stdio.h>
 #include <string.h>
@@ -172,8 +172,8 @@ void measure(Ctx *c, std::ostringstream &rep) {
         rep << ", ";
         sweep(c, TUNE_MAC_BK, {64, 32, 16}, run, rep);
     }
-    if (beta <= 8) {   // hoisted key-switch accumulation: 8 steps of 16 ciphertexts
-        const u32 S = 8;
+    if (beta <= 8) {   // hoisted key-switch accumulation: 16 steps of 64 ciphertexts (a convolution's shape)
+        const u32 S = 16, B = 64;
         DBuf D(c, (size_t)B * beta * E * N), x(c, (size_t)B * 2 * lp * N), acc(c, (size_t)S * B * 2 * E * N);
         DBuf keys(c, (size_t)S * c->dnum * 2 * (c->L1 + K) * N);
         CUDA_TRY(cudaMemsetAsync(D.p, 0, D.words * 8, c->stream));
