@@ -316,23 +316,22 @@ __device__ __forceinline__ void inv_pass(u64 *a, int logn, int lgtl, const u64 *
 __device__ __forceinline__ void inv_local(u64 *a, int logn, int nst, const u64 *__restrict__ tw, u64 q, int logl,
                                           u32 goff, bool scale, u64 ninv, u64 ninvs) {
     if (logn >= 10) {
-        int lgt = 0;
+        // the short pass (nst mod 4 stages) first, on the smallest distances, then passes of
+        // four; the last one also applies N^{-1} when asked
+        const int rem = nst % 4;
+        if (rem == 3) inv_pass<3>(a, logn, 0, tw, q, logl, goff);
+        if (rem == 2) inv_pass<2>(a, logn, 0, tw, q, logl, goff);
+        if (rem == 1) inv_pass<1>(a, logn, 0, tw, q, logl, goff);
+        if (rem) __syncthreads();
+        int lgt = rem;
         for (; lgt + 4 < nst; lgt += 4) {
             inv_pass<4>(a, logn, lgt, tw, q, logl, goff);
             __syncthreads();
         }
-        const int rem = nst - lgt;
-        if (scale) {
-            if (rem == 4) inv_pass<4, true>(a, logn, lgt, tw, q, logl, goff, ninv, ninvs);
-            if (rem == 3) inv_pass<3, true>(a, logn, lgt, tw, q, logl, goff, ninv, ninvs);
-            if (rem == 2) inv_pass<2, true>(a, logn, lgt, tw, q, logl, goff, ninv, ninvs);
-            if (rem == 1) inv_pass<1, true>(a, logn, lgt, tw, q, logl, goff, ninv, ninvs);
-        } else {
-            if (rem == 4) inv_pass<4>(a, logn, lgt, tw, q, logl, goff);
-            if (rem == 3) inv_pass<3>(a, logn, lgt, tw, q, logl, goff);
-            if (rem == 2) inv_pass<2>(a, logn, lgt, tw, q, logl, goff);
-            if (rem == 1) inv_pass<1>(a, logn, lgt, tw, q, logl, goff);
-        }
+        if (scale)
+            inv_pass<4, true>(a, logn, lgt, tw, q, logl, goff, ninv, ninvs);
+        else
+            inv_pass<4>(a, logn, lgt, tw, q, logl, goff);
         __syncthreads();
         return;
     }

@@ -3,6 +3,8 @@
 // as the measured integer roofline of the ALU-bound kernels.  Each thread runs
 // independent chains on register values; nothing touches memory except one store
 // per thread at the end (so the work cannot be optimised away).
+#include <algorithm>
+
 #include "ntt_block.cuh"
 #include "ops.cuh"
 
@@ -29,16 +31,19 @@ __global__ void ub_butterfly(u64 *sink, u64 q, u64 w, u64 ws, u32 iters) {
 }
 
 __global__ void ub_mac128(u64 *sink, u64 x, u32 iters) {
+    const u64 M61 = (1ull << 61) - 1;   // operands below 2^61 like the residues
     Acc128 acc[8];
     u64 v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         acc[k].lo = acc[k].hi = 0;
-        v[k] = x * (threadIdx.x + k + 1);
+        v[k] = (x * (threadIdx.x + 7 * k + 1)) & M61;
     }
+    const u64 w = (x ^ 0x5bd1e995ull) & M61;
     for (u32 i = 0; i < iters; ++i) {
+        const u64 y = (w + i) & M61;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) mac128(acc[k], v[k], x + i);
+        for (int k = 0; k < 8; ++k) mac128(acc[k], v[k], y);
     }
     u64 s = 0;
 #pragma unroll
@@ -73,30 +78,31 @@ extern "C" he_status he_ubench(he_ctx *h, double *out) {
         CUDA_TRY(cudaEventCreate(&e1));
         float ms;
         const double nthr = (double)blocks * threads;
-        // warm-up + timed run of each
-        for (int rep = 0; rep < 2; ++rep) {
+        // a warm-up run, then the best of three timed runs of each
+        out[0] = out[1] = out[2] = 0;
+        for (int rep = 0; rep < 4; ++rep) {
             CUDA_TRY(cudaEventRecord(e0, c->stream));
             ub_butterfly<<<blocks, threads, 0, c->stream>>>(sink.p, P.q, w, ws, iters);
             CUDA_TRY(cudaEventRecord(e1, c->stream));
             CUDA_TRY(cudaEventSynchronize(e1));
             CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            out[0] = nthr * iters * 4 / (ms * 1e-3);
+            if (rep) out[0] = std::max(out[0], nthr * iters * 4 / (ms * 1e-3));
             CUDA_TRY(cudaEventRecord(e0, c->stream));
             ub_mac128<<<blocks, threads, 0, c->stream>>>(sink.p, P.q - 1, iters);
             CUDA_TRY(cudaEventRecord(e1, c->stream));
             CUDA_TRY(cudaEventSynchronize(e1));
             CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            out[1] = nthr * iters * 8 / (ms * 1e-3);
+            if (rep) out[1] = std::max(out[1], nthr * iters * 8 / (ms * 1e-3));
             CUDA_TRY(cudaEventRecord(e0, c->stream));
             ub_barrett<<<blocks, threads, 0, c->stream>>>(sink.p, P, iters);
             CUDA_TRY(cudaEventRecord(e1, c->stream));
             CUDA_TRY(cudaEventSynchronize(e1));
             CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            out[2] = nthr * iters * 4 / (ms * 1e-3);
+            if (rep) out[2] = std::max(out[2], nthr * iters * 4 / (ms * 1e-3));
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        c->launches += 6;
+        c->launches += 12;
         return HE_OK;
     } catch (const HeError &e) {
         return e.code;
