@@ -182,17 +182,19 @@ __device__ __forceinline__ void fwd_local(u64 *a, int logn, int st0, const u64 *
                                           u32 goff) {
     const u32 L = 1u << logl;
     if (logn >= 10) {
-        // passes of 4 stages; the last pass (4, 3, 2 or 1 stages) also reduces to [0, q)
-        int st = st0;
+        // the short pass ((logn - st0) mod 4 stages) first, on the largest distances, then
+        // passes of four; the last one also reduces to [0, q)
+        const int rem = (logn - st0) % 4;
+        if (rem == 3) fwd_pass<3>(a, logn, st0, tw, q, logl, goff);
+        if (rem == 2) fwd_pass<2>(a, logn, st0, tw, q, logl, goff);
+        if (rem == 1) fwd_pass<1>(a, logn, st0, tw, q, logl, goff);
+        if (rem) __syncthreads();
+        int st = st0 + rem;
         for (; st + 4 < logn; st += 4) {
             fwd_pass<4>(a, logn, st, tw, q, logl, goff);
             __syncthreads();
         }
-        const int rem = logn - st;
-        if (rem == 4) fwd_pass<4, true>(a, logn, st, tw, q, logl, goff);
-        if (rem == 3) fwd_pass<3, true>(a, logn, st, tw, q, logl, goff);
-        if (rem == 2) fwd_pass<2, true>(a, logn, st, tw, q, logl, goff);
-        if (rem == 1) fwd_pass<1, true>(a, logn, st, tw, q, logl, goff);
+        fwd_pass<4, true>(a, logn, st, tw, q, logl, goff);
         __syncthreads();
         return;
     }
