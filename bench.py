@@ -50,7 +50,7 @@ TUNE_CACHE = os.path.join(ROOT, "paper_2402_03060_gb300", "_build", "tune_cache.
 # kernel source (the hashed function) and launch shape it was taken with, else reported as null
 NCU_TRAFFIC = {
     "ks_lazy": {"bytes_per_launch": 2302e6, "source": "paper_2402_03060_gb300/csrc/keyswitch.cu",
-                "function": "template <int BT, int MAXD>\n__global__ void __launch_bounds__(256, 2) ks_lazy_perm_kernel(",
+                "function": "template <int BT, int MAXD>\n__global__ void __launch_bounds__(256, (BT == 4 && MAXD == 8) ? 2 : 3) ks_lazy_perm_kernel(",
                 "sha256": "ac80882705a9889e1552e6f56ca28541b92f6da26fcc478efe5caa64f5ec6af4",
                 "tuning": {"lazy_bt": 4, "lazy_order": 0}},
     "mac": {"bytes_per_launch": 4909e6, "source": "paper_2402_03060_gb300/csrc/ring.cu",

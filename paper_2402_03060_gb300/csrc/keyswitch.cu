@@ -169,8 +169,10 @@ __global__ void ks_lazy_kernel(u64 *acc, const u64 *__restrict__ D, const u64 *_
 // writes of one limb merge in L2) or ciphertext group fastest (order 1: consecutive CTAs
 // read the same key slice).  Each thread handles BT ciphertexts of one coefficient so that
 // every key word it loads serves BT products; MAXD >= the number of digits.
+// Three CTAs per SM (24 warps: the 64-bit multiply chains need the latency hiding) except
+// for four ciphertexts of eight digits per thread, which needs the registers of two.
 template <int BT, int MAXD>
-__global__ void __launch_bounds__(256, 2) ks_lazy_perm_kernel(u64 *acc, const u64 *__restrict__ D,
+__global__ void __launch_bounds__(256, (BT == 4 && MAXD == 8) ? 2 : 3) ks_lazy_perm_kernel(u64 *__restrict__ acc, const u64 *__restrict__ D,
                                                             const u64 *__restrict__ x, KeyList kl, u32 S, u32 B,
                                                             u32 beta, u32 lp, u32 K, u32 L1, int logn, int order,
                                                             const u64 *__restrict__ pq,
