@@ -195,7 +195,7 @@ void he_model_free(he_model *m);
 he_status he_autotune(he_ctx *ctx, const char *cache_path, char *report, size_t report_len);
 /* The tuned knobs in the order: NTT split, ModDown split, rescale split, MAC
  * output group, key-switch ciphertexts per thread, key-switch grid order,
- * polynomials per MAC CTA (-1 = default).  he_tuning_set overrides them (values outside a knob's
+ * polynomials per MAC CTA, threads per coefficient of a MAC group (-1 = default).  he_tuning_set overrides them (values outside a knob's
  * candidates fall back to the nearest valid launch shape). */
 he_status he_tuning_get(he_ctx *ctx, int32_t *values, size_t n);
 he_status he_tuning_set(he_ctx *ctx, const int32_t *values, size_t n);

@@ -259,7 +259,8 @@ class Context:
         return tuple(out)
 
     # ---- client side
-    TUNE_KNOBS = ("ntt_split", "moddown_split", "rescale_split", "mac_group", "lazy_bt", "lazy_order", "mac_bk")
+    TUNE_KNOBS = ("ntt_split", "moddown_split", "rescale_split", "mac_group", "lazy_bt", "lazy_order", "mac_bk",
+                  "mac_split")
 
     def autotune(self, cache_path: str | None = None) -> dict:
         """he_autotune: time the launch-shape candidates (or read them from cache_path)."""

@@ -208,19 +208,24 @@ void sample_uniform(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u3
 // fewer pairs, so every ciphertext load is a full 32-byte sector.  Each thread
 // keeps all O sums as 128-bit accumulators (products < 2^120, folded every 128 terms).
 #define MAC_DEPTH 8
-template <int OMAX>
-__global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt,
+// OSPLIT threads share one (ciphertext, poly, coefficient): each keeps OMAX of the launch's
+// OMAX * OSPLIT outputs (fewer registers, more resident warps; the second thread's
+// ciphertext loads hit L1)
+template <int OMAX, int OSPLIT>
+__global__ void __launch_bounds__(256, OSPLIT == 1 ? 2 : 3) mac_kernel(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt,
                                                   u32 O, u32 T, u32 BK, u32 lp, u32 logn, size_t x_tstride,
                                                   size_t out_ostride, u32 ntlog, u32 tc, u32 lpq, u32 pbase,
                                                   int accumulate, size_t pt_ostride,
                                                   const PrimeDev *__restrict__ pd) {
     extern __shared__ u64 smem[];
     u64 *xs = smem;                          // [256][MAC_DEPTH]: each thread's own pipeline slots
-    u64 *ps = smem + 256 * MAC_DEPTH;        // [tc][NT][OMAX]: the plaintext tile
+    u64 *ps = smem + 256 * MAC_DEPTH;        // [tc][NT][OW]: the plaintext tile
+    constexpr u32 OW = OMAX * OSPLIT;
     const u32 N = 1u << logn, NT = 1u << ntlog;
     const u32 tid = threadIdx.x;
-    const u32 nl = tid & (NT - 1);
-    const u32 bk = blockIdx.x * (256u >> ntlog) + (tid >> ntlog);
+    const u32 osub = tid % OSPLIT, rt = tid / OSPLIT;
+    const u32 nl = rt & (NT - 1);
+    const u32 bk = blockIdx.x * ((256u / OSPLIT) >> ntlog) + (rt >> ntlog);
     const u32 n0 = blockIdx.y * NT;
     const u32 l = blockIdx.z;
     const bool active = bk < BK;
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
         for (u32 idx = tid; idx < O * tcc * NT; idx += blockDim.x) {
             const u32 j = idx & (NT - 1), r = idx >> ntlog;
             const u32 tt = r % tcc, o = r / tcc;
-            cp_async8(ps + (tt * NT + j) * OMAX + o,
+            cp_async8(ps + (tt * NT + j) * OW + o,
                       pt + (size_t)o * pt_ostride + (size_t)(t0 + tt) * pstride_t + (size_t)l * N + n0 + j);
         }
         cp_commit();
@@ -258,7 +263,8 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
             const u64 xv = myx[t % MAC_DEPTH];
             if (active) {
                 // this thread's OMAX plaintext words of term t, 16-byte loads at fixed offsets
-                const ulonglong2 *pv = reinterpret_cast<const ulonglong2 *>(ps + (tt * NT + nl) * OMAX);
+                const u64 *pw0 = ps + (tt * NT + nl) * OW + osub * OMAX;
+                const ulonglong2 *pv = reinterpret_cast<const ulonglong2 *>(pw0);
                 u64 pw[OMAX];
 #pragma unroll
                 for (int o = 0; o < OMAX / 2; ++o) {
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
                     pw[2 * o] = v.x;
                     pw[2 * o + 1] = v.y;
                 }
-                if (OMAX & 1) pw[OMAX - 1] = ps[(tt * NT + nl) * OMAX + OMAX - 1];
+                if (OMAX & 1) pw[OMAX - 1] = pw0[OMAX - 1];
 #pragma unroll
                 for (int o = 0; o < OMAX; ++o) mac128(acc[o], pw[o], xv);
             }
@@ -286,8 +292,8 @@ __global__ void __launch_bounds__(256, 2) mac_kernel(u64 *out, const u64 *__rest
     if (!active) return;
 #pragma unroll
     for (int o = 0; o < OMAX; ++o)
-        if (o < (int)O) {
-            u64 *dst = out + o * out_ostride + xoff;
+        if (osub * OMAX + o < O) {
+            u64 *dst = out + (osub * OMAX + o) * out_ostride + xoff;
             if (accumulate) mac128(acc[o], *dst, 1);
             *dst = reduce128(acc[o].lo, acc[o].hi, P);
         }
@@ -362,19 +368,22 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
         return;
     }
     const u32 bk_max = (u32)tune_get(c, TUNE_MAC_BK, 64);   // polynomials per CTA (tuned: 16, 32, 64)
-    u32 bkc = 1;
-    while (bkc < BK && bkc < bk_max) bkc <<= 1;
-    u32 ntlog = 0;
-    while ((1u << ntlog) * bkc < 256) ++ntlog;
-    if ((1u << ntlog) > c->N) throw HeError(HE_EINVAL, "mac: ring too small");
-    const u32 NT = 1u << ntlog;
     // outputs in groups of at most G (the accumulators of a group live in registers;
-    // every group re-reads the inputs x); G is tuned, 12 by default
+    // every group re-reads the inputs x); G is tuned, 12 by default.  With the split
+    // knob a group of more than 6 outputs is shared by two threads per coefficient.
     const u32 G = (u32)tune_get(c, TUNE_MAC_GROUP, 12);
+    const u32 split = (u32)tune_get(c, TUNE_MAC_SPLIT, 1);
     for (u32 o0 = 0; o0 < O; o0 += G) {
         const u32 oc = O - o0 < G ? O - o0 : G;
+        const u32 os = split == 2 && oc > 6 && oc <= 12 ? 2 : 1;
+        u32 bkc = 1;
+        while (bkc < BK && bkc < bk_max / os) bkc <<= 1;
+        u32 ntlog = 0;
+        while ((1u << ntlog) * bkc * os < 256) ++ntlog;
+        if ((1u << ntlog) > c->N) throw HeError(HE_EINVAL, "mac: ring too small");
+        const u32 NT = 1u << ntlog;
         // shared memory: pipeline slots + plaintext tile within the 48 KB default
-        const u32 ow = oc <= 1 ? 1 : oc <= 2 ? 2 : oc <= 4 ? 4 : oc <= 6 ? 6 : oc <= 8 ? 8 : 12;   // template width
+        const u32 ow = os == 2 ? 12 : oc <= 1 ? 1 : oc <= 2 ? 2 : oc <= 4 ? 4 : oc <= 6 ? 6 : oc <= 8 ? 8 : 12;
         u32 tc = (6144 - 256 * MAC_DEPTH) / (ow * NT);
         if (tc < 1) tc = 1;
         if (tc > T) tc = T;
@@ -383,21 +392,23 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
         const u64 *ptc = pt + (size_t)o0 * pt_ostride;
         u64 *outc = out + (size_t)o0 * out_ostride;
         prof_begin(c);
-#define MAC_LAUNCH(OM)                                                                                        \
-    mac_kernel<OM><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride, out_ostride, \
-                                                   ntlog, tc, lpq, pbase, accumulate, pt_ostride, c->pdev)
-        if (oc <= 1)
-            MAC_LAUNCH(1);
+#define MAC_LAUNCH(OM, OS)                                                                                        \
+    mac_kernel<OM, OS><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride, out_ostride, \
+                                                       ntlog, tc, lpq, pbase, accumulate, pt_ostride, c->pdev)
+        if (os == 2)
+            MAC_LAUNCH(6, 2);
+        else if (oc <= 1)
+            MAC_LAUNCH(1, 1);
         else if (oc <= 2)
-            MAC_LAUNCH(2);
+            MAC_LAUNCH(2, 1);
         else if (oc <= 4)
-            MAC_LAUNCH(4);
+            MAC_LAUNCH(4, 1);
         else if (oc <= 6)
-            MAC_LAUNCH(6);
+            MAC_LAUNCH(6, 1);
         else if (oc <= 8)
-            MAC_LAUNCH(8);
+            MAC_LAUNCH(8, 1);
         else
-            MAC_LAUNCH(12);
+            MAC_LAUNCH(12, 1);
 #undef MAC_LAUNCH
         note_launch(c, "mac", 8.0 * c->N * ((double)oc * T * lp + (double)T * B * 2 * lp + (double)oc * B * 2 * lp),
                     (double)oc * T * B * 2 * lp * c->N);

@@ -32,7 +32,7 @@ int tune_split(const Ctx *c, int knob) {
 namespace {
 
 const char *knob_name[TUNE_COUNT] = {"ntt_split", "moddown_split", "rescale_split", "mac_group", "lazy_bt",
-                                     "lazy_order", "mac_bk"};
+                                     "lazy_order", "mac_bk", "mac_split"};
 
 float time_ms(Ctx *c, const std::function<void()> &f) {
     f();   // warm-up
@@ -168,7 +168,10 @@ void measure(Ctx *c, std::ostringstream &rep) {
             mac(c, out.p, (size_t)Bm * 2 * E * N, x.p, (size_t)Bm * 2 * E * N, pt.p, O, T, Bm, E, lp, c->L1, 0, 0);
         };
         c->tuned[TUNE_MAC_BK] = 64;
+        c->tuned[TUNE_MAC_SPLIT] = 1;
         sweep(c, TUNE_MAC_GROUP, {12, 8, 6, 4}, run, rep);
+        rep << ", ";
+        sweep(c, TUNE_MAC_SPLIT, {1, 2}, run, rep);
         rep << ", ";
         sweep(c, TUNE_MAC_BK, {64, 32, 16}, run, rep);
     }

@@ -23,9 +23,9 @@ def G():
 
 
 SETTINGS = [
-    dict(ntt_split=1, moddown_split=1, rescale_split=1, mac_group=4, lazy_bt=1, lazy_order=1, mac_bk=16),
-    dict(ntt_split=0, moddown_split=1, rescale_split=0, mac_group=6, lazy_bt=4, lazy_order=0, mac_bk=32),
-    dict(ntt_split=1, moddown_split=0, rescale_split=1, mac_group=8, lazy_bt=2, lazy_order=1, mac_bk=64),
+    dict(ntt_split=1, moddown_split=1, rescale_split=1, mac_group=4, lazy_bt=1, lazy_order=1, mac_bk=16, mac_split=1),
+    dict(ntt_split=0, moddown_split=1, rescale_split=0, mac_group=6, lazy_bt=4, lazy_order=0, mac_bk=32, mac_split=2),
+    dict(ntt_split=1, moddown_split=0, rescale_split=1, mac_group=12, lazy_bt=2, lazy_order=1, mac_bk=64, mac_split=2),
 ]
 
 
