@@ -51,12 +51,8 @@ TUNE_CACHE = os.path.join(ROOT, "paper_2402_03060_gb300", "_build", "tune_cache.
 NCU_TRAFFIC = {
     "ks_lazy": {"bytes_per_launch": 2302e6, "source": "paper_2402_03060_gb300/csrc/keyswitch.cu",
                 "function": "template <int BT, int MAXD>\n__global__ void __launch_bounds__(256, (BT == 4 && MAXD == 8) ? 2 : 3) ks_lazy_perm_kernel(",
-                "sha256": "ac80882705a9889e1552e6f56ca28541b92f6da26fcc478efe5caa64f5ec6af4",
+                "sha256": "24666afba43388aa5d3c13fc761e1ac129362410d2f08f4db211f27ce329f4bd",
                 "tuning": {"lazy_bt": 4, "lazy_order": 0}},
-    "mac": {"bytes_per_launch": 4909e6, "source": "paper_2402_03060_gb300/csrc/ring.cu",
-            "function": "template <int OMAX>\n__global__ void __launch_bounds__(256, 2) mac_kernel(",
-            "sha256": "ddabf7ca8e89c99613d27a846e0fe88c6a37d6814754f35e898a2b1246633552",
-            "tuning": {"mac_group": 12, "mac_bk": 64}},
 }
 
 

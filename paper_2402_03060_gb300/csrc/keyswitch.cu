@@ -40,7 +40,10 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) modup_ntt_kernel(u64 *D, cons
     const u64 *tj = tab + (size_t)j * (2 * alpha + alpha * E);
     const u64 *xb = xc + ((size_t)b * lp + lo) * N;
     if (nd == 1) {
-        // single-limb digit: reduce each coefficient mod q_t; 16-byte loads, four in flight per thread
+        // single-limb digit: reduce each coefficient (< q_j) mod q_t -- nothing to do when
+        // q_j < q_t, one conditional subtraction when q_j < 2 q_t; 16-byte loads, four in flight
+        const u64 qj = pd[lo].q;
+        const int mode = qj <= P.q ? 0 : qj < 2 * P.q ? 1 : 2;
         const ulonglong2 *x2 = reinterpret_cast<const ulonglong2 *>(xb + pt.lo);
         const u32 half = pt.n / 2;
         for (u32 k0 = threadIdx.x; k0 < half; k0 += 4 * blockDim.x) {
@@ -54,8 +57,16 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) modup_ntt_kernel(u64 *D, cons
             for (int u = 0; u < 4; ++u) {
                 const u32 k = k0 + u * blockDim.x;
                 if (k < half) {
-                    sm[spad(2 * k)] = reduce64(v[u].x, P);
-                    sm[spad(2 * k + 1)] = reduce64(v[u].y, P);
+                    u64 a = v[u].x, b = v[u].y;
+                    if (mode == 1) {
+                        a = a >= P.q ? a - P.q : a;
+                        b = b >= P.q ? b - P.q : b;
+                    } else if (mode == 2) {
+                        a = reduce64(a, P);
+                        b = reduce64(b, P);
+                    }
+                    sm[spad(2 * k)] = a;
+                    sm[spad(2 * k + 1)] = b;
                 }
             }
         }

@@ -49,16 +49,6 @@ static const u64 *get_pts(Ctx *c, PtCache *pc, const std::string &key, std::vect
     return p;
 }
 
-static Cts stack_sum(Ctx *c, const Cts &base, u32 T, u32 Bt) {
-    // sum of T consecutive batches of Bt ciphertexts inside base
-    const size_t w = (size_t)Bt * cts_ct_words(c, base.lp);
-    Cts acc = cts_alloc(c, Bt, base.lp, base.scale, base.lay);
-    CUDA_TRY(cudaMemcpyAsync(acc.data(), base.data(), w * 8, cudaMemcpyDeviceToDevice, c->stream));
-    for (u32 t = 1; t < T; ++t)
-        ew_binop(c, OP_ADD, acc.data(), acc.data(), base.data() + t * w, Bt * 2 * base.lp, base.lp, base.lp, 0);
-    return acc;
-}
-
 // ------------------------------------------------------------------ layers
 // Algorithm 1 (Sec. IV-B).  w: [co][ci][kh][kw].  Rotations Rot(C_in(i), I*(k + W_img*j));
 // per output channel: sum of Mul(rot, K(o,i,j,k)) with K the weight (times the
@@ -598,8 +588,8 @@ Cts model_infer(he_model *m, const Cts &x, bool use_graph) {
 // ------------------------------------------------------------------ C ABI
 static thread_local std::string g_err;
 
-// lets entry points in other translation units report through he_last_error()
-const char *noalloc_set_error(const char *msg) {
+// the message he_last_error() returns on this thread (entry points of every translation unit)
+const char *set_last_error(const char *msg) {
     g_err = msg;
     return g_err.c_str();
 }

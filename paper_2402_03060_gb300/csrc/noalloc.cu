@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) noalloc_rescale(u64 *out, con
         ob[n] = mul_shoup(sub_mod(ib[n], sm[spad(n)], P.q), rc.w[i], rc.ws[i], P.q);
 }
 
-extern const char *noalloc_set_error(const char *msg);
+extern const char *set_last_error(const char *msg);
 
 extern "C" he_status he_rescale_noalloc(he_ctx *h, const uint64_t *in, uint64_t *out, uint32_t batch,
                                         uint32_t limbs) {
@@ -149,10 +149,10 @@ extern "C" he_status he_rescale_noalloc(he_ctx *h, const uint64_t *in, uint64_t 
         c->launches += 3;
         return HE_OK;
     } catch (const HeError &e) {
-        noalloc_set_error(e.what());
+        set_last_error(e.what());
         return e.code;
     } catch (const std::exception &e) {
-        noalloc_set_error(e.what());
+        set_last_error(e.what());
         return HE_EINVAL;
     }
 }

@@ -264,7 +264,7 @@ static size_t model_bytes(const he_model *m) {
 }
 
 // ------------------------------------------------------------------ C ABI
-const char *noalloc_set_error(const char *msg);
+const char *set_last_error(const char *msg);
 
 template <class F>
 static he_status srv_guard(F &&f) {
@@ -272,10 +272,10 @@ static he_status srv_guard(F &&f) {
         f();
         return HE_OK;
     } catch (const HeError &e) {
-        noalloc_set_error(e.what());
+        set_last_error(e.what());
         return e.code;
     } catch (const std::exception &e) {
-        noalloc_set_error(e.what());
+        set_last_error(e.what());
         return HE_EINVAL;
     }
 }

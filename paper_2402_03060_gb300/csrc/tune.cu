@@ -204,7 +204,7 @@ void measure(Ctx *c, std::ostringstream &rep) {
 
 }  // namespace
 
-const char *noalloc_set_error(const char *msg);
+const char *set_last_error(const char *msg);
 
 extern "C" he_status he_autotune(he_ctx *h, const char *cache_path, char *report, size_t report_len) {
     try {
@@ -244,10 +244,10 @@ extern "C" he_status he_autotune(he_ctx *h, const char *cache_path, char *report
         }
         return HE_OK;
     } catch (const HeError &e) {
-        noalloc_set_error(e.what());
+        set_last_error(e.what());
         return e.code;
     } catch (const std::exception &e) {
-        noalloc_set_error(e.what());
+        set_last_error(e.what());
         return HE_EINVAL;
     }
 }
