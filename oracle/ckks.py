@@ -415,6 +415,12 @@ class Ckks:
         q = self.q[: a.lp]
         return Ct(np.stack([self.add(a.d[0], b.d[0], q), self.add(a.d[1], b.d[1], q)]), a.scale)
 
+    def drop_level(self, a: Ct) -> Ct:
+        """Drop-Level (Sec. III-B, reading C11) as a modulus drop: the top limb of each
+        polynomial is discarded; message and scale are unchanged."""
+        assert a.lp >= 2, "level exhausted"
+        return Ct(np.ascontiguousarray(a.d[:, : a.lp - 1]), a.scale)
+
     def ct_add_plain(self, a: Ct, pt: np.ndarray) -> Ct:
         q = self.q[: a.lp]
         return Ct(np.stack([self.add(a.d[0], pt, q), a.d[1].copy()]), a.scale)

@@ -56,6 +56,8 @@ def forward(x, layers, dims=2):
             x = conv(x, spec["w"], spec["b"], spec["stride"])
         elif op == "square":
             x = x * x
+        elif op == "approx_relu":   # Sec. IV-F: 0.375373 + 0.5 x + 0.117071 x^2
+            x = 0.375373 + 0.5 * x + 0.117071 * x * x
         elif op == "avgpool":
             x = avgpool(x, spec["k"], dims)
         elif op == "flatten":

@@ -152,6 +152,39 @@ def square(be, xs, lay: Layout):
     return [be.square(x) for x in xs], replace(lay, pending=lay.pending * lay.pending)
 
 
+# the degree-2 approximation of ReLU the paper uses (Sec. IV-F, Exp. 3 / M3): c0 + c1 x + c2 x^2
+RELU_C0, RELU_C1, RELU_C2 = 0.375373, 0.5, 0.117071
+
+
+def valid_positions(lay: Layout):
+    """Slots of one sample that hold values: I*(r*W_img + c) for a feature map,
+    [0, D) after flatten / FC."""
+    if lay.flat:
+        return np.arange(lay.D)
+    H = lay.H if lay.dims == 2 else 1
+    return np.array([lay.I * (r * lay.W_img + c) for r in range(H) for c in range(lay.W)])
+
+
+def approx_relu(be, xs, lay: Layout):
+    """Approximate ReLU f(x) = c0 + c1 x + c2 x^2 (Sec. IV-F), 2 levels.  A pending
+    pooling factor p is folded in as f(p x) = c0 + (c1 p) x + (c2 p^2) x^2 (Sec. IV-C).
+    Reading: a = Rescale(Mul(x^2, c2 p^2)); b = Rescale(Mul(x, c1 p)) with the
+    plaintext encoded at the scale that lands b on a's scale, then its top limb
+    dropped (Drop-Level as a modulus drop) to reach a's level; f = a + b + c0.  All
+    three constants sit at the valid slots only, so every other slot ends at zero."""
+    p = lay.pending
+    pos = valid_positions(lay)
+    m2 = slot_vector(lay, pos, RELU_C2 * p * p)
+    m1 = slot_vector(lay, pos, RELU_C1 * p)
+    m0 = slot_vector(lay, pos, RELU_C0)
+    outs = []
+    for x in xs:
+        a = be.rescale(be.mul_mask(be.square(x), m2))
+        b = be.mul_rescale_to(x, m1, a)
+        outs.append(be.add_mask(be.add(a, b), m0))
+    return outs, replace(lay, pending=1.0)
+
+
 def flatten(be, xs, lay: Layout):
     """Sec. IV-E: gather every channel's W x H values into one contiguous block.
 
@@ -299,6 +332,8 @@ def run_layers(be, xs, layers, lay: Layout, conv_mode: str = "hoisted"):
             xs, lay = conv(be, xs, spec["w"], spec["b"], spec["stride"], lay, conv_mode)
         elif op == "square":
             xs, lay = square(be, xs, lay)
+        elif op == "approx_relu":
+            xs, lay = approx_relu(be, xs, lay)
         elif op == "avgpool":
             xs, lay = avgpool(be, xs, spec["k"], lay)
         elif op == "flatten":
@@ -339,6 +374,8 @@ def plan(layers, W_img: int, H_img: int, dims: int = 2):
             prev = "conv"
         elif op == "square":
             levels += 1
+        elif op == "approx_relu":
+            levels += 2
         elif op == "avgpool":
             c = spec["k"]
             ckh = c if dims == 2 else 1
@@ -416,6 +453,20 @@ class HeBackend:
         lp = xs[0].lp
         enc = [[[self.he.encode_ext(v, self.he.scale, lp) for v in wi] for wi in wo] for wo in weights]
         return self.he.lincomb(xs, steps, enc, self.he.scale, rescale=True)
+
+    def mul_rescale_to(self, x, v, target):
+        """x (.) v rescaled onto target's scale and level: the plaintext is encoded at
+        target.scale * q_top / x.scale, the product rescaled and its top limbs
+        dropped down to target's level; the scale is then set to target's (equal up
+        to the rounding of that quotient)."""
+        self.count["pmul"] += 1
+        self.count["rescale"] += 1
+        s = target.scale * float(self.he.q[x.lp - 1]) / x.scale
+        y = self.he.rescale(self.he.ct_mul_plain(x, self.he.encode(v, s, x.lp), s))
+        while y.lp > target.lp:
+            y = self.he.drop_level(y)
+        y.scale = target.scale
+        return y
 
     def add(self, x, y):
         return self.he.ct_add(x, y)

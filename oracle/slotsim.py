@@ -65,6 +65,12 @@ class SlotSim:
     def lincomb_rescale(self, xs, steps, weights):
         return [self.rescale(y) for y in self.lincomb(xs, steps, weights)]
 
+    def mul_rescale_to(self, x, v, target):
+        assert not x.pending_rescale and not target.pending_rescale and x.used < target.used
+        self.count["pmul"] += 1
+        self.count["rescale"] += 1
+        return SV(x.v * v, target.used, False)
+
     def add(self, x, y):
         assert x.used == y.used and x.pending_rescale == y.pending_rescale, "level mismatch"
         return SV(x.v + y.v, x.used, x.pending_rescale)

@@ -86,10 +86,13 @@ def test_cnn_against_torch():
     assert np.abs(t.numpy().reshape(-1) - cnn.forward(s[0], m1, dims=1)).max() < 1e-12
 
 
-@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "M1", "M7"])
+@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "m3", "M1", "M7"])
 def test_slot_algorithms_equal_direct_cnn(name):
     if name == "lenet1":
         model, Wi, Hi, dims, slots = W.lenet1(), 28, 28, 2, 8192
+        gen = lambda n: W.images(n)
+    elif name == "m3":
+        model, Wi, Hi, dims, slots = W.m3_relu(), 28, 28, 2, 8192
         gen = lambda n: W.images(n)
     elif name.startswith("cnn1d"):
         model = W.cnn1d(fc_sum="tree" if name.endswith("tree") else "linear")
@@ -117,7 +120,7 @@ def test_slot_algorithms_equal_direct_cnn(name):
     assert np.abs(y1.v[:len(ref)] - y.v[:len(ref)]).max() < 1e-12
 
 
-@pytest.mark.parametrize("name", ["M1", "M2", "M4", "M7"])
+@pytest.mark.parametrize("name", ["M1", "M2", "M3", "M4", "M7"])
 def test_levels_per_layer_match_paper_tables(name):
     g = GOLD["mult_per_layer"][name]
     model = build_model(g["layers"])
@@ -219,3 +222,17 @@ def test_tree_rotation_sum(m):
     assert np.abs(a.v - direct).max() < 1e-9 and np.abs(b.v - direct).max() < 1e-9
     n_rot = (m.bit_length() - 1) + bin(m).count("1") - 1
     assert tree.count["rot"] == n_rot == len(layers.tree_steps(d, m))
+
+
+def test_approx_relu_folds_the_pooling_factor():
+    """f(p x) for a pending factor p: approx_relu after avgpool equals the FP64
+    f applied to the average (Sec. IV-C), and its constant term sits only at the
+    valid slots."""
+    rng = np.random.default_rng(9)
+    model = [{"op": "conv2d", "w": rng.normal(0, 0.3, (2, 1, 3, 3)), "b": rng.normal(0, 0.1, 2), "stride": 1},
+             {"op": "avgpool", "k": 2}, {"op": "approx_relu"}, {"op": "flatten"}]
+    img = W.images(1)
+    y, lay, be, _ = run_sim(model, img, 28, 28, 2, 2048)
+    ref = cnn.forward(img[0], model)
+    assert np.abs(y.v[:len(ref)] - ref).max() < 1e-12
+    assert np.all(y.v[len(ref):lay.stride] == 0)

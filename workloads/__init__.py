@@ -81,6 +81,21 @@ def lenet5_sq(seed: int = WEIGHT_SEED):
     ]
 
 
+def m3_relu(seed: int = WEIGHT_SEED):
+    """The paper's M3 shape (Exp. 3): conv 1->6 K3, approximate ReLU, avgpool 2,
+    flatten, FC 1014->120, approximate ReLU, FC 120->10 (9 levels)."""
+    rng = np.random.default_rng(seed)
+    return [
+        {"op": "conv2d", "w": _normal(rng, (6, 1, 3, 3)), "b": _normal(rng, (6,)), "stride": 1},
+        {"op": "approx_relu"},
+        {"op": "avgpool", "k": 2},
+        {"op": "flatten"},
+        {"op": "fc", "w": _normal(rng, (120, 1014)), "b": _normal(rng, (120,))},
+        {"op": "approx_relu"},
+        {"op": "fc", "w": _normal(rng, (10, 120)), "b": _normal(rng, (10,))},
+    ]
+
+
 def images(n: int, H: int = 28, W: int = 28, seed: int = INPUT_SEED) -> np.ndarray:
     return np.stack([np.random.default_rng(seed + i).uniform(0.0, 1.0, (H, W)) for i in range(n)])
 
@@ -95,6 +110,8 @@ PARAMS = {
     "conv1": dict(logn=13, data_bits=[60, 40, 40], special_bits=[60], dnum=3, log2_scale=40),
     "lenet1": dict(logn=14, data_bits=[60] + [40] * 7, special_bits=[60], dnum=8, log2_scale=40),
     "cnn1d": dict(logn=14, data_bits=[60] + [40] * 6, special_bits=[60], dnum=7, log2_scale=40),
+    # M3 with approximate ReLU: 9 levels
+    "m3": dict(logn=14, data_bits=[60] + [40] * 9, special_bits=[60], dnum=10, log2_scale=40),
     # LeNet-5-shaped net with x^2 activations: 11 levels at N = 2^15
     "lenet5": dict(logn=15, data_bits=[60] + [40] * 11, special_bits=[60], dnum=12, log2_scale=40),
 }
