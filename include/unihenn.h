@@ -129,6 +129,11 @@ he_status he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
 /* Mul (C) of each ciphertext by itself, relinearised and rescaled (square
  * activation, paper Sec. IV-F). */
 he_status he_square(he_ctx *ctx, he_ct *const *in, uint32_t n, he_ct **out);
+/* Approximate ReLU f(x) = 0.375373 + 0.5 x + 0.117071 x^2 (paper Sec. IV-F, model M3) on n
+ * channel ciphertexts; 2 levels.  A pending average-pooling factor p is folded in as
+ * f(p x) (Sec. IV-C).  The constant and the coefficients are applied at the layout's valid
+ * slots only.  out[n] are new handles.  Errors: HE_ELEVEL (fewer than three limbs), HE_EINVAL. */
+he_status he_approx_relu(he_ctx *ctx, he_ct *const *in, uint32_t n, he_ct **out);
 
 /* ---- UniHENN layers (paper Sec. IV) on channel lists -------------------- */
 /* Algorithm 1: in[ch_in] -> out[ch_out]; w [ch_out][ch_in][K][K] (conv2d) or
@@ -150,9 +155,9 @@ he_status he_fc(he_ctx *ctx, const he_ct *in, const double *W, const double *b, 
                 uint32_t dout, he_ct **out);
 
 /* ---- compiled models, batched inference ------------------------------- */
-enum { HE_CONV2D = 1, HE_CONV1D = 2, HE_SQUARE = 3, HE_AVGPOOL = 4, HE_FLATTEN = 5, HE_FC = 6 };
+enum { HE_CONV2D = 1, HE_CONV1D = 2, HE_SQUARE = 3, HE_AVGPOOL = 4, HE_FLATTEN = 5, HE_FC = 6, HE_APPROX_RELU = 7 };
 typedef struct {
-    uint32_t op;       /* HE_CONV2D ... HE_FC */
+    uint32_t op;       /* HE_CONV2D ... HE_APPROX_RELU */
     uint32_t ch_in;    /* conv: input channels; FC: DAT_in */
     uint32_t ch_out;   /* conv: output channels; FC: DAT_out */
     uint32_t k;        /* conv kernel size; average-pooling size; FC: how the final rotation sum

@@ -83,6 +83,8 @@ def layers_to_c(layers):
             e.w, e.b = _dptr(w), _dptr(b)
         elif op == "square":
             e.op = _lib.HE_SQUARE
+        elif op == "approx_relu":
+            e.op = _lib.HE_APPROX_RELU
         elif op == "avgpool":
             e.op = _lib.HE_AVGPOOL
             e.k = l["k"]
@@ -359,6 +361,9 @@ class Context:
 
     def square(self, cts):
         return self._multi(len(cts), load().he_square, self._chan(cts), len(cts))
+
+    def approx_relu(self, cts):
+        return self._multi(len(cts), load().he_approx_relu, self._chan(cts), len(cts))
 
     def conv2d(self, cts, w, b, stride=1, incremental=False):
         w = np.ascontiguousarray(w, dtype=np.float64)

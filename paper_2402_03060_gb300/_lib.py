@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libunihenn.so")
 HE_OK, HE_EINVAL, HE_ENOMEM, HE_ELEVEL, HE_ESCALE, HE_ESLOTS, HE_ENOKEY, HE_ECUDA, HE_ETIMEOUT, HE_EOVERFLOW = range(10)
 STATUS_NAMES = ["HE_OK", "HE_EINVAL", "HE_ENOMEM", "HE_ELEVEL", "HE_ESCALE", "HE_ESLOTS", "HE_ENOKEY",
                 "HE_ECUDA", "HE_ETIMEOUT", "HE_EOVERFLOW"]
-HE_CONV2D, HE_CONV1D, HE_SQUARE, HE_AVGPOOL, HE_FLATTEN, HE_FC = 1, 2, 3, 4, 5, 6
+HE_CONV2D, HE_CONV1D, HE_SQUARE, HE_AVGPOOL, HE_FLATTEN, HE_FC, HE_APPROX_RELU = 1, 2, 3, 4, 5, 6, 7
 
 
 class he_params(ctypes.Structure):
@@ -73,6 +73,7 @@ SIGNATURES = {
     "he_mul_plain": (_int, [_vp, _vp, ctypes.POINTER(_dbl), _pp]),
     "he_add": (_int, [_vp, _vp, _vp, _pp]),
     "he_square": (_int, [_vp, _pp, _u32, _pp]),
+    "he_approx_relu": (_int, [_vp, _pp, _u32, _pp]),
     "he_conv2d": (_int, [_vp, _pp, _u32, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), _u32, _u32, _u32, _int, _pp]),
     "he_conv1d": (_int, [_vp, _pp, _u32, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), _u32, _u32, _u32, _int, _pp]),
     "he_avgpool": (_int, [_vp, _pp, _u32, _u32, _pp]),

@@ -589,6 +589,15 @@ Cts ct_rescale(Ctx *c, const Cts &a) {
     return o;
 }
 
+// Drop-Level as a modulus drop: the top limb of every polynomial is discarded (exact)
+Cts ct_drop_level(Ctx *c, const Cts &a) {
+    if (a.lp < 2) throw HeError(HE_ELEVEL, "drop level: no level left");
+    Cts o = cts_alloc(c, a.B, a.lp - 1, a.scale, a.lay);
+    CUDA_TRY(cudaMemcpy2DAsync(o.data(), (size_t)(a.lp - 1) * c->N * 8, a.data(), (size_t)a.lp * c->N * 8,
+                               (size_t)(a.lp - 1) * c->N * 8, (size_t)a.B * 2, cudaMemcpyDeviceToDevice, c->stream));
+    return o;
+}
+
 Cts ct_mul_pt(Ctx *c, const Cts &a, const u64 *pt, double pt_scale) {
     Cts o = cts_alloc(c, a.B, a.lp, a.scale * pt_scale, a.lay);
     ew_bcast(c, OP_MUL, o.data(), a.data(), pt, a.B, a.lp, 3);

@@ -174,6 +174,53 @@ static Feat layer_square(Ctx *c, const Feat &in) {
     return f;
 }
 
+// Approximate ReLU f(x) = c0 + c1 x + c2 x^2 (Sec. IV-F), 2 levels.  A pending pooling factor p
+// is folded in: f(p x) = c0 + (c1 p) x + (c2 p^2) x^2 (Sec. IV-C).  a = Rescale(Mul(x^2, c2 p^2));
+// b = Rescale(Mul(x, c1 p)) with the plaintext encoded at the scale that lands b on a's scale,
+// then its top limb dropped to a's level; f = a + b + c0.  The constants sit at the valid slots
+// only, so every other slot ends at zero.
+static const double RELU_C0 = 0.375373, RELU_C1 = 0.5, RELU_C2 = 0.117071;
+
+static Feat layer_approx_relu(Ctx *c, const Feat &in, PtCache *pc, const std::string &key) {
+    const Layout &L = in.x.lay;
+    const u32 lp = in.x.lp;
+    if (lp < 3) throw HeError(HE_ELEVEL, "approximate ReLU: needs two levels");
+    std::vector<u32> pos;
+    if (L.prev == PREV_FLAT || L.prev == PREV_FC) {
+        for (u32 t = 0; t < L.D; ++t) pos.push_back(t);
+    } else {
+        const u32 H = L.dims == 2 ? L.H : 1;
+        for (u32 r = 0; r < H; ++r)
+            for (u32 cc = 0; cc < L.W; ++cc) pos.push_back(L.I * (r * L.W_img + cc));
+    }
+    const double p = L.pending;
+    std::vector<DBuf> tmp;
+    auto mask = [&](const std::string &k, double v, double scale, u32 level) {
+        std::vector<u32> off, ps;
+        std::vector<double> val;
+        if (!pc || !pc->pts.count(k)) {
+            off = {0, (u32)pos.size()};
+            ps = pos;
+            val.assign(pos.size(), v);
+        }
+        return get_pts(c, pc, k, tmp, L, off, ps, val, scale, level);
+    };
+    Cts s2 = ct_square(c, in.x);                                              // level lp-1
+    const u64 *m2 = mask(key + ":r2", RELU_C2 * p * p, c->scale, lp - 1);
+    Cts a = ct_rescale(c, ct_mul_pt(c, s2, m2, c->scale));                    // level lp-2
+    const double sb = a.scale * (double)c->primes[lp - 1] / in.x.scale;
+    const u64 *m1 = mask(key + ":r1", RELU_C1 * p, sb, lp);
+    Cts b = ct_drop_level(c, ct_rescale(c, ct_mul_pt(c, in.x, m1, sb)));       // level lp-2
+    b.scale = a.scale;
+    Cts y = ct_add(c, a, b);
+    const u64 *m0 = mask(key + ":r0", RELU_C0, a.scale, lp - 2);
+    ct_add_pt_inplace(c, y, m0);
+    y.lay.pending = 1.0;
+    Feat f = in;
+    f.x = y;
+    return f;
+}
+
 // Sec. IV-E: remove intervals / invalid values, pack the channels.
 // Every mask-rotate-sum stage  sum_k Rot(m_k (.) x, r_k)  is evaluated as one hoisted
 // combination  sum_k Rot(m_k, r_k) (.) Rot(x, r_k)  (the masks are rotated in the clear),
@@ -399,6 +446,8 @@ static Plan plan_layers(const std::vector<LayerSpec> &ls, u32 Wi, u32 Hi) {
             prev = PREV_CONV;
         } else if (s.op == HE_SQUARE) {
             levels += 1;
+        } else if (s.op == HE_APPROX_RELU) {
+            levels += 2;
         } else if (s.op == HE_AVGPOOL) {
             u32 c = s.k, ckh = dims == 2 ? c : 1;
             if (c < 1 || c > W) throw HeError(HE_EINVAL, "pool size does not fit");
@@ -485,7 +534,7 @@ static std::vector<LayerSpec> copy_layers(const he_layer *layers, size_t n, u32 
             s.w.assign(l.w, l.w + nw);
             s.b.assign(l.b, l.b + l.ch_out);
         }
-        if (l.op < HE_CONV2D || l.op > HE_FC) throw HeError(HE_EINVAL, "unknown layer op");
+        if (l.op < HE_CONV2D || l.op > HE_APPROX_RELU) throw HeError(HE_EINVAL, "unknown layer op");
         out.push_back(std::move(s));
     }
     (void)Hi;
@@ -493,15 +542,16 @@ static std::vector<LayerSpec> copy_layers(const he_layer *layers, size_t n, u32 
 }
 
 static Feat run_layers(Ctx *c, Feat f, const std::vector<LayerSpec> &ls, PtCache *pc) {
-    static const char *opname[] = {"?", "conv2d", "conv1d", "square", "avgpool", "flatten", "fc"};
+    static const char *opname[] = {"?", "conv2d", "conv1d", "square", "avgpool", "flatten", "fc", "approx_relu"};
     for (size_t i = 0; i < ls.size(); ++i) {
         const LayerSpec &s = ls[i];
         std::string key = fmt("L%zu", i);
-        c->prof_tag = fmt("%zu%s", i, opname[s.op <= HE_FC ? s.op : 0]);
+        c->prof_tag = fmt("%zu%s", i, opname[s.op <= HE_APPROX_RELU ? s.op : 0]);
         switch (s.op) {
             case HE_CONV2D: f = layer_conv(c, f, s, s.k, s.k, false, pc, key); break;
             case HE_CONV1D: f = layer_conv(c, f, s, 1, s.k, false, pc, key); break;
             case HE_SQUARE: f = layer_square(c, f); break;
+            case HE_APPROX_RELU: f = layer_approx_relu(c, f, pc, key); break;
             case HE_AVGPOOL: f = layer_avgpool(c, f, s.k); break;
             case HE_FLATTEN: f = layer_flatten(c, f, pc, key); break;
             case HE_FC:
@@ -835,6 +885,16 @@ he_status he_square(he_ctx *h, he_ct *const *in, uint32_t n, he_ct **out) {
         if (!out) throw HeError(HE_EINVAL, "bad arguments");
         Feat f = gather_channels(c, in, n);
         scatter_channels(c, layer_square(c, f), out);
+    });
+}
+
+he_status he_approx_relu(he_ctx *h, he_ct *const *in, uint32_t n, he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        CtxLock lk_(c);
+        if (!out) throw HeError(HE_EINVAL, "bad arguments");
+        Feat f = gather_channels(c, in, n);
+        scatter_channels(c, layer_approx_relu(c, f, nullptr, "approx_relu"), out);
     });
 }
 

@@ -50,10 +50,12 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(L, n)
 
 
-@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "conv"])
+@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "m3", "conv"])
 def test_planner_matches_oracle(lib, name):
     if name == "lenet1":
         model, Wi, Hi = W.lenet1(), 28, 28
+    elif name == "m3":
+        model, Wi, Hi = W.m3_relu(), 28, 28
     elif name == "cnn1d":
         model, Wi, Hi = W.cnn1d(), 1024, 1
     elif name == "cnn1d_tree":

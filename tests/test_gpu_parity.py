@@ -243,6 +243,31 @@ def test_cnn1d_tree_fc_dnum3_bit_exact(G):
     assert np.abs(ctx.decrypt(out, 5)[0] - cnn.forward(x[0, 0], model, dims=1)).max() < 1e-3
 
 
+def test_m3_approx_relu_small_ring_bit_exact(G):
+    """M3 (approximate ReLU after a convolution and after an FC, 9 levels) at N = 4096,
+    dnum = 3, against the oracle; the approx_relu layer call gives the model's
+    intermediate ciphertext; logits against the FP64 CNN."""
+    P = dict(logn=12, data_bits=[60] + [40] * 9, special_bits=[60, 60, 60], dnum=3, log2_scale=40)
+    model = W.m3_relu()
+    stride, levels, steps = G.plan(model, 28, 28)
+    assert levels == 9
+    ctx, he = make_pair(G, P, steps)
+    img = W.images(1)
+    gct = ctx.encrypt(img, 1, stride, W.ENC_SEED)
+    out = ctx.compile(model, 28, 28, 1).infer(gct, use_graph=True)
+    want = run_oracle_model(he, model, img, 28, 28, stride, 1, W.ENC_SEED)
+    assert_same(ctx, out, he, want)
+    assert np.abs(ctx.decrypt(out, 10)[0] - cnn.forward(img[0], model)).max() < 1e-3
+    # the layer calls: conv then approx_relu equals the first two layers of the model
+    conv_out = ctx.conv2d([gct], model[0]["w"], model[0]["b"])
+    relu_out = ctx.approx_relu(conv_out)
+    ref = ctx.compile(model[:2], 28, 28, 1).infer(gct)
+    got = np.stack([ctx.export(r) for r in relu_out])
+    want2 = ctx.export(ref)
+    # the model keeps the 6 channels as one batch, channel-major
+    assert np.array_equal(got.reshape(want2.shape), want2)
+
+
 def test_batched_equals_single_and_uneven_tail(G):
     """3 ciphertexts x 2 samples (5 samples: an uneven last ciphertext) in one
     batch give the same ciphertexts as each ciphertext alone."""
