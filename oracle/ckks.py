@@ -416,7 +416,7 @@ class Ckks:
         return Ct(np.stack([self.add(a.d[0], b.d[0], q), self.add(a.d[1], b.d[1], q)]), a.scale)
 
     def drop_level(self, a: Ct) -> Ct:
-        """Drop-Level (Sec. III-B, reading C11) as a modulus drop: the top limb of each
+        """Drop-Level (Sec. IV-A, reading C11) as a modulus drop: the top limb of each
         polynomial is discarded; message and scale are unchanged."""
         assert a.lp >= 2, "level exhausted"
         return Ct(np.ascontiguousarray(a.d[:, : a.lp - 1]), a.scale)

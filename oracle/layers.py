@@ -318,9 +318,43 @@ def fc(be, xs, M, bias, lay: Layout, sum_mode: str = "linear"):
     return [out], replace(lay, pending=1.0, prev="fc", D=dout, W=dout)
 
 
+# --------------------------------------------------------------- batch combining
+def pack_steps(stride: int, n: int):
+    """Rotation steps pack() uses for n single-sample ciphertexts: right by i*stride."""
+    return [-i * stride for i in range(1, n)]
+
+
+def pack(be, xs, lays):
+    """Sec. III-B: combine ciphertexts into one: the i-th input is rotated right by
+    (the samples before it) * stride and the rotations are added.  Every input
+    has the input layout of the same image size and stride; the result carries
+    all their samples in order.  Evaluated as one combination of the per-input
+    rotations with a single ModDown (as the channel packing of the flatten)."""
+    l0 = lays[0]
+    off, steps = 0, []
+    for lay in lays:
+        assert lay.prev == "input" and (lay.W_img, lay.H_img, lay.stride, lay.dims, lay.slots) == \
+            (l0.W_img, l0.H_img, l0.stride, l0.dims, l0.slots), "pack: inputs differ in layout"
+        steps.append(-off * l0.stride)
+        off += lay.n_samples
+    assert off * l0.stride <= l0.slots, "pack: the samples do not fit in the slots"
+    y = be.lincomb_diag(list(xs), steps) if len(xs) > 1 else xs[0]
+    return y, replace(l0, n_samples=off)
+
+
 # --------------------------------------------------------------- model
 def run_model(be, x, layers, lay: Layout, conv_mode: str = "hoisted"):
-    """Evaluate a layer list (dicts as produced by ``workloads``) on [x]."""
+    """Evaluate a layer list (dicts as produced by ``workloads``) on [x].
+
+    Drop-Level (Sec. IV-A): when x has more levels left than the model consumes,
+    its top levels are dropped first (reading C11: as a modulus drop), so every
+    layer runs on the fewest limbs."""
+    left = be.levels_left(x)
+    if left is not None:
+        need = plan(layers, lay.W_img, lay.H_img, lay.dims)["levels"]
+        assert left >= need, "not enough levels for this model"
+        for _ in range(left - need):
+            x = be.drop_level(x)
     return run_layers(be, [x], layers, lay, conv_mode)
 
 
@@ -467,6 +501,12 @@ class HeBackend:
             y = self.he.drop_level(y)
         y.scale = target.scale
         return y
+
+    def levels_left(self, x):
+        return x.lp - 1
+
+    def drop_level(self, x):
+        return self.he.drop_level(x)
 
     def add(self, x, y):
         return self.he.ct_add(x, y)

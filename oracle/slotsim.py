@@ -29,6 +29,10 @@ class SlotSim:
     def wrap(v):
         return SV(np.asarray(v, dtype=np.float64))
 
+    @staticmethod
+    def levels_left(x):
+        return None        # cleartext: no level budget, Drop-Level never applies
+
     def rot(self, x, r):
         self.count["rot"] += 1
         return SV(np.roll(x.v, -r), x.used, x.pending_rescale)

@@ -50,9 +50,11 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(L, n)
 
 
-@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "m3", "conv"])
+@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "m3", "conv", "M1", "M4", "M6", "M7"])
 def test_planner_matches_oracle(lib, name):
-    if name == "lenet1":
+    if name in W.PAPER_MODELS:
+        model, Wi, Hi = W.paper_model(name)
+    elif name == "lenet1":
         model, Wi, Hi = W.lenet1(), 28, 28
     elif name == "m3":
         model, Wi, Hi = W.m3_relu(), 28, 28

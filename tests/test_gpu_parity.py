@@ -268,6 +268,39 @@ def test_m3_approx_relu_small_ring_bit_exact(G):
     assert np.array_equal(got.reshape(want2.shape), want2)
 
 
+def _paper_model_case(G, name, n_samples):
+    model, Wi, Hi = W.paper_model(name)
+    dims = 1 if Hi == 1 else 2
+    stride, levels, steps = G.plan(model, Wi, Hi)
+    logn = max(11, int(np.ceil(np.log2(stride * n_samples))) + 1)
+    P = dict(logn=logn, data_bits=[60] + [40] * levels, special_bits=[60, 60, 60], dnum=3, log2_scale=40)
+    ctx, he = make_pair(G, P, steps)
+    x = W.images(n_samples, Hi, Wi) if dims == 2 else W.signals(n_samples, Wi)[:, 0]
+    gct = ctx.encrypt(x, n_samples, stride, W.ENC_SEED)
+    out = ctx.compile(model, Wi, Hi, n_samples).infer(gct, use_graph=True)
+    want = run_oracle_model(he, model, x, Wi, Hi, stride, n_samples, W.ENC_SEED, dims=dims)
+    assert_same(ctx, out, he, want)
+    n_out = model[-1]["w"].shape[0]
+    logits = ctx.decrypt(out, n_out)
+    for b in range(n_samples):
+        assert np.abs(logits[b] - cnn.forward(x[b], model, dims=dims)).max() < 1e-3
+
+
+@pytest.mark.parametrize("name", ["M1", "M6", "M7"])
+def test_paper_models_bit_exact(G, name):
+    """The paper's M1 (conv K4 S3, flatten after the convolution), M6 (16x16, conv K4
+    S2) and M7 (1-D, two strided convolutions): two samples per ciphertext, dnum = 3,
+    bit-exact against the oracle; logits against the FP64 CNN."""
+    _paper_model_case(G, name, 2)
+
+
+@pytest.mark.slow
+def test_lenet5_m4_bit_exact(G):
+    """The paper's M4 (LeNet-5: conv3 16->120 leaves 1x1 per channel, so the
+    flatten is channel packing alone, no level): bit-exact against the oracle."""
+    _paper_model_case(G, "M4", 1)
+
+
 def test_batched_equals_single_and_uneven_tail(G):
     """3 ciphertexts x 2 samples (5 samples: an uneven last ciphertext) in one
     batch give the same ciphertexts as each ciphertext alone."""

@@ -36,7 +36,8 @@ def test_single_conv_incremental_full_size():
     ref = cnn.forward(img, model)             # 24 x 24
     got = np.array([dec[r * 28 + c] for r in range(24) for c in range(24)])
     assert np.abs(got - ref).max() < 1e-6
-    assert ys[0].lp == 2 and be.count["rot"] == 24 and be.count["pmul"] == 25
+    # the chain has two levels, the model needs one: Drop-Level (Sec. IV-A) removes the other first
+    assert ys[0].lp == 1 and be.count["rot"] == 24 and be.count["pmul"] == 25
 
 
 def test_lenet1_small_ring_logits():
@@ -63,3 +64,68 @@ def test_packed_samples_equal_single():
     for b in range(2):
         ref = cnn.forward(imgs[b], model)
         assert np.abs(dec2[b * 784 + idx] - ref.reshape(-1)).max() < 1e-6
+
+
+def test_pack_on_the_slot_simulator_equals_packed_encryption():
+    """Sec. III-B on cleartext: single-sample vectors rotated right by i*stride and
+    added are exactly the multi-sample layout, and the model gives the same outputs."""
+    from oracle import slotsim
+    model, Wi, Hi = W.paper_model("M7")
+    pl = layers.plan(model, Wi, Hi, 1)
+    slots, n = 1024, 5
+    sig = W.signals(n, Wi)[:, 0]
+    be = slotsim.SlotSim()
+    singles = []
+    for s in sig:
+        v = np.zeros(slots)
+        v[:Wi] = s
+        singles.append(be.wrap(v))
+    lays = [layers.input_layout(Wi, Hi, pl["stride"], 1, slots, 1)] * n
+    y, lay = layers.pack(be, singles, lays)
+    assert lay.n_samples == n
+    want = np.zeros(slots)
+    for b, s in enumerate(sig):
+        want[b * pl["stride"]: b * pl["stride"] + Wi] = s
+    assert np.array_equal(y.v, want)
+    out, _ = layers.run_model(be, y, model, lay)
+    for b in range(n):
+        ref = cnn.forward(sig[b], model, dims=1)
+        assert np.abs(out[0].v[b * pl["stride"]: b * pl["stride"] + 5] - ref).max() < 1e-12
+
+
+def test_pack_and_drop_level_on_ciphertexts():
+    """Sec. III-B and IV-A on the CKKS oracle: three ciphertexts (1, 2 and 1 samples)
+    packed into one decrypt to the concatenation; encrypted with two more levels than
+    the model needs, the model drops them first (same final level as an exact chain)
+    and every sample's logits match the FP64 CNN."""
+    model, Wi, Hi = W.paper_model("M7")
+    pl = layers.plan(model, Wi, Hi, 1)
+    L = pl["levels"] + 2
+    P = dict(logn=11, data_bits=[60] + [40] * L, special_bits=[60, 60, 60], dnum=3, log2_scale=40)
+    he = ckks.Ckks(seed=W.KEY_SEED, **P)
+    stride, slots = pl["stride"], 1024
+    he.keygen(sorted(set(pl["steps"]) | set(layers.pack_steps(stride, 4))))
+    sig = W.signals(4, Wi)[:, 0]
+    groups = [sig[0:1], sig[1:3], sig[3:4]]
+    cts, lays = [], []
+    for k, g in enumerate(groups):
+        x = np.zeros(slots)
+        for b, s in enumerate(g):
+            x[b * stride: b * stride + Wi] = s
+        cts.append(he.encrypt(x, W.ENC_SEED + k))
+        lays.append(layers.input_layout(Wi, Hi, stride, len(g), slots, 1))
+    be = layers.HeBackend(he)
+    y, lay = layers.pack(be, cts, lays)
+    assert lay.n_samples == 4 and y.lp == L + 1
+    want = np.zeros(slots)
+    for b, s in enumerate(sig):
+        want[b * stride: b * stride + Wi] = s
+    assert np.abs(he.decrypt(y) - want).max() < 1e-6
+    # Drop-Level leaves the message untouched (decryption reads limb q_0 alone)
+    assert np.array_equal(he.decrypt(he.drop_level(y)), he.decrypt(y))
+    out, _ = layers.run_model(be, y, model, lay)
+    assert out[0].lp == 1
+    dec = he.decrypt(out[0])
+    for b in range(4):
+        ref = cnn.forward(sig[b], model, dims=1)
+        assert np.abs(dec[b * stride: b * stride + 5] - ref).max() < 1e-3

@@ -86,9 +86,13 @@ def test_cnn_against_torch():
     assert np.abs(t.numpy().reshape(-1) - cnn.forward(s[0], m1, dims=1)).max() < 1e-12
 
 
-@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "m3", "M1", "M7"])
+@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "m3", "M1", "M4", "M6", "M7"])
 def test_slot_algorithms_equal_direct_cnn(name):
-    if name == "lenet1":
+    if name in ("M4", "M6"):
+        model, Wi, Hi = W.paper_model(name)
+        dims, slots = 2, 8192
+        gen = lambda n: W.images(n, Hi, Wi)
+    elif name == "lenet1":
         model, Wi, Hi, dims, slots = W.lenet1(), 28, 28, 2, 8192
         gen = lambda n: W.images(n)
     elif name == "m3":
@@ -120,7 +124,7 @@ def test_slot_algorithms_equal_direct_cnn(name):
     assert np.abs(y1.v[:len(ref)] - y.v[:len(ref)]).max() < 1e-12
 
 
-@pytest.mark.parametrize("name", ["M1", "M2", "M3", "M4", "M7"])
+@pytest.mark.parametrize("name", ["M1", "M2", "M3", "M4", "M6", "M7"])
 def test_levels_per_layer_match_paper_tables(name):
     g = GOLD["mult_per_layer"][name]
     model = build_model(g["layers"])

@@ -82,7 +82,7 @@ def lenet5_sq(seed: int = WEIGHT_SEED):
 
 
 def m3_relu(seed: int = WEIGHT_SEED):
-    """The paper's M3 shape (Exp. 3): conv 1->6 K3, approximate ReLU, avgpool 2,
+    """The paper's M3 shape (Exp. 3, Sec. VII-C): conv 1->6 K3, approximate ReLU, avgpool 2,
     flatten, FC 1014->120, approximate ReLU, FC 120->10 (9 levels)."""
     rng = np.random.default_rng(seed)
     return [
@@ -94,6 +94,51 @@ def m3_relu(seed: int = WEIGHT_SEED):
         {"op": "approx_relu"},
         {"op": "fc", "w": _normal(rng, (10, 120)), "b": _normal(rng, (10,))},
     ]
+
+
+def _from_shapes(spec, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for l in spec:
+        if l[0] == "conv2d":
+            _, ci, co, k, s = l
+            out.append({"op": "conv2d", "w": _normal(rng, (co, ci, k, k)), "b": _normal(rng, (co,)), "stride": s})
+        elif l[0] == "conv1d":
+            _, ci, co, k, s = l
+            out.append({"op": "conv1d", "w": _normal(rng, (co, ci, k)), "b": _normal(rng, (co,)), "stride": s})
+        elif l[0] == "fc":
+            _, din, dout = l
+            out.append({"op": "fc", "w": _normal(rng, (dout, din)), "b": _normal(rng, (dout,))})
+        elif l[0] == "avgpool":
+            out.append({"op": "avgpool", "k": l[1]})
+        else:
+            out.append({"op": l[0]})
+    return out
+
+
+# The paper's other model shapes (Sec. VII, tables of detailed parameters), as
+# (op, CH_in, CH_out, K, S) / (fc, DAT_in, DAT_out) lists, with the input size each implies.
+PAPER_MODELS = {
+    # Exp. 1: conv 1->8 K4 S3 on 28x28 (8x8 outputs), flatten after the convolution
+    "M1": ([("conv2d", 1, 8, 4, 3), ("square",), ("flatten",), ("fc", 648, 64), ("square",), ("fc", 64, 10)],
+           28, 28),
+    # Exp. 4: LeNet-5 with x^2; conv3 16->120 K5 leaves 1x1 per channel (32x32 input)
+    "M4": ([("conv2d", 1, 6, 5, 1), ("square",), ("avgpool", 2), ("conv2d", 6, 16, 5, 1), ("square",),
+            ("avgpool", 2), ("conv2d", 16, 120, 5, 1), ("square",), ("flatten",), ("fc", 120, 84), ("square",),
+            ("fc", 84, 10)], 32, 32),
+    # Exp. 6: USPS 16x16, conv 1->6 K4 S2 (7x7 outputs, 294 = DAT_in of FC1)
+    "M6": ([("conv2d", 1, 6, 4, 2), ("square",), ("flatten",), ("fc", 294, 64), ("square",), ("fc", 64, 10)],
+           16, 16),
+    # Exp. 7: 1-D CNN on length 128 (flatten 4 x 32 = 128 = DAT_in of FC1)
+    "M7": ([("conv1d", 1, 2, 2, 2), ("square",), ("conv1d", 2, 4, 2, 2), ("flatten",), ("fc", 128, 32),
+            ("square",), ("fc", 32, 5)], 128, 1),
+}
+
+
+def paper_model(name: str, seed: int = WEIGHT_SEED):
+    """(layers with N(0, 0.1^2) weights, W_img, H_img) of one of PAPER_MODELS."""
+    spec, Wi, Hi = PAPER_MODELS[name]
+    return _from_shapes(spec, seed), Wi, Hi
 
 
 def images(n: int, H: int = 28, W: int = 28, seed: int = INPUT_SEED) -> np.ndarray:
