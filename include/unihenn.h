@@ -101,6 +101,25 @@ he_status he_encrypt(he_ctx *ctx, const double *x, int x_on_device, uint32_t W, 
  * Errors: HE_EINVAL, HE_ECUDA. */
 he_status he_decrypt(he_ctx *ctx, const he_ct *ct, double *out, int out_on_device, size_t n_per_sample);
 
+/* Batch combining (paper Sec. III-B), a client-side step: n ciphertexts, each a
+ * batch of one in the input layout of the same image size and stride (as
+ * he_encrypt makes them), become one ciphertext.  Input i is rotated right by
+ * s_i * stride, s_i = the sample positions of the inputs before it, and all are
+ * added: one key switch per input after the first, summed over Q u P with a
+ * single ModDown.  The result's layout has the sum of the inputs' sample
+ * positions.  Needs the Galois keys of the steps -s_i*stride.  *out is a new
+ * handle.  Errors: HE_EINVAL (null, batch != 1, layouts differ), HE_ESLOTS
+ * (the samples do not fit in N/2 slots), HE_ESCALE / HE_EINVAL (scale or level
+ * differ), HE_ENOKEY. */
+he_status he_pack(he_ctx *ctx, he_ct *const *in, uint32_t n, he_ct **out);
+
+/* Drop-Level (paper Sec. IV-A) as a modulus drop: the top `levels` limbs of
+ * every polynomial are removed; message, scale and layout are unchanged (levels
+ * = 0 gives a new handle on the same data).  he_infer applies it by itself to an
+ * input with more levels than the model consumes.  *out is a new handle.
+ * Errors: HE_EINVAL, HE_ELEVEL (fewer than levels + 1 limbs). */
+he_status he_drop_level(he_ctx *ctx, const he_ct *in, uint32_t levels, he_ct **out);
+
 /* Batch size, active limbs L' and scale of a ciphertext batch. */
 he_status he_ct_info(const he_ct *ct, uint32_t *batch, uint32_t *limbs, double *scale);
 

@@ -107,6 +107,11 @@ def plan(layers, W_img: int, H_img: int):
     return stride.value, levels.value, list(steps)
 
 
+def pack_steps(stride: int, n: int):
+    """Rotation steps he_pack needs for n one-sample ciphertexts: right by k*stride."""
+    return [-k * stride for k in range(1, n)]
+
+
 class Model:
     def __init__(self, ctx: "Context", h, keep):
         self.ctx, self._keep = ctx, keep
@@ -361,6 +366,13 @@ class Context:
 
     def square(self, cts):
         return self._multi(len(cts), load().he_square, self._chan(cts), len(cts))
+
+    def pack(self, cts) -> Ct:
+        """he_pack: one ciphertext carrying the samples of every input, in order."""
+        return self._one(load().he_pack, self._chan(cts), len(cts))
+
+    def drop_level(self, ct: Ct, levels: int = 1) -> Ct:
+        return self._one(load().he_drop_level, ct.h, levels)
 
     def approx_relu(self, cts):
         return self._multi(len(cts), load().he_approx_relu, self._chan(cts), len(cts))

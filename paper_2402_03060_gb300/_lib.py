@@ -70,6 +70,8 @@ SIGNATURES = {
     "he_rotate": (_int, [_vp, _vp, _i32, _pp]),
     "he_rotate_hoisted": (_int, [_vp, _vp, ctypes.POINTER(_i32), _sz, _pp]),
     "he_rescale": (_int, [_vp, _vp, _pp]),
+    "he_pack": (_int, [_vp, _pp, _u32, _pp]),
+    "he_drop_level": (_int, [_vp, _vp, _u32, _pp]),
     "he_mul_plain": (_int, [_vp, _vp, ctypes.POINTER(_dbl), _pp]),
     "he_add": (_int, [_vp, _vp, _vp, _pp]),
     "he_square": (_int, [_vp, _pp, _u32, _pp]),

@@ -589,13 +589,20 @@ Cts ct_rescale(Ctx *c, const Cts &a) {
     return o;
 }
 
-// Drop-Level as a modulus drop: the top limb of every polynomial is discarded (exact)
+// Drop-Level (Sec. IV-A) as a modulus drop: the top limbs of every polynomial are
+// discarded down to `keep` limbs (exact; message and scale unchanged)
+Cts ct_drop_to(Ctx *c, const Cts &a, u32 keep) {
+    if (keep < 1 || keep > a.lp) throw HeError(HE_ELEVEL, "drop level: not that many levels left");
+    if (keep == a.lp) return a;
+    Cts o = cts_alloc(c, a.B, keep, a.scale, a.lay);
+    CUDA_TRY(cudaMemcpy2DAsync(o.data(), (size_t)keep * c->N * 8, a.data(), (size_t)a.lp * c->N * 8,
+                               (size_t)keep * c->N * 8, (size_t)a.B * 2, cudaMemcpyDeviceToDevice, c->stream));
+    return o;
+}
+
 Cts ct_drop_level(Ctx *c, const Cts &a) {
     if (a.lp < 2) throw HeError(HE_ELEVEL, "drop level: no level left");
-    Cts o = cts_alloc(c, a.B, a.lp - 1, a.scale, a.lay);
-    CUDA_TRY(cudaMemcpy2DAsync(o.data(), (size_t)(a.lp - 1) * c->N * 8, a.data(), (size_t)a.lp * c->N * 8,
-                               (size_t)(a.lp - 1) * c->N * 8, (size_t)a.B * 2, cudaMemcpyDeviceToDevice, c->stream));
-    return o;
+    return ct_drop_to(c, a, a.lp - 1);
 }
 
 Cts ct_mul_pt(Ctx *c, const Cts &a, const u64 *pt, double pt_scale) {

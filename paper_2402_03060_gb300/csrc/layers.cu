@@ -573,9 +573,12 @@ void model_check_input(const he_model *m, const Cts &x) {
     if (x.lp < m->plan.levels + 1) throw HeError(HE_ELEVEL, "not enough levels for this model");
 }
 
-Cts model_infer(he_model *m, const Cts &x, bool use_graph) {
+Cts model_infer(he_model *m, const Cts &x_in, bool use_graph) {
     Ctx *c = m->c;
-    model_check_input(m, x);
+    model_check_input(m, x_in);
+    // Drop-Level (Sec. IV-A): a ciphertext with more levels than the model consumes
+    // loses its top limbs first, so every layer runs on the fewest limbs
+    const Cts x = ct_drop_to(c, x_in, m->plan.levels + 1);
     Feat f;
     f.x = x;
     f.CH = 1;
@@ -834,6 +837,47 @@ he_status he_rotate_hoisted(he_ctx *h, const he_ct *in, const int32_t *steps, si
         if (!in || !out || !steps || !n) throw HeError(HE_EINVAL, "bad arguments");
         std::vector<Cts> r = ct_rotate_hoisted(c, in->x, std::vector<int>(steps, steps + n));
         for (size_t i = 0; i < n; ++i) out[i] = ct_wrap(c, r[i]);
+    });
+}
+
+he_status he_drop_level(he_ctx *h, const he_ct *in, uint32_t levels, he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        CtxLock lk_(c);
+        if (!in || !out) throw HeError(HE_EINVAL, "bad arguments");
+        if (levels >= in->x.lp) throw HeError(HE_ELEVEL, "drop level: not that many levels left");
+        *out = ct_wrap(c, ct_drop_to(c, in->x, in->x.lp - levels));
+    });
+}
+
+// Sec. III-B: input i rotated right by (sample positions before it) * stride, all added;
+// one combination of the per-input rotations with a single ModDown
+he_status he_pack(he_ctx *h, he_ct *const *in, uint32_t n, he_ct **out) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        CtxLock lk_(c);
+        if (!in || !out || !n) throw HeError(HE_EINVAL, "bad arguments");
+        for (u32 i = 0; i < n; ++i)
+            if (!in[i]) throw HeError(HE_EINVAL, "null ciphertext");
+        const Layout &L0 = in[0]->x.lay;
+        std::vector<int> steps;
+        u64 off = 0;
+        for (u32 i = 0; i < n; ++i) {
+            const Cts &x = in[i]->x;
+            const Layout &L = x.lay;
+            if (x.B != 1) throw HeError(HE_EINVAL, "pack: every input must be one ciphertext");
+            if (L.prev != PREV_INPUT || L.W_img != L0.W_img || L.H_img != L0.H_img || L.stride != L0.stride ||
+                L.dims != L0.dims)
+                throw HeError(HE_EINVAL, "pack: inputs differ in layout");
+            steps.push_back(-(int)(off * L0.stride));
+            off += L.n_samples;
+        }
+        if (off * L0.stride > c->N / 2) throw HeError(HE_ESLOTS, "pack: the samples do not fit in the slots");
+        Feat f = gather_channels(c, in, n);
+        Cts y = n > 1 ? ct_lincomb_diag(c, f.x, n, 1, steps) : f.x;
+        y.lay = L0;
+        y.lay.n_samples = (u32)off;
+        *out = ct_wrap(c, y);
     });
 }
 

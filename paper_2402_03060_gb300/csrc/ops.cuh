@@ -45,6 +45,7 @@ Cts ct_add(Ctx *c, const Cts &a, const Cts &b);
 void ct_add_inplace(Ctx *c, Cts &a, const Cts &b);
 Cts ct_rescale(Ctx *c, const Cts &a);
 Cts ct_drop_level(Ctx *c, const Cts &a);
+Cts ct_drop_to(Ctx *c, const Cts &a, u32 keep);
 Cts ct_rotate(Ctx *c, const Cts &a, int step);
 // Rotations of one batch by several steps sharing one ModUp.  out[i] = Rot(a, steps[i]).
 // All outputs live in one buffer, step i at offset i*B*2*lp*N (the layout the MAC reads).

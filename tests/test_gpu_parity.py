@@ -301,6 +301,43 @@ def test_lenet5_m4_bit_exact(G):
     _paper_model_case(G, "M4", 1)
 
 
+def test_pack_and_drop_level_bit_exact(G):
+    """Batch combining (Sec. III-B) of three ciphertexts carrying 1, 2 and 1 samples,
+    and Drop-Level (Sec. IV-A): the chain has two more levels than M7 consumes, so
+    the model drops them first.  Every ciphertext bit-exact against the oracle."""
+    model, Wi, Hi = W.paper_model("M7")
+    stride, levels, steps = G.plan(model, Wi, Hi)
+    P = dict(logn=11, data_bits=[60] + [40] * (levels + 2), special_bits=[60, 60, 60], dnum=3, log2_scale=40)
+    ctx, he = make_pair(G, P, sorted(set(steps) | set(G.pack_steps(stride, 4))))
+    sig = W.signals(4, Wi)[:, 0]
+    groups = [sig[0:1], sig[1:3], sig[3:4]]
+    gcts = [ctx.encrypt(g, len(g), stride, W.ENC_SEED + k) for k, g in enumerate(groups)]
+    octs = [he.encrypt(slots_of(g, stride, he.n // 2), W.ENC_SEED + k) for k, g in enumerate(groups)]
+    lays = [olayers.input_layout(Wi, Hi, stride, len(g), he.n // 2, 1) for g in groups]
+    for g, o in zip(gcts, octs):
+        assert_same(ctx, g, he, o)
+    gp = ctx.pack(gcts)
+    be = olayers.HeBackend(he)
+    op, lay = olayers.pack(be, octs, lays)
+    assert_same(ctx, gp, he, op)
+    assert_same(ctx, ctx.drop_level(gp, 2), he, he.drop_level(he.drop_level(op)))
+    out = ctx.compile(model, Wi, Hi, 4).infer(gp, use_graph=True)
+    want, _ = olayers.run_model(be, op, model, lay)
+    assert_same(ctx, out, he, want[0])
+    logits = ctx.decrypt(out, 5)
+    for b in range(4):
+        assert np.abs(logits[b] - cnn.forward(sig[b], model, dims=1)).max() < 1e-3
+    from paper_2402_03060_gb300 import HeError
+    other = ctx.encrypt(sig[:1], 1, stride + 8, W.ENC_SEED)
+    with pytest.raises(HeError):
+        ctx.pack([gcts[0], other])                      # another stride
+    with pytest.raises(HeError) as e:
+        ctx.pack([gcts[1]] * 5)                         # 10 samples x 128 slots > 1024
+    assert "HE_ESLOTS" in str(e.value)
+    with pytest.raises(HeError):
+        ctx.drop_level(gp, levels + 3)                  # more levels than the ciphertext has
+
+
 def test_batched_equals_single_and_uneven_tail(G):
     """3 ciphertexts x 2 samples (5 samples: an uneven last ciphertext) in one
     batch give the same ciphertexts as each ciphertext alone."""
