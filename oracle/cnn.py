@@ -47,9 +47,12 @@ def avgpool(x, c, dims=2):
 
 
 def forward(x, layers, dims=2):
-    """x: [H][W] (or [W] for dims=1) -> output vector."""
+    """x: [H][W] or [C][H][W] (or [W] for dims=1) -> output vector."""
     x = np.asarray(x, dtype=np.float64)
-    x = x[None, None, :] if dims == 1 else x[None, :, :]
+    if dims == 1:
+        x = x[None, None, :]
+    elif x.ndim == 2:
+        x = x[None, :, :]
     for spec in layers:
         op = spec["op"]
         if op in ("conv2d", "conv1d"):

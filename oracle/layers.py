@@ -48,15 +48,19 @@ class Layout:
     pending: float = 1.0   # deferred factor of average pooling (Sec. IV-C)
     prev: str = "input"    # last layer that set the layout: input/conv/avgpool/flatten/fc
     D: int = 0             # after flatten / FC: values at slots [0, D) of each sample
+    C: int = 1             # input channels in one ciphertext (channel i at i*W_img*H_img)
 
     @property
     def flat(self) -> bool:
         return self.prev in ("flatten", "fc")
 
 
-def input_layout(W_img, H_img, stride, n_samples, slots, dims=2) -> Layout:
+def input_layout(W_img, H_img, stride, n_samples, slots, dims=2, channels=1) -> Layout:
+    """A sample's channels flattened channel-major, row-major (Sec. III-A): value
+    (i, r, c) at i*W_img*H_img + r*W_img + c of the sample."""
     assert stride * n_samples <= slots, "samples do not fit in the slots"
-    return Layout(W_img, H_img, W_img, H_img, 1, stride, n_samples, slots, dims)
+    assert channels * W_img * H_img <= stride, "a sample does not fit in the stride"
+    return Layout(W_img, H_img, W_img, H_img, 1, stride, n_samples, slots, dims, C=channels)
 
 
 def slot_vector(lay: Layout, positions, values) -> np.ndarray:
@@ -85,7 +89,10 @@ def conv(be, xs, w, bias, S: int, lay: Layout, mode: str = "hoisted"):
     if w.ndim == 3:
         w = w[:, :, None, :]
     co, ci, kh, kw = w.shape
-    assert ci == len(xs)
+    # an input of several channels in one ciphertext (Sec. III-A): input channel i is
+    # read through the extra rotation i*W_img*H_img, all rotations hoisted together
+    packed = len(xs) == 1 and ci > 1 and lay.prev == "input" and lay.C == ci
+    assert packed or ci == len(xs)
     I = lay.I
     offs = [(j, k) for j in range(kh) for k in range(kw)]
     step = {o: I * (o[1] + lay.W_img * o[0]) for o in offs}
@@ -96,7 +103,13 @@ def conv(be, xs, w, bias, S: int, lay: Layout, mode: str = "hoisted"):
     def kvec(o, i, off):
         return slot_vector(lay, pos, float(w[o, i, off[0], off[1]]) * lay.pending)
 
-    if mode == "hoisted":
+    if packed:
+        assert mode == "hoisted", "channels in one ciphertext: hoisted mode only"
+        chan = lay.W_img * lay.H_img
+        steps = [i * chan + step[off] for off in offs for i in range(ci)]
+        weights = [[[kvec(o, i, off) for off in offs for i in range(ci)]] for o in range(co)]
+        scaled = be.lincomb_rescale(xs, steps, weights)
+    elif mode == "hoisted":
         # all rotations of every input channel and all products in one hoisted
         # linear combination per output channel, rescaled
         weights = [[[kvec(o, i, off) for off in offs] for i in range(ci)] for o in range(co)]
@@ -126,7 +139,7 @@ def conv(be, xs, w, bias, S: int, lay: Layout, mode: str = "hoisted"):
     for o in range(co):
         acc = be.add_mask(scaled[o], slot_vector(lay, pos, float(bias[o])))
         outs.append(acc)
-    return outs, replace(lay, W=Wout, H=Hout, I=Iout, pending=1.0, prev="conv")
+    return outs, replace(lay, W=Wout, H=Hout, I=Iout, pending=1.0, prev="conv", C=1)
 
 
 def conv_steps(lay: Layout, kh: int, kw: int, mode: str = "hoisted"):
@@ -390,7 +403,9 @@ def plan(layers, W_img: int, H_img: int, dims: int = 2):
     """
     W, H, I, ch = W_img, H_img, 1, 1
     prev = "input"
-    need = W_img * H_img
+    # the input's channels: CH_in of a first convolution (all in one ciphertext)
+    C = np.asarray(layers[0]["w"]).shape[1] if layers and layers[0]["op"] in ("conv2d", "conv1d") else 1
+    need = C * W_img * H_img
     levels = 0
     steps: set[int] = set()
     flat_D = 0
@@ -401,7 +416,8 @@ def plan(layers, W_img: int, H_img: int, dims: int = 2):
             kh = w.shape[2] if w.ndim == 4 else 1
             kw = w.shape[-1]
             S = spec["stride"]
-            steps |= {I * (k + W_img * j) for j in range(kh) for k in range(kw)}
+            chans = range(w.shape[1]) if prev == "input" else [0]
+            steps |= {i * W_img * H_img + I * (k + W_img * j) for i in chans for j in range(kh) for k in range(kw)}
             H, W, I = (H - kh) // S + 1, (W - kw) // S + 1, I * S
             ch = w.shape[0]
             levels += 1

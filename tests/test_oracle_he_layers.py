@@ -129,3 +129,21 @@ def test_pack_and_drop_level_on_ciphertexts():
     for b in range(4):
         ref = cnn.forward(sig[b], model, dims=1)
         assert np.abs(dec[b * stride: b * stride + 5] - ref).max() < 1e-3
+
+
+def test_three_channel_input_logits():
+    """M5's layer sequence (channel-narrowed) on a 3x32x32 input encrypted as one
+    ciphertext, channel-major (Sec. III-A): the first convolution reads channel i
+    through the extra rotation i*32*32; logits against the FP64 CNN."""
+    model = W.m5_narrow()
+    pl = layers.plan(model, 32, 32)
+    assert pl["stride"] == 3 * 32 * 32 and pl["levels"] == 8
+    P = dict(logn=13, data_bits=[60] + [40] * 8, special_bits=[60, 60, 60], dnum=3, log2_scale=40)
+    he = ckks.Ckks(seed=W.KEY_SEED, **P)
+    he.keygen(pl["steps"])
+    img = W.images(1, 32, 32, C=3)
+    x = np.zeros(he.n // 2)
+    x[: img[0].size] = img[0].reshape(-1)
+    lay = layers.input_layout(32, 32, pl["stride"], 1, he.n // 2, 2, channels=3)
+    ys, _ = layers.run_model(layers.HeBackend(he), he.encrypt(x, W.ENC_SEED), model, lay)
+    assert np.abs(he.decrypt(ys[0])[:10] - cnn.forward(img[0], model)).max() < 1e-3

@@ -42,9 +42,9 @@ def pack(samples, stride, slots):
     return x
 
 
-def run_sim(model, samples, W_img, H_img, dims, slots):
+def run_sim(model, samples, W_img, H_img, dims, slots, channels=1):
     pl = layers.plan(model, W_img, H_img, dims)
-    lay = layers.input_layout(W_img, H_img, pl["stride"], len(samples), slots, dims)
+    lay = layers.input_layout(W_img, H_img, pl["stride"], len(samples), slots, dims, channels)
     be = slotsim.SlotSim()
     x = be.wrap(pack(samples, pl["stride"], slots))
     ys, lay = layers.run_model(be, x, model, lay)
@@ -84,11 +84,31 @@ def test_cnn_against_torch():
         elif l["op"] == "fc":
             t = F.linear(t.reshape(1, -1), torch.tensor(l["w"]), torch.tensor(l["b"]))
     assert np.abs(t.numpy().reshape(-1) - cnn.forward(s[0], m1, dims=1)).max() < 1e-12
+    # three input channels (M5, CIFAR-10 shaped)
+    m5, _, _ = W.paper_model("M5")
+    x3 = W.images(1, 32, 32, C=3)[0]
+    t = torch.tensor(x3, dtype=torch.float64)[None]
+    for l in m5:
+        if l["op"] == "conv2d":
+            t = F.conv2d(t, torch.tensor(l["w"]), torch.tensor(l["b"]), stride=l["stride"])
+        elif l["op"] == "square":
+            t = t * t
+        elif l["op"] == "avgpool":
+            t = F.avg_pool2d(t, l["k"])
+        elif l["op"] == "flatten":
+            t = t.reshape(1, -1)
+        elif l["op"] == "fc":
+            t = F.linear(t, torch.tensor(l["w"]), torch.tensor(l["b"]))
+    assert np.abs(t.numpy().reshape(-1) - cnn.forward(x3, m5)).max() < 1e-12
 
 
-@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "m3", "M1", "M4", "M6", "M7"])
+@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "m3", "M1", "M4", "m5n", "M6", "M7"])
 def test_slot_algorithms_equal_direct_cnn(name):
-    if name in ("M4", "M6"):
+    channels = 1
+    if name == "m5n":
+        model, Wi, Hi, dims, slots, channels = W.m5_narrow(), 32, 32, 2, 8192, 3
+        gen = lambda n: W.images(n, 32, 32, C=3)
+    elif name in ("M4", "M6"):
         model, Wi, Hi = W.paper_model(name)
         dims, slots = 2, 8192
         gen = lambda n: W.images(n, Hi, Wi)
@@ -114,27 +134,50 @@ def test_slot_algorithms_equal_direct_cnn(name):
     pl = layers.plan(model, Wi, Hi, dims)
     ns = slots // pl["stride"]
     samples = gen(ns)
-    y, lay, be, _ = run_sim(model, samples, Wi, Hi, dims, slots)
+    y, lay, be, _ = run_sim(model, samples, Wi, Hi, dims, slots, channels)
     for b in range(ns):
         ref = cnn.forward(samples[b], model, dims=dims)
         got = y.v[b * pl["stride"]: b * pl["stride"] + len(ref)]
         assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
     # packing changes nothing: sample 0 alone gives the same numbers
-    y1, _, _, _ = run_sim(model, samples[:1], Wi, Hi, dims, slots)
+    y1, _, _, _ = run_sim(model, samples[:1], Wi, Hi, dims, slots, channels)
     assert np.abs(y1.v[:len(ref)] - y.v[:len(ref)]).max() < 1e-12
 
 
-@pytest.mark.parametrize("name", ["M1", "M2", "M3", "M4", "M6", "M7"])
+def _narrow(spec, cap=8):
+    """The same layer sequence with at most `cap` channels per convolution (levels
+    and layouts do not depend on channel counts); the first FC shrinks with them."""
+    out, ch, ch_orig = [], None, None
+    for l in spec:
+        if l[0] == "conv2d":
+            co = min(l[2], cap)
+            out.append(["conv2d", l[1] if ch is None else ch, co, l[3], l[4]])
+            ch, ch_orig = co, l[2]
+        elif l[0] == "fc" and ch_orig is not None:
+            out.append(["fc", l[1] * ch // ch_orig, l[2]])
+            ch_orig = None
+        else:
+            out.append(list(l))
+    return out
+
+
+@pytest.mark.parametrize("name", ["M1", "M2", "M3", "M4", "M5", "M6", "M7"])
 def test_levels_per_layer_match_paper_tables(name):
     g = GOLD["mult_per_layer"][name]
     model = build_model(g["layers"])
     Wi, Hi = g["input"]
+    C = g.get("channels", 1)
     dims = 1 if Hi == 1 else 2
     pl = layers.plan(model, Wi, Hi, dims)
+    assert pl["levels"] == g["total"]
+    if C > 1:        # run the channel-narrowed copy (128 full-size channels are too big here)
+        model = build_model(_narrow(g["layers"]))
+        pl = layers.plan(model, Wi, Hi, dims)
     slots = 1 << max(11, int(np.ceil(np.log2(pl["stride"]))))
-    lay = layers.input_layout(Wi, Hi, pl["stride"], 1, slots, dims)
+    lay = layers.input_layout(Wi, Hi, pl["stride"], 1, slots, dims, C)
     be = slotsim.SlotSim()
-    xs = [be.wrap(pack(W.images(1, Hi, Wi) if dims == 2 else W.signals(1, Wi)[:, 0], pl["stride"], slots))]
+    x0 = W.images(1, Hi, Wi, C=C) if dims == 2 else W.signals(1, Wi)[:, 0]
+    xs = [be.wrap(pack(x0, pl["stride"], slots))]
     used = []
     for spec in model:
         before = xs[0].used

@@ -1,9 +1,10 @@
 """Seeded synthetic workloads shaped like the paper's experiments.
 
 Shared by the tests, the benchmark and the oracle as INPUT GENERATORS ONLY:
-nothing here performs homomorphic-encryption arithmetic.  MNIST, USPS and the
+nothing here performs homomorphic-encryption arithmetic.  MNIST, USPS, CIFAR-10 and the
 ECG set are not available, so (paper Sec. VI datasets -> stand-ins):
   * MNIST 28x28 gray images      -> U[0,1] 28x28 images, sample i seeded 1000+i
+  * USPS 16x16, CIFAR-10 3x32x32  -> U[0,1] images of those shapes, seeded the same way
   * 1-D ECG beats                -> N(0,1) signals of length 1024, seeded 1000+i
   * trained weights               -> N(0, 0.1^2) weights and biases, seed 42
 Model shapes: a single 5x5 convolution
@@ -126,6 +127,10 @@ PAPER_MODELS = {
     "M4": ([("conv2d", 1, 6, 5, 1), ("square",), ("avgpool", 2), ("conv2d", 6, 16, 5, 1), ("square",),
             ("avgpool", 2), ("conv2d", 16, 120, 5, 1), ("square",), ("flatten",), ("fc", 120, 84), ("square",),
             ("fc", 84, 10)], 32, 32),
+    # Exp. 5: CIFAR-10 3x32x32 (the three channels in one ciphertext); pool 4 leaves 1x1x128
+    "M5": ([("conv2d", 3, 16, 3, 1), ("square",), ("avgpool", 2), ("conv2d", 16, 64, 4, 1), ("square",),
+            ("avgpool", 2), ("conv2d", 64, 128, 3, 1), ("square",), ("avgpool", 4), ("flatten",),
+            ("fc", 128, 10)], 32, 32),
     # Exp. 6: USPS 16x16, conv 1->6 K4 S2 (7x7 outputs, 294 = DAT_in of FC1)
     "M6": ([("conv2d", 1, 6, 4, 2), ("square",), ("flatten",), ("fc", 294, 64), ("square",), ("fc", 64, 10)],
            16, 16),
@@ -135,14 +140,25 @@ PAPER_MODELS = {
 }
 
 
+def m5_narrow(seed: int = WEIGHT_SEED):
+    """M5's layer sequence (3-channel 32x32 input, kernels 3/4/3, pools 2/2/4) with
+    4, 8 and 8 channels instead of 16, 64 and 128: the same levels and layouts at a
+    size the oracle runs in seconds."""
+    return _from_shapes([("conv2d", 3, 4, 3, 1), ("square",), ("avgpool", 2), ("conv2d", 4, 8, 4, 1), ("square",),
+                         ("avgpool", 2), ("conv2d", 8, 8, 3, 1), ("square",), ("avgpool", 4), ("flatten",),
+                         ("fc", 8, 10)], seed)
+
+
 def paper_model(name: str, seed: int = WEIGHT_SEED):
     """(layers with N(0, 0.1^2) weights, W_img, H_img) of one of PAPER_MODELS."""
     spec, Wi, Hi = PAPER_MODELS[name]
     return _from_shapes(spec, seed), Wi, Hi
 
 
-def images(n: int, H: int = 28, W: int = 28, seed: int = INPUT_SEED) -> np.ndarray:
-    return np.stack([np.random.default_rng(seed + i).uniform(0.0, 1.0, (H, W)) for i in range(n)])
+def images(n: int, H: int = 28, W: int = 28, seed: int = INPUT_SEED, C: int = 1) -> np.ndarray:
+    """[n][H][W] (C = 1) or [n][C][H][W] U[0,1] images (CIFAR-10 -> C = 3)."""
+    shape = (H, W) if C == 1 else (C, H, W)
+    return np.stack([np.random.default_rng(seed + i).uniform(0.0, 1.0, shape) for i in range(n)])
 
 
 def signals(n: int, length: int = 1024, seed: int = INPUT_SEED) -> np.ndarray:
