@@ -95,6 +95,16 @@ he_status he_encrypt(he_ctx *ctx, const double *x, int x_on_device, uint32_t W, 
                      uint32_t n_samples, uint32_t samples_per_ct, uint32_t stride,
                      uint64_t enc_seed, he_ct **out);
 
+/* he_encrypt for samples of C channels, x [n_samples][C][H][W]: each sample is
+ * flattened channel-major, row-major (Sec. III-A), value (i, r, c) at slot
+ * offset i*W*H + r*W + c of its position; C*W*H <= stride.  A model whose first
+ * convolution has CH_in = C reads input channel i through an extra rotation by
+ * i*W*H.  C = 1 is he_encrypt.  Errors as he_encrypt; HE_EINVAL for C > 1 with
+ * H = 1. */
+he_status he_encrypt_channels(he_ctx *ctx, const double *x, int x_on_device, uint32_t C, uint32_t W, uint32_t H,
+                              uint32_t n_samples, uint32_t samples_per_ct, uint32_t stride, uint64_t enc_seed,
+                              he_ct **out);
+
 /* Decrypt and decode: out is [B*samples_per_ct][n_per_sample] doubles (host or
  * device), the slots k*stride + [0, n_per_sample) of every sample position.
  * Decoding reads limb q_0, valid while |message * scale| < q_0/2.

@@ -288,7 +288,8 @@ class Context:
         check(load().he_tuning_set(self.h, v, len(v)))
 
     def encrypt(self, x, samples_per_ct: int, stride: int, enc_seed: int) -> Ct:
-        """x: [n][H][W] (2-D) or [n][W] (1-D), numpy (host) or CUDA torch tensor (device)."""
+        """x: [n][H][W] (2-D), [n][C][H][W] (C channels in one ciphertext) or [n][W]
+        (1-D), numpy (host) or CUDA torch tensor (device)."""
         out = ctypes.c_void_p()
         if hasattr(x, "is_cuda") and x.is_cuda:
             xs = x.contiguous()
@@ -300,10 +301,13 @@ class Context:
             shape = keep.shape
             ptr, dev = keep.ctypes.data_as(ctypes.c_void_p), 0
         if len(shape) == 2:
-            n, H, W = shape[0], 1, shape[1]
+            n, C, H, W = shape[0], 1, 1, shape[1]
+        elif len(shape) == 3:
+            (n, H, W), C = shape, 1
         else:
-            n, H, W = shape
-        check(load().he_encrypt(self.h, ptr, dev, W, H, n, samples_per_ct, stride, enc_seed, ctypes.byref(out)))
+            n, C, H, W = shape
+        check(load().he_encrypt_channels(self.h, ptr, dev, C, W, H, n, samples_per_ct, stride, enc_seed,
+                                         ctypes.byref(out)))
         del keep
         return Ct(self, out)
 

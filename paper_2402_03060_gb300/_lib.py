@@ -62,6 +62,7 @@ SIGNATURES = {
     "he_context_primes": (_int, [_vp, ctypes.POINTER(_u64), _sz]),
     "he_keygen": (_int, [_vp, ctypes.POINTER(_i32), _sz]),
     "he_encrypt": (_int, [_vp, _vp, _int, _u32, _u32, _u32, _u32, _u32, _u64, _pp]),
+    "he_encrypt_channels": (_int, [_vp, _vp, _int, _u32, _u32, _u32, _u32, _u32, _u32, _u64, _pp]),
     "he_decrypt": (_int, [_vp, _vp, _vp, _int, _sz]),
     "he_ct_info": (_int, [_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32), ctypes.POINTER(_dbl)]),
     "he_ct_layout": (_int, [_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),

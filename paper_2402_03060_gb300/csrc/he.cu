@@ -524,11 +524,11 @@ Cts cts_view(const Cts &base, size_t off_words, u32 B) {
     return t;
 }
 
-Cts encrypt(Ctx *c, const double *x_dev, u32 W, u32 H, u32 nsamp, u32 spc, u32 stride, u64 enc_seed) {
+Cts encrypt(Ctx *c, const double *x_dev, u32 W, u32 H, u32 nsamp, u32 spc, u32 stride, u64 enc_seed, u32 C) {
     if (!c->have_keys) throw HeError(HE_EINVAL, "he_keygen has not run");
-    if (!nsamp) throw HeError(HE_EINVAL, "no samples to encrypt");
+    if (!nsamp || !C) throw HeError(HE_EINVAL, "no samples to encrypt");
     const u32 N = c->N, M = N / 2, L1 = c->L1;
-    if (!spc || !stride || (u64)spc * stride > M || (u64)W * H > stride)
+    if (!spc || !stride || (u64)spc * stride > M || (u64)C * W * H > stride)
         throw HeError(HE_ESLOTS, "samples do not fit in the slots");
     const u32 B = (nsamp + spc - 1) / spc;
     Layout lay;
@@ -538,9 +538,10 @@ Cts encrypt(Ctx *c, const double *x_dev, u32 W, u32 H, u32 nsamp, u32 spc, u32 s
     lay.stride = stride;
     lay.n_samples = spc;
     lay.dims = H == 1 ? 1 : 2;
+    lay.C = C;
     Cts out = cts_alloc(c, B, L1, c->scale, lay);
     DBuf z(c, (size_t)B * M);
-    pack_samples(c, reinterpret_cast<double *>(z.p), x_dev, nsamp, spc, stride, W * H, B);
+    pack_samples(c, reinterpret_cast<double *>(z.p), x_dev, nsamp, spc, stride, C * W * H, B);
     for (u32 b0 = 0; b0 < B; b0 += SEEDLIST_MAX) {
         const u32 nb = std::min<u32>(SEEDLIST_MAX, B - b0);
         DBuf me(c, (size_t)nb * L1 * N), e1(c, (size_t)nb * L1 * N), u(c, (size_t)nb * L1 * N);

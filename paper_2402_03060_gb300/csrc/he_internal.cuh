@@ -214,6 +214,7 @@ struct Layout {
     double pending = 1.0;       // deferred pooling factor
     int prev = 0;               // 0 input, 1 conv, 2 avgpool, 3 flatten, 4 fc
     u32 D = 0;                  // flattened length
+    u32 C = 1;                  // input channels in one ciphertext (channel i at i*W_img*H_img)
 };
 enum { PREV_INPUT = 0, PREV_CONV = 1, PREV_POOL = 2, PREV_FLAT = 3, PREV_FC = 4 };
 

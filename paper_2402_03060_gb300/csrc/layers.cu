@@ -58,14 +58,20 @@ static Feat layer_conv(Ctx *c, const Feat &in, const LayerSpec &sp, u32 kh, u32 
                        const std::string &key) {
     const Layout &L = in.x.lay;
     const u32 ci = sp.ci, co = sp.co, S = sp.s, B = in.B, lp = in.x.lp, N = c->N;
-    if (in.CH != ci) throw HeError(HE_EINVAL, "conv: channel count mismatch");
+    // an input of several channels in one ciphertext (Sec. III-A): input channel i is read
+    // through the extra rotation i*W_img*H_img; all its rotations are hoisted together
+    const bool packed = in.CH == 1 && L.prev == PREV_INPUT && L.C > 1;
+    if (packed ? L.C != ci : in.CH != ci) throw HeError(HE_EINVAL, "conv: channel count mismatch");
+    if (packed && incremental) throw HeError(HE_EINVAL, "conv: channels in one ciphertext need hoisted mode");
     if (lp < 2) throw HeError(HE_ELEVEL, "conv: no level left");
     if (kh > L.H || kw > L.W) throw HeError(HE_EINVAL, "conv: kernel larger than the feature map");
     const u32 Hout = (L.H - kh) / S + 1, Wout = (L.W - kw) / S + 1, Iout = L.I * S;
     const u32 KK = kh * kw;
-    std::vector<int> steps;
+    std::vector<int> steps;   // packed: step t = kk*ci + i, matching the plaintext order below
     for (u32 j = 0; j < kh; ++j)
-        for (u32 k = 0; k < kw; ++k) steps.push_back((int)(L.I * (k + L.W_img * j)));
+        for (u32 k = 0; k < kw; ++k)
+            for (u32 i = 0; i < (packed ? ci : 1u); ++i)
+                steps.push_back((int)(i * L.W_img * L.H_img + L.I * (k + L.W_img * j)));
     const size_t ctw = cts_ct_words(c, lp);
     std::vector<u32> vpos = valid_positions(L, Hout, Wout, Iout);
     const u32 T = KK * ci;
@@ -94,7 +100,7 @@ static Feat layer_conv(Ctx *c, const Feat &in, const LayerSpec &sp, u32 kh, u32 
     if (!incremental) {
         // one hoisted linear combination per output channel, ModDown and rescale as one division each
         const u64 *pts = weight_pts(c->K);
-        out = ct_lincomb(c, in.x, ci, B, steps, pts, co, c->scale, true);
+        out = ct_lincomb(c, in.x, packed ? 1 : ci, B, steps, pts, co, c->scale, true);
     } else {
         // rotated inputs R[off][ch*B + b]  (T index = off*ci + ch)
         Cts R = cts_alloc(c, KK * ci * B, lp, in.x.scale, L);
@@ -136,6 +142,7 @@ static Feat layer_conv(Ctx *c, const Feat &in, const LayerSpec &sp, u32 kh, u32 
     L2.I = Iout;
     L2.pending = 1.0;
     L2.prev = PREV_CONV;
+    L2.C = 1;
     out.lay = L2;
     Feat f;
     f.x = out;
@@ -428,7 +435,11 @@ static Feat layer_fc(Ctx *c, const Feat &in, const LayerSpec &sp, PtCache *pc, c
 // valid value inside it), CH*W*H of a flatten, W_vec of an FC); levels and steps.
 static Plan plan_layers(const std::vector<LayerSpec> &ls, u32 Wi, u32 Hi) {
     const u32 dims = Hi == 1 ? 1 : 2;
-    u32 W = Wi, H = Hi, I = 1, ch = 1, need = Wi * Hi, levels = 0;
+    // the input's channels: CH_in of a first convolution, all in one ciphertext (Sec. III-A)
+    const u32 C = !ls.empty() && (ls[0].op == HE_CONV2D || ls[0].op == HE_CONV1D) ? ls[0].ci : 1;
+    if (C < 1 || (C > 1 && dims == 1)) throw HeError(HE_EINVAL, "input channels need a 2-D image");
+    if ((u64)C * Wi * Hi > (1u << 30)) throw HeError(HE_EINVAL, "input too large");
+    u32 W = Wi, H = Hi, I = 1, ch = 1, need = C * Wi * Hi, levels = 0;
     int prev = PREV_INPUT;
     std::set<int> st;
     for (const LayerSpec &s : ls) {
@@ -436,8 +447,10 @@ static Plan plan_layers(const std::vector<LayerSpec> &ls, u32 Wi, u32 Hi) {
             u32 kh = s.op == HE_CONV2D ? s.k : 1, kw = s.k;
             if (s.op == HE_CONV2D && dims == 1) throw HeError(HE_EINVAL, "conv2d on a 1-D input");
             if (kh > H || kw > W || s.s < 1) throw HeError(HE_EINVAL, "conv kernel does not fit");
-            for (u32 j = 0; j < kh; ++j)
-                for (u32 k = 0; k < kw; ++k) st.insert((int)(I * (k + Wi * j)));
+            const u32 nch = prev == PREV_INPUT ? C : 1;
+            for (u32 i = 0; i < nch; ++i)
+                for (u32 j = 0; j < kh; ++j)
+                    for (u32 k = 0; k < kw; ++k) st.insert((int)(i * Wi * Hi + I * (k + Wi * j)));
             H = (H - kh) / s.s + 1;
             W = (W - kw) / s.s + 1;
             I *= s.s;
@@ -511,6 +524,7 @@ static Plan plan_layers(const std::vector<LayerSpec> &ls, u32 Wi, u32 Hi) {
     Plan p;
     p.stride = need;
     p.levels = levels;
+    p.C = C;
     p.steps.assign(st.begin(), st.end());
     return p;
 }
@@ -568,7 +582,7 @@ static Feat run_layers(Ctx *c, Feat f, const std::vector<LayerSpec> &ls, PtCache
 void model_check_input(const he_model *m, const Cts &x) {
     const Layout &L = x.lay;
     if (L.W_img != m->W_img || L.H_img != m->H_img || L.n_samples != m->spc || L.stride < m->plan.stride ||
-        L.prev != PREV_INPUT)
+        L.prev != PREV_INPUT || L.C != m->plan.C)
         throw HeError(HE_EINVAL, "ciphertext layout does not match the model");
     if (x.lp < m->plan.levels + 1) throw HeError(HE_ELEVEL, "not enough levels for this model");
 }
@@ -743,11 +757,17 @@ he_status he_keygen(he_ctx *h, const int32_t *steps, size_t n) {
 
 he_status he_encrypt(he_ctx *h, const double *x, int x_on_device, uint32_t W, uint32_t H, uint32_t nsamp,
                      uint32_t spc, uint32_t stride, uint64_t enc_seed, he_ct **out) {
+    return he_encrypt_channels(h, x, x_on_device, 1, W, H, nsamp, spc, stride, enc_seed, out);
+}
+
+he_status he_encrypt_channels(he_ctx *h, const double *x, int x_on_device, uint32_t C, uint32_t W, uint32_t H,
+                              uint32_t nsamp, uint32_t spc, uint32_t stride, uint64_t enc_seed, he_ct **out) {
     return guard([&] {
         Ctx *c = CX(h);
         CtxLock lk_(c);
-        if (!x || !out || !W || !H || !nsamp) throw HeError(HE_EINVAL, "bad arguments");
-        const size_t len = (size_t)nsamp * W * H;
+        if (!x || !out || !C || !W || !H || !nsamp) throw HeError(HE_EINVAL, "bad arguments");
+        if (C > 1 && H == 1) throw HeError(HE_EINVAL, "several input channels need a 2-D image");
+        const size_t len = (size_t)nsamp * C * W * H;
         const double *xd = x;
         DBuf tmp;
         if (!x_on_device) {
@@ -755,7 +775,7 @@ he_status he_encrypt(he_ctx *h, const double *x, int x_on_device, uint32_t W, ui
             CUDA_TRY(cudaMemcpyAsync(tmp.p, x, len * 8, cudaMemcpyHostToDevice, c->stream));
             xd = reinterpret_cast<const double *>(tmp.p);
         }
-        Cts ct = encrypt(c, xd, W, H, nsamp, spc, stride, enc_seed);
+        Cts ct = encrypt(c, xd, W, H, nsamp, spc, stride, enc_seed, C);
         if (!x_on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
         *out = ct_wrap(c, ct);
     });

@@ -14,7 +14,7 @@ struct LayerSpec {
 };
 
 struct Plan {
-    u32 stride = 0, levels = 0;
+    u32 stride = 0, levels = 0, C = 1;   // C: input channels of the first convolution
     std::vector<int> steps;
 };
 

@@ -40,7 +40,7 @@ void enc_combine(Ctx *c, u64 *ct, const u64 *u, const u64 *me, const u64 *e1, u3
 void decrypt_decode(Ctx *c, double *out, const u64 *ct, u32 B, u32 lp, double scale, u32 stride, u32 ns, u32 nper);
 
 // he.cu
-Cts encrypt(Ctx *c, const double *x_dev, u32 W, u32 H, u32 nsamp, u32 spc, u32 stride, u64 enc_seed);
+Cts encrypt(Ctx *c, const double *x_dev, u32 W, u32 H, u32 nsamp, u32 spc, u32 stride, u64 enc_seed, u32 C = 1);
 Cts ct_add(Ctx *c, const Cts &a, const Cts &b);
 void ct_add_inplace(Ctx *c, Cts &a, const Cts &b);
 Cts ct_rescale(Ctx *c, const Cts &a);

@@ -50,10 +50,13 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(L, n)
 
 
-@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "m3", "conv", "M1", "M4", "M6", "M7"])
+@pytest.mark.parametrize("name", ["lenet1", "cnn1d", "cnn1d_tree", "lenet5", "m3", "conv", "M1", "M4", "M5", "m5n",
+                                  "M6", "M7"])
 def test_planner_matches_oracle(lib, name):
     if name in W.PAPER_MODELS:
         model, Wi, Hi = W.paper_model(name)
+    elif name == "m5n":
+        model, Wi, Hi = W.m5_narrow(), 32, 32
     elif name == "lenet1":
         model, Wi, Hi = W.lenet1(), 28, 28
     elif name == "m3":

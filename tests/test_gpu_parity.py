@@ -301,6 +301,45 @@ def test_lenet5_m4_bit_exact(G):
     _paper_model_case(G, "M4", 1)
 
 
+def test_three_channel_input_bit_exact(G):
+    """M5's layer sequence (channel-narrowed) on 3x32x32 inputs, the three channels
+    in one ciphertext (the first convolution hoists 3 x 9 rotations of it): bit-exact
+    against the oracle at N = 8192, logits against the FP64 CNN; a single-channel
+    ciphertext is refused by the model."""
+    model = W.m5_narrow()
+    stride, levels, steps = G.plan(model, 32, 32)
+    assert (stride, levels) == (3072, 8)
+    P = dict(logn=13, data_bits=[60] + [40] * 8, special_bits=[60, 60, 60], dnum=3, log2_scale=40)
+    ctx, he = make_pair(G, P, steps)
+    img = W.images(1, 32, 32, C=3)
+    gct = ctx.encrypt(img, 1, stride, W.ENC_SEED)
+    m = ctx.compile(model, 32, 32, 1)
+    out = m.infer(gct, use_graph=True)
+    lay = olayers.input_layout(32, 32, stride, 1, he.n // 2, 2, channels=3)
+    oct_ = he.encrypt(slots_of(img, stride, he.n // 2), W.ENC_SEED)
+    assert_same(ctx, gct, he, oct_)
+    want, _ = olayers.run_model(olayers.HeBackend(he), oct_, model, lay)
+    assert_same(ctx, out, he, want[0])
+    assert np.abs(ctx.decrypt(out, 10)[0] - cnn.forward(img[0], model)).max() < 1e-3
+    from paper_2402_03060_gb300 import HeError
+    with pytest.raises(HeError):
+        m.infer(ctx.encrypt(img[:, 0], 1, stride, W.ENC_SEED))
+
+
+def test_m5_full_logits(G):
+    """The paper's M5 (CIFAR-10 shaped: 3 -> 16 -> 64 -> 128 channels, 8 levels) at
+    N = 2^13, one 3x32x32 sample: logits against the FP64 CNN.  The compiled model
+    holds about 50 GB of encoded weight masks (90,544 masks over Q u P limbs)."""
+    model, Wi, Hi = W.paper_model("M5")
+    stride, levels, steps = G.plan(model, Wi, Hi)
+    P = dict(logn=13, data_bits=[60] + [40] * levels, special_bits=[60, 60, 60], dnum=3, log2_scale=40)
+    ctx = G.Context(seed=W.KEY_SEED, **P)
+    ctx.keygen(steps)
+    imgs = W.images(1, 32, 32, C=3)
+    out = ctx.compile(model, Wi, Hi, 1).infer(ctx.encrypt(imgs, 1, stride, W.ENC_SEED))
+    assert np.abs(ctx.decrypt(out, 10)[0] - cnn.forward(imgs[0], model)).max() < 1e-3
+
+
 def test_pack_and_drop_level_bit_exact(G):
     """Batch combining (Sec. III-B) of three ciphertexts carrying 1, 2 and 1 samples,
     and Drop-Level (Sec. IV-A): the chain has two more levels than M7 consumes, so
