@@ -253,6 +253,7 @@ static u32 bitrev(u32 x, int bits) {
 // ------------------------------------------------------------------ context
 void ntt_init_attrs(Ctx *c);
 void keyswitch_init(Ctx *c);
+void mac_init(Ctx *c);
 
 Ctx *ctx_create(const he_params *p) {
     if (!p || p->log2n < 4 || p->log2n > 15 || p->n_data < 1 || p->n_data > 32 || p->n_special < 1 ||
@@ -360,6 +361,7 @@ Ctx *ctx_create(const he_params *p) {
     CUDA_TRY(cudaMemset(c->err_flag, 0, sizeof(int)));
     ntt_init_attrs(c.get());
     keyswitch_init(c.get());
+    mac_init(c.get());
     encode_init(c.get());
     return c.release();
 }

@@ -204,9 +204,11 @@ void sample_uniform(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u3
 // (ciphertext, poly) pairs; it stages the plaintext tile pt[0..O)[t-chunk][l][n-tile]
 // in shared memory once and every thread reuses it for its own pair, so a
 // plaintext word is read from global memory once per 256/NT pairs instead of
-// once per pair.  Lanes of a warp cover 4+ consecutive coefficients of 8 or
-// fewer pairs, so every ciphertext load is a full 32-byte sector.  Each thread
-// keeps all O sums as 128-bit accumulators (products < 2^120, folded every 128 terms).
+// once per pair.  The tiles are double-buffered: the copies of tile k+1 are issued
+// when tile k starts and land while it is computed.  Lanes of a warp cover 4+
+// consecutive coefficients of 8 or fewer pairs, so every ciphertext load is a full
+// 32-byte sector.  Each thread keeps all O sums as 128-bit accumulators (products
+// < 2^120, folded every 128 terms).
 #define MAC_DEPTH 8
 // OSPLIT threads share one (ciphertext, poly, coefficient): each keeps OMAX of the launch's
 // OMAX * OSPLIT outputs (fewer registers, more resident warps; the second thread's
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(256, OSPLIT == 1 ? 2 : 3) mac_kernel(u64 *out,
                                                   const PrimeDev *__restrict__ pd) {
     extern __shared__ u64 smem[];
     u64 *xs = smem;                          // [256][MAC_DEPTH]: each thread's own pipeline slots
-    u64 *ps = smem + 256 * MAC_DEPTH;        // [tc][NT][OW]: the plaintext tile
+    u64 *ps0 = smem + 256 * MAC_DEPTH;       // two plaintext tiles, each [tc][NT][OW]
     constexpr u32 OW = OMAX * OSPLIT;
     const u32 N = 1u << logn, NT = 1u << ntlog;
     const u32 tid = threadIdx.x;
@@ -235,28 +237,41 @@ __global__ void __launch_bounds__(256, OSPLIT == 1 ? 2 : 3) mac_kernel(u64 *out,
     for (int o = 0; o < OMAX; ++o) acc[o].lo = acc[o].hi = 0;
     const size_t xoff = ((size_t)bk * lp + l) * N + n0 + nl;   // bk = b*2 + k
     const size_t pstride_t = (size_t)lp * N;
+    const size_t tile_words = (size_t)tc * NT * OW;
     u64 *myx = xs + tid * MAC_DEPTH;
-    // prologue: the first MAC_DEPTH terms in flight (one commit group per term)
+    // the plaintext words of terms [t0, t0 + tc) into dst, every word in flight at once
+    // (one commit group)
+    auto load_tile = [&](u32 t0, u64 *dst) {
+        const u32 tcc = T - t0 < tc ? T - t0 : tc;
+        for (u32 idx = tid; idx < O * tcc * NT; idx += blockDim.x) {
+            const u32 j = idx & (NT - 1), r = idx >> ntlog;
+            const u32 tt = r % tcc, o = r / tcc;
+            cp_async8(dst + (tt * NT + j) * OW + o,
+                      pt + (size_t)o * pt_ostride + (size_t)(t0 + tt) * pstride_t + (size_t)l * N + n0 + j);
+        }
+        cp_commit();
+    };
+    // prologue: the first MAC_DEPTH terms in flight (one commit group per term), then tile 0
 #pragma unroll
     for (int d = 0; d < MAC_DEPTH; ++d) {
         if (active && (u32)d < T) cp_async8(myx + d, x + (size_t)d * x_tstride + xoff);
         cp_commit();
     }
-    u32 cnt = 0;
-    for (u32 t0 = 0; t0 < T; t0 += tc) {
+    load_tile(0, ps0);
+    u32 cnt = 0, k = 0;
+    for (u32 t0 = 0; t0 < T; t0 += tc, ++k) {
         const u32 tcc = T - t0 < tc ? T - t0 : tc;
+        const u64 *ps = ps0 + (k & 1) * tile_words;
+        // this thread's copies of tile k are older than the newest MAC_DEPTH - 1 commit
+        // groups once the previous (full) tile ran at least that many terms (one group per term)
+        if (k > 0 && tc >= MAC_DEPTH - 1)
+            cp_wait<MAC_DEPTH - 1>();
+        else
+            cp_wait<0>();
+        // every thread's copies of tile k are visible and every thread is done with tile
+        // k-1, whose buffer now receives tile k+1
         __syncthreads();
-        // the tile is copied with cp.async, every word in flight at once, then waited for
-        // (the older ciphertext copies of the pipeline complete with it)
-        for (u32 idx = tid; idx < O * tcc * NT; idx += blockDim.x) {
-            const u32 j = idx & (NT - 1), r = idx >> ntlog;
-            const u32 tt = r % tcc, o = r / tcc;
-            cp_async8(ps + (tt * NT + j) * OW + o,
-                      pt + (size_t)o * pt_ostride + (size_t)(t0 + tt) * pstride_t + (size_t)l * N + n0 + j);
-        }
-        cp_commit();
-        cp_wait<0>();
-        __syncthreads();
+        if (t0 + tc < T) load_tile(t0 + tc, ps0 + ((k + 1) & 1) * tile_words);
         for (u32 tt = 0; tt < tcc; ++tt) {
             const u32 t = t0 + tt;
             cp_wait<MAC_DEPTH - 1>();        // the copy of term t has landed
@@ -347,6 +362,15 @@ __global__ void __launch_bounds__(256) mac_small_kernel(u64 *out, const u64 *__r
         }
 }
 
+void mac_init(Ctx *c) {
+    (void)c;
+    for (const void *f : {(const void *)mac_kernel<1, 1>, (const void *)mac_kernel<2, 1>,
+                          (const void *)mac_kernel<4, 1>, (const void *)mac_kernel<6, 1>,
+                          (const void *)mac_kernel<8, 1>, (const void *)mac_kernel<12, 1>,
+                          (const void *)mac_kernel<6, 2>})
+        CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+}
+
 void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O, u32 T, u32 B,
          u32 lp, u32 lpq, u32 pbase, int accumulate, size_t pt_ostride) {
     if (!pt_ostride) pt_ostride = (size_t)T * lp * c->N;
@@ -382,12 +406,13 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
         while ((1u << ntlog) * bkc * os < 256) ++ntlog;
         if ((1u << ntlog) > c->N) throw HeError(HE_EINVAL, "mac: ring too small");
         const u32 NT = 1u << ntlog;
-        // shared memory: pipeline slots + plaintext tile within the 48 KB default
+        // shared memory: pipeline slots (16 KB) + two plaintext tiles of at most 40 KB each
+        // (28 KB with the split, which keeps three CTAs per SM)
         const u32 ow = os == 2 ? 12 : oc <= 1 ? 1 : oc <= 2 ? 2 : oc <= 4 ? 4 : oc <= 6 ? 6 : oc <= 8 ? 8 : 12;
-        u32 tc = (6144 - 256 * MAC_DEPTH) / (ow * NT);
+        u32 tc = (os == 2 ? 3584u : 5120u) / (ow * NT);
         if (tc < 1) tc = 1;
         if (tc > T) tc = T;
-        const size_t smem = ((size_t)ow * tc * NT + 256 * MAC_DEPTH) * 8;
+        const size_t smem = (2 * (size_t)ow * tc * NT + 256 * MAC_DEPTH) * 8;
         dim3 grid((BK + bkc - 1) / bkc, c->N / NT, lp);
         const u64 *ptc = pt + (size_t)o0 * pt_ostride;
         u64 *outc = out + (size_t)o0 * out_ostride;

@@ -258,8 +258,9 @@ def test_m3_approx_relu_small_ring_bit_exact(G):
     want = run_oracle_model(he, model, img, 28, 28, stride, 1, W.ENC_SEED)
     assert_same(ctx, out, he, want)
     assert np.abs(ctx.decrypt(out, 10)[0] - cnn.forward(img[0], model)).max() < 1e-3
-    # the layer calls: conv then approx_relu equals the first two layers of the model
-    conv_out = ctx.conv2d([gct], model[0]["w"], model[0]["b"])
+    # the layer calls: conv then approx_relu equals the first two layers of the model, which
+    # first drops the input to the 3 levels they consume (Drop-Level)
+    conv_out = ctx.conv2d([ctx.drop_level(gct, levels - 3)], model[0]["w"], model[0]["b"])
     relu_out = ctx.approx_relu(conv_out)
     ref = ctx.compile(model[:2], 28, 28, 1).infer(gct)
     got = np.stack([ctx.export(r) for r in relu_out])
