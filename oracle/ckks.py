@@ -193,6 +193,33 @@ def galois_elt(r: int, logn: int) -> int:
     return pow(5, r % m, 2 << logn)
 
 
+def naf_terms(r: int, slots: int):
+    """The rotation r (taken mod the slot count, in (-slots/2, slots/2]) as the signed
+    powers of two of its non-adjacent form (Reitwiesner 1960), lowest first: every
+    nonzero digit d_i in {-1, 1}, no two adjacent, r = sum d_i 2^i."""
+    v = r % slots
+    if v > slots // 2:
+        v -= slots
+    out, i = [], 0
+    while v != 0:
+        if v % 2:
+            d = 2 - v % 4          # v = 1 (mod 4) -> +1, v = 3 (mod 4) -> -1
+            v -= d
+            out.append(d * (1 << i))
+        v //= 2
+        i += 1
+    return out
+
+
+def pow2_steps(slots: int):
+    """The rotation steps of a power-of-two key set: +-2^k for 2^k < slots."""
+    k, out = 1, []
+    while k < slots:
+        out += [k, -k]
+        k *= 2
+    return out
+
+
 # ------------------------------------------------------------ the scheme
 @dataclass
 class Ct:
@@ -514,6 +541,22 @@ class Ckks:
         c1 = self.automorph_eval(ct.d[1], g)
         k0, k1 = self.keyswitch(c1, self.keys.gk[g])
         return Ct(np.stack([self.add(c0, k0, q), k1]), ct.scale)
+
+    def rotate_naf(self, ct: Ct, r: int, cache=None) -> Ct:
+        """Rot(ct, r) with power-of-two keys only: the rotations of naf_terms(r) applied
+        one after another, lowest first.  cache maps a partial sum of those terms to its
+        ciphertext, so the rotations of one input share their common prefixes (the
+        prefix of a non-adjacent form is the non-adjacent form of the partial sum)."""
+        cur, acc = ct, 0
+        for t in naf_terms(r, self.n // 2):
+            acc += t
+            if cache is not None and acc in cache:
+                cur = cache[acc]
+                continue
+            cur = self.rotate(cur, t)
+            if cache is not None:
+                cache[acc] = cur
+        return cur if acc else ct.copy()
 
     def rotate_hoisted(self, ct: Ct, steps) -> dict:
         """Several rotations of one ciphertext sharing one ModUp of c1."""

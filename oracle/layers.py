@@ -466,31 +466,75 @@ def plan(layers, W_img: int, H_img: int, dims: int = 2):
 
 # --------------------------------------------------------------- CKKS backend
 class HeBackend:
-    """The CKKS oracle as a layer backend; counts the operations it performs."""
+    """The CKKS oracle as a layer backend; counts the operations it performs.
 
-    def __init__(self, he):
+    naf=True: the context holds power-of-two Galois keys only (the key set SEAL
+    generates by default).  Every rotation is then a chain of power-of-two rotations
+    (``Ckks.rotate_naf``), and a linear combination of rotations is evaluated as
+    rotate-then-multiply: the rotated ciphertexts of one input (chains sharing their
+    prefixes), the products with the plaintexts over Q_l (Mul (P)) summed, then the
+    rescale (reading C7)."""
+
+    def __init__(self, he, naf: bool = False):
         self.he = he
+        self.naf = naf
         self.count = {"rot": 0, "pmul": 0, "rescale": 0, "square": 0}
+
+    def _rots(self, x, steps):
+        cache = {}
+        return [self.he.rotate_naf(x, s, cache) for s in steps]
 
     def rot(self, x, r):
         self.count["rot"] += 1
-        return self.he.rotate(x, r)
+        return self.he.rotate_naf(x, r) if self.naf else self.he.rotate(x, r)
 
     def rot_many(self, x, steps):
         self.count["rot"] += len({s for s in steps if s % (self.he.n // 2)})
+        if self.naf:
+            return dict(zip(steps, self._rots(x, steps)))
         return self.he.rotate_hoisted(x, steps)
 
     def lincomb_diag(self, xs, steps):
         m = self.he.n // 2
         self.count["rot"] += len([s for s in steps if s % m])
+        if self.naf:
+            ys = [self.he.rotate_naf(x, s) for x, s in zip(xs, steps)]
+            acc = ys[0]
+            for y in ys[1:]:
+                acc = self.he.ct_add(acc, y)
+            return acc
         return self.he.lincomb_diag(xs, steps)
+
+    def _naf_lincomb(self, xs, steps, weights):
+        rots = [self._rots(x, steps) for x in xs]
+        if weights is None:
+            outs = []
+            for r in rots:
+                acc = r[0]
+                for y in r[1:]:
+                    acc = self.he.ct_add(acc, y)
+                outs.append(acc)
+            return outs
+        lp = xs[0].lp
+        outs = []
+        for wo in weights:
+            acc = None
+            for i, wi in enumerate(wo):
+                for s, v in enumerate(wi):
+                    t = self.he.ct_mul_plain(rots[i][s], self.he.encode(v, self.he.scale, lp), self.he.scale)
+                    acc = t if acc is None else self.he.ct_add(acc, t)
+            outs.append(acc)
+        return outs
 
     def lincomb(self, xs, steps, weights):
         m = self.he.n // 2
         self.count["rot"] += len(xs) * len({s % m for s in steps if s % m})
+        if weights is not None:
+            self.count["pmul"] += sum(len(wi) for wo in weights for wi in wo)
+        if self.naf:
+            return self._naf_lincomb(xs, steps, weights)
         if weights is None:
             return self.he.lincomb(xs, steps, None)
-        self.count["pmul"] += sum(len(wi) for wo in weights for wi in wo)
         lp = xs[0].lp
         enc = [[[self.he.encode_ext(v, self.he.scale, lp) for v in wi] for wi in wo] for wo in weights]
         return self.he.lincomb(xs, steps, enc, self.he.scale)
@@ -500,6 +544,8 @@ class HeBackend:
         self.count["rot"] += len(xs) * len({s % m for s in steps if s % m})
         self.count["pmul"] += sum(len(wi) for wo in weights for wi in wo)
         self.count["rescale"] += len(weights)
+        if self.naf:
+            return [self.he.rescale(y) for y in self._naf_lincomb(xs, steps, weights)]
         lp = xs[0].lp
         enc = [[[self.he.encode_ext(v, self.he.scale, lp) for v in wi] for wi in wo] for wo in weights]
         return self.he.lincomb(xs, steps, enc, self.he.scale, rescale=True)

@@ -147,3 +147,26 @@ def test_three_channel_input_logits():
     lay = layers.input_layout(32, 32, pl["stride"], 1, he.n // 2, 2, channels=3)
     ys, _ = layers.run_model(layers.HeBackend(he), he.encrypt(x, W.ENC_SEED), model, lay)
     assert np.abs(he.decrypt(ys[0])[:10] - cnn.forward(img[0], model)).max() < 1e-3
+
+
+def test_power_of_two_keys_model_logits():
+    """The 1-D M7 with power-of-two Galois keys only (every rotation a chain of its
+    non-adjacent form, linear combinations as rotate-then-multiply): logits against
+    the FP64 CNN, with far fewer keys than the per-step set."""
+    model, Wi, Hi = W.paper_model("M7")
+    pl = layers.plan(model, Wi, Hi, 1)
+    P = dict(logn=11, data_bits=[60] + [40] * pl["levels"], special_bits=[60, 60, 60], dnum=3, log2_scale=40)
+    he = ckks.Ckks(seed=W.KEY_SEED, **P)
+    keys = ckks.pow2_steps(he.n // 2)
+    assert len(set(keys)) < len(pl["steps"])
+    he.keygen(keys)
+    sig = W.signals(2, Wi)[:, 0]
+    x = np.zeros(he.n // 2)
+    for b in range(2):
+        x[b * pl["stride"]: b * pl["stride"] + Wi] = sig[b]
+    lay = layers.input_layout(Wi, Hi, pl["stride"], 2, he.n // 2, 1)
+    ys, _ = layers.run_model(layers.HeBackend(he, naf=True), he.encrypt(x, W.ENC_SEED), model, lay)
+    dec = he.decrypt(ys[0])
+    for b in range(2):
+        ref = cnn.forward(sig[b], model, dims=1)
+        assert np.abs(dec[b * pl["stride"]: b * pl["stride"] + 5] - ref).max() < 1e-3

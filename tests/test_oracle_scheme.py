@@ -157,3 +157,50 @@ def test_lincomb_with_rescale_matches_lincomb_then_rescale(which, request):
     want = sum(np.roll(x, -s) * w for s, w in zip(steps, ws))
     assert np.abs(he.decrypt(fused)[:M] - want).max() < 1e-5
     assert np.abs(he.decrypt(fused)[:M] - he.decrypt(plain)[:M]).max() < 1e-5
+
+
+def test_naf_terms_are_the_minimal_signed_binary_form():
+    """naf_terms: the terms sum to r mod the slots, are signed powers of two at
+    strictly increasing, non-adjacent positions, and their count equals the minimal
+    number of signed powers of two summing to r (brute force over small r)."""
+    M = 64
+    # minimal weight of r as a sum of +-2^k (k < 8), by breadth-first search over sums
+    best, frontier = {0: 0}, [0]
+    terms = [s * (1 << k) for k in range(8) for s in (1, -1)]
+    for w in range(1, 6):
+        nxt = []
+        for v in frontier:
+            for t in terms:
+                u = v + t
+                if abs(u) <= 256 and u not in best:
+                    best[u] = w
+                    nxt.append(u)
+        frontier = nxt
+    for r in range(-2 * M, 2 * M):
+        t = ckks.naf_terms(r, M)
+        assert sum(t) % M == r % M
+        v = sum(t)
+        assert -M // 2 < v <= M // 2
+        pos = [abs(x).bit_length() - 1 for x in t]
+        assert all(abs(x) == 1 << p for x, p in zip(t, pos))
+        assert all(b - a >= 2 for a, b in zip(pos, pos[1:]))
+        assert len(t) == best[v], (r, t)
+    assert ckks.naf_terms(0, M) == [] and ckks.naf_terms(M, M) == []
+    assert sorted(set(ckks.pow2_steps(M))) == sorted({s * (1 << k) for k in range(6) for s in (1, -1)})
+
+
+def test_rotation_with_power_of_two_keys_only():
+    """With the power-of-two key set alone, every rotation (composed from its
+    non-adjacent form) decrypts to the rolled slots; shared prefixes are reused."""
+    h = ckks.Ckks(logn=10, data_bits=[60, 40, 40], special_bits=[60], dnum=3, log2_scale=40, seed=11)
+    M = h.n // 2
+    h.keygen(rot_steps=ckks.pow2_steps(M))
+    z = np.random.default_rng(5).uniform(-1, 1, M)
+    ct = h.encrypt(z, 9000)
+    cache = {}
+    for r in [1, 3, 7, 100, -45, 255, 511, -511, 512, 1000]:
+        y = h.rotate_naf(ct, r, cache)
+        assert np.abs(h.decrypt(y) - np.roll(z, -r)).max() < 1e-6, r
+    # the chain for 7 = 8 - 1 reuses the cached rotation by -1 of the chain for 3 = 4 - 1
+    assert -1 in cache and 3 in cache and 7 in cache
+    assert np.array_equal(h.rotate_naf(ct, 0).d, ct.d)
