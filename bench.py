@@ -97,6 +97,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-op-per-launch comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--samples", type=int, default=N_SAMPLES)
+    ap.add_argument("--keys", default="step", choices=["step", "pow2"],
+                    help="Galois keys: one per rotation step (default) or the power-of-two set")
     ap.add_argument("--ncu-step", action="store_true",
                     help="after set-up and warm-up run ONE eager step between cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off) and exit")
@@ -171,13 +173,16 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def lenet_setup(G, torch, device, stream, n_samples):
+def lenet_setup(G, torch, device, stream, n_samples, keys="step"):
     P = W.PARAMS["lenet1"]
     model = W.lenet1()
     stride, levels, steps = G.plan(model, 28, 28)
     ctx = G.Context(seed=W.KEY_SEED, device=device, stream=stream.cuda_stream, **P)
     ctx.autotune(TUNE_CACHE)
-    ctx.keygen(steps)
+    if keys == "pow2":
+        ctx.keygen_pow2()   # the power-of-two key set: rotations as non-adjacent-form chains
+    else:
+        ctx.keygen(steps)
     m = ctx.compile(model, 28, 28, SPC)
     imgs = W.images(n_samples)
     return ctx, m, stride, model, imgs
@@ -380,7 +385,7 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl")
 
     stream = torch.cuda.Stream()
-    ctx, model, stride, layers, imgs = lenet_setup(G, torch, local, stream, args.samples)
+    ctx, model, stride, layers, imgs = lenet_setup(G, torch, local, stream, args.samples, args.keys)
     n_ct = -(-args.samples // SPC)
     x_dev = torch.from_numpy(imgs).to(f"cuda:{local}")
     x_host = torch.from_numpy(imgs).pin_memory()
@@ -540,6 +545,8 @@ def run_ours(args, rank, world, local):
         "data": "synthetic U[0,1] 28x28 images, N(0,0.1^2) weights (MNIST / trained weights absent)",
         "config": {"workload": "batched LeNet-1-shaped, 64 ciphertexts x 10 samples (last 3), 633 samples",
                    "ckks": "N=16384, [60,40x7|60], Delta=2^40, dnum=8", "samples_per_gpu": args.samples,
+                   "galois_keys": ("power of two (+-2^k), rotations as non-adjacent-form chains"
+                                   if args.keys == "pow2" else "one per rotation step of the model"),
                    "l2": "working set > L2 (keys + masks + ciphertexts, several GB)",
                    "parallelism": f"replicas x{world}", "autotuned": ctx.tuning()},
         "e2e": {"value": round(total_samples / (ms_e2e / 1e3), 3), "unit": UNIT,

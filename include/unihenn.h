@@ -82,6 +82,16 @@ he_status he_context_primes(const he_ctx *ctx, uint64_t *out, size_t n);
  * Errors: HE_EINVAL, HE_ENOMEM, HE_ECUDA. */
 he_status he_keygen(he_ctx *ctx, const int32_t *rot_steps, size_t n_steps);
 
+/* he_keygen with the power-of-two Galois key set, the key set the paper's SEAL
+ * setup uses: keys for the steps +-2^k (2^k < N/2) only, 2*log2(N/2) keys in
+ * place of one per distinct step.  From then on every rotation is the chain of
+ * rotations of its step's non-adjacent form (Reitwiesner), lowest power first,
+ * chains of one input sharing their common prefixes, and each linear combination
+ * of rotations is evaluated as rotate-then-multiply over Q_l followed by the
+ * rescale (more key switches, far less key memory).  he_keygen returns the
+ * context to one key per step.  Errors: HE_ENOMEM, HE_ECUDA. */
+he_status he_keygen_pow2(he_ctx *ctx);
+
 /* Flatten and encrypt (paper Sec. III-A/B): x is [n_samples][H][W] doubles,
  * host memory (x_on_device = 0) or device memory (1).  Sample k goes to
  * ciphertext k / samples_per_ct at slot offset (k % samples_per_ct)*stride,

@@ -240,6 +240,10 @@ class Context:
         arr = (ctypes.c_int32 * max(1, len(steps)))(*steps)
         check(load().he_keygen(self.h, arr, len(steps)))
 
+    def keygen_pow2(self):
+        """he_keygen_pow2: power-of-two Galois keys only; rotations by non-adjacent-form chains."""
+        check(load().he_keygen_pow2(self.h))
+
     def sync(self):
         check(load().he_sync(self.h))
 

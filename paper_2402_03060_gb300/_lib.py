@@ -61,6 +61,7 @@ SIGNATURES = {
     "he_context_destroy": (None, [_vp]),
     "he_context_primes": (_int, [_vp, ctypes.POINTER(_u64), _sz]),
     "he_keygen": (_int, [_vp, ctypes.POINTER(_i32), _sz]),
+    "he_keygen_pow2": (_int, [_vp]),
     "he_encrypt": (_int, [_vp, _vp, _int, _u32, _u32, _u32, _u32, _u32, _u64, _pp]),
     "he_encrypt_channels": (_int, [_vp, _vp, _int, _u32, _u32, _u32, _u32, _u32, _u32, _u64, _pp]),
     "he_decrypt": (_int, [_vp, _vp, _vp, _int, _sz]),

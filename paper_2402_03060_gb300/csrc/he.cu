@@ -624,9 +624,19 @@ static size_t acc_chunk(Ctx *c, u32 B, u32 lp, size_t nsteps) {
     return std::min(lim, nsteps);
 }
 
+Cts ct_rotate_naf(Ctx *c, const Cts &a, int step, std::map<int64_t, Cts> *cache);
+
 void ct_rotate_hoisted_into(Ctx *c, const Cts &a, const std::vector<int> &steps, u64 *out) {
     const u32 N = c->N, lp = a.lp, B = a.B, E = lp + c->K;
     const size_t ctw = (size_t)B * 2 * lp * N;
+    if (c->naf) {   // power-of-two keys: chains sharing their prefixes
+        std::map<int64_t, Cts> cache;
+        for (size_t i = 0; i < steps.size(); ++i) {
+            Cts r = ct_rotate_naf(c, a, steps[i], &cache);
+            CUDA_TRY(cudaMemcpyAsync(out + i * ctw, r.data(), ctw * 8, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        return;
+    }
     std::vector<int> ks;      // positions that need a key switch
     for (size_t i = 0; i < steps.size(); ++i) {
         u32 g = c->galois_elt(steps[i]);
@@ -670,7 +680,52 @@ std::vector<Cts> ct_rotate_hoisted(Ctx *c, const Cts &a, const std::vector<int> 
     return out;
 }
 
+// The rotation step r (taken mod N/2, in (-N/4, N/4]) as the signed powers of two of its
+// non-adjacent form (Reitwiesner 1960), lowest first.
+std::vector<int> naf_terms(int64_t r, u32 slots) {
+    int64_t v = ((r % (int64_t)slots) + slots) % slots;
+    if (v > (int64_t)slots / 2) v -= slots;
+    std::vector<int> out;
+    for (int i = 0; v != 0; ++i) {
+        if (v & 1) {
+            const int64_t d = 2 - (((v % 4) + 4) % 4);   // v = 1 (mod 4) -> +1, 3 (mod 4) -> -1
+            v -= d;
+            out.push_back((int)(d * ((int64_t)1 << i)));
+        }
+        v /= 2;   // exact: v is even here
+    }
+    return out;
+}
+
+static Cts ct_rotate_direct(Ctx *c, const Cts &a, int step);
+
+// Rot(a, r) with power-of-two keys: the rotations of naf_terms(r) one after another. cache
+// (partial sum -> ciphertext) lets the rotations of one input share their common prefixes.
+Cts ct_rotate_naf(Ctx *c, const Cts &a, int step, std::map<int64_t, Cts> *cache) {
+    const std::vector<int> terms = naf_terms(step, c->N / 2);
+    if (terms.empty()) return ct_rotate_direct(c, a, 0);   // a copy
+    Cts cur = a;
+    int64_t acc = 0;
+    for (int t : terms) {
+        acc += t;
+        if (cache) {
+            auto it = cache->find(acc);
+            if (it != cache->end()) {
+                cur = it->second;
+                continue;
+            }
+        }
+        cur = ct_rotate_direct(c, cur, t);
+        if (cache) cache->emplace(acc, cur);
+    }
+    return cur;
+}
+
 Cts ct_rotate(Ctx *c, const Cts &a, int step) {
+    return c->naf ? ct_rotate_naf(c, a, step, nullptr) : ct_rotate_direct(c, a, step);
+}
+
+static Cts ct_rotate_direct(Ctx *c, const Cts &a, int step) {
     const u32 N = c->N, lp = a.lp, B = a.B, E = lp + c->K;
     u32 g = c->galois_elt(step);
     Cts o = cts_alloc(c, B, lp, a.scale, a.lay);
@@ -717,6 +772,17 @@ Cts ct_square(Ctx *c, const Cts &a) {
 Cts ct_lincomb_diag(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps) {
     const u32 N = c->N, lp = X.lp, E = lp + c->K, Bt = CH * B;
     if (X.B != Bt || steps.size() != CH) throw HeError(HE_EINVAL, "lincomb_diag: shape mismatch");
+    if (c->naf) {   // power-of-two keys: each channel rotated by its own chain, then summed
+        const size_t bw = (size_t)B * cts_ct_words(c, lp);
+        Cts R = cts_alloc(c, Bt, lp, X.scale, X.lay);
+        for (u32 i = 0; i < CH; ++i) {
+            Cts r = ct_rotate_naf(c, cts_view(X, i * bw, B), steps[i], nullptr);
+            CUDA_TRY(cudaMemcpyAsync(R.data() + i * bw, r.data(), bw * 8, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        Cts out = cts_alloc(c, B, lp, X.scale, X.lay);
+        sum_stack(c, out.data(), R.data(), bw, CH, B * 2 * lp, lp, lp, c->L1, 0);
+        return out;
+    }
     const u32 beta = ks_digits(c, lp);
     bool any_ks = false;
     for (int s : steps)
@@ -757,10 +823,36 @@ Cts ct_lincomb_diag(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> 
 // Q_l u P with t = s*CH + i, or nullptr for the plain sums Y_i = sum_s Rot(X_i, steps[s])
 // (one output per channel).  The weighted key-switch accumulators, with P*sigma(c0)
 // folded in, are summed over Q_l u P and ModDown runs once per output ciphertext.
+// Power-of-two keys: rotate-then-multiply.  The whole batch X is rotated by every step
+// (chains sharing their prefixes), the plaintexts pts [O][S*CH][lp][N] (over Q_l) multiply
+// the rotations and the products are summed (or the rotations are summed); then the
+// usual rescale.
+static Cts ct_lincomb_naf(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps, const u64 *pts,
+                          u32 O, double pt_scale, bool rescale) {
+    const u32 N = c->N, lp = X.lp, Bt = CH * B, S = (u32)steps.size();
+    const size_t bw = (size_t)B * cts_ct_words(c, lp);   // one block of B ciphertexts
+    Cts R = cts_alloc(c, S * Bt, lp, X.scale, X.lay);    // [s][channel][b]
+    std::map<int64_t, Cts> cache;
+    for (u32 s = 0; s < S; ++s) {
+        Cts r = ct_rotate_naf(c, X, steps[s], &cache);
+        CUDA_TRY(cudaMemcpyAsync(R.data() + (size_t)s * CH * bw, r.data(), (size_t)CH * bw * 8,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+    }
+    cache.clear();
+    const u32 nout = pts ? O : CH;
+    Cts Z = cts_alloc(c, nout * B, lp, X.scale * (pts ? pt_scale : 1.0), X.lay);
+    if (pts)
+        mac(c, Z.data(), bw, R.data(), bw, pts, O, S * CH, B, lp, lp, c->L1, 0, (size_t)S * CH * lp * N);
+    else
+        sum_stack(c, Z.data(), R.data(), (size_t)CH * bw, S, CH * B * 2 * lp, lp, lp, c->L1, 0);
+    return rescale ? ct_rescale(c, Z) : Z;
+}
+
 Cts ct_lincomb(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps, const u64 *pts, u32 O,
                double pt_scale, bool rescale) {
     const u32 N = c->N, lp = X.lp, E = lp + c->K, Bt = CH * B, S = (u32)steps.size();
     if (X.B != Bt) throw HeError(HE_EINVAL, "lincomb: batch mismatch");
+    if (c->naf) return ct_lincomb_naf(c, X, CH, B, steps, pts, O, pt_scale, rescale);
     bool any_ks = false;
     for (int s : steps)
         if (c->galois_elt(s) != 1) {

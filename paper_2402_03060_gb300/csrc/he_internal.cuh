@@ -259,6 +259,7 @@ struct Ctx : std::enable_shared_from_this<Ctx> {
     Pool *active = nullptr;        // pool that new buffers come from (a model's private pool during graph capture)
     // keys
     bool have_keys = false;
+    bool naf = false;              // power-of-two Galois keys only: rotations by non-adjacent-form chains
     DBuf sk;                       // [L1+K][N] eval
     DBuf pk;                       // [2][L1][N]
     DBuf rlk;                      // [dnum][2][L1+K][N]

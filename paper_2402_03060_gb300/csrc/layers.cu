@@ -99,7 +99,7 @@ static Feat layer_conv(Ctx *c, const Feat &in, const LayerSpec &sp, u32 kh, u32 
     Cts out;
     if (!incremental) {
         // one hoisted linear combination per output channel, ModDown and rescale as one division each
-        const u64 *pts = weight_pts(c->K);
+        const u64 *pts = weight_pts(ks_ext(c));
         out = ct_lincomb(c, in.x, packed ? 1 : ci, B, steps, pts, co, c->scale, true);
     } else {
         // rotated inputs R[off][ch*B + b]  (T index = off*ci + ch)
@@ -262,7 +262,7 @@ static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string
         Layout flat = L;
         flat.n_samples = 1;
         flat.stride = M;
-        const u64 *pts = get_pts(c, pc, name, tmp, flat, off, apos, val, c->scale, x.lp, c->K);
+        const u64 *pts = get_pts(c, pc, name, tmp, flat, off, apos, val, c->scale, x.lp, ks_ext(c));
         return ct_lincomb(c, x, 1, x.B, steps, pts, 1, c->scale, true);
     };
     if (L.prev == PREV_POOL) {
@@ -396,7 +396,7 @@ static Feat layer_fc(Ctx *c, const Feat &in, const LayerSpec &sp, PtCache *pc, c
                 off.push_back((u32)pos.size());
             }
         }
-        pts = get_pts(c, pc, key + ":wx", tmp, L, off, pos, val, c->scale, lp, c->K);
+        pts = get_pts(c, pc, key + ":wx", tmp, L, off, pos, val, c->scale, lp, ks_ext(c));
     }
     (void)T;
     (void)ctw;
@@ -752,6 +752,21 @@ he_status he_keygen(he_ctx *h, const int32_t *steps, size_t n) {
         CtxLock lk_(c);
         if (n && !steps) throw HeError(HE_EINVAL, "null steps");
         keygen(c, std::vector<int>(steps, steps + n));
+        c->naf = false;
+    });
+}
+
+he_status he_keygen_pow2(he_ctx *h) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        CtxLock lk_(c);
+        std::vector<int> steps;
+        for (u32 k = 1; k < c->N / 2; k *= 2) {
+            steps.push_back((int)k);
+            steps.push_back(-(int)k);
+        }
+        keygen(c, steps);
+        c->naf = true;
     });
 }
 
@@ -1071,7 +1086,13 @@ he_status he_model_compile(he_ctx *h, const he_layer *layers, size_t n, uint32_t
         m->plan = plan_layers(m->layers, Wi, Hi);
         if ((u64)m->plan.stride * spc > c->N / 2) throw HeError(HE_ESLOTS, "samples do not fit in the slots");
         if (m->plan.levels + 1 > c->L1) throw HeError(HE_ELEVEL, "the modulus chain is too short for this model");
-        for (int s : m->plan.steps) require_key(c, s);
+        for (int s : m->plan.steps) {
+            if (!c->naf) {
+                require_key(c, s);
+                continue;
+            }
+            for (int t : naf_terms(s, c->N / 2)) require_key(c, t);
+        }
         *out = m.release();
     });
 }

@@ -341,6 +341,45 @@ def test_m5_full_logits(G):
     assert np.abs(ctx.decrypt(out, 10)[0] - cnn.forward(imgs[0], model)).max() < 1e-3
 
 
+@pytest.mark.parametrize("name", ["M7", "lenet1"])
+def test_power_of_two_keys_bit_exact(G, name):
+    """Power-of-two Galois keys (the paper's SEAL key set): every rotation a chain of
+    its non-adjacent form, every linear combination rotate-then-multiply.  M7 (two
+    samples) and LeNet-1 (one sample, incl. the rotation calls) at small rings,
+    bit-exact against the oracle in the same mode; logits against the FP64 CNN."""
+    if name == "M7":
+        model, Wi, Hi = W.paper_model("M7")
+        dims, ns = 1, 2
+    else:
+        model, Wi, Hi = W.lenet1(), 28, 28
+        dims, ns = 2, 1
+    stride, levels, steps = G.plan(model, Wi, Hi)
+    logn = max(11, int(np.ceil(np.log2(stride * ns))) + 1)
+    P = dict(logn=logn, data_bits=[60] + [40] * levels, special_bits=[60, 60, 60], dnum=3, log2_scale=40)
+    ctx = G.Context(seed=W.KEY_SEED, **P)
+    ctx.keygen_pow2()
+    he = ckks.Ckks(seed=W.KEY_SEED, **P)
+    he.keygen(ckks.pow2_steps(he.n // 2))
+    x = W.images(ns, Hi, Wi) if dims == 2 else W.signals(ns, Wi)[:, 0]
+    gct = ctx.encrypt(x, ns, stride, W.ENC_SEED)
+    out = ctx.compile(model, Wi, Hi, ns).infer(gct, use_graph=True)
+    lay = olayers.input_layout(Wi, Hi, stride, ns, he.n // 2, dims)
+    oct_ = he.encrypt(slots_of(x, stride, he.n // 2), W.ENC_SEED)
+    want, _ = olayers.run_model(olayers.HeBackend(he, naf=True), oct_, model, lay)
+    assert_same(ctx, out, he, want[0])
+    n_out = model[-1]["w"].shape[0]
+    logits = ctx.decrypt(out, n_out)
+    for b in range(ns):
+        assert np.abs(logits[b] - cnn.forward(x[b], model, dims=dims)).max() < 1e-3
+    if name == "lenet1":
+        for r in (1, 27, -100, 511):
+            assert_same(ctx, ctx.rotate(gct, r), he, he.rotate_naf(oct_, r))
+        hs = ctx.rotate_hoisted(gct, [3, 7, 0])
+        cache = {}
+        for g, r in zip(hs, [3, 7, 0]):
+            assert_same(ctx, g, he, he.rotate_naf(oct_, r, cache))
+
+
 def test_pack_and_drop_level_bit_exact(G):
     """Batch combining (Sec. III-B) of three ciphertexts carrying 1, 2 and 1 samples,
     and Drop-Level (Sec. IV-A): the chain has two more levels than M7 consumes, so
