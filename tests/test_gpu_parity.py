@@ -525,16 +525,46 @@ def test_degenerate_cases(G, pair_small):
 
 @pytest.mark.slow
 def test_lenet1_full_size_bit_exact(G):
-    """LeNet-1 at N=16384 with 10 samples in one ciphertext, against the oracle."""
+    """The benchmark's launch configuration: LeNet-1 at N=16384, 633 samples in 64
+    ciphertexts (the last with 3), autotuned launch shapes, one graph launch.  The first
+    and the ragged last ciphertext are compared with the oracle run on each alone."""
     P = W.PARAMS["lenet1"]
     model = W.lenet1()
     stride, levels, steps = G.plan(model, 28, 28)
     ctx, he = make_pair(G, P, steps)
-    imgs = W.images(10)
+    ctx.autotune()
+    imgs = W.images(633)
     m = ctx.compile(model, 28, 28, 10)
     out = m.infer(ctx.encrypt(imgs, 10, stride, W.ENC_SEED), use_graph=True)
-    want = run_oracle_model(he, model, imgs, 28, 28, stride, 10, W.ENC_SEED)
-    assert_same(ctx, out, he, want)
+    assert out.batch == 64
+    for b in (0, 63):
+        want = run_oracle_model(he, model, imgs[10 * b: 10 * b + 10], 28, 28, stride, 10, W.ENC_SEED + b)
+        assert_same(ctx, out, he, want, b)
     logits = ctx.decrypt(out, 10)
-    for k in range(10):
+    for k in list(range(10)) + [630, 631, 632]:
         assert np.abs(logits[k] - cnn.forward(imgs[k], model)).max() < 1e-3
+
+
+def test_maximum_sizes_bit_exact(G):
+    """The largest chain the library takes (32 data primes, 4 special primes) with the
+    widest digits (alpha = 8 limbs, dnum = 4) and with the most digits (dnum = 16):
+    encrypt, hoisted and single rotations, square, rescale, bit-exact against the oracle."""
+    for dnum in (4, 16):
+        P = dict(logn=11, data_bits=[30] * 32, special_bits=[60] * 4, dnum=dnum, log2_scale=25)
+        steps = [1, -7, 300]
+        ctx, he = make_pair(G, P, steps)
+        M = he.n // 2
+        x = np.random.default_rng(dnum).uniform(-1, 1, (1, M))
+        g = ctx.encrypt(x, 1, M, 11)
+        o = he.encrypt(x[0], 11)
+        assert_same(ctx, g, he, o)
+        for r in steps:
+            assert_same(ctx, ctx.rotate(g, r), he, he.rotate(o, r))
+        # the chain is meaningful too: a digit of 8 x 30 bits against P of 240 bits
+        assert np.abs(ctx.decrypt(ctx.rotate(g, 300), M)[0] - np.roll(x[0], -300)).max() < 0.05
+        hs = ctx.rotate_hoisted(g, steps)
+        ho = he.rotate_hoisted(o, steps)
+        for gr, r in zip(hs, steps):
+            assert_same(ctx, gr, he, ho[r])
+        assert_same(ctx, ctx.square([g])[0], he, he.square(o))
+        assert_same(ctx, ctx.rescale(g), he, he.rescale(o))
