@@ -107,6 +107,10 @@ def parse():
                          "the continuous-batching loop; prints request-latency percentiles")
     ap.add_argument("--requests", type=int, default=600, help="requests of the --serve trace")
     ap.add_argument("--rate", type=float, default=200.0, help="arrivals per second of the --serve trace")
+    ap.add_argument("--serve-max-batch", type=int, default=8, help="ciphertexts per batch of one model")
+    ap.add_argument("--serve-inflight", type=int, default=1, help="batches of one model in flight")
+    ap.add_argument("--serve-padded", action="store_true",
+                    help="pad batches to a power of two (default: one graph per exact batch size)")
     ap.add_argument("--ncu-conv", action="store_true",
                     help="small case for full ncu captures: ONE hoisted conv2d layer call (4 -> 12 channels, 5x5, "
                          "8 ciphertexts per channel, N = 16384, top level) between cudaProfilerStart/Stop, then exit")
@@ -232,7 +236,8 @@ def run_serve(args, local):
     __graft_entry__.build()
     import paper_2402_03060_gb300 as G
     t_setup = time.perf_counter()
-    srv = G.Server(max_batch=8, max_wait_us=2000)
+    srv = G.Server(max_batch=args.serve_max_batch, max_wait_us=2000, max_inflight=args.serve_inflight,
+                   exact_batches=not args.serve_padded)
     ctxs, models, strides, layers = [], [], [], []
     for i, (name, fn, Wi, Hi, spc, nout) in enumerate(SERVE_MODELS):
         ly = fn()
@@ -350,7 +355,10 @@ def run_serve(args, local):
             "dtype": "u64 (RNS residues), f64 encode", "data": "synthetic",
             "config": {"workload": "serving mix, one sample per request",
                        "models": {m[0]: W.SERVE_PARAMS[m[0]] for m in SERVE_MODELS},
-                       "max_batch_cts": 8, "max_wait_us": 2000, "arrival_seed": W.ARRIVAL_SEED},
+                       "max_batch_cts": args.serve_max_batch, "max_wait_us": 2000,
+                       "max_inflight_per_model": args.serve_inflight,
+                       "batches": "padded to a power of two" if args.serve_padded else "exact sizes",
+                       "arrival_seed": W.ARRIVAL_SEED},
             "setup_s": round(t_setup, 1), "per_model": main["per_model"], "service_cost": service,
             "offered_load": round(offered, 3), "at_80pct_capacity": knee}
 

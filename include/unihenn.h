@@ -249,10 +249,11 @@ he_status he_tuning_set(he_ctx *ctx, const int32_t *values, size_t n);
  * service model: clients send ciphertexts encrypted under their public key,
  * the server evaluates the network with the evaluation keys and returns
  * encrypted results; paper Sec. III).  One host thread serves every added
- * model, each from a FIFO queue: while a model has fewer than two batches in
- * flight, the queued requests (in arrival order, up to max_batch
- * ciphertexts) are gathered into one batch padded to a power of two and run
- * on the model's stream; requests that arrive meanwhile join the next batch.
+ * model, each from a FIFO queue: while a model has fewer than max_inflight
+ * batches in flight, the queued requests (in arrival order, up to max_batch
+ * ciphertexts) are gathered into one batch (padded to a power of two unless
+ * exact_batches) and run on the model's stream; requests that arrive meanwhile
+ * join the next batch.
  * A request's result is bit-identical whether it ran alone or in a mix.
  * Thread safety: submit / wait / stats may be called from any thread; the
  * contexts of the added models stay usable from other threads (every entry
@@ -265,6 +266,11 @@ typedef struct {
     uint64_t mem_budget;    /* device bytes for the models (their contexts' pools: keys and cached masks,
                                and their graph pools) plus the ciphertexts of queued and running
                                requests; 0: unlimited */
+    uint32_t max_inflight;  /* batches of one model queued on its stream at once; 0: 2.  With 1, the
+                               next batch is formed when the running one completes (larger batches
+                               under load, one model's work never queued behind itself) */
+    uint32_t exact_batches; /* 0: a batch is padded to a power of two (log2(max_batch)+1 graphs per
+                               model); 1: one graph per batch size 1..max_batch, no padding */
 } he_server_opts;
 typedef struct {
     uint64_t requests;        /* finished requests */
@@ -278,7 +284,8 @@ typedef struct {
 /* Starts the loop's thread.  HE_EINVAL if max_batch is 0. */
 he_status he_server_create(const he_server_opts *opt, he_server **out);
 /* Adds a compiled model (borrowed: it must outlive the server).  Runs the model
- * once on zero ciphertexts for every batch shape (1, 2, 4, .. max_batch) at the
+ * once on zero ciphertexts for every batch shape (1, 2, 4, .. max_batch, or
+ * 1, 2, 3, .. max_batch with exact_batches) at the
  * context's top level, capturing their CUDA graphs, then admits it: HE_ENOMEM
  * if the budget cannot hold what the model and its context keep on the device.
  * The ids are 0, 1, 2, ... in order of addition. */

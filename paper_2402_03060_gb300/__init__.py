@@ -137,9 +137,10 @@ class Model:
 class Server:
     """he_server_*: continuous-batching request loop over compiled models."""
 
-    def __init__(self, max_batch: int = 8, max_wait_us: int = 0, mem_budget: int = 0):
+    def __init__(self, max_batch: int = 8, max_wait_us: int = 0, mem_budget: int = 0, max_inflight: int = 0,
+                 exact_batches: bool = False):
         self._models, self._req_ctx = [], {}
-        opt = _lib.he_server_opts(max_batch, max_wait_us, mem_budget)
+        opt = _lib.he_server_opts(max_batch, max_wait_us, mem_budget, max_inflight, int(exact_batches))
         h = ctypes.c_void_p()
         check(load().he_server_create(ctypes.byref(opt), ctypes.byref(h)))
         self.h = h
@@ -184,11 +185,12 @@ class Server:
             pass
 
 
-def simulate_server(max_batch, max_wait_us, base_us, per_ct_us, arrival_us, model_of, cts_of, mem_budget=0):
+def simulate_server(max_batch, max_wait_us, base_us, per_ct_us, arrival_us, model_of, cts_of, mem_budget=0,
+                    max_inflight=0, exact_batches=False):
     """he_server_simulate: the serving loop on simulated models (no GPU).
     Returns (batch id per request, latency ms per request)."""
     n = len(arrival_us)
-    opt = _lib.he_server_opts(max_batch, max_wait_us, mem_budget)
+    opt = _lib.he_server_opts(max_batch, max_wait_us, mem_budget, max_inflight, int(exact_batches))
     f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
     u32 = lambda a: np.ascontiguousarray(a, dtype=np.uint32)
     base, per, arr = f64(base_us), f64(per_ct_us), f64(arrival_us)

@@ -37,7 +37,8 @@ class he_kernel_stat(ctypes.Structure):
 
 
 class he_server_opts(ctypes.Structure):
-    _fields_ = [("max_batch", ctypes.c_uint32), ("max_wait_us", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64)]
+    _fields_ = [("max_batch", ctypes.c_uint32), ("max_wait_us", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
+                ("max_inflight", ctypes.c_uint32), ("exact_batches", ctypes.c_uint32)]
 
 
 class he_server_stats(ctypes.Structure):

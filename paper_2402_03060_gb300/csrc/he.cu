@@ -49,20 +49,29 @@ void note_launch(Ctx *c, const char *what, double bytes, double ops) {
 }
 
 // ------------------------------------------------------------------ pool
+static thread_local bool tl_capturing = false;
+void set_capturing(bool on) { tl_capturing = on; }
+
 void *Pool::get(size_t bytes) {
     bytes = (bytes + 4095) & ~(size_t)4095;
     if (bytes == 0) bytes = 4096;
     auto it = free_.find(bytes);
+    if (graph)
+        for (it = free_.lower_bound(bytes); it != free_.end() && it->second.empty(); ++it) {
+        }
     void *p = nullptr;
     if (it != free_.end() && !it->second.empty()) {
         p = it->second.back();
         it->second.pop_back();
+        bytes = it->first;   // the block's own size
         bytes_cached -= bytes;
     } else {
         cudaError_t e = cudaMalloc(&p, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            // give cached blocks back and retry once
+            // give cached blocks back and retry once -- not a graph pool's (captured graphs
+            // use them) and not during a capture (the release synchronises the device)
+            if (graph || tl_capturing) throw HeError(HE_ENOMEM, fmt("device allocation of %zu bytes failed", bytes));
             release_cached();
             e = cudaMalloc(&p, bytes);
             if (e != cudaSuccess) {

@@ -172,6 +172,8 @@ struct HeError : std::runtime_error {
 
 struct Ctx;
 void prof_begin(Ctx *c);                                        // start event of the next launch (profiling)
+// set while this thread captures a CUDA graph: no device-wide synchronisation then
+void set_capturing(bool on);
 // error check, launch counter, end event; bytes = algorithmic bytes, ops = algorithmic primitive
 // operations of the launch (NTT butterflies or 64x64->128 multiply-accumulates)
 void note_launch(Ctx *c, const char *what, double bytes = 0, double ops = 0);
@@ -183,6 +185,11 @@ struct Pool {
     std::map<size_t, std::vector<void *>> free_;
     std::map<void *, size_t> size_;
     size_t bytes_live = 0, bytes_cached = 0;
+    // a compiled model's graph pool: a request takes the smallest cached block of at least
+    // its size (not only an exact size), so the model's graphs, which never run
+    // concurrently, hold the largest batch shape's buffers once for every shape; and its
+    // cached blocks are never freed while the model lives (captured graphs refer to them)
+    bool graph = false;
     void *get(size_t bytes);
     void put(void *p);
     void release_cached();

@@ -602,8 +602,12 @@ Cts model_infer(he_model *m, const Cts &x_in, bool use_graph) {
     auto it = m->graphs.find(key);
     const size_t inw = (size_t)x.B * cts_ct_words(c, x.lp);
     if (it == m->graphs.end()) {
-        // eager run (fills the plaintext cache and sizes the private pool), then capture
-        run_layers(c, f, m->layers, &m->pc);
+        // the first time: an eager run fills the plaintext cache (the masks depend on the
+        // layout, not on the batch size); then a warm run in the private pool and the capture
+        if (!m->pc_filled) {
+            run_layers(c, f, m->layers, &m->pc);
+            m->pc_filled = true;
+        }
         CUDA_TRY(cudaStreamSynchronize(c->stream));
         ModelGraph g;
         c->active = &m->gpool;
@@ -619,16 +623,19 @@ Cts model_infer(he_model *m, const Cts &x_in, bool use_graph) {
             c->profiling = false;   // no event records inside the graph
             const u64 before = c->launches;
             CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+            set_capturing(true);
             Feat r;
             try {
                 r = run_layers(c, fi, m->layers, &m->pc);
             } catch (...) {
+                set_capturing(false);
                 cudaGraph_t tmpg = nullptr;
                 cudaStreamEndCapture(c->stream, &tmpg);
                 if (tmpg) cudaGraphDestroy(tmpg);
                 c->profiling = prof;
                 throw;
             }
+            set_capturing(false);
             c->profiling = prof;
             g.kernels = c->launches - before;
             c->launches = before;
@@ -1077,6 +1084,7 @@ he_status he_model_compile(he_ctx *h, const he_layer *layers, size_t n, uint32_t
         CtxLock lk_(c);
         if (!layers || !n || !out || !spc) throw HeError(HE_EINVAL, "bad arguments");
         std::unique_ptr<he_model> m(new he_model());
+        m->gpool.graph = true;   // the model's graphs run one at a time on its context's stream
         m->keep = c->shared_from_this();
         m->c = c;
         m->layers = copy_layers(layers, n, Hi);

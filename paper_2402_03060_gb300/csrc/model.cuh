@@ -34,6 +34,7 @@ struct he_model {
     u32 W_img = 0, H_img = 0, spc = 0;
     Plan plan;
     PtCache pc;
+    bool pc_filled = false;                // pc holds every plaintext of the model's layout
     Pool gpool;                            // private pool of the captured graphs
     std::map<std::string, ModelGraph> graphs;
     ~he_model() {

@@ -218,7 +218,7 @@ static void server_loop(he_server *s) {
         for (u32 k = 0; k < nm; ++k) {
             const u32 mi = (s->rr + k) % nm;
             Model &M = *s->models[mi];
-            if (M.q.empty() || M.inflight >= 2) continue;
+            if (M.q.empty() || M.inflight >= s->opt.max_inflight) continue;
             u32 total = 0;
             for (Request *r : M.q) {
                 if (total + r->B > s->opt.max_batch) break;
@@ -246,7 +246,7 @@ static void server_loop(he_server *s) {
                 got += r->B;
                 b->reqs.push_back(r);
             }
-            b->bucket = pow2_at_least(got);   // <= max_batch, a power of two
+            b->bucket = s->opt.exact_batches ? got : pow2_at_least(got);   // <= max_batch
             M.inflight++;
             s->inflight++;
             s->rr = mi + 1;
@@ -285,14 +285,21 @@ static void start_threads(he_server *s) {
     if (s->simulate) s->sim_thread = std::thread(sim_loop, s);
 }
 
+// max_batch rounded down to a power of two; max_inflight 0 -> 2
+static he_server_opts normalized(he_server_opts o) {
+    o.max_batch = pow2_at_most(o.max_batch);
+    if (!o.max_inflight) o.max_inflight = 2;
+    o.exact_batches = o.exact_batches ? 1 : 0;
+    return o;
+}
+
 extern "C" {
 
 he_status he_server_create(const he_server_opts *opt, he_server **out) {
     return srv_guard([&] {
         if (!opt || !out || opt->max_batch < 1) throw HeError(HE_EINVAL, "bad server options");
         he_server *s = new he_server();
-        s->opt = *opt;
-        s->opt.max_batch = pow2_at_most(opt->max_batch);
+        s->opt = normalized(*opt);
         start_threads(s);
         *out = s;
     });
@@ -316,7 +323,8 @@ he_status he_server_add_model(he_server *s, he_model *m, uint32_t *model_id) {
             L.stride = m->plan.stride;
             L.n_samples = m->spc;
             L.dims = m->H_img == 1 ? 1 : 2;
-            for (u32 b = 1; b <= s->opt.max_batch; b <<= 1) {
+            // largest shape first: the smaller shapes' captures reuse its buffers in the model's graph pool
+            for (u32 b = s->opt.max_batch; b >= 1; b = s->opt.exact_batches ? b - 1 : b >> 1) {
                 Cts x = cts_alloc(c, b, lp, c->scale, L);
                 CUDA_TRY(cudaMemsetAsync(x.data(), 0, (size_t)b * cts_ct_words(c, lp) * 8, c->stream));
                 Cts y = model_infer(m, x, true);
@@ -472,8 +480,7 @@ he_status he_server_simulate(const he_server_opts *opt, uint32_t n_models, const
             opt->max_batch < 1)
             throw HeError(HE_EINVAL, "bad arguments");
         he_server *s = new he_server();
-        s->opt = *opt;
-        s->opt.max_batch = pow2_at_most(opt->max_batch);
+        s->opt = normalized(*opt);
         s->simulate = true;
         for (u32 i = 0; i < n_models; ++i) {
             std::unique_ptr<Model> M(new Model());
