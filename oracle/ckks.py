@@ -660,6 +660,32 @@ class Ckks:
             z1 = self.add(z1, a1, basis)
         return Ct(np.stack([self.moddown(z0), self.moddown(z1)]), cts[0].scale)
 
+    def lincomb_chan(self, cts, steps, weights, pt_scale: float, rescale: bool = False) -> Ct:
+        """One output from inputs that each have their own rotation steps:
+
+            Y = sum_i sum_k w[i][k] (.) Rot(ct_i, steps[i][k])
+
+        Each input's rotations share one ModUp (hoisting); the weighted accumulator pairs
+        (see ``lincomb``) of every input and step are summed over Q_l u P and ModDown runs
+        once -- or, with rescale, the single division by q_top * P.  w[i][k] are plaintexts
+        over Q_l u P; the output scale is ct.scale * pt_scale (then / q_top)."""
+        lp = cts[0].lp
+        E = lp + self.K
+        basis, _ = self.ext_basis(lp)
+        z0 = np.zeros((E, self.n), dtype=np.uint64)
+        z1 = np.zeros_like(z0)
+        for ct, st, ws in zip(cts, steps, weights):
+            assert ct.lp == lp and ct.scale == cts[0].scale and len(st) == len(ws)
+            digs = self.modup(ct.d[1]) if any(galois_elt(r, self.logn) != 1 for r in st) else None
+            for r, w in zip(st, ws):
+                a0, a1 = self._lazy_acc(ct, r, digs)
+                lib().o_muladd(_p(z0), _p(_u(a0)), _p(_u(w)), E, self.n, _p(basis))
+                lib().o_muladd(_p(z1), _p(_u(a1)), _p(_u(w)), E, self.n, _p(basis))
+        if rescale:
+            return Ct(np.stack([self.moddown_rescale(z0), self.moddown_rescale(z1)]),
+                      cts[0].scale * pt_scale / float(self.q[lp - 1]))
+        return Ct(np.stack([self.moddown(z0), self.moddown(z1)]), cts[0].scale * pt_scale)
+
     def _lazy_acc(self, ct: Ct, r: int, digs=None):
         """The Q_l u P accumulator pair of Rot(ct, r) before ModDown (see ``lincomb``)."""
         lp = ct.lp

@@ -224,10 +224,11 @@ def flatten(be, xs, lay: Layout):
         rolled = [np.roll(m, -s) for m, s in zip(masks, steps)]
         return be.lincomb_rescale([x], steps, [[rolled]])[0]
 
+    stages = []   # the masked rotation sums (masks, steps), in order
     if lay.prev == "avgpool":
         steps = [c * (I - 1) for c in range(W)]
         masks = [slot_vector(lay, [I * (r * Wi + c) for r in rows], pending) for c in range(W)]
-        cur = [masked_rotation_sum(x, masks, steps) for x in cur]
+        stages.append((masks, steps))
         pending = 1.0
     elif lay.prev == "conv":
         assert pending == 1.0
@@ -239,18 +240,29 @@ def flatten(be, xs, lay: Layout):
                 cols = range(I * u, min(I * u + I, W))
                 masks.append(slot_vector(lay, [I * r * Wi + I * I * u + (cc - I * u) for r in rows for cc in cols],
                                          1.0))
-            new = []
-            for x in cur:
-                y = be.lincomb([x], [m * (I - 1) for m in range(I)], None)[0]
-                new.append(masked_rotation_sum(y, masks, steps))
-            cur = new
+            cur = [be.lincomb([x], [m * (I - 1) for m in range(I)], None)[0] for x in cur]
+            stages.append((masks, steps))
     else:
         raise ValueError("flatten must follow a convolution or an average pooling")
     if H > 1:
         steps = [r * (Wi * I - W) for r in rows]
         masks = [slot_vector(lay, [I * r * Wi + c for c in range(W)], 1.0) for r in rows]
+        stages.append((masks, steps))
+    for masks, steps in stages[:-1]:
         cur = [masked_rotation_sum(x, masks, steps) for x in cur]
-    acc = be.lincomb_diag(cur, [-o * W * H for o in range(len(cur))]) if len(cur) > 1 else cur[0]
+    CH = len(cur)
+    if not stages:
+        acc = be.lincomb_diag(cur, [-o * W * H for o in range(CH)]) if CH > 1 else cur[0]
+    elif CH == 1:
+        acc = masked_rotation_sum(cur[0], *stages[-1])
+    else:
+        # the last masked stage and the channel packing as one combination (reading C12):
+        # channel o's term Rot(m_k (.) y_o, s_k) moved right by o*W*H is
+        # Rot(m_k, s_k - o*W*H) (.) Rot(y_o, s_k - o*W*H); one ModDown and rescale for all
+        masks, steps = stages[-1]
+        st = [[s - o * W * H for s in steps] for o in range(CH)]
+        ws = [[np.roll(m, -t) for m, t in zip(masks, st[o])] for o in range(CH)]
+        acc = be.lincomb_chan_rescale(cur, st, ws)
     D = len(xs) * W * H
     return [acc], replace(lay, pending=pending, prev="flatten", D=D, W=D, H=1, I=1)
 
@@ -434,17 +446,23 @@ def plan(layers, W_img: int, H_img: int, dims: int = 2):
             prev = "avgpool"
         elif op in ("flatten", "fc"):
             if prev in ("conv", "avgpool"):
+                stage_steps = []   # steps of the masked stages, in order
                 if prev == "avgpool":
                     levels += 1
-                    steps |= {c * (I - 1) for c in range(W)}
+                    stage_steps.append([c * (I - 1) for c in range(W)])
                 elif I > 1 and W > 1:
                     levels += 1
                     steps |= {m * (I - 1) for m in range(I)}
-                    steps |= {u * I * (I - 1) for u in range(-(-W // I))}
+                    stage_steps.append([u * I * (I - 1) for u in range(-(-W // I))])
                 if H > 1:
                     levels += 1
-                    steps |= {r * (W_img * I - W) for r in range(H)}
-                steps |= {-o * W * H for o in range(ch)}
+                    stage_steps.append([r * (W_img * I - W) for r in range(H)])
+                for st in stage_steps[:-1]:
+                    steps |= set(st)
+                if stage_steps:   # the last stage merged with the channel packing
+                    steps |= {s - o * W * H for s in stage_steps[-1] for o in range(ch)}
+                else:
+                    steps |= {-o * W * H for o in range(ch)}
                 flat_D = ch * W * H
                 need = max(need, flat_D)
                 prev = "flatten"
@@ -549,6 +567,25 @@ class HeBackend:
         lp = xs[0].lp
         enc = [[[self.he.encode_ext(v, self.he.scale, lp) for v in wi] for wi in wo] for wo in weights]
         return self.he.lincomb(xs, steps, enc, self.he.scale, rescale=True)
+
+    def lincomb_chan_rescale(self, xs, steps, weights):
+        """Rescale(sum_i sum_k w[i][k] (.) Rot(x_i, steps[i][k])): one output, each input
+        with its own steps."""
+        m = self.he.n // 2
+        self.count["rot"] += sum(len({s % m for s in st if s % m}) for st in steps)
+        self.count["pmul"] += sum(len(w) for w in weights)
+        self.count["rescale"] += 1
+        lp = xs[0].lp
+        if self.naf:
+            acc = None
+            for x, st, ws in zip(xs, steps, weights):
+                rots = self._rots(x, st)
+                for y, v in zip(rots, ws):
+                    t = self.he.ct_mul_plain(y, self.he.encode(v, self.he.scale, lp), self.he.scale)
+                    acc = t if acc is None else self.he.ct_add(acc, t)
+            return self.he.rescale(acc)
+        enc = [[self.he.encode_ext(v, self.he.scale, lp) for v in ws] for ws in weights]
+        return self.he.lincomb_chan(xs, steps, enc, self.he.scale, rescale=True)
 
     def mul_rescale_to(self, x, v, target):
         """x (.) v rescaled onto target's scale and level: the plaintext is encoded at

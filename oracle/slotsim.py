@@ -48,6 +48,16 @@ class SlotSim:
             assert x.used == xs[0].used and not x.pending_rescale
         return SV(sum(np.roll(x.v, -s) for x, s in zip(xs, steps)), xs[0].used, False)
 
+    def lincomb_chan_rescale(self, xs, steps, weights):
+        m = len(xs[0].v)
+        self.count["rot"] += sum(len({s % m for s in st if s % m}) for st in steps)
+        self.count["pmul"] += sum(len(w) for w in weights)
+        self.count["rescale"] += 1
+        for x in xs[1:]:
+            assert x.used == xs[0].used and not x.pending_rescale
+        v = sum(np.roll(x.v, -s) * w for x, st, ws in zip(xs, steps, weights) for s, w in zip(st, ws))
+        return SV(v, xs[0].used + 1, False)
+
     def lincomb(self, xs, steps, weights):
         m = len(xs[0].v)
         self.count["rot"] += len(xs) * len({s % m for s in steps if s % m})
