@@ -251,6 +251,9 @@ def flatten(be, xs, lay: Layout):
     for masks, steps in stages[:-1]:
         cur = [masked_rotation_sum(x, masks, steps) for x in cur]
     CH = len(cur)
+    if stages and not merge_last_stage(len(stages[-1][1]), CH):
+        last = stages.pop()
+        cur = [masked_rotation_sum(x, *last) for x in cur]
     if not stages:
         acc = be.lincomb_diag(cur, [-o * W * H for o in range(CH)]) if CH > 1 else cur[0]
     elif CH == 1:
@@ -265,6 +268,15 @@ def flatten(be, xs, lay: Layout):
         acc = be.lincomb_chan_rescale(cur, st, ws)
     D = len(xs) * W * H
     return [acc], replace(lay, pending=pending, prev="flatten", D=D, W=D, H=1, I=1)
+
+
+# The flatten's last masked stage (K steps) is merged with the packing of CH channels when the
+# merged combination needs at most this many rotation steps (K*CH Galois keys instead of K + CH)
+MERGE_MAX_STEPS = 128
+
+
+def merge_last_stage(k: int, ch: int) -> bool:
+    return ch > 1 and k * ch <= MERGE_MAX_STEPS
 
 
 def fc_rot_matrix(M: np.ndarray):
@@ -457,11 +469,13 @@ def plan(layers, W_img: int, H_img: int, dims: int = 2):
                 if H > 1:
                     levels += 1
                     stage_steps.append([r * (W_img * I - W) for r in range(H)])
-                for st in stage_steps[:-1]:
-                    steps |= set(st)
-                if stage_steps:   # the last stage merged with the channel packing
+                if stage_steps and merge_last_stage(len(stage_steps[-1]), ch):
+                    for st in stage_steps[:-1]:
+                        steps |= set(st)
                     steps |= {s - o * W * H for s in stage_steps[-1] for o in range(ch)}
                 else:
+                    for st in stage_steps:
+                        steps |= set(st)
                     steps |= {-o * W * H for o in range(ch)}
                 flat_D = ch * W * H
                 need = max(need, flat_D)
