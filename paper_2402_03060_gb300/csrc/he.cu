@@ -832,6 +832,85 @@ Cts ct_lincomb_diag(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> 
 // Q_l u P with t = s*CH + i, or nullptr for the plain sums Y_i = sum_s Rot(X_i, steps[s])
 // (one output per channel).  The weighted key-switch accumulators, with P*sigma(c0)
 // folded in, are summed over Q_l u P and ModDown runs once per output ciphertext.
+// One output from channels that each have their own steps (every channel the same count K):
+//   Y = sum_i sum_k pts[i][k] (.) Rot(X_i, steps[i][k])
+// X holds CH*B ciphertexts (channel-major); pts [CH][K][lp+K_sp][N] over Q_l u P (over Q_l
+// with power-of-two keys).  Each channel's rotations share one ModUp; the weighted
+// accumulators of every channel are summed over Q_l u P and ModDown (with rescale: the one
+// division by q_top * P) runs once.
+Cts ct_rotate_naf(Ctx *c, const Cts &a, int step, std::map<int64_t, Cts> *cache);
+
+Cts ct_lincomb_chan(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<std::vector<int>> &steps, const u64 *pts,
+                    double pt_scale, bool rescale) {
+    const u32 N = c->N, lp = X.lp, Bt = CH * B;
+    if (X.B != Bt || steps.size() != CH || !CH) throw HeError(HE_EINVAL, "lincomb_chan: shape mismatch");
+    const u32 K = (u32)steps[0].size();
+    for (const auto &st : steps) {
+        if (st.size() != K || !K) throw HeError(HE_EINVAL, "lincomb_chan: steps per channel differ");
+        for (int s : st)
+            if (c->naf) {
+                for (int t : naf_terms(s, N / 2)) require_key(c, t);
+            } else if (c->galois_elt(s) != 1) {
+                require_key(c, s);
+            }
+    }
+    const size_t bw = (size_t)B * cts_ct_words(c, lp);   // one channel's block of B ciphertexts
+    if (c->naf) {
+        const size_t pw = (size_t)lp * N;
+        Cts Z = cts_alloc(c, B, lp, X.scale * pt_scale, X.lay);
+        Cts R = cts_alloc(c, K * B, lp, X.scale, X.lay);
+        for (u32 i = 0; i < CH; ++i) {
+            std::map<int64_t, Cts> cache;
+            const Cts Xi = cts_view(X, i * bw, B);
+            for (u32 k = 0; k < K; ++k) {
+                Cts r = ct_rotate_naf(c, Xi, steps[i][k], &cache);
+                CUDA_TRY(cudaMemcpyAsync(R.data() + k * bw, r.data(), bw * 8, cudaMemcpyDeviceToDevice, c->stream));
+            }
+            mac(c, Z.data(), bw, R.data(), bw, pts + (size_t)i * K * pw, 1, K, B, lp, lp, c->L1, i > 0,
+                (size_t)CH * K * pw);
+        }
+        return rescale ? ct_rescale(c, Z) : Z;
+    }
+    const u32 E = lp + c->K, beta = ks_digits(c, lp);
+    DBuf D(c, (size_t)Bt * beta * E * N);
+    ks_modup(c, D.p, X.data() + (size_t)lp * N, (size_t)2 * lp * N, Bt, lp);
+    const size_t zw = (size_t)B * 2 * E * N;
+    DBuf Z(c, zw);
+    const size_t per_step = zw * 8;
+    size_t chunk = ((size_t)4 << 30) / (per_step ? per_step : 1);
+    chunk = std::max<size_t>(1, std::min<size_t>(chunk, KEYLIST_MAX));
+    DBuf acc(c, std::min<size_t>(chunk, K) * zw);
+    for (u32 i = 0; i < CH; ++i) {
+        for (u32 s0 = 0; s0 < K; s0 += (u32)chunk) {
+            const u32 Sc = std::min<u32>((u32)chunk, K - s0);
+            KeyList kl;
+            for (u32 s = 0; s < Sc; ++s) {
+                const u32 g = c->galois_elt(steps[i][s0 + s]);
+                kl.g[s] = g;
+                kl.ginv[s] = c->galois_inverse(g);
+                kl.key[s] = g == 1 ? nullptr : c->gk.at(g).p;
+                kl.keyp[s] = g == 1 ? nullptr : c->gkp.at(g).p;
+            }
+            ks_lazy(c, acc.p, D.p + (size_t)i * B * beta * E * N, X.data() + i * bw, kl, Sc, B, lp);
+            // Z += sum_{k in chunk} pts[i][k] (.) acc[k]
+            mac(c, Z.p, zw, acc.p, zw, pts + ((size_t)i * K + s0) * E * N, 1, Sc, B, E, lp, c->L1, i > 0 || s0 > 0,
+                (size_t)CH * K * E * N);
+        }
+    }
+    if (rescale) {
+        if (lp < 2) throw HeError(HE_ELEVEL, "rescale: no level left");
+        Cts out = cts_alloc(c, B, lp - 1, X.scale * pt_scale / (double)c->primes[lp - 1], X.lay);
+        ks_moddown_rescale(c, out.data(), Z.p, B, lp);
+        return out;
+    }
+    Cts out = cts_alloc(c, B, lp, X.scale * pt_scale, X.lay);
+    KeyList none;
+    none.g[0] = 1;
+    none.key[0] = nullptr;
+    ks_moddown(c, out.data(), Z.p, nullptr, 0, 0, none, 1, B, lp);
+    return out;
+}
+
 // Power-of-two keys: rotate-then-multiply.  The whole batch X is rotated by every step
 // (chains sharing their prefixes), the plaintexts pts [O][S*CH][lp][N] (over Q_l) multiply
 // the rotations and the products are summed (or the rotations are summed); then the

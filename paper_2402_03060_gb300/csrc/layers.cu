@@ -228,33 +228,46 @@ static Feat layer_approx_relu(Ctx *c, const Feat &in, PtCache *pc, const std::st
     return f;
 }
 
+// The flatten's last masked stage (K steps) is merged with the packing of CH channels when the
+// merged combination needs at most this many rotation steps (K*CH Galois keys instead of K + CH)
+static const u32 MERGE_MAX_STEPS = 128;
+static bool merge_last_stage(u32 k, u32 ch) { return ch > 1 && k * ch <= MERGE_MAX_STEPS; }
+
 // Sec. IV-E: remove intervals / invalid values, pack the channels.
 // Every mask-rotate-sum stage  sum_k Rot(m_k (.) x, r_k)  is evaluated as one hoisted
 // combination  sum_k Rot(m_k, r_k) (.) Rot(x, r_k)  (the masks are rotated in the clear),
-// followed by one rescale; channel o is then rotated right by o*W*H and all channels are
-// summed with one ModDown.
+// followed by one rescale.  The last stage and the channel packing (channel o rotated right
+// by o*W*H) are one combination: channel o's terms use the steps r_k - o*W*H and the masks
+// rotated by them, with one ModDown and rescale for the packed output.
 static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string &key) {
     const Layout &L = in.x.lay;
-    const u32 I = L.I, W = L.W, H = L.H, Wi = L.W_img;
+    const u32 I = L.I, W = L.W, H = L.H, Wi = L.W_img, CH = in.CH;
     const u32 M = c->N / 2;
     std::vector<DBuf> tmp;
     Cts cur = in.x;
     double pending = L.pending;
+    struct Stage {
+        std::string name;
+        std::vector<std::vector<u32>> pos;   // within-sample positions of each mask
+        std::vector<int> steps;
+        double v;
+    };
+    std::vector<Stage> stages;
     // masks (within-sample positions, one value each) rotated left by their steps and
-    // replicated over every sample position; encoded over Q_l u P at the input level
-    auto stage = [&](const Cts &x, const std::string &k, const std::vector<std::vector<u32>> &pos,
-                     const std::vector<int> &steps, double v) {
-        const std::string name = key + k;
+    // replicated over every sample position, encoded over Q_l u P at the input level;
+    // mask j of the list uses pos[mk[j]] rotated by st[j]
+    auto masks = [&](const std::string &name, const Stage &S, const std::vector<u32> &mk, const std::vector<int> &st,
+                     u32 lp) {
         std::vector<u32> off, apos;
         std::vector<double> val;
         if (!pc || !pc->pts.count(name)) {
             off.push_back(0);
-            for (size_t m = 0; m < pos.size(); ++m) {
+            for (size_t j = 0; j < mk.size(); ++j) {
                 for (u32 b = 0; b < L.n_samples; ++b)
-                    for (u32 p : pos[m]) {
-                        int64_t a = ((int64_t)b * L.stride + p - steps[m]) % (int64_t)M;
+                    for (u32 p : S.pos[mk[j]]) {
+                        int64_t a = ((int64_t)b * L.stride + p - st[j]) % (int64_t)M;
                         apos.push_back((u32)(a < 0 ? a + M : a));
-                        val.push_back(v);
+                        val.push_back(S.v);
                     }
                 off.push_back((u32)apos.size());
             }
@@ -262,60 +275,83 @@ static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string
         Layout flat = L;
         flat.n_samples = 1;
         flat.stride = M;
-        const u64 *pts = get_pts(c, pc, name, tmp, flat, off, apos, val, c->scale, x.lp, ks_ext(c));
-        return ct_lincomb(c, x, 1, x.B, steps, pts, 1, c->scale, true);
+        return get_pts(c, pc, name, tmp, flat, off, apos, val, c->scale, lp, ks_ext(c));
+    };
+    auto run_stage = [&](const Cts &x, const Stage &S) {
+        std::vector<u32> mk;
+        for (u32 k = 0; k < S.steps.size(); ++k) mk.push_back(k);
+        const u64 *pts = masks(key + S.name, S, mk, S.steps, x.lp);
+        return ct_lincomb(c, x, 1, x.B, S.steps, pts, 1, c->scale, true);
     };
     if (L.prev == PREV_POOL) {
-        std::vector<std::vector<u32>> pos(W);
-        std::vector<int> steps;
+        Stage S{":cols", std::vector<std::vector<u32>>(W), {}, pending};
         for (u32 cc = 0; cc < W; ++cc) {
-            for (u32 r = 0; r < H; ++r) pos[cc].push_back(I * (r * Wi + cc));
-            steps.push_back((int)(cc * (I - 1)));
+            for (u32 r = 0; r < H; ++r) S.pos[cc].push_back(I * (r * Wi + cc));
+            S.steps.push_back((int)(cc * (I - 1)));
         }
-        cur = stage(cur, ":cols", pos, steps, pending);
+        stages.push_back(S);
         pending = 1.0;
     } else if (L.prev == PREV_CONV) {
         if (pending != 1.0) throw HeError(HE_EINVAL, "flatten: unexpected pending factor");
         if (I > 1 && W > 1) {
             std::vector<int> st;
             for (u32 m = 0; m < I; ++m) st.push_back((int)(m * (I - 1)));
-            Cts y = ct_lincomb(c, cur, 1, cur.B, st, nullptr, 0, 1.0);
+            cur = ct_lincomb(c, cur, 1, cur.B, st, nullptr, 0, 1.0);
             const u32 nblk = (W + I - 1) / I;
-            std::vector<std::vector<u32>> pos(nblk);
-            std::vector<int> steps;
+            Stage S{":blks", std::vector<std::vector<u32>>(nblk), {}, 1.0};
             for (u32 u = 0; u < nblk; ++u) {
                 for (u32 r = 0; r < H; ++r)
                     for (u32 cc = I * u; cc < std::min(I * u + I, W); ++cc)
-                        pos[u].push_back(I * r * Wi + I * I * u + (cc - I * u));
-                steps.push_back((int)(u * I * (I - 1)));
+                        S.pos[u].push_back(I * r * Wi + I * I * u + (cc - I * u));
+                S.steps.push_back((int)(u * I * (I - 1)));
             }
-            cur = stage(y, ":blks", pos, steps, 1.0);
+            stages.push_back(S);
         }
     } else {
         throw HeError(HE_EINVAL, "flatten must follow a convolution or an average pooling");
     }
     if (H > 1) {
-        std::vector<std::vector<u32>> pos(H);
-        std::vector<int> steps;
+        Stage S{":rows", std::vector<std::vector<u32>>(H), {}, 1.0};
         for (u32 r = 0; r < H; ++r) {
-            for (u32 cc = 0; cc < W; ++cc) pos[r].push_back(I * r * Wi + cc);
-            steps.push_back((int)(r * (Wi * I - W)));
+            for (u32 cc = 0; cc < W; ++cc) S.pos[r].push_back(I * r * Wi + cc);
+            S.steps.push_back((int)(r * (Wi * I - W)));
         }
-        cur = stage(cur, ":rows", pos, steps, 1.0);
+        stages.push_back(S);
     }
-    // pack: channel o rotated right by o*W*H, one ModDown for the sum
+    for (size_t k = 0; k + 1 < stages.size(); ++k) cur = run_stage(cur, stages[k]);
+    if (!stages.empty() && !merge_last_stage((u32)stages.back().steps.size(), CH)) {
+        cur = run_stage(cur, stages.back());
+        stages.clear();
+    }
     Cts acc;
-    if (in.CH > 1) {
-        std::vector<int> steps;
-        for (u32 o = 0; o < in.CH; ++o) steps.push_back(-(int)(o * W * H));
-        acc = ct_lincomb_diag(c, cur, in.CH, in.B, steps);
+    if (stages.empty()) {
+        if (CH > 1) {   // pack: channel o rotated right by o*W*H, one ModDown for the sum
+            std::vector<int> steps;
+            for (u32 o = 0; o < CH; ++o) steps.push_back(-(int)(o * W * H));
+            acc = ct_lincomb_diag(c, cur, CH, in.B, steps);
+        } else {
+            acc = cur;
+        }
+    } else if (CH == 1) {
+        acc = run_stage(cur, stages.back());
     } else {
-        acc = cur;
+        const Stage &S = stages.back();
+        std::vector<std::vector<int>> st(CH);
+        std::vector<u32> mk;
+        std::vector<int> flat_st;
+        for (u32 o = 0; o < CH; ++o)
+            for (u32 k = 0; k < S.steps.size(); ++k) {
+                st[o].push_back(S.steps[k] - (int)(o * W * H));
+                mk.push_back(k);
+                flat_st.push_back(st[o].back());
+            }
+        const u64 *pts = masks(key + S.name + ":pack", S, mk, flat_st, cur.lp);
+        acc = ct_lincomb_chan(c, cur, CH, in.B, st, pts, c->scale, true);
     }
     Layout L2 = L;
     L2.pending = pending;
     L2.prev = PREV_FLAT;
-    L2.D = in.CH * W * H;
+    L2.D = CH * W * H;
     L2.W = L2.D;
     L2.H = 1;
     L2.I = 1;
@@ -472,19 +508,31 @@ static Plan plan_layers(const std::vector<LayerSpec> &ls, u32 Wi, u32 Hi) {
             prev = PREV_POOL;
         } else if (s.op == HE_FLATTEN || s.op == HE_FC) {
             if (prev == PREV_CONV || prev == PREV_POOL) {
+                std::vector<std::vector<int>> stage;   // steps of the masked stages, in order
                 if (prev == PREV_POOL) {
                     levels += 1;
-                    for (u32 c = 0; c < W; ++c) st.insert((int)(c * (I - 1)));
+                    stage.emplace_back();
+                    for (u32 c = 0; c < W; ++c) stage.back().push_back((int)(c * (I - 1)));
                 } else if (I > 1 && W > 1) {
                     levels += 1;
                     for (u32 m = 0; m < I; ++m) st.insert((int)(m * (I - 1)));
-                    for (u32 u = 0; u < (W + I - 1) / I; ++u) st.insert((int)(u * I * (I - 1)));
+                    stage.emplace_back();
+                    for (u32 u = 0; u < (W + I - 1) / I; ++u) stage.back().push_back((int)(u * I * (I - 1)));
                 }
                 if (H > 1) {
                     levels += 1;
-                    for (u32 r = 0; r < H; ++r) st.insert((int)(r * (Wi * I - W)));
+                    stage.emplace_back();
+                    for (u32 r = 0; r < H; ++r) stage.back().push_back((int)(r * (Wi * I - W)));
                 }
-                for (u32 o = 0; o < ch; ++o) st.insert(-(int)(o * W * H));
+                if (!stage.empty() && merge_last_stage((u32)stage.back().size(), ch)) {
+                    // the last stage merged with the channel packing
+                    for (size_t k = 0; k + 1 < stage.size(); ++k) st.insert(stage[k].begin(), stage[k].end());
+                    for (int sk : stage.back())
+                        for (u32 o = 0; o < ch; ++o) st.insert(sk - (int)(o * W * H));
+                } else {
+                    for (const auto &v : stage) st.insert(v.begin(), v.end());
+                    for (u32 o = 0; o < ch; ++o) st.insert(-(int)(o * W * H));
+                }
                 need = std::max(need, ch * W * H);
                 prev = PREV_FLAT;
                 W = ch * W * H;

@@ -61,6 +61,8 @@ Cts ct_square(Ctx *c, const Cts &a);
 Cts ct_lincomb(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps, const u64 *pts, u32 O,
                double pt_scale, bool rescale = false);
 Cts ct_lincomb_diag(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps);
+Cts ct_lincomb_chan(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<std::vector<int>> &steps, const u64 *pts,
+                    double pt_scale, bool rescale);
 Cts ct_mul_pt(Ctx *c, const Cts &a, const u64 *pt, double pt_scale);
 void ct_add_pt_inplace(Ctx *c, Cts &a, const u64 *pt);
 void require_key(Ctx *c, int step);
