@@ -179,12 +179,12 @@ PARAMS = {
 
 # Serving mix: every model's keys with dnum = 3 digits.  A digit then spans up to
 # three (LeNet-1, 1-D CNN) or four (LeNet-5) data primes, so the special modulus
-# P must cover it: three 50-bit primes (150 bits > 140) and four 50-bit primes
-# (200 bits > 180).  At N = 2^14 that makes log QP = 490 bits, above the 438 bits
-# of the 128-bit HE-standard bound; recorded, not hidden.
+# P must cover it: three 50-bit primes (150 bits > 140) and three 60-bit primes
+# (180 bits, the size of LeNet-5's widest digit).  At N = 2^14 that makes log QP =
+# 490 bits, above the 438 bits of the 128-bit HE-standard bound; recorded, not hidden.
 SERVE_PARAMS = {
     "lenet1": dict(logn=14, data_bits=[60] + [40] * 7, special_bits=[50] * 3, dnum=3, log2_scale=40),
-    "lenet5": dict(logn=15, data_bits=[60] + [40] * 11, special_bits=[50] * 4, dnum=3, log2_scale=40),
+    "lenet5": dict(logn=15, data_bits=[60] + [40] * 11, special_bits=[60] * 3, dnum=3, log2_scale=40),
     "cnn1d": dict(logn=14, data_bits=[60] + [40] * 6, special_bits=[50] * 3, dnum=3, log2_scale=40),
 }
 ARRIVAL_SEED = 12345
