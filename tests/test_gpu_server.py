@@ -38,7 +38,8 @@ def two_models(G):
     return (lenet, a), (conv, b)
 
 
-def test_results_identical_alone_and_mixed(G, two_models):
+@pytest.mark.parametrize("policy", [dict(), dict(max_inflight=1, exact_batches=True)])
+def test_results_identical_alone_and_mixed(G, two_models, policy):
     (lenet, (ca, ma, sa)), (conv, (cb, mb, sb)) = two_models
     imgs = W.images(7)
     # requests: (model id, context, stride, images, seed); one request of two ciphertexts
@@ -54,7 +55,7 @@ def test_results_identical_alone_and_mixed(G, two_models):
     for mid, ctx, stride, x, seed in reqs:
         ct = ctx.encrypt(x, 1, stride, seed)
         alone.append(ctx.export(models[mid].infer(ct)))
-    srv = G.Server(max_batch=4)
+    srv = G.Server(max_batch=4, **policy)
     assert srv.add_model(ma) == 0 and srv.add_model(mb) == 1
     ids = []
     for mid, ctx, stride, x, seed in reqs:
