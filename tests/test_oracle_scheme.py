@@ -204,3 +204,24 @@ def test_rotation_with_power_of_two_keys_only():
     # the chain for 7 = 8 - 1 reuses the cached rotation by -1 of the chain for 3 = 4 - 1
     assert -1 in cache and 3 in cache and 7 in cache
     assert np.array_equal(h.rotate_naf(ct, 0).d, ct.d)
+
+
+@pytest.mark.parametrize("rescale", [False, True])
+def test_lincomb_chan_decrypts_to_per_input_rotation_sums(he, rescale):
+    """Each input with its own steps (the flatten's merged stage): the combination
+    decrypts to sum_i sum_k w_ik * roll(x_i, -s_ik); with one input and shared steps it
+    is exactly (bit for bit) the one-output lincomb."""
+    M = he.n // 2
+    rng = np.random.default_rng(31)
+    zs = [rng.uniform(-1, 1, M) for _ in range(2)]
+    cts = [he.encrypt(z, 9300 + i) for i, z in enumerate(zs)]
+    steps = [[0, 3], [-2, 100]]
+    ws = [[rng.uniform(-1, 1, M) for _ in st] for st in steps]
+    enc = [[he.encode_ext(w, he.scale, cts[0].lp) for w in wi] for wi in ws]
+    out = he.lincomb_chan(cts, steps, enc, he.scale, rescale=rescale)
+    want = sum(w * np.roll(z, -s) for z, st, wi in zip(zs, steps, ws) for s, w in zip(st, wi))
+    got = he.decrypt(out if rescale else he.rescale(out))
+    assert np.abs(got - want).max() < 1e-5
+    one = he.lincomb_chan(cts[:1], [[1, 7]], [enc[0]], he.scale, rescale=rescale)
+    ref = he.lincomb(cts[:1], [1, 7], [[enc[0]]], he.scale, rescale=rescale)[0]
+    assert np.array_equal(one.d, ref.d) and one.scale == ref.scale
