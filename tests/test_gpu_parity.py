@@ -328,17 +328,20 @@ def test_three_channel_input_bit_exact(G):
 
 
 def test_m5_full_logits(G):
-    """The paper's M5 (CIFAR-10 shaped: 3 -> 16 -> 64 -> 128 channels, 8 levels) at
-    N = 2^13, one 3x32x32 sample: logits against the FP64 CNN.  The compiled model
-    holds about 50 GB of encoded weight masks (90,544 masks over Q u P limbs)."""
+    """The paper's M5 (CIFAR-10 shaped: 3 -> 16 -> 64 -> 128 channels, 8 levels) with
+    the paper's 8192 slots (N = 2^14), two 3x32x32 samples per ciphertext: logits
+    against the FP64 CNN.  The compiled model holds about 100 GB of encoded weight
+    masks (90,544 masks over Q u P limbs)."""
     model, Wi, Hi = W.paper_model("M5")
     stride, levels, steps = G.plan(model, Wi, Hi)
-    P = dict(logn=13, data_bits=[60] + [40] * levels, special_bits=[60, 60, 60], dnum=3, log2_scale=40)
+    P = dict(logn=14, data_bits=[60] + [40] * levels, special_bits=[60, 60, 60], dnum=3, log2_scale=40)
     ctx = G.Context(seed=W.KEY_SEED, **P)
     ctx.keygen(steps)
-    imgs = W.images(1, 32, 32, C=3)
-    out = ctx.compile(model, Wi, Hi, 1).infer(ctx.encrypt(imgs, 1, stride, W.ENC_SEED))
-    assert np.abs(ctx.decrypt(out, 10)[0] - cnn.forward(imgs[0], model)).max() < 1e-3
+    imgs = W.images(2, 32, 32, C=3)
+    out = ctx.compile(model, Wi, Hi, 2).infer(ctx.encrypt(imgs, 2, stride, W.ENC_SEED))
+    logits = ctx.decrypt(out, 10)
+    for b in range(2):
+        assert np.abs(logits[b] - cnn.forward(imgs[b], model)).max() < 1e-3
 
 
 @pytest.mark.parametrize("name", ["M7", "lenet1"])
