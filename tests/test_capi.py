@@ -74,6 +74,27 @@ def test_planner_matches_oracle(lib, name):
     assert stride == p["stride"] and levels == p["levels"] and steps == p["steps"]
 
 
+@pytest.mark.parametrize("co", [16, 17])
+def test_planner_flatten_merge_boundary(lib, co):
+    """The flatten's last masked stage (8 rows) is merged with the packing of co channels
+    when 8*co <= 128 rotation steps: both planners agree on either side of the bound."""
+    rng = np.random.default_rng(co)
+    model = [{"op": "conv2d", "w": rng.normal(0, 0.1, (co, 1, 5, 5)), "b": np.zeros(co), "stride": 1},
+             {"op": "square"}, {"op": "avgpool", "k": 3}, {"op": "flatten"},
+             {"op": "fc", "w": rng.normal(0, 0.1, (10, co * 64)), "b": np.zeros(10)}]
+    stride, levels, steps = lib.plan(model, 28, 28)
+    p = olayers.plan(model, 28, 28, 2)
+    assert stride == p["stride"] and levels == p["levels"] and steps == p["steps"]
+    rows = {r * (28 * 3 - 8) for r in range(8)}            # the last stage: 8 rows
+    merged = {s - o * 64 for s in rows for o in range(co)} - {0}
+    probe = 7 * 76 - 15 * 64                               # row 7 of channel 15: a merged step only
+    if 8 * co <= olayers.MERGE_MAX_STEPS:
+        assert merged <= set(steps) and probe in steps     # rows x channels, one combination
+    else:
+        assert rows - {0} <= set(steps) and {-o * 64 for o in range(1, co)} <= set(steps)
+        assert probe not in steps
+
+
 def test_planner_rejects_bad_models(lib):
     from paper_2402_03060_gb300 import HeError
     bad = [{"op": "conv2d", "w": np.zeros((1, 1, 30, 30)), "b": np.zeros(1), "stride": 1}]
