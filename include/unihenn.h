@@ -223,6 +223,13 @@ he_status he_model_compile(he_ctx *ctx, const he_layer *layers, size_t n, uint32
  * use_graph = 1 replays a captured CUDA graph after the first call of a given
  * batch size. */
 he_status he_infer(he_model *m, const he_ct *in, int use_graph, he_ct **out);
+/* Memory for the encoded weight masks of a convolution (0, the default: no limit, every
+ * mask is encoded once and kept).  A convolution whose masks over Q u P take more than
+ * `bytes` keeps only their sparse description on the device and encodes them at every
+ * inference, in groups of output channels whose masks fit in `bytes` (more work per
+ * inference, bounded memory; the results are bit-identical).  Takes effect for layers
+ * not yet run.  Errors: HE_EINVAL. */
+he_status he_model_set_mask_budget(he_model *m, uint64_t bytes);
 void he_model_free(he_model *m);
 
 /* ---- autotuning --------------------------------------------------------- */

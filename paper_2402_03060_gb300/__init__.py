@@ -117,6 +117,11 @@ class Model:
         self.ctx, self._keep = ctx, keep
         self.h = h if isinstance(h, ctypes.c_void_p) else ctypes.c_void_p(h)
 
+    def set_mask_budget(self, nbytes: int):
+        """he_model_set_mask_budget: encode a convolution's masks per inference when they
+        would take more than nbytes (0: keep every mask)."""
+        check(load().he_model_set_mask_budget(self.h, nbytes))
+
     def infer(self, ct: Ct, use_graph: bool = False) -> Ct:
         out = ctypes.c_void_p()
         check(load().he_infer(self.h, ct.h, int(use_graph), ctypes.byref(out)))

@@ -89,6 +89,7 @@ SIGNATURES = {
     "he_model_compile": (_int, [_vp, ctypes.POINTER(he_layer), _sz, _u32, _u32, _u32, _pp]),
     "he_infer": (_int, [_vp, _vp, _int, _pp]),
     "he_model_free": (None, [_vp]),
+    "he_model_set_mask_budget": (_int, [_vp, _u64]),
     "he_ntt": (_int, [_vp, _vp, _u32, ctypes.POINTER(_u32), _int]),
     "he_rescale_noalloc": (_int, [_vp, _vp, _vp, _u32, _u32]),
     "he_sync": (_int, [_vp]),

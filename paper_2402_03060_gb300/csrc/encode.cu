@@ -287,6 +287,9 @@ void encode_dense(Ctx *c, u64 *out, const double *z, u32 nv, double scale, u32 l
     if (check) check_err(c);
 }
 
+void encode_sparse_dev(Ctx *c, u64 *out, const u32 *off, u32 nv, const u32 *pos, const double *val, u32 stride,
+                       u32 ns, double scale, u32 lp, u32 ext);
+
 // sparse slot vectors (host arrays), eval form out [nv][lp + ext][N]: limbs q_0..q_{lp-1},
 // then (ext = K) the special primes, i.e. the plaintext over Q_l u P.
 void encode_sparse(Ctx *c, u64 *out, const std::string &key, const std::vector<u32> &off,
@@ -302,20 +305,31 @@ void encode_sparse(Ctx *c, u64 *out, const std::string &key, const std::vector<u
     memcpy(h.data() + o_pos, pos.data(), pos.size() * 4);
     memcpy(h.data() + o_val, val.data(), val.size() * 8);
     (void)key;
+    (void)M;
     DBuf tmp(c, h.size());
     CUDA_TRY(cudaMemcpyAsync(tmp.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream));
     u64 *d = tmp.p;
-    double f = scale / (double)M;
+    encode_sparse_dev(c, out, reinterpret_cast<const u32 *>(d + o_off), nv, reinterpret_cast<const u32 *>(d + o_pos),
+                      reinterpret_cast<const double *>(d + o_val), stride, ns, scale, lpq, ext);
+    check_err(c);   // also keeps the host staging vector alive until the upload is done
+}
+
+// The same from a device-resident description (no host staging and no synchronisation, so it
+// can run inside a graph capture): mask v < nv covers pos/val entries [off[v], off[v+1]).
+void encode_sparse_dev(Ctx *c, u64 *out, const u32 *off, u32 nv, const u32 *pos, const double *val, u32 stride,
+                       u32 ns, double scale, u32 lp, u32 ext) {
+    const u32 M = c->N / 2;
+    const u32 lpq = lp;
+    lp += ext;
+    if (!nv) return;
+    const double f = scale / (double)M;
     prof_begin(c);
     launch_parts(c, encode_sparse_kernel<0>, encode_sparse_kernel<1>, dim3(nv), ntt_min_split(c->logn), fft_threads(M >> ntt_min_split(c->logn)),
-                 fft_smem(c, ntt_min_split(c->logn)), out,
-                 reinterpret_cast<const u32 *>(d + o_off), reinterpret_cast<const u32 *>(d + o_pos),
-                 reinterpret_cast<const double *>(d + o_val), stride, ns, lp, c->logn, f, (const double *)c->fft_w,
-                 (const double *)c->fft_t, (const u32 *)c->slot_pos_br, (const PrimeDev *)c->pdev, c->err_flag, lpq,
-                 c->L1);
+                 fft_smem(c, ntt_min_split(c->logn)), out, off, pos, val, stride, ns, lp, c->logn, f,
+                 (const double *)c->fft_w, (const double *)c->fft_t, (const u32 *)c->slot_pos_br,
+                 (const PrimeDev *)c->pdev, c->err_flag, lpq, c->L1);
     note_launch(c, "encode_sparse");
     ntt_forward(c, out, rows_regular(nv * lp, lp, lpq, c->L1));
-    check_err(c);   // also keeps the host staging vector alive until the upload is done
 }
 
 void check_encode_errors(Ctx *c) { check_err(c); }

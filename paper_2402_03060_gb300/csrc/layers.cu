@@ -97,7 +97,58 @@ static Feat layer_conv(Ctx *c, const Feat &in, const LayerSpec &sp, u32 kh, u32 
         return get_pts(c, pc, k, tmp, L, off, pos, val, c->scale, lp, ext);
     };
     Cts out;
-    if (!incremental) {
+    const u32 E2 = lp + ks_ext(c);
+    const size_t per_out = (size_t)T * E2 * N;   // words of one output channel's masks
+    if (!incremental && pc && pc->mask_budget && (size_t)co * per_out * 8 > pc->mask_budget) {
+        // masks too large to keep: their sparse description is cached on the device and they
+        // are encoded at every run, for groups of output channels that fit the budget
+        const std::string dk = key + (ks_ext(c) ? ":wdx" : ":wd");
+        if (!pc->pts.count(dk)) {
+            std::vector<u32> off{0}, pos;
+            std::vector<double> val;
+            for (u32 o = 0; o < co; ++o)
+                for (u32 t = 0; t < T; ++t) {
+                    u32 kk = t / ci, i = t % ci, j = kk / kw, k2 = kk % kw;
+                    double wv = sp.w[(((size_t)o * ci + i) * kh + j) * kw + k2] * L.pending;
+                    for (u32 p : vpos) {
+                        pos.push_back(p);
+                        val.push_back(wv);
+                    }
+                    off.push_back((u32)pos.size());
+                }
+            const size_t o_pos = off.size() / 2 + 1, o_val = o_pos + pos.size() / 2 + 1;
+            std::vector<u64> h(o_val + val.size(), 0);
+            memcpy(h.data(), off.data(), off.size() * 4);
+            memcpy(h.data() + o_pos, pos.data(), pos.size() * 4);
+            memcpy(h.data() + o_val, val.data(), val.size() * 8);
+            Pool *saved = c->active;
+            c->active = nullptr;   // cached data lives in the context pool
+            DBuf d(c, h.size());
+            c->active = saved;
+            CUDA_TRY(cudaMemcpyAsync(d.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));   // h is staged from the stack
+            pc->pts.emplace(dk, std::move(d));
+            pc->desc[dk] = {o_pos, o_val};
+        }
+        const u64 *d = pc->pts.at(dk).p;
+        const std::vector<size_t> &dd = pc->desc.at(dk);
+        const u32 *off_d = reinterpret_cast<const u32 *>(d);
+        const u32 *pos_d = reinterpret_cast<const u32 *>(d + dd[0]);
+        const double *val_d = reinterpret_cast<const double *>(d + dd[1]);
+        const u32 og = (u32)std::max<size_t>(1, std::min<size_t>(co, pc->mask_budget / 8 / per_out));
+        for (u32 o0 = 0; o0 < co; o0 += og) {
+            const u32 oc = std::min(og, co - o0);
+            DBuf m(c, (size_t)oc * per_out);
+            for (u32 o = o0; o < o0 + oc; ++o)
+                encode_sparse_dev(c, m.p + (size_t)(o - o0) * per_out, off_d + (size_t)o * T, T, pos_d, val_d,
+                                  L.stride, L.n_samples, c->scale, lp, ks_ext(c));
+            Cts r = ct_lincomb(c, in.x, packed ? 1 : ci, B, steps, m.p, oc, c->scale, true);
+            if (o0 == 0) out = cts_alloc(c, co * B, r.lp, r.scale, r.lay);
+            const size_t w = (size_t)oc * B * cts_ct_words(c, r.lp);
+            CUDA_TRY(cudaMemcpyAsync(out.data() + (size_t)o0 * B * cts_ct_words(c, r.lp), r.data(), w * 8,
+                                     cudaMemcpyDeviceToDevice, c->stream));
+        }
+    } else if (!incremental) {
         // one hoisted linear combination per output channel, ModDown and rescale as one division each
         const u64 *pts = weight_pts(ks_ext(c));
         out = ct_lincomb(c, in.x, packed ? 1 : ci, B, steps, pts, co, c->scale, true);
@@ -1160,6 +1211,14 @@ he_status he_infer(he_model *m, const he_ct *in, int use_graph, he_ct **out) {
         CtxLock lk(c);
         CUDA_TRY(cudaSetDevice(c->device));
         *out = ct_wrap(c, model_infer(m, in->x, use_graph != 0));
+    });
+}
+
+he_status he_model_set_mask_budget(he_model *m, uint64_t bytes) {
+    return guard([&] {
+        if (!m) throw HeError(HE_EINVAL, "null model");
+        CtxLock lk(m->c);
+        m->pc.mask_budget = (size_t)bytes;
     });
 }
 

@@ -6,6 +6,11 @@
 // cached encoded plaintexts of a compiled model (nullptr: encode every call)
 struct PtCache {
     std::map<std::string, DBuf> pts;
+    // a convolution whose masks take more than this many bytes (0: no limit) keeps only their
+    // sparse description here and encodes them at every run, output channels in groups
+    // whose masks fit the budget
+    size_t mask_budget = 0;
+    std::map<std::string, std::vector<size_t>> desc;   // word offsets of off / pos / val, counts
 };
 
 struct LayerSpec {

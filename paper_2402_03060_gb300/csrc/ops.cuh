@@ -31,6 +31,8 @@ void keygen(Ctx *c, const std::vector<int> &steps);
 // encode.cu
 void encode_init(Ctx *c);
 void encode_dense(Ctx *c, u64 *out, const double *z, u32 nv, double scale, u32 lp, bool check);
+void encode_sparse_dev(Ctx *c, u64 *out, const u32 *off, u32 nv, const u32 *pos, const double *val, u32 stride,
+                       u32 ns, double scale, u32 lp, u32 ext);
 void encode_sparse(Ctx *c, u64 *out, const std::string &key, const std::vector<u32> &off,
                    const std::vector<u32> &pos, const std::vector<double> &val, u32 stride, u32 ns, double scale,
                    u32 lp, u32 ext = 0);

@@ -383,6 +383,47 @@ def test_power_of_two_keys_bit_exact(G, name):
             assert_same(ctx, g, he, he.rotate_naf(oct_, r, cache))
 
 
+@pytest.mark.parametrize("name", ["lenet1", "m5n"])
+def test_mask_budget_streams_masks_bit_identical(G, name):
+    """With a mask budget smaller than a convolution's masks, the masks are encoded at
+    every inference in output-channel groups (here one channel per group): the
+    ciphertexts equal the cached-mask model's, eagerly and through a CUDA graph."""
+    if name == "lenet1":
+        model, Wi, Hi, C = W.lenet1(), 28, 28, 1
+        P = W.small_params("lenet1", 11)
+    else:
+        model, Wi, Hi, C = W.m5_narrow(), 32, 32, 3
+        P = dict(logn=13, data_bits=[60] + [40] * 8, special_bits=[60, 60, 60], dnum=3, log2_scale=40)
+    stride, levels, steps = G.plan(model, Wi, Hi)
+    ctx = G.Context(seed=W.KEY_SEED, **P)
+    ctx.keygen(steps)
+    ct = ctx.encrypt(W.images(1, Hi, Wi, C=C), 1, stride, W.ENC_SEED)
+    ref = ctx.export(ctx.compile(model, Wi, Hi, 1).infer(ct, use_graph=True))
+    m = ctx.compile(model, Wi, Hi, 1)
+    m.set_mask_budget(1)
+    assert np.array_equal(ctx.export(m.infer(ct)), ref)
+    assert np.array_equal(ctx.export(m.infer(ct, use_graph=True)), ref)
+    assert np.array_equal(ctx.export(m.infer(ct, use_graph=True)), ref)
+
+
+@pytest.mark.slow
+def test_m5_ring_2_15_with_mask_budget(G):
+    """M5 at N = 2^15 (five 3x32x32 samples per ciphertext): its convolutions' masks
+    (~200 GB if kept) are encoded per inference within a 24 GB budget; logits against the
+    FP64 CNN."""
+    model, Wi, Hi = W.paper_model("M5")
+    stride, levels, steps = G.plan(model, Wi, Hi)
+    P = dict(logn=15, data_bits=[60] + [40] * levels, special_bits=[60, 60, 60], dnum=3, log2_scale=40)
+    ctx = G.Context(seed=W.KEY_SEED, **P)
+    ctx.keygen(steps)
+    imgs = W.images(5, 32, 32, C=3)
+    m = ctx.compile(model, Wi, Hi, 5)
+    m.set_mask_budget(24 << 30)
+    logits = ctx.decrypt(m.infer(ctx.encrypt(imgs, 5, stride, W.ENC_SEED), use_graph=True), 10)
+    for b in range(5):
+        assert np.abs(logits[b] - cnn.forward(imgs[b], model)).max() < 1e-3
+
+
 def test_pack_and_drop_level_bit_exact(G):
     """Batch combining (Sec. III-B) of three ciphertexts carrying 1, 2 and 1 samples,
     and Drop-Level (Sec. IV-A): the chain has two more levels than M7 consumes, so
