@@ -252,8 +252,9 @@ def flatten(be, xs, lay: Layout):
         cur = [masked_rotation_sum(x, masks, steps) for x in cur]
     CH = len(cur)
     if stages and not merge_last_stage(len(stages[-1][1]), CH):
-        last = stages.pop()
+        last = stages[-1]
         cur = [masked_rotation_sum(x, *last) for x in cur]
+        stages = []            # every stage applied; the packing follows on its own
     if not stages:
         acc = be.lincomb_diag(cur, [-o * W * H for o in range(CH)]) if CH > 1 else cur[0]
     elif CH == 1:

@@ -170,3 +170,31 @@ def test_power_of_two_keys_model_logits():
     for b in range(2):
         ref = cnn.forward(sig[b], model, dims=1)
         assert np.abs(dec[b * pl["stride"]: b * pl["stride"] + 5] - ref).max() < 1e-3
+
+
+def test_merged_flatten_packing_decrypts_like_separate_stages(monkeypatch):
+    """The flatten's last masked stage merged with the channel packing (one combination,
+    one ModDown) and evaluated separately (stage, rescale, then the packing) decrypt to
+    the same values on the CKKS oracle; the ciphertexts differ only by key-switch rounding."""
+    model = W.lenet1()[:7]                          # up to and including the flatten
+    pl = layers.plan(W.lenet1(), 28, 28)
+    P = W.small_params("lenet1", 11)
+    he = ckks.Ckks(seed=W.KEY_SEED, **P)
+    steps = set(pl["steps"])
+    monkeypatch.setattr(layers, "MERGE_MAX_STEPS", 0)
+    steps |= set(layers.plan(W.lenet1(), 28, 28)["steps"])
+    he.keygen(sorted(steps))
+    img = W.images(1)
+    x = np.zeros(he.n // 2)
+    x[:784] = img[0].reshape(-1)
+    lay = layers.input_layout(28, 28, pl["stride"], 1, he.n // 2)
+    ct = he.encrypt(x, W.ENC_SEED)
+    sep, _ = layers.run_model(layers.HeBackend(he), ct, model, lay)
+    monkeypatch.setattr(layers, "MERGE_MAX_STEPS", 128)
+    mer, lay2 = layers.run_model(layers.HeBackend(he), ct, model, lay)
+    assert mer[0].lp == sep[0].lp and abs(mer[0].scale - sep[0].scale) < 1e-9 * sep[0].scale
+    a, b = he.decrypt(mer[0])[:192], he.decrypt(sep[0])[:192]
+    assert np.abs(a - b).max() < 1e-6 and not np.array_equal(mer[0].d, sep[0].d)
+    # and both are the FP64 CNN's flattened features
+    feats = cnn.forward(img[0], model)
+    assert np.abs(a - feats).max() < 1e-4

@@ -283,3 +283,17 @@ def test_approx_relu_folds_the_pooling_factor():
     ref = cnn.forward(img[0], model)
     assert np.abs(y.v[:len(ref)] - ref).max() < 1e-12
     assert np.all(y.v[len(ref):lay.stride] == 0)
+
+
+@pytest.mark.parametrize("co", [16, 17])
+def test_flatten_merge_boundary_on_the_slot_simulator(co):
+    """Pooled flatten with 8 rows: merged with the packing of 16 channels (128 steps), kept
+    separate for 17 (136): both equal the FP64 CNN."""
+    rng = np.random.default_rng(co)
+    model = [{"op": "conv2d", "w": rng.normal(0, 0.1, (co, 1, 5, 5)), "b": rng.normal(0, 0.1, co), "stride": 1},
+             {"op": "square"}, {"op": "avgpool", "k": 3}, {"op": "flatten"},
+             {"op": "fc", "w": rng.normal(0, 0.1, (10, co * 64)), "b": rng.normal(0, 0.1, 10)}]
+    img = W.images(1)
+    y, _, be, pl = run_sim(model, img, 28, 28, 2, 2048)
+    ref = cnn.forward(img[0], model)
+    assert np.abs(y.v[:10] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
