@@ -383,6 +383,24 @@ def test_power_of_two_keys_bit_exact(G, name):
             assert_same(ctx, g, he, he.rotate_naf(oct_, r, cache))
 
 
+@pytest.mark.parametrize("co", [16, 17])
+def test_flatten_merge_boundary_bit_exact(G, co):
+    """A pooled flatten with 8 rows over 16 channels (merged with the packing: 128 steps)
+    and over 17 (stages and packing separate): bit-exact against the oracle."""
+    rng = np.random.default_rng(co)
+    model = [{"op": "conv2d", "w": rng.normal(0, 0.1, (co, 1, 5, 5)), "b": rng.normal(0, 0.1, co), "stride": 1},
+             {"op": "square"}, {"op": "avgpool", "k": 3}, {"op": "flatten"},
+             {"op": "fc", "w": rng.normal(0, 0.1, (10, co * 64)), "b": rng.normal(0, 0.1, 10)}]
+    stride, levels, steps = G.plan(model, 28, 28)
+    P = dict(logn=12, data_bits=[60] + [40] * levels, special_bits=[60, 60], dnum=3, log2_scale=40)
+    ctx, he = make_pair(G, P, steps)
+    img = W.images(1)
+    out = ctx.compile(model, 28, 28, 1).infer(ctx.encrypt(img, 1, stride, W.ENC_SEED), use_graph=True)
+    want = run_oracle_model(he, model, img, 28, 28, stride, 1, W.ENC_SEED)
+    assert_same(ctx, out, he, want)
+    assert np.abs(ctx.decrypt(out, 10)[0] - cnn.forward(img[0], model)).max() < 1e-3
+
+
 @pytest.mark.parametrize("name", ["lenet1", "m5n"])
 def test_mask_budget_streams_masks_bit_identical(G, name):
     """With a mask budget smaller than a convolution's masks, the masks are encoded at
