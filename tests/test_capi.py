@@ -104,3 +104,22 @@ def test_planner_rejects_bad_models(lib):
     bad_fc = W.lenet1()[:-1] + [{"op": "fc", "w": np.zeros((10, 100)), "b": np.zeros(10)}]
     with pytest.raises(HeError):
         lib.plan(bad_fc, 28, 28)
+
+
+@pytest.mark.parametrize("case", ["1d_pool_merged", "1d_pool_separate", "conv_two_stages_separate"])
+def test_planner_flatten_variants(lib, case):
+    rng = np.random.default_rng(7)
+    if case.startswith("1d"):
+        co = 4 if case.endswith("merged") else 40
+        model = [{"op": "conv1d", "w": rng.normal(0, 0.1, (co, 1, 3)), "b": rng.normal(0, 0.1, co), "stride": 1},
+                 {"op": "square"}, {"op": "avgpool", "k": 2}, {"op": "flatten"},
+                 {"op": "fc", "w": rng.normal(0, 0.1, (5, co * 31)), "b": rng.normal(0, 0.1, 5)}]
+        Wi, Hi = 64, 1
+    else:
+        model = [{"op": "conv2d", "w": rng.normal(0, 0.1, (17, 1, 4, 4)), "b": rng.normal(0, 0.1, 17), "stride": 3},
+                 {"op": "square"}, {"op": "flatten"},
+                 {"op": "fc", "w": rng.normal(0, 0.1, (10, 17 * 81)), "b": rng.normal(0, 0.1, 10)}]
+        Wi, Hi = 28, 28
+    stride, levels, steps = lib.plan(model, Wi, Hi)
+    p = olayers.plan(model, Wi, Hi, 1 if Hi == 1 else 2)
+    assert stride == p["stride"] and levels == p["levels"] and steps == p["steps"]

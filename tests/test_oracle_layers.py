@@ -297,3 +297,26 @@ def test_flatten_merge_boundary_on_the_slot_simulator(co):
     y, _, be, pl = run_sim(model, img, 28, 28, 2, 2048)
     ref = cnn.forward(img[0], model)
     assert np.abs(y.v[:10] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("case", ["1d_pool_merged", "1d_pool_separate", "conv_two_stages_separate"])
+def test_flatten_variants_on_the_slot_simulator(case):
+    """Flatten after 1-D pooling (one masked stage, merged with the packing of 4 channels or
+    kept separate for 40: 32 * 40 > 128 steps) and after a strided 2-D convolution with two
+    masked stages over 17 channels (kept separate): equal to the FP64 CNN."""
+    rng = np.random.default_rng(7)
+    if case.startswith("1d"):
+        co = 4 if case.endswith("merged") else 40
+        model = [{"op": "conv1d", "w": rng.normal(0, 0.1, (co, 1, 3)), "b": rng.normal(0, 0.1, co), "stride": 1},
+                 {"op": "square"}, {"op": "avgpool", "k": 2}, {"op": "flatten"},
+                 {"op": "fc", "w": rng.normal(0, 0.1, (5, co * 31)), "b": rng.normal(0, 0.1, 5)}]
+        x, Wi, Hi, dims = W.signals(1, 64)[:, 0], 64, 1, 1
+    else:
+        model = [{"op": "conv2d", "w": rng.normal(0, 0.1, (17, 1, 4, 4)), "b": rng.normal(0, 0.1, 17), "stride": 3},
+                 {"op": "square"}, {"op": "flatten"},
+                 {"op": "fc", "w": rng.normal(0, 0.1, (10, 17 * 81)), "b": rng.normal(0, 0.1, 10)}]
+        x, Wi, Hi, dims = W.images(1), 28, 28, 2
+    pl = layers.plan(model, Wi, Hi, dims)
+    y, _, _, _ = run_sim(model, x, Wi, Hi, dims, 1 << max(11, int(np.ceil(np.log2(pl["stride"])))))
+    ref = cnn.forward(x[0], model, dims=dims)
+    assert np.abs(y.v[:len(ref)] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
