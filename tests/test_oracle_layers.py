@@ -299,7 +299,8 @@ def test_flatten_merge_boundary_on_the_slot_simulator(co):
     assert np.abs(y.v[:10] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
 
 
-@pytest.mark.parametrize("case", ["1d_pool_merged", "1d_pool_separate", "conv_two_stages_separate"])
+@pytest.mark.parametrize("case", ["1d_pool_merged", "1d_pool_separate", "conv_two_stages_separate",
+                                  "one_channel_pool", "one_channel_conv"])
 def test_flatten_variants_on_the_slot_simulator(case):
     """Flatten after 1-D pooling (one masked stage, merged with the packing of 4 channels or
     kept separate for 40: 32 * 40 > 128 steps) and after a strided 2-D convolution with two
@@ -311,6 +312,15 @@ def test_flatten_variants_on_the_slot_simulator(case):
                  {"op": "square"}, {"op": "avgpool", "k": 2}, {"op": "flatten"},
                  {"op": "fc", "w": rng.normal(0, 0.1, (5, co * 31)), "b": rng.normal(0, 0.1, 5)}]
         x, Wi, Hi, dims = W.signals(1, 64)[:, 0], 64, 1, 1
+    elif case == "one_channel_pool":
+        model = [{"op": "conv2d", "w": rng.normal(0, 0.1, (1, 1, 5, 5)), "b": rng.normal(0, 0.1, 1), "stride": 1},
+                 {"op": "avgpool", "k": 2}, {"op": "flatten"},
+                 {"op": "fc", "w": rng.normal(0, 0.1, (10, 144)), "b": rng.normal(0, 0.1, 10)}]
+        x, Wi, Hi, dims = W.images(1), 28, 28, 2
+    elif case == "one_channel_conv":
+        model = [{"op": "conv2d", "w": rng.normal(0, 0.1, (1, 1, 4, 4)), "b": rng.normal(0, 0.1, 1), "stride": 3},
+                 {"op": "flatten"}, {"op": "fc", "w": rng.normal(0, 0.1, (10, 81)), "b": rng.normal(0, 0.1, 10)}]
+        x, Wi, Hi, dims = W.images(1), 28, 28, 2
     else:
         model = [{"op": "conv2d", "w": rng.normal(0, 0.1, (17, 1, 4, 4)), "b": rng.normal(0, 0.1, 17), "stride": 3},
                  {"op": "square"}, {"op": "flatten"},
