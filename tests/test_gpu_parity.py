@@ -401,6 +401,31 @@ def test_flatten_merge_boundary_bit_exact(G, co):
     assert np.abs(ctx.decrypt(out, 10)[0] - cnn.forward(img[0], model)).max() < 1e-3
 
 
+@pytest.mark.parametrize("case", ["one_channel_pool", "1d_pool_merged"])
+def test_flatten_shapes_bit_exact(G, case):
+    """A one-channel flatten after pooling (no packing) and a 1-D pooled flatten whose single
+    stage is merged with the packing of 4 channels: bit-exact against the oracle."""
+    rng = np.random.default_rng(7)
+    if case == "one_channel_pool":
+        model = [{"op": "conv2d", "w": rng.normal(0, 0.1, (1, 1, 5, 5)), "b": rng.normal(0, 0.1, 1), "stride": 1},
+                 {"op": "avgpool", "k": 2}, {"op": "flatten"},
+                 {"op": "fc", "w": rng.normal(0, 0.1, (10, 144)), "b": rng.normal(0, 0.1, 10)}]
+        x, Wi, Hi, dims = W.images(1), 28, 28, 2
+    else:
+        model = [{"op": "conv1d", "w": rng.normal(0, 0.1, (4, 1, 3)), "b": rng.normal(0, 0.1, 4), "stride": 1},
+                 {"op": "square"}, {"op": "avgpool", "k": 2}, {"op": "flatten"},
+                 {"op": "fc", "w": rng.normal(0, 0.1, (5, 124)), "b": rng.normal(0, 0.1, 5)}]
+        x, Wi, Hi, dims = W.signals(1, 64)[:, 0], 64, 1, 1
+    stride, levels, steps = G.plan(model, Wi, Hi)
+    P = dict(logn=11, data_bits=[60] + [40] * levels, special_bits=[60, 60], dnum=3, log2_scale=40)
+    ctx, he = make_pair(G, P, steps)
+    out = ctx.compile(model, Wi, Hi, 1).infer(ctx.encrypt(x, 1, stride, W.ENC_SEED), use_graph=True)
+    want = run_oracle_model(he, model, x, Wi, Hi, stride, 1, W.ENC_SEED, dims=dims)
+    assert_same(ctx, out, he, want)
+    n_out = model[-1]["w"].shape[0]
+    assert np.abs(ctx.decrypt(out, n_out)[0] - cnn.forward(x[0], model, dims=dims)).max() < 1e-3
+
+
 @pytest.mark.parametrize("name", ["lenet1", "m5n"])
 def test_mask_budget_streams_masks_bit_identical(G, name):
     """With a mask budget smaller than a convolution's masks, the masks are encoded at
