@@ -216,15 +216,15 @@ def test_conv_operation_counts(ci, co, k):
     assert be.count["rescale"] == co
 
 
-@pytest.mark.parametrize("din,dout", [(64, 10), (192, 10), (648, 64), (120, 84), (4080, 5)])
+@pytest.mark.parametrize("din,dout", [(64, 10), (192, 10), (648, 64), (120, 84), (4080, 5), (5, 10), (10, 10), (7, 3), (1, 4)])
 def test_fc_operation_counts(din, dout):
     """Sec. IV-D: O(DAT_out) products and O(DAT_in/DAT_out + DAT_out) rotations."""
     rng = np.random.default_rng(1)
     M = rng.normal(size=(dout, din))
     Wv = -(-din // dout) * dout
+    # slots >= 2 * W_vec, so that no step o - W_vec coincides with a step o modulo the slots
     lay = layers.Layout(W_img=din, H_img=1, W=din, H=1, I=1, stride=max(Wv, din), n_samples=1,
-                        slots=1 << int(np.ceil(np.log2(max(Wv, din)))) if max(Wv, din) > 1 else 1, dims=1,
-                        prev="flatten", D=din)
+                        slots=1 << int(np.ceil(np.log2(2 * max(Wv, din)))), dims=1, prev="flatten", D=din)
     be = slotsim.SlotSim()
     x = np.zeros(lay.slots)
     x[:din] = rng.normal(size=din)
@@ -300,7 +300,7 @@ def test_flatten_merge_boundary_on_the_slot_simulator(co):
 
 
 @pytest.mark.parametrize("case", ["1d_pool_merged", "1d_pool_separate", "conv_two_stages_separate",
-                                  "one_channel_pool", "one_channel_conv"])
+                                  "one_channel_pool", "one_channel_conv", "odd_pool"])
 def test_flatten_variants_on_the_slot_simulator(case):
     """Flatten after 1-D pooling (one masked stage, merged with the packing of 4 channels or
     kept separate for 40: 32 * 40 > 128 steps) and after a strided 2-D convolution with two
@@ -312,6 +312,11 @@ def test_flatten_variants_on_the_slot_simulator(case):
                  {"op": "square"}, {"op": "avgpool", "k": 2}, {"op": "flatten"},
                  {"op": "fc", "w": rng.normal(0, 0.1, (5, co * 31)), "b": rng.normal(0, 0.1, 5)}]
         x, Wi, Hi, dims = W.signals(1, 64)[:, 0], 64, 1, 1
+    elif case == "odd_pool":   # 27 x 27 after the convolution: pooling by 2 drops the last row and column
+        model = [{"op": "conv2d", "w": rng.normal(0, 0.1, (3, 1, 2, 2)), "b": rng.normal(0, 0.1, 3), "stride": 1},
+                 {"op": "square"}, {"op": "avgpool", "k": 2}, {"op": "flatten"},
+                 {"op": "fc", "w": rng.normal(0, 0.1, (10, 3 * 169)), "b": rng.normal(0, 0.1, 10)}]
+        x, Wi, Hi, dims = W.images(1), 28, 28, 2
     elif case == "one_channel_pool":
         model = [{"op": "conv2d", "w": rng.normal(0, 0.1, (1, 1, 5, 5)), "b": rng.normal(0, 0.1, 1), "stride": 1},
                  {"op": "avgpool", "k": 2}, {"op": "flatten"},
