@@ -426,6 +426,28 @@ def test_flatten_shapes_bit_exact(G, case):
     assert np.abs(ctx.decrypt(out, n_out)[0] - cnn.forward(x[0], model, dims=dims)).max() < 1e-3
 
 
+def test_fc_shapes_bit_exact(G):
+    """Alg. 2 with DAT_in < DAT_out (12 -> 20: W_vec = DAT_out, a one-term rotation sum),
+    DAT_in = DAT_out (20 -> 20) and a width that is not a multiple (20 -> 7): bit-exact
+    against the oracle, logits against the FP64 CNN."""
+    rng = np.random.default_rng(11)
+    model = [{"op": "conv1d", "w": rng.normal(0, 0.3, (2, 1, 3)), "b": rng.normal(0, 0.1, 2), "stride": 1},
+             {"op": "flatten"},
+             {"op": "fc", "w": rng.normal(0, 0.3, (20, 12)), "b": rng.normal(0, 0.1, 20)},
+             {"op": "fc", "w": rng.normal(0, 0.3, (20, 20)), "b": rng.normal(0, 0.1, 20)},
+             {"op": "fc", "w": rng.normal(0, 0.3, (7, 20)), "b": rng.normal(0, 0.1, 7)}]
+    stride, levels, steps = G.plan(model, 8, 1)
+    P = dict(logn=11, data_bits=[60] + [40] * levels, special_bits=[60, 60], dnum=3, log2_scale=40)
+    ctx, he = make_pair(G, P, steps)
+    x = W.signals(2, 8)[:, 0]
+    out = ctx.compile(model, 8, 1, 2).infer(ctx.encrypt(x, 2, stride, W.ENC_SEED), use_graph=True)
+    want = run_oracle_model(he, model, x, 8, 1, stride, 2, W.ENC_SEED, dims=1)
+    assert_same(ctx, out, he, want)
+    logits = ctx.decrypt(out, 7)
+    for b in range(2):
+        assert np.abs(logits[b] - cnn.forward(x[b], model, dims=1)).max() < 1e-3
+
+
 @pytest.mark.parametrize("name", ["lenet1", "m5n"])
 def test_mask_budget_streams_masks_bit_identical(G, name):
     """With a mask budget smaller than a convolution's masks, the masks are encoded at
