@@ -277,7 +277,9 @@ typedef struct {
                                next batch is formed when the running one completes (larger batches
                                under load, one model's work never queued behind itself) */
     uint32_t exact_batches; /* 0: a batch is padded to a power of two (log2(max_batch)+1 graphs per
-                               model); 1: one graph per batch size 1..max_batch, no padding */
+                               model); 1: one graph per batch size 1..max_batch, no padding.
+                               Under load, max_inflight = 1 with exact_batches = 1 gave the lower
+                               median and tail latency (bench.py --serve uses them) */
 } he_server_opts;
 typedef struct {
     uint64_t requests;        /* finished requests */
