@@ -571,16 +571,23 @@ def test_layer_calls_match_model(G):
 
 
 def test_cnn1d_logits(G):
-    P = dict(W.PARAMS["cnn1d"])
-    P["logn"] = 13
+    """The 1-D CNN workload at its configured size: N = 2^14, [60, 40 x 6 | 60], 32
+    ciphertexts of two signals each (64 samples) in one graph launch; every sample's
+    logits against the FP64 CNN, and one ciphertext of the batch equals it run alone."""
+    P = W.PARAMS["cnn1d"]
     model = W.cnn1d()
     stride, levels, steps = G.plan(model, 1024, 1)
     ctx = G.Context(seed=W.KEY_SEED, **P)
     ctx.keygen(steps)
-    sig = W.signals(1)[:, 0]
-    m = ctx.compile(model, 1024, 1, 1)
-    out = m.infer(ctx.encrypt(sig, 1, stride, W.ENC_SEED))
-    assert np.abs(ctx.decrypt(out, 5)[0] - cnn.forward(sig[0], model, dims=1)).max() < 1e-3
+    sig = W.signals(64)[:, 0]
+    m = ctx.compile(model, 1024, 1, 2)
+    out = m.infer(ctx.encrypt(sig, 2, stride, W.ENC_SEED), use_graph=True)
+    assert out.batch == 32
+    logits = ctx.decrypt(out, 5)
+    for k in range(64):
+        assert np.abs(logits[k] - cnn.forward(sig[k], model, dims=1)).max() < 1e-3, k
+    alone = m.infer(ctx.encrypt(sig[62:], 2, stride, W.ENC_SEED + 31))
+    assert np.array_equal(ctx.export(out)[31], ctx.export(alone)[0])
 
 
 def test_error_codes(G, pair_small):
