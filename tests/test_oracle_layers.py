@@ -335,3 +335,19 @@ def test_flatten_variants_on_the_slot_simulator(case):
     y, _, _, _ = run_sim(model, x, Wi, Hi, dims, 1 << max(11, int(np.ceil(np.log2(pl["stride"])))))
     ref = cnn.forward(x[0], model, dims=dims)
     assert np.abs(y.v[:len(ref)] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_approx_relu_coefficients_are_the_papers():
+    """Both oracle parts (the layer algorithm and the FP64 CNN) use the printed polynomial,
+    and after average pooling by c the layer's coefficients are the paper's folded ones."""
+    g = GOLD["approx_relu"]
+    assert (layers.RELU_C0, layers.RELU_C1, layers.RELU_C2) == (g["c0"], g["c1"], g["c2"])
+    x = np.linspace(-3, 3, 13)
+    got = cnn.forward(x.reshape(1, -1), [{"op": "approx_relu"}])
+    assert np.array_equal(got, g["c0"] + g["c1"] * x + g["c2"] * x * x)
+    # one pooled value v = mean of a c x c block: the layer sees the block sum s = c^2 v with p = 1/c^2
+    for c in (2, 3):
+        s = 1.7
+        folded = g["c0"] + g["c1"] / c ** 2 * s + g["c2"] / c ** 4 * s * s
+        p = 1.0 / c ** 2
+        assert abs((layers.RELU_C0 + layers.RELU_C1 * p * s + layers.RELU_C2 * p * p * s * s) - folded) < 1e-15
