@@ -104,6 +104,19 @@ def test_planner_rejects_bad_models(lib):
     bad_fc = W.lenet1()[:-1] + [{"op": "fc", "w": np.zeros((10, 100)), "b": np.zeros(10)}]
     with pytest.raises(HeError):
         lib.plan(bad_fc, 28, 28)
+    conv2d_on_signal = [{"op": "conv2d", "w": np.zeros((1, 1, 3, 3)), "b": np.zeros(1), "stride": 1}]
+    with pytest.raises(HeError):
+        lib.plan(conv2d_on_signal, 64, 1)
+    channels_on_signal = [{"op": "conv1d", "w": np.zeros((2, 3, 3)), "b": np.zeros(2), "stride": 1}]
+    with pytest.raises(HeError):
+        lib.plan(channels_on_signal, 64, 1)      # several input channels need a 2-D image
+    big_pool = [{"op": "conv2d", "w": np.zeros((1, 1, 3, 3)), "b": np.zeros(1), "stride": 1},
+                {"op": "avgpool", "k": 30}]
+    with pytest.raises(HeError):
+        lib.plan(big_pool, 28, 28)
+    fc_first = [{"op": "fc", "w": np.zeros((10, 784)), "b": np.zeros(10)}]
+    with pytest.raises(HeError):
+        lib.plan(fc_first, 28, 28)               # FC needs a flattened input
 
 
 @pytest.mark.parametrize("case", ["1d_pool_merged", "1d_pool_separate", "conv_two_stages_separate"])
