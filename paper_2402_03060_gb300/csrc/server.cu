@@ -5,12 +5,13 @@
 // and returns encrypted results.  This loop serves several compiled models
 // (possibly on different contexts and ring degrees) from one host thread:
 //   * each model has a FIFO queue; a request is one ciphertext batch (he_ct);
-//   * whenever a model has fewer than two batches in flight, the worker takes
-//     the queued requests in arrival order, as many as fit in max_batch
-//     ciphertexts, gathers them into one batch padded to a power of two (so a
-//     model sees at most log2(max_batch)+1 batch shapes, each replayed from its
-//     own CUDA graph) and launches it on the model's stream -- requests that
-//     arrive while a batch runs join the next one (continuous batching);
+//   * whenever a model has fewer than max_inflight batches in flight (2 by
+//     default), the worker takes the queued requests in arrival order, as many as
+//     fit in max_batch ciphertexts, gathers them into one batch -- padded to a
+//     power of two (a model sees at most log2(max_batch)+1 batch shapes) or, with
+//     exact_batches, of its own size -- replayed from that shape's CUDA graph, and
+//     launches it on the model's stream; requests that arrive while a batch runs
+//     join the next one (continuous batching);
 //   * completion is signalled from the stream (cudaLaunchHostFunc), the result
 //     batch is split into per-request views, and waiting clients are woken;
 //   * admission: a model is accepted only if the device bytes it holds (keys,
