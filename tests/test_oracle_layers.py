@@ -351,3 +351,22 @@ def test_approx_relu_coefficients_are_the_papers():
         folded = g["c0"] + g["c1"] / c ** 2 * s + g["c2"] / c ** 4 * s * s
         p = 1.0 / c ** 2
         assert abs((layers.RELU_C0 + layers.RELU_C1 * p * s + layers.RELU_C2 * p * p * s * s) - folded) < 1e-15
+
+
+@pytest.mark.parametrize("name", ["M1", "M4", "M5", "M6", "M7"])
+def test_workload_shapes_are_the_paper_tables(name):
+    """The workloads' model builders use exactly the layer parameters of the paper's tables
+    (golden fixture), and the input size each table implies."""
+    g = GOLD["mult_per_layer"][name]
+    spec, Wi, Hi = W.PAPER_MODELS[name]
+    assert [list(l) for l in spec] == g["layers"]
+    assert [Wi, Hi] == g["input"]
+    model, _, _ = W.paper_model(name)
+    for l, m in zip(g["layers"], model):
+        assert m["op"] == l[0]
+        if l[0] in ("conv2d", "conv1d"):
+            assert m["w"].shape[:2] == (l[2], l[1]) and m["w"].shape[-1] == l[3] and m["stride"] == l[4]
+        elif l[0] == "fc":
+            assert m["w"].shape == (l[2], l[1])
+        elif l[0] == "avgpool":
+            assert m["k"] == l[1]
