@@ -370,3 +370,17 @@ def test_workload_shapes_are_the_paper_tables(name):
             assert m["w"].shape == (l[2], l[1])
         elif l[0] == "avgpool":
             assert m["k"] == l[1]
+
+
+@pytest.mark.parametrize("name,build", [("M2", W.lenet1), ("M3", W.m3_relu)])
+def test_lenet1_and_m3_builders_are_the_paper_tables(name, build):
+    g = GOLD["mult_per_layer"][name]
+    model = build()
+    assert [m["op"] for m in model] == [l[0] for l in g["layers"]]
+    for l, m in zip(g["layers"], model):
+        if l[0] == "conv2d":
+            assert m["w"].shape == (l[2], l[1], l[3], l[3]) and m["stride"] == l[4]
+        elif l[0] == "fc":
+            assert m["w"].shape == (l[2], l[1])
+        elif l[0] == "avgpool":
+            assert m["k"] == l[1]
