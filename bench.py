@@ -106,6 +106,9 @@ def parse():
                     help="serving benchmark instead: Poisson arrivals over a LeNet-1 / LeNet-5 / 1-D CNN mix through "
                          "the continuous-batching loop; prints request-latency percentiles")
     ap.add_argument("--requests", type=int, default=600, help="requests of the --serve trace")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the default run's short serving trace")
+    ap.add_argument("--no-serve", action="store_true", help="skip the default run's serving leg")
     ap.add_argument("--rate", type=float, default=200.0, help="arrivals per second of the --serve trace")
     ap.add_argument("--serve-max-batch", type=int, default=8, help="ciphertexts per batch of one model")
     ap.add_argument("--serve-inflight", type=int, default=1, help="batches of one model in flight")
@@ -224,11 +227,14 @@ SERVE_MODELS = (  # name, layers, image W, H, samples per ciphertext, logits
 )
 
 
-def run_serve(args, local):
+def run_serve(args, local, requests=None, full=True):
     """Poisson(rate) requests, each one sample of a uniformly drawn model; the
     clients' ciphertexts are encrypted beforehand and submitted to the serving
     loop at their arrival times; a second thread collects the results.
-    Latency = submit to completion on the device."""
+    Latency = submit to completion on the device.  full=False (the default
+    benchmark's serving leg): the main trace only, no per-layer breakdown and no
+    second trace at 80 % of capacity."""
+    requests = requests or args.requests
     import threading
     import torch
     torch.cuda.set_device(local)
@@ -269,16 +275,19 @@ def run_serve(args, local):
             ctx.sync()
             row[f"ms_batch{b}"] = round((time.perf_counter() - t) / 3 * 1e3, 2)
         ct = ctx.encrypt(x, spc, strides[i], W.ENC_SEED)
-        ctx.profile_begin()
-        models[i].infer(ct)
-        tagged = ctx.profile_end()
+        tagged = {}
+        if full:
+            ctx.profile_begin()
+            models[i].infer(ct)
+            tagged = ctx.profile_end()
         layers_ms, kern_ms = {}, {}
         for key, (nl, ms, byt, ops) in tagged.items():
             lay, _, kern = key.rpartition("/")
             layers_ms[lay or "other"] = round(layers_ms.get(lay or "other", 0.0) + ms, 2)
             kern_ms[kern] = round(kern_ms.get(kern, 0.0) + ms, 2)
-        row["eager_batch8_layers_ms"] = layers_ms
-        row["eager_batch8_kernels_ms"] = dict(sorted(kern_ms.items(), key=lambda kv: -kv[1])[:8])
+        if full:
+            row["eager_batch8_layers_ms"] = layers_ms
+            row["eager_batch8_kernels_ms"] = dict(sorted(kern_ms.items(), key=lambda kv: -kv[1])[:8])
         service[name] = row
     def trace(rate, n, seed):
         """Replay n Poisson(rate) arrivals; latencies as the loop reports them."""
@@ -337,19 +346,21 @@ def run_serve(args, local):
                 "throughput_req_per_s": round(n / (done_t.max() - t0), 2), "per_model": per_model}
 
     offered = args.rate / len(SERVE_MODELS) * sum(v["ms_batch8"] / 8 for v in service.values()) / 1e3
-    main = trace(args.rate, args.requests, W.ARRIVAL_SEED)
+    main = trace(args.rate, requests, W.ARRIVAL_SEED)
     st = srv.stats()
     for i, (name, *_rest) in enumerate(SERVE_MODELS):
         si = srv.stats(i)
         main["per_model"][name].update({"batches": si["batches"], "mean_batch_cts": round(si["mean_batch"], 2)})
-    # the same mix at 80 % of the capacity the batch-of-8 service costs allow
-    knee_rate = round(0.8 * args.rate / max(offered, 1e-9), 1)
-    knee = trace(knee_rate, args.requests, W.ARRIVAL_SEED + 1)
+    knee = None
+    if full:
+        # the same mix at 80 % of the capacity the batch-of-8 service costs allow
+        knee_rate = round(0.8 * args.rate / max(offered, 1e-9), 1)
+        knee = trace(knee_rate, requests, W.ARRIVAL_SEED + 1)
     srv.close()
     return {"metric": "serving request latency p99 (Poisson arrivals, LeNet-1 / LeNet-5 / 1-D CNN mix)",
             "value": main["p99_ms"], "unit": "ms", "n_gpus": 1, "higher_is_better": False,
             "p50_ms": main["p50_ms"], "max_ms": main["max_ms"], "throughput_req_per_s": main["throughput_req_per_s"],
-            "requests": args.requests, "rate_per_s": args.rate,
+            "requests": requests, "rate_per_s": args.rate,
             "loop_stats": {"p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
                            "mean_batch_cts": round(st["mean_batch"], 2), "batches": st["batches"]},
             "dtype": "u64 (RNS residues), f64 encode", "data": "synthetic",
@@ -475,7 +486,7 @@ def run_ours(args, rank, world, local):
         lk = layer or "encrypt/decrypt"
         layer_ms[lk] = layer_ms.get(lk, 0.0) + ms
     # measured integer roofline: register-only throughput of the primitives
-    bfly_peak, mac_peak, _barrett_peak = ctx.ubench()
+    bfly_peak, mac_peak, _barrett_peak, ub_sms = ctx.ubench()
     stats = {k: tuple(v) for k, v in stats.items()}
 
     # one-op-per-launch path: each ciphertext alone, eager
@@ -541,11 +552,12 @@ def run_ours(args, rank, world, local):
         roof.update({"traffic": ncu_traffic(name, ctx.tuning()), "launches_per_step": nl, "avg_launch_us": round(tms / nl * 1e3, 2),
                      "share_of_eager_step": round(share, 3),
                      "primitive_peaks": {"butterflies_per_s": float(f"{bfly_peak:.4g}"),
-                                         "mac128_per_s": float(f"{mac_peak:.4g}")},
-                     "kernels": kern_rows,
-                     "layers_ms": {k: round(v, 3) for k, v in layer_ms.items()},
-                     "top_layer_kernels_ms": {k: round(v[1], 3) for k, v in
-                                              sorted(tagged.items(), key=lambda kv: -kv[1][1])[:12]}})
+                                         "mac128_per_s": float(f"{mac_peak:.4g}"),
+                                         "barrett_per_s": float(f"{_barrett_peak:.4g}"), "sm_count": int(ub_sms)}})
+    profile = {"kernels": kern_rows if stats else {},
+               "layers_ms": {k: round(v, 3) for k, v in layer_ms.items()},
+               "top_layer_kernels_ms": {k: round(v[1], 3) for k, v in
+                                        sorted(tagged.items(), key=lambda kv: -kv[1][1])[:12]}}
     res = {
         "metric": METRIC, "value": round(whole_job_rate(args.samples, world, ms_step), 3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 3),
@@ -560,9 +572,11 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": round(total_samples / (ms_e2e / 1e3), 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(args.samples * 784 * 8), "d2h_bytes_per_step": int(n_ct * SPC * 10 * 8)},
         "gpu_launches": int(launches),
-        "plain": plain,
         "roofline": roof,
+        "profile": profile,
         "clocks": clk,
+        "plain": round(plain["value"], 3) if plain else None,
+        "plain_detail": plain,
     }
     res["_logits"] = (chk, imgs, layers)
     return res, ctx
@@ -675,8 +689,27 @@ def main():
         for k in list(range(0, len(imgs), max(1, len(imgs) // 7)))[:8] + [len(imgs) - 1]:
             worst = max(worst, float(np.abs(chk[k] - cnn.forward(imgs[k], layers)).max()))
         res["max_abs_logit_err_vs_fp64"] = worst
+    if rank == 0 and world == 1 and not args.no_serve:
+        # the serving mix (Poisson arrivals over LeNet-1 / LeNet-5 / 1-D CNN, continuous batching),
+        # a short trace: request latency percentiles beside the batched throughput
+        del ctx
+        try:
+            sv = run_serve(args, local, requests=args.serve_requests, full=False)
+            res["serve"] = {"p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "max_ms": sv["max_ms"],
+                            "throughput_req_per_s": sv["throughput_req_per_s"], "requests": sv["requests"],
+                            "rate_per_s": sv["rate_per_s"], "offered_load": sv["offered_load"],
+                            "mean_batch_cts": sv["loop_stats"]["mean_batch_cts"], "setup_s": sv["setup_s"],
+                            "workload": "Poisson arrivals, one-sample requests, uniform LeNet-1 (N=2^14) / "
+                                        "LeNet-5 (N=2^15) / 1-D CNN (N=2^14) mix, dnum=3 keys resident, "
+                                        "max 8 ciphertexts per batch"}
+        except Exception as e:   # the throughput line stands without it
+            res["serve"] = {"error": f"{type(e).__name__}: {e}"[:300]}
     if rank == 0:
-        print(json.dumps(res))
+        # the bulky per-kernel profile first, the headline extras last (short tails stay readable)
+        order = [k for k in res if k not in ("profile", "plain_detail", "cpu_baseline", "max_abs_logit_err_vs_fp64",
+                                             "clocks", "plain", "serve")]
+        tail = ["profile", "plain_detail", "cpu_baseline", "max_abs_logit_err_vs_fp64", "clocks", "plain", "serve"]
+        print(json.dumps({k: res[k] for k in order + [k for k in tail if k in res]}))
 
 
 if __name__ == "__main__":

@@ -92,6 +92,25 @@ he_status he_keygen(he_ctx *ctx, const int32_t *rot_steps, size_t n_steps);
  * context to one key per step.  Errors: HE_ENOMEM, HE_ECUDA. */
 he_status he_keygen_pow2(he_ctx *ctx);
 
+/* Evaluation schedule of the layer calls on this context and of the models compiled on it
+ * from then on (a compiled model keeps the schedule it was compiled with).
+ *   HE_SCHEDULE_FUSED (0, the default): the rotations of one input share one ModUp
+ *     (hoisting); a linear combination of rotations (convolution, pooling, the flatten's
+ *     stages, FC, channel packing) is accumulated over Q_l u P with one ModDown per output;
+ *     a ModDown followed by a rescale is one division by q_top * P; the flatten's last
+ *     stage may be merged with the channel packing.  The same slot values as the literal
+ *     schedule, other ciphertext bits (other key-switch and rescale rounding).
+ *   HE_SCHEDULE_LITERAL (1): the paper's order, one operation at a time -- Algorithm 1
+ *     (Sec. IV-B), the pooling of Sec. IV-C, the flatten steps of Sec. IV-E and Algorithm 2
+ *     (Sec. IV-D) as listed: every Rot is its own key switch (ModUp, inner product,
+ *     ModDown, plus sigma_g(c0)), Mul (P) by the mask over Q_l, Add, then the centred
+ *     rescale; square = tensor, relinearise (ModDown), rescale; a flatten stage multiplies
+ *     the masks first and rotates the products; the channel packing follows the last
+ *     stage.  Its models need the steps he_model_plan_schedule gives for it.
+ * Errors: HE_EINVAL (unknown schedule). */
+enum { HE_SCHEDULE_FUSED = 0, HE_SCHEDULE_LITERAL = 1 };
+he_status he_context_set_schedule(he_ctx *ctx, uint32_t schedule);
+
 /* Flatten and encrypt (paper Sec. III-A/B): x is [n_samples][H][W] doubles,
  * host memory (x_on_device = 0) or device memory (1).  Sample k goes to
  * ciphertext k / samples_per_ct at slot offset (k % samples_per_ct)*stride,
@@ -214,6 +233,12 @@ typedef struct {
  * steps (to pass to he_keygen).  steps may be NULL to query *n_steps. */
 he_status he_model_plan(const he_layer *layers, size_t n, uint32_t W_img, uint32_t H_img,
                         uint32_t *stride, uint32_t *levels, int32_t *steps, size_t *n_steps);
+/* he_model_plan for a given schedule (HE_SCHEDULE_*): the literal schedule never merges the
+ * flatten's last stage with the channel packing, so its step set differs; he_model_plan is
+ * this call with HE_SCHEDULE_FUSED. */
+he_status he_model_plan_schedule(const he_layer *layers, size_t n, uint32_t W_img, uint32_t H_img,
+                                 uint32_t schedule, uint32_t *stride, uint32_t *levels, int32_t *steps,
+                                 size_t *n_steps);
 /* Compile: copies the weights; plaintext masks are encoded on the device at
  * the first he_infer and cached in the model.  Errors: HE_ENOKEY, HE_ELEVEL, HE_ESLOTS. */
 he_status he_model_compile(he_ctx *ctx, const he_layer *layers, size_t n, uint32_t W_img, uint32_t H_img,
@@ -271,8 +296,9 @@ typedef struct {
     uint32_t max_wait_us;   /* while a model's batch runs, a partial next batch waits up to this long for
                                more requests before it is launched behind it; 0: launch at once */
     uint64_t mem_budget;    /* device bytes for the models (their contexts' pools: keys and cached masks,
-                               and their graph pools) plus the ciphertexts of queued and running
-                               requests; 0: unlimited */
+                               and their graph pools) plus the input ciphertexts of the requests
+                               submitted and not yet collected (queued, running, or finished and
+                               waiting for he_server_wait); 0: unlimited */
     uint32_t max_inflight;  /* batches of one model queued on its stream at once; 0: 2.  With 1, the
                                next batch is formed when the running one completes (larger batches
                                under load, one model's work never queued behind itself) */
@@ -302,8 +328,11 @@ he_status he_server_add_model(he_server *srv, he_model *model, uint32_t *model_i
 /* Queues a request: the ciphertext batch `in` (a fresh encryption of the
  * model's input layout, at most max_batch ciphertexts, on the model's context).
  * The server keeps its own reference to the buffer; the caller may free `in`.
- * HE_ENOMEM when admitting it would exceed the budget (retry after collecting
- * results), HE_EINVAL / HE_ELEVEL when it does not fit the model. */
+ * HE_ENOMEM when admitting it would exceed the budget: the request is not
+ * queued; it is admitted when submitted again after he_server_wait has
+ * collected enough results (admission by memory, paper Sec. III service model:
+ * the server holds every client's ciphertexts until they are returned).
+ * HE_EINVAL / HE_ELEVEL when it does not fit the model. */
 he_status he_server_submit(he_server *srv, uint32_t model_id, const he_ct *in, uint64_t *req_id);
 /* Waits up to timeout_ms for a request and collects it: *out receives the
  * result (caller frees it with he_ct_free; NULL out frees it), *latency_ms
@@ -328,6 +357,16 @@ he_status he_server_simulate(const he_server_opts *opt, uint32_t n_models, const
                              const double *per_ct_us, size_t n_req, const double *arrival_us,
                              const uint32_t *model_of, const uint32_t *cts_of, uint64_t *batch_of,
                              double *latency_ms);
+/* he_server_simulate with memory admission: every simulated ciphertext counts as one
+ * byte of opt->mem_budget (the simulated models hold none) from its request's
+ * submission until the request completes.  A request the budget cannot hold on
+ * arrival is refused (refusals[k] = 1, else 0) and submitted again, in arrival order
+ * behind earlier refused ones, as completions free the budget; its latency counts
+ * from its arrival.  refusals is optional. */
+he_status he_server_simulate_admission(const he_server_opts *opt, uint32_t n_models, const double *base_us,
+                                       const double *per_ct_us, size_t n_req, const double *arrival_us,
+                                       const uint32_t *model_of, const uint32_t *cts_of, uint64_t *batch_of,
+                                       double *latency_ms, uint32_t *refusals);
 
 /* ---- low level ------------------------------------------------------- */
 /* In-place forward (inverse = 0) or inverse negacyclic NTT of n_limbs device
@@ -342,6 +381,8 @@ he_status he_ntt(he_ctx *ctx, uint64_t *data, uint32_t n_limbs, const uint32_t *
  * owned by another allocator.
  * in: device [batch][2][limbs][N] evaluation-form ciphertexts (the he_ct
  * layout); out: device [batch][2][limbs-1][N]; the result equals he_rescale's.
+ * in and out must not overlap (the output's limb stride differs from the
+ * input's, so an in-place call cannot work): overlapping ranges get HE_EINVAL.
  * Work is queued on the context's stream.  The only working memory is a
  * file-scope device array of 2^19 words (4 MiB) held by every GPU that loads
  * the library until the process exits: batch*2*N must not exceed 2^19 (16
@@ -375,7 +416,9 @@ typedef struct {
 /* Measured integer roofline: register-only throughput on this device of the
  * modular primitives the kernels use.  out[0] = lazy NTT butterflies/s,
  * out[1] = 64x64->128-bit multiply-accumulates/s, out[2] = Barrett modular
- * products/s.  Runs a few short kernels on the context's stream and waits. */
+ * products/s, out[3] = the device's SM count (each kernel's grid is that many SMs
+ * times the CTAs per SM it reaches).  out holds 4 doubles.  Runs a few short
+ * kernels on the context's stream and waits. */
 he_status he_ubench(he_ctx *ctx, double *out);
 
 he_status he_profile_begin(he_ctx *ctx);

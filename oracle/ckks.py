@@ -702,6 +702,27 @@ class Ckks:
         c0g = self.automorph_eval(ct.d[0], g)
         return np.concatenate([self.add(a0[:lp], self.mul(c0g, Pq, q), q), a0[lp:]]), a1
 
+    def tensor_square(self, ct: Ct):
+        """(d0, d1, d2) = (a0^2, 2 a0 a1, a1^2): decrypts with (1, s, s^2) to m^2."""
+        q = self.q[: ct.lp]
+        a0, a1 = ct.d[0], ct.d[1]
+        return (self.mul(a0, a0, q), self.add(self.mul(a0, a1, q), self.mul(a1, a0, q), q),
+                self.mul(a1, a1, q))
+
+    def relinearise(self, d, scale: float) -> Ct:
+        """(d0, d1) + KS(d2): the key switch of d2 with the relinearisation key (ModUp,
+        inner product, ModDown of each polynomial) added to (d0, d1)."""
+        d0, d1, d2 = d
+        q = self.q[: d0.shape[0]]
+        k0, k1 = self.keyswitch(d2, self.keys.rlk)
+        return Ct(np.stack([self.add(d0, k0, q), self.add(d1, k1, q)]), scale)
+
+    def square_literal(self, ct: Ct) -> Ct:
+        """Mul (C) of a ciphertext by itself in the textbook order (reading C15), one step
+        at a time: the tensor, relinearisation, then the centred rescale of reading C7."""
+        assert ct.lp >= 2, "level exhausted"
+        return self.rescale(self.relinearise(self.tensor_square(ct), ct.scale * ct.scale))
+
     def square(self, ct: Ct) -> Ct:
         """Ciphertext tensor with itself, relinearisation, rescale (reading C15).
         Relinearisation and rescale end in one division by q_top * P: the key-switch

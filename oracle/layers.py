@@ -220,7 +220,17 @@ def flatten(be, xs, lay: Layout):
     cur = list(xs)
     pending = lay.pending
 
+    literal = getattr(be, "literal", False)
+
     def masked_rotation_sum(x, masks, steps):
+        if literal:
+            # the steps of Sec. IV-E in their order: each mask multiplied with the
+            # ciphertext, each product rotated left, the rotations added; one rescale
+            acc = None
+            for m, s in zip(masks, steps):
+                t = be.rot(be.mul_mask(x, m), s)
+                acc = t if acc is None else be.add(acc, t)
+            return be.rescale(acc)
         rolled = [np.roll(m, -s) for m, s in zip(masks, steps)]
         return be.lincomb_rescale([x], steps, [[rolled]])[0]
 
@@ -251,7 +261,7 @@ def flatten(be, xs, lay: Layout):
     for masks, steps in stages[:-1]:
         cur = [masked_rotation_sum(x, masks, steps) for x in cur]
     CH = len(cur)
-    if stages and not merge_last_stage(len(stages[-1][1]), CH):
+    if stages and not merge_last_stage(len(stages[-1][1]), CH, literal):
         last = stages[-1]
         cur = [masked_rotation_sum(x, *last) for x in cur]
         stages = []            # every stage applied; the packing follows on its own
@@ -276,8 +286,10 @@ def flatten(be, xs, lay: Layout):
 MERGE_MAX_STEPS = 128
 
 
-def merge_last_stage(k: int, ch: int) -> bool:
-    return ch > 1 and k * ch <= MERGE_MAX_STEPS
+def merge_last_stage(k: int, ch: int, literal: bool = False) -> bool:
+    """Whether the fused schedule merges the flatten's last stage with the packing (the
+    paper-order schedule never does)."""
+    return not literal and ch > 1 and k * ch <= MERGE_MAX_STEPS
 
 
 def fc_rot_matrix(M: np.ndarray):
@@ -419,13 +431,16 @@ def run_layers(be, xs, layers, lay: Layout, conv_mode: str = "hoisted"):
     return xs, lay
 
 
-def plan(layers, W_img: int, H_img: int, dims: int = 2):
+def plan(layers, W_img: int, H_img: int, dims: int = 2, schedule: str = "fused"):
     """Layout sizes of Sec. V: the slots one sample needs (the stride), the number
     of levels the model consumes, and the rotation steps it uses.
 
     Stride = max(input W_img*H_img (Theorem 1 keeps every later valid value
     inside it), CH*W*H of each flatten (V-C), W_vec of each FC (V-D)).
+    schedule "literal" (the paper's order, ``HeBackend(literal=True)``) never merges the
+    flatten's last stage with the packing, so its steps are the stages' and the packing's.
     """
+    assert schedule in ("fused", "literal"), schedule
     W, H, I, ch = W_img, H_img, 1, 1
     prev = "input"
     # the input's channels: CH_in of a first convolution (all in one ciphertext)
@@ -470,7 +485,7 @@ def plan(layers, W_img: int, H_img: int, dims: int = 2):
                 if H > 1:
                     levels += 1
                     stage_steps.append([r * (W_img * I - W) for r in range(H)])
-                if stage_steps and merge_last_stage(len(stage_steps[-1]), ch):
+                if stage_steps and merge_last_stage(len(stage_steps[-1]), ch, schedule == "literal"):
                     for st in stage_steps[:-1]:
                         steps |= set(st)
                     steps |= {s - o * W * H for s in stage_steps[-1] for o in range(ch)}
@@ -501,44 +516,66 @@ def plan(layers, W_img: int, H_img: int, dims: int = 2):
 class HeBackend:
     """The CKKS oracle as a layer backend; counts the operations it performs.
 
-    naf=True: the context holds power-of-two Galois keys only (the key set SEAL
-    generates by default).  Every rotation is then a chain of power-of-two rotations
-    (``Ckks.rotate_naf``), and a linear combination of rotations is evaluated as
-    rotate-then-multiply: the rotated ciphertexts of one input (chains sharing their
-    prefixes), the products with the plaintexts over Q_l (Mul (P)) summed, then the
-    rescale (reading C7)."""
+    Three schedules, each bit-compared with the GPU library in the same mode:
 
-    def __init__(self, he, naf: bool = False):
+    * default ("fused"): the rotations of one input share one ModUp (hoisting), a
+      linear combination of rotations is accumulated over Q_l u P with one ModDown
+      per output, ModDown and rescale are one division by q_top * P, and the
+      flatten's last stage may be merged with the channel packing.  Each of these is
+      an evaluation order of the same slot algebra, pinned against the literal
+      schedule by decryption.
+    * literal=True: the paper's order, one operation at a time (Alg. 1, Sec. IV-C,
+      Sec. IV-E, Alg. 2 as printed): every Rot is its own key switch (ModUp, inner
+      product, ModDown, + sigma(c0)); Mul (P) by the mask over Q_l; Add; the rescale
+      of reading C7; square = tensor, relinearise, rescale; the flatten's stages are
+      mask, rotate, add, and the packing follows them.
+    * naf=True: the context holds power-of-two Galois keys only (the key set SEAL
+      generates by default).  Every rotation is then a chain of power-of-two rotations
+      (``Ckks.rotate_naf``), and a linear combination of rotations is evaluated as
+      rotate-then-multiply: the rotated ciphertexts of one input (chains sharing their
+      prefixes), the products with the plaintexts over Q_l (Mul (P)) summed, then the
+      rescale (reading C7)."""
+
+    def __init__(self, he, naf: bool = False, literal: bool = False):
         self.he = he
         self.naf = naf
+        self.literal = literal
         self.count = {"rot": 0, "pmul": 0, "rescale": 0, "square": 0}
 
+    @property
+    def _seq(self) -> bool:
+        """rotate-then-multiply, one rotation at a time (literal or power-of-two keys)"""
+        return self.naf or self.literal
+
+    def _rot1(self, x, r, cache=None):
+        return self.he.rotate_naf(x, r, cache) if self.naf else self.he.rotate(x, r)
+
     def _rots(self, x, steps):
-        cache = {}
-        return [self.he.rotate_naf(x, s, cache) for s in steps]
+        cache = {} if self.naf else None
+        return [self._rot1(x, s, cache) for s in steps]
 
     def rot(self, x, r):
-        self.count["rot"] += 1
-        return self.he.rotate_naf(x, r) if self.naf else self.he.rotate(x, r)
+        self.count["rot"] += 1 if r % (self.he.n // 2) else 0
+        return self._rot1(x, r)
 
     def rot_many(self, x, steps):
         self.count["rot"] += len({s for s in steps if s % (self.he.n // 2)})
-        if self.naf:
+        if self._seq:
             return dict(zip(steps, self._rots(x, steps)))
         return self.he.rotate_hoisted(x, steps)
 
     def lincomb_diag(self, xs, steps):
         m = self.he.n // 2
         self.count["rot"] += len([s for s in steps if s % m])
-        if self.naf:
-            ys = [self.he.rotate_naf(x, s) for x, s in zip(xs, steps)]
+        if self._seq:
+            ys = [self._rot1(x, s) for x, s in zip(xs, steps)]
             acc = ys[0]
             for y in ys[1:]:
                 acc = self.he.ct_add(acc, y)
             return acc
         return self.he.lincomb_diag(xs, steps)
 
-    def _naf_lincomb(self, xs, steps, weights):
+    def _seq_lincomb(self, xs, steps, weights):
         rots = [self._rots(x, steps) for x in xs]
         if weights is None:
             outs = []
@@ -564,8 +601,8 @@ class HeBackend:
         self.count["rot"] += len(xs) * len({s % m for s in steps if s % m})
         if weights is not None:
             self.count["pmul"] += sum(len(wi) for wo in weights for wi in wo)
-        if self.naf:
-            return self._naf_lincomb(xs, steps, weights)
+        if self._seq:
+            return self._seq_lincomb(xs, steps, weights)
         if weights is None:
             return self.he.lincomb(xs, steps, None)
         lp = xs[0].lp
@@ -577,8 +614,8 @@ class HeBackend:
         self.count["rot"] += len(xs) * len({s % m for s in steps if s % m})
         self.count["pmul"] += sum(len(wi) for wo in weights for wi in wo)
         self.count["rescale"] += len(weights)
-        if self.naf:
-            return [self.he.rescale(y) for y in self._naf_lincomb(xs, steps, weights)]
+        if self._seq:
+            return [self.he.rescale(y) for y in self._seq_lincomb(xs, steps, weights)]
         lp = xs[0].lp
         enc = [[[self.he.encode_ext(v, self.he.scale, lp) for v in wi] for wi in wo] for wo in weights]
         return self.he.lincomb(xs, steps, enc, self.he.scale, rescale=True)
@@ -591,7 +628,7 @@ class HeBackend:
         self.count["pmul"] += sum(len(w) for w in weights)
         self.count["rescale"] += 1
         lp = xs[0].lp
-        if self.naf:
+        if self._seq:
             acc = None
             for x, st, ws in zip(xs, steps, weights):
                 rots = self._rots(x, st)
@@ -640,4 +677,4 @@ class HeBackend:
 
     def square(self, x):
         self.count["square"] += 1
-        return self.he.square(x)
+        return self.he.square_literal(x) if self.literal else self.he.square(x)

@@ -95,15 +95,16 @@ def layers_to_c(layers):
     return arr, keep
 
 
-def plan(layers, W_img: int, H_img: int):
-    """he_model_plan: (stride, levels, rotation steps)."""
+def plan(layers, W_img: int, H_img: int, schedule: str = "fused"):
+    """he_model_plan_schedule: (stride, levels, rotation steps); schedule "fused" or "literal"."""
     arr, keep = layers_to_c(layers)
     L = load()
+    sc = _lib.SCHEDULES[schedule]
     stride, levels, n = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_size_t(0)
-    check(L.he_model_plan(arr, len(layers), W_img, H_img, ctypes.byref(stride), ctypes.byref(levels), None,
-                          ctypes.byref(n)))
+    check(L.he_model_plan_schedule(arr, len(layers), W_img, H_img, sc, ctypes.byref(stride), ctypes.byref(levels),
+                                   None, ctypes.byref(n)))
     steps = (ctypes.c_int32 * n.value)()
-    check(L.he_model_plan(arr, len(layers), W_img, H_img, None, None, steps, ctypes.byref(n)))
+    check(L.he_model_plan_schedule(arr, len(layers), W_img, H_img, sc, None, None, steps, ctypes.byref(n)))
     return stride.value, levels.value, list(steps)
 
 
@@ -191,9 +192,10 @@ class Server:
 
 
 def simulate_server(max_batch, max_wait_us, base_us, per_ct_us, arrival_us, model_of, cts_of, mem_budget=0,
-                    max_inflight=0, exact_batches=False):
-    """he_server_simulate: the serving loop on simulated models (no GPU).
-    Returns (batch id per request, latency ms per request)."""
+                    max_inflight=0, exact_batches=False, with_refusals=False):
+    """he_server_simulate_admission: the serving loop on simulated models (no GPU); mem_budget
+    counts simulated ciphertexts.  Returns (batch id per request, latency ms per request), and
+    with with_refusals also the refusal flag of each request."""
     n = len(arrival_us)
     opt = _lib.he_server_opts(max_batch, max_wait_us, mem_budget, max_inflight, int(exact_batches))
     f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
@@ -202,11 +204,14 @@ def simulate_server(max_batch, max_wait_us, base_us, per_ct_us, arrival_us, mode
     mo, co = u32(model_of), u32(cts_of)
     batch = np.zeros(n, dtype=np.uint64)
     lat = np.zeros(n, dtype=np.float64)
+    ref = np.zeros(n, dtype=np.uint32)
     P = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t))
-    check(load().he_server_simulate(ctypes.byref(opt), len(base), P(base, ctypes.c_double), P(per, ctypes.c_double),
-                                    n, P(arr, ctypes.c_double), P(mo, ctypes.c_uint32), P(co, ctypes.c_uint32),
-                                    P(batch, ctypes.c_uint64), P(lat, ctypes.c_double)))
-    return batch, lat
+    check(load().he_server_simulate_admission(ctypes.byref(opt), len(base), P(base, ctypes.c_double),
+                                              P(per, ctypes.c_double), n, P(arr, ctypes.c_double),
+                                              P(mo, ctypes.c_uint32), P(co, ctypes.c_uint32),
+                                              P(batch, ctypes.c_uint64), P(lat, ctypes.c_double),
+                                              P(ref, ctypes.c_uint32)))
+    return (batch, lat, ref) if with_refusals else (batch, lat)
 
 
 class Context:
@@ -251,6 +256,11 @@ class Context:
         """he_keygen_pow2: power-of-two Galois keys only; rotations by non-adjacent-form chains."""
         check(load().he_keygen_pow2(self.h))
 
+    def set_schedule(self, schedule: str):
+        """he_context_set_schedule: "fused" (the default) or "literal" (the paper's order, one
+        operation at a time) for the layer calls and the models compiled from then on."""
+        check(load().he_context_set_schedule(self.h, _lib.SCHEDULES[schedule]))
+
     def sync(self):
         check(load().he_sync(self.h))
 
@@ -271,8 +281,9 @@ class Context:
                                        float(buf[i].ops)) for i in range(min(n.value, cap))}
 
     def ubench(self):
-        """Measured register-only throughput: (butterflies/s, 128-bit MACs/s, Barrett products/s)."""
-        out = (ctypes.c_double * 3)()
+        """Measured register-only throughput: (butterflies/s, 128-bit MACs/s, Barrett products/s,
+        SM count of the device the grids were sized for)."""
+        out = (ctypes.c_double * 4)()
         check(load().he_ubench(self.h, out))
         return tuple(out)
 

@@ -16,6 +16,8 @@ HE_OK, HE_EINVAL, HE_ENOMEM, HE_ELEVEL, HE_ESCALE, HE_ESLOTS, HE_ENOKEY, HE_ECUD
 STATUS_NAMES = ["HE_OK", "HE_EINVAL", "HE_ENOMEM", "HE_ELEVEL", "HE_ESCALE", "HE_ESLOTS", "HE_ENOKEY",
                 "HE_ECUDA", "HE_ETIMEOUT", "HE_EOVERFLOW"]
 HE_CONV2D, HE_CONV1D, HE_SQUARE, HE_AVGPOOL, HE_FLATTEN, HE_FC, HE_APPROX_RELU = 1, 2, 3, 4, 5, 6, 7
+HE_SCHEDULE_FUSED, HE_SCHEDULE_LITERAL = 0, 1
+SCHEDULES = {"fused": HE_SCHEDULE_FUSED, "literal": HE_SCHEDULE_LITERAL}
 
 
 class he_params(ctypes.Structure):
@@ -63,6 +65,7 @@ SIGNATURES = {
     "he_context_primes": (_int, [_vp, ctypes.POINTER(_u64), _sz]),
     "he_keygen": (_int, [_vp, ctypes.POINTER(_i32), _sz]),
     "he_keygen_pow2": (_int, [_vp]),
+    "he_context_set_schedule": (_int, [_vp, _u32]),
     "he_encrypt": (_int, [_vp, _vp, _int, _u32, _u32, _u32, _u32, _u32, _u64, _pp]),
     "he_encrypt_channels": (_int, [_vp, _vp, _int, _u32, _u32, _u32, _u32, _u32, _u32, _u64, _pp]),
     "he_decrypt": (_int, [_vp, _vp, _vp, _int, _sz]),
@@ -86,6 +89,8 @@ SIGNATURES = {
     "he_fc": (_int, [_vp, _vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), _u32, _u32, _pp]),
     "he_model_plan": (_int, [ctypes.POINTER(he_layer), _sz, _u32, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32),
                              ctypes.POINTER(_i32), ctypes.POINTER(_sz)]),
+    "he_model_plan_schedule": (_int, [ctypes.POINTER(he_layer), _sz, _u32, _u32, _u32, ctypes.POINTER(_u32),
+                                      ctypes.POINTER(_u32), ctypes.POINTER(_i32), ctypes.POINTER(_sz)]),
     "he_model_compile": (_int, [_vp, ctypes.POINTER(he_layer), _sz, _u32, _u32, _u32, _pp]),
     "he_infer": (_int, [_vp, _vp, _int, _pp]),
     "he_model_free": (None, [_vp]),
@@ -110,6 +115,10 @@ SIGNATURES = {
     "he_server_simulate": (_int, [ctypes.POINTER(he_server_opts), _u32, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl),
                                   _sz, ctypes.POINTER(_dbl), ctypes.POINTER(_u32), ctypes.POINTER(_u32),
                                   ctypes.POINTER(_u64), ctypes.POINTER(_dbl)]),
+    "he_server_simulate_admission": (_int, [ctypes.POINTER(he_server_opts), _u32, ctypes.POINTER(_dbl),
+                                            ctypes.POINTER(_dbl), _sz, ctypes.POINTER(_dbl), ctypes.POINTER(_u32),
+                                            ctypes.POINTER(_u32), ctypes.POINTER(_u64), ctypes.POINTER(_dbl),
+                                            ctypes.POINTER(_u32)]),
     "he_last_error": (ctypes.c_char_p, []),
 }
 

@@ -734,6 +734,13 @@ Cts ct_rotate(Ctx *c, const Cts &a, int step) {
     return c->naf ? ct_rotate_naf(c, a, step, nullptr) : ct_rotate_direct(c, a, step);
 }
 
+// one rotation of a rotate-then-multiply combination: with power-of-two keys the chain of its
+// non-adjacent form (cache: prefixes shared between the rotations of one input), else the
+// step's own key switch (paper-order schedule)
+static Cts rotate_seq(Ctx *c, const Cts &a, int step, std::map<int64_t, Cts> *cache) {
+    return c->naf ? ct_rotate_naf(c, a, step, cache) : ct_rotate_direct(c, a, step);
+}
+
 static Cts ct_rotate_direct(Ctx *c, const Cts &a, int step) {
     const u32 N = c->N, lp = a.lp, B = a.B, E = lp + c->K;
     u32 g = c->galois_elt(step);
@@ -769,6 +776,13 @@ Cts ct_square(Ctx *c, const Cts &a) {
     kl.g[0] = 1;
     DBuf acc(c, (size_t)B * 2 * E * N);
     ks_inner(c, acc.p, D.p, kl, 1, B, lp);
+    if (c->literal) {
+        // one step at a time: relinearise (ModDown of both accumulators, plus d0 / d1), then the
+        // centred rescale
+        Cts rl = cts_alloc(c, B, lp, a.scale * a.scale, a.lay);
+        ks_moddown(c, rl.data(), acc.p, d.p, (size_t)3 * lp * N, 3, kl, 1, B, lp);
+        return ct_rescale(c, rl);
+    }
     // relinearise and rescale as one division by q_top * P: P * (d0, d1) joins the accumulators
     ks_add_p_times(c, acc.p, d.p, B, lp);
     Cts r = cts_alloc(c, B, lp - 1, a.scale * a.scale / (double)c->primes[lp - 1], a.lay);
@@ -781,11 +795,11 @@ Cts ct_square(Ctx *c, const Cts &a) {
 Cts ct_lincomb_diag(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps) {
     const u32 N = c->N, lp = X.lp, E = lp + c->K, Bt = CH * B;
     if (X.B != Bt || steps.size() != CH) throw HeError(HE_EINVAL, "lincomb_diag: shape mismatch");
-    if (c->naf) {   // power-of-two keys: each channel rotated by its own chain, then summed
+    if (seq_lincomb(c)) {   // each channel rotated on its own (a chain with power-of-two keys), then summed
         const size_t bw = (size_t)B * cts_ct_words(c, lp);
         Cts R = cts_alloc(c, Bt, lp, X.scale, X.lay);
         for (u32 i = 0; i < CH; ++i) {
-            Cts r = ct_rotate_naf(c, cts_view(X, i * bw, B), steps[i], nullptr);
+            Cts r = rotate_seq(c, cts_view(X, i * bw, B), steps[i], nullptr);
             CUDA_TRY(cudaMemcpyAsync(R.data() + i * bw, r.data(), bw * 8, cudaMemcpyDeviceToDevice, c->stream));
         }
         Cts out = cts_alloc(c, B, lp, X.scale, X.lay);
@@ -855,7 +869,7 @@ Cts ct_lincomb_chan(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<std::
             }
     }
     const size_t bw = (size_t)B * cts_ct_words(c, lp);   // one channel's block of B ciphertexts
-    if (c->naf) {
+    if (seq_lincomb(c)) {
         const size_t pw = (size_t)lp * N;
         Cts Z = cts_alloc(c, B, lp, X.scale * pt_scale, X.lay);
         Cts R = cts_alloc(c, K * B, lp, X.scale, X.lay);
@@ -863,7 +877,7 @@ Cts ct_lincomb_chan(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<std::
             std::map<int64_t, Cts> cache;
             const Cts Xi = cts_view(X, i * bw, B);
             for (u32 k = 0; k < K; ++k) {
-                Cts r = ct_rotate_naf(c, Xi, steps[i][k], &cache);
+                Cts r = rotate_seq(c, Xi, steps[i][k], &cache);
                 CUDA_TRY(cudaMemcpyAsync(R.data() + k * bw, r.data(), bw * 8, cudaMemcpyDeviceToDevice, c->stream));
             }
             mac(c, Z.data(), bw, R.data(), bw, pts + (size_t)i * K * pw, 1, K, B, lp, lp, c->L1, i > 0,
@@ -911,18 +925,19 @@ Cts ct_lincomb_chan(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<std::
     return out;
 }
 
-// Power-of-two keys: rotate-then-multiply.  The whole batch X is rotated by every step
-// (chains sharing their prefixes), the plaintexts pts [O][S*CH][lp][N] (over Q_l) multiply
-// the rotations and the products are summed (or the rotations are summed); then the
-// usual rescale.
-static Cts ct_lincomb_naf(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps, const u64 *pts,
+// Rotate-then-multiply (power-of-two keys, and the paper-order schedule: Alg. 1 / Alg. 2 as
+// printed).  The whole batch X is rotated by every step (chains sharing their prefixes with
+// power-of-two keys, one key switch per step otherwise), the plaintexts pts [O][S*CH][lp][N]
+// (over Q_l) multiply the rotations and the products are summed (or the rotations are
+// summed); then the centred rescale.
+static Cts ct_lincomb_seq(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &steps, const u64 *pts,
                           u32 O, double pt_scale, bool rescale) {
     const u32 N = c->N, lp = X.lp, Bt = CH * B, S = (u32)steps.size();
     const size_t bw = (size_t)B * cts_ct_words(c, lp);   // one block of B ciphertexts
     Cts R = cts_alloc(c, S * Bt, lp, X.scale, X.lay);    // [s][channel][b]
     std::map<int64_t, Cts> cache;
     for (u32 s = 0; s < S; ++s) {
-        Cts r = ct_rotate_naf(c, X, steps[s], &cache);
+        Cts r = rotate_seq(c, X, steps[s], &cache);
         CUDA_TRY(cudaMemcpyAsync(R.data() + (size_t)s * CH * bw, r.data(), (size_t)CH * bw * 8,
                                  cudaMemcpyDeviceToDevice, c->stream));
     }
@@ -940,7 +955,7 @@ Cts ct_lincomb(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &step
                double pt_scale, bool rescale) {
     const u32 N = c->N, lp = X.lp, E = lp + c->K, Bt = CH * B, S = (u32)steps.size();
     if (X.B != Bt) throw HeError(HE_EINVAL, "lincomb: batch mismatch");
-    if (c->naf) return ct_lincomb_naf(c, X, CH, B, steps, pts, O, pt_scale, rescale);
+    if (seq_lincomb(c)) return ct_lincomb_seq(c, X, CH, B, steps, pts, O, pt_scale, rescale);
     bool any_ks = false;
     for (int s : steps)
         if (c->galois_elt(s) != 1) {

@@ -267,6 +267,9 @@ struct Ctx : std::enable_shared_from_this<Ctx> {
     // keys
     bool have_keys = false;
     bool naf = false;              // power-of-two Galois keys only: rotations by non-adjacent-form chains
+    // paper-order schedule (he_context_set_schedule): every rotation its own key switch, masks
+    // multiplied over Q_l after the rotation, the centred rescale; no hoisted combination
+    bool literal = false;
     DBuf sk;                       // [L1+K][N] eval
     DBuf pk;                       // [2][L1][N]
     DBuf rlk;                      // [dnum][2][L1+K][N]

@@ -280,9 +280,10 @@ static Feat layer_approx_relu(Ctx *c, const Feat &in, PtCache *pc, const std::st
 }
 
 // The flatten's last masked stage (K steps) is merged with the packing of CH channels when the
-// merged combination needs at most this many rotation steps (K*CH Galois keys instead of K + CH)
+// merged combination needs at most this many rotation steps (K*CH Galois keys instead of K + CH);
+// never in the paper-order schedule
 static const u32 MERGE_MAX_STEPS = 128;
-static bool merge_last_stage(u32 k, u32 ch) { return ch > 1 && k * ch <= MERGE_MAX_STEPS; }
+static bool merge_last_stage(u32 k, u32 ch, bool literal) { return !literal && ch > 1 && k * ch <= MERGE_MAX_STEPS; }
 
 // Sec. IV-E: remove intervals / invalid values, pack the channels.
 // Every mask-rotate-sum stage  sum_k Rot(m_k (.) x, r_k)  is evaluated as one hoisted
@@ -290,6 +291,9 @@ static bool merge_last_stage(u32 k, u32 ch) { return ch > 1 && k * ch <= MERGE_M
 // followed by one rescale.  The last stage and the channel packing (channel o rotated right
 // by o*W*H) are one combination: channel o's terms use the steps r_k - o*W*H and the masks
 // rotated by them, with one ModDown and rescale for the packed output.
+// In the paper-order schedule a stage is the steps as listed: each mask multiplied with the
+// ciphertext over Q_l, each product rotated left by its own key switch, the rotations added,
+// then the centred rescale; the packing follows the last stage.
 static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string &key) {
     const Layout &L = in.x.lay;
     const u32 I = L.I, W = L.W, H = L.H, Wi = L.W_img, CH = in.CH;
@@ -331,6 +335,21 @@ static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string
     auto run_stage = [&](const Cts &x, const Stage &S) {
         std::vector<u32> mk;
         for (u32 k = 0; k < S.steps.size(); ++k) mk.push_back(k);
+        if (c->literal) {
+            const u32 K = (u32)S.steps.size(), B = x.B, lp = x.lp;
+            const size_t bw = (size_t)B * cts_ct_words(c, lp);
+            const u64 *pts = masks(key + S.name + ":lit", S, mk, std::vector<int>(K, 0), lp);   // not rotated
+            Cts Y = cts_alloc(c, K * B, lp, x.scale * c->scale, x.lay);   // Y_k = m_k (.) x
+            mac(c, Y.data(), bw, x.data(), bw, pts, K, 1, B, lp);
+            Cts R = cts_alloc(c, K * B, lp, Y.scale, x.lay);
+            for (u32 k = 0; k < K; ++k) {
+                Cts r = ct_rotate(c, cts_view(Y, k * bw, B), S.steps[k]);
+                CUDA_TRY(cudaMemcpyAsync(R.data() + k * bw, r.data(), bw * 8, cudaMemcpyDeviceToDevice, c->stream));
+            }
+            Cts Z = cts_alloc(c, B, lp, Y.scale, x.lay);
+            sum_stack(c, Z.data(), R.data(), bw, K, B * 2 * lp, lp, lp, c->L1, 0);
+            return ct_rescale(c, Z);
+        }
         const u64 *pts = masks(key + S.name, S, mk, S.steps, x.lp);
         return ct_lincomb(c, x, 1, x.B, S.steps, pts, 1, c->scale, true);
     };
@@ -370,7 +389,7 @@ static Feat layer_flatten(Ctx *c, const Feat &in, PtCache *pc, const std::string
         stages.push_back(S);
     }
     for (size_t k = 0; k + 1 < stages.size(); ++k) cur = run_stage(cur, stages[k]);
-    if (!stages.empty() && !merge_last_stage((u32)stages.back().steps.size(), CH)) {
+    if (!stages.empty() && !merge_last_stage((u32)stages.back().steps.size(), CH, c->literal)) {
         cur = run_stage(cur, stages.back());
         stages.clear();
     }
@@ -520,7 +539,7 @@ static Feat layer_fc(Ctx *c, const Feat &in, const LayerSpec &sp, PtCache *pc, c
 // ------------------------------------------------------------------ planner
 // Sec. V: the slots one sample needs = max(input W*H (Theorem 1 keeps every later
 // valid value inside it), CH*W*H of a flatten, W_vec of an FC); levels and steps.
-static Plan plan_layers(const std::vector<LayerSpec> &ls, u32 Wi, u32 Hi) {
+static Plan plan_layers(const std::vector<LayerSpec> &ls, u32 Wi, u32 Hi, bool literal) {
     const u32 dims = Hi == 1 ? 1 : 2;
     // the input's channels: CH_in of a first convolution, all in one ciphertext (Sec. III-A)
     const u32 C = !ls.empty() && (ls[0].op == HE_CONV2D || ls[0].op == HE_CONV1D) ? ls[0].ci : 1;
@@ -575,7 +594,7 @@ static Plan plan_layers(const std::vector<LayerSpec> &ls, u32 Wi, u32 Hi) {
                     stage.emplace_back();
                     for (u32 r = 0; r < H; ++r) stage.back().push_back((int)(r * (Wi * I - W)));
                 }
-                if (!stage.empty() && merge_last_stage((u32)stage.back().size(), ch)) {
+                if (!stage.empty() && merge_last_stage((u32)stage.back().size(), ch, literal)) {
                     // the last stage merged with the channel packing
                     for (size_t k = 0; k + 1 < stage.size(); ++k) st.insert(stage[k].begin(), stage[k].end());
                     for (int sk : stage.back())
@@ -686,9 +705,18 @@ void model_check_input(const he_model *m, const Cts &x) {
     if (x.lp < m->plan.levels + 1) throw HeError(HE_ELEVEL, "not enough levels for this model");
 }
 
+// the schedule a model was compiled with, for the duration of one of its runs
+struct ScheduleScope {
+    Ctx *c;
+    bool saved;
+    ScheduleScope(Ctx *cx, bool literal) : c(cx), saved(cx->literal) { c->literal = literal; }
+    ~ScheduleScope() { c->literal = saved; }
+};
+
 Cts model_infer(he_model *m, const Cts &x_in, bool use_graph) {
     Ctx *c = m->c;
     model_check_input(m, x_in);
+    ScheduleScope sched(c, m->literal);
     // Drop-Level (Sec. IV-A): a ciphertext with more levels than the model consumes
     // loses its top limbs first, so every layer runs on the fewest limbs
     const Cts x = ct_drop_to(c, x_in, m->plan.levels + 1);
@@ -859,6 +887,15 @@ he_status he_keygen(he_ctx *h, const int32_t *steps, size_t n) {
         if (n && !steps) throw HeError(HE_EINVAL, "null steps");
         keygen(c, std::vector<int>(steps, steps + n));
         c->naf = false;
+    });
+}
+
+he_status he_context_set_schedule(he_ctx *h, uint32_t schedule) {
+    return guard([&] {
+        Ctx *c = CX(h);
+        CtxLock lk_(c);
+        if (schedule != HE_SCHEDULE_FUSED && schedule != HE_SCHEDULE_LITERAL) throw HeError(HE_EINVAL, "unknown schedule");
+        c->literal = schedule == HE_SCHEDULE_LITERAL;
     });
 }
 
@@ -1161,9 +1198,15 @@ he_status he_fc(he_ctx *h, const he_ct *in, const double *Wm, const double *b, u
 
 he_status he_model_plan(const he_layer *layers, size_t n, uint32_t Wi, uint32_t Hi, uint32_t *stride,
                         uint32_t *levels, int32_t *steps, size_t *n_steps) {
+    return he_model_plan_schedule(layers, n, Wi, Hi, HE_SCHEDULE_FUSED, stride, levels, steps, n_steps);
+}
+
+he_status he_model_plan_schedule(const he_layer *layers, size_t n, uint32_t Wi, uint32_t Hi, uint32_t schedule,
+                                 uint32_t *stride, uint32_t *levels, int32_t *steps, size_t *n_steps) {
     return guard([&] {
         if (!layers || !n || !Wi || !Hi) throw HeError(HE_EINVAL, "bad arguments");
-        Plan p = plan_layers(copy_layers(layers, n, Hi), Wi, Hi);
+        if (schedule != HE_SCHEDULE_FUSED && schedule != HE_SCHEDULE_LITERAL) throw HeError(HE_EINVAL, "unknown schedule");
+        Plan p = plan_layers(copy_layers(layers, n, Hi), Wi, Hi, schedule == HE_SCHEDULE_LITERAL);
         if (stride) *stride = p.stride;
         if (levels) *levels = p.levels;
         if (n_steps) {
@@ -1190,7 +1233,8 @@ he_status he_model_compile(he_ctx *h, const he_layer *layers, size_t n, uint32_t
         m->W_img = Wi;
         m->H_img = Hi;
         m->spc = spc;
-        m->plan = plan_layers(m->layers, Wi, Hi);
+        m->literal = c->literal;
+        m->plan = plan_layers(m->layers, Wi, Hi, m->literal);
         if ((u64)m->plan.stride * spc > c->N / 2) throw HeError(HE_ESLOTS, "samples do not fit in the slots");
         if (m->plan.levels + 1 > c->L1) throw HeError(HE_ELEVEL, "the modulus chain is too short for this model");
         for (int s : m->plan.steps) {

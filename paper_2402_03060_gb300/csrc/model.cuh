@@ -38,6 +38,7 @@ struct he_model {
     std::vector<LayerSpec> layers;
     u32 W_img = 0, H_img = 0, spc = 0;
     Plan plan;
+    bool literal = false;                  // compiled under the paper-order schedule
     PtCache pc;
     bool pc_filled = false;                // pc holds every plaintext of the model's layout
     Pool gpool;                            // private pool of the captured graphs

@@ -121,6 +121,13 @@ extern "C" he_status he_rescale_noalloc(he_ctx *h, const uint64_t *in, uint64_t 
                                          "(at most %u ciphertexts at N = %u)",
                                          (size_t)batch * 2 * N, NOALLOC_SCRATCH_WORDS,
                                          NOALLOC_SCRATCH_WORDS / (2 * N), N));
+        {
+            // the kernels read `in` while other blocks write `out` (with another limb stride):
+            // the two ranges must not share a word
+            const uintptr_t i0 = (uintptr_t)in, i1 = i0 + (uintptr_t)batch * 2 * limbs * N * 8;
+            const uintptr_t o0 = (uintptr_t)out, o1 = o0 + (uintptr_t)batch * 2 * (limbs - 1) * N * 8;
+            if (i0 < o1 && o0 < i1) throw HeError(HE_EINVAL, "he_rescale_noalloc: in and out overlap");
+        }
         CUDA_TRY(cudaSetDevice(c->device));
         u64 *scratch = scratch_address(c->device);
         static std::once_flag attr_once[64];

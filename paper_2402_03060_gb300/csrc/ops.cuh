@@ -47,9 +47,12 @@ Cts ct_add(Ctx *c, const Cts &a, const Cts &b);
 void ct_add_inplace(Ctx *c, Cts &a, const Cts &b);
 Cts ct_rescale(Ctx *c, const Cts &a);
 Cts ct_drop_level(Ctx *c, const Cts &a);
+// linear combinations of rotations evaluated rotate-then-multiply, one rotation at a time:
+// with power-of-two keys (chains) and in the paper-order schedule (direct rotations)
+inline bool seq_lincomb(const Ctx *c) { return c->naf || c->literal; }
 // limbs beyond Q_l that the plaintexts of ct_lincomb carry: K (hoisted, over Q_l u P), or 0
-// with power-of-two keys (rotate-then-multiply over Q_l)
-inline u32 ks_ext(const Ctx *c) { return c->naf ? 0 : c->K; }
+// when combinations are rotate-then-multiply (over Q_l)
+inline u32 ks_ext(const Ctx *c) { return seq_lincomb(c) ? 0 : c->K; }
 // a rotation step as the signed powers of two of its non-adjacent form, lowest first
 std::vector<int> naf_terms(int64_t r, u32 slots);
 Cts ct_drop_to(Ctx *c, const Cts &a, u32 keep);

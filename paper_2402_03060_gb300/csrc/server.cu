@@ -16,7 +16,10 @@
 //     batch is split into per-request views, and waiting clients are woken;
 //   * admission: a model is accepted only if the device bytes it holds (keys,
 //     cached masks, graph pools) fit the memory budget, and a request only if
-//     the budget still holds its ciphertext bytes while it is queued or running.
+//     the budget still holds its ciphertext bytes from submission until its
+//     result is collected (queued, running, or finished and not yet collected);
+//     a refused request gets HE_ENOMEM and may be submitted again once results
+//     have been collected.
 // Every ciphertext's result is independent of the batch it ran in (all kernels
 // act per ciphertext), so a request's output is bit-identical alone or mixed.
 //
@@ -95,7 +98,7 @@ struct he_server {
     std::deque<Batch *> done;
     u64 next_req = 1, next_batch = 1;
     u32 rr = 0, inflight = 0;
-    size_t resident = 0, pending = 0;         // bytes: models' holdings; queued + running requests
+    size_t resident = 0, pending = 0;         // bytes: models' holdings; requests submitted, not yet collected
     std::vector<Ctx *> counted;               // contexts whose pools are already in `resident`
     bool stop = false;
     std::thread worker;
@@ -203,7 +206,7 @@ static void server_loop(he_server *s) {
                 r->err = b->err;
                 r->msg = b->msg;
                 r->t_done = b->t_done;
-                s->pending -= r->bytes;
+                if (s->simulate) s->pending -= r->bytes;   // simulated requests are collected on completion
                 M.requests++;
                 M.lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
             }
@@ -258,6 +261,11 @@ static void server_loop(he_server *s) {
         }
         if (!launched && s->done.empty()) s->cv.wait_until(lk, wake);
     }
+}
+
+// whether the budget holds `bytes` more of requests (caller holds s->mu)
+static bool admits(const he_server *s, size_t bytes) {
+    return !s->opt.mem_budget || s->resident + s->pending + bytes <= s->opt.mem_budget;
 }
 
 static size_t model_bytes(const he_model *m) {
@@ -360,8 +368,8 @@ he_status he_server_submit(he_server *s, uint32_t model_id, const he_ct *in, uin
         if (in->c != M.m->c) throw HeError(HE_EINVAL, "ciphertext belongs to another context");
         model_check_input(M.m, in->x);
         const size_t bytes = (size_t)in->x.B * cts_ct_words(in->c, in->x.lp) * 8;
-        if (s->opt.mem_budget && s->resident + s->pending + bytes > s->opt.mem_budget)
-            throw HeError(HE_ENOMEM, "admission refused: the memory budget is held by queued and running requests");
+        if (!admits(s, bytes))
+            throw HeError(HE_ENOMEM, "admission refused: the memory budget is held by requests not yet collected");
         Request *r = new Request();
         r->id = s->next_req++;
         r->model = model_id;
@@ -387,6 +395,8 @@ he_status he_server_wait(he_server *s, uint64_t req_id, uint32_t timeout_ms, he_
         if (!s->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->state == 2; }))
             throw HeError(HE_ETIMEOUT, "request not finished within the timeout");
         s->reqs.erase(it);
+        s->pending -= r->bytes;   // collected: its bytes leave the budget
+        s->cv.notify_all();
         lk.unlock();
         const he_status err = r->err;
         const std::string msg = r->msg;
@@ -476,6 +486,14 @@ he_status he_server_simulate(const he_server_opts *opt, uint32_t n_models, const
                              const double *per_ct_us, size_t n_req, const double *arrival_us,
                              const uint32_t *model_of, const uint32_t *cts_of, uint64_t *batch_of,
                              double *latency_ms) {
+    return he_server_simulate_admission(opt, n_models, base_us, per_ct_us, n_req, arrival_us, model_of, cts_of,
+                                        batch_of, latency_ms, nullptr);
+}
+
+he_status he_server_simulate_admission(const he_server_opts *opt, uint32_t n_models, const double *base_us,
+                                       const double *per_ct_us, size_t n_req, const double *arrival_us,
+                                       const uint32_t *model_of, const uint32_t *cts_of, uint64_t *batch_of,
+                                       double *latency_ms, uint32_t *refusals) {
     return srv_guard([&] {
         if (!opt || !n_models || !base_us || !per_ct_us || (n_req && (!arrival_us || !model_of || !cts_of)) ||
             opt->max_batch < 1)
@@ -491,27 +509,58 @@ he_status he_server_simulate(const he_server_opts *opt, uint32_t n_models, const
         }
         start_threads(s);
         std::vector<Request *> all(n_req, nullptr);
+        std::vector<uint32_t> refused(n_req, 0);   // 1: refused on arrival, admitted later
+        std::deque<size_t> blocked;   // refused requests, retried in arrival order as the budget frees
         const auto t0 = SrvClock::now();
         he_status bad = HE_OK;
-        for (size_t k = 0; k < n_req; ++k) {
-            std::this_thread::sleep_until(t0 + std::chrono::microseconds((long long)arrival_us[k]));
-            std::lock_guard<std::mutex> lk(s->mu);
-            if (model_of[k] >= n_models || cts_of[k] < 1 || cts_of[k] > s->opt.max_batch) {
-                bad = HE_EINVAL;
-                break;
-            }
+        // admit request k if the budget holds it (one simulated ciphertext counts as one byte;
+        // the simulated models hold none); the latency counts from its first submission
+        auto try_admit = [&](size_t k, SrvClock::time_point first) {
+            const size_t bytes = cts_of[k];
+            if (!admits(s, bytes)) return false;
             Request *r = new Request();
             r->id = s->next_req++;
             r->model = model_of[k];
             r->B = cts_of[k];
-            r->t_submit = SrvClock::now();
+            r->bytes = bytes;
+            r->t_submit = first;
+            s->pending += bytes;
             all[k] = r;
             s->models[r->model]->q.push_back(r);
             s->cv.notify_all();
+            return true;
+        };
+        std::vector<SrvClock::time_point> first(n_req);
+        auto retry_blocked = [&] {
+            while (!blocked.empty() && try_admit(blocked.front(), first[blocked.front()])) blocked.pop_front();
+        };
+        for (size_t k = 0; k < n_req; ++k) {
+            const auto due = t0 + std::chrono::microseconds((long long)arrival_us[k]);
+            std::unique_lock<std::mutex> lk(s->mu);
+            // until request k is due, admit refused ones whenever a completion frees the budget
+            while (!blocked.empty() && SrvClock::now() < due) {
+                retry_blocked();
+                if (!blocked.empty()) s->cv.wait_until(lk, due);
+            }
+            lk.unlock();
+            std::this_thread::sleep_until(due);
+            lk.lock();
+            if (model_of[k] >= n_models || cts_of[k] < 1 || cts_of[k] > s->opt.max_batch) {
+                bad = HE_EINVAL;
+                break;
+            }
+            first[k] = SrvClock::now();
+            retry_blocked();
+            if (!blocked.empty() || !try_admit(k, first[k])) {   // FIFO: behind the refused ones
+                refused[k] = 1;
+                blocked.push_back(k);
+            }
         }
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv.wait(lk, [&] {
+                if (bad == HE_OK) retry_blocked();
+                if (bad == HE_OK && !blocked.empty()) return false;
                 for (Request *r : all)
                     if (r && r->state != 2) return false;
                 return true;
@@ -520,6 +569,7 @@ he_status he_server_simulate(const he_server_opts *opt, uint32_t n_models, const
         for (size_t k = 0; k < n_req; ++k) {
             if (!all[k]) continue;
             if (batch_of) batch_of[k] = all[k]->batch;
+            if (refusals) refusals[k] = refused[k];
             if (latency_ms)
                 latency_ms[k] = std::chrono::duration<double, std::milli>(all[k]->t_done - all[k]->t_submit).count();
             delete all[k];

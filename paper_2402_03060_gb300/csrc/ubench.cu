@@ -62,14 +62,25 @@ __global__ void ub_barrett(u64 *sink, PrimeDev P, u32 iters) {
 }
 
 // Times each primitive with CUDA events on the context's stream; results per second:
-// out[0] butterflies/s, out[1] 64x64->128 multiply-accumulates/s, out[2] Barrett products/s.
+// out[0] butterflies/s, out[1] 64x64->128 multiply-accumulates/s, out[2] Barrett products/s,
+// out[3] the SM count the grids were sized for (SMs x resident CTAs per SM of each kernel).
 extern "C" he_status he_ubench(he_ctx *h, double *out) {
     try {
         if (!h || !h->c || !out) return HE_EINVAL;
         Ctx *c = h->c.get();
         CtxLock lk(c);
         CUDA_TRY(cudaSetDevice(c->device));
-        const u32 blocks = 152 * 8, threads = 256, iters = 4096;
+        // every SM of this device filled to the occupancy each kernel reaches
+        int sms = 0;
+        CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+        const u32 threads = 256, iters = 4096;
+        int occ[3] = {0, 0, 0};
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], ub_butterfly, threads, 0));
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], ub_mac128, threads, 0));
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], ub_barrett, threads, 0));
+        u32 grid[3];
+        for (int k = 0; k < 3; ++k) grid[k] = (u32)sms * (u32)std::max(1, occ[k]);
+        const u32 blocks = std::max(grid[0], std::max(grid[1], grid[2]));
         DBuf sink(c, (size_t)blocks * threads);
         const PrimeDev P = c->pdev_h[0];
         const u64 w = P.q / 3, ws = (u64)(((unsigned __int128)w << 64) / P.q);
@@ -77,28 +88,30 @@ extern "C" he_status he_ubench(he_ctx *h, double *out) {
         CUDA_TRY(cudaEventCreate(&e0));
         CUDA_TRY(cudaEventCreate(&e1));
         float ms;
-        const double nthr = (double)blocks * threads;
+        const double nthr0 = (double)grid[0] * threads, nthr1 = (double)grid[1] * threads,
+                     nthr2 = (double)grid[2] * threads;
         // a warm-up run, then the best of three timed runs of each
         out[0] = out[1] = out[2] = 0;
+        out[3] = sms;
         for (int rep = 0; rep < 4; ++rep) {
             CUDA_TRY(cudaEventRecord(e0, c->stream));
-            ub_butterfly<<<blocks, threads, 0, c->stream>>>(sink.p, P.q, w, ws, iters);
+            ub_butterfly<<<grid[0], threads, 0, c->stream>>>(sink.p, P.q, w, ws, iters);
             CUDA_TRY(cudaEventRecord(e1, c->stream));
             CUDA_TRY(cudaEventSynchronize(e1));
             CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep) out[0] = std::max(out[0], nthr * iters * 4 / (ms * 1e-3));
+            if (rep) out[0] = std::max(out[0], nthr0 * iters * 4 / (ms * 1e-3));
             CUDA_TRY(cudaEventRecord(e0, c->stream));
-            ub_mac128<<<blocks, threads, 0, c->stream>>>(sink.p, P.q - 1, iters);
+            ub_mac128<<<grid[1], threads, 0, c->stream>>>(sink.p, P.q - 1, iters);
             CUDA_TRY(cudaEventRecord(e1, c->stream));
             CUDA_TRY(cudaEventSynchronize(e1));
             CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep) out[1] = std::max(out[1], nthr * iters * 8 / (ms * 1e-3));
+            if (rep) out[1] = std::max(out[1], nthr1 * iters * 8 / (ms * 1e-3));
             CUDA_TRY(cudaEventRecord(e0, c->stream));
-            ub_barrett<<<blocks, threads, 0, c->stream>>>(sink.p, P, iters);
+            ub_barrett<<<grid[2], threads, 0, c->stream>>>(sink.p, P, iters);
             CUDA_TRY(cudaEventRecord(e1, c->stream));
             CUDA_TRY(cudaEventSynchronize(e1));
             CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep) out[2] = std::max(out[2], nthr * iters * 4 / (ms * 1e-3));
+            if (rep) out[2] = std::max(out[2], nthr2 * iters * 4 / (ms * 1e-3));
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

@@ -105,3 +105,44 @@ def test_admission_and_errors(G, two_models):
     with pytest.raises(G.HeError):
         srv.submit(0, big)               # three ciphertexts > max_batch 2
     srv.close()
+
+
+def test_memory_admission_refuses_and_readmits(G):
+    """A budget that holds the model plus exactly k = 2 request ciphertexts: two requests
+    are admitted, the third gets HE_ENOMEM (the first two are not collected yet); after one
+    he_server_wait collects a result the retried third request is admitted.  Every result
+    is bit-identical to the same request run alone through the compiled model."""
+    P = W.PARAMS["lenet1"]
+    lenet = W.lenet1()
+    ctx, m, stride = setup_model(G, lenet, P, 28, 28, 10)
+    imgs = W.images(30)
+    cts = [ctx.encrypt(imgs[10 * i: 10 * i + 10], 10, stride, W.ENC_SEED + i) for i in range(3)]
+    alone = [ctx.export(m.infer(ct, use_graph=True)) for ct in cts]
+    ct_bytes = 2 * ctx.n_data * ctx.n * 8          # one top-level ciphertext
+    # the model's residency as the server counts it (the graphs are captured by the first add)
+    probe = G.Server(max_batch=2, max_inflight=1, exact_batches=True)
+    probe.add_model(m)
+    probe.close()
+    probe = G.Server(max_batch=2, max_inflight=1, exact_batches=True)
+    probe.add_model(m)
+    resident = probe.stats()["resident_bytes"]
+    probe.close()
+    srv = G.Server(max_batch=2, max_inflight=1, exact_batches=True, mem_budget=resident + 2 * ct_bytes + ct_bytes // 2)
+    srv.add_model(m)
+    assert abs(srv.stats()["resident_bytes"] - resident) < ct_bytes // 2
+    r0 = srv.submit(0, cts[0])
+    r1 = srv.submit(0, cts[1])
+    with pytest.raises(G.HeError) as e:
+        srv.submit(0, cts[2])
+    assert e.value.status == 2 and "admission" in str(e.value)
+    out0, _ = srv.wait(r0)
+    r2 = srv.submit(0, cts[2])       # one result collected: room for one ciphertext again
+    out1, _ = srv.wait(r1)
+    out2, _ = srv.wait(r2)
+    for out, want in zip((out0, out1, out2), alone):
+        assert np.array_equal(ctx.export(out), want)
+    logits = ctx.decrypt(out2, 10)
+    for s in range(10):
+        assert np.abs(logits[s] - cnn.forward(imgs[20 + s], lenet)).max() < 1e-3
+    assert srv.stats()["requests"] == 3
+    srv.close()

@@ -108,3 +108,35 @@ def test_one_batch_in_flight_and_exact_batches_cut_latency():
     check_fifo(b1, mo, co, 8)
     assert np.median(lat1) < 0.8 * np.median(lat2)
     assert np.percentile(lat1, 99) < np.percentile(lat2, 99)
+
+
+def test_memory_admission_refuses_then_admits_in_order():
+    """mem_budget holds exactly k = 3 request ciphertexts: of six one-ciphertext requests
+    arriving at once, the first three are admitted and run as one batch; the other three
+    are refused on arrival and admitted, in arrival order, once that batch completes."""
+    n, k = 6, 3
+    arr = np.zeros(n)
+    mo = np.zeros(n, np.uint32)
+    co = np.ones(n, np.uint32)
+    batch, lat, ref = lib.simulate_server(8, 0, [20000.0], [0.0], arr, mo, co, mem_budget=k, max_inflight=1,
+                                          with_refusals=True)
+    assert ref.tolist() == [0, 0, 0, 1, 1, 1]
+    check_fifo(batch, mo, co, 8)
+    assert len(set(batch[:k].tolist())) == 1 and len(set(batch[k:].tolist())) == 1
+    assert batch[k] > batch[0]
+    # the refused ones waited for the first batch: about two batch times from their arrival
+    assert np.all(lat[:k] < 35.0) and np.all(lat[k:] >= 39.0) and np.all(lat[k:] < 80.0)
+
+
+def test_memory_admission_unlimited_and_multi_ciphertext_requests():
+    """Without a budget nothing is refused; a two-ciphertext request needs room for both."""
+    arr = np.array([0.0, 0.0, 0.0, 1000.0])
+    mo = np.zeros(4, np.uint32)
+    co = np.array([1, 1, 2, 1], np.uint32)
+    _, _, ref = lib.simulate_server(8, 0, [10000.0], [0.0], arr, mo, co, with_refusals=True)
+    assert ref.tolist() == [0, 0, 0, 0]
+    # budget 3: requests 0 and 1 fit (2 cts), request 2 (2 cts) does not, request 3 queues behind it
+    batch, lat, ref = lib.simulate_server(8, 0, [10000.0], [0.0], arr, mo, co, mem_budget=3, max_inflight=1,
+                                          with_refusals=True)
+    assert ref.tolist() == [0, 0, 1, 1]
+    check_fifo(batch, mo, co, 8)

@@ -58,3 +58,9 @@ def test_rescale_noalloc_matches_rescale(G):
         G.check(L.he_rescale_noalloc(ctx.h, ctypes.c_void_p(d_in.data_ptr()), ctypes.c_void_p(d_out.data_ptr()),
                                      1, 1))
     assert e.value.status == 3
+    # in and out overlapping (in place, or shifted by one word): refused on the host, nothing launched
+    for shift in (0, 8):
+        with pytest.raises(G.HeError) as e:
+            G.check(L.he_rescale_noalloc(ctx.h, ctypes.c_void_p(d_in.data_ptr()),
+                                         ctypes.c_void_p(d_in.data_ptr() + shift), 1, 4))
+        assert e.value.status == 1 and "overlap" in str(e.value)

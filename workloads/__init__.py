@@ -149,6 +149,14 @@ def m5_narrow(seed: int = WEIGHT_SEED):
                          ("fc", 8, 10)], seed)
 
 
+def m4_narrow(seed: int = WEIGHT_SEED):
+    """M4's layer sequence (LeNet-5 with x^2 on 32x32: three 5x5 convolutions, the last to 1x1,
+    pools 2/2, FC, x^2, FC) with 2, 4 and 8 channels instead of 6, 16 and 120."""
+    return _from_shapes([("conv2d", 1, 2, 5, 1), ("square",), ("avgpool", 2), ("conv2d", 2, 4, 5, 1), ("square",),
+                         ("avgpool", 2), ("conv2d", 4, 8, 5, 1), ("square",), ("flatten",), ("fc", 8, 6),
+                         ("square",), ("fc", 6, 10)], seed)
+
+
 def paper_model(name: str, seed: int = WEIGHT_SEED):
     """(layers with N(0, 0.1^2) weights, W_img, H_img) of one of PAPER_MODELS."""
     spec, Wi, Hi = PAPER_MODELS[name]
