@@ -134,7 +134,10 @@ he_status he_encrypt_channels(he_ctx *ctx, const double *x, int x_on_device, uin
                               uint32_t n_samples, uint32_t samples_per_ct, uint32_t stride, uint64_t enc_seed,
                               he_ct **out);
 
-/* Decrypt and decode: out is [B*samples_per_ct][n_per_sample] doubles (host or
+/* Decrypt and decode (paper Sec. III, Fig. 1: the client decrypts the encrypted
+ * result with its secret key and reads its values from the slots; decoding is the
+ * canonical-embedding inverse of he_encrypt's encoding, Sec. II-B).
+ * out is [B*samples_per_ct][n_per_sample] doubles (host or
  * device), the slots k*stride + [0, n_per_sample) of every sample position.
  * Decoding reads limb q_0, valid while |message * scale| < q_0/2.
  * Errors: HE_EINVAL, HE_ECUDA. */
@@ -239,12 +242,19 @@ he_status he_model_plan(const he_layer *layers, size_t n, uint32_t W_img, uint32
 he_status he_model_plan_schedule(const he_layer *layers, size_t n, uint32_t W_img, uint32_t H_img,
                                  uint32_t schedule, uint32_t *stride, uint32_t *levels, int32_t *steps,
                                  size_t *n_steps);
-/* Compile: copies the weights; plaintext masks are encoded on the device at
- * the first he_infer and cached in the model.  Errors: HE_ENOKEY, HE_ELEVEL, HE_ESLOTS. */
+/* Compile a layer list (paper Sec. IV: the model is fixed on the server side and its
+ * layers are converted to HE operations once -- Algorithm 1 kernels, Algorithm 2's
+ * pre-rotated weight matrix M_rot, the flatten masks of Sec. IV-E), for inputs of the
+ * flattened layout with samples_per_ct samples per ciphertext (Sec. III-B).  Copies the
+ * weights; the plaintext masks are encoded on the device at the first he_infer and
+ * cached in the model.  Errors: HE_ENOKEY, HE_ELEVEL, HE_ESLOTS. */
 he_status he_model_compile(he_ctx *ctx, const he_layer *layers, size_t n, uint32_t W_img, uint32_t H_img,
                            uint32_t samples_per_ct, he_model **out);
-/* Run the compiled model on a ciphertext batch (all layers, every ciphertext
- * of the batch in the same kernel launches); *out receives the logits batch.
+/* Run the compiled model on a ciphertext batch (paper Sec. III, Fig. 1: the server
+ * evaluates the network on the client's ciphertexts; Sec. III-B: each ciphertext carries
+ * samples_per_ct samples; Sec. IV-A: an input with more levels than the model consumes is
+ * first reduced by Drop-Level).  All layers, every ciphertext of the batch in the same
+ * kernel launches; *out receives the logits batch.
  * use_graph = 1 replays a captured CUDA graph after the first call of a given
  * batch size. */
 he_status he_infer(he_model *m, const he_ct *in, int use_graph, he_ct **out);

@@ -309,6 +309,8 @@ struct RowSet {         // rows of N words: row r at base + off(r)*N, prime pidx
 };
 void ntt_forward(Ctx *c, u64 *base, const RowSet &rs);
 void ntt_inverse(Ctx *c, u64 *base, const RowSet &rs);
+// the inner launch of the two-kernel NTT over the rows of rs (ntt_block.cuh)
+void ntt2_inner(Ctx *c, u64 *base, const RowSet &rs, int inverse);
 RowSet rows_regular(u32 n, u32 period, u32 lp, u32 pbase);
 RowSet rows_list(Ctx *c, const std::string &key, const std::vector<u32> &packed);
 
@@ -323,5 +325,9 @@ struct CtxLock {
 
 // a tuned knob, or dflt when it was not tuned
 static inline int tune_get(const Ctx *c, int knob, int dflt) { return c->tuned[knob] >= 0 ? c->tuned[knob] : dflt; }
-// limb split of an NTT-carrying kernel family: tuned, but never below what N requires
-int tune_split(const Ctx *c, int knob);
+// limb layout of an NTT-carrying kernel family (TUNE_NTT / TUNE_MODDOWN / TUNE_RESCALE):
+// 0 one CTA per limb, 1 a 2-CTA cluster per limb, NTT_TWO_KERNEL an outer launch over columns
+// and an inner launch over 1024-coefficient blocks (ntt_block.cuh); tuned, else the default
+// for N (two-kernel from 2^14 up), never a layout N does not allow
+#define NTT_TWO_KERNEL 2
+int ntt_layout(const Ctx *c, int knob);

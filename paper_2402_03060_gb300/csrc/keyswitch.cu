@@ -88,6 +88,56 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) modup_ntt_kernel(u64 *D, cons
     block_store(D + (size_t)off * N + pt.lo, sm, pt.n);
 }
 
+// The same rows in the two-kernel form (ntt_block.cuh): the base conversion of each converted
+// row's digit computed straight into the registers of its outer forward stages (one column per
+// thread), written to D; the inner stages then run over the same rows of D in place.
+template <int R>
+__global__ void __launch_bounds__(NTT2_COLS) modup2_outer_kernel(u64 *D, const u64 *__restrict__ xc, RowSet rs,
+                                                                 u32 lp, u32 K, u32 alpha, u32 beta,
+                                                                 const u64 *__restrict__ tab,
+                                                                 const u64 *__restrict__ tw_all,
+                                                                 const PrimeDev *__restrict__ pd) {
+    const u32 N = 1024u << R;
+    const u32 v = rs.list[blockIdx.x];
+    const u32 off = v >> 8, prime = v & 0xff;
+    const u32 E = lp + K;
+    const u32 t = off % E, bj = off / E;
+    const u32 j = bj % beta, b = bj / beta;
+    const u32 lo = j * alpha;
+    const u32 hi = lo + alpha < lp ? lo + alpha : lp;
+    const u32 nd = hi - lo;
+    const PrimeDev P = pd[prime];
+    const u64 *tj = tab + (size_t)j * (2 * alpha + alpha * E);
+    const u64 *xb = xc + ((size_t)b * lp + lo) * N;
+    const u32 g = blockIdx.y * NTT2_COLS + threadIdx.x;
+    u64 x[1 << R];
+    if (nd == 1) {
+        // single-limb digit: each coefficient (< q_j) reduced mod q_t
+        const u64 qj = pd[lo].q;
+#pragma unroll
+        for (int k = 0; k < (1 << R); ++k) {
+            u64 a = __ldg(xb + g + 1024u * k);
+            if (qj > P.q) a = qj < 2 * P.q ? (a >= P.q ? a - P.q : a) : reduce64(a, P);
+            x[k] = a;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < (1 << R); ++k) {
+            const u32 n = g + 1024u * k;
+            Acc128 acc = {0, 0};
+            for (u32 i = 0; i < nd; ++i) {
+                const u64 y = mul_shoup(__ldg(xb + (size_t)i * N + n), tj[i], tj[alpha + i], pd[lo + i].q);
+                mac128(acc, y, tj[2 * alpha + (size_t)i * E + t]);
+            }
+            x[k] = redc128(acc.lo, acc.hi, P);
+        }
+    }
+    outer_fwd_regs<R>(x, tw_all + (size_t)prime * 4 * N, P.q);
+    u64 *drow = D + (size_t)off * N + g;
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) drow[1024u * k] = x[k];
+}
+
 // the digits' own rows of D, copied from the evaluation-form input: D[b][j][t] = xe[b][t], t in digit j
 __global__ void modup_own_kernel(u64 *D, const u64 *__restrict__ xe, size_t xe_bstride, u32 lp, u32 K, u32 alpha,
                                  u32 beta, int logn) {
@@ -339,6 +389,132 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) moddown_kernel(u64 *out, cons
     }
 }
 
+// ModDown (or ModDown + rescale) in the two-kernel form.  Rows of the output: r =
+// ((s*B + b)*2 + k)*lpo + i.  The outer launch converts the dropped rows of acc (D -> q_i) straight
+// into the registers of the row's outer forward stages and writes them to the output row; the
+// inner launch runs the inner stages of each 1024-coefficient block in place and combines:
+// out = (acc_i - conv) * D^-1 (+ the addend gathered by sigma_g), as moddown_kernel does.
+template <int R>
+__global__ void __launch_bounds__(NTT2_COLS) moddown2_outer_kernel(u64 *out, const u64 *__restrict__ acc, u32 lp,
+                                                                   u32 K, u32 L1, u32 dbase, u32 KD, u32 lpo,
+                                                                   const u64 *__restrict__ mdtab,
+                                                                   const u64 *__restrict__ tw_all,
+                                                                   const PrimeDev *__restrict__ pd) {
+    const u32 N = 1024u << R;
+    const u32 r = blockIdx.x, i = r % lpo, sbk = r / lpo;
+    const u32 E = lp + K;
+    const PrimeDev P = pd[i];
+    const u64 *ab = acc + (size_t)sbk * E * N;
+    const u32 g = blockIdx.y * NTT2_COLS + threadIdx.x;
+    u64 x[1 << R];
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) {
+        const u32 n = g + 1024u * k;
+        if (KD == 1) {
+            x[k] = reduce64(ab[(size_t)dbase * N + n], P);
+        } else {
+            Acc128 a = {0, 0};
+            for (u32 kk = 0; kk < KD; ++kk) {
+                const u32 row = dbase + kk;
+                const PrimeDev &Pk = pd[row < lp ? row : L1 + (row - lp)];
+                const u64 hm = mdtab[2 * KD + (size_t)kk * L1 + i];   // Montgomery form
+                mac128(a, mul_shoup(ab[(size_t)row * N + n], mdtab[kk], mdtab[KD + kk], Pk.q), hm);
+            }
+            x[k] = redc128(a.lo, a.hi, P);
+        }
+    }
+    outer_fwd_regs<R>(x, tw_all + (size_t)i * 4 * N, P.q);
+    u64 *orow = out + (size_t)r * N + g;
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) orow[1024u * k] = x[k];
+}
+
+__global__ void __launch_bounds__(NTT2_INNER_THREADS) moddown2_inner_kernel(
+    u64 *out, const u64 *__restrict__ acc, const u64 *__restrict__ addend, size_t addend_bstride, u32 add_mask,
+    KeyList kl, u32 B, u32 lp, u32 K, u32 L1, u32 KD, u32 lpo, int logn, const u64 *__restrict__ mdtab,
+    const u64 *__restrict__ tw_all, const PrimeDev *__restrict__ pd) {
+    __shared__ u64 sm[1024 + 1024 / 16];
+    const u32 N = 1u << logn;
+    const u32 r = blockIdx.x, i = r % lpo, sbk = r / lpo;
+    const u32 k = sbk & 1, sb = sbk >> 1, s = sb / B, b = sb % B;
+    const u32 E = lp + K;
+    const PrimeDev P = pd[i];
+    const u32 goff = 1024u * blockIdx.y;
+    u64 *ob = out + (size_t)r * N;
+    block_load(sm, ob + goff, 1024);
+    inner_fwd_block(sm, logn, tw_all + (size_t)i * 4 * N, P.q, goff);
+    const u64 pinv = mdtab[2 * KD + (size_t)KD * L1 + i];
+    const u64 pinvs = mdtab[2 * KD + (size_t)KD * L1 + L1 + i];
+    const u64 *ai = acc + (size_t)sbk * E * N + (size_t)i * N;
+    const bool add = addend && ((add_mask >> k) & 1);
+    const u64 *adb = add ? addend + (size_t)b * addend_bstride + ((size_t)k * lpo + i) * N : nullptr;
+    const u32 g = kl.g[s];
+    for (u32 k2 = threadIdx.x; k2 < 512; k2 += blockDim.x) {
+        const u32 n = goff + 2 * k2;
+        const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ai + n);
+        u64 o0 = mul_shoup(sub_mod(x.x, sm[spad(2 * k2)], P.q), pinv, pinvs, P.q);
+        u64 o1 = mul_shoup(sub_mod(x.y, sm[spad(2 * k2 + 1)], P.q), pinv, pinvs, P.q);
+        if (add) {
+            o0 = add_mod(o0, adb[g == 1 ? n : galois_src(n, g, logn)], P.q);
+            o1 = add_mod(o1, adb[g == 1 ? n + 1 : galois_src(n + 1, g, logn)], P.q);
+        }
+        ulonglong2 o;
+        o.x = o0;
+        o.y = o1;
+        *reinterpret_cast<ulonglong2 *>(ob + n) = o;
+    }
+}
+
+// Rescale in the two-kernel form: rows r = (b*2 + k)*(lp-1) + i of the output; the outer launch
+// reduces the centred top limb (coefficient form, top) mod q_i into the outer stages, the inner
+// one finishes the NTT and combines out = (in_i - that) * q_top^-1.
+template <int R>
+__global__ void __launch_bounds__(NTT2_COLS) rescale2_outer_kernel(u64 *out, const u64 *__restrict__ top, u32 lp,
+                                                                   const u64 *__restrict__ tw_all,
+                                                                   const PrimeDev *__restrict__ pd) {
+    const u32 N = 1024u << R;
+    const u32 r = blockIdx.x, i = r % (lp - 1), bk = r / (lp - 1);
+    const PrimeDev P = pd[i];
+    const u64 qt = pd[lp - 1].q;
+    const u64 *tb = top + (size_t)bk * N;
+    const u32 g = blockIdx.y * NTT2_COLS + threadIdx.x;
+    u64 x[1 << R];
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) {
+        const u64 v = tb[g + 1024u * k];
+        x[k] = v > qt / 2 ? neg_mod(reduce64(qt - v, P), P.q) : reduce64(v, P);
+    }
+    outer_fwd_regs<R>(x, tw_all + (size_t)i * 4 * N, P.q);
+    u64 *orow = out + (size_t)r * N + g;
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) orow[1024u * k] = x[k];
+}
+
+__global__ void __launch_bounds__(NTT2_INNER_THREADS) rescale2_inner_kernel(u64 *out, const u64 *__restrict__ in,
+                                                                            u32 lp, int logn,
+                                                                            const u64 *__restrict__ rtab,
+                                                                            const u64 *__restrict__ tw_all,
+                                                                            const PrimeDev *__restrict__ pd) {
+    __shared__ u64 sm[1024 + 1024 / 16];
+    const u32 N = 1u << logn;
+    const u32 r = blockIdx.x, i = r % (lp - 1), bk = r / (lp - 1);
+    const PrimeDev P = pd[i];
+    const u32 goff = 1024u * blockIdx.y;
+    u64 *ob = out + (size_t)r * N;
+    block_load(sm, ob + goff, 1024);
+    inner_fwd_block(sm, logn, tw_all + (size_t)i * 4 * N, P.q, goff);
+    const u64 w = rtab[i], ws = rtab[lp - 1 + i];
+    const u64 *ib = in + ((size_t)bk * lp + i) * N;
+    for (u32 k2 = threadIdx.x; k2 < 512; k2 += blockDim.x) {
+        const u32 n = goff + 2 * k2;
+        const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ib + n);
+        ulonglong2 o;
+        o.x = mul_shoup(sub_mod(x.x, sm[spad(2 * k2)], P.q), w, ws, P.q);
+        o.y = mul_shoup(sub_mod(x.y, sm[spad(2 * k2 + 1)], P.q), w, ws, P.q);
+        *reinterpret_cast<ulonglong2 *>(ob + n) = o;
+    }
+}
+
 // acc[b][k][t] += P * d[b][k][t] on the data limbs t < lp (d: [B][3][lp][N], k < 2)
 __global__ void add_p_times_kernel(u64 *acc, const u64 *__restrict__ d, u32 lp, u32 K, int logn,
                                    const u64 *__restrict__ pq, const PrimeDev *__restrict__ pd, u32 B) {
@@ -537,14 +713,24 @@ void ks_modup(Ctx *c, u64 *D, const u64 *xe, size_t xe_bstride, u32 B, u32 lp) {
         }
     RowSet rs = rows_list(c, key, rows);
     if (rs.n == 0) return;
+    // the digit rows read (mostly from L2), each converted row written once; butterflies of its NTT
+    const double bytes = 8.0 * N * (double)rs.n * (1.0 + c->alpha), bfly = (double)rs.n * (N / 2);
+    const int sp = ntt_layout(c, TUNE_NTT);
+    if (sp == NTT_TWO_KERNEL) {
+        prof_begin(c);
+        NTT2_OUTER_LAUNCH(c, modup2_outer_kernel, c->logn, rs.n, D, (const u64 *)xc.p, rs, lp, c->K, c->alpha, beta,
+                          tab, (const u64 *)c->tw, (const PrimeDev *)c->pdev);
+        note_launch(c, "modup_ntt", bytes * c->alpha / (1.0 + c->alpha), bfly * (c->logn - NTT2_INNER_LOGN));
+        prof_begin(c);
+        ntt2_inner(c, D, rs, 0);
+        note_launch(c, "modup_ntt", bytes / (1.0 + c->alpha), bfly * NTT2_INNER_LOGN);
+        return;
+    }
     prof_begin(c);
-    const int sp = tune_split(c, TUNE_NTT);
     launch_parts(c, modup_ntt_kernel<0>, modup_ntt_kernel<1>, dim3(rs.n), sp, ntt_part_threads(c->logn, sp),
                  ntt_part_smem(c->logn, sp), D, (const u64 *)xc.p, rs, lp, c->K, c->alpha, beta, c->logn, tab,
                  (const u64 *)c->tw, (const PrimeDev *)c->pdev);
-    // the digit rows read (mostly from L2), each converted row written once; butterflies of its NTT
-    note_launch(c, "modup_ntt", 8.0 * N * (double)rs.n * (1.0 + c->alpha),
-                (double)rs.n * (N / 2) * c->logn);
+    note_launch(c, "modup_ntt", bytes, bfly * c->logn);
 }
 
 // acc [S][B][2][lp+K][N] = sum_j sigma_{g_s}(D_j) (o) key_s,j
@@ -611,6 +797,35 @@ void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u3
                 (double)S * B * E * N * 2 * beta);
 }
 
+// the division of acc [S][B][2][lp+K][N] by the dropped basis (KD rows from dbase) onto lpo output
+// limbs, in the tuned limb layout; bytes = the algorithmic bytes of the operation
+static void moddown_launch(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bstride, u32 add_mask,
+                           const KeyList &kl, u32 S, u32 B, u32 lp, u32 dbase, u32 KD, u32 lpo, const u64 *tab,
+                           double bytes) {
+    const u32 N = c->N;
+    const double bfly = (double)S * B * 2 * lpo * (N / 2);
+    const int sp = ntt_layout(c, TUNE_MODDOWN);
+    if (sp == NTT_TWO_KERNEL) {
+        const u32 rows = S * B * 2 * lpo;
+        prof_begin(c);
+        NTT2_OUTER_LAUNCH(c, moddown2_outer_kernel, c->logn, rows, out, (const u64 *)acc, lp, c->K, c->L1, dbase,
+                          KD, lpo, tab, (const u64 *)c->tw, (const PrimeDev *)c->pdev);
+        note_launch(c, "moddown", bytes / 2, bfly * (c->logn - NTT2_INNER_LOGN));
+        prof_begin(c);
+        moddown2_inner_kernel<<<dim3(rows, N >> NTT2_INNER_LOGN), NTT2_INNER_THREADS, 0, c->stream>>>(
+            out, (const u64 *)acc, addend, addend_bstride, add_mask, kl, B, lp, c->K, c->L1, KD, lpo, c->logn, tab,
+            (const u64 *)c->tw, (const PrimeDev *)c->pdev);
+        note_launch(c, "moddown", bytes / 2, bfly * NTT2_INNER_LOGN);
+        return;
+    }
+    dim3 grid(lpo, 2, S * B);
+    prof_begin(c);
+    launch_parts(c, moddown_kernel<0>, moddown_kernel<1>, grid, sp, ntt_part_threads(c->logn, sp),
+                 ntt_part_smem(c->logn, sp), out, (const u64 *)acc, addend, addend_bstride, add_mask, kl, B, lp,
+                 c->K, c->L1, dbase, KD, lpo, c->logn, tab, (const u64 *)c->tw, (const PrimeDev *)c->pdev);
+    note_launch(c, "moddown", bytes, bfly * c->logn);
+}
+
 // out [S][B][2][lp][N] = ModDown(acc) (+ addend: poly k of ct b gathered by sigma_{g_s} when add_mask bit k)
 void ks_moddown(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bstride, u32 add_mask,
                 const KeyList &kl, u32 S, u32 B, u32 lp) {
@@ -622,16 +837,8 @@ void ks_moddown(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bst
         for (u32 k = 0; k < 2; ++k)
             for (u32 kk = 0; kk < c->K; ++kk) rows.push_back((((sb * 2 + k) * E + lp + kk) << 8) | (c->L1 + kk));
     ntt_inverse(c, acc, rows_list(c, key, rows));
-    dim3 grid(lp, 2, S * B);
-    prof_begin(c);
-    const int sp = tune_split(c, TUNE_MODDOWN);
-    launch_parts(c, moddown_kernel<0>, moddown_kernel<1>, grid, sp, ntt_part_threads(c->logn, sp),
-                 ntt_part_smem(c->logn, sp), out, (const u64 *)acc, addend, addend_bstride, add_mask, kl, B, lp,
-                 c->K, c->L1, lp, c->K, lp, c->logn, moddown_table(c), (const u64 *)c->tw,
-                 (const PrimeDev *)c->pdev);
-    note_launch(c, "moddown",
-                8.0 * N * (double)S * B * (2.0 * E + (addend ? __builtin_popcount(add_mask) : 0) * lp + 2.0 * lp),
-                (double)S * B * 2 * lp * (N / 2) * c->logn);
+    moddown_launch(c, out, acc, addend, addend_bstride, add_mask, kl, S, B, lp, lp, c->K, lp, moddown_table(c),
+                   8.0 * N * (double)S * B * (2.0 * E + (addend ? __builtin_popcount(add_mask) : 0) * lp + 2.0 * lp));
 }
 
 // out [nct][2][lp-1][N] = ModDown and rescale of acc [nct][2][lp+K][N] as one division by q_top * P
@@ -650,15 +857,8 @@ void ks_moddown_rescale(Ctx *c, u64 *out, u64 *acc, u32 nct, u32 lp) {
     KeyList none;
     none.g[0] = 1;
     none.key[0] = nullptr;
-    dim3 grid(lp - 1, 2, nct);
-    prof_begin(c);
-    const int sp = tune_split(c, TUNE_MODDOWN);
-    launch_parts(c, moddown_kernel<0>, moddown_kernel<1>, grid, sp, ntt_part_threads(c->logn, sp),
-                 ntt_part_smem(c->logn, sp), out, (const u64 *)acc, (const u64 *)nullptr, (size_t)0, 0u, none,
-                 nct, lp, c->K, c->L1, lp - 1, c->K + 1, lp - 1, c->logn, moddown_rescale_table(c, lp),
-                 (const u64 *)c->tw, (const PrimeDev *)c->pdev);
-    note_launch(c, "moddown", 8.0 * N * (double)nct * (2.0 * E + 2.0 * (lp - 1)),
-                (double)nct * 2 * (lp - 1) * (N / 2) * c->logn);
+    moddown_launch(c, out, acc, nullptr, 0, 0, none, 1, nct, lp, lp - 1, c->K + 1, lp - 1,
+                   moddown_rescale_table(c, lp), 8.0 * N * (double)nct * (2.0 * E + 2.0 * (lp - 1)));
 }
 
 // acc [B][2][lp+K][N] += P * (d0, d1) on the data limbs; d [B][3][lp][N]
@@ -677,10 +877,23 @@ void rescale_batch(Ctx *c, u64 *out, const u64 *in, u32 B, u32 lp) {
     DBuf top(c, (size_t)B * 2 * N);
     gather_rows(c, top.p, in + (size_t)(lp - 1) * N, B * 2, lp);
     ntt_inverse(c, top.p, rows_regular(B * 2, 1, 0, lp - 1));
+    const double bytes = 8.0 * N * (double)B * 2 * (lp + 1 + lp - 1), bfly = (double)B * 2 * (lp - 1) * (N / 2);
+    const int sp = ntt_layout(c, TUNE_RESCALE);
+    if (sp == NTT_TWO_KERNEL) {
+        const u32 rows = B * 2 * (lp - 1);
+        prof_begin(c);
+        NTT2_OUTER_LAUNCH(c, rescale2_outer_kernel, c->logn, rows, out, (const u64 *)top.p, lp, (const u64 *)c->tw,
+                          (const PrimeDev *)c->pdev);
+        note_launch(c, "rescale", bytes / 2, bfly * (c->logn - NTT2_INNER_LOGN));
+        prof_begin(c);
+        rescale2_inner_kernel<<<dim3(rows, N >> NTT2_INNER_LOGN), NTT2_INNER_THREADS, 0, c->stream>>>(
+            out, in, lp, c->logn, rescale_table(c, lp), (const u64 *)c->tw, (const PrimeDev *)c->pdev);
+        note_launch(c, "rescale", bytes / 2, bfly * NTT2_INNER_LOGN);
+        return;
+    }
     dim3 grid(lp - 1, 2, B);
     prof_begin(c);
-    const int sp = tune_split(c, TUNE_RESCALE);
     launch_parts(c, rescale_kernel<0>, rescale_kernel<1>, grid, sp, ntt_part_threads(c->logn, sp), ntt_part_smem(c->logn, sp), out, in,
                  (const u64 *)top.p, lp, c->logn, rescale_table(c, lp), (const u64 *)c->tw, (const PrimeDev *)c->pdev);
-    note_launch(c, "rescale", 8.0 * N * (double)B * 2 * (lp + 1 + lp - 1), (double)B * 2 * (lp - 1) * (N / 2) * c->logn);
+    note_launch(c, "rescale", bytes, bfly * c->logn);
 }

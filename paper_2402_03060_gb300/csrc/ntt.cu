@@ -35,14 +35,79 @@ __global__ void __launch_bounds__(NTT_MAX_THREADS) ntt_rows_kernel(u64 *base, Ro
     block_store(g, sm, pt.n);
 }
 
+// two-kernel form (ntt_block.cuh): the outer stages of every row, one column per thread
+template <int R>
+__global__ void __launch_bounds__(NTT2_COLS) ntt2_outer_kernel(u64 *base, RowSet rs, const u64 *tw_all,
+                                                               const PrimeDev *pd, int inverse) {
+    const u32 N = 1024u << R;
+    u32 off, prime;
+    row_of(rs, blockIdx.x, off, prime);
+    u64 *col = base + (size_t)off * N + blockIdx.y * NTT2_COLS + threadIdx.x;
+    const u64 *tw = tw_all + (size_t)prime * 4 * N;
+    const PrimeDev P = pd[prime];
+    u64 v[1 << R];
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) v[k] = col[1024u * k];
+    if (inverse)
+        outer_inv_regs<R>(v, tw, N, P.q, P.ninv, P.ninvs);
+    else
+        outer_fwd_regs<R>(v, tw, P.q);
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) col[1024u * k] = v[k];
+}
+
+// ... and the inner stages of every 1024-coefficient block (grid.x = rows, grid.y = blocks)
+__global__ void __launch_bounds__(NTT2_INNER_THREADS) ntt2_inner_kernel(u64 *base, RowSet rs, const u64 *tw_all,
+                                                                        const PrimeDev *pd, int logn, int inverse) {
+    __shared__ u64 sm[1024 + 1024 / 16];
+    const u32 N = 1u << logn;
+    u32 off, prime;
+    row_of(rs, blockIdx.x, off, prime);
+    const u32 goff = 1024u * blockIdx.y;
+    u64 *g = base + (size_t)off * N + goff;
+    const u64 *tw = tw_all + (size_t)prime * 4 * N;
+    const u64 q = pd[prime].q;
+    block_load(sm, g, 1024);
+    if (inverse)
+        inner_inv_block(sm, logn, tw, q, goff);
+    else
+        inner_fwd_block(sm, logn, tw, q, goff);
+    block_store(g, sm, 1024);
+}
+
+// the inner launch of the two-kernel form over the rows of rs (forward after, inverse before the outer one)
+void ntt2_inner(Ctx *c, u64 *base, const RowSet &rs, int inverse) {
+    ntt2_inner_kernel<<<dim3(rs.n, c->N >> NTT2_INNER_LOGN), NTT2_INNER_THREADS, 0, c->stream>>>(
+        base, rs, (const u64 *)c->tw, (const PrimeDev *)c->pdev, c->logn, inverse);
+}
+
 static void ntt_launch(Ctx *c, u64 *base, const RowSet &rs, int inverse) {
     if (rs.n == 0) return;
-    prof_begin(c);
-    const int sp = tune_split(c, TUNE_NTT);
-    launch_parts(c, ntt_rows_kernel<0>, ntt_rows_kernel<1>, dim3(rs.n), sp, ntt_part_threads(c->logn, sp), ntt_part_smem(c->logn, sp), base, rs,
-                 (const u64 *)c->tw, (const PrimeDev *)c->pdev, c->logn, inverse);
+    if (rs.n > 0x7fffffffu) throw HeError(HE_EINVAL, "NTT: too many rows");
+    const char *name = inverse ? "intt" : "ntt";
     // each limb read and written once; (N/2) log2 N butterflies per limb
-    note_launch(c, inverse ? "intt" : "ntt", 16.0 * rs.n * c->N, (double)rs.n * (c->N / 2) * c->logn);
+    const double bytes = 16.0 * rs.n * c->N, bfly = (double)rs.n * (c->N / 2);
+    const int sp = ntt_layout(c, TUNE_NTT);
+    if (sp == NTT_TWO_KERNEL) {
+        // the algorithmic bytes split evenly, the butterflies by stage count (10 inner, logn - 10 outer)
+        auto inner = [&] {
+            prof_begin(c);
+            ntt2_inner(c, base, rs, inverse);
+            note_launch(c, name, bytes / 2, bfly * NTT2_INNER_LOGN);
+        };
+        if (inverse) inner();
+        prof_begin(c);
+        NTT2_OUTER_LAUNCH(c, ntt2_outer_kernel, c->logn, rs.n, base, rs, (const u64 *)c->tw,
+                          (const PrimeDev *)c->pdev, inverse);
+        note_launch(c, name, bytes / 2, bfly * (c->logn - NTT2_INNER_LOGN));
+        if (!inverse) inner();
+        return;
+    }
+    prof_begin(c);
+    launch_parts(c, ntt_rows_kernel<0>, ntt_rows_kernel<1>, dim3(rs.n), sp, ntt_part_threads(c->logn, sp),
+                 ntt_part_smem(c->logn, sp), base, rs, (const u64 *)c->tw, (const PrimeDev *)c->pdev, c->logn,
+                 inverse);
+    note_launch(c, name, bytes, bfly * c->logn);
 }
 
 void ntt_forward(Ctx *c, u64 *base, const RowSet &rs) { ntt_launch(c, base, rs, 0); }

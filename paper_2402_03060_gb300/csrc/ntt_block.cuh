@@ -399,3 +399,91 @@ __device__ __forceinline__ void block_store(u64 *__restrict__ g, const u64 *s, u
         g2[k] = v;
     }
 }
+
+// ---------------------------------------------------------------- two-kernel form
+// A limb of N = 2^logn (11 <= logn <= 15) transformed by two launches instead of one CTA (or
+// cluster) holding it whole.  Write a coefficient index as j = 1024 k + e: the R = logn - 10
+// "outer" stages (distances N/2 .. 1024) act on the 1024 columns {e + 1024 k : k < 2^R}, one
+// column per thread in registers; the ten "inner" stages (distances 512 .. 1) act on each
+// 1024-coefficient block alone, one small CTA per block with the block in shared memory.
+// Forward: outer launch, then inner; inverse: inner, then outer (with the N^-1 factor).  Every
+// butterfly is the one-CTA transform's (same twiddle, same lazy reduction), so the results are
+// the same bits.  The blocks are independent, so many small CTAs share an SM and their loads,
+// stores and arithmetic overlap -- the one-CTA form runs one 512-thread CTA per SM at N = 2^14
+// with all its warps in the same phase.  Cost: one more pass of the limb through L2 / HBM.
+#define NTT2_INNER_LOGN 10
+#define NTT2_COLS 128          // columns (threads) per CTA of an outer launch
+#define NTT2_INNER_THREADS 64  // threads per CTA of an inner launch: one radix-16 group each
+static inline bool ntt2_ok(int logn) { return logn >= 11 && logn <= 15; }
+
+// R outer forward stages on one column held in registers (stage st pairs k and k + 2^(R-1-st);
+// its twiddle index m + (k >> (R - st)) with m = 2^st does not depend on the column)
+template <int R>
+__device__ __forceinline__ void outer_fwd_regs(u64 (&v)[1 << R], const u64 *__restrict__ tw, u64 q) {
+    const u64 q2 = 2 * q;
+#pragma unroll
+    for (int st = 0; st < R; ++st) {
+        const int h = 1 << (R - 1 - st);
+#pragma unroll
+        for (int k0 = 0; k0 < (1 << R); k0 += 2 * h) {
+            const ulonglong2 W = tw_fwd(tw, (1u << st) + (u32)(k0 >> (R - st)));
+#pragma unroll
+            for (int kk = 0; kk < h; ++kk) {
+                u64 U = v[k0 + kk];
+                if (U >= q2) U -= q2;
+                const u64 V = shoup_lazy(v[k0 + kk + h], W.x, W.y, q);
+                v[k0 + kk] = U + V;
+                v[k0 + kk + h] = U - V + q2;
+            }
+        }
+    }
+}
+
+// R outer inverse stages (distances 1024 * 2^b, b = 0 .. R-1) on one column, then the N^-1 factor
+template <int R>
+__device__ __forceinline__ void outer_inv_regs(u64 (&v)[1 << R], const u64 *__restrict__ tw, u32 N, u64 q,
+                                               u64 ninv, u64 ninvs) {
+    const u64 q2 = 2 * q;
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+        const int d = 1 << b;
+        const u32 hb = N >> (NTT2_INNER_LOGN + 1 + b);
+#pragma unroll
+        for (int k0 = 0; k0 < (1 << R); k0 += 2 * d) {
+            const ulonglong2 W = tw_inv(tw, N, hb + (u32)(k0 >> (b + 1)));
+#pragma unroll
+            for (int kk = 0; kk < d; ++kk) {
+                const u64 U = v[k0 + kk], V = v[k0 + kk + d];
+                u64 sm = U + V;
+                if (sm >= q2) sm -= q2;
+                v[k0 + kk] = sm;
+                v[k0 + kk + d] = shoup_lazy(U - V + q2, W.x, W.y, q);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k) v[k] = mul_shoup(v[k], ninv, ninvs, q);
+}
+
+// the ten inner forward stages of the block at goff (held in sm by the caller), outputs in [0, q)
+__device__ __forceinline__ void inner_fwd_block(u64 *sm, int logn, const u64 *__restrict__ tw, u64 q, u32 goff) {
+    fwd_local(sm, logn, logn - NTT2_INNER_LOGN, tw, q, NTT2_INNER_LOGN, goff);
+}
+// the ten inner inverse stages of the block at goff (no N^-1 factor: the outer launch applies it)
+__device__ __forceinline__ void inner_inv_block(u64 *sm, int logn, const u64 *__restrict__ tw, u64 q, u32 goff) {
+    inv_local(sm, logn, NTT2_INNER_LOGN, tw, q, NTT2_INNER_LOGN, goff, false, 0, 0);
+}
+
+// launch the outer kernel template instance for R = logn - 10 (grid.x = rows, grid.y = column tiles)
+#define NTT2_OUTER_LAUNCH(c, KERN, logn, rows, ...)                                                     \
+    do {                                                                                                \
+        const dim3 g__((rows), (1u << NTT2_INNER_LOGN) / NTT2_COLS);                                    \
+        switch ((logn) - NTT2_INNER_LOGN) {                                                             \
+            case 1: KERN<1><<<g__, NTT2_COLS, 0, (c)->stream>>>(__VA_ARGS__); break;                    \
+            case 2: KERN<2><<<g__, NTT2_COLS, 0, (c)->stream>>>(__VA_ARGS__); break;                    \
+            case 3: KERN<3><<<g__, NTT2_COLS, 0, (c)->stream>>>(__VA_ARGS__); break;                    \
+            case 4: KERN<4><<<g__, NTT2_COLS, 0, (c)->stream>>>(__VA_ARGS__); break;                    \
+            case 5: KERN<5><<<g__, NTT2_COLS, 0, (c)->stream>>>(__VA_ARGS__); break;                    \
+            default: throw HeError(HE_EINVAL, "two-kernel NTT: ring degree out of range");             \
+        }                                                                                               \
+    } while (0)

@@ -177,7 +177,8 @@ static void retire_batch(he_server *s, Batch *b) {
     if (s->simulate) return;
     Ctx *c = b->M->m->c;
     CtxLock lk(c);
-    const size_t cw = cts_ct_words(c, b->reqs[0]->in.lp);
+    // each request's slice of the result batch, in the result's own ciphertext size
+    const size_t cw = cts_ct_words(c, b->out.lp);
     size_t at = 0;
     for (Request *r : b->reqs) {
         if (b->err == HE_OK) r->out = ct_wrap(c, cts_view(b->out, at * cw, r->B));

@@ -2,9 +2,11 @@
 //
 // Every knob changes how work is laid out over CTAs, never the arithmetic, so
 // all choices give bit-identical ciphertexts:
-//   * limb split (NTT, fused ModDown, fused rescale): one CTA per limb, or a
+//   * limb layout (NTT, fused ModDown, fused rescale): one CTA per limb, a
 //     2-CTA cluster per limb (half the shared memory and threads per CTA, so
-//     more CTAs resident per SM, at the cost of one stage through DSMEM);
+//     more CTAs resident per SM, at the cost of one stage through DSMEM), or
+//     two launches -- the outer stages over columns, the inner ten over
+//     independent 1024-coefficient blocks (many small CTAs per SM);
 //   * MAC output group: how many output accumulators one launch keeps in
 //     registers (fewer: more resident warps, but the inputs are re-read per group);
 //   * hoisted key-switch accumulation: ciphertexts per thread (key reuse in
@@ -22,11 +24,18 @@
 #include "ntt_block.cuh"
 #include "ops.cuh"
 
-int tune_split(const Ctx *c, int knob) {
-    const int mn = ntt_min_split(c->logn);
+static bool layout_ok(int logn, int v) {
+    if (v == NTT_TWO_KERNEL) return ntt2_ok(logn);
+    if (v == 1) return ntt_can_split(logn);
+    return v == 0 && !ntt_min_split(logn);
+}
+
+static int layout_default(int logn) { return logn >= 14 && ntt2_ok(logn) ? NTT_TWO_KERNEL : ntt_min_split(logn); }
+
+int ntt_layout(const Ctx *c, int knob) {
     const int v = c->tuned[knob];
-    if (v < 0 || !ntt_can_split(c->logn)) return mn;
-    return v > mn ? v : mn;
+    if (v >= 0 && layout_ok(c->logn, v)) return v;
+    return layout_default(c->logn);
 }
 
 namespace {
@@ -79,7 +88,7 @@ void sweep(Ctx *c, int knob, const std::vector<int> &cands, const std::function<
 std::string cache_key(const Ctx *c) {
     cudaDeviceProp prop;
     CUDA_TRY(cudaGetDeviceProperties(&prop, c->device));
-    std::string k = fmt("%s|sm%d%d|logn%d|L%u|K%u|dnum%u", prop.name, prop.major, prop.minor, c->logn, c->L1, c->K,
+    std::string k = fmt("v2|%s|sm%d%d|logn%d|L%u|K%u|dnum%u", prop.name, prop.major, prop.minor, c->logn, c->L1, c->K,
                         c->dnum);
     for (char &ch : k)
         if (ch == '"' || ch == '\\') ch = '_';
@@ -135,8 +144,14 @@ std::string entry_of(const Ctx *c) {
 void measure(Ctx *c, std::ostringstream &rep) {
     const u32 N = c->N, lp = c->L1, K = c->K, E = lp + K, B = 16;
     const u32 beta = ks_digits(c, lp);
-    const bool can = ntt_can_split(c->logn) && !ntt_min_split(c->logn);
-    const std::vector<int> splits = can ? std::vector<int>{0, 1} : std::vector<int>{ntt_min_split(c->logn)};
+    // limb layouts this N allows, the default first (kept unless another is 2 % faster)
+    std::vector<int> splits;
+    {
+        const int dflt = layout_default(c->logn);
+        splits.push_back(dflt);
+        for (int v : {0, 1, NTT_TWO_KERNEL})
+            if (v != dflt && layout_ok(c->logn, v)) splits.push_back(v);
+    }
     rep << "{";
     {   // NTT of 2*lp limbs of 16 ciphertexts
         DBuf a(c, (size_t)B * 2 * lp * N);

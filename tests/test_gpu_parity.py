@@ -60,11 +60,16 @@ def test_primes_match_oracle(G):
         assert ctx.primes() == ckks.gen_primes(list(P["data_bits"]) + list(P["special_bits"]), P["logn"])
 
 
-@pytest.mark.parametrize("logn", [4, 10, 13, 14, 15])
-def test_ntt_matches_oracle(G, logn):
+# limb layouts: None the default for N, 0 one CTA per limb, 1 a 2-CTA cluster, 2 the two-kernel
+# form (outer stages over columns, inner stages over 1024-coefficient blocks)
+@pytest.mark.parametrize("logn,layout", [(4, None), (10, None), (13, None), (14, None), (15, None),
+                                         (11, 2), (12, 2), (13, 2), (14, 0), (14, 1), (15, 1)])
+def test_ntt_matches_oracle(G, logn, layout):
     import torch
     P = dict(logn=logn, data_bits=[60, 40], special_bits=[60], dnum=2, log2_scale=30)
     ctx = G.Context(seed=1, **P)
+    if layout is not None:
+        ctx.set_tuning(ntt_split=layout)
     he = ckks.Ckks(seed=1, **P)
     qs = ctx.primes()
     rng = np.random.default_rng(logn)

@@ -22,17 +22,22 @@ def G():
     return lib
 
 
+# limb layouts: 0 one CTA per limb, 1 a 2-CTA cluster, 2 the two-kernel form (outer stages over
+# columns, inner stages over 1024-coefficient blocks)
 SETTINGS = [
     dict(ntt_split=1, moddown_split=1, rescale_split=1, mac_group=4, lazy_bt=1, lazy_order=1, mac_bk=16, mac_split=1),
     dict(ntt_split=0, moddown_split=1, rescale_split=0, mac_group=6, lazy_bt=4, lazy_order=0, mac_bk=32, mac_split=2),
     dict(ntt_split=1, moddown_split=0, rescale_split=1, mac_group=12, lazy_bt=2, lazy_order=1, mac_bk=64, mac_split=2),
+    dict(ntt_split=2, moddown_split=2, rescale_split=2, mac_group=8, lazy_bt=2, lazy_order=0, mac_bk=32, mac_split=1),
+    dict(ntt_split=2, moddown_split=0, rescale_split=1, mac_group=12, lazy_bt=4, lazy_order=1, mac_bk=64, mac_split=1),
 ]
 
 
-@pytest.mark.parametrize("params", ["lenet1", "serve_lenet1"])
+@pytest.mark.parametrize("params", ["lenet1", "serve_lenet1", "lenet1_2_14"])
 def test_every_launch_shape_gives_the_same_ciphertexts(G, params):
-    P = dict(W.PARAMS["lenet1"] if params == "lenet1" else W.SERVE_PARAMS["lenet1"])
-    P["logn"] = 12                      # 2048 slots: two samples per ciphertext
+    P = dict(W.SERVE_PARAMS["lenet1"] if params == "serve_lenet1" else W.PARAMS["lenet1"])
+    if params != "lenet1_2_14":
+        P["logn"] = 12                  # 2048 slots: two samples per ciphertext
     model = W.lenet1()
     stride, levels, steps = G.plan(model, 28, 28)
     ctx = G.Context(seed=W.KEY_SEED, **P)
