@@ -279,9 +279,11 @@ void he_model_free(he_model *m);
  * Call it before he_model_compile / the first he_infer: captured CUDA graphs
  * keep the shapes they were captured with.  Errors: HE_EINVAL, HE_ENOMEM, HE_ECUDA. */
 he_status he_autotune(he_ctx *ctx, const char *cache_path, char *report, size_t report_len);
-/* The tuned knobs in the order: NTT split, ModDown split, rescale split, MAC
- * output group, key-switch ciphertexts per thread, key-switch grid order,
- * polynomials per MAC CTA, threads per coefficient of a MAC group (-1 = default).  he_tuning_set overrides them (values outside a knob's
+/* The tuned knobs in the order: NTT limb layout, ModDown limb layout, rescale limb layout
+ * (0 one CTA per limb, 1 a 2-CTA cluster, 2 two launches: outer stages over columns,
+ * inner stages over 1024-coefficient blocks), MAC output group, key-switch ciphertexts
+ * per thread, key-switch grid order, polynomials per MAC CTA, threads per coefficient of
+ * a MAC group, ciphertexts per thread of the one-pass combination (-1 = default).  he_tuning_set overrides them (values outside a knob's
  * candidates fall back to the nearest valid launch shape). */
 he_status he_tuning_get(he_ctx *ctx, int32_t *values, size_t n);
 he_status he_tuning_set(he_ctx *ctx, const int32_t *values, size_t n);

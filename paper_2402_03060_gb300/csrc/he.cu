@@ -890,10 +890,7 @@ Cts ct_lincomb_chan(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<std::
     ks_modup(c, D.p, X.data() + (size_t)lp * N, (size_t)2 * lp * N, Bt, lp);
     const size_t zw = (size_t)B * 2 * E * N;
     DBuf Z(c, zw);
-    const size_t per_step = zw * 8;
-    size_t chunk = ((size_t)4 << 30) / (per_step ? per_step : 1);
-    chunk = std::max<size_t>(1, std::min<size_t>(chunk, KEYLIST_MAX));
-    DBuf acc(c, std::min<size_t>(chunk, K) * zw);
+    const size_t chunk = KEYLIST_MAX;
     for (u32 i = 0; i < CH; ++i) {
         for (u32 s0 = 0; s0 < K; s0 += (u32)chunk) {
             const u32 Sc = std::min<u32>((u32)chunk, K - s0);
@@ -905,10 +902,9 @@ Cts ct_lincomb_chan(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<std::
                 kl.key[s] = g == 1 ? nullptr : c->gk.at(g).p;
                 kl.keyp[s] = g == 1 ? nullptr : c->gkp.at(g).p;
             }
-            ks_lazy(c, acc.p, D.p + (size_t)i * B * beta * E * N, X.data() + i * bw, kl, Sc, B, lp);
-            // Z += sum_{k in chunk} pts[i][k] (.) acc[k]
-            mac(c, Z.p, zw, acc.p, zw, pts + ((size_t)i * K + s0) * E * N, 1, Sc, B, E, lp, c->L1, i > 0 || s0 > 0,
-                (size_t)CH * K * E * N);
+            // Z += sum_{k in chunk} pts[i][k] (.) A_k(X_i), the accumulators summed in registers
+            ks_comb(c, Z.p, D.p + (size_t)i * B * beta * E * N, X.data() + i * bw, kl, Sc, 1, B, lp,
+                    pts + ((size_t)i * K + s0) * E * N, 1, (size_t)K * E * N, i > 0 || s0 > 0);
         }
     }
     if (rescale) {
@@ -970,11 +966,17 @@ Cts ct_lincomb(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &step
     const u32 nout = pts ? O : CH;   // outputs, each a batch of B ciphertexts
     const size_t zw = (size_t)B * 2 * E * N;    // one output batch over Q u P
     DBuf Z(c, (size_t)nout * zw);
-    // steps per chunk: bounded by the key list and by ~4 GB of accumulators
+    // the one-pass combination for plain sums and single outputs (measured: with four outputs, the
+    // first convolution, the per-step accumulators with their shared key loads are faster)
+    const bool comb = (!pts || O == 1) && (size_t)(pts ? B : Bt) <= 4 * 65535;
+    // steps per chunk: bounded by the key list and, when per-step accumulators are kept, by ~16 GB of
+    // them (every chunk after the first re-reads and re-writes the output accumulators, so one chunk
+    // for the second LeNet-1 convolution's 25 steps of 256 ciphertexts, 11.7 GB)
     const size_t per_step = (size_t)Bt * 2 * E * N * 8;
-    size_t chunk = ((size_t)4 << 30) / (per_step ? per_step : 1);
+    size_t chunk = comb ? KEYLIST_MAX : ((size_t)16 << 30) / (per_step ? per_step : 1);
     chunk = std::max<size_t>(1, std::min<size_t>(chunk, KEYLIST_MAX));
-    DBuf acc(c, std::min<size_t>(chunk, S) * Bt * 2 * E * N);
+    DBuf acc;
+    if (!comb) acc = DBuf(c, std::min<size_t>(chunk, S) * Bt * 2 * E * N);
     for (u32 s0 = 0; s0 < S; s0 += (u32)chunk) {
         const u32 Sc = std::min<u32>((u32)chunk, S - s0);
         KeyList kl;
@@ -984,6 +986,13 @@ Cts ct_lincomb(Ctx *c, const Cts &X, u32 CH, u32 B, const std::vector<int> &step
             kl.ginv[s] = c->galois_inverse(g);
             kl.key[s] = g == 1 ? nullptr : c->gk.at(g).p;
             kl.keyp[s] = g == 1 ? nullptr : c->gkp.at(g).p;
+        }
+        if (comb) {
+            // few outputs (pooling, the flatten's stages, FC, a first convolution): every step's
+            // accumulator summed in registers, one pass, no per-step accumulators in memory
+            ks_comb(c, Z.p, D.p, X.data(), kl, Sc, CH, B, lp, pts ? pts + (size_t)s0 * CH * E * N : nullptr, O,
+                    (size_t)S * CH * E * N, s0 > 0);
+            continue;
         }
         ks_lazy(c, acc.p, D.p, X.data(), kl, Sc, Bt, lp);
         if (pts) {

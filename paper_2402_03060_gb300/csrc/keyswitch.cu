@@ -314,6 +314,134 @@ __global__ void __launch_bounds__(256, (BT == 4 && MAXD == 8) ? 2 : 3) ks_lazy_p
     }
 }
 
+// A hoisted linear combination accumulated in one pass, with the digits gathered at each step's
+// Galois permutation (the addressing of ks_inner_kernel) instead of one accumulator per step
+// written out and summed by a second kernel:
+//   weighted (w != null): Z[o][b] (+)= sum_{s<S} sum_{i<CH} w[o][s*CH + i] (.) A_s(X_{i*B+b}),  o < O
+//   plain    (w == null): Z[c]    (+)= sum_{s<S} A_s(X_c) for every input ciphertext c < CH*B
+// with A_s(X) = (sum_j sigma_g(D_j) (.) ksk_{g,j,0} + P*sigma_g(c0),  sum_j sigma_g(D_j) (.) ksk_{g,j,1})
+// over Q_l u P (A_s = (P*c0, P*c1) for g = 1) -- the accumulators of ks_lazy_kernel, same values.
+// Z [O or CH*B][2][E][N]; w [O][S*CH][E][N] at ostride words per output.  One thread per
+// coefficient of one limb for BT ciphertexts, both polynomials; grid (n-tiles, ciphertext groups,
+// limbs), n-tiles fastest, so the digit rows of a group stay in L2 while their tiles are gathered.
+// The weighted sums are 128-bit lazy (folded every 64 terms), the plain ones reduced per term.
+// OM = 0: the plain form (w must be null), else the weighted form with up to OM outputs.
+template <int OM, int BT>
+__global__ void __launch_bounds__(256, BT == 2 ? 3 : 2) ks_comb_kernel(u64 *__restrict__ Z, const u64 *__restrict__ D,
+                                                      const u64 *__restrict__ x, KeyList kl, u32 S, u32 CH, u32 B,
+                                                      u32 beta, u32 lp, u32 K, u32 L1, int logn,
+                                                      const u64 *__restrict__ w, u32 O, size_t w_ostride,
+                                                      int accumulate, const u64 *__restrict__ pq,
+                                                      const PrimeDev *__restrict__ pd) {
+    const u32 N = 1u << logn;
+    const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 t = blockIdx.z;
+    const u32 E = lp + K;
+    const u32 pt = t < lp ? t : L1 + (t - lp);
+    const PrimeDev P = pd[pt];
+    const size_t kstride = (size_t)(L1 + K) * N;
+    constexpr bool weighted = OM > 0;
+    constexpr int OA = OM > 0 ? OM : 1;
+    // the ciphertexts of this thread: weighted -> b = bg*BT + u of every channel; plain -> c = bg*BT + u
+    const u32 nb = weighted ? B : CH * B;
+    const u32 c0 = blockIdx.y * BT;
+    if (n >= N) return;
+    Acc128 zw[weighted ? OA : 1][weighted ? BT : 1][2];
+    u64 zp[weighted ? 1 : BT][2];
+#pragma unroll
+    for (int o = 0; o < (weighted ? OA : 1); ++o)
+#pragma unroll
+        for (int u = 0; u < (weighted ? BT : 1); ++u) zw[o][u][0] = zw[o][u][1] = Acc128{0, 0};
+#pragma unroll
+    for (int u = 0; u < (weighted ? 1 : BT); ++u) zp[u][0] = zp[u][1] = 0;
+    const u32 nch = weighted ? CH : 1;
+    u32 terms = 0;
+    for (u32 s = 0; s < S; ++s) {
+        const u32 g = kl.g[s];
+        const u32 src = g == 1 ? n : galois_src(n, g, logn);
+        const u64 *key = kl.key[s];
+        for (u32 i = 0; i < nch; ++i) {
+            u64 a[BT][2];
+#pragma unroll
+            for (int u = 0; u < BT; ++u) {
+                const u32 bb = c0 + u < nb ? c0 + u : nb - 1;      // clamp: duplicates are not stored
+                const u32 ct = weighted ? i * B + bb : bb;
+                const u64 *xb = x + (size_t)ct * 2 * lp * N;
+                if (g == 1) {
+                    a[u][0] = t < lp ? mul_shoup(xb[(size_t)t * N + n], pq[2 * t], pq[2 * t + 1], P.q) : 0;
+                    a[u][1] = t < lp ? mul_shoup(xb[(size_t)(lp + t) * N + n], pq[2 * t], pq[2 * t + 1], P.q) : 0;
+                    continue;
+                }
+                Acc128 s0 = {0, 0}, s1 = {0, 0};
+                const u64 *Db = D + ((size_t)ct * beta * E + t) * N + src;
+                for (u32 j = 0; j < beta; ++j) {
+                    const u64 d = Db[(size_t)j * E * N];
+                    const u64 *kj = key + (size_t)j * 2 * kstride + (size_t)pt * N + n;
+                    mac128(s0, d, __ldg(kj));
+                    mac128(s1, d, __ldg(kj + kstride));
+                }
+                u64 r0 = redc128(s0.lo, s0.hi, P);   // keys are in Montgomery form
+                if (t < lp) r0 = add_mod(r0, mul_shoup(xb[(size_t)t * N + src], pq[2 * t], pq[2 * t + 1], P.q), P.q);
+                a[u][0] = r0;
+                a[u][1] = redc128(s1.lo, s1.hi, P);
+            }
+            if constexpr (weighted) {
+#pragma unroll
+                for (int o = 0; o < OA; ++o) {
+                    if (o >= (int)O) break;
+                    const u64 wv = __ldg(w + (size_t)o * w_ostride + ((size_t)(s * CH + i) * E + t) * N + n);
+#pragma unroll
+                    for (int u = 0; u < BT; ++u) {
+                        mac128(zw[o][u][0], a[u][0], wv);
+                        mac128(zw[o][u][1], a[u][1], wv);
+                    }
+                }
+                if (++terms == 64) {   // products < 2^122: fold before the 128-bit sums can overflow
+                    terms = 0;
+#pragma unroll
+                    for (int o = 0; o < OA; ++o)
+#pragma unroll
+                        for (int u = 0; u < BT; ++u)
+#pragma unroll
+                            for (int k = 0; k < 2; ++k) zw[o][u][k] = Acc128{reduce128(zw[o][u][k].lo, zw[o][u][k].hi, P), 0};
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < BT; ++u) {
+                    zp[u][0] = add_mod(zp[u][0], a[u][0], P.q);
+                    zp[u][1] = add_mod(zp[u][1], a[u][1], P.q);
+                }
+            }
+        }
+    }
+    const size_t zct = (size_t)2 * E * N;   // one output ciphertext over Q_l u P
+#pragma unroll
+    for (int u = 0; u < BT; ++u) {
+        if (c0 + u >= nb) break;
+        if constexpr (weighted) {
+#pragma unroll
+            for (int o = 0; o < OA; ++o) {
+                if (o >= (int)O) break;
+                u64 *zo = Z + ((size_t)o * B + c0 + u) * zct + (size_t)t * N + n;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    u64 v = reduce128(zw[o][u][k].lo, zw[o][u][k].hi, P);
+                    if (accumulate) v = add_mod(v, zo[(size_t)k * E * N], P.q);
+                    zo[(size_t)k * E * N] = v;
+                }
+            }
+        } else {
+            u64 *zo = Z + (size_t)(c0 + u) * zct + (size_t)t * N + n;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                u64 v = zp[u][k];
+                if (accumulate) v = add_mod(v, zo[(size_t)k * E * N], P.q);
+                zo[(size_t)k * E * N] = v;
+            }
+        }
+    }
+}
+
 // Division by the dropped basis D of the accumulators acc [S][B][2][lp+K][N]: D is
 // the KD rows starting at row dbase (dbase = lp: the special primes, ModDown;
 // dbase = lp-1: the top data prime and the special primes, ModDown and rescale in
@@ -824,6 +952,46 @@ static void moddown_launch(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t
                  ntt_part_smem(c->logn, sp), out, (const u64 *)acc, addend, addend_bstride, add_mask, kl, B, lp,
                  c->K, c->L1, dbase, KD, lpo, c->logn, tab, (const u64 *)c->tw, (const PrimeDev *)c->pdev);
     note_launch(c, "moddown", bytes, bfly * c->logn);
+}
+
+// Z = the hoisted combination of ks_comb_kernel for the steps of kl (at most KEYLIST_MAX); w null:
+// one plain sum per input ciphertext, else one weighted output summed over the CH channels
+void ks_comb(Ctx *c, u64 *Z, const u64 *D, const u64 *x, const KeyList &kl, u32 S, u32 CH, u32 B, u32 lp,
+             const u64 *w, u32 O, size_t w_ostride, int accumulate) {
+    const u32 N = c->N, E = lp + c->K, beta = ks_digits(c, lp);
+    const bool weighted = w != nullptr;
+    if (weighted && O != 1) throw HeError(HE_EINVAL, "ks_comb: one weighted output");
+    if (S > KEYLIST_MAX) throw HeError(HE_EINVAL, "ks_comb: too many steps in one launch");
+    u32 nks = 0;
+    for (u32 s = 0; s < S; ++s)
+        if (kl.g[s] != 1) {
+            if (!kl.key[s] || !D) throw HeError(HE_EINVAL, "ks_comb: a key-switched step without key or digits");
+            ++nks;
+        }
+    // ciphertexts per thread (tuned): 4 shares every key word between more products, 2 keeps
+    // three CTAs per SM
+    const u32 bt = tune_get(c, TUNE_COMB_BT, 4) == 2 ? 2 : 4;
+    const u32 nb = weighted ? B : CH * B;
+    const dim3 grid((N + 255) / 256, (nb + bt - 1) / bt, E);
+    if (grid.y > 65535) throw HeError(HE_EINVAL, "ks_comb: batch too large for one launch");
+    prof_begin(c);
+#define COMB_LAUNCH(OMV, BTV)                                                                                   \
+    ks_comb_kernel<OMV, BTV><<<grid, 256, 0, c->stream>>>(Z, D, x, kl, S, CH, B, beta, lp, c->K, c->L1, c->logn, \
+                                                          weighted ? w : nullptr, O, w_ostride, accumulate,     \
+                                                          pmod_table(c), c->pdev)
+    if (weighted) {
+        if (bt == 2) COMB_LAUNCH(1, 2); else COMB_LAUNCH(1, 4);
+    } else {
+        if (bt == 2) COMB_LAUNCH(0, 2); else COMB_LAUNCH(0, 4);
+    }
+#undef COMB_LAUNCH
+    // the digits, keys, weights and the inputs' c0 read once, the outputs written once; 64x64->128
+    // multiply-accumulates of the key products and of the weights
+    const double Bt = (double)CH * B, nout = weighted ? O : Bt;
+    note_launch(c, "ks_comb",
+                8.0 * N * (Bt * beta * E + nks * 2.0 * beta * E + (weighted ? (double)O * S * CH * E : 0) + Bt * lp +
+                           nout * 2 * E * (accumulate ? 2 : 1)),
+                (double)N * E * 2 * (nks * Bt * beta + (weighted ? (double)O * S * CH * B : 0)));
 }
 
 // out [S][B][2][lp][N] = ModDown(acc) (+ addend: poly k of ct b gathered by sigma_{g_s} when add_mask bit k)

@@ -19,6 +19,8 @@ u32 ks_digits(const Ctx *c, u32 lp);
 void ks_modup(Ctx *c, u64 *D, const u64 *xe, size_t xe_bstride, u32 B, u32 lp);
 void ks_inner(Ctx *c, u64 *acc, const u64 *D, const KeyList &kl, u32 S, u32 B, u32 lp);
 void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u32 S, u32 B, u32 lp);
+void ks_comb(Ctx *c, u64 *Z, const u64 *D, const u64 *x, const KeyList &kl, u32 S, u32 CH, u32 B, u32 lp,
+             const u64 *w, u32 O, size_t w_ostride, int accumulate);
 void ks_moddown(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bstride, u32 add_mask,
                 const KeyList &kl, u32 S, u32 B, u32 lp);
 void rescale_batch(Ctx *c, u64 *out, const u64 *in, u32 B, u32 lp);

@@ -11,7 +11,8 @@
 //     registers (fewer: more resident warps, but the inputs are re-read per group);
 //   * hoisted key-switch accumulation: ciphertexts per thread (key reuse in
 //     registers vs. registers per thread) and grid order (coefficient tiles
-//     fastest vs. ciphertext groups fastest, i.e. key-slice reuse in L2).
+//     fastest vs. ciphertext groups fastest, i.e. key-slice reuse in L2);
+//   * one-pass combination (ks_comb): ciphertexts per thread.
 // Each knob is timed with CUDA events on scratch data shaped like the context's
 // top level (16 to 64 ciphertexts), the fastest kept; results are cached in a JSON
 // file keyed by device name and parameters so a later process skips the sweep.
@@ -41,7 +42,7 @@ int ntt_layout(const Ctx *c, int knob) {
 namespace {
 
 const char *knob_name[TUNE_COUNT] = {"ntt_split", "moddown_split", "rescale_split", "mac_group", "lazy_bt",
-                                     "lazy_order", "mac_bk", "mac_split"};
+                                     "lazy_order", "mac_bk", "mac_split", "comb_bt"};
 
 float time_ms(Ctx *c, const std::function<void()> &f) {
     f();   // warm-up
@@ -211,6 +212,14 @@ void measure(Ctx *c, std::ostringstream &rep) {
         sweep(c, TUNE_LAZY_BT, bts, run, rep);
         rep << ", ";
         sweep(c, TUNE_LAZY_ORDER, {0, 1}, run, rep);
+        // the one-pass combination of a pooling's shape: three key-switched steps and the identity
+        // summed per ciphertext
+        KeyList kc = kl;
+        kc.g[3] = 1;
+        kc.key[3] = kc.keyp[3] = nullptr;
+        DBuf z(c, (size_t)B * 2 * E * N);
+        rep << ", ";
+        sweep(c, TUNE_COMB_BT, {4, 2}, [&] { ks_comb(c, z.p, D.p, x.p, kc, 4, 1, B, lp, nullptr, 0, 0, 0); }, rep);
     }
     rep << "}";
     CUDA_TRY(cudaStreamSynchronize(c->stream));

@@ -28,8 +28,10 @@ SETTINGS = [
     dict(ntt_split=1, moddown_split=1, rescale_split=1, mac_group=4, lazy_bt=1, lazy_order=1, mac_bk=16, mac_split=1),
     dict(ntt_split=0, moddown_split=1, rescale_split=0, mac_group=6, lazy_bt=4, lazy_order=0, mac_bk=32, mac_split=2),
     dict(ntt_split=1, moddown_split=0, rescale_split=1, mac_group=12, lazy_bt=2, lazy_order=1, mac_bk=64, mac_split=2),
-    dict(ntt_split=2, moddown_split=2, rescale_split=2, mac_group=8, lazy_bt=2, lazy_order=0, mac_bk=32, mac_split=1),
-    dict(ntt_split=2, moddown_split=0, rescale_split=1, mac_group=12, lazy_bt=4, lazy_order=1, mac_bk=64, mac_split=1),
+    dict(ntt_split=2, moddown_split=2, rescale_split=2, mac_group=8, lazy_bt=2, lazy_order=0, mac_bk=32, mac_split=1,
+         comb_bt=2),
+    dict(ntt_split=2, moddown_split=0, rescale_split=1, mac_group=12, lazy_bt=4, lazy_order=1, mac_bk=64, mac_split=1,
+         comb_bt=4),
 ]
 
 
@@ -59,7 +61,7 @@ def test_autotune_and_cache(G, tmp_path):
     ctx = G.Context(seed=1, **P)
     path = str(tmp_path / "tune.json")
     rep = ctx.autotune(path)
-    assert "ntt_split" in rep and "mac_group" in rep and "lazy_order" in rep and "mac_bk" in rep
+    assert "ntt_split" in rep and "mac_group" in rep and "lazy_order" in rep and "mac_bk" in rep and "comb_bt" in rep
     chosen = ctx.tuning()
     assert all(v >= 0 for v in chosen.values())
     assert chosen["mac_group"] == rep["mac_group"]["chosen"]
