@@ -116,6 +116,8 @@ def parse():
     ap.add_argument("--samples", type=int, default=N_SAMPLES)
     ap.add_argument("--keys", default="step", choices=["step", "pow2"],
                     help="Galois keys: one per rotation step (default) or the power-of-two set")
+    ap.add_argument("--schedule", default="fused", choices=["fused", "literal"],
+                    help="evaluation schedule: fused (default) or the paper's order, one operation at a time")
     ap.add_argument("--ncu-step", action="store_true",
                     help="after set-up and warm-up run ONE eager step between cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off) and exit")
@@ -197,12 +199,13 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def lenet_setup(G, torch, device, stream, n_samples, keys="step"):
+def lenet_setup(G, torch, device, stream, n_samples, keys="step", schedule="fused"):
     P = W.PARAMS["lenet1"]
     model = W.lenet1()
-    stride, levels, steps = G.plan(model, 28, 28)
+    stride, levels, steps = G.plan(model, 28, 28, schedule=schedule)
     ctx = G.Context(seed=W.KEY_SEED, device=device, stream=stream.cuda_stream, **P)
     ctx.autotune(TUNE_CACHE)
+    ctx.set_schedule(schedule)
     if keys == "pow2":
         ctx.keygen_pow2()   # the power-of-two key set: rotations as non-adjacent-form chains
     else:
@@ -425,7 +428,7 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl")
 
     stream = torch.cuda.Stream()
-    ctx, model, stride, layers, imgs = lenet_setup(G, torch, local, stream, args.samples, args.keys)
+    ctx, model, stride, layers, imgs = lenet_setup(G, torch, local, stream, args.samples, args.keys, args.schedule)
     n_ct = -(-args.samples // SPC)
     x_dev = torch.from_numpy(imgs).to(f"cuda:{local}")
     x_host = torch.from_numpy(imgs).pin_memory()
@@ -537,7 +540,7 @@ def run_ours(args, rank, world, local):
         peak_hbm = pk["hbm_gbs"] if pk else 6800.0
         alu_peak = {"ntt": bfly_peak, "intt": bfly_peak, "moddown": bfly_peak, "rescale": bfly_peak,
                     "modup_ntt": bfly_peak,
-                    "mac": mac_peak, "ks_lazy": mac_peak, "ks_inner": mac_peak}
+                    "mac": mac_peak, "ks_lazy": mac_peak, "ks_inner": mac_peak, "ks_comb": mac_peak}
 
         def views(v):
             nl, tms, byt, ops = v
@@ -590,6 +593,7 @@ def run_ours(args, rank, world, local):
                    "ckks": "N=16384, [60,40x7|60], Delta=2^40, dnum=8", "samples_per_gpu": args.samples,
                    "galois_keys": ("power of two (+-2^k), rotations as non-adjacent-form chains"
                                    if args.keys == "pow2" else "one per rotation step of the model"),
+                   "schedule": args.schedule,
                    "l2": "working set > L2 (keys + masks + ciphertexts, several GB)",
                    "parallelism": f"replicas x{world}", "autotuned": ctx.tuning()},
         "e2e": {"value": round(total_samples / (ms_e2e / 1e3), 3), "unit": UNIT,
