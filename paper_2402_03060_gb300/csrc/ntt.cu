@@ -1,7 +1,8 @@
-// ntt.cu -- batched negacyclic NTT / inverse NTT over sets of limbs.
-// One CTA per limb (row of N words), or a cluster of two CTAs per limb above
-// N = 2^14; the limb is staged in shared memory (N*8 bytes: 128 KiB at
-// N = 16384), transformed with part_ntt_* and written back.
+// ntt.cu -- batched negacyclic NTT / inverse NTT over sets of limbs, in the limb layout the
+// context uses (ntt_layout): one CTA per limb (row of N words) or a cluster of two CTAs per
+// limb, the limb staged in shared memory (N*8 bytes: 128 KiB at N = 16384) and transformed
+// with part_ntt_*; or the two-kernel form of ntt_block.cuh (outer stages over the 1024
+// columns, inner stages over 1024-coefficient blocks), the default from N = 2^14.
 #include "ntt_block.cuh"
 
 __device__ __forceinline__ void row_of(const RowSet &rs, u32 r, u32 &off, u32 &prime) {

@@ -16,6 +16,9 @@
 // and a group loads 15 twiddle pairs for 32 butterflies.  Shared memory is
 // padded by one word per 16 so that the strided group loads are conflict-free.
 //
+// The two-kernel form at the end of this file transforms a limb by two launches instead
+// (outer stages over columns in registers, inner stages over 1024-coefficient blocks).
+//
 // Limbs larger than one CTA's shared memory (N = 2^15: 256 KiB) are split over
 // a cluster of two CTAs ("parts"): CTA r holds coefficients [r*N/2, (r+1)*N/2).
 // The one stage whose butterflies join the halves (distance N/2: the first
