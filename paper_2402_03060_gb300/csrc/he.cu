@@ -775,16 +775,17 @@ Cts ct_square(Ctx *c, const Cts &a) {
     kl.key[0] = c->rlk.p;
     kl.g[0] = 1;
     DBuf acc(c, (size_t)B * 2 * E * N);
-    ks_inner(c, acc.p, D.p, kl, 1, B, lp);
     if (c->literal) {
         // one step at a time: relinearise (ModDown of both accumulators, plus d0 / d1), then the
         // centred rescale
+        ks_inner(c, acc.p, D.p, kl, 1, B, lp);
         Cts rl = cts_alloc(c, B, lp, a.scale * a.scale, a.lay);
         ks_moddown(c, rl.data(), acc.p, d.p, (size_t)3 * lp * N, 3, kl, 1, B, lp);
         return ct_rescale(c, rl);
     }
     // relinearise and rescale as one division by q_top * P: P * (d0, d1) joins the accumulators
-    ks_add_p_times(c, acc.p, d.p, B, lp);
+    // in the inner product's own pass
+    ks_inner(c, acc.p, D.p, kl, 1, B, lp, d.p, (size_t)3 * lp * N);
     Cts r = cts_alloc(c, B, lp - 1, a.scale * a.scale / (double)c->primes[lp - 1], a.lay);
     ks_moddown_rescale(c, r.data(), acc.p, B, lp);
     return r;

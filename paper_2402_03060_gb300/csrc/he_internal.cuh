@@ -312,6 +312,8 @@ void ntt_forward(Ctx *c, u64 *base, const RowSet &rs);
 void ntt_inverse(Ctx *c, u64 *base, const RowSet &rs);
 // the inner launch of the two-kernel NTT over the rows of rs (ntt_block.cuh)
 void ntt2_inner(Ctx *c, u64 *base, const RowSet &rs, int inverse);
+// dst [B][lp][N] = inverse NTT of limbs 0..lp-1 of B polynomials at src, batch stride src_bstride
+void ntt_inverse_from(Ctx *c, u64 *dst, const u64 *src, size_t src_bstride, u32 B, u32 lp);
 RowSet rows_regular(u32 n, u32 period, u32 lp, u32 pbase);
 RowSet rows_list(Ctx *c, const std::string &key, const std::vector<u32> &packed);
 

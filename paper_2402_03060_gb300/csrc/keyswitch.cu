@@ -149,8 +149,11 @@ __global__ void modup_own_kernel(u64 *D, const u64 *__restrict__ xe, size_t xe_b
     D[(((size_t)b * beta + j) * E + t) * N + n] = xe[(size_t)b * xe_bstride + (size_t)t * N + n];
 }
 
+// acc [S][B][2][E][N] = sum_j sigma_g(D_j) (o) key_j; with padd: + P * (padd0, padd1) on the data
+// limbs (padd[b] at b * padd_bstride words, polynomial k at k * lp * N; pq: [P]_{q_t} and Shoup pairs)
 __global__ void ks_inner_kernel(u64 *acc, const u64 *__restrict__ D, KeyList kl, u32 B, u32 beta, u32 lp, u32 K,
-                                u32 L1, int logn, const PrimeDev *__restrict__ pd) {
+                                u32 L1, int logn, const PrimeDev *__restrict__ pd, const u64 *__restrict__ padd,
+                                size_t padd_bstride, const u64 *__restrict__ pq) {
     const u32 N = 1u << logn;
     const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
@@ -172,8 +175,14 @@ __global__ void ks_inner_kernel(u64 *acc, const u64 *__restrict__ D, KeyList kl,
     }
     const PrimeDev &P = pd[pt];
     u64 *o = acc + (((size_t)s * B + b) * 2 * E + t) * N + n;
-    o[0] = redc128(a0.lo, a0.hi, P);   // keys are in Montgomery form
-    o[(size_t)E * N] = redc128(a1.lo, a1.hi, P);
+    u64 r0 = redc128(a0.lo, a0.hi, P), r1 = redc128(a1.lo, a1.hi, P);   // keys are in Montgomery form
+    if (padd && t < lp) {
+        const u64 *x = padd + (size_t)b * padd_bstride + (size_t)t * N + n;
+        r0 = add_mod(r0, mul_shoup(x[0], pq[2 * t], pq[2 * t + 1], P.q), P.q);
+        r1 = add_mod(r1, mul_shoup(x[(size_t)lp * N], pq[2 * t], pq[2 * t + 1], P.q), P.q);
+    }
+    o[0] = r0;
+    o[(size_t)E * N] = r1;
 }
 
 // Accumulators of a hoisted linear combination, before any ModDown:
@@ -643,21 +652,6 @@ __global__ void __launch_bounds__(NTT2_INNER_THREADS) rescale2_inner_kernel(u64 
     }
 }
 
-// acc[b][k][t] += P * d[b][k][t] on the data limbs t < lp (d: [B][3][lp][N], k < 2)
-__global__ void add_p_times_kernel(u64 *acc, const u64 *__restrict__ d, u32 lp, u32 K, int logn,
-                                   const u64 *__restrict__ pq, const PrimeDev *__restrict__ pd, u32 B) {
-    const u32 N = 1u << logn;
-    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (size_t)B * 2 * lp * N) return;
-    const u32 n = (u32)(idx & (N - 1));
-    size_t r = idx >> logn;
-    const u32 t = (u32)(r % lp), k = (u32)((r / lp) % 2), b = (u32)(r / (2 * lp));
-    const u64 q = pd[t].q;
-    u64 *a = acc + (((size_t)b * 2 + k) * (lp + K) + t) * N + n;
-    const u64 x = d[(((size_t)b * 3 + k) * lp + t) * N + n];
-    *a = add_mod(*a, mul_shoup(x, pq[2 * t], pq[2 * t + 1], q), q);
-}
-
 template <int SPLIT>
 __global__ void __launch_bounds__(NTT_MAX_THREADS) rescale_kernel(u64 *out, const u64 *__restrict__ in,
                                                        const u64 *__restrict__ top, u32 lp, int logn,
@@ -815,10 +809,8 @@ void ks_modup(Ctx *c, u64 *D, const u64 *xe, size_t xe_bstride, u32 B, u32 lp) {
     const u32 N = c->N, E = lp + c->K, beta = ks_digits(c, lp);
     if ((size_t)B * beta * E >= (1u << 24)) throw HeError(HE_EINVAL, "ModUp: batch too large for one launch");
     DBuf xc(c, (size_t)B * lp * N);
-    // contiguous copy of the eval rows, then inverse NTT to coefficient form
-    CUDA_TRY(cudaMemcpy2DAsync(xc.p, (size_t)lp * N * 8, xe, xe_bstride * 8, (size_t)lp * N * 8, B,
-                               cudaMemcpyDeviceToDevice, c->stream));
-    ntt_inverse(c, xc.p, rows_regular(B * lp, lp, lp, 0));
+    // the eval rows in coefficient form, contiguous
+    ntt_inverse_from(c, xc.p, xe, xe_bstride, B, lp);
     const u64 *tab = modup_table(c, lp);
     // own rows: copies of the evaluation-form input
     {
@@ -861,16 +853,21 @@ void ks_modup(Ctx *c, u64 *D, const u64 *xe, size_t xe_bstride, u32 B, u32 lp) {
     note_launch(c, "modup_ntt", bytes, bfly * c->logn);
 }
 
-// acc [S][B][2][lp+K][N] = sum_j sigma_{g_s}(D_j) (o) key_s,j
-void ks_inner(Ctx *c, u64 *acc, const u64 *D, const KeyList &kl, u32 S, u32 B, u32 lp) {
+static const u64 *pmod_table(Ctx *c);
+
+// acc [S][B][2][lp+K][N] = sum_j sigma_{g_s}(D_j) (o) key_s,j (+ P * (padd0, padd1) when padd is given)
+void ks_inner(Ctx *c, u64 *acc, const u64 *D, const KeyList &kl, u32 S, u32 B, u32 lp, const u64 *padd,
+              size_t padd_bstride) {
     const u32 N = c->N, E = lp + c->K;
     dim3 grid((N + 255) / 256, E, S * B);
     prof_begin(c);
-    ks_inner_kernel<<<grid, 256, 0, c->stream>>>(acc, D, kl, B, ks_digits(c, lp), lp, c->K, c->L1, c->logn, c->pdev);
+    ks_inner_kernel<<<grid, 256, 0, c->stream>>>(acc, D, kl, B, ks_digits(c, lp), lp, c->K, c->L1, c->logn, c->pdev,
+                                                 padd, padd_bstride, padd ? pmod_table(c) : nullptr);
     {
         const double beta = ks_digits(c, lp);
-        // digits read once, each step's key read once, accumulators written once
-        note_launch(c, "ks_inner", 8.0 * N * ((double)B * beta * E + (double)S * 2 * beta * E + (double)S * B * 2 * E));
+        // digits read once, each step's key read once, accumulators written once (+ the addends read once)
+        note_launch(c, "ks_inner", 8.0 * N * ((double)B * beta * E + (double)S * 2 * beta * E + (double)S * B * 2 * E +
+                                              (padd ? (double)S * B * 2 * lp : 0.0)));
     }
 }
 
@@ -1027,15 +1024,6 @@ void ks_moddown_rescale(Ctx *c, u64 *out, u64 *acc, u32 nct, u32 lp) {
     none.key[0] = nullptr;
     moddown_launch(c, out, acc, nullptr, 0, 0, none, 1, nct, lp, lp - 1, c->K + 1, lp - 1,
                    moddown_rescale_table(c, lp), 8.0 * N * (double)nct * (2.0 * E + 2.0 * (lp - 1)));
-}
-
-// acc [B][2][lp+K][N] += P * (d0, d1) on the data limbs; d [B][3][lp][N]
-void ks_add_p_times(Ctx *c, u64 *acc, const u64 *d, u32 B, u32 lp) {
-    const size_t total = (size_t)B * 2 * lp * c->N;
-    prof_begin(c);
-    add_p_times_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(acc, d, lp, c->K, c->logn,
-                                                                            pmod_table(c), c->pdev, B);
-    note_launch(c, "add_p_times", 8.0 * c->N * (double)B * 2 * lp * 3);
 }
 
 // out [B][2][lp-1][N] = rescale(in [B][2][lp][N])

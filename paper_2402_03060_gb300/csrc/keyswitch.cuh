@@ -17,7 +17,8 @@ struct KeyList {
 void keyswitch_init(Ctx *c);
 u32 ks_digits(const Ctx *c, u32 lp);
 void ks_modup(Ctx *c, u64 *D, const u64 *xe, size_t xe_bstride, u32 B, u32 lp);
-void ks_inner(Ctx *c, u64 *acc, const u64 *D, const KeyList &kl, u32 S, u32 B, u32 lp);
+void ks_inner(Ctx *c, u64 *acc, const u64 *D, const KeyList &kl, u32 S, u32 B, u32 lp, const u64 *padd = nullptr,
+              size_t padd_bstride = 0);
 void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u32 S, u32 B, u32 lp);
 void ks_comb(Ctx *c, u64 *Z, const u64 *D, const u64 *x, const KeyList &kl, u32 S, u32 CH, u32 B, u32 lp,
              const u64 *w, u32 O, size_t w_ostride, int accumulate);
@@ -25,4 +26,3 @@ void ks_moddown(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t addend_bst
                 const KeyList &kl, u32 S, u32 B, u32 lp);
 void rescale_batch(Ctx *c, u64 *out, const u64 *in, u32 B, u32 lp);
 void ks_moddown_rescale(Ctx *c, u64 *out, u64 *acc, u32 nct, u32 lp);
-void ks_add_p_times(Ctx *c, u64 *acc, const u64 *d, u32 B, u32 lp);
