@@ -283,8 +283,11 @@ he_status he_autotune(he_ctx *ctx, const char *cache_path, char *report, size_t 
  * (0 one CTA per limb, 1 a 2-CTA cluster, 2 two launches: outer stages over columns,
  * inner stages over 1024-coefficient blocks), MAC output group, key-switch ciphertexts
  * per thread, key-switch grid order, polynomials per MAC CTA, threads per coefficient of
- * a MAC group, ciphertexts per thread of the one-pass combination (-1 = default).  he_tuning_set overrides them (values outside a knob's
- * candidates fall back to the nearest valid launch shape). */
+ * a MAC group, ciphertexts per thread of the one-pass combination, the number of
+ * ciphertexts from which a single-output weighted combination of one channel folds its
+ * weights into the keys (default 16; not timed by he_autotune) (-1 = default).
+ * he_tuning_set overrides them (values outside a knob's candidates fall back to the
+ * nearest valid launch shape). */
 he_status he_tuning_get(he_ctx *ctx, int32_t *values, size_t n);
 he_status he_tuning_set(he_ctx *ctx, const int32_t *values, size_t n);
 

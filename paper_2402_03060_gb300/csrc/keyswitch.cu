@@ -335,7 +335,10 @@ __global__ void __launch_bounds__(256, (BT == 4 && MAXD == 8) ? 2 : 3) ks_lazy_p
 // limbs), n-tiles fastest, so the digit rows of a group stay in L2 while their tiles are gathered.
 // The weighted sums are 128-bit lazy (folded every 64 terms), the plain ones reduced per term.
 // OM = 0: the plain form (w must be null), else the weighted form with up to OM outputs.
-template <int OM, int BT>
+// MAXD > 0: at most MAXD digits, unrolled -- a step's key words are loaded once per thread into
+// registers and serve every ciphertext and channel of the thread, and a ciphertext's digit words
+// are all in flight before its products; MAXD = 0: any digit count, one digit at a time.
+template <int OM, int BT, int MAXD>
 __global__ void __launch_bounds__(256, BT == 2 ? 3 : 2) ks_comb_kernel(u64 *__restrict__ Z, const u64 *__restrict__ D,
                                                       const u64 *__restrict__ x, KeyList kl, u32 S, u32 CH, u32 B,
                                                       u32 beta, u32 lp, u32 K, u32 L1, int logn,
@@ -351,6 +354,7 @@ __global__ void __launch_bounds__(256, BT == 2 ? 3 : 2) ks_comb_kernel(u64 *__re
     const size_t kstride = (size_t)(L1 + K) * N;
     constexpr bool weighted = OM > 0;
     constexpr int OA = OM > 0 ? OM : 1;
+    constexpr int KD = MAXD > 0 ? MAXD : 1;
     // the ciphertexts of this thread: weighted -> b = bg*BT + u of every channel; plain -> c = bg*BT + u
     const u32 nb = weighted ? B : CH * B;
     const u32 c0 = blockIdx.y * BT;
@@ -369,6 +373,17 @@ __global__ void __launch_bounds__(256, BT == 2 ? 3 : 2) ks_comb_kernel(u64 *__re
         const u32 g = kl.g[s];
         const u32 src = g == 1 ? n : galois_src(n, g, logn);
         const u64 *key = kl.key[s];
+        u64 k0[KD], k1[KD];
+        if constexpr (MAXD > 0) {
+            if (g != 1) {
+                const u64 *kp = key + (size_t)pt * N + n;
+#pragma unroll
+                for (int j = 0; j < MAXD; ++j) {
+                    k0[j] = j < (int)beta ? __ldg(kp + (size_t)j * 2 * kstride) : 0;
+                    k1[j] = j < (int)beta ? __ldg(kp + (size_t)j * 2 * kstride + kstride) : 0;
+                }
+            }
+        }
         for (u32 i = 0; i < nch; ++i) {
             u64 a[BT][2];
 #pragma unroll
@@ -383,18 +398,30 @@ __global__ void __launch_bounds__(256, BT == 2 ? 3 : 2) ks_comb_kernel(u64 *__re
                 }
                 Acc128 s0 = {0, 0}, s1 = {0, 0};
                 const u64 *Db = D + ((size_t)ct * beta * E + t) * N + src;
-                for (u32 j = 0; j < beta; ++j) {
-                    const u64 d = Db[(size_t)j * E * N];
-                    const u64 *kj = key + (size_t)j * 2 * kstride + (size_t)pt * N + n;
-                    mac128(s0, d, __ldg(kj));
-                    mac128(s1, d, __ldg(kj + kstride));
+                if constexpr (MAXD > 0) {
+                    u64 d[MAXD];
+#pragma unroll
+                    for (int j = 0; j < MAXD; ++j) d[j] = j < (int)beta ? Db[(size_t)j * E * N] : 0;
+#pragma unroll
+                    for (int j = 0; j < MAXD; ++j)
+                        if (j < (int)beta) {
+                            mac128(s0, d[j], k0[j]);
+                            mac128(s1, d[j], k1[j]);
+                        }
+                } else {
+                    for (u32 j = 0; j < beta; ++j) {
+                        const u64 d = Db[(size_t)j * E * N];
+                        const u64 *kj = key + (size_t)j * 2 * kstride + (size_t)pt * N + n;
+                        mac128(s0, d, __ldg(kj));
+                        mac128(s1, d, __ldg(kj + kstride));
+                    }
                 }
                 u64 r0 = redc128(s0.lo, s0.hi, P);   // keys are in Montgomery form
                 if (t < lp) r0 = add_mod(r0, mul_shoup(xb[(size_t)t * N + src], pq[2 * t], pq[2 * t + 1], P.q), P.q);
                 a[u][0] = r0;
                 a[u][1] = redc128(s1.lo, s1.hi, P);
             }
-            if constexpr (weighted) {
+        if constexpr (weighted) {
 #pragma unroll
                 for (int o = 0; o < OA; ++o) {
                     if (o >= (int)O) break;
@@ -449,6 +476,142 @@ __global__ void __launch_bounds__(256, BT == 2 ? 3 : 2) ks_comb_kernel(u64 *__re
             }
         }
     }
+}
+
+// The same combinations with one lazy 128-bit sum per output polynomial and one reduction at
+// the end, for plain sums and for single-output weighted sums of one channel whose weights were
+// folded into the keys beforehand (ks_fold_kernel):
+//   poly 0: Z[c] (+)= REDC( sum_s [ sum_j sigma_s(D_j) (.) K'_{s,j,0} + sigma_s(c0) (.) P'_s ] )
+//   poly 1: Z[c] (+)= REDC( sum_s   sum_j sigma_s(D_j) (.) K'_{s,j,1} )
+// (an identity step adds c0 (.) P'_s and c1 (.) P'_s), every operand K', P' carrying a factor
+// 2^64 that the one Montgomery reduction of the reduced sum removes:
+//   plain:    K' = the Montgomery keys,   P'_s = [P 2^64]_{q_t};
+//   weighted: K' = K~ (.) w_s (K~ the Montgomery key),  P'_s = [P 2^64]_{q_t} (.) w_s.
+// These are the residues of ks_comb_kernel, summed in another order: identical results, without a
+// reduction and a Shoup product per step.  Keys of step s at kl.key[s] + j*2*kst + k*kst +
+// row*N, row = t on a data limb, krow_sp + (t - lp) on a special one; pw [S][lp][N] (weighted) or
+// null (plain: pmont [2*t] = [P 2^64]_{q_t}).  Grid as ks_comb_kernel, one ciphertext each of BT.
+template <int BT, int MAXD>
+__global__ void __launch_bounds__(256, BT == 2 ? 3 : 2) ks_comb_lazy_kernel(
+    u64 *__restrict__ Z, const u64 *__restrict__ D, const u64 *__restrict__ x, KeyList kl, u32 S, u32 nb, u32 beta,
+    u32 lp, u32 K, u32 L1, u32 krow_sp, size_t kst, const u64 *__restrict__ pw, const u64 *__restrict__ pmont,
+    int accumulate, int logn, const PrimeDev *__restrict__ pd) {
+    const u32 N = 1u << logn;
+    const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 t = blockIdx.z;
+    const u32 E = lp + K;
+    const PrimeDev P = pd[t < lp ? t : L1 + (t - lp)];
+    const u32 krow = t < lp ? t : krow_sp + (t - lp);
+    const u32 c0 = blockIdx.y * BT;
+    if (n >= N) return;
+    Acc128 z[BT][2];
+#pragma unroll
+    for (int u = 0; u < BT; ++u) z[u][0] = z[u][1] = Acc128{0, 0};
+    const u32 per = (MAXD > 0 ? (u32)MAXD : beta) + 1;   // products one step adds to a sum, at most
+    u32 terms = 0;
+    for (u32 s = 0; s < S; ++s) {
+        if (terms + per > 63) {   // products < 2^122: fold before a 128-bit sum could overflow
+#pragma unroll
+            for (int u = 0; u < BT; ++u)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) z[u][k] = Acc128{reduce128(z[u][k].lo, z[u][k].hi, P), 0};
+            terms = 0;
+        }
+        terms += per;
+        const u32 g = kl.g[s];
+        const u32 src = g == 1 ? n : galois_src(n, g, logn);
+        const u64 cw = t < lp ? (pw ? pw[((size_t)s * lp + t) * N + n] : pmont[2 * t]) : 0;
+        if (g == 1) {
+            if (t < lp) {
+#pragma unroll
+                for (int u = 0; u < BT; ++u) {
+                    const u32 bb = c0 + u < nb ? c0 + u : nb - 1;   // clamp: duplicates are not stored
+                    const u64 *xb = x + (size_t)bb * 2 * lp * N;
+                    mac128(z[u][0], xb[(size_t)t * N + n], cw);
+                    mac128(z[u][1], xb[(size_t)(lp + t) * N + n], cw);
+                }
+            }
+            continue;
+        }
+        const u64 *kp = kl.key[s] + (size_t)krow * N + n;
+        size_t db[BT];   // word offset of each ciphertext's digit 0 at the gathered coefficient
+#pragma unroll
+        for (int u = 0; u < BT; ++u) {
+            const u32 bb = c0 + u < nb ? c0 + u : nb - 1;   // clamp: duplicates are not stored
+            db[u] = ((size_t)bb * beta * E + t) * N + src;
+        }
+        // each key word is loaded once and serves the BT ciphertexts
+        if constexpr (MAXD > 0) {
+#pragma unroll
+            for (int j = 0; j < MAXD; ++j)
+                if (j < (int)beta) {
+                    const u64 k0 = __ldg(kp + (size_t)j * 2 * kst), k1 = __ldg(kp + (size_t)j * 2 * kst + kst);
+#pragma unroll
+                    for (int u = 0; u < BT; ++u) {
+                        const u64 d = D[db[u] + (size_t)j * E * N];
+                        mac128(z[u][0], d, k0);
+                        mac128(z[u][1], d, k1);
+                    }
+                }
+        } else {
+            for (u32 j = 0; j < beta; ++j) {
+                const u64 k0 = __ldg(kp + (size_t)j * 2 * kst), k1 = __ldg(kp + (size_t)j * 2 * kst + kst);
+#pragma unroll
+                for (int u = 0; u < BT; ++u) {
+                    const u64 d = D[db[u] + (size_t)j * E * N];
+                    mac128(z[u][0], d, k0);
+                    mac128(z[u][1], d, k1);
+                }
+            }
+        }
+        if (t < lp) {
+#pragma unroll
+            for (int u = 0; u < BT; ++u) {
+                const u32 bb = c0 + u < nb ? c0 + u : nb - 1;
+                mac128(z[u][0], x[(size_t)bb * 2 * lp * N + (size_t)t * N + src], cw);
+            }
+        }
+    }
+    const size_t zct = (size_t)2 * E * N;   // one output ciphertext over Q_l u P
+#pragma unroll
+    for (int u = 0; u < BT; ++u) {
+        if (c0 + u >= nb) break;
+        u64 *zo = Z + (size_t)(c0 + u) * zct + (size_t)t * N + n;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            u64 v = redc128(reduce128(z[u][k].lo, z[u][k].hi, P), 0, P);   // the sum times 2^-64
+            if (accumulate) v = add_mod(v, zo[(size_t)k * E * N], P.q);
+            zo[(size_t)k * E * N] = v;
+        }
+    }
+}
+
+// The operands of a single-output weighted combination of one channel for ks_comb_lazy_kernel,
+// with the weights w [S][E][N] (over Q_l u P) folded in:
+//   F [S][beta][2][E][N]: K' (.) w_s of every key-switched step (K' the Montgomery key);
+//   pw [S][lp][N]: [P 2^64]_{q_t} (.) w_s on the data limbs.
+// Grid (n-tiles, E, S).
+__global__ void ks_fold_kernel(u64 *__restrict__ F, u64 *__restrict__ pw, KeyList kl, const u64 *__restrict__ w,
+                               u32 beta, u32 lp, u32 K, u32 L1, int logn, const u64 *__restrict__ pmont,
+                               const PrimeDev *__restrict__ pd) {
+    const u32 N = 1u << logn;
+    const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 t = blockIdx.y, s = blockIdx.z;
+    if (n >= N) return;
+    const u32 E = lp + K;
+    const u32 pt = t < lp ? t : L1 + (t - lp);
+    const PrimeDev P = pd[pt];
+    const u64 wv = w[((size_t)s * E + t) * N + n];
+    if (kl.g[s] != 1) {
+        const size_t kstride = (size_t)(L1 + K) * N;
+        const u64 *key = kl.key[s] + (size_t)pt * N + n;
+        u64 *f = F + ((size_t)s * beta * 2 * E + t) * N + n;
+        for (u32 j = 0; j < beta; ++j)
+#pragma unroll
+            for (u32 k = 0; k < 2; ++k)
+                f[((size_t)j * 2 + k) * E * N] = mul_mod(__ldg(key + (size_t)j * 2 * kstride + k * kstride), wv, P);
+    }
+    if (t < lp) pw[((size_t)s * lp + t) * N + n] = mul_shoup(wv, pmont[2 * t], pmont[2 * t + 1], P.q);
 }
 
 // Division by the dropped basis D of the accumulators acc [S][B][2][lp+K][N]: D is
@@ -886,6 +1049,21 @@ static const u64 *pmod_table(Ctx *c) {
     return c->const_table(key, h);
 }
 
+// [P 2^64]_{q_t} with Shoup companions for the data primes (P in Montgomery form)
+static const u64 *pmont_table(Ctx *c) {
+    std::string key = "PqMont";
+    auto it = c->cache.find(key);
+    if (it != c->cache.end()) return it->second.p;
+    std::vector<u64> h(2 * c->L1);
+    for (u32 t = 0; t < c->L1; ++t) {
+        u64 q = c->primes[t], v = 1;
+        for (u32 k = 0; k < c->K; ++k) v = mulmod_h(v, c->primes[c->L1 + k] % q, q);
+        h[2 * t] = (u64)(((unsigned __int128)v << 64) % q);
+        h[2 * t + 1] = shoup_h(h[2 * t], q);
+    }
+    return c->const_table(key, h);
+}
+
 // acc [S][B][2][lp+K][N]: lazy key-switch accumulators of the steps in kl (key nullptr, g = 1: identity)
 void ks_lazy(Ctx *c, u64 *acc, const u64 *D, const u64 *x, const KeyList &kl, u32 S, u32 B, u32 lp) {
     const u32 N = c->N, E = lp + c->K;
@@ -971,24 +1149,70 @@ void ks_comb(Ctx *c, u64 *Z, const u64 *D, const u64 *x, const KeyList &kl, u32 
     const u32 nb = weighted ? B : CH * B;
     const dim3 grid((N + 255) / 256, (nb + bt - 1) / bt, E);
     if (grid.y > 65535) throw HeError(HE_EINVAL, "ks_comb: batch too large for one launch");
+    // digits unrolled up to 8 (the key words of a step held in registers), any count otherwise
+    const int md = beta <= 4 ? 4 : beta <= 8 ? 8 : 0;
+    const double Bt = (double)CH * B;
+    // The lazy form (one reduction per output): plain sums, and weighted sums of one channel over
+    // enough ciphertexts to pay for folding the weights into the keys (S*2*beta*E*N products,
+    // against nb times that in the combination)
+    const int fold_min = tune_get(c, TUNE_COMB_FOLD, COMB_FOLD_MIN_B);
+    const bool fold = weighted && CH == 1 && (int)B >= std::max(1, fold_min);
+    if (!weighted || fold) {
+        DBuf F, PW;
+        KeyList kf = kl;
+        u32 krow_sp = c->L1;
+        size_t kst = (size_t)(c->L1 + c->K) * N;
+        const u64 *pw = nullptr;
+        if (fold) {
+            if (nks) F = DBuf(c, (size_t)S * beta * 2 * E * N);
+            PW = DBuf(c, (size_t)S * lp * N);
+            prof_begin(c);
+            ks_fold_kernel<<<dim3((N + 255) / 256, E, S), 256, 0, c->stream>>>(
+                F.p, PW.p, kl, w, beta, lp, c->K, c->L1, c->logn, pmont_table(c), c->pdev);
+            // the keys read and their folded copies written, the weights read, pw written
+            note_launch(c, "ks_fold", 8.0 * N * (nks * 4.0 * beta * E + (double)S * E + (double)S * lp));
+            for (u32 s = 0; s < S; ++s)
+                if (kl.g[s] != 1) kf.key[s] = F.p + (size_t)s * beta * 2 * E * N;
+            krow_sp = lp;
+            kst = (size_t)E * N;
+            pw = PW.p;
+        }
+        prof_begin(c);
+#define LAZY_LAUNCH(BTV, MDV)                                                                                    \
+    ks_comb_lazy_kernel<BTV, MDV><<<grid, 256, 0, c->stream>>>(Z, D, x, kf, S, nb, beta, lp, c->K, c->L1, krow_sp, \
+                                                              kst, pw, pmont_table(c), accumulate, c->logn,     \
+                                                              c->pdev)
+        if (bt == 2) {
+            if (md == 4) LAZY_LAUNCH(2, 4); else if (md == 8) LAZY_LAUNCH(2, 8); else LAZY_LAUNCH(2, 0);
+        } else {
+            if (md == 4) LAZY_LAUNCH(4, 4); else if (md == 8) LAZY_LAUNCH(4, 8); else LAZY_LAUNCH(4, 0);
+        }
+#undef LAZY_LAUNCH
+        // the digits, keys (or folded keys and pw) and the inputs read once, the outputs written
+        // once; 64x64->128 multiply-accumulates: the key products and one c0 product per step
+        note_launch(c, "ks_comb",
+                    8.0 * N * (Bt * beta * E + nks * 2.0 * beta * E + (fold ? (double)S * lp : 0) + Bt * lp +
+                               Bt * 2 * E * (accumulate ? 2 : 1)),
+                    (double)N * (2.0 * E * nks * Bt * beta + Bt * S * lp));
+        return;
+    }
     prof_begin(c);
-#define COMB_LAUNCH(OMV, BTV)                                                                                   \
-    ks_comb_kernel<OMV, BTV><<<grid, 256, 0, c->stream>>>(Z, D, x, kl, S, CH, B, beta, lp, c->K, c->L1, c->logn, \
-                                                          weighted ? w : nullptr, O, w_ostride, accumulate,     \
-                                                          pmod_table(c), c->pdev)
-    if (weighted) {
-        if (bt == 2) COMB_LAUNCH(1, 2); else COMB_LAUNCH(1, 4);
+#define COMB_LAUNCH(BTV, MDV)                                                                                   \
+    ks_comb_kernel<1, BTV, MDV><<<grid, 256, 0, c->stream>>>(Z, D, x, kl, S, CH, B, beta, lp, c->K, c->L1,      \
+                                                             c->logn, w, O, w_ostride, accumulate, pmod_table(c), \
+                                                             c->pdev)
+    if (bt == 2) {
+        if (md == 4) COMB_LAUNCH(2, 4); else if (md == 8) COMB_LAUNCH(2, 8); else COMB_LAUNCH(2, 0);
     } else {
-        if (bt == 2) COMB_LAUNCH(0, 2); else COMB_LAUNCH(0, 4);
+        if (md == 4) COMB_LAUNCH(4, 4); else if (md == 8) COMB_LAUNCH(4, 8); else COMB_LAUNCH(4, 0);
     }
 #undef COMB_LAUNCH
     // the digits, keys, weights and the inputs' c0 read once, the outputs written once; 64x64->128
     // multiply-accumulates of the key products and of the weights
-    const double Bt = (double)CH * B, nout = weighted ? O : Bt;
     note_launch(c, "ks_comb",
-                8.0 * N * (Bt * beta * E + nks * 2.0 * beta * E + (weighted ? (double)O * S * CH * E : 0) + Bt * lp +
-                           nout * 2 * E * (accumulate ? 2 : 1)),
-                (double)N * E * 2 * (nks * Bt * beta + (weighted ? (double)O * S * CH * B : 0)));
+                8.0 * N * (Bt * beta * E + nks * 2.0 * beta * E + (double)O * S * CH * E + Bt * lp +
+                           (double)O * 2 * E * (accumulate ? 2 : 1)),
+                (double)N * E * 2 * (nks * Bt * beta + (double)O * S * CH * B));
 }
 
 // out [S][B][2][lp][N] = ModDown(acc) (+ addend: poly k of ct b gathered by sigma_{g_s} when add_mask bit k)

@@ -4,6 +4,9 @@
 #include "ring.cuh"
 
 #define KEYLIST_MAX 64
+// a single-output weighted combination of one channel folds its weights into the keys from this
+// many ciphertexts on
+#define COMB_FOLD_MIN_B 16
 // Per rotation step s of one launch: the switching key [dnum][2][L+1+K][N] and
 // the Galois element applied to the ModUp'ed digits (1 = none); for the
 // pre-permuted form, ginv is the inverse Galois element g^{-1} mod 2N.

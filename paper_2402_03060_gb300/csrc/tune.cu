@@ -42,7 +42,7 @@ int ntt_layout(const Ctx *c, int knob) {
 namespace {
 
 const char *knob_name[TUNE_COUNT] = {"ntt_split", "moddown_split", "rescale_split", "mac_group", "lazy_bt",
-                                     "lazy_order", "mac_bk", "mac_split", "comb_bt"};
+                                     "lazy_order", "mac_bk", "mac_split", "comb_bt", "comb_fold"};
 
 float time_ms(Ctx *c, const std::function<void()> &f) {
     f();   // warm-up
@@ -89,7 +89,7 @@ void sweep(Ctx *c, int knob, const std::vector<int> &cands, const std::function<
 std::string cache_key(const Ctx *c) {
     cudaDeviceProp prop;
     CUDA_TRY(cudaGetDeviceProperties(&prop, c->device));
-    std::string k = fmt("v2|%s|sm%d%d|logn%d|L%u|K%u|dnum%u", prop.name, prop.major, prop.minor, c->logn, c->L1, c->K,
+    std::string k = fmt("v3|%s|sm%d%d|logn%d|L%u|K%u|dnum%u", prop.name, prop.major, prop.minor, c->logn, c->L1, c->K,
                         c->dnum);
     for (char &ch : k)
         if (ch == '"' || ch == '\\') ch = '_';
@@ -221,6 +221,7 @@ void measure(Ctx *c, std::ostringstream &rep) {
         rep << ", ";
         sweep(c, TUNE_COMB_BT, {4, 2}, [&] { ks_comb(c, z.p, D.p, x.p, kc, 4, 1, B, lp, nullptr, 0, 0, 0); }, rep);
     }
+    c->tuned[TUNE_COMB_FOLD] = COMB_FOLD_MIN_B;   // recorded, not timed
     rep << "}";
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->pool.release_cached();   // the scratch above goes back to the device

@@ -32,6 +32,12 @@ SETTINGS = [
          comb_bt=2),
     dict(ntt_split=2, moddown_split=0, rescale_split=1, mac_group=12, lazy_bt=4, lazy_order=1, mac_bk=64, mac_split=1,
          comb_bt=4),
+    # single-output weighted combinations with their weights folded into the keys from one
+    # ciphertext on (the default folds from 16: not at these batch sizes)
+    dict(ntt_split=2, moddown_split=2, rescale_split=2, mac_group=12, lazy_bt=4, lazy_order=0, mac_bk=64, mac_split=1,
+         comb_bt=2, comb_fold=1),
+    dict(ntt_split=2, moddown_split=2, rescale_split=2, mac_group=12, lazy_bt=4, lazy_order=0, mac_bk=64, mac_split=1,
+         comb_bt=4, comb_fold=1),
 ]
 
 
