@@ -285,7 +285,9 @@ he_status he_autotune(he_ctx *ctx, const char *cache_path, char *report, size_t 
  * per thread, key-switch grid order, polynomials per MAC CTA, threads per coefficient of
  * a MAC group, ciphertexts per thread of the one-pass combination, the number of
  * ciphertexts from which a single-output weighted combination of one channel folds its
- * weights into the keys (default 16; not timed by he_autotune) (-1 = default).
+ * weights into the keys (default 16; not timed by he_autotune), the largest prime (in
+ * bytes: 0 for none, the default; 5 for the 40-bit primes; 8 for every prime) whose limbs of
+ * a mask MAC of six or more outputs run on the tensor cores (-1 = default).
  * he_tuning_set overrides them (values outside a knob's candidates fall back to the
  * nearest valid launch shape). */
 he_status he_tuning_get(he_ctx *ctx, int32_t *values, size_t n);

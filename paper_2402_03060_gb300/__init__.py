@@ -289,7 +289,7 @@ class Context:
 
     # ---- client side
     TUNE_KNOBS = ("ntt_split", "moddown_split", "rescale_split", "mac_group", "lazy_bt", "lazy_order", "mac_bk",
-                  "mac_split", "comb_bt", "comb_fold")
+                  "mac_split", "comb_bt", "comb_fold", "mac_tc")
 
     def autotune(self, cache_path: str | None = None) -> dict:
         """he_autotune: time the launch-shape candidates (or read them from cache_path)."""

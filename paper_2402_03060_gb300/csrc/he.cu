@@ -370,6 +370,7 @@ Ctx *ctx_create(const he_params *p) {
     CUDA_TRY(cudaMemset(c->err_flag, 0, sizeof(int)));
     ntt_init_attrs(c.get());
     keyswitch_init(c.get());
+    mac_tc_init();
     mac_init(c.get());
     encode_init(c.get());
     return c.release();

@@ -237,6 +237,7 @@ enum {
     TUNE_MAC_SPLIT,    // threads per coefficient sharing a MAC group of 7..12 outputs: 1 / 2
     TUNE_COMB_BT,      // ciphertexts per thread of the one-pass combination (ks_comb): 2 / 4
     TUNE_COMB_FOLD,    // ciphertexts from which a one-channel weighted combination folds its weights into the keys
+    TUNE_MAC_TC,       // MAC of 6+ outputs: limbs of at most this many bytes on the tensor cores (0 none, default / 5 / 8)
     TUNE_COUNT
 };
 
@@ -245,7 +246,7 @@ struct Ctx : std::enable_shared_from_this<Ctx> {
     // multi-launch operations) between threads: every C entry point and the
     // serving loop hold it while they enqueue work or release buffers.
     std::recursive_mutex mu;
-    int tuned[TUNE_COUNT] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1};   // -1: default
+    int tuned[TUNE_COUNT] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};   // -1: default
     // parameters
     int logn = 0;
     u32 N = 0, L1 = 0, K = 0, dnum = 0, alpha = 0;

@@ -217,7 +217,7 @@ template <int OMAX, int OSPLIT>
 __global__ void __launch_bounds__(256, OSPLIT == 1 ? 2 : 3) mac_kernel(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt,
                                                   u32 O, u32 T, u32 BK, u32 lp, u32 logn, size_t x_tstride,
                                                   size_t out_ostride, u32 ntlog, u32 tc, u32 lpq, u32 pbase,
-                                                  int accumulate, size_t pt_ostride,
+                                                  int accumulate, size_t pt_ostride, u32 l0,
                                                   const PrimeDev *__restrict__ pd) {
     extern __shared__ u64 smem[];
     u64 *xs = smem;                          // [256][MAC_DEPTH]: each thread's own pipeline slots
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(256, OSPLIT == 1 ? 2 : 3) mac_kernel(u64 *out,
     const u32 nl = rt & (NT - 1);
     const u32 bk = blockIdx.x * ((256u / OSPLIT) >> ntlog) + (rt >> ntlog);
     const u32 n0 = blockIdx.y * NT;
-    const u32 l = blockIdx.z;
+    const u32 l = l0 + blockIdx.z;
     const bool active = bk < BK;
     const PrimeDev P = pd[l < lpq ? l : pbase + (l - lpq)];
     Acc128 acc[OMAX];
@@ -371,12 +371,40 @@ void mac_init(Ctx *c) {
         CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
 }
 
+static void mac_tc(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O, u32 T,
+                   u32 B, u32 lp, u32 lpq, u32 pbase, int accumulate, size_t pt_ostride, u32 l0, u32 nl);
+static u32 mac_tc_bytes(const Ctx *c, u32 p);
+static void mac_int(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O,
+                    u32 T, u32 B, u32 lp, u32 lpq, u32 pbase, int accumulate, size_t pt_ostride, u32 l0, u32 nl);
+
 void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O, u32 T, u32 B,
          u32 lp, u32 lpq, u32 pbase, int accumulate, size_t pt_ostride) {
     if (!pt_ostride) pt_ostride = (size_t)T * lp * c->N;
     // pt [O][T][lp][N]; x [T] blocks of [B][2][lp][N] at x_tstride; out [O] blocks at out_ostride.
     // Limb l < lpq uses data prime l, limb l >= lpq special prime pbase + l - lpq.
     if (lpq == ~0u) lpq = lp;
+    const int tcmax = tune_get(c, TUNE_MAC_TC, 0);   // limbs of at most this many bytes on the tensor cores
+    if (O < 6 || tcmax <= 0) {
+        mac_int(c, out, out_ostride, x, x_tstride, pt, O, T, B, lp, lpq, pbase, accumulate, pt_ostride, 0, lp);
+        return;
+    }
+    // runs of consecutive limbs on the same units
+    for (u32 l0 = 0; l0 < lp;) {
+        auto on_tc = [&](u32 l) { return (int)mac_tc_bytes(c, l < lpq ? l : pbase + (l - lpq)) <= tcmax; };
+        const bool tc = on_tc(l0);
+        u32 l1 = l0 + 1;
+        while (l1 < lp && on_tc(l1) == tc) ++l1;
+        if (tc)
+            mac_tc(c, out, out_ostride, x, x_tstride, pt, O, T, B, lp, lpq, pbase, accumulate, pt_ostride, l0, l1 - l0);
+        else
+            mac_int(c, out, out_ostride, x, x_tstride, pt, O, T, B, lp, lpq, pbase, accumulate, pt_ostride, l0, l1 - l0);
+        l0 = l1;
+    }
+}
+
+// mac() on the integer units over the limbs [l0, l0 + nl)
+static void mac_int(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O,
+                    u32 T, u32 B, u32 lp, u32 lpq, u32 pbase, int accumulate, size_t pt_ostride, u32 l0, u32 nl) {
     const u32 BK = 2 * B;
     if (O <= 2) {
         const size_t total = (size_t)BK * lp * c->N;
@@ -413,13 +441,13 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
         if (tc < 1) tc = 1;
         if (tc > T) tc = T;
         const size_t smem = (2 * (size_t)ow * tc * NT + 256 * MAC_DEPTH) * 8;
-        dim3 grid((BK + bkc - 1) / bkc, c->N / NT, lp);
+        dim3 grid((BK + bkc - 1) / bkc, c->N / NT, nl);
         const u64 *ptc = pt + (size_t)o0 * pt_ostride;
         u64 *outc = out + (size_t)o0 * out_ostride;
         prof_begin(c);
 #define MAC_LAUNCH(OM, OS)                                                                                        \
     mac_kernel<OM, OS><<<grid, 256, smem, c->stream>>>(outc, x, ptc, oc, T, BK, lp, c->logn, x_tstride, out_ostride, \
-                                                       ntlog, tc, lpq, pbase, accumulate, pt_ostride, c->pdev)
+                                                       ntlog, tc, lpq, pbase, accumulate, pt_ostride, l0, c->pdev)
         if (os == 2)
             MAC_LAUNCH(6, 2);
         else if (oc <= 1)
@@ -435,8 +463,276 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
         else
             MAC_LAUNCH(12, 1);
 #undef MAC_LAUNCH
-        note_launch(c, "mac", 8.0 * c->N * ((double)oc * T * lp + (double)T * B * 2 * lp + (double)oc * B * 2 * lp),
-                    (double)oc * T * B * 2 * lp * c->N);
+        note_launch(c, "mac", 8.0 * c->N * ((double)oc * T * nl + (double)T * B * 2 * nl + (double)oc * B * 2 * nl),
+                    (double)oc * T * B * 2 * nl * c->N);
+    }
+}
+
+// --------------------------------------------------------------- tensor-core MAC
+// The same sums out[o][c] (+)= sum_{t<T} pt[o][t] (.) x[t][c] (mod q_l, c = 2b + k a column), per
+// coefficient n and limb l a matrix product W (O x T) X (T x columns), on the tensor cores
+// (mma.sync m16n8k16, fp16 operands, fp32 accumulation).  A residue v < 256^C (C = the bytes of
+// q_l) is written v = sum_{a<C} d_a 256^a + Cc with d_a = (byte a of v) - 128 in [-128, 127],
+// exact in fp16, and Cc = 128 (256^C - 1) / 255.  Then
+//   sum_t w_t x_t = sum_{k<2C-1} 2^(8k) S_k + Cc sum_t w_t + Cc sum_t x_t - T' Cc^2,
+//   S_k = sum_{a+b=k} sum_t e_a(w_t) d_b(x_t)      (e, d the digits of w, x)
+// over the T' = 16 * ceil(T / 16) terms staged (the padding terms are zeros on both sides and
+// drop out of the identity).  |e d| <= 2^14 and a shift collects at most C <= 8 digit pairs, so
+// with T' <= MAC_TC_TMAX every partial sum of S_k is an integer below 2^24 in magnitude: the fp32
+// accumulation is exact.  The S_k are assembled in 128-bit integers and reduced mod q.
+//
+// CTA: one limb, 4 consecutive coefficients, 32 columns; 16 warps, warp w takes coefficient
+// w / 4 and the 8-column tile w % 4 (an m16n8 tile: outputs on the rows).  The terms stream in
+// chunks of 16 through three shared-memory stages filled by cp.async (4 consecutive lanes copy
+// the 4 coefficients of one row: full 32-byte sectors); rows are 16 terms + 8 words of padding,
+// so the 16-byte fragment reads of a warp are free of bank conflicts.
+#define MAC_TC_TMAX 112
+#define MAC_TC_ROW 24                                         // words per staged row (16 terms + pad)
+#define MAC_TC_XS (4 * 32 * MAC_TC_ROW)                       // x stage: [4 n][32 columns][row]
+#define MAC_TC_WS (4 * 16 * MAC_TC_ROW)                       // w stage: [4 n][16 outputs][row]
+#define MAC_TC_STAGES 3
+#define MAC_TC_WD (4 * 8 * 32 * 4 / 2)                       // w digits [4 n][C <= 8][32 lanes][4] u32, in words
+#define MAC_TC_SMEM ((size_t)(MAC_TC_STAGES * (MAC_TC_XS + MAC_TC_WS) + MAC_TC_WD + 4 * 16 + 4 * 32) * 8)
+#define MAC_TC_TAB 20                                         // constants per prime
+
+__device__ __forceinline__ void cp_async8_zfill(u64 *smem, const u64 *gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 8 : 0;   // 0: nothing read, the destination is zero-filled
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+
+// digit a of v0 and of v1 as an fp16 pair (low half v0): (byte | 0x6400) is 1024 + byte in fp16
+__device__ __forceinline__ u32 tc_digits(u64 v0, u64 v1, int a) {
+    const u32 w0 = a < 4 ? (u32)v0 : (u32)(v0 >> 32), w1 = a < 4 ? (u32)v1 : (u32)(v1 >> 32);
+    const u32 p = (__byte_perm(w0, w1, (u32)(a & 3) | ((u32)(4 + (a & 3)) << 8)) & 0x00ff00ffu) | 0x64006400u;
+    u32 r;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(p), "r"(0x64806480u));   // - 1152 = - (1024 + 128)
+    return r;
+}
+
+__device__ __forceinline__ void mma_16816(float *d, const u32 *a, u32 b0, u32 b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// (lo, hi) += s * c, s < 2^32, c < 2^64
+__device__ __forceinline__ void mac_u32(u64 &lo, u64 &hi, u32 s, u64 c) {
+    const u64 pl = (u64)s * (u32)c, ph = (u64)s * (u32)(c >> 32);
+    asm("add.cc.u64 %0, %0, %2;\n\t"
+        "addc.u64 %1, %1, 0;\n\t"
+        "add.cc.u64 %0, %0, %3;\n\t"
+        "addc.u64 %1, %1, %4;"
+        : "+l"(lo), "+l"(hi)
+        : "l"(pl), "l"(ph << 32), "l"(ph >> 32));
+}
+
+template <int C>
+__device__ __forceinline__ void mac_tc_body(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt, u32 O,
+                                            u32 T, u32 BK, u32 lp, u32 l, u32 logn, size_t x_tstride,
+                                            size_t out_ostride, int accumulate, size_t pt_ostride, const PrimeDev &P,
+                                            const u64 *__restrict__ tab, u64 *smem) {
+    constexpr int NS = 2 * C - 1;
+    const u32 N = 1u << logn;
+    const u32 n0 = blockIdx.y * 4, col0 = blockIdx.x * 32;
+    const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const u32 g = lane >> 2, tg = lane & 3, nn = warp >> 2, ct = warp & 3;
+    const u32 nk = (T + 15) / 16;
+    const size_t lstride = (size_t)lp * N;   // one column (or term of pt) to the next
+    u32 *wd = reinterpret_cast<u32 *>(smem + MAC_TC_STAGES * (MAC_TC_XS + MAC_TC_WS));   // [4 n][C][32 lanes][4]
+    u64 *wsum_s = smem + MAC_TC_STAGES * (MAC_TC_XS + MAC_TC_WS) + MAC_TC_WD;          // [4 n][16 o]
+    u64 *xsum_s = wsum_s + 4 * 16;                                                      // [4 n][32 columns]
+
+    // this thread's copies, the same offsets every chunk: x rows (n, col) of terms tid/128 + 4r,
+    // w rows (n, o) of terms tid/64 + 8r
+    const u32 xn = tid & 3, xcol = (tid >> 2) & 31, xt = tid >> 7;
+    const u32 wn = tid & 3, wo = (tid >> 2) & 15, wt = tid >> 6;
+    const bool xok = col0 + xcol < BK, wok = wo < O;
+    const u64 *xsrc = x + (size_t)xt * x_tstride + (size_t)(col0 + xcol) * lstride + (size_t)l * N + n0 + xn;
+    const u64 *wsrc = pt + (size_t)wo * pt_ostride + (size_t)wt * lstride + (size_t)l * N + n0 + wn;
+    const size_t xstep = 4 * x_tstride, wstep = 8 * lstride;
+    auto issue = [&](u32 kc) {
+        u64 *xs = smem + (kc % MAC_TC_STAGES) * (MAC_TC_XS + MAC_TC_WS), *ws = xs + MAC_TC_XS;
+        const u32 t0 = kc * 16;
+        const u64 *xp = xsrc + (size_t)t0 * x_tstride;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const bool ok = xok && t0 + xt + 4 * r < T;
+            cp_async8_zfill(xs + (xn * 32 + xcol) * MAC_TC_ROW + xt + 4 * r, ok ? xp + r * xstep : x, ok);
+        }
+        const u64 *wp = wsrc + (size_t)t0 * lstride;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const bool ok = wok && t0 + wt + 8 * r < T;
+            cp_async8_zfill(ws + (wn * 16 + wo) * MAC_TC_ROW + wt + 8 * r, ok ? wp + r * wstep : pt, ok);
+        }
+    };
+
+    float acc[NS][4];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
+    // 128-bit running sums of the staged rows: threads 0..63 the w rows (n, o), 64..191 the x rows (n, c)
+    u64 slo = 0, shi = 0;
+    // the w digits this thread writes in fragment order: coefficient dn, lane dl, register dr
+    const u32 dn = tid >> 7, dl = (tid >> 2) & 31, dr = tid & 3;
+    const u32 dro = (dl >> 2) + (dr & 1) * 8, drt = 2 * (dl & 3) + (dr >> 1) * 8;
+    issue(0);
+    cp_commit();
+    if (nk > 1) issue(1);
+    cp_commit();
+    for (u32 kc = 0; kc < nk; ++kc) {
+        if (kc + 2 < nk) issue(kc + 2);
+        cp_commit();
+        cp_wait<2>();
+        __syncthreads();   // chunk kc staged; the digits of chunk kc-1 are consumed
+        const u64 *xs = smem + (kc % MAC_TC_STAGES) * (MAC_TC_XS + MAC_TC_WS), *ws = xs + MAC_TC_XS;
+        {   // w digits of this chunk, once per coefficient, in the A-fragment order of every lane
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(ws + (dn * 16 + dro) * MAC_TC_ROW + drt);
+#pragma unroll
+            for (int a = 0; a < C; ++a) wd[((dn * C + a) * 32 + dl) * 4 + dr] = tc_digits(v.x, v.y, a);
+        }
+        if (tid < 192) {
+            const u64 *row = tid < 64 ? ws + tid * MAC_TC_ROW : xs + (tid - 64) * MAC_TC_ROW;
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+                asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(slo), "+l"(shi) : "l"(row[t]));
+        }
+        // B fragments: the digits of x[t][col] for t = 2tg, 2tg+1 (b0) and 2tg+8, 2tg+9 (b1), col = 8ct + g
+        const u64 *xr = xs + (nn * 32 + ct * 8 + g) * MAC_TC_ROW;
+        const ulonglong2 xa = *reinterpret_cast<const ulonglong2 *>(xr + 2 * tg);
+        const ulonglong2 xb = *reinterpret_cast<const ulonglong2 *>(xr + 2 * tg + 8);
+        u32 bf[C][2];
+#pragma unroll
+        for (int b = 0; b < C; ++b) {
+            bf[b][0] = tc_digits(xa.x, xa.y, b);
+            bf[b][1] = tc_digits(xb.x, xb.y, b);
+        }
+        __syncthreads();   // the w digits are written
+#pragma unroll
+        for (int a = 0; a < C; ++a) {
+            const uint4 av = *reinterpret_cast<const uint4 *>(wd + ((nn * C + a) * 32 + lane) * 4);
+            const u32 af[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+            for (int b = 0; b < C; ++b) mma_16816(acc[a + b], af, bf[b][0], bf[b][1]);
+        }
+    }
+    if (tid < 64)
+        wsum_s[tid] = reduce128(slo, shi, P);
+    else if (tid < 192)
+        xsum_s[tid - 64] = reduce128(slo, shi, P);
+    __syncthreads();
+    // u_k = S_k + 2^24 >= 0, three shifts at a time combined in 64 bits (< 2^42) and multiplied by
+    // 2^(8k) mod q into a 128-bit sum (< 5 * 2^103), reduced; then - 2^24 sum_k 2^(8k)
+    // + Cc (sum w + sum x) - T' Cc^2
+    const u64 q = P.q;
+    const u64 tcc2 = mul_mod((u64)(nk * 16) % q, tab[MAC_TC_TAB - 1], P);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const u32 o = g + (e >> 1) * 8, col = col0 + ct * 8 + 2 * tg + (e & 1);
+        if (o >= O || col >= BK) continue;
+        Acc128 sum = {0, 0};
+#pragma unroll
+        for (int k0 = 0; k0 < NS; k0 += 3) {
+            u64 v = 0;
+#pragma unroll
+            for (int j = 2; j >= 0; --j)
+                if (k0 + j < NS) v = (v << 8) + (u64)(u32)(__float2int_rn(acc[k0 + j][e]) + (1 << 24));
+            mac128(sum, v, tab[1 + k0]);
+        }
+        u64 r = sub_mod(reduce128(sum.lo, sum.hi, P), tab[16], q);
+        const u64 sw = add_mod(wsum_s[nn * 16 + o], xsum_s[nn * 32 + (col - col0)], q);
+        r = add_mod(r, mul_shoup(sw, tab[17], tab[18], q), q);
+        r = sub_mod(r, tcc2, q);
+        u64 *dst = out + (size_t)o * out_ostride + (size_t)col * lstride + (size_t)l * N + n0 + nn;
+        if (accumulate) r = add_mod(r, *dst, q);
+        *dst = r;
+    }
+}
+
+__global__ void __launch_bounds__(512, 1) mac_tc_kernel(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt,
+                                                        u32 O, u32 T, u32 BK, u32 lp, u32 l0, u32 logn,
+                                                        size_t x_tstride, size_t out_ostride, u32 lpq, u32 pbase,
+                                                        int accumulate, size_t pt_ostride,
+                                                        const u64 *__restrict__ tctab,
+                                                        const PrimeDev *__restrict__ pd) {
+    extern __shared__ u64 smem[];
+    const u32 l = l0 + blockIdx.z;
+    const u32 p = l < lpq ? l : pbase + (l - lpq);
+    const PrimeDev P = pd[p];
+    const u64 *tab = tctab + (size_t)p * MAC_TC_TAB;
+    switch ((int)tab[0]) {
+#define MAC_TC_CASE(CV)                                                                                            \
+    case CV:                                                                                                       \
+        mac_tc_body<CV>(out, x, pt, O, T, BK, lp, l, logn, x_tstride, out_ostride, accumulate, pt_ostride, P, tab, \
+                        smem);                                                                                     \
+        break;
+        MAC_TC_CASE(1) MAC_TC_CASE(2) MAC_TC_CASE(3) MAC_TC_CASE(4)
+        MAC_TC_CASE(5) MAC_TC_CASE(6) MAC_TC_CASE(7) MAC_TC_CASE(8)
+#undef MAC_TC_CASE
+        default: break;
+    }
+}
+
+// per prime: C (bytes of q), 2^(8k) mod q (k < 15), 2^24 sum_{k<2C-1} 2^(8k) mod q, Cc mod q with
+// its Shoup companion, Cc^2 mod q
+static const u64 *mac_tc_table(Ctx *c) {
+    auto it = c->cache.find("mac_tc");
+    if (it != c->cache.end()) return it->second.p;
+    const size_t np = c->primes.size();
+    std::vector<u64> h(np * MAC_TC_TAB, 0);
+    for (size_t p = 0; p < np; ++p) {
+        const u64 q = c->primes[p];
+        const int bits = 64 - __builtin_clzll(q), C = (bits + 7) / 8;
+        u64 *t = h.data() + p * MAC_TC_TAB;
+        t[0] = (u64)C;
+        unsigned __int128 pw = 1 % q, zs = 0;
+        for (int k = 0; k < 15; ++k) {
+            t[1 + k] = (u64)pw;
+            if (k < 2 * C - 1) zs = (zs + pw) % q;
+            pw = (pw << 8) % q;
+        }
+        t[16] = (u64)(((zs << 24)) % q);
+        unsigned __int128 cc = 0;   // 128 * sum_{a<C} 256^a
+        for (int a = 0; a < C; ++a) cc = (cc << 8) + 128;
+        const u64 ccq = (u64)(cc % q);
+        t[17] = ccq;
+        t[18] = (u64)(((unsigned __int128)ccq << 64) / q);
+        t[19] = (u64)((unsigned __int128)ccq * ccq % q);
+    }
+    return c->const_table("mac_tc", h);
+}
+
+void mac_tc_init() {
+    CUDA_TRY(cudaFuncSetAttribute((const void *)mac_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)MAC_TC_SMEM));
+}
+
+static u32 mac_tc_bytes(const Ctx *c, u32 p) {
+    const int bits = 64 - __builtin_clzll(c->primes[p]);
+    return (u32)(bits + 7) / 8;
+}
+
+// mac() on the tensor cores over the limbs [l0, l0 + nl): groups of at most 16 outputs and
+// MAC_TC_TMAX terms per launch
+static void mac_tc(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O, u32 T,
+                   u32 B, u32 lp, u32 lpq, u32 pbase, int accumulate, size_t pt_ostride, u32 l0, u32 nl) {
+    const u32 BK = 2 * B;
+    if (c->N < 4) throw HeError(HE_EINVAL, "mac: ring too small");
+    const u64 *tab = mac_tc_table(c);
+    for (u32 o0 = 0; o0 < O; o0 += 16) {
+        const u32 oc = std::min<u32>(16, O - o0);
+        for (u32 t0 = 0; t0 < T; t0 += MAC_TC_TMAX) {
+            const u32 tc = std::min<u32>(MAC_TC_TMAX, T - t0);
+            const dim3 grid((BK + 31) / 32, c->N / 4, nl);
+            prof_begin(c);
+            mac_tc_kernel<<<grid, 512, MAC_TC_SMEM, c->stream>>>(
+                out + (size_t)o0 * out_ostride, x + (size_t)t0 * x_tstride,
+                pt + (size_t)o0 * pt_ostride + (size_t)t0 * lp * c->N, oc, tc, BK, lp, l0, c->logn, x_tstride,
+                out_ostride, lpq, pbase, accumulate || t0 > 0, pt_ostride, tab, c->pdev);
+            note_launch(c, "mac", 8.0 * c->N * ((double)oc * tc * nl + (double)tc * B * 2 * nl + (double)oc * B * 2 * nl),
+                        (double)oc * tc * B * 2 * nl * c->N);
+        }
     }
 }
 

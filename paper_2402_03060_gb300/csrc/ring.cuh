@@ -17,6 +17,7 @@ void galois_permute(Ctx *c, u64 *out, const u64 *in, u32 rows, u32 g);
 void tensor_square(Ctx *c, u64 *d, const u64 *a, u32 B, u32 lp);
 void sample_small(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u32 period, u32 lp, u32 pbase, int kind);
 void sample_uniform(Ctx *c, u64 *out, const SeedList &sl, u32 nvec, u32 rows, u32 period, u32 lp, u32 pbase);
+void mac_tc_init();   // once per context: the tensor-core MAC's shared-memory limit
 void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O, u32 T, u32 B,
          u32 lp, u32 lpq = ~0u, u32 pbase = 0, int accumulate = 0, size_t pt_ostride = 0);
 // out[r] (+)= sum_{s<S} a[s*stride_words + r*N ...] over rows r < nrows, prime map (period, lp, pbase)

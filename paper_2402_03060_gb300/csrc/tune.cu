@@ -42,7 +42,7 @@ int ntt_layout(const Ctx *c, int knob) {
 namespace {
 
 const char *knob_name[TUNE_COUNT] = {"ntt_split", "moddown_split", "rescale_split", "mac_group", "lazy_bt",
-                                     "lazy_order", "mac_bk", "mac_split", "comb_bt", "comb_fold"};
+                                     "lazy_order", "mac_bk", "mac_split", "comb_bt", "comb_fold", "mac_tc"};
 
 float time_ms(Ctx *c, const std::function<void()> &f) {
     f();   // warm-up
@@ -190,6 +190,16 @@ void measure(Ctx *c, std::ostringstream &rep) {
         sweep(c, TUNE_MAC_SPLIT, {1, 2}, run, rep);
         rep << ", ";
         sweep(c, TUNE_MAC_BK, {64, 32, 16}, run, rep);
+    }
+    {   // the same outputs over 48 terms: tensor cores or integer units
+        const u32 O = 12, T = 48, Bm = 32;
+        DBuf pt(c, (size_t)O * T * E * N), x(c, (size_t)T * Bm * 2 * E * N), out(c, (size_t)O * Bm * 2 * E * N);
+        CUDA_TRY(cudaMemsetAsync(pt.p, 0, pt.words * 8, c->stream));
+        CUDA_TRY(cudaMemsetAsync(x.p, 0, x.words * 8, c->stream));
+        rep << ", ";
+        sweep(c, TUNE_MAC_TC, {0, 5, 8}, [&] {
+            mac(c, out.p, (size_t)Bm * 2 * E * N, x.p, (size_t)Bm * 2 * E * N, pt.p, O, T, Bm, E, lp, c->L1, 0, 0);
+        }, rep);
     }
     if (beta <= 8) {   // hoisted key-switch accumulation: 16 steps of 64 ciphertexts (a convolution's shape)
         const u32 S = 16, B = 64;

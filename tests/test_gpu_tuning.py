@@ -38,6 +38,12 @@ SETTINGS = [
          comb_bt=2, comb_fold=1),
     dict(ntt_split=2, moddown_split=2, rescale_split=2, mac_group=12, lazy_bt=4, lazy_order=0, mac_bk=64, mac_split=1,
          comb_bt=4, comb_fold=1),
+    # the mask MAC of six or more outputs on the tensor cores: every limb, or the limbs of primes
+    # of at most five bytes (the others on the integer units)
+    dict(ntt_split=2, moddown_split=2, rescale_split=2, mac_group=12, lazy_bt=4, lazy_order=0, mac_bk=64, mac_split=1,
+         comb_bt=4, mac_tc=8),
+    dict(ntt_split=2, moddown_split=2, rescale_split=2, mac_group=8, lazy_bt=2, lazy_order=0, mac_bk=32, mac_split=2,
+         comb_bt=2, mac_tc=5),
 ]
 
 
