@@ -314,8 +314,10 @@ void ntt_forward(Ctx *c, u64 *base, const RowSet &rs);
 void ntt_inverse(Ctx *c, u64 *base, const RowSet &rs);
 // the inner launch of the two-kernel NTT over the rows of rs (ntt_block.cuh)
 void ntt2_inner(Ctx *c, u64 *base, const RowSet &rs, int inverse);
-// dst [B][lp][N] = inverse NTT of limbs 0..lp-1 of B polynomials at src, batch stride src_bstride
-void ntt_inverse_from(Ctx *c, u64 *dst, const u64 *src, size_t src_bstride, u32 B, u32 lp);
+// dst [B][lp][N] = inverse NTT of limbs 0..lp-1 of B polynomials at src, batch stride src_bstride;
+// true when the rows were also copied to the ModUp digits' own rows of own [B][beta][E][N]
+bool ntt_inverse_from(Ctx *c, u64 *dst, const u64 *src, size_t src_bstride, u32 B, u32 lp, u64 *own = nullptr,
+                      u32 beta = 0, u32 E = 0);
 RowSet rows_regular(u32 n, u32 period, u32 lp, u32 pbase);
 RowSet rows_list(Ctx *c, const std::string &key, const std::vector<u32> &packed);
 

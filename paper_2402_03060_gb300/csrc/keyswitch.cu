@@ -299,10 +299,11 @@ __global__ void __launch_bounds__(256, (BT == 4 && MAXD == 8) ? 2 : 3) ks_lazy_p
         const u64 *k0 = ksm + ((s & 1) * 2 + 0) * MAXD * 256 + threadIdx.x;
         const u64 *k1 = ksm + ((s & 1) * 2 + 1) * MAXD * 256 + threadIdx.x;
         const u32 dst = g == 1 ? n : galois_src(n, kl.ginv[s], logn);
+        u64 *os = acc + (((size_t)s * B + b0) * 2 * E + t) * N;   // step s, ciphertext b0
 #pragma unroll
         for (int u = 0; u < BT; ++u) {
             if (b0 + u >= B) break;
-            u64 *o = acc + (((size_t)s * B + b0 + u) * 2 * E + t) * N;
+            u64 *o = os + (size_t)u * 2 * E * N;
             if (g == 1) {
                 o[n] = pc0[u];
                 o[(size_t)E * N + n] = pc1[u];
@@ -972,11 +973,11 @@ void ks_modup(Ctx *c, u64 *D, const u64 *xe, size_t xe_bstride, u32 B, u32 lp) {
     const u32 N = c->N, E = lp + c->K, beta = ks_digits(c, lp);
     if ((size_t)B * beta * E >= (1u << 24)) throw HeError(HE_EINVAL, "ModUp: batch too large for one launch");
     DBuf xc(c, (size_t)B * lp * N);
-    // the eval rows in coefficient form, contiguous
-    ntt_inverse_from(c, xc.p, xe, xe_bstride, B, lp);
+    // the eval rows in coefficient form, contiguous (and copied to the digits' own rows of D as read)
+    const bool own_done = ntt_inverse_from(c, xc.p, xe, xe_bstride, B, lp, D, beta, E);
     const u64 *tab = modup_table(c, lp);
     // own rows: copies of the evaluation-form input
-    {
+    if (!own_done) {
         dim3 grid((N + 255) / 256, lp, B);
         prof_begin(c);
         modup_own_kernel<<<grid, 256, 0, c->stream>>>(D, xe, xe_bstride, lp, c->K, c->alpha, beta, c->logn);

@@ -83,41 +83,56 @@ void ntt2_inner(Ctx *c, u64 *base, const RowSet &rs, int inverse) {
 }
 
 // inner inverse stages of rows read from a strided source: row r = b*lp + t of dst (prime t) is
-// limb t of ciphertext b at src + b*src_bstride + t*N (the c1 rows of a ciphertext batch, say)
+// limb t of ciphertext b at src + b*src_bstride + t*N (the c1 rows of a ciphertext batch, say).
+// With own: each row is also copied as read to the ModUp digits' own row, D[b][t/alpha][t] of
+// D [B][beta][E][N].
 __global__ void __launch_bounds__(NTT2_INNER_THREADS) ntt2_inner_inv_from_kernel(u64 *dst, const u64 *__restrict__ src,
                                                                                  size_t src_bstride, u32 lp,
-                                                                                 const u64 *tw_all,
+                                                                                 u64 *own, u32 alpha, u32 beta,
+                                                                                 u32 E, const u64 *tw_all,
                                                                                  const PrimeDev *pd, int logn) {
     __shared__ u64 sm[1024 + 1024 / 16];
     const u32 N = 1u << logn;
     const u32 r = blockIdx.x, b = r / lp, t = r % lp;
     const u32 goff = 1024u * blockIdx.y;
-    block_load(sm, src + (size_t)b * src_bstride + (size_t)t * N + goff, 1024);
+    const ulonglong2 *g2 = reinterpret_cast<const ulonglong2 *>(src + (size_t)b * src_bstride + (size_t)t * N + goff);
+    ulonglong2 *o2 =
+        own ? reinterpret_cast<ulonglong2 *>(own + (((size_t)b * beta + t / alpha) * E + t) * N + goff) : nullptr;
+    for (u32 k = threadIdx.x; k < 512; k += blockDim.x) {
+        const ulonglong2 v = g2[k];
+        sm[spad(2 * k)] = v.x;
+        sm[spad(2 * k + 1)] = v.y;
+        if (o2) o2[k] = v;
+    }
+    __syncthreads();
     inner_inv_block(sm, logn, tw_all + (size_t)t * 4 * N, pd[t].q, goff);
     block_store(dst + (size_t)r * N + goff, sm, 1024);
 }
 
 // dst [B][lp][N] = inverse NTT of limbs 0..lp-1 of the B ciphertext polynomials at src (batch
-// stride src_bstride words): the two-kernel form reads the rows where they are; the other
-// layouts copy them first
-void ntt_inverse_from(Ctx *c, u64 *dst, const u64 *src, size_t src_bstride, u32 B, u32 lp) {
+// stride src_bstride words): the two-kernel form reads the rows where they are (and, with own,
+// copies them to the ModUp digits' own rows of own [B][beta][E][N]: returns true); the other
+// layouts copy them first (returns false: own untouched)
+bool ntt_inverse_from(Ctx *c, u64 *dst, const u64 *src, size_t src_bstride, u32 B, u32 lp, u64 *own, u32 beta,
+                      u32 E) {
     const RowSet rs = rows_regular(B * lp, lp, lp, 0);
     if (ntt_layout(c, TUNE_NTT) != NTT_TWO_KERNEL) {
         CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)lp * c->N * 8, src, src_bstride * 8, (size_t)lp * c->N * 8, B,
                                    cudaMemcpyDeviceToDevice, c->stream));
         ntt_inverse(c, dst, rs);
-        return;
+        return false;
     }
-    if (rs.n == 0) return;
+    if (rs.n == 0) return own != nullptr;
     if (rs.n > 0x7fffffffu) throw HeError(HE_EINVAL, "NTT: too many rows");
     const double bytes = 16.0 * rs.n * c->N, bfly = (double)rs.n * (c->N / 2);
     prof_begin(c);
     ntt2_inner_inv_from_kernel<<<dim3(rs.n, c->N >> NTT2_INNER_LOGN), NTT2_INNER_THREADS, 0, c->stream>>>(
-        dst, src, src_bstride, lp, (const u64 *)c->tw, (const PrimeDev *)c->pdev, c->logn);
-    note_launch(c, "intt", bytes / 2, bfly * NTT2_INNER_LOGN);
+        dst, src, src_bstride, lp, own, c->alpha, beta, E, (const u64 *)c->tw, (const PrimeDev *)c->pdev, c->logn);
+    note_launch(c, "intt", bytes / 2 + (own ? 8.0 * rs.n * c->N : 0.0), bfly * NTT2_INNER_LOGN);
     prof_begin(c);
     NTT2_OUTER_LAUNCH(c, ntt2_outer_kernel, c->logn, rs.n, dst, rs, (const u64 *)c->tw, (const PrimeDev *)c->pdev, 1);
     note_launch(c, "intt", bytes / 2, bfly * (c->logn - NTT2_INNER_LOGN));
+    return own != nullptr;
 }
 
 static void ntt_launch(Ctx *c, u64 *base, const RowSet &rs, int inverse) {
