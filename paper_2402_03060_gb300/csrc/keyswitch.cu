@@ -324,28 +324,24 @@ __global__ void __launch_bounds__(256, (BT == 4 && MAXD == 8) ? 2 : 3) ks_lazy_p
     }
 }
 
-// A hoisted linear combination accumulated in one pass, with the digits gathered at each step's
-// Galois permutation (the addressing of ks_inner_kernel) instead of one accumulator per step
-// written out and summed by a second kernel:
-//   weighted (w != null): Z[o][b] (+)= sum_{s<S} sum_{i<CH} w[o][s*CH + i] (.) A_s(X_{i*B+b}),  o < O
-//   plain    (w == null): Z[c]    (+)= sum_{s<S} A_s(X_c) for every input ciphertext c < CH*B
+// A weighted hoisted linear combination accumulated in one pass, with the digits gathered at each
+// step's Galois permutation (the addressing of ks_inner_kernel) instead of one accumulator per
+// step written out and summed by a second kernel:
+//   Z[b] (+)= sum_{s<S} sum_{i<CH} w[s*CH + i] (.) A_s(X_{i*B+b})
 // with A_s(X) = (sum_j sigma_g(D_j) (.) ksk_{g,j,0} + P*sigma_g(c0),  sum_j sigma_g(D_j) (.) ksk_{g,j,1})
 // over Q_l u P (A_s = (P*c0, P*c1) for g = 1) -- the accumulators of ks_lazy_kernel, same values.
-// Z [O or CH*B][2][E][N]; w [O][S*CH][E][N] at ostride words per output.  One thread per
-// coefficient of one limb for BT ciphertexts, both polynomials; grid (n-tiles, ciphertext groups,
-// limbs), n-tiles fastest, so the digit rows of a group stay in L2 while their tiles are gathered.
-// The weighted sums are 128-bit lazy (folded every 64 terms), the plain ones reduced per term.
-// OM = 0: the plain form (w must be null), else the weighted form with up to OM outputs.
-// MAXD > 0: at most MAXD digits, unrolled -- a step's key words are loaded once per thread into
-// registers and serve every ciphertext and channel of the thread, and a ciphertext's digit words
-// are all in flight before its products; MAXD = 0: any digit count, one digit at a time.
-template <int OM, int BT, int MAXD>
+// Z [B][2][E][N]; w [S*CH][E][N].  Each step's key sum is reduced (REDC) and multiplied by its
+// weight into a 128-bit sum (folded every 64 terms).  One thread per coefficient of one limb for BT
+// ciphertexts, both polynomials; grid (n-tiles, ciphertext groups, limbs), n-tiles fastest, so the
+// digit rows of a group stay in L2 while their tiles are gathered.  For the combinations of one
+// channel over many ciphertexts ks_comb_lazy_kernel (weights folded into the keys) takes over.
+// MAXD > 0: at most MAXD digits, unrolled; MAXD = 0: any digit count.
+template <int BT, int MAXD>
 __global__ void __launch_bounds__(256, BT == 2 ? 3 : 2) ks_comb_kernel(u64 *__restrict__ Z, const u64 *__restrict__ D,
                                                       const u64 *__restrict__ x, KeyList kl, u32 S, u32 CH, u32 B,
                                                       u32 beta, u32 lp, u32 K, u32 L1, int logn,
-                                                      const u64 *__restrict__ w, u32 O, size_t w_ostride,
-                                                      int accumulate, const u64 *__restrict__ pq,
-                                                      const PrimeDev *__restrict__ pd) {
+                                                      const u64 *__restrict__ w, int accumulate,
+                                                      const u64 *__restrict__ pq, const PrimeDev *__restrict__ pd) {
     const u32 N = 1u << logn;
     const u32 n = blockIdx.x * blockDim.x + threadIdx.x;
     const u32 t = blockIdx.z;
@@ -353,128 +349,88 @@ __global__ void __launch_bounds__(256, BT == 2 ? 3 : 2) ks_comb_kernel(u64 *__re
     const u32 pt = t < lp ? t : L1 + (t - lp);
     const PrimeDev P = pd[pt];
     const size_t kstride = (size_t)(L1 + K) * N;
-    constexpr bool weighted = OM > 0;
-    constexpr int OA = OM > 0 ? OM : 1;
-    constexpr int KD = MAXD > 0 ? MAXD : 1;
-    // the ciphertexts of this thread: weighted -> b = bg*BT + u of every channel; plain -> c = bg*BT + u
-    const u32 nb = weighted ? B : CH * B;
-    const u32 c0 = blockIdx.y * BT;
+    const u32 c0 = blockIdx.y * BT;   // ciphertexts c0 .. c0 + BT - 1 of every channel
     if (n >= N) return;
-    Acc128 zw[weighted ? OA : 1][weighted ? BT : 1][2];
-    u64 zp[weighted ? 1 : BT][2];
+    Acc128 zw[BT][2];
 #pragma unroll
-    for (int o = 0; o < (weighted ? OA : 1); ++o)
-#pragma unroll
-        for (int u = 0; u < (weighted ? BT : 1); ++u) zw[o][u][0] = zw[o][u][1] = Acc128{0, 0};
-#pragma unroll
-    for (int u = 0; u < (weighted ? 1 : BT); ++u) zp[u][0] = zp[u][1] = 0;
-    const u32 nch = weighted ? CH : 1;
+    for (int u = 0; u < BT; ++u) zw[u][0] = zw[u][1] = Acc128{0, 0};
     u32 terms = 0;
     for (u32 s = 0; s < S; ++s) {
         const u32 g = kl.g[s];
         const u32 src = g == 1 ? n : galois_src(n, g, logn);
-        const u64 *key = kl.key[s];
-        u64 k0[KD], k1[KD];
-        if constexpr (MAXD > 0) {
-            if (g != 1) {
-                const u64 *kp = key + (size_t)pt * N + n;
-#pragma unroll
-                for (int j = 0; j < MAXD; ++j) {
-                    k0[j] = j < (int)beta ? __ldg(kp + (size_t)j * 2 * kstride) : 0;
-                    k1[j] = j < (int)beta ? __ldg(kp + (size_t)j * 2 * kstride + kstride) : 0;
-                }
-            }
-        }
-        for (u32 i = 0; i < nch; ++i) {
+        const u64 *kp = g == 1 ? nullptr : kl.key[s] + (size_t)pt * N + n;
+        for (u32 i = 0; i < CH; ++i) {
             u64 a[BT][2];
-#pragma unroll
-            for (int u = 0; u < BT; ++u) {
-                const u32 bb = c0 + u < nb ? c0 + u : nb - 1;      // clamp: duplicates are not stored
-                const u32 ct = weighted ? i * B + bb : bb;
-                const u64 *xb = x + (size_t)ct * 2 * lp * N;
-                if (g == 1) {
-                    a[u][0] = t < lp ? mul_shoup(xb[(size_t)t * N + n], pq[2 * t], pq[2 * t + 1], P.q) : 0;
-                    a[u][1] = t < lp ? mul_shoup(xb[(size_t)(lp + t) * N + n], pq[2 * t], pq[2 * t + 1], P.q) : 0;
-                    continue;
-                }
-                Acc128 s0 = {0, 0}, s1 = {0, 0};
-                const u64 *Db = D + ((size_t)ct * beta * E + t) * N + src;
-                if constexpr (MAXD > 0) {
-                    u64 d[MAXD];
-#pragma unroll
-                    for (int j = 0; j < MAXD; ++j) d[j] = j < (int)beta ? Db[(size_t)j * E * N] : 0;
-#pragma unroll
-                    for (int j = 0; j < MAXD; ++j)
-                        if (j < (int)beta) {
-                            mac128(s0, d[j], k0[j]);
-                            mac128(s1, d[j], k1[j]);
-                        }
-                } else {
-                    for (u32 j = 0; j < beta; ++j) {
-                        const u64 d = Db[(size_t)j * E * N];
-                        const u64 *kj = key + (size_t)j * 2 * kstride + (size_t)pt * N + n;
-                        mac128(s0, d, __ldg(kj));
-                        mac128(s1, d, __ldg(kj + kstride));
-                    }
-                }
-                u64 r0 = redc128(s0.lo, s0.hi, P);   // keys are in Montgomery form
-                if (t < lp) r0 = add_mod(r0, mul_shoup(xb[(size_t)t * N + src], pq[2 * t], pq[2 * t + 1], P.q), P.q);
-                a[u][0] = r0;
-                a[u][1] = redc128(s1.lo, s1.hi, P);
-            }
-        if constexpr (weighted) {
-#pragma unroll
-                for (int o = 0; o < OA; ++o) {
-                    if (o >= (int)O) break;
-                    const u64 wv = __ldg(w + (size_t)o * w_ostride + ((size_t)(s * CH + i) * E + t) * N + n);
-#pragma unroll
-                    for (int u = 0; u < BT; ++u) {
-                        mac128(zw[o][u][0], a[u][0], wv);
-                        mac128(zw[o][u][1], a[u][1], wv);
-                    }
-                }
-                if (++terms == 64) {   // products < 2^122: fold before the 128-bit sums can overflow
-                    terms = 0;
-#pragma unroll
-                    for (int o = 0; o < OA; ++o)
-#pragma unroll
-                        for (int u = 0; u < BT; ++u)
-#pragma unroll
-                            for (int k = 0; k < 2; ++k) zw[o][u][k] = Acc128{reduce128(zw[o][u][k].lo, zw[o][u][k].hi, P), 0};
-                }
-            } else {
+            if (g == 1) {
 #pragma unroll
                 for (int u = 0; u < BT; ++u) {
-                    zp[u][0] = add_mod(zp[u][0], a[u][0], P.q);
-                    zp[u][1] = add_mod(zp[u][1], a[u][1], P.q);
+                    const u32 bb = c0 + u < B ? c0 + u : B - 1;   // clamp: duplicates are not stored
+                    const u64 *xb = x + (size_t)(i * B + bb) * 2 * lp * N;
+                    a[u][0] = t < lp ? mul_shoup(xb[(size_t)t * N + n], pq[2 * t], pq[2 * t + 1], P.q) : 0;
+                    a[u][1] = t < lp ? mul_shoup(xb[(size_t)(lp + t) * N + n], pq[2 * t], pq[2 * t + 1], P.q) : 0;
                 }
+            } else {
+                Acc128 s0[BT], s1[BT];
+                size_t db[BT];   // word offset of each ciphertext's digit 0 at the gathered coefficient
+#pragma unroll
+                for (int u = 0; u < BT; ++u) {
+                    const u32 bb = c0 + u < B ? c0 + u : B - 1;
+                    db[u] = ((size_t)(i * B + bb) * beta * E + t) * N + src;
+                    s0[u] = s1[u] = Acc128{0, 0};
+                }
+                // each key word is loaded once per channel and serves the BT ciphertexts
+                auto digit = [&](u32 j) {
+                    const u64 k0 = __ldg(kp + (size_t)j * 2 * kstride), k1 = __ldg(kp + (size_t)j * 2 * kstride + kstride);
+#pragma unroll
+                    for (int u = 0; u < BT; ++u) {
+                        const u64 d = D[db[u] + (size_t)j * E * N];
+                        mac128(s0[u], d, k0);
+                        mac128(s1[u], d, k1);
+                    }
+                };
+                if constexpr (MAXD > 0) {
+#pragma unroll
+                    for (int j = 0; j < MAXD; ++j)
+                        if (j < (int)beta) digit((u32)j);
+                } else {
+                    for (u32 j = 0; j < beta; ++j) digit(j);
+                }
+#pragma unroll
+                for (int u = 0; u < BT; ++u) {
+                    const u32 bb = c0 + u < B ? c0 + u : B - 1;
+                    const u64 *xb = x + (size_t)(i * B + bb) * 2 * lp * N;
+                    u64 r0 = redc128(s0[u].lo, s0[u].hi, P);   // keys are in Montgomery form
+                    if (t < lp)
+                        r0 = add_mod(r0, mul_shoup(xb[(size_t)t * N + src], pq[2 * t], pq[2 * t + 1], P.q), P.q);
+                    a[u][0] = r0;
+                    a[u][1] = redc128(s1[u].lo, s1[u].hi, P);
+                }
+            }
+            const u64 wv = __ldg(w + ((size_t)(s * CH + i) * E + t) * N + n);
+#pragma unroll
+            for (int u = 0; u < BT; ++u) {
+                mac128(zw[u][0], a[u][0], wv);
+                mac128(zw[u][1], a[u][1], wv);
+            }
+            if (++terms == 64) {   // products < 2^122: fold before the 128-bit sums can overflow
+                terms = 0;
+#pragma unroll
+                for (int u = 0; u < BT; ++u)
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) zw[u][k] = Acc128{reduce128(zw[u][k].lo, zw[u][k].hi, P), 0};
             }
         }
     }
     const size_t zct = (size_t)2 * E * N;   // one output ciphertext over Q_l u P
 #pragma unroll
     for (int u = 0; u < BT; ++u) {
-        if (c0 + u >= nb) break;
-        if constexpr (weighted) {
+        if (c0 + u >= B) break;
+        u64 *zo = Z + (size_t)(c0 + u) * zct + (size_t)t * N + n;
 #pragma unroll
-            for (int o = 0; o < OA; ++o) {
-                if (o >= (int)O) break;
-                u64 *zo = Z + ((size_t)o * B + c0 + u) * zct + (size_t)t * N + n;
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    u64 v = reduce128(zw[o][u][k].lo, zw[o][u][k].hi, P);
-                    if (accumulate) v = add_mod(v, zo[(size_t)k * E * N], P.q);
-                    zo[(size_t)k * E * N] = v;
-                }
-            }
-        } else {
-            u64 *zo = Z + (size_t)(c0 + u) * zct + (size_t)t * N + n;
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                u64 v = zp[u][k];
-                if (accumulate) v = add_mod(v, zo[(size_t)k * E * N], P.q);
-                zo[(size_t)k * E * N] = v;
-            }
+        for (int k = 0; k < 2; ++k) {
+            u64 v = reduce128(zw[u][k].lo, zw[u][k].hi, P);
+            if (accumulate) v = add_mod(v, zo[(size_t)k * E * N], P.q);
+            zo[(size_t)k * E * N] = v;
         }
     }
 }
@@ -1199,9 +1155,8 @@ void ks_comb(Ctx *c, u64 *Z, const u64 *D, const u64 *x, const KeyList &kl, u32 
     }
     prof_begin(c);
 #define COMB_LAUNCH(BTV, MDV)                                                                                   \
-    ks_comb_kernel<1, BTV, MDV><<<grid, 256, 0, c->stream>>>(Z, D, x, kl, S, CH, B, beta, lp, c->K, c->L1,      \
-                                                             c->logn, w, O, w_ostride, accumulate, pmod_table(c), \
-                                                             c->pdev)
+    ks_comb_kernel<BTV, MDV><<<grid, 256, 0, c->stream>>>(Z, D, x, kl, S, CH, B, beta, lp, c->K, c->L1, c->logn,  \
+                                                          w, accumulate, pmod_table(c), c->pdev)
     if (bt == 2) {
         if (md == 4) COMB_LAUNCH(2, 4); else if (md == 8) COMB_LAUNCH(2, 8); else COMB_LAUNCH(2, 0);
     } else {
