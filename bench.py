@@ -136,6 +136,10 @@ def parse():
     ap.add_argument("--ncu-conv", action="store_true",
                     help="small case for full ncu captures: ONE hoisted conv2d layer call (4 -> 12 channels, 5x5, "
                          "8 ciphertexts per channel, N = 16384, top level) between cudaProfilerStart/Stop, then exit")
+    ap.add_argument("--ncu-cts", type=int, default=8, help="ciphertexts per channel of the --ncu-conv case")
+    ap.add_argument("--mac-tc", type=int, default=-1,
+                    help="--ncu-conv: the mac_tc tuning knob (0 integer MAC, 5 the 40-bit limbs on the tensor cores, "
+                         "8 every limb); default: the library's")
     return ap.parse_args()
 
 
@@ -217,7 +221,7 @@ def lenet_setup(G, torch, device, stream, n_samples, keys="step", schedule="fuse
 
 def conv_case(args, local):
     """The second LeNet-1 convolution's shape as one layer call: 25 rotation keys,
-    4 input channels x 8 ciphertexts, 12 output channels (about 2.5 GB on the device),
+    4 input channels x 8 ciphertexts (--ncu-cts), 12 output channels (about 2.5 GB on the device),
     followed by a 2x2 average pooling of the same 4 x 8 ciphertexts (the one-pass
     combination of three rotations and the identity)."""
     import torch
@@ -230,7 +234,9 @@ def conv_case(args, local):
     stream = torch.cuda.Stream()
     ctx = G.Context(seed=W.KEY_SEED, device=local, stream=stream.cuda_stream, **P)
     ctx.keygen(sorted({k + 28 * j for j in range(5) for k in range(5)} - {0}))
-    imgs = W.images(80)
+    if args.mac_tc >= 0:
+        ctx.set_tuning(mac_tc=args.mac_tc)
+    imgs = W.images(SPC * args.ncu_cts)
     cts = [ctx.encrypt(imgs, SPC, 784, W.ENC_SEED + c) for c in range(4)]
     for _ in range(max(args.warmup, 1)):
         ctx.conv2d(cts, w["w"], w["b"])
