@@ -481,18 +481,20 @@ static void mac_int(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x
 // with T' <= MAC_TC_TMAX every partial sum of S_k is an integer below 2^24 in magnitude: the fp32
 // accumulation is exact.  The S_k are assembled in 128-bit integers and reduced mod q.
 //
-// CTA: one limb, 4 consecutive coefficients, 32 columns; 16 warps, warp w takes coefficient
-// w / 4 and the 8-column tile w % 4 (an m16n8 tile: outputs on the rows).  The terms stream in
-// chunks of 16 through three shared-memory stages filled by cp.async (4 consecutive lanes copy
-// the 4 coefficients of one row: full 32-byte sectors); rows are 16 terms + 8 words of padding,
-// so the 16-byte fragment reads of a warp are free of bank conflicts.
+// The masks are decomposed first (mac_tc_prep_kernel): their digits in the A-fragment order of
+// every lane, and sum_t w_t, per coefficient.  CTA of the product: one limb, 4 consecutive
+// coefficients, 32 columns; 16 warps, warp w takes coefficient w / 4 and the 8-column tile w % 4
+// (an m16n8 tile: outputs on the rows) and loads its mask fragments straight from the digit
+// buffer (16 bytes per lane).  The x terms stream in chunks of 16 through three shared-memory
+// stages filled by cp.async (4 consecutive lanes copy the 4 coefficients of one row: full
+// 32-byte sectors), one barrier per chunk; rows are 16 terms + 8 words of padding, so the
+// 16-byte fragment reads of a warp are free of bank conflicts.  The column sums sum_t x_t are
+// taken by the lanes from the words of their own fragments.
 #define MAC_TC_TMAX 112
 #define MAC_TC_ROW 24                                         // words per staged row (16 terms + pad)
 #define MAC_TC_XS (4 * 32 * MAC_TC_ROW)                       // x stage: [4 n][32 columns][row]
-#define MAC_TC_WS (4 * 16 * MAC_TC_ROW)                       // w stage: [4 n][16 outputs][row]
 #define MAC_TC_STAGES 3
-#define MAC_TC_WD (4 * 8 * 32 * 4 / 2)                       // w digits [4 n][C <= 8][32 lanes][4] u32, in words
-#define MAC_TC_SMEM ((size_t)(MAC_TC_STAGES * (MAC_TC_XS + MAC_TC_WS) + MAC_TC_WD + 4 * 16 + 4 * 32) * 8)
+#define MAC_TC_SMEM ((size_t)MAC_TC_STAGES * MAC_TC_XS * 8)
 #define MAC_TC_TAB 20                                         // constants per prime
 
 __device__ __forceinline__ void cp_async8_zfill(u64 *smem, const u64 *gmem, bool valid) {
@@ -528,32 +530,64 @@ __device__ __forceinline__ void mac_u32(u64 &lo, u64 &hi, u32 s, u64 c) {
         : "l"(pl), "l"(ph << 32), "l"(ph >> 32));
 }
 
+// The mask digits of one launch: wd [nl][N/4][nk][4][CS][32 lanes][4] u32 (CS digit slots, C of
+// the limb used) holding, for chunk kc, coefficient n0 + nn and digit a, the A fragment of lane
+// (g, tg): (w[g][t], w[g][t+1]), (w[g+8][t], ..), (w[g][t+8], ..), (w[g+8][t+8], ..), t = 16 kc +
+// 2 tg, zeros beyond O outputs and T terms; wsum [nl][16][N] = sum_t w[o][t] mod q.  Grid
+// (N / 4, nl), 512 threads: thread (nn, lane, reg) = (tid / 128, tid / 4 % 32, tid % 4).
+__global__ void __launch_bounds__(512) mac_tc_prep_kernel(u32 *wd, u64 *wsum, const u64 *__restrict__ pt, u32 O,
+                                                          u32 T, u32 lp, u32 l0, u32 logn, size_t pt_ostride,
+                                                          u32 CS, u32 lpq, u32 pbase, const u64 *__restrict__ tctab,
+                                                          const PrimeDev *__restrict__ pd) {
+    const u32 N = 1u << logn;
+    const u32 nb = blockIdx.x, lr = blockIdx.y, l = l0 + lr, n0 = nb * 4;
+    const u32 p = l < lpq ? l : pbase + (l - lpq);
+    const int C = (int)tctab[(size_t)p * MAC_TC_TAB];
+    const u64 q = pd[p].q;
+    const u32 tid = threadIdx.x, nn = tid >> 7, lane = (tid >> 2) & 31, r = tid & 3;
+    const u32 o = (lane >> 2) + (r & 1) * 8, tr = 2 * (lane & 3) + (r >> 1) * 8;
+    const u32 nk = (T + 15) / 16;
+    const size_t lstride = (size_t)lp * N;
+    const u64 *w = o < O ? pt + (size_t)o * pt_ostride + (size_t)l * N + n0 + nn : pt;
+    u32 *dst = wd + ((size_t)lr * (N / 4) + nb) * nk * 4 * CS * 128 + (nn * CS * 32 + lane) * 4 + r;
+    for (u32 kc = 0; kc < nk; ++kc) {
+        const u32 t = kc * 16 + tr;
+        const u64 v0 = o < O && t < T ? w[(size_t)t * lstride] : 0;
+        const u64 v1 = o < O && t + 1 < T ? w[(size_t)(t + 1) * lstride] : 0;
+        for (int a = 0; a < C; ++a) dst[((size_t)kc * 4 * CS + a) * 128] = tc_digits(v0, v1, a);
+    }
+    if (tid < 64) {   // (o, nn) = (tid % 16, tid / 16)
+        const u32 os = tid & 15, ns = tid >> 4;
+        u64 sum = 0;
+        if (os < O) {
+            const u64 *ws = pt + (size_t)os * pt_ostride + (size_t)l * N + n0 + ns;
+            for (u32 t = 0; t < T; ++t) sum = add_mod(sum, ws[(size_t)t * lstride], q);
+        }
+        wsum[((size_t)lr * 16 + os) * N + n0 + ns] = sum;
+    }
+}
+
 template <int C>
-__device__ __forceinline__ void mac_tc_body(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt, u32 O,
-                                            u32 T, u32 BK, u32 lp, u32 l, u32 logn, size_t x_tstride,
-                                            size_t out_ostride, int accumulate, size_t pt_ostride, const PrimeDev &P,
-                                            const u64 *__restrict__ tab, u64 *smem) {
+__device__ __forceinline__ void mac_tc_body(u64 *out, const u64 *__restrict__ x, const u32 *__restrict__ wd,
+                                            const u64 *__restrict__ wsum, u32 O, u32 T, u32 BK, u32 lp, u32 l,
+                                            u32 lr, u32 logn, size_t x_tstride, size_t out_ostride, u32 CS,
+                                            int accumulate, const PrimeDev &P, const u64 *__restrict__ tab,
+                                            u64 *smem) {
     constexpr int NS = 2 * C - 1;
     const u32 N = 1u << logn;
-    const u32 n0 = blockIdx.y * 4, col0 = blockIdx.x * 32;
+    const u32 nb = blockIdx.y, n0 = nb * 4, col0 = blockIdx.x * 32;
     const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const u32 g = lane >> 2, tg = lane & 3, nn = warp >> 2, ct = warp & 3;
     const u32 nk = (T + 15) / 16;
-    const size_t lstride = (size_t)lp * N;   // one column (or term of pt) to the next
-    u32 *wd = reinterpret_cast<u32 *>(smem + MAC_TC_STAGES * (MAC_TC_XS + MAC_TC_WS));   // [4 n][C][32 lanes][4]
-    u64 *wsum_s = smem + MAC_TC_STAGES * (MAC_TC_XS + MAC_TC_WS) + MAC_TC_WD;          // [4 n][16 o]
-    u64 *xsum_s = wsum_s + 4 * 16;                                                      // [4 n][32 columns]
+    const size_t lstride = (size_t)lp * N;   // one column to the next
 
-    // this thread's copies, the same offsets every chunk: x rows (n, col) of terms tid/128 + 4r,
-    // w rows (n, o) of terms tid/64 + 8r
+    // this thread's copies, the same offsets every chunk: x rows (n, col) of terms tid/128 + 4r
     const u32 xn = tid & 3, xcol = (tid >> 2) & 31, xt = tid >> 7;
-    const u32 wn = tid & 3, wo = (tid >> 2) & 15, wt = tid >> 6;
-    const bool xok = col0 + xcol < BK, wok = wo < O;
+    const bool xok = col0 + xcol < BK;
     const u64 *xsrc = x + (size_t)xt * x_tstride + (size_t)(col0 + xcol) * lstride + (size_t)l * N + n0 + xn;
-    const u64 *wsrc = pt + (size_t)wo * pt_ostride + (size_t)wt * lstride + (size_t)l * N + n0 + wn;
-    const size_t xstep = 4 * x_tstride, wstep = 8 * lstride;
+    const size_t xstep = 4 * x_tstride;
     auto issue = [&](u32 kc) {
-        u64 *xs = smem + (kc % MAC_TC_STAGES) * (MAC_TC_XS + MAC_TC_WS), *ws = xs + MAC_TC_XS;
+        u64 *xs = smem + (kc % MAC_TC_STAGES) * MAC_TC_XS;
         const u32 t0 = kc * 16;
         const u64 *xp = xsrc + (size_t)t0 * x_tstride;
 #pragma unroll
@@ -561,67 +595,54 @@ __device__ __forceinline__ void mac_tc_body(u64 *out, const u64 *__restrict__ x,
             const bool ok = xok && t0 + xt + 4 * r < T;
             cp_async8_zfill(xs + (xn * 32 + xcol) * MAC_TC_ROW + xt + 4 * r, ok ? xp + r * xstep : x, ok);
         }
-        const u64 *wp = wsrc + (size_t)t0 * lstride;
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const bool ok = wok && t0 + wt + 8 * r < T;
-            cp_async8_zfill(ws + (wn * 16 + wo) * MAC_TC_ROW + wt + 8 * r, ok ? wp + r * wstep : pt, ok);
-        }
     };
+    const u32 *wdl = wd + ((size_t)lr * (N / 4) + nb) * nk * 4 * CS * 128 + (nn * CS * 32 + lane) * 4;
 
     float acc[NS][4];
 #pragma unroll
     for (int k = 0; k < NS; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
-    // 128-bit running sums of the staged rows: threads 0..63 the w rows (n, o), 64..191 the x rows (n, c)
-    u64 slo = 0, shi = 0;
-    // the w digits this thread writes in fragment order: coefficient dn, lane dl, register dr
-    const u32 dn = tid >> 7, dl = (tid >> 2) & 31, dr = tid & 3;
-    const u32 dro = (dl >> 2) + (dr & 1) * 8, drt = 2 * (dl & 3) + (dr >> 1) * 8;
+    u64 slo = 0, shi = 0;   // 128-bit sum of this lane's x words: column 8ct + g, four terms a chunk
     issue(0);
     cp_commit();
     if (nk > 1) issue(1);
     cp_commit();
     for (u32 kc = 0; kc < nk; ++kc) {
+        cp_wait<1>();
+        __syncthreads();   // chunk kc staged for every thread; chunk kc-1's stage is free
         if (kc + 2 < nk) issue(kc + 2);
         cp_commit();
-        cp_wait<2>();
-        __syncthreads();   // chunk kc staged; the digits of chunk kc-1 are consumed
-        const u64 *xs = smem + (kc % MAC_TC_STAGES) * (MAC_TC_XS + MAC_TC_WS), *ws = xs + MAC_TC_XS;
-        {   // w digits of this chunk, once per coefficient, in the A-fragment order of every lane
-            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(ws + (dn * 16 + dro) * MAC_TC_ROW + drt);
-#pragma unroll
-            for (int a = 0; a < C; ++a) wd[((dn * C + a) * 32 + dl) * 4 + dr] = tc_digits(v.x, v.y, a);
-        }
-        if (tid < 192) {
-            const u64 *row = tid < 64 ? ws + tid * MAC_TC_ROW : xs + (tid - 64) * MAC_TC_ROW;
-#pragma unroll
-            for (int t = 0; t < 16; ++t)
-                asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(slo), "+l"(shi) : "l"(row[t]));
-        }
+        const u64 *xs = smem + (kc % MAC_TC_STAGES) * MAC_TC_XS;
         // B fragments: the digits of x[t][col] for t = 2tg, 2tg+1 (b0) and 2tg+8, 2tg+9 (b1), col = 8ct + g
         const u64 *xr = xs + (nn * 32 + ct * 8 + g) * MAC_TC_ROW;
         const ulonglong2 xa = *reinterpret_cast<const ulonglong2 *>(xr + 2 * tg);
         const ulonglong2 xb = *reinterpret_cast<const ulonglong2 *>(xr + 2 * tg + 8);
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;\n\t"
+            "add.cc.u64 %0, %0, %3;\n\taddc.u64 %1, %1, 0;\n\t"
+            "add.cc.u64 %0, %0, %4;\n\taddc.u64 %1, %1, 0;\n\t"
+            "add.cc.u64 %0, %0, %5;\n\taddc.u64 %1, %1, 0;"
+            : "+l"(slo), "+l"(shi)
+            : "l"(xa.x), "l"(xa.y), "l"(xb.x), "l"(xb.y));
         u32 bf[C][2];
 #pragma unroll
         for (int b = 0; b < C; ++b) {
             bf[b][0] = tc_digits(xa.x, xa.y, b);
             bf[b][1] = tc_digits(xb.x, xb.y, b);
         }
-        __syncthreads();   // the w digits are written
+        const u32 *wk = wdl + (size_t)kc * 4 * CS * 128;
 #pragma unroll
         for (int a = 0; a < C; ++a) {
-            const uint4 av = *reinterpret_cast<const uint4 *>(wd + ((nn * C + a) * 32 + lane) * 4);
+            const uint4 av = __ldg(reinterpret_cast<const uint4 *>(wk + a * 128));
             const u32 af[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
             for (int b = 0; b < C; ++b) mma_16816(acc[a + b], af, bf[b][0], bf[b][1]);
         }
     }
-    if (tid < 64)
-        wsum_s[tid] = reduce128(slo, shi, P);
-    else if (tid < 192)
-        xsum_s[tid - 64] = reduce128(slo, shi, P);
-    __syncthreads();
+    // column sums: the four lanes of a column (same g) hold its terms; then lane (g, tg) takes
+    // the sums of its output columns 2tg and 2tg + 1 from the lanes that hold them
+    u64 xsum = reduce128(slo, shi, P);
+    xsum = add_mod(xsum, __shfl_xor_sync(0xffffffffu, xsum, 1), P.q);
+    xsum = add_mod(xsum, __shfl_xor_sync(0xffffffffu, xsum, 2), P.q);
+    const u64 xs0 = __shfl_sync(0xffffffffu, xsum, (2 * tg) * 4), xs1 = __shfl_sync(0xffffffffu, xsum, (2 * tg + 1) * 4);
     // u_k = S_k + 2^24 >= 0, three shifts at a time combined in 64 bits (< 2^42) and multiplied by
     // 2^(8k) mod q into a 128-bit sum (< 5 * 2^103), reduced; then - 2^24 sum_k 2^(8k)
     // + Cc (sum w + sum x) - T' Cc^2
@@ -641,7 +662,7 @@ __device__ __forceinline__ void mac_tc_body(u64 *out, const u64 *__restrict__ x,
             mac128(sum, v, tab[1 + k0]);
         }
         u64 r = sub_mod(reduce128(sum.lo, sum.hi, P), tab[16], q);
-        const u64 sw = add_mod(wsum_s[nn * 16 + o], xsum_s[nn * 32 + (col - col0)], q);
+        const u64 sw = add_mod(wsum[((size_t)lr * 16 + o) * N + n0 + nn], (e & 1) ? xs1 : xs0, q);
         r = add_mod(r, mul_shoup(sw, tab[17], tab[18], q), q);
         r = sub_mod(r, tcc2, q);
         u64 *dst = out + (size_t)o * out_ostride + (size_t)col * lstride + (size_t)l * N + n0 + nn;
@@ -650,22 +671,22 @@ __device__ __forceinline__ void mac_tc_body(u64 *out, const u64 *__restrict__ x,
     }
 }
 
-__global__ void __launch_bounds__(512, 1) mac_tc_kernel(u64 *out, const u64 *__restrict__ x, const u64 *__restrict__ pt,
-                                                        u32 O, u32 T, u32 BK, u32 lp, u32 l0, u32 logn,
-                                                        size_t x_tstride, size_t out_ostride, u32 lpq, u32 pbase,
-                                                        int accumulate, size_t pt_ostride,
+__global__ void __launch_bounds__(512, 1) mac_tc_kernel(u64 *out, const u64 *__restrict__ x, const u32 *__restrict__ wd,
+                                                        const u64 *__restrict__ wsum, u32 O, u32 T, u32 BK, u32 lp,
+                                                        u32 l0, u32 logn, size_t x_tstride, size_t out_ostride,
+                                                        u32 CS, u32 lpq, u32 pbase, int accumulate,
                                                         const u64 *__restrict__ tctab,
                                                         const PrimeDev *__restrict__ pd) {
     extern __shared__ u64 smem[];
-    const u32 l = l0 + blockIdx.z;
+    const u32 lr = blockIdx.z, l = l0 + lr;
     const u32 p = l < lpq ? l : pbase + (l - lpq);
     const PrimeDev P = pd[p];
     const u64 *tab = tctab + (size_t)p * MAC_TC_TAB;
     switch ((int)tab[0]) {
-#define MAC_TC_CASE(CV)                                                                                            \
-    case CV:                                                                                                       \
-        mac_tc_body<CV>(out, x, pt, O, T, BK, lp, l, logn, x_tstride, out_ostride, accumulate, pt_ostride, P, tab, \
-                        smem);                                                                                     \
+#define MAC_TC_CASE(CV)                                                                                         \
+    case CV:                                                                                                    \
+        mac_tc_body<CV>(out, x, wd, wsum, O, T, BK, lp, l, lr, logn, x_tstride, out_ostride, CS, accumulate, P, \
+                        tab, smem);                                                                             \
         break;
         MAC_TC_CASE(1) MAC_TC_CASE(2) MAC_TC_CASE(3) MAC_TC_CASE(4)
         MAC_TC_CASE(5) MAC_TC_CASE(6) MAC_TC_CASE(7) MAC_TC_CASE(8)
@@ -714,24 +735,35 @@ static u32 mac_tc_bytes(const Ctx *c, u32 p) {
 }
 
 // mac() on the tensor cores over the limbs [l0, l0 + nl): groups of at most 16 outputs and
-// MAC_TC_TMAX terms per launch
+// MAC_TC_TMAX terms per launch, each launch preceded by the decomposition of its masks
 static void mac_tc(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O, u32 T,
                    u32 B, u32 lp, u32 lpq, u32 pbase, int accumulate, size_t pt_ostride, u32 l0, u32 nl) {
-    const u32 BK = 2 * B;
-    if (c->N < 4) throw HeError(HE_EINVAL, "mac: ring too small");
+    const u32 BK = 2 * B, N = c->N;
+    if (N < 4) throw HeError(HE_EINVAL, "mac: ring too small");
     const u64 *tab = mac_tc_table(c);
+    u32 CS = 1;   // digit slots: the largest prime of the limbs
+    for (u32 l = l0; l < l0 + nl; ++l) CS = std::max(CS, mac_tc_bytes(c, l < lpq ? l : pbase + (l - lpq)));
     for (u32 o0 = 0; o0 < O; o0 += 16) {
         const u32 oc = std::min<u32>(16, O - o0);
         for (u32 t0 = 0; t0 < T; t0 += MAC_TC_TMAX) {
-            const u32 tc = std::min<u32>(MAC_TC_TMAX, T - t0);
-            const dim3 grid((BK + 31) / 32, c->N / 4, nl);
+            const u32 tc = std::min<u32>(MAC_TC_TMAX, T - t0), nk = (tc + 15) / 16;
+            const u64 *ptc = pt + (size_t)o0 * pt_ostride + (size_t)t0 * lp * N;
+            const size_t wd_u32 = (size_t)nl * N * nk * CS * 128;   // [nl][N/4][nk][4][CS][32][4]
+            DBuf wd(c, (wd_u32 + 1) / 2);
+            DBuf ws(c, (size_t)nl * 16 * N);
+            prof_begin(c);
+            mac_tc_prep_kernel<<<dim3(N / 4, nl), 512, 0, c->stream>>>(reinterpret_cast<u32 *>(wd.p), ws.p, ptc, oc,
+                                                                      tc, lp, l0, c->logn, pt_ostride, CS, lpq, pbase,
+                                                                      tab, c->pdev);
+            note_launch(c, "mac_prep", 8.0 * N * ((double)oc * tc * nl + 16.0 * nl) + 4.0 * (double)wd_u32);
+            const dim3 grid((BK + 31) / 32, N / 4, nl);
             prof_begin(c);
             mac_tc_kernel<<<grid, 512, MAC_TC_SMEM, c->stream>>>(
-                out + (size_t)o0 * out_ostride, x + (size_t)t0 * x_tstride,
-                pt + (size_t)o0 * pt_ostride + (size_t)t0 * lp * c->N, oc, tc, BK, lp, l0, c->logn, x_tstride,
-                out_ostride, lpq, pbase, accumulate || t0 > 0, pt_ostride, tab, c->pdev);
-            note_launch(c, "mac", 8.0 * c->N * ((double)oc * tc * nl + (double)tc * B * 2 * nl + (double)oc * B * 2 * nl),
-                        (double)oc * tc * B * 2 * nl * c->N);
+                out + (size_t)o0 * out_ostride, x + (size_t)t0 * x_tstride, reinterpret_cast<const u32 *>(wd.p), ws.p,
+                oc, tc, BK, lp, l0, c->logn, x_tstride, out_ostride, CS, lpq, pbase, accumulate || t0 > 0, tab,
+                c->pdev);
+            note_launch(c, "mac", 8.0 * N * ((double)tc * B * 2 * nl + (double)oc * B * 2 * nl) + 4.0 * (double)wd_u32,
+                        (double)oc * tc * B * 2 * nl * N);
         }
     }
 }
