@@ -1115,6 +1115,8 @@ void ks_comb(Ctx *c, u64 *Z, const u64 *D, const u64 *x, const KeyList &kl, u32 
     const int fold_min = tune_get(c, TUNE_COMB_FOLD, COMB_FOLD_MIN_B);
     const bool fold = weighted && CH == 1 && (int)B >= std::max(1, fold_min);
     if (!weighted || fold) {
+        // one step adds at most beta + 1 products to a 128-bit sum, folded before 63 could overflow it
+        if (beta + 1 > 63) throw HeError(HE_EINVAL, "ks_comb: too many digits for one 128-bit sum");
         DBuf F, PW;
         KeyList kf = kl;
         u32 krow_sp = c->L1;
