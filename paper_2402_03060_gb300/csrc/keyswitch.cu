@@ -1086,8 +1086,11 @@ static void moddown_launch(Ctx *c, u64 *out, u64 *acc, const u64 *addend, size_t
     note_launch(c, "moddown", bytes, bfly * c->logn);
 }
 
-// Z = the hoisted combination of ks_comb_kernel for the steps of kl (at most KEYLIST_MAX); w null:
-// one plain sum per input ciphertext, else one weighted output summed over the CH channels
+// Z = the hoisted combination of the steps of kl (at most KEYLIST_MAX), accumulated in one pass;
+// w null: one plain sum per input ciphertext (ks_comb_lazy_kernel), else one weighted output
+// summed over the CH channels, w [S*CH][E][N] (O must be 1; w_ostride is not used): with one
+// channel and enough ciphertexts the weights are folded into the keys (ks_fold_kernel, then
+// ks_comb_lazy_kernel), otherwise ks_comb_kernel
 void ks_comb(Ctx *c, u64 *Z, const u64 *D, const u64 *x, const KeyList &kl, u32 S, u32 CH, u32 B, u32 lp,
              const u64 *w, u32 O, size_t w_ostride, int accumulate) {
     const u32 N = c->N, E = lp + c->K, beta = ks_digits(c, lp);
