@@ -136,3 +136,42 @@ def test_planner_flatten_variants(lib, case):
     stride, levels, steps = lib.plan(model, Wi, Hi)
     p = olayers.plan(model, Wi, Hi, 1 if Hi == 1 else 2)
     assert stride == p["stride"] and levels == p["levels"] and steps == p["steps"]
+
+
+_NULL_CALLS = r'''
+import ctypes, json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2402_03060_gb300 import _lib
+L = _lib.load()
+out = {}
+for name, (res, args) in sorted(_lib.SIGNATURES.items()):
+    vals = [0.0 if a is ctypes.c_double else
+            0 if a in (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int, ctypes.c_size_t) else None
+            for a in args]
+    r = getattr(L, name)(*vals)
+    out[name] = r if isinstance(r, int) or r is None else repr(r)
+print(json.dumps(out))
+'''
+
+
+def test_every_entry_point_refuses_null_arguments(lib):
+    """Each call of the C ABI with null handles and pointers and zero sizes returns HE_EINVAL (the
+    void teardown calls return, the counters read 0) and crashes nothing -- no GPU needed: the
+    arguments are checked before any device work.  Run in a child process."""
+    import json
+    import subprocess
+    import sys
+    from paper_2402_03060_gb300 import _lib
+    p = subprocess.run([sys.executable, "-c", _NULL_CALLS, ROOT], capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr[-2000:]
+    got = json.loads(p.stdout.strip().splitlines()[-1])
+    assert set(got) == set(_lib.SIGNATURES)
+    for name, r in got.items():
+        if name in ("he_context_destroy", "he_ct_free", "he_model_free", "he_server_destroy"):
+            assert r is None, name
+        elif name == "he_kernel_launches":
+            assert r == 0
+        elif name == "he_last_error":
+            continue
+        else:
+            assert r == _lib.HE_EINVAL, (name, r)
