@@ -371,6 +371,7 @@ void mac_init(Ctx *c) {
         CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
 }
 
+#define MAC_TC_TMAX 112   // terms of one tensor-core MAC launch (the exactness bound below)
 static void mac_tc(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O, u32 T,
                    u32 B, u32 lp, u32 lpq, u32 pbase, int accumulate, size_t pt_ostride, u32 l0, u32 nl);
 static u32 mac_tc_bytes(const Ctx *c, u32 p);
@@ -384,7 +385,8 @@ void mac(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, c
     // Limb l < lpq uses data prime l, limb l >= lpq special prime pbase + l - lpq.
     if (lpq == ~0u) lpq = lp;
     const int tcmax = tune_get(c, TUNE_MAC_TC, 0);   // limbs of at most this many bytes on the tensor cores
-    if (O < 6 || tcmax <= 0) {
+    // the tensor form takes 6 to 16 outputs and at most MAC_TC_TMAX terms (one product launch)
+    if (O < 6 || O > 16 || T > MAC_TC_TMAX || tcmax <= 0) {
         mac_int(c, out, out_ostride, x, x_tstride, pt, O, T, B, lp, lpq, pbase, accumulate, pt_ostride, 0, lp);
         return;
     }
@@ -490,7 +492,6 @@ static void mac_int(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x
 // 32-byte sectors), one barrier per chunk; rows are 16 terms + 8 words of padding, so the
 // 16-byte fragment reads of a warp are free of bank conflicts.  The column sums sum_t x_t are
 // taken by the lanes from the words of their own fragments.
-#define MAC_TC_TMAX 112
 #define MAC_TC_ROW 24                                         // words per staged row (16 terms + pad)
 #define MAC_TC_XS (4 * 32 * MAC_TC_ROW)                       // x stage: [4 n][32 columns][row]
 #define MAC_TC_STAGES 3
@@ -734,38 +735,30 @@ static u32 mac_tc_bytes(const Ctx *c, u32 p) {
     return (u32)(bits + 7) / 8;
 }
 
-// mac() on the tensor cores over the limbs [l0, l0 + nl): groups of at most 16 outputs and
-// MAC_TC_TMAX terms per launch, each launch preceded by the decomposition of its masks
+// mac() on the tensor cores over the limbs [l0, l0 + nl), O <= 16 outputs and T <= MAC_TC_TMAX
+// terms: the decomposition of the masks, then the product
 static void mac_tc(Ctx *c, u64 *out, size_t out_ostride, const u64 *x, size_t x_tstride, const u64 *pt, u32 O, u32 T,
                    u32 B, u32 lp, u32 lpq, u32 pbase, int accumulate, size_t pt_ostride, u32 l0, u32 nl) {
-    const u32 BK = 2 * B, N = c->N;
+    const u32 BK = 2 * B, N = c->N, nk = (T + 15) / 16;
     if (N < 4) throw HeError(HE_EINVAL, "mac: ring too small");
+    if (O > 16 || T > MAC_TC_TMAX) throw HeError(HE_EINVAL, "mac: more outputs or terms than one tensor-core launch");
     const u64 *tab = mac_tc_table(c);
     u32 CS = 1;   // digit slots: the largest prime of the limbs
     for (u32 l = l0; l < l0 + nl; ++l) CS = std::max(CS, mac_tc_bytes(c, l < lpq ? l : pbase + (l - lpq)));
-    for (u32 o0 = 0; o0 < O; o0 += 16) {
-        const u32 oc = std::min<u32>(16, O - o0);
-        for (u32 t0 = 0; t0 < T; t0 += MAC_TC_TMAX) {
-            const u32 tc = std::min<u32>(MAC_TC_TMAX, T - t0), nk = (tc + 15) / 16;
-            const u64 *ptc = pt + (size_t)o0 * pt_ostride + (size_t)t0 * lp * N;
-            const size_t wd_u32 = (size_t)nl * N * nk * CS * 128;   // [nl][N/4][nk][4][CS][32][4]
-            DBuf wd(c, (wd_u32 + 1) / 2);
-            DBuf ws(c, (size_t)nl * 16 * N);
-            prof_begin(c);
-            mac_tc_prep_kernel<<<dim3(N / 4, nl), 512, 0, c->stream>>>(reinterpret_cast<u32 *>(wd.p), ws.p, ptc, oc,
-                                                                      tc, lp, l0, c->logn, pt_ostride, CS, lpq, pbase,
-                                                                      tab, c->pdev);
-            note_launch(c, "mac_prep", 8.0 * N * ((double)oc * tc * nl + 16.0 * nl) + 4.0 * (double)wd_u32);
-            const dim3 grid((BK + 31) / 32, N / 4, nl);
-            prof_begin(c);
-            mac_tc_kernel<<<grid, 512, MAC_TC_SMEM, c->stream>>>(
-                out + (size_t)o0 * out_ostride, x + (size_t)t0 * x_tstride, reinterpret_cast<const u32 *>(wd.p), ws.p,
-                oc, tc, BK, lp, l0, c->logn, x_tstride, out_ostride, CS, lpq, pbase, accumulate || t0 > 0, tab,
-                c->pdev);
-            note_launch(c, "mac", 8.0 * N * ((double)tc * B * 2 * nl + (double)oc * B * 2 * nl) + 4.0 * (double)wd_u32,
-                        (double)oc * tc * B * 2 * nl * N);
-        }
-    }
+    const size_t wd_u32 = (size_t)nl * N * nk * CS * 128;   // [nl][N/4][nk][4][CS][32][4]
+    DBuf wd(c, (wd_u32 + 1) / 2);
+    DBuf ws(c, (size_t)nl * 16 * N);
+    prof_begin(c);
+    mac_tc_prep_kernel<<<dim3(N / 4, nl), 512, 0, c->stream>>>(reinterpret_cast<u32 *>(wd.p), ws.p, pt, O, T, lp, l0,
+                                                              c->logn, pt_ostride, CS, lpq, pbase, tab, c->pdev);
+    note_launch(c, "mac_prep", 8.0 * N * ((double)O * T * nl + 16.0 * nl) + 4.0 * (double)wd_u32);
+    const dim3 grid((BK + 31) / 32, N / 4, nl);
+    prof_begin(c);
+    mac_tc_kernel<<<grid, 512, MAC_TC_SMEM, c->stream>>>(out, x, reinterpret_cast<const u32 *>(wd.p), ws.p, O, T, BK,
+                                                         lp, l0, c->logn, x_tstride, out_ostride, CS, lpq, pbase,
+                                                         accumulate, tab, c->pdev);
+    note_launch(c, "mac", 8.0 * N * ((double)T * B * 2 * nl + (double)O * B * 2 * nl) + 4.0 * (double)wd_u32,
+                (double)O * T * B * 2 * nl * N);
 }
 
 // --------------------------------------------------------------- copies
